@@ -1,0 +1,13 @@
+"""FP64 CPU oracle of FARM relational retrieval.
+
+TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's
+CPU-baseline leg import this package.  The product path (the CUDA library and
+its binding) never does.
+"""
+from .oracle import (ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, OracleParams, build, load,
+                     cosines, ranks, relation, sigmoid, query_all, query_bounds, batch,
+                     topk, num_threads)
+
+__all__ = ["ABOVE", "BELOW", "LEFT_OF", "RIGHT_OF", "NEAR", "OracleParams", "build", "load",
+           "cosines", "ranks", "relation", "sigmoid", "query_all", "query_bounds", "batch",
+           "topk", "num_threads"]

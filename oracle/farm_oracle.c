@@ -1,0 +1,541 @@
+/*
+ * farm_oracle.c -- plain FP64 CPU oracle of FARM's query-time relational
+ * retrieval ("Find Anything using Relational Spatial Memory").
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the package's smoke check and the
+ * CPU-baseline leg of the benchmark load this library.  It shares no code,
+ * header, helper or constant table with the CUDA path, and the product path
+ * never calls it.
+ *
+ * It evaluates the method's plain definition over all N objects, with no
+ * pruning, blocking or reordering beyond what the definition states:
+ *
+ *   score(e; q, M) = max over bindings eta with eta(x*) = e of Verify(eta),
+ *   y_hat = TopK_e score(e)                                (Sec. 2.3; App. B)
+ *
+ * with Verify = Agg as given in App. D.2 step 5 ("Composite scoring") and in
+ * the "Why soft, not hard?" paragraph:
+ *
+ *   s(e) = s_sem(e) * [(1 - w) + w * gbar(e)],   gbar = geometric mean of the
+ *   predicate scores t_i(e),  w = 0.5, s_sem scaled by 0.3 on a class mismatch.
+ *
+ * Because Agg is non-decreasing in every t_i and the anchors of a star-shaped
+ * query are independent once the target is fixed, the best binding takes each
+ * anchor's best witness separately (App. B, "Query-time complexity"):
+ * t_i(e) = max over a in L_i, a != e of r_rho_i(e, a).
+ *
+ * The steps, in the order the paper gives them (App. D.2 steps 3-5):
+ *  1. cos_ij = <u_i/|u_i|, d_j/|d_j|> for the target row (i = 0) and every
+ *     constraint's landmark row (App. D.2 step 3, one embedding channel).
+ *  2. rank_i(j) = 1 + #{j' : cos_ij' > cos_ij, or equal and j' < j}.
+ *  3. s_sem(j) = cf(j) / (mu + rank_0(j)), mu = 5, one reciprocal-rank-fusion
+ *     channel of weight 1; cf = class_mis if the query names a target class
+ *     and c_j differs from it, else 1 (App. D.2 steps 3 and 5).
+ *  4. L_i = the K_a objects of smallest rank_i ("landmarks are bound greedily
+ *     to their top-scoring candidates", App. D.2 step 4).
+ *  5. Closed-form relation scores over the object geometry (App. D.2 step 4):
+ *       above(e,a) = sig((z_e - z_a)/tau_v), below(e,a) = sig((z_a - z_e)/tau_v)
+ *       near(e,a)  = exp(-|p_e - p_a|^2 / (2 sigma_near^2)), sigma_near = 0.5 m
+ *       left_of / right_of: evaluated in the stored views of the target
+ *       candidate e; per view the horizontal image-plane coordinate
+ *       u = X/Z of each centre (X along the camera's right vector f x z_up,
+ *       Z along the viewing direction f); a view counts when both depths
+ *       exceed z_min; left_of = mean over counted views of
+ *       sig((u_a - u_e)/tau_h), right_of = mean of sig((u_e - u_a)/tau_h);
+ *       0.5 when no view counts.
+ *  6. t_i(e) = max_{a in L_i, a != e} r_rho_i(e, a), 0 without a witness; the
+ *     bound anchor is the argmax (lower object index on ties).
+ *  7. gbar = (prod_i t_i)^(1/m) (0 if some t_i = 0, 1 if m = 0);
+ *     s = s_sem * ((1 - w) + w * gbar).
+ *  8. TopK by s descending, lower object index first on ties.
+ *
+ * Readings where the paper is silent (the same list is kept with the design
+ * notes): one retrieval channel; Gaussian Near (App. D.2) rather than the
+ * Hellinger wording of Sec. 2.3; box centres stand in for Gaussian means and
+ * mask centroids; mean over views; the constants tau_v, tau_h, z_min are
+ * parameters; a landmark may not be the target itself; ties go to the lower
+ * object index.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_ABOVE 0
+#define ORC_BELOW 1
+#define ORC_LEFT_OF 2
+#define ORC_RIGHT_OF 3
+#define ORC_NEAR 4
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOMEM -2
+
+typedef struct {
+    double mu;          /* reciprocal-rank offset (5) */
+    double w;           /* blend weight (0.5) */
+    double class_mis;   /* class-mismatch factor (0.3) */
+    double sigma_near;  /* Near Gaussian width, metres (0.5) */
+    double tau_v;       /* Above/Below sigmoid scale, metres */
+    double tau_h;       /* LeftOf/RightOf sigmoid scale, image units */
+    double z_min;       /* minimum camera depth for a view to count, metres */
+    int64_t k_anchor;   /* landmark candidates per constraint (K_a) */
+} orc_params;
+
+typedef struct {
+    int64_t n;
+    int64_t dim;
+    const float *desc;   /* [n, dim] */
+    const int32_t *cls;  /* [n] */
+    const float *box;    /* [6, n]: cx, cy, cz, sx, sy, sz */
+    int64_t n_views;
+    const float *views;  /* [6, n_views, n]: ox, oy, oz, fx, fy, fz */
+} orc_scene;
+
+/* ------------------------------------------------------------------ */
+/* Elementary pieces                                                   */
+/* ------------------------------------------------------------------ */
+
+double orc_sigmoid(double x)
+{
+    if (x >= 0.0) {
+        return 1.0 / (1.0 + exp(-x));
+    }
+    double ex = exp(x);
+    return ex / (1.0 + ex);
+}
+
+static double center(const orc_scene *s, int axis, int64_t j)
+{
+    return (double)s->box[(int64_t)axis * s->n + j];
+}
+
+static double view_comp(const orc_scene *s, int comp, int64_t v, int64_t j)
+{
+    return (double)s->views[((int64_t)comp * s->n_views + v) * s->n + j];
+}
+
+/* Left/right in the stored views of e (step 5).  sign = +1 for left_of,
+ * -1 for right_of. */
+static double viewpoint_lr(const orc_scene *s, const orc_params *p, int64_t e,
+                           int64_t a, double sign)
+{
+    double acc = 0.0;
+    int64_t counted = 0;
+    for (int64_t v = 0; v < s->n_views; ++v) {
+        double ox = view_comp(s, 0, v, e), oy = view_comp(s, 1, v, e), oz = view_comp(s, 2, v, e);
+        double fx = view_comp(s, 3, v, e), fy = view_comp(s, 4, v, e), fz = view_comp(s, 5, v, e);
+        double fn = sqrt(fx * fx + fy * fy + fz * fz);
+        if (!(fn > 0.0)) continue;
+        fx /= fn; fy /= fn; fz /= fn;
+        /* right vector r = f x z_up = (fy, -fx, 0), normalised */
+        double rx = fy, ry = -fx;
+        double rn = sqrt(rx * rx + ry * ry);
+        if (!(rn > 0.0)) continue;  /* camera looking straight up or down */
+        rx /= rn; ry /= rn;
+        double dex = center(s, 0, e) - ox, dey = center(s, 1, e) - oy, dez = center(s, 2, e) - oz;
+        double dax = center(s, 0, a) - ox, day = center(s, 1, a) - oy, daz = center(s, 2, a) - oz;
+        double Ze = dex * fx + dey * fy + dez * fz;
+        double Za = dax * fx + day * fy + daz * fz;
+        if (!(Ze > p->z_min && Za > p->z_min)) continue;
+        double Xe = dex * rx + dey * ry;
+        double Xa = dax * rx + day * ry;
+        double ue = Xe / Ze, ua = Xa / Za;
+        acc += orc_sigmoid(sign * (ua - ue) / p->tau_h);
+        counted += 1;
+    }
+    if (counted == 0) return 0.5;
+    return acc / (double)counted;
+}
+
+/* r_rho(e, a): the soft relation score of predicate `pred` with e as the
+ * target-side argument and a as the anchor (App. D.2 step 4). */
+double orc_relation(const orc_scene *s, const orc_params *p, int32_t pred,
+                    int64_t e, int64_t a)
+{
+    double dz = center(s, 2, e) - center(s, 2, a);
+    switch (pred) {
+    case ORC_ABOVE:
+        return orc_sigmoid(dz / p->tau_v);
+    case ORC_BELOW:
+        return orc_sigmoid(-dz / p->tau_v);
+    case ORC_NEAR: {
+        double dx = center(s, 0, e) - center(s, 0, a);
+        double dy = center(s, 1, e) - center(s, 1, a);
+        double d2 = dx * dx + dy * dy + dz * dz;
+        return exp(-d2 / (2.0 * p->sigma_near * p->sigma_near));
+    }
+    case ORC_LEFT_OF:
+        return viewpoint_lr(s, p, e, a, +1.0);
+    case ORC_RIGHT_OF:
+        return viewpoint_lr(s, p, e, a, -1.0);
+    default:
+        return NAN;
+    }
+}
+
+/* Step 1: cosine of embedding u against every descriptor, all in FP64.
+ * Returns ORC_EINVAL when u or a descriptor has zero or non-finite norm. */
+int orc_cosines(const orc_scene *s, const float *u, double *out)
+{
+    double un = 0.0;
+    for (int64_t k = 0; k < s->dim; ++k) un += (double)u[k] * (double)u[k];
+    un = sqrt(un);
+    if (!(un > 0.0) || !isfinite(un)) return ORC_EINVAL;
+    for (int64_t j = 0; j < s->n; ++j) {
+        const float *d = s->desc + j * s->dim;
+        double dot = 0.0, dn = 0.0;
+        for (int64_t k = 0; k < s->dim; ++k) {
+            dot += (double)u[k] * (double)d[k];
+            dn += (double)d[k] * (double)d[k];
+        }
+        dn = sqrt(dn);
+        if (!(dn > 0.0) || !isfinite(dn)) return ORC_EINVAL;
+        out[j] = dot / (un * dn);
+    }
+    return ORC_OK;
+}
+
+/* Order: larger value first, lower index first among equal values. */
+static int before(const double *c, int64_t a, int64_t b)
+{
+    if (c[a] > c[b]) return 1;
+    if (c[a] < c[b]) return 0;
+    return a < b;
+}
+
+/* Stable merge sort of indices by `before`. */
+static void sort_by_value(int64_t n, const double *c, int64_t *idx, int64_t *tmp)
+{
+    for (int64_t i = 0; i < n; ++i) idx[i] = i;
+    for (int64_t width = 1; width < n; width *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * width) {
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int64_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) tmp[k++] = before(c, idx[j], idx[i]) ? idx[j++] : idx[i++];
+            while (i < mid) tmp[k++] = idx[i++];
+            while (j < hi) tmp[k++] = idx[j++];
+        }
+        memcpy(idx, tmp, (size_t)n * sizeof(int64_t));
+    }
+}
+
+/* Step 2: 1-based ranks.  rank[j] = 1 + #{j' : c[j'] > c[j] or (== and j' < j)}. */
+int orc_ranks(int64_t n, const double *c, int64_t *rank)
+{
+    int64_t *idx = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *tmp = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!idx || !tmp) { free(idx); free(tmp); return ORC_ENOMEM; }
+    sort_by_value(n, c, idx, tmp);
+    for (int64_t r = 0; r < n; ++r) rank[idx[r]] = r + 1;
+    free(idx);
+    free(tmp);
+    return ORC_OK;
+}
+
+/* Step 7 for one candidate. */
+static double compose(const orc_params *p, double s_sem, int32_t m, const double *t)
+{
+    double gbar;
+    if (m == 0) {
+        gbar = 1.0;
+    } else {
+        double lsum = 0.0;
+        int zero = 0;
+        for (int32_t i = 0; i < m; ++i) {
+            if (!(t[i] > 0.0)) { zero = 1; break; }
+            lsum += log(t[i]);
+        }
+        gbar = zero ? 0.0 : exp(lsum / (double)m);
+    }
+    return s_sem * ((1.0 - p->w) + p->w * gbar);
+}
+
+static double class_factor(const orc_scene *s, const orc_params *p, int32_t c_t, int64_t j)
+{
+    return (c_t >= 0 && s->cls[j] != c_t) ? p->class_mis : 1.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* One query, every object: steps 1-7 with all intermediates exposed.  */
+/* ------------------------------------------------------------------ */
+
+/*
+ * u0: target embedding [dim]; c_t: target class (-1 none); m constraints with
+ * predicates preds[m] and landmark embeddings u_c[m, dim].
+ * Outputs (all length n, or m*n for per-constraint arrays; any may be NULL):
+ *   cos0, rank0, s_sem, t[i*n + e], anchor[i*n + e] (-1 without a witness),
+ *   s (composite score).
+ */
+int orc_query_all(const orc_scene *s, const orc_params *p, const float *u0, int32_t c_t,
+                  int32_t m, const int32_t *preds, const float *u_c,
+                  double *cos0_out, int64_t *rank0_out, double *s_sem_out,
+                  double *t_out, int64_t *anchor_out, double *s_out)
+{
+    int64_t n = s->n;
+    if (n <= 0 || m < 0 || m > 64 || p->k_anchor < 1) return ORC_EINVAL;
+    int rc = ORC_OK;
+    double *cos = (double *)malloc((size_t)n * sizeof(double));
+    int64_t *rank = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    double *t = (double *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(double));
+    int64_t *anc = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(int64_t));
+    int64_t *lm = (int64_t *)malloc((size_t)p->k_anchor * sizeof(int64_t));
+    double *ssem = (double *)malloc((size_t)n * sizeof(double));
+    if (!cos || !rank || !t || !anc || !lm || !ssem) { rc = ORC_ENOMEM; goto done; }
+
+    /* Steps 1-3 for the target row. */
+    if ((rc = orc_cosines(s, u0, cos)) != ORC_OK) goto done;
+    if ((rc = orc_ranks(n, cos, rank)) != ORC_OK) goto done;
+    for (int64_t j = 0; j < n; ++j) {
+        ssem[j] = class_factor(s, p, c_t, j) / (p->mu + (double)rank[j]);
+        if (cos0_out) cos0_out[j] = cos[j];
+        if (rank0_out) rank0_out[j] = rank[j];
+        if (s_sem_out) s_sem_out[j] = ssem[j];
+    }
+
+    /* Steps 1, 2, 4, 5, 6 for every constraint. */
+    for (int32_t i = 0; i < m; ++i) {
+        if ((rc = orc_cosines(s, u_c + (int64_t)i * s->dim, cos)) != ORC_OK) goto done;
+        if ((rc = orc_ranks(n, cos, rank)) != ORC_OK) goto done;
+        int64_t n_lm = 0;
+        /* L_i in rank order: walk ranks 1..K_a. */
+        int64_t ka = p->k_anchor < n ? p->k_anchor : n;
+        for (int64_t r = 1; r <= ka; ++r)
+            for (int64_t j = 0; j < n; ++j)
+                if (rank[j] == r) { lm[n_lm++] = j; break; }
+        for (int64_t e = 0; e < n; ++e) {
+            double best = 0.0;
+            int64_t arg = -1;
+            for (int64_t l = 0; l < n_lm; ++l) {
+                int64_t a = lm[l];
+                if (a == e) continue;
+                double r = orc_relation(s, p, preds[i], e, a);
+                if (arg < 0 || r > best || (r == best && a < arg)) { best = r; arg = a; }
+            }
+            t[(int64_t)i * n + e] = arg < 0 ? 0.0 : best;
+            anc[(int64_t)i * n + e] = arg;
+        }
+    }
+
+    /* Step 7. */
+    for (int64_t e = 0; e < n; ++e) {
+        double te[64];
+        for (int32_t i = 0; i < m; ++i) te[i] = t[(int64_t)i * n + e];
+        double sc = compose(p, ssem[e], m, te);
+        if (s_out) s_out[e] = sc;
+    }
+    if (t_out) memcpy(t_out, t, (size_t)m * (size_t)n * sizeof(double));
+    if (anchor_out) memcpy(anchor_out, anc, (size_t)m * (size_t)n * sizeof(int64_t));
+done:
+    free(cos); free(rank); free(t); free(anc); free(lm); free(ssem);
+    return rc;
+}
+
+/* Step 8: the k largest of s (lower index first on ties). */
+int orc_topk(int64_t n, const double *s, int64_t k, int64_t *idx_out)
+{
+    if (k < 0 || k > n) return ORC_EINVAL;
+    int64_t *idx = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *tmp = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!idx || !tmp) { free(idx); free(tmp); return ORC_ENOMEM; }
+    sort_by_value(n, s, idx, tmp);
+    for (int64_t r = 0; r < k; ++r) idx_out[r] = idx[r];
+    free(idx);
+    free(tmp);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* A batch of queries on one scene (OpenMP over queries).              */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Queries in CSR form: query q has constraints c_off[q] .. c_off[q+1]-1 with
+ * predicates c_pred[] and landmark embeddings c_emb[c, dim].
+ * Outputs per query (k entries): out_idx, out_score; per entry and constraint
+ * slot (4 slots, -1 beyond m): out_t, out_anchor.  n_threads <= 0 uses the
+ * OpenMP default.  Returns the first failing query's code.
+ */
+int orc_batch(const orc_scene *s, const orc_params *p, int64_t n_q, const float *tgt_emb,
+              const int32_t *tgt_cls, const int32_t *c_off, const int32_t *c_pred,
+              const float *c_emb, int64_t k, int64_t *out_idx, double *out_score,
+              double *out_t, int64_t *out_anchor, int32_t n_threads)
+{
+    int64_t n = s->n;
+    if (k < 1 || k > n) return ORC_EINVAL;
+    for (int64_t q = 0; q < n_q; ++q) {
+        int32_t m = c_off[q + 1] - c_off[q];
+        if (m < 0 || m > 4) return ORC_EINVAL;
+    }
+    int rc_all = ORC_OK;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t q = 0; q < n_q; ++q) {
+        int32_t m = c_off[q + 1] - c_off[q];
+        double *sc = (double *)malloc((size_t)n * sizeof(double));
+        double *t = (double *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(double));
+        int64_t *anc = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(int64_t));
+        int64_t *top = (int64_t *)malloc((size_t)k * sizeof(int64_t));
+        int rc = (sc && t && anc && top) ? ORC_OK : ORC_ENOMEM;
+        if (rc == ORC_OK)
+            rc = orc_query_all(s, p, tgt_emb + q * s->dim, tgt_cls[q], m, c_pred + c_off[q],
+                               c_emb + (int64_t)c_off[q] * s->dim, NULL, NULL, NULL, t, anc, sc);
+        if (rc == ORC_OK) rc = orc_topk(n, sc, k, top);
+        if (rc == ORC_OK) {
+            for (int64_t r = 0; r < k; ++r) {
+                int64_t e = top[r];
+                out_idx[q * k + r] = e;
+                out_score[q * k + r] = sc[e];
+                for (int32_t i = 0; i < 4; ++i) {
+                    if (out_t) out_t[(q * k + r) * 4 + i] = i < m ? t[(int64_t)i * n + e] : -1.0;
+                    if (out_anchor) out_anchor[(q * k + r) * 4 + i] = i < m ? anc[(int64_t)i * n + e] : -1;
+                }
+            }
+        }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        {
+            if (rc != ORC_OK && rc_all == ORC_OK) rc_all = rc;
+        }
+        free(sc); free(t); free(anc); free(top);
+    }
+    return rc_all;
+}
+
+/* ------------------------------------------------------------------ */
+/* Tie-tolerant bounds: what any valid result may score.               */
+/* ------------------------------------------------------------------ */
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* #{v in sorted ascending a[0..n) : v > x} */
+static int64_t count_greater(const double *a, int64_t n, double x)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] > x) hi = mid; else lo = mid + 1;
+    }
+    return n - lo;
+}
+
+/* #{v : v >= x} */
+static int64_t count_geq(const double *a, int64_t n, double x)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] >= x) hi = mid; else lo = mid + 1;
+    }
+    return n - lo;
+}
+
+/*
+ * When two cosines differ by at most tau, an implementation whose cosines are
+ * within tau/2 of the exact ones may order them either way.  For every object
+ * this gives the range of ranks it can take,
+ *   rank_lo(j) = 1 + #{j' : c_j' > c_j + tau},  rank_hi(j) = #{j' : c_j' >= c_j - tau},
+ * and from them, because every later step is monotone, bounds on what any
+ * such implementation can return:
+ *   s_sem in [cf/(mu + rank_hi), cf/(mu + rank_lo)];
+ *   L_i contains D_i = {a : rank_hi_i(a) <= K_a} and lies in P_i = {a : rank_lo_i(a) <= K_a};
+ *   t_i(e) in [max over D_i \ {e}, max over P_i \ {e}];  s in [s_lo, s_hi].
+ * With tau = 0 on tie-free data every interval is a single point equal to
+ * orc_query_all's result.
+ * Outputs (length n; per-constraint arrays m*n; any may be NULL):
+ *   s_lo, s_hi, t_lo, t_hi, rank_lo0, rank_hi0, and in_p[i*n + a] = 1 when a
+ *   lies in P_i (a valid bound anchor).
+ */
+int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, int32_t c_t,
+                     int32_t m, const int32_t *preds, const float *u_c, double tau,
+                     double *s_lo, double *s_hi, double *t_lo_out, double *t_hi_out,
+                     int64_t *rank_lo0, int64_t *rank_hi0, int8_t *in_p_out)
+{
+    int64_t n = s->n;
+    if (n <= 0 || m < 0 || m > 64 || !(tau >= 0.0)) return ORC_EINVAL;
+    int rc = ORC_OK;
+    double *cos = (double *)malloc((size_t)n * sizeof(double));
+    double *sorted = (double *)malloc((size_t)n * sizeof(double));
+    double *slo = (double *)malloc((size_t)n * sizeof(double));
+    double *shi = (double *)malloc((size_t)n * sizeof(double));
+    double *tlo = (double *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(double));
+    double *thi = (double *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(double));
+    int8_t *in_d = (int8_t *)malloc((size_t)n);
+    int8_t *in_p = (int8_t *)malloc((size_t)n);
+    int64_t *plist = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!cos || !sorted || !slo || !shi || !tlo || !thi || !in_d || !in_p || !plist) { rc = ORC_ENOMEM; goto done; }
+
+    if ((rc = orc_cosines(s, u0, cos)) != ORC_OK) goto done;
+    memcpy(sorted, cos, (size_t)n * sizeof(double));
+    qsort(sorted, (size_t)n, sizeof(double), cmp_double);
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t rlo = 1 + count_greater(sorted, n, cos[j] + tau);
+        int64_t rhi = count_geq(sorted, n, cos[j] - tau);
+        double cf = class_factor(s, p, c_t, j);
+        slo[j] = cf / (p->mu + (double)rhi);
+        shi[j] = cf / (p->mu + (double)rlo);
+        if (rank_lo0) rank_lo0[j] = rlo;
+        if (rank_hi0) rank_hi0[j] = rhi;
+    }
+    for (int32_t i = 0; i < m; ++i) {
+        if ((rc = orc_cosines(s, u_c + (int64_t)i * s->dim, cos)) != ORC_OK) goto done;
+        memcpy(sorted, cos, (size_t)n * sizeof(double));
+        qsort(sorted, (size_t)n, sizeof(double), cmp_double);
+        for (int64_t a = 0; a < n; ++a) {
+            int64_t rlo = 1 + count_greater(sorted, n, cos[a] + tau);
+            int64_t rhi = count_geq(sorted, n, cos[a] - tau);
+            in_d[a] = rhi <= p->k_anchor;
+            in_p[a] = rlo <= p->k_anchor;
+            if (in_p_out) in_p_out[(int64_t)i * n + a] = in_p[a];
+        }
+        int64_t n_p = 0;
+        for (int64_t a = 0; a < n; ++a)
+            if (in_p[a]) plist[n_p++] = a;
+        for (int64_t e = 0; e < n; ++e) {
+            double lo = 0.0, hi = 0.0;
+            for (int64_t l = 0; l < n_p; ++l) {
+                int64_t a = plist[l];
+                if (a == e) continue;
+                double r = orc_relation(s, p, preds[i], e, a);
+                if (r > hi) hi = r;
+                if (in_d[a] && r > lo) lo = r;
+            }
+            tlo[(int64_t)i * n + e] = lo;
+            thi[(int64_t)i * n + e] = hi;
+        }
+    }
+    for (int64_t e = 0; e < n; ++e) {
+        double te[64];
+        for (int32_t i = 0; i < m; ++i) te[i] = tlo[(int64_t)i * n + e];
+        double a = compose(p, slo[e], m, te);
+        for (int32_t i = 0; i < m; ++i) te[i] = thi[(int64_t)i * n + e];
+        double b = compose(p, shi[e], m, te);
+        if (s_lo) s_lo[e] = a;
+        if (s_hi) s_hi[e] = b;
+    }
+    if (t_lo_out) memcpy(t_lo_out, tlo, (size_t)m * (size_t)n * sizeof(double));
+    if (t_hi_out) memcpy(t_hi_out, thi, (size_t)m * (size_t)n * sizeof(double));
+done:
+    free(cos); free(sorted); free(slo); free(shi); free(tlo); free(thi); free(in_d); free(in_p); free(plist);
+    return rc;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,212 @@
+"""ctypes binding of the FP64 oracle in farm_oracle.c (test infrastructure).
+
+`build()` compiles the C file with gcc (OpenMP) into oracle/_build/; every
+function below marshals numpy arrays into the C calls and nothing else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "farm_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+
+ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR = range(5)
+
+
+@dataclasses.dataclass
+class OracleParams:
+    """The method's constants (App. D.2): RRF offset mu = 5, blend weight
+    w = 0.5, class-mismatch factor 0.3, Near width 0.5 m; tau_v, tau_h and
+    z_min are not given by the paper (readings)."""
+    mu: float = 5.0
+    w: float = 0.5
+    class_mis: float = 0.3
+    sigma_near: float = 0.5
+    tau_v: float = 0.25
+    tau_h: float = 0.10
+    z_min: float = 0.05
+    k_anchor: int = 16
+
+
+class _Params(C.Structure):
+    _fields_ = [("mu", C.c_double), ("w", C.c_double), ("class_mis", C.c_double),
+                ("sigma_near", C.c_double), ("tau_v", C.c_double), ("tau_h", C.c_double),
+                ("z_min", C.c_double), ("k_anchor", C.c_int64)]
+
+
+class _Scene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("dim", C.c_int64), ("desc", C.c_void_p),
+                ("cls", C.c_void_p), ("box", C.c_void_p), ("n_views", C.c_int64),
+                ("views", C.c_void_p)]
+
+
+def build(force: bool = False) -> str:
+    """Compile farm_oracle.c into a shared library (gcc, -O2, OpenMP)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P = C.c_void_p
+        lib.orc_sigmoid.restype = C.c_double
+        lib.orc_sigmoid.argtypes = [C.c_double]
+        lib.orc_relation.restype = C.c_double
+        lib.orc_relation.argtypes = [P, P, C.c_int32, C.c_int64, C.c_int64]
+        lib.orc_cosines.restype = C.c_int
+        lib.orc_cosines.argtypes = [P, P, P]
+        lib.orc_ranks.restype = C.c_int
+        lib.orc_ranks.argtypes = [C.c_int64, P, P]
+        lib.orc_query_all.restype = C.c_int
+        lib.orc_query_all.argtypes = [P, P, P, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
+        lib.orc_topk.restype = C.c_int
+        lib.orc_topk.argtypes = [C.c_int64, P, C.c_int64, P]
+        lib.orc_batch.restype = C.c_int
+        lib.orc_batch.argtypes = [P, P, C.c_int64, P, P, P, P, P, C.c_int64, P, P, P, P, C.c_int32]
+        lib.orc_query_bounds.restype = C.c_int
+        lib.orc_query_bounds.argtypes = [P, P, P, C.c_int32, C.c_int32, P, P, C.c_double,
+                                         P, P, P, P, P, P, P]
+        lib.orc_num_threads.restype = C.c_int
+        lib.orc_num_threads.argtypes = []
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class _SceneRef:
+    """Holds contiguous copies of a synth.Scene's arrays alive for a call."""
+
+    def __init__(self, scene):
+        self.desc = np.ascontiguousarray(scene.desc, dtype=np.float32)
+        self.cls = np.ascontiguousarray(scene.cls, dtype=np.int32)
+        self.box = np.ascontiguousarray(scene.box, dtype=np.float32)
+        self.views = np.ascontiguousarray(scene.views, dtype=np.float32)
+        n, dim = self.desc.shape
+        self.n = n
+        self.dim = dim
+        self.c = _Scene(n, dim, _ptr(self.desc), _ptr(self.cls), _ptr(self.box),
+                        int(self.views.shape[1]), _ptr(self.views))
+
+
+def _params(p: OracleParams | None):
+    p = p or OracleParams()
+    return _Params(p.mu, p.w, p.class_mis, p.sigma_near, p.tau_v, p.tau_h, p.z_min, p.k_anchor)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+def num_threads() -> int:
+    return int(load().orc_num_threads())
+
+
+def sigmoid(x: float) -> float:
+    return float(load().orc_sigmoid(float(x)))
+
+
+def relation(scene, pred: int, e: int, a: int, params: OracleParams | None = None) -> float:
+    sr, pp = _SceneRef(scene), _params(params)
+    return float(load().orc_relation(C.byref(sr.c), C.byref(pp), int(pred), int(e), int(a)))
+
+
+def cosines(scene, u) -> np.ndarray:
+    sr = _SceneRef(scene)
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    out = np.zeros(sr.n, np.float64)
+    _check(load().orc_cosines(C.byref(sr.c), _ptr(u), _ptr(out)), "cosines")
+    return out
+
+
+def ranks(c) -> np.ndarray:
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    out = np.zeros(c.shape[0], np.int64)
+    _check(load().orc_ranks(c.shape[0], _ptr(c), _ptr(out)), "ranks")
+    return out
+
+
+def topk(s, k: int) -> np.ndarray:
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    out = np.zeros(k, np.int64)
+    _check(load().orc_topk(s.shape[0], _ptr(s), int(k), _ptr(out)), "topk")
+    return out
+
+
+def query_all(scene, u0, c_t, preds, u_c, params: OracleParams | None = None) -> dict:
+    """Every intermediate of one query over all objects (steps 1-7)."""
+    sr, pp = _SceneRef(scene), _params(params)
+    preds = np.ascontiguousarray(preds, dtype=np.int32)
+    m = int(preds.shape[0])
+    u0 = np.ascontiguousarray(u0, dtype=np.float32)
+    u_c = np.ascontiguousarray(np.asarray(u_c, dtype=np.float32).reshape(m, sr.dim))
+    n = sr.n
+    out = dict(cos0=np.zeros(n), rank0=np.zeros(n, np.int64), s_sem=np.zeros(n),
+               t=np.zeros((m, n)), anchor=np.zeros((m, n), np.int64), s=np.zeros(n))
+    rc = load().orc_query_all(C.byref(sr.c), C.byref(pp), _ptr(u0), int(c_t), m, _ptr(preds),
+                              _ptr(u_c), _ptr(out["cos0"]), _ptr(out["rank0"]), _ptr(out["s_sem"]),
+                              _ptr(out["t"]), _ptr(out["anchor"]), _ptr(out["s"]))
+    _check(rc, "query_all")
+    return out
+
+
+def query_bounds(scene, u0, c_t, preds, u_c, tau: float,
+                 params: OracleParams | None = None) -> dict:
+    """Tie-tolerant bounds on what any result with cosine error <= tau/2 may score."""
+    sr, pp = _SceneRef(scene), _params(params)
+    preds = np.ascontiguousarray(preds, dtype=np.int32)
+    m = int(preds.shape[0])
+    u0 = np.ascontiguousarray(u0, dtype=np.float32)
+    u_c = np.ascontiguousarray(np.asarray(u_c, dtype=np.float32).reshape(m, sr.dim))
+    n = sr.n
+    out = dict(s_lo=np.zeros(n), s_hi=np.zeros(n), t_lo=np.zeros((m, n)), t_hi=np.zeros((m, n)),
+               rank_lo=np.zeros(n, np.int64), rank_hi=np.zeros(n, np.int64),
+               in_p=np.zeros((m, n), np.int8))
+    rc = load().orc_query_bounds(C.byref(sr.c), C.byref(pp), _ptr(u0), int(c_t), m, _ptr(preds),
+                                 _ptr(u_c), float(tau), _ptr(out["s_lo"]), _ptr(out["s_hi"]),
+                                 _ptr(out["t_lo"]), _ptr(out["t_hi"]), _ptr(out["rank_lo"]),
+                                 _ptr(out["rank_hi"]), _ptr(out["in_p"]))
+    _check(rc, "query_bounds")
+    return out
+
+
+def batch(scene, qb, k: int, params: OracleParams | None = None, n_threads: int = 0) -> dict:
+    """TopK of every query in `qb` against one scene (OpenMP over queries)."""
+    sr, pp = _SceneRef(scene), _params(params)
+    n_q = qb.n_q
+    tgt = np.ascontiguousarray(qb.tgt_emb, dtype=np.float32)
+    tcls = np.ascontiguousarray(qb.tgt_cls, dtype=np.int32)
+    coff = np.ascontiguousarray(qb.c_off, dtype=np.int32)
+    cpred = np.ascontiguousarray(qb.c_pred, dtype=np.int32)
+    cemb = np.ascontiguousarray(qb.c_emb, dtype=np.float32)
+    out = dict(idx=np.zeros((n_q, k), np.int64), score=np.zeros((n_q, k)),
+               t=np.zeros((n_q, k, 4)), anchor=np.zeros((n_q, k, 4), np.int64))
+    rc = load().orc_batch(C.byref(sr.c), C.byref(pp), n_q, _ptr(tgt), _ptr(tcls), _ptr(coff),
+                          _ptr(cpred), _ptr(cemb if cemb.size else np.zeros(1, np.float32)),
+                          int(k), _ptr(out["idx"]), _ptr(out["score"]), _ptr(out["t"]),
+                          _ptr(out["anchor"]), int(n_threads))
+    _check(rc, "batch")
+    return out
