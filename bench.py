@@ -1,0 +1,318 @@
+"""Benchmark: relational queries/s on one GB300 for the 20,000-object site scene.
+
+Workload (default): one 120x120x10 m scene, N = 20,000 objects, D = 1152
+FP32 descriptors over 400 classes (30% in 20 look-alike classes), 8 stored
+views per object; 4,096 queries with 1-4 constraints; TopK = 10.  A step is
+one farm_query_batch + farm_topk over the whole batch (similarity, rank
+select, relations, composite, TopK).
+
+Prints one JSON line.  `value` times device-resident inputs with CUDA events on
+the library's stream; `e2e` times the same steps through host buffers (pinned
+H2D of the embeddings and query metadata, D2H of the TopK records) by wall
+clock.  `roofline` reports the dominant kernel (the similarity contraction)
+from the library's own stage events over the timed region.  `cpu_baseline` is
+the FP64 oracle on the host cores on a bounded query sample.
+
+--impl reference times the oracle itself, as it stands, on the host cores.
+Under torchrun every rank runs its own replica (weak scaling, no collective on
+the data path; one barrier and a max over ranks for the timing).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "site_n20k_d1152"
+K_TOP = 10
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(scene, qb, k, n_sample, seed=0):
+    import oracle
+    qs = np.sort(np.random.default_rng(seed).choice(qb.n_q, size=min(n_sample, qb.n_q), replace=False))
+    sub = qb.subset(qs)
+    t0 = time.perf_counter()
+    oracle.batch(scene, sub, k)
+    dt = time.perf_counter() - t0
+    return {"value": sub.n_q / dt, "unit": "queries/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{sub.n_q} of the {qb.n_q} queries (seeded), FP64 oracle, OpenMP over "
+                      f"queries, {dt:.1f} s wall"}
+
+
+def run_reference(args):
+    """The oracle on the host cores: the only reference implementation there is."""
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    oracle.build()
+    import synth
+    scenes, qb = synth.workload(args.workload)
+    sc = scenes[0]
+    n_per_step = args.ref_queries
+    rng = np.random.default_rng(1)
+    for _ in range(args.warmup):
+        oracle.batch(sc, qb.subset(rng.choice(qb.n_q, size=8, replace=False)), K_TOP)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        sub = qb.subset(np.sort(rng.choice(qb.n_q, size=n_per_step, replace=False)))
+        oracle.batch(sc, sub, K_TOP)
+    dt = time.perf_counter() - t0
+    value = n_per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "relational queries/s", "value": value, "unit": "queries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_objects": sc.n, "dim": sc.dim,
+                   "queries_per_step": n_per_step, "top_k": K_TOP},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{n_per_step} seeded queries of {args.workload} per step"},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_simt", "bf16"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-sample", type=int, default=384)
+    ap.add_argument("--ref-queries", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build()
+    if dist:
+        dist.barrier()
+    import paper_2606_15476_gb300 as F
+    import synth
+
+    scenes, qb = synth.workload(args.workload)
+    sc = scenes[0]
+    prec = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16}[args.precision]
+    stream = torch.cuda.Stream()          # the library and the timing events share it
+    torch.cuda.set_stream(stream)
+    ctx = F.farm_create(local, stream)
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    n_q, n_c = qb.n_q, qb.n_c
+    d_tgt = torch.from_numpy(qb.tgt_emb).cuda()
+    d_cemb = torch.from_numpy(qb.c_emb).cuda()
+    o_idx = torch.empty((n_q, K_TOP), dtype=torch.int32, device="cuda")
+    o_score = torch.empty((n_q, K_TOP), dtype=torch.float32, device="cuda")
+    o_pred = torch.empty((n_q, K_TOP, 4), dtype=torch.float32, device="cuda")
+    o_anc = torch.empty((n_q, K_TOP, 4), dtype=torch.int32, device="cuda")
+
+    def step_device():
+        h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec)
+        F.farm_topk(ctx, h, K_TOP, n_q, o_idx, o_score, o_pred, o_anc)
+
+    for _ in range(args.warmup):
+        step_device()
+    F.farm_sync(ctx)
+    F.farm_stage_times(ctx, reset=True)
+    F.farm_set_profiling(ctx, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step_device()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    F.farm_sync(ctx)
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, launches = F.farm_stage_times(ctx, reset=True)
+    F.farm_set_profiling(ctx, False)
+    ms_step = ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        dist.barrier()
+
+    # ---- end to end through host buffers (pinned), same steps
+    h_tgt = torch.from_numpy(qb.tgt_emb).pin_memory().numpy()
+    h_cemb = torch.from_numpy(qb.c_emb).pin_memory().numpy()
+    h_out = dict(idx=torch.empty((n_q, K_TOP), dtype=torch.int32).pin_memory().numpy(),
+                 score=torch.empty((n_q, K_TOP), dtype=torch.float32).pin_memory().numpy(),
+                 pred=torch.empty((n_q, K_TOP, 4), dtype=torch.float32).pin_memory().numpy(),
+                 anchor=torch.empty((n_q, K_TOP, 4), dtype=torch.int32).pin_memory().numpy())
+
+    def step_host():
+        h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec)
+        F.farm_topk(ctx, h, K_TOP, n_q, h_out["idx"], h_out["score"], h_out["pred"], h_out["anchor"])
+
+    for _ in range(args.warmup):
+        step_host()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = (n_q + n_c) * sc.dim * 4 + 4 * (3 * n_q + 1 + n_c)
+    d2h = n_q * K_TOP * (4 + 4 + 16 + 16)
+
+    # ---- roofline of the similarity contraction (stage 1), measured over the timed region
+    peaks, peak_kind = _peaks()
+    rows = n_q + n_c
+    flops_step = 2.0 * rows * sc.n * sc.dim
+    gemm_ms = stage_ms[1] / args.steps
+    if args.precision == "fp32":
+        # three TF32 products per FP32-accurate product; TF32 peak = bf16 peak x (1.1 / 2.25)
+        peak = peaks["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
+        bound, unit = "tensor", "TFLOP/s"
+        peak_note = f"{peak_kind} sustained bf16 x 1.1/2.25 (TF32) / 3 (three-term split)"
+    elif args.precision == "bf16":
+        peak = peaks["bf16_tflops_sustained"]
+        bound, unit = "tensor", "TFLOP/s"
+        peak_note = f"{peak_kind} sustained bf16"
+    else:
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        bound, unit = "alu", "TFLOP/s"
+        peak_note = "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+    achieved = flops_step / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0
+
+    line = {
+        "metric": "relational queries/s", "value": world * n_q / (ms_step * 1e-3),
+        "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp32_simt": "f32", "bf16": "bf16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_objects": sc.n, "dim": sc.dim, "n_views": sc.n_views,
+                   "queries": n_q, "constraint_rows": n_c, "top_k": K_TOP,
+                   "precision": args.precision, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (descriptor splits 184 MB + similarity block 1.15 GB)"},
+        "e2e": {"value": world * n_q / (e2e_ms * 1e-3), "unit": "queries/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "stage_ms_per_step": {"prepare": stage_ms[0] / args.steps, "similarity": gemm_ms,
+                              "select": stage_ms[2] / args.steps, "compose": stage_ms[3] / args.steps},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "kernel": "similarity", "peak_source": peak_note},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"] = cpu_baseline(sc, qb, K_TOP, args.cpu_sample)
+    F.farm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

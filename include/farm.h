@@ -1,0 +1,225 @@
+/*
+ * farm.h -- C ABI of the GB300 (sm_103a) relational-retrieval library.
+ *
+ * The library implements the query-time scoring stage of FARM ("Find Anything
+ * using Relational Spatial Memory"): given an object-level memory M and a
+ * parsed query q, it returns y_hat = g(q, M) (Sec. 2.1, "Relational object
+ * retrieval"), realised as
+ *
+ *   score(e; q, M) = max over bindings eta with eta(x*) = e of Verify(eta),
+ *   y_hat          = TopK_e score(e)                          (Sec. 2.3; App. B)
+ *
+ * with the unary score s_sem given by reciprocal-rank fusion of descriptor
+ * similarity (App. D.2 step 3), the closed-form relation evaluators of App. D.2
+ * step 4 (Above, Below, LeftOf, RightOf, Near), anchors bound greedily to
+ * their best witness among the top-K_a landmark candidates (App. B,
+ * "Query-time complexity"; App. D.2 step 4) and the composite
+ * s = s_sem * [(1 - w) + w * gbar] of App. D.2 step 5.
+ *
+ * Conventions for every call:
+ *  - Every call returns a farm_status and never aborts the process.  On an
+ *    error, farm_last_error(ctx) holds a one-line message.
+ *  - Inputs are owned by the caller and never retained after the call
+ *    returns (device inputs: after the work the call enqueues has run).
+ *    The context owns all device memory it allocates.
+ *  - Work is enqueued on the context's CUDA stream in call order.  Calls that
+ *    write host memory synchronise that stream before returning.
+ *  - A context is used by one host thread at a time.
+ *  - Invalid arguments (null pointers, non-positive sizes, unknown scene,
+ *    more than FARM_MAX_CONSTRAINTS constraints, k out of range, non-finite
+ *    host data) are reported as FARM_EINVAL before anything is enqueued.
+ *    Embeddings in device memory are checked on the GPU: a zero or non-finite
+ *    row is reported by the next synchronising call (farm_topk with host
+ *    outputs, or farm_sync) as FARM_EINVAL.
+ */
+#ifndef FARM_H
+#define FARM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct farm_ctx farm_ctx;
+
+typedef enum {
+    FARM_OK = 0,
+    FARM_EINVAL = 1,    /* bad argument or input data */
+    FARM_ENOMEM = 2,    /* a device or host allocation failed */
+    FARM_ECUDA = 3,     /* a CUDA call failed (message has the CUDA error) */
+    FARM_ESTATE = 4,    /* call out of order (e.g. stale batch handle) */
+    FARM_ETIMEOUT = 5   /* a bounded device-side wait gave up */
+} farm_status;
+
+/* Predicate codes (App. B predicate vocabulary; evaluators of App. D.2 step 4). */
+typedef enum {
+    FARM_ABOVE = 0,     /* sig((z_e - z_a) / tau_v) */
+    FARM_BELOW = 1,     /* sig((z_a - z_e) / tau_v) */
+    FARM_LEFT_OF = 2,   /* mean over the candidate's stored views of sig((u_a - u_e) / tau_h) */
+    FARM_RIGHT_OF = 3,  /* mean over the candidate's stored views of sig((u_e - u_a) / tau_h) */
+    FARM_NEAR = 4       /* exp(-|p_e - p_a|^2 / (2 sigma_near^2)) */
+} farm_pred;
+
+/* Arithmetic of the descriptor-similarity stage (App. D.2 step 3). */
+typedef enum {
+    FARM_PREC_FP32 = 0,       /* FP32-accurate: tcgen05 tensor cores, 3-term split TF32 */
+    FARM_PREC_BF16 = 1,       /* BF16 operands, FP32 accumulate, FP32 rescore of the borderline */
+    FARM_PREC_FP32_SIMT = 3   /* FP32 FMA on the CUDA cores (independent check path) */
+} farm_precision;
+
+#define FARM_MAX_CONSTRAINTS 4
+#define FARM_MAX_VIEWS 16
+
+/* flags */
+#define FARM_PTR_DEVICE 1u    /* the call's array arguments are device pointers */
+
+/*
+ * The method's constants.  mu = 5 (reciprocal-rank offset), w = 0.5 (blend
+ * weight), class_mis = 0.3 (soft class factor), sigma_near = 0.5 m are given in
+ * App. D.2 steps 3-5.  tau_v (m), tau_h (image-plane units), z_min (m) and
+ * k_anchor (landmark candidates per constraint, K_a of App. B) are not given
+ * by the paper; farm_default_params sets 0.25, 0.10, 0.05 and 16.
+ * k_max is the largest k a later farm_topk may ask for: farm_query_batch keeps
+ * only candidates that can still reach the top k_max (see farm_query_batch).
+ * rescore is the number of candidates per row the BF16 path re-scores in FP32.
+ */
+typedef struct {
+    float mu;
+    float w;
+    float class_mis;
+    float sigma_near;
+    float tau_v;
+    float tau_h;
+    float z_min;
+    int32_t k_anchor;
+    int32_t k_max;
+    int32_t rescore;
+} farm_params;
+
+/* Fills *p with the defaults above (k_max = 10, rescore = 256). */
+void farm_default_params(farm_params *p);
+
+/*
+ * Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * the context enqueues on (NULL: the context creates and owns a stream).
+ * `params` may be NULL (defaults).  Requirements: 0 < w < 1, 0 < class_mis <= 1,
+ * mu >= 0, sigma_near, tau_v, tau_h > 0, z_min >= 0, 1 <= k_anchor <= 256,
+ * 1 <= k_max and the resulting target-candidate bound <= 512 (see
+ * farm_query_batch).
+ */
+farm_status farm_create(farm_ctx **out, int device, void *cuda_stream, const farm_params *params);
+
+/* Frees every device buffer of the context (synchronises its stream). */
+farm_status farm_destroy(farm_ctx *ctx);
+
+/*
+ * Uploads (or replaces) scene `scene_id` (0 <= scene_id < 4096): the memory
+ * M_t of Sec. 2.2, one entity per object.
+ *   n       number of objects (>= 1)
+ *   dim     descriptor length (1 .. 8192)
+ *   desc    [n, dim] row-major FP32 descriptors; normalised to unit length on
+ *           the GPU (a zero or non-finite row is FARM_EINVAL for host data)
+ *   cls     [n] int32 object classes (compared with a query's target class)
+ *   box     [6, n] FP32 SoA rows cx, cy, cz, sx, sy, sz (metres, z up); the
+ *           centre stands in for the entity's Gaussian mean
+ *   n_views number of stored views per object (0 .. FARM_MAX_VIEWS)
+ *   views   [6, n_views, n] FP32 SoA rows ox, oy, oz, fx, fy, fz: camera
+ *           position and viewing direction of each stored view (App. D.1
+ *           step 6 keeps such views); NULL when n_views == 0
+ *   flags   FARM_PTR_DEVICE when the arrays are device pointers
+ * The data is copied; the call returns once the copies are enqueued.
+ */
+farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32_t dim,
+                               const float *desc, const int32_t *cls, const float *box,
+                               int32_t n_views, const float *views, uint32_t flags);
+
+/*
+ * Enqueues the scoring of n_q queries (n_q >= 0).  Each query is the typed
+ * QueryGraph of App. D.2 step 1 reduced to a star: a target embedding, a
+ * target class, and up to 4 constraints rho_i(x*, a_i), each a predicate and a
+ * landmark embedding.
+ *   scene_of_q [n_q]       host int32 scene of each query (uploaded scene ids)
+ *   tgt_emb    [n_q, dim]  FP32 target embeddings (any norm; normalised on the GPU)
+ *   tgt_cls    [n_q]       host int32 target class, -1 = none (class factor off)
+ *   c_off      [n_q + 1]   host int32 CSR offsets: query q owns constraints
+ *                          c_off[q] .. c_off[q+1]-1 (at most 4); c_off[0] = 0
+ *   c_pred     [n_c]       host int32 farm_pred codes, n_c = c_off[n_q]
+ *   c_emb      [n_c, dim]  FP32 landmark embeddings
+ *   precision  a farm_precision value
+ *   flags      FARM_PTR_DEVICE: tgt_emb and c_emb are device pointers (the
+ *              other arrays are always host memory)
+ *   batch_handle  receives the handle that farm_topk takes
+ * Only target candidates whose rank r can still place them in the top k_max
+ * are scored: a candidate scores at most 1/(mu + r) while k_max objects score
+ * at least (1 - w) * class_mis / (mu + k_max), so candidates of rank above
+ * R = ceil((mu + k_max) / ((1 - w) * class_mis) - mu) (95 at the defaults)
+ * cannot enter the result.  The result is the same as scoring every object.
+ * A new farm_query_batch call invalidates the previous handle.
+ */
+farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of_q,
+                             const float *tgt_emb, const int32_t *tgt_cls, const int32_t *c_off,
+                             const int32_t *c_pred, const float *c_emb, int32_t precision,
+                             uint32_t flags, uint64_t *batch_handle);
+
+/*
+ * Writes the TopK of every query of a batch, the ScoredCandidate records of
+ * App. D.2 step 7: for query q and rank j < k,
+ *   out_idx   [n_q, k]     int32 object index, best first (lower index on ties)
+ *   out_score [n_q, k]     FP32 composite score s
+ *   out_pred  [n_q, k, 4]  FP32 per-constraint score t_i (-1 beyond the
+ *                          query's constraints; NULL to skip)
+ *   out_anchor[n_q, k, 4]  int32 bound landmark object (-1 without a witness
+ *                          or beyond the constraints; NULL to skip)
+ * 1 <= k <= k_max and k <= n of every scene in the batch.
+ * flags: FARM_PTR_DEVICE when the outputs are device pointers (no
+ * synchronisation); otherwise the call synchronises and reports device-side
+ * input errors.
+ */
+farm_status farm_topk(farm_ctx *ctx, uint64_t batch_handle, int32_t k, int32_t *out_idx,
+                      float *out_score, float *out_pred, int32_t *out_anchor, uint32_t flags);
+
+/* Synchronises the context's stream and reports device-side errors. */
+farm_status farm_sync(farm_ctx *ctx);
+
+/*
+ * Cosine similarity of n_rows embeddings against every object of a scene,
+ * computed by the kernels of `precision` (App. D.2 step 3):
+ *   emb [n_rows, dim] FP32, out [n_rows, n] FP32 (host or device per flags).
+ */
+farm_status farm_similarity(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb,
+                            int32_t precision, float *out, uint32_t flags);
+
+/*
+ * The ranked candidate lists of the last batch (host outputs, synchronises):
+ *   tgt_idx [n_q, r_tgt]   target candidates in rank order (rank 1 first)
+ *   lm_idx  [n_c, k_lm]    each constraint's landmark candidates in rank order
+ * *r_tgt_out and *k_lm_out receive the list lengths (taken per batch as
+ * min(R, n) and min(k_anchor, n) over its scenes; shorter lists are padded
+ * with -1).  Any pointer may be NULL.
+ */
+farm_status farm_candidates(farm_ctx *ctx, uint64_t batch_handle, int32_t *tgt_idx,
+                            int32_t *lm_idx, int32_t *r_tgt_out, int32_t *k_lm_out);
+
+/*
+ * Stage timing.  With profiling on, every farm_query_batch records CUDA events
+ * around its stages on the context stream.  farm_stage_times synchronises and
+ * writes the accumulated milliseconds of FARM_N_STAGES stages (prepare,
+ * similarity, select, compose) to ms_out, the number of kernels the context
+ * launched to *launches_out, and with reset != 0 clears both.
+ */
+#define FARM_N_STAGES 4
+farm_status farm_set_profiling(farm_ctx *ctx, int32_t on);
+farm_status farm_stage_times(farm_ctx *ctx, float *ms_out, int64_t *launches_out, int32_t reset);
+
+/* One-line description of the last error on this context ("" if none). */
+const char *farm_last_error(farm_ctx *ctx);
+
+/* Library version string. */
+const char *farm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FARM_H */

@@ -1,0 +1,16 @@
+"""GB300-native (sm_103a) relational retrieval over an object-level spatial memory.
+
+The compute path is the CUDA library libfarm.so (C ABI in include/farm.h);
+`farm` is its thin ctypes binding with the same entry-point names.
+"""
+from . import farm
+from .farm import (FarmError, FarmParams, farm_candidates, farm_create, farm_default_params,
+                   farm_destroy, farm_last_error, farm_memory_upload, farm_query_batch,
+                   farm_set_profiling, farm_similarity, farm_stage_times, farm_sync, farm_topk,
+                   farm_version, PREC_FP32, PREC_BF16, PREC_FP32_SIMT, PTR_DEVICE)
+
+__all__ = ["farm", "FarmError", "FarmParams", "farm_candidates", "farm_create",
+           "farm_default_params", "farm_destroy", "farm_last_error", "farm_memory_upload",
+           "farm_query_batch", "farm_set_profiling", "farm_similarity", "farm_stage_times",
+           "farm_sync", "farm_topk", "farm_version", "PREC_FP32", "PREC_BF16", "PREC_FP32_SIMT",
+           "PTR_DEVICE"]

@@ -1,0 +1,779 @@
+// farm_api.cu -- the C ABI of include/farm.h: argument checks, device memory,
+// query planning and the stream-ordered launch sequence
+//
+//   normalise rows -> similarity (App. D.2 step 3) -> per-row rank select
+//   (steps 3-4) -> relations, best witnesses, composite and sort (steps 4-5)
+//   -> TopK prefix copy (step 7).
+#include <algorithm>
+#include <cstdint>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "farm_internal.h"
+
+using farm::Buf;
+using farm::Ctx;
+using farm::Scene;
+using farm::SceneDev;
+
+struct farm_ctx {
+    Ctx c;
+    SceneDev *d_scenes = nullptr;
+    // host copies of the last batch's plan (for farm_candidates)
+    std::vector<int32_t> h_perm;      // caller query -> planned query
+    std::vector<int32_t> h_cplan;     // caller constraint -> planned constraint
+    // pinned staging for per-batch metadata
+    int32_t *h_stage = nullptr;
+    size_t h_stage_n = 0;
+    cudaEvent_t stage_done = nullptr;
+    // profiling marks
+    struct Mark { int stage; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+constexpr int kMaxScenes = 4096;
+constexpr size_t kSimCapBytes = size_t(4) << 30;   // similarity block per launch group
+
+farm_status fail(farm_ctx *ctx, farm_status st, const std::string &msg)
+{
+    if (ctx) ctx->c.err = msg;
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? FARM_ENOMEM : FARM_ECUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+#define LAUNCH(call)              \
+    do {                          \
+        ctx->c.launches += 1;     \
+        CK(call);                 \
+    } while (0)
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+int64_t target_bound(const farm_params &p)
+{
+    // A candidate of rank r scores at most 1/(mu + r); k_max objects score at
+    // least (1 - w) * class_mis / (mu + k_max).  Keep every rank that can tie.
+    double r = ((double)p.mu + (double)p.k_max) / ((1.0 - (double)p.w) * (double)p.class_mis) -
+               (double)p.mu;
+    return (int64_t)std::floor(r) + 1;
+}
+
+bool params_ok(const farm_params &p, std::string &why)
+{
+    if (!(p.w > 0.f && p.w < 1.f)) { why = "w must lie in (0, 1)"; return false; }
+    if (!(p.class_mis > 0.f && p.class_mis <= 1.f)) { why = "class_mis must lie in (0, 1]"; return false; }
+    if (!(p.mu >= 0.f) || !std::isfinite(p.mu)) { why = "mu must be >= 0"; return false; }
+    if (!(p.sigma_near > 0.f && p.tau_v > 0.f && p.tau_h > 0.f)) { why = "sigma_near, tau_v, tau_h must be > 0"; return false; }
+    if (!(p.z_min >= 0.f) || !std::isfinite(p.z_min)) { why = "z_min must be >= 0"; return false; }
+    if (p.k_anchor < 1 || p.k_anchor > farm::kMaxAnchorCands) { why = "k_anchor must lie in [1, 256]"; return false; }
+    if (p.k_max < 1) { why = "k_max must be >= 1"; return false; }
+    if (target_bound(p) > farm::kMaxTargetCands) {
+        why = "(mu + k_max) / ((1 - w) * class_mis) - mu exceeds 512 target candidates";
+        return false;
+    }
+    if (p.rescore < 1 || p.rescore > 4096) { why = "rescore must lie in [1, 4096]"; return false; }
+    return true;
+}
+
+cudaError_t ws_get(farm_ctx *ctx, Buf b, size_t bytes, void **out)
+{
+    auto &ws = ctx->c.ws;
+    if (bytes == 0) bytes = 16;
+    if (ws.bytes[b] < bytes) {
+        if (ws.ptr[b]) {
+            cudaError_t e = cudaStreamSynchronize(ctx->c.stream);
+            if (e != cudaSuccess) return e;
+            cudaFree(ws.ptr[b]);
+            ws.ptr[b] = nullptr;
+            ws.bytes[b] = 0;
+        }
+        size_t grow = bytes + bytes / 8;
+        cudaError_t e = cudaMalloc(&ws.ptr[b], grow);
+        if (e != cudaSuccess) return e;
+        ws.bytes[b] = grow;
+    }
+    *out = ws.ptr[b];
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t ws_get(farm_ctx *ctx, Buf b, size_t count, T **out)
+{
+    void *p = nullptr;
+    cudaError_t e = ws_get(ctx, b, count * sizeof(T), &p);
+    *out = static_cast<T *>(p);
+    return e;
+}
+
+void free_scene(Scene &s)
+{
+    cudaFree(s.desc32); cudaFree(s.desc_hi); cudaFree(s.desc_lo); cudaFree(s.desc_bf16);
+    cudaFree(s.cls); cudaFree(s.pos); cudaFree(s.size); cudaFree(s.views);
+    s = Scene{};
+}
+
+int mark_begin(farm_ctx *ctx, int stage)
+{
+    if (!ctx->c.profiling) return -1;
+    cudaEvent_t a, b;
+    if (ctx->pool.size() >= 2) {
+        a = ctx->pool.back(); ctx->pool.pop_back();
+        b = ctx->pool.back(); ctx->pool.pop_back();
+    } else {
+        if (cudaEventCreate(&a) != cudaSuccess) return -1;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
+    }
+    cudaEventRecord(a, ctx->c.stream);
+    ctx->marks.push_back({stage, a, b});
+    return (int)ctx->marks.size() - 1;
+}
+
+void mark_end(farm_ctx *ctx, int m)
+{
+    if (m >= 0) cudaEventRecord(ctx->marks[m].b, ctx->c.stream);
+}
+
+bool all_finite(const float *x, int64_t count)
+{
+    for (int64_t i = 0; i < count; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+farm_status check_device_errors(farm_ctx *ctx)
+{
+    Ctx &c = ctx->c;
+    CK(cudaMemcpyAsync(c.h_err, c.d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    const int32_t e = *c.h_err;
+    if (e == 0) return FARM_OK;
+    CK(cudaMemsetAsync(c.d_err, 0, sizeof(int32_t), c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    c.batch_valid = false;
+    if (e & farm::kErrTimeout) return fail(ctx, FARM_ETIMEOUT, "a bounded device-side wait gave up");
+    if (e & farm::kErrBadDesc)
+        return fail(ctx, FARM_EINVAL, "a descriptor row has zero or non-finite norm");
+    return fail(ctx, FARM_EINVAL, "an embedding row has zero or non-finite norm");
+}
+
+// Normalised operand rows for `prec` into the workspace; returns pointers.
+struct RowOps {
+    float *q32 = nullptr, *qhi = nullptr, *qlo = nullptr;
+    uint16_t *qbf = nullptr;
+};
+
+cudaError_t alloc_rows(farm_ctx *ctx, int32_t prec, int64_t rows, int32_t dim_pad, RowOps &r)
+{
+    const size_t cnt = (size_t)std::max<int64_t>(rows, 1) * dim_pad;
+    cudaError_t e = cudaSuccess;
+    if (prec == FARM_PREC_FP32_SIMT || prec == FARM_PREC_BF16) {
+        if ((e = ws_get(ctx, farm::B_Q32, cnt, &r.q32)) != cudaSuccess) return e;
+    }
+    if (prec == FARM_PREC_FP32) {
+        if ((e = ws_get(ctx, farm::B_QHI, cnt, &r.qhi)) != cudaSuccess) return e;
+        if ((e = ws_get(ctx, farm::B_QLO, cnt, &r.qlo)) != cudaSuccess) return e;
+    }
+    if (prec == FARM_PREC_BF16) {
+        if ((e = ws_get(ctx, farm::B_QBF, cnt, &r.qbf)) != cudaSuccess) return e;
+    }
+    return e;
+}
+
+// S rows [r0, r0 + rows) of the planned row space against scene s.
+farm_status run_similarity(farm_ctx *ctx, int32_t prec, const RowOps &ops, int64_t r0,
+                           int64_t rows, const Scene &s, float *S, int64_t ld_s)
+{
+    Ctx &c = ctx->c;
+    const int64_t off = r0 * s.dim_pad;
+    switch (prec) {
+    case FARM_PREC_FP32_SIMT:
+        LAUNCH(farm::launch_sim_simt(ops.q32 + off, s.desc32, S, rows, s.n, s.dim_pad, ld_s, c.stream));
+        return FARM_OK;
+    case FARM_PREC_FP32:
+        if (!farm::sim_tc_available())
+            return fail(ctx, FARM_EINVAL, "the tensor-core FP32 similarity path is not built");
+        LAUNCH(farm::launch_sim_tc_tf32x3(ops.qhi + off, ops.qlo + off, s.desc_hi, s.desc_lo, S,
+                                          rows, s.n, s.dim_pad, ld_s, c.num_sms, c.stream));
+        return FARM_OK;
+    default:
+        return fail(ctx, FARM_EINVAL, "precision not supported by this build");
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+const char *farm_version(void) { return "farm-gb300 0.1 (sm_103a)"; }
+
+void farm_default_params(farm_params *p)
+{
+    if (!p) return;
+    p->mu = 5.0f;
+    p->w = 0.5f;
+    p->class_mis = 0.3f;
+    p->sigma_near = 0.5f;
+    p->tau_v = 0.25f;
+    p->tau_h = 0.10f;
+    p->z_min = 0.05f;
+    p->k_anchor = 16;
+    p->k_max = 10;
+    p->rescore = 256;
+}
+
+const char *farm_last_error(farm_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+farm_status farm_destroy(farm_ctx *ctx)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    cudaSetDevice(c.device);
+    if (c.stream) cudaStreamSynchronize(c.stream);
+    for (auto &s : c.scenes)
+        if (s.present) free_scene(s);
+    for (int b = 0; b < farm::B_COUNT; ++b) cudaFree(c.ws.ptr[b]);
+    cudaFree(c.d_err);
+    cudaFree(ctx->d_scenes);
+    if (c.h_err) cudaFreeHost(c.h_err);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
+    for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+    delete ctx;
+    return FARM_OK;
+}
+
+farm_status farm_create(farm_ctx **out, int device, void *cuda_stream, const farm_params *params)
+{
+    if (!out) return FARM_EINVAL;
+    *out = nullptr;
+    farm_params p;
+    farm_default_params(&p);
+    if (params) p = *params;
+    std::string why;
+    if (!params_ok(p, why)) return FARM_EINVAL;
+    farm_ctx *ctx = new farm_ctx();
+    Ctx &c = ctx->c;
+    c.device = device;
+    c.params = p;
+    c.scenes.resize(kMaxScenes);
+    auto bail = [&](farm_status st) {
+        farm_destroy(ctx);
+        return st;
+    };
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return bail(FARM_ECUDA);
+    if (cudaSetDevice(device) != cudaSuccess) return bail(FARM_ECUDA);
+    if (cuda_stream) {
+        c.stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess) return bail(FARM_ECUDA);
+        c.own_stream = true;
+    }
+    if (cudaMalloc(&c.d_err, sizeof(int32_t)) != cudaSuccess) return bail(FARM_ENOMEM);
+    if (cudaMemset(c.d_err, 0, sizeof(int32_t)) != cudaSuccess) return bail(FARM_ECUDA);
+    if (cudaHostAlloc(&c.h_err, sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) return bail(FARM_ENOMEM);
+    if (cudaMalloc(&ctx->d_scenes, kMaxScenes * sizeof(SceneDev)) != cudaSuccess) return bail(FARM_ENOMEM);
+    if (cudaMemset(ctx->d_scenes, 0, kMaxScenes * sizeof(SceneDev)) != cudaSuccess) return bail(FARM_ECUDA);
+    if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) return bail(FARM_ECUDA);
+    if (cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return bail(FARM_ECUDA);
+    *out = ctx;
+    return FARM_OK;
+}
+
+farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32_t dim,
+                               const float *desc, const int32_t *cls, const float *box,
+                               int32_t n_views, const float *views, uint32_t flags)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    if (scene_id < 0 || scene_id >= kMaxScenes) return fail(ctx, FARM_EINVAL, "scene_id out of range");
+    if (n < 1 || n > 0x7fffffff) return fail(ctx, FARM_EINVAL, "n must lie in [1, 2^31)");
+    if (dim < 1 || dim > 8192) return fail(ctx, FARM_EINVAL, "dim must lie in [1, 8192]");
+    if (!desc || !cls || !box) return fail(ctx, FARM_EINVAL, "desc, cls and box must be non-null");
+    if (n_views < 0 || n_views > FARM_MAX_VIEWS) return fail(ctx, FARM_EINVAL, "n_views must lie in [0, 16]");
+    if (n_views > 0 && !views) return fail(ctx, FARM_EINVAL, "views must be non-null when n_views > 0");
+    const bool dev = (flags & FARM_PTR_DEVICE) != 0;
+    if (!dev) {
+        if (!all_finite(box, 6 * n)) return fail(ctx, FARM_EINVAL, "box holds a non-finite value");
+        if (n_views > 0 && !all_finite(views, 6 * (int64_t)n_views * n))
+            return fail(ctx, FARM_EINVAL, "views hold a non-finite value");
+        for (int64_t j = 0; j < n; ++j) {
+            double ss = 0.0;
+            const float *d = desc + j * dim;
+            for (int32_t k = 0; k < dim; ++k) ss += (double)d[k] * (double)d[k];
+            if (!(ss > 0.0) || !std::isfinite(ss))
+                return fail(ctx, FARM_EINVAL, "descriptor row " + std::to_string(j) + " has zero or non-finite norm");
+        }
+    }
+    CK(cudaSetDevice(c.device));
+    Scene &s = c.scenes[scene_id];
+    if (s.present) {
+        CK(cudaStreamSynchronize(c.stream));
+        free_scene(s);
+    }
+    Scene ns;
+    ns.n = n;
+    ns.dim = dim;
+    ns.dim_pad = (int32_t)round_up(dim, farm::kDimAlign);
+    ns.n_views = n_views;
+    const size_t nd = (size_t)n * ns.dim_pad;
+    auto bailmem = [&](cudaError_t e) {
+        free_scene(ns);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? FARM_ENOMEM : FARM_ECUDA,
+                    std::string("scene upload: ") + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&ns.desc32, nd * 4)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.desc_hi, nd * 4)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.desc_lo, nd * 4)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.desc_bf16, nd * 2)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.cls, (size_t)n * 4)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.pos, (size_t)n * 12)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.size, (size_t)n * 12)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.views, (size_t)n * std::max(n_views, 1) * farm::kViewStride * 4)) != cudaSuccess)
+        return bailmem(e);
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const float *d_desc = desc;
+    float *tmp_desc = nullptr, *tmp_views = nullptr;
+    if (!dev) {
+        if ((e = cudaMallocAsync(&tmp_desc, (size_t)n * dim * 4, c.stream)) != cudaSuccess) return bailmem(e);
+        if ((e = cudaMemcpyAsync(tmp_desc, desc, (size_t)n * dim * 4, kind, c.stream)) != cudaSuccess)
+            return bailmem(e);
+        d_desc = tmp_desc;
+    }
+    ctx->c.launches += 1;
+    if ((e = farm::launch_normalize_rows(d_desc, nullptr, n, dim, ns.dim_pad, ns.desc32, ns.desc_hi,
+                                         ns.desc_lo, ns.desc_bf16, c.d_err, farm::kErrBadDesc,
+                                         c.stream)) != cudaSuccess)
+        return bailmem(e);
+    if ((e = cudaMemcpyAsync(ns.cls, cls, (size_t)n * 4, kind, c.stream)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMemcpyAsync(ns.pos, box, (size_t)n * 12, kind, c.stream)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMemcpyAsync(ns.size, box + 3 * n, (size_t)n * 12, kind, c.stream)) != cudaSuccess)
+        return bailmem(e);
+    if (n_views > 0) {
+        const float *d_views = views;
+        if (!dev) {
+            const size_t vb = (size_t)6 * n_views * n * 4;
+            if ((e = cudaMallocAsync(&tmp_views, vb, c.stream)) != cudaSuccess) return bailmem(e);
+            if ((e = cudaMemcpyAsync(tmp_views, views, vb, kind, c.stream)) != cudaSuccess) return bailmem(e);
+            d_views = tmp_views;
+        }
+        ctx->c.launches += 1;
+        if ((e = farm::launch_prepare_views(d_views, n, n_views, ns.views, c.stream)) != cudaSuccess)
+            return bailmem(e);
+    }
+    if (tmp_desc) cudaFreeAsync(tmp_desc, c.stream);
+    if (tmp_views) cudaFreeAsync(tmp_views, c.stream);
+    SceneDev sd{ns.pos, ns.views, ns.cls, n, n_views, 0};
+    if ((e = cudaMemcpyAsync(ctx->d_scenes + scene_id, &sd, sizeof(sd), cudaMemcpyHostToDevice, c.stream)) !=
+        cudaSuccess)
+        return bailmem(e);
+    // the host-side SceneDev is a stack value: make sure it has been consumed
+    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return bailmem(e);
+    ns.present = true;
+    s = ns;
+    c.batch_valid = false;
+    return FARM_OK;
+}
+
+farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of_q,
+                             const float *tgt_emb, const int32_t *tgt_cls, const int32_t *c_off,
+                             const int32_t *c_pred, const float *c_emb, int32_t precision,
+                             uint32_t flags, uint64_t *batch_handle)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    if (!batch_handle) return fail(ctx, FARM_EINVAL, "batch_handle must be non-null");
+    if (n_q < 0 || n_q > 0x7fffffff) return fail(ctx, FARM_EINVAL, "n_q out of range");
+    if (precision != FARM_PREC_FP32 && precision != FARM_PREC_BF16 && precision != FARM_PREC_FP32_SIMT)
+        return fail(ctx, FARM_EINVAL, "unknown precision");
+    if (n_q > 0 && (!scene_of_q || !tgt_emb || !tgt_cls || !c_off))
+        return fail(ctx, FARM_EINVAL, "scene_of_q, tgt_emb, tgt_cls and c_off must be non-null");
+    const bool dev = (flags & FARM_PTR_DEVICE) != 0;
+    int64_t n_c = 0;
+    int32_t dim = -1;
+    int64_t min_n = INT64_MAX, max_n = 0;
+    if (n_q > 0) {
+        if (c_off[0] != 0) return fail(ctx, FARM_EINVAL, "c_off[0] must be 0");
+        for (int64_t q = 0; q < n_q; ++q) {
+            const int32_t m = c_off[q + 1] - c_off[q];
+            if (m < 0 || m > FARM_MAX_CONSTRAINTS)
+                return fail(ctx, FARM_EINVAL, "query " + std::to_string(q) + " has " + std::to_string(m) +
+                                                  " constraints (0..4 allowed)");
+            const int32_t sid = scene_of_q[q];
+            if (sid < 0 || sid >= kMaxScenes || !c.scenes[sid].present)
+                return fail(ctx, FARM_EINVAL, "query " + std::to_string(q) + " names an unknown scene");
+            const Scene &s = c.scenes[sid];
+            if (dim < 0) dim = s.dim;
+            if (s.dim != dim) return fail(ctx, FARM_EINVAL, "all scenes of a batch must share dim");
+            min_n = std::min(min_n, s.n);
+            max_n = std::max(max_n, s.n);
+        }
+        n_c = c_off[n_q];
+        if (n_c > 0 && (!c_pred || !c_emb)) return fail(ctx, FARM_EINVAL, "c_pred and c_emb must be non-null");
+        for (int64_t i = 0; i < n_c; ++i)
+            if (c_pred[i] < 0 || c_pred[i] > FARM_NEAR)
+                return fail(ctx, FARM_EINVAL, "unknown predicate code " + std::to_string(c_pred[i]));
+    }
+    c.batch_valid = false;
+    *batch_handle = 0;
+    CK(cudaSetDevice(c.device));
+    const farm_params &p = c.params;
+    const int64_t Rb = target_bound(p);
+    if (n_q == 0) {
+        c.batch_gen += 1;
+        c.batch_valid = true;
+        c.batch_nq = 0;
+        c.batch_nc = 0;
+        c.batch_min_n = 0;
+        ctx->h_perm.clear();
+        ctx->h_cplan.clear();
+        *batch_handle = c.batch_gen;
+        return FARM_OK;
+    }
+    const int32_t stride_t = (int32_t)std::min<int64_t>(Rb, max_n);
+    const int32_t stride_l = (int32_t)std::min<int64_t>(p.k_anchor, max_n);
+    const int32_t dim_pad = (int32_t)round_up(dim, farm::kDimAlign);
+
+    // ---- plan: group queries by scene (stable), rows = [targets, constraints] per group
+    struct Group { int32_t sid; int64_t nq = 0, nc = 0, row0 = 0, q0 = 0, cp0 = 0; };
+    std::vector<int32_t> order((size_t)n_q);
+    for (int64_t q = 0; q < n_q; ++q) order[q] = (int32_t)q;
+    bool sorted = true;
+    for (int64_t q = 1; q < n_q; ++q) sorted &= scene_of_q[q] >= scene_of_q[q - 1];
+    if (!sorted)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return scene_of_q[a] < scene_of_q[b]; });
+    std::vector<Group> groups;
+    for (int64_t i = 0; i < n_q; ++i) {
+        const int32_t q = order[i];
+        if (groups.empty() || groups.back().sid != scene_of_q[q]) {
+            Group g;
+            g.sid = scene_of_q[q];
+            g.q0 = i;
+            groups.push_back(g);
+        }
+        groups.back().nq += 1;
+        groups.back().nc += c_off[q + 1] - c_off[q];
+    }
+    int64_t row = 0, cp = 0;
+    for (auto &g : groups) {
+        g.row0 = row;
+        g.cp0 = cp;
+        row += g.nq + g.nc;
+        cp += g.nc;
+    }
+    const int64_t rows_total = row;
+    // staging layout (int32): rowmap[n_q + n_c] | perm[n_q] | qmeta[n_q * 8]
+    const size_t need = (size_t)(n_q + n_c) + (size_t)n_q + (size_t)n_q * 8;
+    CK(cudaEventSynchronize(ctx->stage_done));
+    if (ctx->h_stage_n < need) {
+        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+        ctx->h_stage = nullptr;
+        ctx->h_stage_n = 0;
+        CK(cudaHostAlloc(&ctx->h_stage, need * sizeof(int32_t) * 5 / 4, cudaHostAllocDefault));
+        ctx->h_stage_n = need * 5 / 4;
+    }
+    int32_t *h_rowmap = ctx->h_stage;
+    int32_t *h_perm = h_rowmap + (n_q + n_c);
+    int32_t *h_meta = h_perm + n_q;
+    ctx->h_perm.assign((size_t)n_q, 0);
+    ctx->h_cplan.assign((size_t)n_c, 0);
+    for (const auto &g : groups) {
+        const Scene &s = c.scenes[g.sid];
+        const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
+        const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
+        int64_t cpos = 0;
+        for (int64_t k = 0; k < g.nq; ++k) {
+            const int64_t pq = g.q0 + k;       // planned query index
+            const int32_t q = order[pq];
+            h_rowmap[q] = (int32_t)(g.row0 + k);
+            h_perm[q] = (int32_t)pq;
+            ctx->h_perm[q] = (int32_t)pq;
+            const int32_t m = c_off[q + 1] - c_off[q];
+            int32_t pr[4] = {0, 0, 0, 0};
+            for (int32_t i = 0; i < m; ++i) {
+                const int64_t cc = c_off[q] + i;                  // caller constraint
+                const int64_t pc = g.cp0 + cpos + i;              // planned constraint
+                h_rowmap[n_q + cc] = (int32_t)(g.row0 + g.nq + cpos + i);
+                ctx->h_cplan[cc] = (int32_t)pc;
+                pr[i] = c_pred[cc];
+            }
+            int32_t *mt = h_meta + pq * 8;
+            mt[farm::QM_SCENE] = g.sid;
+            mt[farm::QM_CLS] = tgt_cls[q];
+            mt[farm::QM_M] = m;
+            mt[farm::QM_C0] = (int32_t)(g.cp0 + cpos);
+            mt[farm::QM_PRED01] = pr[0] | (pr[1] << 16);
+            mt[farm::QM_PRED23] = pr[2] | (pr[3] << 16);
+            mt[farm::QM_R] = Rs;
+            mt[farm::QM_KLM] = klm;
+            cpos += m;
+        }
+    }
+
+    // ---- device buffers
+    int32_t *d_rowmap, *d_perm, *d_meta, *tsel_idx, *lsel_idx, *o_idx, *o_anc;
+    float *tsel_cos, *o_score, *o_t, *d_raw = nullptr;
+    CK(ws_get(ctx, farm::B_ROWMAP, (size_t)(n_q + n_c), &d_rowmap));
+    CK(ws_get(ctx, farm::B_PERM, (size_t)n_q, &d_perm));
+    CK(ws_get(ctx, farm::B_QMETA, (size_t)n_q * 8, &d_meta));
+    CK(ws_get(ctx, farm::B_TSEL_IDX, (size_t)n_q * stride_t, &tsel_idx));
+    CK(ws_get(ctx, farm::B_TSEL_COS, (size_t)n_q * stride_t, &tsel_cos));
+    CK(ws_get(ctx, farm::B_LSEL_IDX, (size_t)std::max<int64_t>(n_c, 1) * stride_l, &lsel_idx));
+    CK(ws_get(ctx, farm::B_OUT_IDX, (size_t)n_q * stride_t, &o_idx));
+    CK(ws_get(ctx, farm::B_OUT_SCORE, (size_t)n_q * stride_t, &o_score));
+    CK(ws_get(ctx, farm::B_OUT_T, (size_t)n_q * stride_t * 4, &o_t));
+    CK(ws_get(ctx, farm::B_OUT_ANCHOR, (size_t)n_q * stride_t * 4, &o_anc));
+    RowOps ops;
+    CK(alloc_rows(ctx, precision, rows_total, dim_pad, ops));
+    int64_t max_ld = 0, max_rows = 0;
+    for (const auto &g : groups) {
+        const int64_t ld = round_up(c.scenes[g.sid].n, 32);
+        max_ld = std::max(max_ld, ld);
+        max_rows = std::max(max_rows, g.nq + g.nc);
+    }
+    const int64_t chunk_rows = std::max<int64_t>(1, std::min<int64_t>(max_rows, (int64_t)(kSimCapBytes / (max_ld * 4))));
+    float *d_sim;
+    CK(ws_get(ctx, farm::B_SIM, (size_t)chunk_rows * max_ld, &d_sim));
+
+    // ---- stage 0: inputs and normalisation
+    const int m0 = mark_begin(ctx, 0);
+    CK(cudaMemcpyAsync(d_rowmap, h_rowmap, (size_t)(n_q + n_c) * 4, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(d_perm, h_perm, (size_t)n_q * 4, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(d_meta, h_meta, (size_t)n_q * 8 * 4, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaEventRecord(ctx->stage_done, c.stream));
+    const float *src_t = tgt_emb, *src_c = c_emb;
+    if (!dev) {
+        CK(ws_get(ctx, farm::B_RAW, (size_t)(n_q + n_c) * dim, &d_raw));
+        CK(cudaMemcpyAsync(d_raw, tgt_emb, (size_t)n_q * dim * 4, cudaMemcpyHostToDevice, c.stream));
+        if (n_c > 0)
+            CK(cudaMemcpyAsync(d_raw + (size_t)n_q * dim, c_emb, (size_t)n_c * dim * 4, cudaMemcpyHostToDevice,
+                               c.stream));
+        src_t = d_raw;
+        src_c = d_raw + (size_t)n_q * dim;
+    }
+    LAUNCH(farm::launch_normalize_rows(src_t, d_rowmap, n_q, dim, dim_pad, ops.q32, ops.qhi, ops.qlo, ops.qbf,
+                                       c.d_err, farm::kErrBadRow, c.stream));
+    if (n_c > 0)
+        LAUNCH(farm::launch_normalize_rows(src_c, d_rowmap + n_q, n_c, dim, dim_pad, ops.q32, ops.qhi, ops.qlo,
+                                           ops.qbf, c.d_err, farm::kErrBadRow, c.stream));
+    mark_end(ctx, m0);
+
+    // ---- stages 1-2: similarity and rank selection per scene group, in row chunks
+    for (const auto &g : groups) {
+        const Scene &s = c.scenes[g.sid];
+        const int64_t ld = round_up(s.n, 32);
+        const int64_t rows_g = g.nq + g.nc;
+        const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
+        const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
+        const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows_g, (int64_t)(kSimCapBytes / (ld * 4))));
+        for (int64_t r0 = 0; r0 < rows_g; r0 += chunk) {
+            const int64_t r1 = std::min(rows_g, r0 + chunk);
+            const int m1 = mark_begin(ctx, 1);
+            farm_status st = run_similarity(ctx, precision, ops, g.row0 + r0, r1 - r0, s, d_sim, ld);
+            if (st != FARM_OK) return st;
+            mark_end(ctx, m1);
+            const int64_t ntr = std::max<int64_t>(0, std::min<int64_t>(g.nq - r0, r1 - r0));
+            const int m2 = mark_begin(ctx, 2);
+            LAUNCH(farm::launch_select_rows(d_sim, ld, s.n, r1 - r0, ntr, Rs, klm, tsel_idx, tsel_cos,
+                                            g.q0 + r0, stride_t, lsel_idx, g.cp0 + r0 + ntr - g.nq, stride_l,
+                                            c.stream));
+            mark_end(ctx, m2);
+        }
+    }
+
+    // ---- stage 3: relations, composite, sort
+    const int m3 = mark_begin(ctx, 3);
+    farm::ComposeArgs ca;
+    ca.n_q = n_q;
+    ca.qmeta = d_meta;
+    ca.tsel_idx = tsel_idx;
+    ca.lsel_idx = lsel_idx;
+    ca.stride_t = stride_t;
+    ca.stride_l = stride_l;
+    ca.scenes = ctx->d_scenes;
+    ca.p = p;
+    ca.out_idx = o_idx;
+    ca.out_score = o_score;
+    ca.out_t = o_t;
+    ca.out_anchor = o_anc;
+    LAUNCH(farm::launch_compose(ca, c.stream));
+    mark_end(ctx, m3);
+
+    c.batch_gen += 1;
+    c.batch_valid = true;
+    c.batch_nq = n_q;
+    c.batch_nc = n_c;
+    c.batch_rtgt = stride_t;
+    c.batch_klm = stride_l;
+    c.batch_min_n = (int32_t)std::min<int64_t>(min_n, 0x7fffffff);
+    *batch_handle = c.batch_gen;
+    return FARM_OK;
+}
+
+farm_status farm_topk(farm_ctx *ctx, uint64_t batch_handle, int32_t k, int32_t *out_idx, float *out_score,
+                      float *out_pred, int32_t *out_anchor, uint32_t flags)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    if (!c.batch_valid || batch_handle != c.batch_gen || batch_handle == 0)
+        return fail(ctx, FARM_ESTATE, "stale or unknown batch handle");
+    if (k < 1 || k > c.params.k_max) return fail(ctx, FARM_EINVAL, "k must lie in [1, k_max]");
+    if (c.batch_nq == 0) return FARM_OK;
+    if (k > c.batch_min_n) return fail(ctx, FARM_EINVAL, "k exceeds the object count of a scene in the batch");
+    if (!out_idx || !out_score) return fail(ctx, FARM_EINVAL, "out_idx and out_score must be non-null");
+    CK(cudaSetDevice(c.device));
+    const bool dev = (flags & FARM_PTR_DEVICE) != 0;
+    const int64_t n_q = c.batch_nq;
+    int32_t *d_perm = static_cast<int32_t *>(c.ws.ptr[farm::B_PERM]);
+    const int32_t *i_idx = static_cast<int32_t *>(c.ws.ptr[farm::B_OUT_IDX]);
+    const float *i_score = static_cast<float *>(c.ws.ptr[farm::B_OUT_SCORE]);
+    const float *i_t = static_cast<float *>(c.ws.ptr[farm::B_OUT_T]);
+    const int32_t *i_anc = static_cast<int32_t *>(c.ws.ptr[farm::B_OUT_ANCHOR]);
+    if (dev) {
+        LAUNCH(farm::launch_gather_topk(n_q, k, c.batch_rtgt, d_perm, i_idx, i_score, i_t, i_anc, out_idx,
+                                        out_score, out_pred, out_anchor, c.stream));
+        return FARM_OK;
+    }
+    // device staging: idx | score | t[4] | anchor[4] per entry
+    int32_t *s_idx;
+    CK(ws_get(ctx, farm::B_TOPK, (size_t)n_q * k * 10, &s_idx));
+    float *s_score = reinterpret_cast<float *>(s_idx + n_q * k);
+    float *s_t = out_pred ? reinterpret_cast<float *>(s_idx + n_q * k * 2) : nullptr;
+    int32_t *s_anc = out_anchor ? s_idx + n_q * k * 6 : nullptr;
+    LAUNCH(farm::launch_gather_topk(n_q, k, c.batch_rtgt, d_perm, i_idx, i_score, i_t, i_anc, s_idx, s_score,
+                                    s_t, s_anc, c.stream));
+    CK(cudaMemcpyAsync(out_idx, s_idx, (size_t)n_q * k * 4, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(out_score, s_score, (size_t)n_q * k * 4, cudaMemcpyDeviceToHost, c.stream));
+    if (out_pred) CK(cudaMemcpyAsync(out_pred, s_t, (size_t)n_q * k * 16, cudaMemcpyDeviceToHost, c.stream));
+    if (out_anchor) CK(cudaMemcpyAsync(out_anchor, s_anc, (size_t)n_q * k * 16, cudaMemcpyDeviceToHost, c.stream));
+    return check_device_errors(ctx);
+}
+
+farm_status farm_sync(farm_ctx *ctx)
+{
+    if (!ctx) return FARM_EINVAL;
+    CK(cudaSetDevice(ctx->c.device));
+    return check_device_errors(ctx);
+}
+
+farm_status farm_similarity(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb, int32_t precision,
+                            float *out, uint32_t flags)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    if (scene_id < 0 || scene_id >= kMaxScenes || !c.scenes[scene_id].present)
+        return fail(ctx, FARM_EINVAL, "unknown scene");
+    if (n_rows < 0) return fail(ctx, FARM_EINVAL, "n_rows must be >= 0");
+    if (n_rows == 0) return FARM_OK;
+    if (!emb || !out) return fail(ctx, FARM_EINVAL, "emb and out must be non-null");
+    if (precision != FARM_PREC_FP32 && precision != FARM_PREC_FP32_SIMT)
+        return fail(ctx, FARM_EINVAL, "similarity is available for FP32 and FP32_SIMT");
+    CK(cudaSetDevice(c.device));
+    const Scene &s = c.scenes[scene_id];
+    const bool dev = (flags & FARM_PTR_DEVICE) != 0;
+    const float *src = emb;
+    if (!dev) {
+        float *raw;
+        CK(ws_get(ctx, farm::B_RAW, (size_t)n_rows * s.dim, &raw));
+        CK(cudaMemcpyAsync(raw, emb, (size_t)n_rows * s.dim * 4, cudaMemcpyHostToDevice, c.stream));
+        src = raw;
+    }
+    RowOps ops;
+    CK(alloc_rows(ctx, precision, n_rows, s.dim_pad, ops));
+    LAUNCH(farm::launch_normalize_rows(src, nullptr, n_rows, s.dim, s.dim_pad, ops.q32, ops.qhi, ops.qlo, ops.qbf,
+                                       c.d_err, farm::kErrBadRow, c.stream));
+    float *S = out;
+    if (!dev) CK(ws_get(ctx, farm::B_SIM, (size_t)n_rows * s.n, &S));
+    farm_status st = run_similarity(ctx, precision, ops, 0, n_rows, s, S, s.n);
+    if (st != FARM_OK) return st;
+    if (!dev) {
+        CK(cudaMemcpyAsync(out, S, (size_t)n_rows * s.n * 4, cudaMemcpyDeviceToHost, c.stream));
+        return check_device_errors(ctx);
+    }
+    return FARM_OK;
+}
+
+farm_status farm_candidates(farm_ctx *ctx, uint64_t batch_handle, int32_t *tgt_idx, int32_t *lm_idx,
+                            int32_t *r_tgt_out, int32_t *k_lm_out)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    if (!c.batch_valid || batch_handle != c.batch_gen || batch_handle == 0)
+        return fail(ctx, FARM_ESTATE, "stale or unknown batch handle");
+    if (r_tgt_out) *r_tgt_out = c.batch_rtgt;
+    if (k_lm_out) *k_lm_out = c.batch_klm;
+    if (c.batch_nq == 0) return FARM_OK;
+    CK(cudaSetDevice(c.device));
+    const int64_t n_q = c.batch_nq, n_c = c.batch_nc;
+    std::vector<int32_t> t((size_t)n_q * c.batch_rtgt), l((size_t)std::max<int64_t>(n_c, 1) * c.batch_klm);
+    CK(cudaMemcpyAsync(t.data(), c.ws.ptr[farm::B_TSEL_IDX], t.size() * 4, cudaMemcpyDeviceToHost, c.stream));
+    if (n_c > 0)
+        CK(cudaMemcpyAsync(l.data(), c.ws.ptr[farm::B_LSEL_IDX], (size_t)n_c * c.batch_klm * 4,
+                           cudaMemcpyDeviceToHost, c.stream));
+    farm_status st = check_device_errors(ctx);
+    if (st != FARM_OK) return st;
+    if (tgt_idx)
+        for (int64_t q = 0; q < n_q; ++q)
+            std::memcpy(tgt_idx + q * c.batch_rtgt, t.data() + (size_t)ctx->h_perm[q] * c.batch_rtgt,
+                        (size_t)c.batch_rtgt * 4);
+    if (lm_idx)
+        for (int64_t i = 0; i < n_c; ++i)
+            std::memcpy(lm_idx + i * c.batch_klm, l.data() + (size_t)ctx->h_cplan[i] * c.batch_klm,
+                        (size_t)c.batch_klm * 4);
+    return FARM_OK;
+}
+
+farm_status farm_set_profiling(farm_ctx *ctx, int32_t on)
+{
+    if (!ctx) return FARM_EINVAL;
+    ctx->c.profiling = on != 0;
+    return FARM_OK;
+}
+
+farm_status farm_stage_times(farm_ctx *ctx, float *ms_out, int64_t *launches_out, int32_t reset)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    CK(cudaSetDevice(c.device));
+    CK(cudaStreamSynchronize(c.stream));
+    for (auto &m : ctx->marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess && m.stage >= 0 && m.stage < FARM_N_STAGES)
+            c.stage_ms[m.stage] += ms;
+        ctx->pool.push_back(m.a);
+        ctx->pool.push_back(m.b);
+    }
+    ctx->marks.clear();
+    if (ms_out)
+        for (int i = 0; i < FARM_N_STAGES; ++i) ms_out[i] = (float)c.stage_ms[i];
+    if (launches_out) *launches_out = c.launches;
+    if (reset) {
+        for (int i = 0; i < FARM_N_STAGES; ++i) c.stage_ms[i] = 0.0;
+        c.launches = 0;
+    }
+    return FARM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// farm_internal.h -- device data layout and kernel entry points shared by the
+// translation units of libfarm (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/farm.h"
+
+namespace farm {
+
+// Descriptor rows are zero-padded to a multiple of this many elements so
+// that every row starts on a 256-byte boundary for the tensor-memory-access
+// (TMA) loads of the tensor-core kernels; zero padding leaves dot products
+// unchanged.
+constexpr int kDimAlign = 64;
+
+// Largest target-candidate list (ranks kept per target row) and landmark
+// list (K_a) the select and compose kernels handle.
+constexpr int kMaxTargetCands = 512;
+constexpr int kMaxAnchorCands = 256;
+
+// Per stored view, the compose kernel reads 8 floats: camera origin (3),
+// unit viewing direction f (3) and unit right vector r = f x z_up (2; its z
+// component is 0).  A view whose direction is zero or vertical has f = 0,
+// which no depth test passes (z_min >= 0).
+constexpr int kViewStride = 8;
+
+// Bits of the device error word.
+constexpr int kErrBadRow = 1;        // zero or non-finite embedding row
+constexpr int kErrBadDesc = 2;       // zero or non-finite descriptor row
+constexpr int kErrTimeout = 4;       // a bounded wait gave up
+
+struct Scene {
+    bool present = false;
+    int64_t n = 0;
+    int32_t dim = 0;
+    int32_t dim_pad = 0;
+    int32_t n_views = 0;
+    float *desc32 = nullptr;    // [n, dim_pad] unit rows, FP32
+    float *desc_hi = nullptr;   // [n, dim_pad] TF32-representable high part
+    float *desc_lo = nullptr;   // [n, dim_pad] residual desc32 - desc_hi
+    uint16_t *desc_bf16 = nullptr;  // [n, dim_pad] BF16 of desc32
+    int32_t *cls = nullptr;     // [n]
+    float *pos = nullptr;       // [3, n] centres (SoA)
+    float *size = nullptr;      // [3, n]
+    float *views = nullptr;     // [n, n_views, kViewStride]
+};
+
+struct Workspace {
+    // grow-only device buffers (bytes recorded alongside)
+    void *ptr[24] = {};
+    size_t bytes[24] = {};
+};
+
+enum Buf {
+    B_RAW = 0,      // raw embedding rows as given [n_q + n_c, dim]
+    B_Q32,          // normalised rows [rows, dim_pad]
+    B_QHI,          // TF32 high part
+    B_QLO,          // TF32 residual
+    B_QBF,          // BF16 rows
+    B_SIM,          // similarity block [rows_chunk, n]
+    B_ROWMAP,       // int32 [n_q + n_c] planned row of each source row
+    B_PERM,         // int32 [n_q] planned position of each caller query
+    B_TSEL_IDX,     // int32 [n_q, r_tgt] target candidates
+    B_TSEL_COS,     // float [n_q, r_tgt]
+    B_LSEL_IDX,     // int32 [n_c, k_lm] landmark candidates
+    B_QMETA,        // int32 [n_q, 8] per-query metadata
+    B_OUT_IDX,      // int32 [n_q, r_tgt] composed candidates, best first
+    B_OUT_SCORE,    // float [n_q, r_tgt]
+    B_OUT_T,        // float [n_q, r_tgt, 4]
+    B_OUT_ANCHOR,   // int32 [n_q, r_tgt, 4]
+    B_TOPK,         // int32/float [n_q, k, 10] TopK staging for host outputs
+    B_COUNT
+};
+
+// Per-query metadata row (int32 x 8) consumed by the compose kernel.
+enum QMeta {
+    QM_SCENE = 0, QM_CLS, QM_M, QM_C0, QM_PRED01, QM_PRED23, QM_R, QM_KLM
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    farm_params params{};
+    std::string err;
+    std::vector<Scene> scenes;
+    Workspace ws;
+    int32_t *d_err = nullptr;     // device error word
+    int32_t *h_err = nullptr;     // pinned host mirror
+    // batch state
+    uint64_t batch_gen = 0;
+    bool batch_valid = false;
+    int64_t batch_nq = 0;
+    int64_t batch_nc = 0;
+    int32_t batch_rtgt = 0;       // candidate list length (stride)
+    int32_t batch_klm = 0;        // landmark list length (stride)
+    int32_t batch_min_n = 0;      // smallest scene size in the batch
+    // profiling
+    bool profiling = false;
+    cudaEvent_t ev[8] = {};
+    double stage_ms[FARM_N_STAGES] = {};
+    int64_t launches = 0;
+    int num_sms = 0;
+};
+
+// ---- kernel launchers (each returns cudaGetLastError() after launching) ----
+
+// Unit-normalise `rows` rows of length dim into dst rows of length dim_pad
+// (zero tail); optionally also write the TF32 split and BF16 copies.  Rows
+// with zero or non-finite norm set err_bit in *err and are written as zeros.
+// dst_rows: optional int32 [rows] scatter map (src row r goes to dst row dst_rows[r]).
+cudaError_t launch_normalize_rows(const float *src, const int32_t *dst_rows, int64_t rows,
+                                  int32_t dim, int32_t dim_pad, float *dst32, float *dst_hi,
+                                  float *dst_lo, uint16_t *dst_bf16, int32_t *err, int err_bit,
+                                  cudaStream_t s);
+
+// Pre-compute the per-view record of kViewStride floats from SoA views.
+cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_views,
+                                 float *out, cudaStream_t s);
+
+// S[r, j] = <Q[r], D[j]> for r < rows, j < n (FP32 FMA, CUDA cores).
+cudaError_t launch_sim_simt(const float *q, const float *d, float *S, int64_t rows, int64_t n,
+                            int32_t dim_pad, int64_t ld_s, cudaStream_t s);
+
+// Same product on the tensor cores with three TF32 terms (hi*hi + hi*lo + lo*hi).
+cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const float *d_hi,
+                                 const float *d_lo, float *S, int64_t rows, int64_t n,
+                                 int32_t dim_pad, int64_t ld_s, int num_sms, cudaStream_t s);
+bool sim_tc_available();
+
+// Per row r of S (rows x n, leading dim ld_s): the R_r largest entries in
+// (value desc, index asc) order, R_r = r < n_tgt_rows ? r_tgt : r_lm.
+// Target rows write tsel_idx/tsel_cos[r * r_tgt + k]; landmark rows write
+// lsel_idx[(r - n_tgt_rows) * k_lm + k].  Rows are numbered from row0 in the
+// output arrays (tsel row = tsel_row0 + r, lsel row = lsel_row0 + r - n_tgt_rows).
+cudaError_t launch_select_rows(const float *S, int64_t ld_s, int64_t n, int64_t rows,
+                               int64_t n_tgt_rows, int32_t r_tgt, int32_t k_lm,
+                               int32_t *tsel_idx, float *tsel_cos, int64_t tsel_row0,
+                               int32_t stride_t, int32_t *lsel_idx, int64_t lsel_row0,
+                               int32_t stride_l, cudaStream_t s);
+
+// Device-side view of one scene, indexed by scene id in a device table.
+struct SceneDev {
+    const float *pos;       // [3, n]
+    const float *views;     // [n, n_views, kViewStride]
+    const int32_t *cls;     // [n]
+    int64_t n;
+    int32_t n_views;
+    int32_t pad;
+};
+
+struct ComposeArgs {
+    int64_t n_q;
+    const int32_t *qmeta;       // [n_q, 8] (planned query order)
+    const int32_t *tsel_idx;    // [n_q, stride_t]
+    const int32_t *lsel_idx;    // [n_c, stride_l]
+    int32_t stride_t, stride_l;
+    const SceneDev *scenes;     // device table indexed by scene id
+    farm_params p;
+    int32_t *out_idx;           // [n_q, stride_t]
+    float *out_score;
+    float *out_t;               // [n_q, stride_t, 4]
+    int32_t *out_anchor;
+};
+cudaError_t launch_compose(const ComposeArgs &a, cudaStream_t s);
+
+// out[q * k + j] = src[perm[q] * ld + j] (and the 4-wide breakdown): the TopK
+// prefix of each query's sorted candidates, back in the caller's query order.
+cudaError_t launch_gather_topk(int64_t n_q, int32_t k, int32_t ld, const int32_t *perm,
+                               const int32_t *idx,
+                               const float *score, const float *t, const int32_t *anchor,
+                               int32_t *o_idx, float *o_score, float *o_t, int32_t *o_anchor,
+                               cudaStream_t s);
+
+}  // namespace farm

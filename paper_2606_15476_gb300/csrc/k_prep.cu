@@ -1,0 +1,117 @@
+// k_prep.cu -- row normalisation, operand splits and per-view records.
+//
+// Descriptors and query embeddings enter the similarity stage (App. D.2
+// step 3) as unit vectors, so a dot product is the cosine.  For the
+// FP32-accurate tensor-core path every unit row x is also stored as
+//   x_hi = x rounded to TF32 (11 significant bits),  x_lo = TF32(x - x_hi),
+// so that x_hi*y_hi + x_hi*y_lo + x_lo*y_hi reproduces x*y to about 2^-21
+// relative per product (the dropped x_lo*y_lo term and the rounding of x_lo
+// are both of that order).
+#include <cuda_bf16.h>
+
+#include "farm_internal.h"
+
+namespace farm {
+namespace {
+
+__device__ __forceinline__ float tf32_round(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// One warp per row.
+__global__ void normalize_rows_kernel(const float *__restrict__ src, const int32_t *__restrict__ dst_rows,
+                                      int64_t rows, int32_t dim, int32_t dim_pad,
+                                      float *__restrict__ dst32, float *__restrict__ dst_hi,
+                                      float *__restrict__ dst_lo, uint16_t *__restrict__ dst_bf16,
+                                      int32_t *err, int err_bit)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    const float *x = src + row * (int64_t)dim;
+    float ss = 0.f;
+    for (int k = lane; k < dim; k += 32) ss = fmaf(x[k], x[k], ss);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const float nrm = sqrtf(ss);
+    const bool bad = !(nrm > 0.f) || !isfinite(nrm);
+    if (bad && lane == 0) atomicOr(err, err_bit);
+    const int64_t drow = dst_rows ? (int64_t)dst_rows[row] : row;
+    const int64_t base = drow * (int64_t)dim_pad;
+    for (int k = lane; k < dim_pad; k += 32) {
+        float v = (k < dim && !bad) ? x[k] / nrm : 0.f;
+        if (dst32) dst32[base + k] = v;
+        if (dst_hi) {
+            float hi = tf32_round(v);
+            dst_hi[base + k] = hi;
+            dst_lo[base + k] = tf32_round(v - hi);
+        }
+        if (dst_bf16) {
+            __nv_bfloat16 b = __float2bfloat16_rn(v);
+            dst_bf16[base + k] = *reinterpret_cast<uint16_t *>(&b);
+        }
+    }
+}
+
+// One thread per (object, view).
+__global__ void prepare_views_kernel(const float *__restrict__ v, int64_t n, int32_t n_views,
+                                     float *__restrict__ out)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * n_views) return;
+    const int64_t j = t / n_views;
+    const int32_t w = (int32_t)(t - j * n_views);
+    const int64_t plane = (int64_t)n_views * n;
+    const int64_t at = (int64_t)w * n + j;
+    float ox = v[0 * plane + at], oy = v[1 * plane + at], oz = v[2 * plane + at];
+    float fx = v[3 * plane + at], fy = v[4 * plane + at], fz = v[5 * plane + at];
+    float fn = sqrtf(fx * fx + fy * fy + fz * fz);
+    float rx = 0.f, ry = 0.f;
+    if (fn > 0.f && isfinite(fn)) {
+        fx /= fn; fy /= fn; fz /= fn;
+        rx = fy; ry = -fx;
+        float rn = sqrtf(rx * rx + ry * ry);
+        if (rn > 0.f) {
+            rx /= rn; ry /= rn;
+        } else {
+            fx = fy = fz = 0.f; rx = ry = 0.f;
+        }
+    } else {
+        fx = fy = fz = 0.f;
+    }
+    float *o = out + t * kViewStride;
+    o[0] = ox; o[1] = oy; o[2] = oz;
+    o[3] = fx; o[4] = fy; o[5] = fz;
+    o[6] = rx; o[7] = ry;
+}
+
+}  // namespace
+
+cudaError_t launch_normalize_rows(const float *src, const int32_t *dst_rows, int64_t rows,
+                                  int32_t dim, int32_t dim_pad, float *dst32, float *dst_hi,
+                                  float *dst_lo, uint16_t *dst_bf16, int32_t *err, int err_bit,
+                                  cudaStream_t s)
+{
+    if (rows <= 0) return cudaSuccess;
+    const int warps = 8;
+    const int64_t blocks = (rows + warps - 1) / warps;
+    normalize_rows_kernel<<<(unsigned)blocks, warps * 32, 0, s>>>(src, dst_rows, rows, dim, dim_pad,
+                                                                   dst32, dst_hi, dst_lo, dst_bf16,
+                                                                   err, err_bit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_views, float *out,
+                                 cudaStream_t s)
+{
+    const int64_t total = n * n_views;
+    if (total <= 0) return cudaSuccess;
+    const int th = 256;
+    prepare_views_kernel<<<(unsigned)((total + th - 1) / th), th, 0, s>>>(views_soa, n, n_views, out);
+    return cudaGetLastError();
+}
+
+}  // namespace farm

@@ -1,0 +1,235 @@
+"""ctypes binding of libfarm (include/farm.h), one function per C entry point.
+
+Argument marshalling only: numpy arrays are host pointers, CUDA torch tensors
+are device pointers (FARM_PTR_DEVICE); every step of the computation runs in
+the library's kernels.  If libfarm.so is missing this module raises at import
+time -- there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+PREC_FP32 = 0
+PREC_BF16 = 1
+PREC_FP32_SIMT = 3
+PTR_DEVICE = 1
+N_STAGES = 4
+STATUS = {0: "FARM_OK", 1: "FARM_EINVAL", 2: "FARM_ENOMEM", 3: "FARM_ECUDA", 4: "FARM_ESTATE",
+          5: "FARM_ETIMEOUT"}
+
+
+class FarmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+
+
+class FarmParams(C.Structure):
+    _fields_ = [("mu", C.c_float), ("w", C.c_float), ("class_mis", C.c_float),
+                ("sigma_near", C.c_float), ("tau_v", C.c_float), ("tau_h", C.c_float),
+                ("z_min", C.c_float), ("k_anchor", C.c_int32), ("k_max", C.c_int32),
+                ("rescore", C.c_int32)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libfarm.so is not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P, I32, I64, U32, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+    sig = {
+        "farm_default_params": (None, [P]),
+        "farm_create": (C.c_int, [P, C.c_int, P, P]),
+        "farm_destroy": (C.c_int, [P]),
+        "farm_memory_upload": (C.c_int, [P, I32, I64, I32, P, P, P, I32, P, U32]),
+        "farm_query_batch": (C.c_int, [P, I64, P, P, P, P, P, P, I32, U32, P]),
+        "farm_topk": (C.c_int, [P, U64, I32, P, P, P, P, U32]),
+        "farm_sync": (C.c_int, [P]),
+        "farm_similarity": (C.c_int, [P, I32, I64, P, I32, P, U32]),
+        "farm_candidates": (C.c_int, [P, U64, P, P, P, P]),
+        "farm_set_profiling": (C.c_int, [P, I32]),
+        "farm_stage_times": (C.c_int, [P, P, P, I32]),
+        "farm_last_error": (C.c_char_p, [P]),
+        "farm_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def exported_symbols():
+    return ["farm_default_params", "farm_create", "farm_destroy", "farm_memory_upload",
+            "farm_query_batch", "farm_topk", "farm_sync", "farm_similarity", "farm_candidates",
+            "farm_set_profiling", "farm_stage_times", "farm_last_error", "farm_version"]
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+class _Arr:
+    """A pointer plus the object that keeps its memory alive."""
+
+    def __init__(self, x, dtype, name, allow_device=True):
+        self.keep = None
+        self.device = False
+        if x is None:
+            self.ptr = None
+            return
+        if _is_cuda_tensor(x):
+            if not allow_device:
+                raise FarmError(1, f"{name} must be host memory")
+            import torch
+            tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+            t = x if (x.dtype == tdt and x.is_contiguous()) else x.to(tdt).contiguous()
+            self.keep = t
+            self.ptr = C.c_void_p(t.data_ptr())
+            self.device = True
+            return
+        if hasattr(x, "numpy") and not isinstance(x, np.ndarray):
+            x = x.detach().cpu().numpy()
+        a = np.ascontiguousarray(x, dtype=dtype)
+        self.keep = a
+        self.ptr = a.ctypes.data_as(C.c_void_p)
+
+
+def _ck(ctx, st):
+    if st != 0:
+        msg = _lib.farm_last_error(ctx).decode() if ctx else ""
+        raise FarmError(st, msg)
+
+
+def _flags(*arrs):
+    devs = {a.device for a in arrs if a.ptr is not None}
+    if len(devs) > 1:
+        raise FarmError(1, "mixing host and device arrays in one call")
+    return PTR_DEVICE if devs == {True} else 0
+
+
+def farm_version() -> str:
+    return _lib.farm_version().decode()
+
+
+def farm_default_params() -> FarmParams:
+    p = FarmParams()
+    _lib.farm_default_params(C.byref(p))
+    return p
+
+
+def farm_create(device: int = 0, stream=None, params: FarmParams | None = None):
+    ctx = C.c_void_p()
+    s = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    st = _lib.farm_create(C.byref(ctx), int(device), s, C.byref(params) if params else None)
+    if st != 0:
+        raise FarmError(st, "farm_create failed (bad params or no CUDA device)")
+    return ctx
+
+
+def farm_destroy(ctx) -> None:
+    _ck(None, _lib.farm_destroy(ctx))
+
+
+def farm_last_error(ctx) -> str:
+    return _lib.farm_last_error(ctx).decode()
+
+
+def farm_memory_upload(ctx, scene_id: int, desc, cls, box, views=None) -> None:
+    d = _Arr(desc, np.float32, "desc")
+    c = _Arr(cls, np.int32, "cls")
+    b = _Arr(box, np.float32, "box")
+    n, dim = (int(desc.shape[0]), int(desc.shape[1]))
+    n_views = 0 if views is None else int(views.shape[1])
+    v = _Arr(views if n_views > 0 else None, np.float32, "views")
+    flags = _flags(d, c, b, v)
+    _ck(ctx, _lib.farm_memory_upload(ctx, int(scene_id), n, dim, d.ptr, c.ptr, b.ptr, n_views,
+                                     v.ptr, flags))
+
+
+def farm_query_batch(ctx, scene_of_q, tgt_emb, tgt_cls, c_off, c_pred, c_emb,
+                     precision: int = PREC_FP32) -> int:
+    n_q = int(len(tgt_cls))
+    s = _Arr(scene_of_q, np.int32, "scene_of_q", allow_device=False)
+    tc = _Arr(tgt_cls, np.int32, "tgt_cls", allow_device=False)
+    co = _Arr(c_off, np.int32, "c_off", allow_device=False)
+    cp = _Arr(c_pred, np.int32, "c_pred", allow_device=False)
+    te = _Arr(tgt_emb, np.float32, "tgt_emb")
+    ce = _Arr(c_emb, np.float32, "c_emb")
+    flags = _flags(te, ce)
+    h = C.c_uint64()
+    _ck(ctx, _lib.farm_query_batch(ctx, n_q, s.ptr, te.ptr, tc.ptr, co.ptr, cp.ptr, ce.ptr,
+                                   int(precision), flags, C.byref(h)))
+    return int(h.value)
+
+
+def farm_topk(ctx, handle: int, k: int, n_q: int, out_idx=None, out_score=None, out_pred=None,
+              out_anchor=None, breakdown: bool = True):
+    """TopK of a batch.  Without output arrays, returns new numpy arrays."""
+    if out_idx is None:
+        out_idx = np.zeros((n_q, k), np.int32)
+        out_score = np.zeros((n_q, k), np.float32)
+        if breakdown:
+            out_pred = np.zeros((n_q, k, 4), np.float32)
+            out_anchor = np.zeros((n_q, k, 4), np.int32)
+    arrs = [out_idx, out_score, out_pred, out_anchor]
+    dev = any(_is_cuda_tensor(a) for a in arrs if a is not None)
+    for a in arrs:
+        if a is None:
+            continue
+        if dev != _is_cuda_tensor(a):
+            raise FarmError(1, "mixing host and device outputs")
+        if not dev and not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+            raise FarmError(1, "host outputs must be C-contiguous numpy arrays")
+    ptr = (lambda a: None if a is None else C.c_void_p(a.data_ptr() if dev else a.ctypes.data))
+    _ck(ctx, _lib.farm_topk(ctx, C.c_uint64(handle), int(k), ptr(out_idx), ptr(out_score),
+                            ptr(out_pred), ptr(out_anchor), PTR_DEVICE if dev else 0))
+    return dict(idx=out_idx, score=out_score, pred=out_pred, anchor=out_anchor)
+
+
+def farm_sync(ctx) -> None:
+    _ck(ctx, _lib.farm_sync(ctx))
+
+
+def farm_similarity(ctx, scene_id: int, emb, n: int, precision: int = PREC_FP32, out=None):
+    e = _Arr(emb, np.float32, "emb")
+    rows = int(emb.shape[0])
+    if out is None:
+        out = np.zeros((rows, n), np.float32)
+    dev = _is_cuda_tensor(out)
+    if dev != e.device:
+        raise FarmError(1, "emb and out must both be host or both be device")
+    optr = C.c_void_p(out.data_ptr() if dev else out.ctypes.data)
+    _ck(ctx, _lib.farm_similarity(ctx, int(scene_id), rows, e.ptr, int(precision), optr,
+                                  PTR_DEVICE if dev else 0))
+    return out
+
+
+def farm_candidates(ctx, handle: int, n_q: int, n_c: int):
+    r = C.c_int32()
+    k = C.c_int32()
+    _ck(ctx, _lib.farm_candidates(ctx, C.c_uint64(handle), None, None, C.byref(r), C.byref(k)))
+    t = np.full((n_q, r.value), -1, np.int32)
+    l = np.full((max(n_c, 0), k.value), -1, np.int32)
+    _ck(ctx, _lib.farm_candidates(ctx, C.c_uint64(handle), t.ctypes.data_as(C.c_void_p),
+                                  l.ctypes.data_as(C.c_void_p), None, None))
+    return t, l
+
+
+def farm_set_profiling(ctx, on: bool) -> None:
+    _ck(ctx, _lib.farm_set_profiling(ctx, 1 if on else 0))
+
+
+def farm_stage_times(ctx, reset: bool = True):
+    ms = (C.c_float * N_STAGES)()
+    n = C.c_int64()
+    _ck(ctx, _lib.farm_stage_times(ctx, ms, C.byref(n), 1 if reset else 0))
+    return list(ms), int(n.value)

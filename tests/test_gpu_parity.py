@@ -1,0 +1,310 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: cosines within 1e-5 (absolute, unit vectors); composite scores
+within 1e-5 relative; TopK index lists equal wherever the oracle's result is
+unique at a cosine tie tolerance of 2e-5 (two cosines each within 1e-5 can
+only swap when they differ by at most 2e-5), otherwise valid under the
+oracle's bounds (oracle/parity.py).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import parity
+import synth
+from synth import QueryBatch, Scene
+
+pytestmark = pytest.mark.gpu
+
+# FARM_TEST_PREC restricts the run to one similarity path (default: both)
+_ONLY = os.environ.get("FARM_TEST_PREC")
+PRECISIONS = [_ONLY] if _ONLY else ["fp32", "fp32_simt"]
+DEFAULT = PRECISIONS[0]
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2606_15476_gb300 as F
+    return F
+
+
+def prec_code(F, name):
+    return {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16}[name]
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    c = F.farm_create(0)
+    yield c
+    F.farm_destroy(c)
+
+
+def run(F, ctx, qb, prec, k=10):
+    h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred,
+                           qb.c_emb, prec)
+    return h, F.farm_topk(ctx, h, k, qb.n_q)
+
+
+@pytest.fixture(scope="module")
+def room():
+    scenes, qb = synth.workload("room_n200_d512")
+    return scenes[0], qb
+
+
+@pytest.fixture(scope="module")
+def site():
+    scenes, qb = synth.workload("site_n20k_d1152")
+    return scenes[0], qb
+
+
+# ---- similarity (App. D.2 step 3) -------------------------------------------
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_cosines_within_1e5_of_fp64(F, ctx, room, prec):
+    sc, qb = room
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    rows = np.concatenate([qb.tgt_emb, qb.c_emb])
+    got = F.farm_similarity(ctx, 0, rows, sc.n, prec_code(F, prec))
+    for r in range(0, rows.shape[0], 7):
+        ref = oracle.cosines(sc, rows[r])
+        np.testing.assert_allclose(got[r], ref, rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_cosines_site_scale(F, ctx, site, prec):
+    sc, qb = site
+    F.farm_memory_upload(ctx, 1, sc.desc, sc.cls, sc.box, sc.views)
+    rows = np.concatenate([qb.tgt_emb[:40], qb.c_emb[:40]])
+    got = F.farm_similarity(ctx, 1, rows, sc.n, prec_code(F, prec))
+    err = 0.0
+    for r in range(0, rows.shape[0], 5):
+        ref = oracle.cosines(sc, rows[r])
+        err = max(err, float(np.max(np.abs(got[r] - ref))))
+    assert err <= 1e-5, err
+
+
+# ---- end-to-end parity -------------------------------------------------------
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_room_all_queries(F, ctx, room, prec):
+    sc, qb = room
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    h, out = run(F, ctx, qb, prec_code(F, prec))
+    rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"])
+    assert rep.ok(), rep.summary()
+    assert rep.n_exact >= qb.n_q // 2, rep.summary()
+    t, l = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
+    fails = parity.check_candidates(sc, qb, t, l)
+    assert not fails, fails[:3]
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_site_scene_query_slice(F, ctx, site, prec):
+    """The 20,000-object site scene, 160 queries: many tiles and a ragged tail."""
+    sc, qb = site
+    F.farm_memory_upload(ctx, 1, sc.desc, sc.cls, sc.box, sc.views)
+    sub = qb.subset(range(160))
+    sub.scene_of_q[:] = 1
+    h, out = run(F, ctx, sub, prec_code(F, prec))
+    rep = parity.check_topk(sc, sub, 10, out["idx"], out["score"], out["pred"], out["anchor"])
+    assert rep.ok(), rep.summary()
+    t, l = F.farm_candidates(ctx, h, sub.n_q, sub.n_c)
+    fails = parity.check_candidates(sc, sub, t, l, queries=range(0, 160, 8))
+    assert not fails, fails[:3]
+
+
+@pytest.mark.parametrize("prec", [DEFAULT])
+def test_site_full_batch_sampled(F, ctx, site, prec):
+    """All 4,096 queries in one batch (the benchmark's launch shape); 48 sampled checks."""
+    sc, qb = site
+    F.farm_memory_upload(ctx, 1, sc.desc, sc.cls, sc.box, sc.views)
+    qb = qb.subset(range(qb.n_q))
+    qb.scene_of_q[:] = 1
+    h, out = run(F, ctx, qb, prec_code(F, prec))
+    sample = np.random.default_rng(0).choice(qb.n_q, size=48, replace=False)
+    rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"],
+                            queries=sample)
+    assert rep.ok(), rep.summary()
+    # properties that hold for every query at any size
+    assert np.all(np.diff(out["score"], axis=1) <= 0)
+    assert np.all((out["idx"] >= 0) & (out["idx"] < sc.n))
+    m = np.diff(qb.c_off)
+    assert np.all(out["score"] > 0)
+    for q in range(0, qb.n_q, 97):
+        assert np.all(out["anchor"][q, :, m[q]:] == -1)
+
+
+# ---- edge cases ---------------------------------------------------------------
+
+def _scene_from(rng, n, dim, n_views=3, extent=(8.0, 8.0, 3.0)):
+    from scenes_util import tiny_scene
+    return tiny_scene(rng, n, dim, n_views=n_views, extent=extent)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("n,dim", [(5, 16), (1037, 100), (3, 7)])
+def test_small_and_ragged_scenes(F, ctx, prec, n, dim):
+    rng = np.random.default_rng(n * 31 + dim)
+    sc = _scene_from(rng, n, dim)
+    qb = synth.make_queries(5, Scene(desc=sc.desc, cls=sc.cls, box=sc.box, views=sc.views,
+                                     centroids=np.eye(3, dim), noise_sigma=0.3),
+                            24, m_choices=(0, 1, 2, 3, 4))
+    qb.scene_of_q[:] = 2
+    F.farm_memory_upload(ctx, 2, sc.desc, sc.cls, sc.box, sc.views)
+    k = min(10, n)
+    h, out = run(F, ctx, qb, prec_code(F, prec), k=k)
+    rep = parity.check_topk(sc, qb, k, out["idx"], out["score"], out["pred"], out["anchor"])
+    assert rep.ok(), rep.summary()
+
+
+def test_single_object_scene(F, ctx):
+    rng = np.random.default_rng(3)
+    sc = _scene_from(rng, 1, 8)
+    F.farm_memory_upload(ctx, 3, sc.desc, sc.cls, sc.box, sc.views)
+    qb = QueryBatch(tgt_emb=rng.standard_normal((2, 8)).astype(np.float32),
+                    tgt_cls=np.array([-1, 0], np.int32), c_off=np.array([0, 0, 2], np.int32),
+                    c_pred=np.array([0, 2], np.int32),
+                    c_emb=rng.standard_normal((2, 8)).astype(np.float32),
+                    scene_of_q=np.full(2, 3, np.int32))
+    h, out = run(F, ctx, qb, prec_code(F, DEFAULT), k=1)
+    assert out["idx"].tolist() == [[0], [0]]
+    # no witness: the only landmark is the target itself -> t = 0, score = (1-w) s_sem
+    assert out["score"][1, 0] == pytest.approx(0.5 * 1.0 / 6.0, rel=1e-6)
+    assert out["anchor"][1, 0, :2].tolist() == [-1, -1]
+    assert out["score"][0, 0] == pytest.approx(1.0 / 6.0, rel=1e-6)
+
+
+def test_multi_scene_batch(F, ctx):
+    rng = np.random.default_rng(9)
+    scenes = []
+    for sid, n in [(10, 300), (11, 57), (12, 1200)]:
+        sc = synth.make_scene(sid, n, 64, extent=(9.0, 9.0, 3.0), n_classes=6, n_views=4)
+        F.farm_memory_upload(ctx, sid, sc.desc, sc.cls, sc.box, sc.views)
+        scenes.append((sid, sc))
+    parts = []
+    for sid, sc in scenes:
+        parts.append(synth.make_queries(sid + 50, sc, 20, m_choices=(0, 1, 2, 4), scene_id=sid))
+    qb = synth.scenes.concat_batches(parts)
+    perm = rng.permutation(qb.n_q)       # interleave the scenes
+    qb = qb.subset(perm)
+    h, out = run(F, ctx, qb, prec_code(F, DEFAULT), k=10)
+    for sid, sc in scenes:
+        qs = np.flatnonzero(qb.scene_of_q == sid)
+        sub = qb.subset(qs)
+        rep = parity.check_topk(sc, sub, 10, out["idx"][qs], out["score"][qs], out["pred"][qs],
+                                out["anchor"][qs])
+        assert rep.ok(), (sid, rep.summary())
+
+
+def test_device_pointers_match_host(F, ctx, room):
+    import torch
+    sc, qb = room
+    F.farm_memory_upload(ctx, 4, torch.from_numpy(sc.desc).cuda(), torch.from_numpy(sc.cls).cuda(),
+                         torch.from_numpy(sc.box).cuda(), torch.from_numpy(sc.views).cuda())
+    sub = qb.subset(range(32))
+    sub.scene_of_q[:] = 4
+    h = F.farm_query_batch(ctx, sub.scene_of_q, torch.from_numpy(sub.tgt_emb).cuda(), sub.tgt_cls,
+                           sub.c_off, sub.c_pred, torch.from_numpy(sub.c_emb).cuda(), prec_code(F, DEFAULT))
+    di = torch.zeros((sub.n_q, 10), dtype=torch.int32, device="cuda")
+    ds = torch.zeros((sub.n_q, 10), dtype=torch.float32, device="cuda")
+    F.farm_topk(ctx, h, 10, sub.n_q, di, ds)
+    F.farm_sync(ctx)
+    h2, host = run(F, ctx, sub, prec_code(F, DEFAULT))
+    np.testing.assert_array_equal(di.cpu().numpy(), host["idx"])
+    np.testing.assert_array_equal(ds.cpu().numpy(), host["score"])
+
+
+def test_results_are_deterministic(F, ctx, room):
+    sc, qb = room
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    _, a = run(F, ctx, qb, prec_code(F, DEFAULT))
+    _, b = run(F, ctx, qb, prec_code(F, DEFAULT))
+    for key in ("idx", "score", "pred", "anchor"):
+        np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_worked_scene_on_gpu(F):
+    from scenes_util import golden_case, load_golden
+    g = load_golden("lamp_below_dartboard_left_of_poster.json")
+    p = F.farm_default_params()
+    p.k_anchor = g["params"]["k_anchor"]
+    c = F.farm_create(0, None, p)
+    try:
+        names = [o["name"] for o in g["objects"]]
+        for which, exp in g["expected"].items():
+            sc, qb = golden_case(g, which)
+            F.farm_memory_upload(c, 0, sc.desc, sc.cls, sc.box, sc.views)
+            _, out = run(F, c, qb, prec_code(F, DEFAULT), k=3)
+            assert names[out["idx"][0, 0]] == exp["top1"], which
+            assert out["score"][0, 0] == pytest.approx(exp["top1_score"], abs=exp["score_tol"])
+    finally:
+        F.farm_destroy(c)
+
+
+# ---- errors are reported, never faulted ------------------------------------------
+
+def test_invalid_calls(F, ctx, room):
+    sc, qb = room
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    sub = qb.subset(range(4))
+    h, _ = run(F, ctx, sub, prec_code(F, DEFAULT))
+    with pytest.raises(F.FarmError) as e:
+        F.farm_topk(ctx, h, 11, sub.n_q)          # k > k_max
+    assert e.value.status == 1
+    h2, _ = run(F, ctx, sub, prec_code(F, DEFAULT))
+    with pytest.raises(F.FarmError) as e:
+        F.farm_topk(ctx, h, 5, sub.n_q)           # stale handle
+    assert e.value.status == 4
+    bad = sub.subset(range(4))
+    bad.scene_of_q[:] = 77                        # unknown scene
+    with pytest.raises(F.FarmError):
+        run(F, ctx, bad, prec_code(F, DEFAULT))
+    bad = sub.subset(range(4))
+    bad.c_pred[:] = 9                             # unknown predicate
+    if bad.n_c:
+        with pytest.raises(F.FarmError):
+            run(F, ctx, bad, prec_code(F, DEFAULT))
+    five = QueryBatch(tgt_emb=sub.tgt_emb[:1], tgt_cls=sub.tgt_cls[:1],
+                      c_off=np.array([0, 5], np.int32), c_pred=np.zeros(5, np.int32),
+                      c_emb=np.repeat(sub.tgt_emb[:1], 5, axis=0), scene_of_q=np.zeros(1, np.int32))
+    with pytest.raises(F.FarmError):
+        run(F, ctx, five, prec_code(F, DEFAULT))            # 5 constraints
+    zero = sub.subset(range(2))
+    zero.tgt_emb[1] = 0.0                         # detected on the GPU, reported at the sync
+    h = F.farm_query_batch(ctx, zero.scene_of_q, zero.tgt_emb, zero.tgt_cls, zero.c_off,
+                           zero.c_pred, zero.c_emb, prec_code(F, DEFAULT))
+    with pytest.raises(F.FarmError) as e:
+        F.farm_topk(ctx, h, 5, zero.n_q)
+    assert e.value.status == 1
+    # the context stays usable
+    _, out = run(F, ctx, sub, prec_code(F, DEFAULT))
+    assert out["idx"].shape == (4, 10)
+
+
+def test_empty_batch(F, ctx, room):
+    sc, qb = room
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    empty = qb.subset([])
+    h = F.farm_query_batch(ctx, empty.scene_of_q, empty.tgt_emb, empty.tgt_cls, empty.c_off,
+                           empty.c_pred, empty.c_emb, prec_code(F, DEFAULT))
+    out = F.farm_topk(ctx, h, 10, 0)
+    assert out["idx"].shape == (0, 10)
+
+
+def test_stage_profiling_counts_launches(F, ctx, room):
+    sc, qb = room
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    F.farm_stage_times(ctx, reset=True)
+    F.farm_set_profiling(ctx, True)
+    run(F, ctx, qb, prec_code(F, DEFAULT))
+    ms, launches = F.farm_stage_times(ctx, reset=True)
+    F.farm_set_profiling(ctx, False)
+    assert launches >= 5
+    assert all(x > 0 for x in ms), ms
