@@ -206,7 +206,7 @@ farm_status run_similarity(farm_ctx *ctx, int32_t prec, const RowOps &ops, int64
         if (!farm::sim_tc_available())
             return fail(ctx, FARM_EINVAL, "the tensor-core FP32 similarity path is not built");
         LAUNCH(farm::launch_sim_tc_tf32x3(ops.qhi + off, ops.qlo + off, s.desc_hi, s.desc_lo, S,
-                                          rows, s.n, s.dim_pad, ld_s, c.num_sms, c.stream));
+                                          rows, s.n, s.dim_pad, ld_s, c.num_sms, c.d_err, c.stream));
         return FARM_OK;
     default:
         return fail(ctx, FARM_EINVAL, "precision not supported by this build");

@@ -130,7 +130,8 @@ cudaError_t launch_sim_simt(const float *q, const float *d, float *S, int64_t ro
 // Same product on the tensor cores with three TF32 terms (hi*hi + hi*lo + lo*hi).
 cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const float *d_hi,
                                  const float *d_lo, float *S, int64_t rows, int64_t n,
-                                 int32_t dim_pad, int64_t ld_s, int num_sms, cudaStream_t s);
+                                 int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err,
+                                 cudaStream_t s);
 bool sim_tc_available();
 
 // Per row r of S (rows x n, leading dim ld_s): the R_r largest entries in

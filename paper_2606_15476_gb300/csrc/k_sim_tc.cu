@@ -1,14 +1,337 @@
-// k_sim_tc.cu -- tensor-core similarity (placeholder until the tcgen05 kernel lands).
+// k_sim_tc.cu -- descriptor similarity on the 5th-generation tensor cores
+// (App. D.2 step 3: the cosine of every query row against every object).
+//
+//   S[r, j] = <q_r, d_j> ~= q_hi.d_hi + q_hi.d_lo + q_lo.d_hi      (three TF32 products)
+//
+// with x_hi = TF32(x) and x_lo = TF32(x - x_hi) prepared by the normalisation
+// kernel.  The dropped x_lo*y_lo term and the rounding of x_lo are each about
+// 2^-21 of |x*y|, so the result is FP32-accurate; all three products
+// accumulate into one FP32 accumulator in tensor memory (TMEM).
+//
+// Kernel organisation (one 128 x 256 tile of S per CTA, 192 threads):
+//   warp 0      TMA producer: for each 16-wide K slice loads q_hi, q_lo
+//               (128 rows) and d_hi, d_lo (256 rows) into one pipeline stage
+//               (64-byte swizzle), signalling a "full" mbarrier with the byte count;
+//   warp 1      allocates 256 TMEM columns; one thread issues, per K slice,
+//               2 K-steps x 3 products of tcgen05.mma.cta_group::1.kind::tf32
+//               (M=128, N=256, K=8) and tcgen05.commit to the stage's "empty"
+//               mbarrier, finally to the "accumulator ready" mbarrier;
+//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns at a time and store
+//               the rows of S (bounds-checked).
+// Four pipeline stages of 48 KB each.  Every mbarrier wait is bounded: on
+// expiry the kernel raises the error flag, stops issuing work, waits (bounded)
+// for the copies it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "farm_internal.h"
 
 namespace farm {
+namespace {
 
-bool sim_tc_available() { return false; }
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 16;                       // FP32 elements per K slice (64 bytes)
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 4;         // 8 KB
+constexpr int B_BYTES = BN * BK * 4;         // 16 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 48 KB
+constexpr int TMEM_COLS = 256;
+constexpr int THREADS = 192;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;    // try_wait polls before giving up (about a second)
+constexpr int GROUP_M = 16;                  // tile raster: 16 row tiles share each column tile
 
-cudaError_t launch_sim_tc_tf32x3(const float *, const float *, const float *, const float *, float *, int64_t,
-                                 int64_t, int32_t, int64_t, int, cudaStream_t)
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    return cudaErrorNotSupported;
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
+// 64 bytes, 8-row core groups 512 bytes apart (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)0 << 16;                             // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512u >> 4) << 32;                   // stride byte offset
+    d |= (uint64_t)1 << 46;                             // descriptor version
+    d |= (uint64_t)4 << 61;                             // layout: 64-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M=128, N=256.
+__host__ __device__ constexpr uint32_t idesc_tf32()
+{
+    return (1u << 4)                      // D format F32
+           | (2u << 7)                    // A format TF32
+           | (2u << 10)                   // B format TF32
+           | ((uint32_t)(BN >> 3) << 17)  // N / 8
+           | ((uint32_t)(BM >> 4) << 24); // M / 16
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc_tf32()), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+sim_tc_tf32x3_kernel(const __grid_constant__ CUtensorMap map_qhi, const __grid_constant__ CUtensorMap map_qlo,
+                     const __grid_constant__ CUtensorMap map_dhi, const __grid_constant__ CUtensorMap map_dlo,
+                     float *__restrict__ S, int64_t rows, int64_t n, int32_t k_slices, int64_t ld_s,
+                     int32_t m_tiles, int32_t n_tiles, int32_t *err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_ready = empty + STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_ready + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // grouped raster over (m tile, n tile)
+    const int tile = blockIdx.x;
+    const int per_group = GROUP_M * n_tiles;
+    const int g = tile / per_group;
+    const int first_m = g * GROUP_M;
+    const int gm = min(GROUP_M, m_tiles - first_m);
+    const int in_g = tile - g * per_group;
+    const int mt = first_m + in_g % gm;
+    const int nt = in_g / gm;
+    const int m0 = mt * BM, n0 = nt * BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_ready, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < k_slices; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u) || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                uint8_t *st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                const int kx = kb * BK;
+                tma_load_2d(st, &map_qhi, &full[s], kx, m0);
+                tma_load_2d(st + A_BYTES, &map_qlo, &full[s], kx, m0);
+                tma_load_2d(st + 2 * A_BYTES, &map_dhi, &full[s], kx, n0);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &map_dlo, &full[s], kx, n0);
+                issued = kb + 1;
+            }
+            if (*abort_flag) {
+                // let the copies already issued land before shared memory is released
+                for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+                    mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u);
+                atomicOr(err, kErrTimeout);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int kb = 0; kb < k_slices; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (!mbar_wait(&full[s], ph) || *abort_flag) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t a_hi = st, a_lo = st + A_BYTES;
+                const uint32_t b_hi = st + 2 * A_BYTES, b_lo = st + 2 * A_BYTES + B_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 8; ++kk) {
+                    const uint32_t off = kk * 32;     // 8 TF32 values = 32 bytes along K
+                    mma_tf32(tmem, smem_desc_sw64(a_hi + off), smem_desc_sw64(b_hi + off), (kb | kk) != 0);
+                    mma_tf32(tmem, smem_desc_sw64(a_hi + off), smem_desc_sw64(b_lo + off), 1u);
+                    mma_tf32(tmem, smem_desc_sw64(a_lo + off), smem_desc_sw64(b_hi + off), 1u);
+                }
+                mma_commit(&empty[s]);
+            }
+            if (ok) mma_commit(acc_ready);
+            else atomicOr(err, kErrTimeout);
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
+        const int quad = warp & 3;
+        const bool ready = mbar_wait(acc_ready, 0u) && !*abort_flag;
+        if (!ready) *abort_flag = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (ready) {
+            const int r_local = quad * 32 + lane;
+            const int64_t r = (int64_t)m0 + r_local;
+            float *srow = S + r * ld_s;
+            const bool vec = (ld_s % 4) == 0;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
+                const int64_t col0 = (int64_t)n0 + c * 32;
+                if (r < rows) {
+                    if (vec && col0 + 32 <= n) {
+#pragma unroll
+                        for (int i = 0; i < 32; i += 4)
+                            *reinterpret_cast<float4 *>(srow + col0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (col0 + i < n) srow[col0 + i] = v[i];
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool get_encoder()
+{
+    if (g_encode) return true;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return true;
+}
+
+// 2D FP32 tensor [outer, inner] row-major, box [box_outer, BK], 64-byte swizzle.
+bool make_map(CUtensorMap *m, const float *base, int64_t inner, int64_t outer, int box_outer)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * 4};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool sim_tc_available() { return get_encoder(); }
+
+cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const float *d_hi, const float *d_lo, float *S,
+                                 int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err,
+                                 cudaStream_t s)
+{
+    (void)num_sms;
+    if (rows <= 0 || n <= 0) return cudaSuccess;
+    if (dim_pad % BK != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (!get_encoder()) return cudaErrorNotSupported;
+    // TMA: 16-byte aligned bases and row strides (dim_pad is a multiple of 64 floats)
+    const uintptr_t al = (uintptr_t)q_hi | (uintptr_t)q_lo | (uintptr_t)d_hi | (uintptr_t)d_lo;
+    if (al & 15u) return cudaErrorMisalignedAddress;
+    CUtensorMap mqh, mql, mdh, mdl;
+    if (!make_map(&mqh, q_hi, dim_pad, rows, BM) || !make_map(&mql, q_lo, dim_pad, rows, BM) ||
+        !make_map(&mdh, d_hi, dim_pad, n, BN) || !make_map(&mdl, d_lo, dim_pad, n, BN))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(sim_tc_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const int m_tiles = (int)((rows + BM - 1) / BM);
+    const int n_tiles = (int)((n + BN - 1) / BN);
+    const int64_t tiles = (int64_t)m_tiles * n_tiles;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    sim_tc_tf32x3_kernel<<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(mqh, mql, mdh, mdl, S, rows, n, dim_pad / BK,
+                                                                        ld_s, m_tiles, n_tiles, err);
+    return cudaGetLastError();
 }
 
 }  // namespace farm

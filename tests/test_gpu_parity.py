@@ -167,6 +167,7 @@ def test_small_and_ragged_scenes(F, ctx, prec, n, dim):
 def test_single_object_scene(F, ctx):
     rng = np.random.default_rng(3)
     sc = _scene_from(rng, 1, 8)
+    sc.cls[:] = 0
     F.farm_memory_upload(ctx, 3, sc.desc, sc.cls, sc.box, sc.views)
     qb = QueryBatch(tgt_emb=rng.standard_normal((2, 8)).astype(np.float32),
                     tgt_cls=np.array([-1, 0], np.int32), c_off=np.array([0, 0, 2], np.int32),
