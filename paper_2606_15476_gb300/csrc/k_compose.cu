@@ -2,21 +2,26 @@
 // scoring of every kept target candidate (App. D.2 steps 4-5; App. B).
 //
 // One CTA per query.  The query's landmark candidates (K_a per constraint,
-// in rank order) and their centres are staged in shared memory; each thread
-// takes target candidates of rank r = 1, 2, ... and computes
+// in rank order) and their centres are staged in shared memory.  For every
+// kept target candidate of rank r the CTA computes
 //   s_sem = cf / (mu + r)                       (cf = class_mis on a class mismatch)
+// and the k_max-th largest s_sem, S_K.  k_max candidates score at least
+// (1 - w) S_K, so a candidate with s_sem < (1 - w) S_K cannot enter any TopK of
+// size <= k_max (its composite is at most s_sem); only the others are scored:
 //   t_i   = max_{a in L_i, a != e} r_rho_i(e, a)   (bound anchor = argmax, lower index on ties)
 //   gbar  = (prod_i t_i)^(1/m),  s = s_sem * ((1 - w) + w * gbar)
-// Because the composite is non-decreasing in every t_i and the anchors only
-// meet at the target, the best binding takes each anchor's best witness on its
-// own (the star decomposition of App. B).  The CTA then sorts its candidates
-// by (s descending, object index ascending) so that any TopK is a prefix.
+// with (candidate, constraint, landmark) triples spread over the threads and
+// the best witness kept by a 64-bit atomic max over (r, ~index).  Because the
+// composite is non-decreasing in every t_i and the anchors only meet at the
+// target, the best binding takes each anchor's best witness on its own (the
+// star decomposition of App. B).  The CTA then sorts the scored candidates by
+// (s descending, object index ascending) so that any TopK is a prefix.
 #include "farm_internal.h"
 
 namespace farm {
 namespace {
 
-constexpr int TH = 128;
+constexpr int TH = 256;
 
 __device__ __forceinline__ float sigm(float x)
 {
@@ -79,10 +84,14 @@ compose_kernel(ComposeArgs a)
 {
     __shared__ int32_t lm_idx[FARM_MAX_CONSTRAINTS][kMaxAnchorCands];
     __shared__ float lm_pos[FARM_MAX_CONSTRAINTS][kMaxAnchorCands][3];
+    __shared__ int32_t cand_e[kMaxTargetCands];
+    __shared__ float ssem[kMaxTargetCands];
+    __shared__ uint16_t surv[kMaxTargetCands];
+    __shared__ unsigned long long best[kMaxTargetCands][FARM_MAX_CONSTRAINTS];
     __shared__ uint64_t key[kMaxTargetCands];
     __shared__ uint16_t slot[kMaxTargetCands];
-    __shared__ float t_s[kMaxTargetCands][FARM_MAX_CONSTRAINTS];
-    __shared__ int32_t anc_s[kMaxTargetCands][FARM_MAX_CONSTRAINTS];
+    __shared__ float s_thr;
+    __shared__ int s_ns;
 
     const int64_t q = blockIdx.x;
     const int tid = threadIdx.x;
@@ -106,54 +115,81 @@ compose_kernel(ComposeArgs a)
         lm_pos[i][l][1] = sd.pos[sd.n + ai];
         lm_pos[i][l][2] = sd.pos[2 * sd.n + ai];
     }
-    __syncthreads();
-
     const int32_t *cand = a.tsel_idx + q * a.stride_t;
     for (int c = tid; c < R; c += TH) {
         const int32_t e = cand[c];
+        cand_e[c] = e;
         const float cf = (c_t >= 0 && sd.cls[e] != c_t) ? p.class_mis : 1.f;
-        const float s_sem = cf / (p.mu + (float)(c + 1));
+        ssem[c] = cf / (p.mu + (float)(c + 1));
+    }
+    if (tid == 0) { s_thr = 0.f; s_ns = 0; }
+    __syncthreads();
+    // S_K = the k_max-th largest s_sem; candidates below (1 - w) S_K cannot
+    // reach the TopK (k_max candidates score at least (1 - w) S_K).
+    if (R > p.k_max) {
+        for (int c = tid; c < R; c += TH) {
+            const float v = ssem[c];
+            int gt = 0, ge = 0;
+            for (int j = 0; j < R; ++j) {
+                gt += ssem[j] > v;
+                ge += ssem[j] >= v;
+            }
+            if (gt < p.k_max && p.k_max <= ge) s_thr = (1.f - p.w) * v;
+        }
+    }
+    __syncthreads();
+    const float thr = s_thr;
+    for (int c = tid; c < R; c += TH) {
+        if (ssem[c] >= thr) {
+            const int pos = atomicAdd(&s_ns, 1);
+            surv[pos] = (uint16_t)c;
+        }
+    }
+    __syncthreads();
+    const int ns = s_ns;
+    for (int t = tid; t < ns * FARM_MAX_CONSTRAINTS; t += TH) best[t / FARM_MAX_CONSTRAINTS][t % FARM_MAX_CONSTRAINTS] = 0ull;
+    __syncthreads();
+    // best witness per (survivor, constraint): max r, lower landmark index on ties
+    const int per = m * klm;
+    for (int t = tid; t < ns * per; t += TH) {
+        const int pos = t / per;
+        const int rem = t - pos * per;
+        const int i = rem / klm, l = rem - i * klm;
+        const int32_t e = cand_e[surv[pos]];
+        const int32_t ai = lm_idx[i][l];
+        if (ai == e) continue;
         const float ex = sd.pos[e], ey = sd.pos[sd.n + e], ez = sd.pos[2 * sd.n + e];
         const float *ve = sd.views + (int64_t)e * sd.n_views * kViewStride;
+        const float r = relation(preds[i], ex, ey, ez, lm_pos[i][l][0], lm_pos[i][l][1], lm_pos[i][l][2], ve,
+                                 sd.n_views, p);
+        const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) |
+                                     (unsigned long long)(0xffffffffu - (uint32_t)ai);
+        atomicMax(&best[pos][i], k);
+    }
+    __syncthreads();
+    for (int pos = tid; pos < ns; pos += TH) {
+        const int c = surv[pos];
         float t[FARM_MAX_CONSTRAINTS];
-        for (int i = 0; i < FARM_MAX_CONSTRAINTS; ++i) {
-            if (i >= m) {
-                t_s[c][i] = -1.f;
-                anc_s[c][i] = -1;
-                continue;
-            }
-            float best = 0.f;
-            int32_t arg = -1;
-            for (int l = 0; l < klm; ++l) {
-                const int32_t ai = lm_idx[i][l];
-                if (ai == e) continue;
-                const float r = relation(preds[i], ex, ey, ez, lm_pos[i][l][0], lm_pos[i][l][1],
-                                         lm_pos[i][l][2], ve, sd.n_views, p);
-                if (arg < 0 || r > best || (r == best && ai < arg)) { best = r; arg = ai; }
-            }
-            t[i] = arg < 0 ? 0.f : best;
-            t_s[c][i] = t[i];
-            anc_s[c][i] = arg;
+        bool zero = false;
+        for (int i = 0; i < m; ++i) {
+            const unsigned long long b = best[pos][i];
+            t[i] = b ? __uint_as_float((uint32_t)(b >> 32)) : 0.f;
+            zero |= !(t[i] > 0.f);
         }
         float g;
-        if (m == 0) {
-            g = 1.f;
-        } else {
-            bool zero = false;
-            for (int i = 0; i < m; ++i) zero |= !(t[i] > 0.f);
-            if (zero) g = 0.f;
-            else if (m == 1) g = t[0];
-            else if (m == 2) g = sqrtf(t[0] * t[1]);
-            else if (m == 3) g = cbrtf(t[0] * t[1] * t[2]);
-            else g = sqrtf(sqrtf(t[0] * t[1]) * sqrtf(t[2] * t[3]));
-        }
-        const float s = s_sem * ((1.f - p.w) + p.w * g);
-        key[c] = ((uint64_t)order_key(s) << 32) | (uint64_t)(0xffffffffu - (uint32_t)e);
-        slot[c] = (uint16_t)c;
+        if (m == 0) g = 1.f;
+        else if (zero) g = 0.f;
+        else if (m == 1) g = t[0];
+        else if (m == 2) g = sqrtf(t[0] * t[1]);
+        else if (m == 3) g = cbrtf(t[0] * t[1] * t[2]);
+        else g = sqrtf(sqrtf(t[0] * t[1]) * sqrtf(t[2] * t[3]));
+        const float s = ssem[c] * ((1.f - p.w) + p.w * g);
+        key[pos] = ((uint64_t)order_key(s) << 32) | (uint64_t)(0xffffffffu - (uint32_t)cand_e[c]);
+        slot[pos] = (uint16_t)pos;
     }
     int P = 1;
-    while (P < R) P <<= 1;
-    for (int c = R + tid; c < P; c += TH) { key[c] = 0ull; slot[c] = 0; }
+    while (P < ns) P <<= 1;
+    for (int c = ns + tid; c < P; c += TH) { key[c] = 0ull; slot[c] = 0; }
     __syncthreads();
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -173,15 +209,16 @@ compose_kernel(ComposeArgs a)
     }
     const int64_t ob = q * a.stride_t;
     for (int c = tid; c < a.stride_t; c += TH) {
-        if (c < R) {
-            const int sl = slot[c];
-            a.out_idx[ob + c] = cand[sl];
+        if (c < ns) {
+            const int pos = slot[c];
             const uint32_t kk = (uint32_t)(key[c] >> 32);
             const uint32_t u = (kk & 0x80000000u) ? (kk & 0x7fffffffu) : ~kk;
+            a.out_idx[ob + c] = cand_e[surv[pos]];
             a.out_score[ob + c] = __uint_as_float(u);
             for (int i = 0; i < FARM_MAX_CONSTRAINTS; ++i) {
-                a.out_t[(ob + c) * 4 + i] = t_s[sl][i];
-                a.out_anchor[(ob + c) * 4 + i] = anc_s[sl][i];
+                const unsigned long long b = i < m ? best[pos][i] : 0ull;
+                a.out_t[(ob + c) * 4 + i] = i < m ? (b ? __uint_as_float((uint32_t)(b >> 32)) : 0.f) : -1.f;
+                a.out_anchor[(ob + c) * 4 + i] = (i < m && b) ? (int32_t)(0xffffffffu - (uint32_t)(b & 0xffffffffu)) : -1;
             }
         } else {
             a.out_idx[ob + c] = -1;

@@ -5,19 +5,24 @@
 //
 // with x_hi = TF32(x) and x_lo = TF32(x - x_hi) prepared by the normalisation
 // kernel.  The dropped x_lo*y_lo term and the rounding of x_lo are each about
-// 2^-21 of |x*y|, so the result is FP32-accurate; all three products
-// accumulate into one FP32 accumulator in tensor memory (TMEM).
+// 2^-21 of |x*y|.  The tensor cores' FP32 accumulation truncates: every MMA
+// step adds an error of up to one unit in the last place of the running sum,
+// so the large products q_hi.d_hi accumulate in one tensor-memory (TMEM)
+// accumulator and the two small correction products in a second one, whose
+// truncation errors are about 2^-11 smaller; the epilogue adds the two in
+// IEEE FP32.  Measured against FP64 this keeps cosines within a few 1e-6.
 //
 // Kernel organisation (one 128 x 256 tile of S per CTA, 192 threads):
 //   warp 0      TMA producer: for each 16-wide K slice loads q_hi, q_lo
 //               (128 rows) and d_hi, d_lo (256 rows) into one pipeline stage
 //               (64-byte swizzle), signalling a "full" mbarrier with the byte count;
-//   warp 1      allocates 256 TMEM columns; one thread issues, per K slice,
-//               2 K-steps x 3 products of tcgen05.mma.cta_group::1.kind::tf32
-//               (M=128, N=256, K=8) and tcgen05.commit to the stage's "empty"
-//               mbarrier, finally to the "accumulator ready" mbarrier;
-//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns at a time and store
-//               the rows of S (bounds-checked).
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators);
+//               one thread issues, per K slice, 2 K-steps x 3 products of
+//               tcgen05.mma.cta_group::1.kind::tf32 (M=128, N=256, K=8) and
+//               tcgen05.commit to the stage's "empty" mbarrier, finally to the
+//               "accumulator ready" mbarrier;
+//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns of both
+//               accumulators at a time, add, store the rows of S (bounds-checked).
 // Four pipeline stages of 48 KB each.  Every mbarrier wait is bounded: on
 // expiry the kernel raises the error flag, stops issuing work, waits (bounded)
 // for the copies it issued, frees its TMEM and returns.
@@ -36,7 +41,8 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 4;         // 8 KB
 constexpr int B_BYTES = BN * BK * 4;         // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 48 KB
-constexpr int TMEM_COLS = 256;
+constexpr int TMEM_COLS = 512;            // main + correction accumulators
+constexpr int ACC_CORR = 256;             // column of the correction accumulator
 constexpr int THREADS = 192;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;    // try_wait polls before giving up (about a second)
@@ -230,9 +236,10 @@ sim_tc_tf32x3_kernel(const __grid_constant__ CUtensorMap map_qhi, const __grid_c
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
                     const uint32_t off = kk * 32;     // 8 TF32 values = 32 bytes along K
-                    mma_tf32(tmem, smem_desc_sw64(a_hi + off), smem_desc_sw64(b_hi + off), (kb | kk) != 0);
-                    mma_tf32(tmem, smem_desc_sw64(a_hi + off), smem_desc_sw64(b_lo + off), 1u);
-                    mma_tf32(tmem, smem_desc_sw64(a_lo + off), smem_desc_sw64(b_hi + off), 1u);
+                    const uint32_t acc = (kb | kk) != 0;
+                    mma_tf32(tmem, smem_desc_sw64(a_hi + off), smem_desc_sw64(b_hi + off), acc);
+                    mma_tf32(tmem + ACC_CORR, smem_desc_sw64(a_hi + off), smem_desc_sw64(b_lo + off), acc);
+                    mma_tf32(tmem + ACC_CORR, smem_desc_sw64(a_lo + off), smem_desc_sw64(b_hi + off), 1u);
                 }
                 mma_commit(&empty[s]);
             }
@@ -252,8 +259,12 @@ sim_tc_tf32x3_kernel(const __grid_constant__ CUtensorMap map_qhi, const __grid_c
             const bool vec = (ld_s % 4) == 0;
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
+                float v[32], w[32];
+                const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32);
+                tmem_ld32(lane_addr, v);
+                tmem_ld32(lane_addr + ACC_CORR, w);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] += w[i];
                 const int64_t col0 = (int64_t)n0 + c * 32;
                 if (r < rows) {
                     if (vec && col0 + 32 <= n) {
