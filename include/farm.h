@@ -202,6 +202,42 @@ farm_status farm_candidates(farm_ctx *ctx, uint64_t batch_handle, int32_t *tgt_i
                             int32_t *lm_idx, int32_t *r_tgt_out, int32_t *k_lm_out);
 
 /*
+ * Ranked object lists for embedding rows, without allocating device memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate GPU memory while serving queries: a process on a robot
+ * whose GPU memory budget is fixed at start-up (mapping and model workers own
+ * the rest of it), or a real-time loop that must not call cudaMalloc/cudaFree
+ * because they may synchronise the device and take unbounded time.
+ * farm_query_batch grows its workspace on demand; this call does not.
+ *
+ * For each of n_rows embeddings (device pointer emb, [n_rows, dim] FP32, dim
+ * of the scene) it writes the r objects of scene `scene_id` with the largest
+ * cosine, in rank order (larger cosine first, lower index on ties), to
+ * out_idx ([n_rows, r] int32, device) and their cosines to out_cos
+ * ([n_rows, r] FP32, device, may be NULL) -- the candidate ranking of App. D.2
+ * step 3 -- using the similarity arithmetic of `precision` (FARM_PREC_FP32 or
+ * FARM_PREC_FP32_SIMT).  1 <= r <= min(512, n).
+ *
+ * Memory: every intermediate array (normalised rows and the
+ * n_rows x round_up(n, 32) similarity block) lives in one statically
+ * allocated device array of FARM_NOALLOC_SCRATCH_BYTES that each GPU loading
+ * the library holds until the process exits.  The call allocates and frees
+ * nothing.  Sizes that do not fit return FARM_EINVAL (split the rows into
+ * smaller calls).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents (nothing in it needs to start at zero): calls whose
+ * work overlaps on the GPU -- on different streams or contexts of the same
+ * device -- race on it and must be serialised by the caller.
+ * Work is enqueued on the context's stream; nothing is synchronised.  A zero
+ * or non-finite row is reported by the next farm_sync as FARM_EINVAL.
+ */
+#define FARM_NOALLOC_SCRATCH_BYTES (32u << 20)
+farm_status farm_rank_rows_noalloc(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb,
+                                   int32_t r, int32_t precision, int32_t *out_idx, float *out_cos);
+
+/*
  * Stage timing.  With profiling on, every farm_query_batch records CUDA events
  * around its stages on the context stream.  farm_stage_times synchronises and
  * writes the accumulated milliseconds of FARM_N_STAGES stages (prepare,

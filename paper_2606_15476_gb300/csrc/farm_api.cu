@@ -35,6 +35,10 @@ struct farm_ctx {
     std::vector<cudaEvent_t> pool;
 };
 
+namespace farm {
+Ctx *ctx_of(farm_ctx *ctx) { return &ctx->c; }
+}  // namespace farm
+
 namespace {
 
 constexpr int kMaxScenes = 4096;

@@ -108,6 +108,9 @@ struct Ctx {
     int num_sms = 0;
 };
 
+// The internal state behind a public farm_ctx handle.
+Ctx *ctx_of(farm_ctx *ctx);
+
 // ---- kernel launchers (each returns cudaGetLastError() after launching) ----
 
 // Unit-normalise `rows` rows of length dim into dst rows of length dim_pad

@@ -52,6 +52,7 @@ def _load():
         "farm_sync": (C.c_int, [P]),
         "farm_similarity": (C.c_int, [P, I32, I64, P, I32, P, U32]),
         "farm_candidates": (C.c_int, [P, U64, P, P, P, P]),
+        "farm_rank_rows_noalloc": (C.c_int, [P, I32, I64, P, I32, I32, P, P]),
         "farm_set_profiling": (C.c_int, [P, I32]),
         "farm_stage_times": (C.c_int, [P, P, P, I32]),
         "farm_last_error": (C.c_char_p, [P]),
@@ -70,7 +71,8 @@ _lib = _load()
 def exported_symbols():
     return ["farm_default_params", "farm_create", "farm_destroy", "farm_memory_upload",
             "farm_query_batch", "farm_topk", "farm_sync", "farm_similarity", "farm_candidates",
-            "farm_set_profiling", "farm_stage_times", "farm_last_error", "farm_version"]
+            "farm_rank_rows_noalloc", "farm_set_profiling", "farm_stage_times", "farm_last_error",
+            "farm_version"]
 
 
 def _is_cuda_tensor(x) -> bool:
@@ -222,6 +224,20 @@ def farm_candidates(ctx, handle: int, n_q: int, n_c: int):
     _ck(ctx, _lib.farm_candidates(ctx, C.c_uint64(handle), t.ctypes.data_as(C.c_void_p),
                                   l.ctypes.data_as(C.c_void_p), None, None))
     return t, l
+
+
+def farm_rank_rows_noalloc(ctx, scene_id: int, emb, r: int, precision: int, out_idx, out_cos=None):
+    """Rank lists of device embedding rows with no allocation (CUDA tensors only)."""
+    for name, t in (("emb", emb), ("out_idx", out_idx), ("out_cos", out_cos)):
+        if t is not None and not _is_cuda_tensor(t):
+            raise FarmError(1, f"{name} must be a CUDA tensor")
+    e = _Arr(emb, np.float32, "emb")
+    if not (out_idx.is_contiguous() and (out_cos is None or out_cos.is_contiguous())):
+        raise FarmError(1, "outputs must be contiguous")
+    _ck(ctx, _lib.farm_rank_rows_noalloc(ctx, int(scene_id), int(emb.shape[0]), e.ptr, int(r), int(precision),
+                                         C.c_void_p(out_idx.data_ptr()),
+                                         None if out_cos is None else C.c_void_p(out_cos.data_ptr())))
+    return out_idx, out_cos
 
 
 def farm_set_profiling(ctx, on: bool) -> None:
