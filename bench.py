@@ -104,16 +104,17 @@ class ClockSampler:
 
 
 def cpu_baseline(scene, qb, k, n_sample, seed=0):
+    """The oracle on a seeded query sample: its rate, and its TopK for recall."""
     import oracle
     qs = np.sort(np.random.default_rng(seed).choice(qb.n_q, size=min(n_sample, qb.n_q), replace=False))
     sub = qb.subset(qs)
     t0 = time.perf_counter()
-    oracle.batch(scene, sub, k)
+    ref = oracle.batch(scene, sub, k)
     dt = time.perf_counter() - t0
     return {"value": sub.n_q / dt, "unit": "queries/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"{sub.n_q} of the {qb.n_q} queries (seeded), FP64 oracle, OpenMP over "
-                      f"queries, {dt:.1f} s wall"}
+                      f"queries, {dt:.1f} s wall"}, qs, ref["idx"]
 
 
 def run_reference(args):
@@ -305,7 +306,11 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        line["cpu_baseline"] = cpu_baseline(sc, qb, K_TOP, args.cpu_sample)
+        base, qs, ref_idx = cpu_baseline(sc, qb, K_TOP, args.cpu_sample)
+        line["cpu_baseline"] = base
+        got = h_out["idx"][qs]
+        hits = sum(len(set(got[i].tolist()) & set(ref_idx[i].tolist())) for i in range(len(qs)))
+        line["recall_at_10_vs_oracle"] = {"value": hits / (K_TOP * len(qs)), "queries": int(len(qs))}
     F.farm_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -82,7 +82,9 @@ typedef enum {
  * by the paper; farm_default_params sets 0.25, 0.10, 0.05 and 16.
  * k_max is the largest k a later farm_topk may ask for: farm_query_batch keeps
  * only candidates that can still reach the top k_max (see farm_query_batch).
- * rescore is the number of candidates per row the BF16 path re-scores in FP32.
+ * rescore (1 .. 512) is the number of candidates per target row the BF16 path
+ * re-scores in FP32 (at least the rank bound R of farm_query_batch); landmark
+ * rows re-score max(rescore / 4, k_anchor).
  */
 typedef struct {
     float mu;
@@ -153,7 +155,7 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
  * Only target candidates whose rank r can still place them in the top k_max
  * are scored: a candidate scores at most 1/(mu + r) while k_max objects score
  * at least (1 - w) * class_mis / (mu + k_max), so candidates of rank above
- * R = ceil((mu + k_max) / ((1 - w) * class_mis) - mu) (95 at the defaults)
+ * R = floor((mu + k_max) / ((1 - w) * class_mis) - mu) + 1 (96 at the defaults)
  * cannot enter the result.  The result is the same as scoring every object.
  * A new farm_query_batch call invalidates the previous handle.
  */
@@ -184,7 +186,8 @@ farm_status farm_sync(farm_ctx *ctx);
 
 /*
  * Cosine similarity of n_rows embeddings against every object of a scene,
- * computed by the kernels of `precision` (App. D.2 step 3):
+ * computed by the kernels of `precision` (App. D.2 step 3; FARM_PREC_BF16
+ * returns the BF16 stage's approximate cosines):
  *   emb [n_rows, dim] FP32, out [n_rows, n] FP32 (host or device per flags).
  */
 farm_status farm_similarity(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb,

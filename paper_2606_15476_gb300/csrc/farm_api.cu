@@ -88,7 +88,7 @@ bool params_ok(const farm_params &p, std::string &why)
         why = "(mu + k_max) / ((1 - w) * class_mis) - mu exceeds 512 target candidates";
         return false;
     }
-    if (p.rescore < 1 || p.rescore > 4096) { why = "rescore must lie in [1, 4096]"; return false; }
+    if (p.rescore < 1 || p.rescore > farm::kMaxTargetCands) { why = "rescore must lie in [1, 512]"; return false; }
     return true;
 }
 
@@ -212,9 +212,25 @@ farm_status run_similarity(farm_ctx *ctx, int32_t prec, const RowOps &ops, int64
         LAUNCH(farm::launch_sim_tc_tf32x3(ops.qhi + off, ops.qlo + off, s.desc_hi, s.desc_lo, S,
                                           rows, s.n, s.dim_pad, ld_s, c.num_sms, c.d_err, c.stream));
         return FARM_OK;
+    case FARM_PREC_BF16:
+        if (!farm::sim_tc_available())
+            return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
+        LAUNCH(farm::launch_sim_tc_bf16(ops.qbf + off, s.desc_bf16, S, rows, s.n, s.dim_pad, ld_s, c.num_sms,
+                                        c.d_err, c.stream));
+        return FARM_OK;
     default:
         return fail(ctx, FARM_EINVAL, "precision not supported by this build");
     }
+}
+
+// Candidates kept per row by the BF16 stage before the FP32 rescore.
+int32_t bf16_keep_target(const farm_params &p, int32_t R, int64_t n)
+{
+    return (int32_t)std::min<int64_t>(std::max<int32_t>(p.rescore, R), n);
+}
+int32_t bf16_keep_landmark(const farm_params &p, int32_t klm, int64_t n)
+{
+    return (int32_t)std::min<int64_t>(std::max<int32_t>(p.rescore / 4, klm), n);
 }
 
 }  // namespace
@@ -551,6 +567,13 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     CK(ws_get(ctx, farm::B_OUT_ANCHOR, (size_t)n_q * stride_t * 4, &o_anc));
     RowOps ops;
     CK(alloc_rows(ctx, precision, rows_total, dim_pad, ops));
+    int32_t *bsel_t = nullptr, *bsel_l = nullptr;
+    const int32_t cstride_t = bf16_keep_target(p, stride_t, max_n);
+    const int32_t cstride_l = bf16_keep_landmark(p, stride_l, max_n);
+    if (precision == FARM_PREC_BF16) {
+        CK(ws_get(ctx, farm::B_BSEL_T, (size_t)n_q * cstride_t, &bsel_t));
+        CK(ws_get(ctx, farm::B_BSEL_L, (size_t)std::max<int64_t>(n_c, 1) * cstride_l, &bsel_l));
+    }
     int64_t max_ld = 0, max_rows = 0;
     for (const auto &g : groups) {
         const int64_t ld = round_up(c.scenes[g.sid].n, 32);
@@ -600,9 +623,25 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             mark_end(ctx, m1);
             const int64_t ntr = std::max<int64_t>(0, std::min<int64_t>(g.nq - r0, r1 - r0));
             const int m2 = mark_begin(ctx, 2);
-            LAUNCH(farm::launch_select_rows(d_sim, ld, s.n, r1 - r0, ntr, Rs, klm, tsel_idx, tsel_cos,
-                                            g.q0 + r0, stride_t, lsel_idx, g.cp0 + r0 + ntr - g.nq, stride_l,
-                                            c.stream));
+            if (precision != FARM_PREC_BF16) {
+                LAUNCH(farm::launch_select_rows(d_sim, ld, s.n, r1 - r0, ntr, Rs, klm, tsel_idx, tsel_cos,
+                                                g.q0 + r0, stride_t, lsel_idx, g.cp0 + r0 + ntr - g.nq, stride_l,
+                                                c.stream));
+            } else {
+                // BF16 stage keeps C candidates per row; FP32 rescore keeps R (or K_a) of them
+                const int32_t Ct = bf16_keep_target(p, Rs, s.n), Cl = bf16_keep_landmark(p, klm, s.n);
+                const int64_t lrow0 = g.cp0 + r0 + ntr - g.nq;
+                LAUNCH(farm::launch_select_rows(d_sim, ld, s.n, r1 - r0, ntr, Ct, Cl, bsel_t, nullptr, g.q0 + r0,
+                                                cstride_t, bsel_l, lrow0, cstride_l, c.stream));
+                if (ntr > 0)
+                    LAUNCH(farm::launch_rescore(ops.q32, g.row0 + r0, dim_pad, s.desc32, bsel_t, Ct, cstride_t,
+                                                g.q0 + r0, ntr, Rs, tsel_idx, tsel_cos, stride_t, g.q0 + r0,
+                                                c.stream));
+                if (r1 - r0 - ntr > 0)
+                    LAUNCH(farm::launch_rescore(ops.q32, g.row0 + r0 + ntr, dim_pad, s.desc32, bsel_l, Cl, cstride_l,
+                                                lrow0, r1 - r0 - ntr, klm, lsel_idx, nullptr, stride_l, lrow0,
+                                                c.stream));
+            }
             mark_end(ctx, m2);
         }
     }
@@ -692,8 +731,8 @@ farm_status farm_similarity(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, con
     if (n_rows < 0) return fail(ctx, FARM_EINVAL, "n_rows must be >= 0");
     if (n_rows == 0) return FARM_OK;
     if (!emb || !out) return fail(ctx, FARM_EINVAL, "emb and out must be non-null");
-    if (precision != FARM_PREC_FP32 && precision != FARM_PREC_FP32_SIMT)
-        return fail(ctx, FARM_EINVAL, "similarity is available for FP32 and FP32_SIMT");
+    if (precision != FARM_PREC_FP32 && precision != FARM_PREC_FP32_SIMT && precision != FARM_PREC_BF16)
+        return fail(ctx, FARM_EINVAL, "unknown precision");
     CK(cudaSetDevice(c.device));
     const Scene &s = c.scenes[scene_id];
     const bool dev = (flags & FARM_PTR_DEVICE) != 0;

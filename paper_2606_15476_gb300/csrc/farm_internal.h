@@ -74,6 +74,8 @@ enum Buf {
     B_OUT_T,        // float [n_q, r_tgt, 4]
     B_OUT_ANCHOR,   // int32 [n_q, r_tgt, 4]
     B_TOPK,         // int32/float [n_q, k, 10] TopK staging for host outputs
+    B_BSEL_T,       // int32 [n_q, C_t] BF16-stage target candidates (before FP32 rescore)
+    B_BSEL_L,       // int32 [n_c, C_l] BF16-stage landmark candidates
     B_COUNT
 };
 
@@ -135,6 +137,9 @@ cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const flo
                                  const float *d_lo, float *S, int64_t rows, int64_t n,
                                  int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err,
                                  cudaStream_t s);
+// BF16 operands, FP32 accumulation (first stage of the reduced-precision path).
+cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
+                               int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s);
 bool sim_tc_available();
 
 // Per row r of S (rows x n, leading dim ld_s): the R_r largest entries in
@@ -157,6 +162,14 @@ struct SceneDev {
     int32_t n_views;
     int32_t pad;
 };
+
+// Re-score C candidates per row with exact FP32 dot products of unit rows and
+// keep the R best in rank order: row r (of `rows`) uses Q32 row q_row0 + r,
+// candidates cand[(cand_row0 + r) * cand_stride + c], writes
+// out_idx/out_cos[(out_row0 + r) * out_stride + i] (-1 / 0 past R).
+cudaError_t launch_rescore(const float *Q32, int64_t q_row0, int32_t dim_pad, const float *D32, const int32_t *cand,
+                           int32_t C, int32_t cand_stride, int64_t cand_row0, int64_t rows, int32_t R,
+                           int32_t *out_idx, float *out_cos, int32_t out_stride, int64_t out_row0, cudaStream_t s);
 
 struct ComposeArgs {
     int64_t n_q;

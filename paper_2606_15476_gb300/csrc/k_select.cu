@@ -209,13 +209,32 @@ __device__ __forceinline__ void find_bucket(const uint32_t *hist, uint32_t remai
     __syncthreads();
 }
 
-__device__ __forceinline__ void hist_add(uint32_t *hist, uint32_t bin, bool valid)
+// Bitonic sort of P (a power of two <= TH) 64-bit keys in shared memory,
+// descending, one element per thread.  Stages whose partners lie in the same
+// warp synchronise the warp only.
+__device__ __forceinline__ void bitonic_desc(uint64_t *cand, int P)
 {
-    const unsigned lane = threadIdx.x & 31u;
-    const uint32_t b = valid ? bin : 0xffffffffu;
-    const unsigned peers = __match_any_sync(0xffffffffu, b);
-    if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    const int i = threadIdx.x;
+    int prev_j = TH;
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32 || prev_j >= 32) __syncthreads();
+            else __syncwarp();
+            if (i < P) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = cand[i], b = cand[ixj];
+                    const bool desc = (i & k) == 0;
+                    if (desc ? (a < b) : (a > b)) { cand[i] = b; cand[ixj] = a; }
+                }
+            }
+            prev_j = j;
+        }
+    }
+    __syncthreads();
 }
+
+constexpr int kVecHalf = kRowSmemMax / 8 / TH;   // float4 loads per thread per batch (two batches)
 
 __global__ void __launch_bounds__(TH, 2)
 select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, int64_t n_tgt_rows,
@@ -235,22 +254,33 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
     const float *row = S + r * ld_s;
     const bool is_tgt = r < n_tgt_rows;
     const int R = is_tgt ? r_tgt : k_lm;
+    const int n4 = n & ~3;
 
+    // issue the row's loads in two batches of kVecHalf float4 per thread, then
+    // histogram the top 11 bits of each key
     for (int i = tid; i < 2048; i += TH) hist[i] = 0;
     __syncthreads();
-    // stage the row as order keys; histogram of the top 11 bits
-    const int n4 = n & ~3;
-    for (int base = 0; base < n4; base += 4 * TH) {
-        const int i = base + 4 * tid;
-        const bool ok = i < n4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ok) v = *reinterpret_cast<const float4 *>(row + i);
-        const uint32_t k0 = order_key(v.x), k1 = order_key(v.y), k2 = order_key(v.z), k3 = order_key(v.w);
-        if (ok) *reinterpret_cast<uint4 *>(keys + i) = make_uint4(k0, k1, k2, k3);
-        hist_add(hist, k0 >> 21, ok);
-        hist_add(hist, k1 >> 21, ok);
-        hist_add(hist, k2 >> 21, ok);
-        hist_add(hist, k3 >> 21, ok);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        float4 buf[kVecHalf];
+#pragma unroll
+        for (int u = 0; u < kVecHalf; ++u) {
+            const int i = ((half * kVecHalf + u) * TH + tid) * 4;
+            buf[u] = i < n4 ? __ldg(reinterpret_cast<const float4 *>(row + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kVecHalf; ++u) {
+            const int i = ((half * kVecHalf + u) * TH + tid) * 4;
+            if (i < n4) {
+                const uint4 k = make_uint4(order_key(buf[u].x), order_key(buf[u].y), order_key(buf[u].z),
+                                           order_key(buf[u].w));
+                *reinterpret_cast<uint4 *>(keys + i) = k;
+                atomicAdd(&hist[k.x >> 21], 1u);
+                atomicAdd(&hist[k.y >> 21], 1u);
+                atomicAdd(&hist[k.z >> 21], 1u);
+                atomicAdd(&hist[k.w >> 21], 1u);
+            }
+        }
     }
     if (tid < n - n4) {
         const uint32_t k = order_key(row[n4 + tid]);
@@ -261,13 +291,16 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
     find_bucket<2048>(hist, (uint32_t)R, wsum, &s_bin, &s_rem, &s_cnt);
     const uint32_t b1 = s_bin;
     uint32_t remaining = s_rem;
-    // second digit: bits 10..20 among keys with top digit b1
+    const int nv = (n + 3) >> 2;   // uint4 groups (the tail group is masked by index)
+    // second digit: bits 10..20 among keys whose top digit is b1
     for (int i = tid; i < 2048; i += TH) hist[i] = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += TH) {
-        const int i = base + tid;
-        const uint32_t k = i < n ? keys[i] : 0u;
-        hist_add(hist, (k >> 10) & 2047u, i < n && (k >> 21) == b1);
+    for (int g = tid; g < nv; g += TH) {
+        const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
+        const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (4 * g + c < n && (kk[c] >> 21) == b1) atomicAdd(&hist[(kk[c] >> 10) & 2047u], 1u);
     }
     __syncthreads();
     find_bucket<2048>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
@@ -276,10 +309,12 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
     // third digit: bits 0..9
     for (int i = tid; i < 1024; i += TH) hist[i] = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += TH) {
-        const int i = base + tid;
-        const uint32_t k = i < n ? keys[i] : 0u;
-        hist_add(hist, k & 1023u, i < n && (k >> 10) == p2);
+    for (int g = tid; g < nv; g += TH) {
+        const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
+        const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (4 * g + c < n && (kk[c] >> 10) == p2) atomicAdd(&hist[kk[c] & 1023u], 1u);
     }
     __syncthreads();
     find_bucket<1024>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
@@ -290,11 +325,16 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
 
     if (tid == 0) s_app = 0;
     __syncthreads();
-    for (int i = tid; i < n; i += TH) {
-        const uint32_t k = keys[i];
-        if (k > T || (take_all_eq && k == T)) {
-            const int pos = atomicAdd(&s_app, 1);
-            cand[pos] = ((uint64_t)k << 32) | (uint64_t)(0xffffffffu - (uint32_t)i);
+    for (int g = tid; g < nv; g += TH) {
+        const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
+        const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = 4 * g + c;
+            if (i < n && (kk[c] > T || (take_all_eq && kk[c] == T))) {
+                const int pos = atomicAdd(&s_app, 1);
+                cand[pos] = ((uint64_t)kk[c] << 32) | (uint64_t)(0xffffffffu - (uint32_t)i);
+            }
         }
     }
     __syncthreads();
@@ -323,20 +363,7 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
     int P = 1;
     while (P < R) P <<= 1;
     for (int i = R + tid; i < P; i += TH) cand[i] = 0ull;
-    __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < P; i += TH) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t a = cand[i], b = cand[ixj];
-                    const bool desc = (i & k) == 0;
-                    if (desc ? (a < b) : (a > b)) { cand[i] = b; cand[ixj] = a; }
-                }
-            }
-            __syncthreads();
-        }
-    }
+    bitonic_desc(cand, P);
     if (is_tgt) {
         int32_t *oi = tsel_idx + (tsel_row0 + r) * (int64_t)stride_t;
         float *oc = tsel_cos ? tsel_cos + (tsel_row0 + r) * (int64_t)stride_t : nullptr;

@@ -1,8 +1,14 @@
 // k_sim_tc.cu -- descriptor similarity on the 5th-generation tensor cores
 // (App. D.2 step 3: the cosine of every query row against every object).
 //
-//   S[r, j] = <q_r, d_j> ~= q_hi.d_hi + q_hi.d_lo + q_lo.d_hi      (three TF32 products)
+// Two arithmetic modes share one kernel template:
+//  * FP32-accurate, three TF32 products:
+//      S[r, j] = <q_r, d_j> ~= q_hi.d_hi + q_hi.d_lo + q_lo.d_hi
+//  * BF16: S[r, j] ~= <bf16(q_r), bf16(d_j)> with FP32 accumulation, the
+//    first stage of the reduced-precision path (its borderline candidates are
+//    re-scored in FP32 afterwards).
 //
+// FP32-accurate mode:
 // with x_hi = TF32(x) and x_lo = TF32(x - x_hi) prepared by the normalisation
 // kernel.  The dropped x_lo*y_lo term and the rounding of x_lo are each about
 // 2^-21 of |x*y|.  The tensor cores' FP32 accumulation truncates: every MMA
@@ -13,12 +19,14 @@
 // IEEE FP32.  Measured against FP64 this keeps cosines within a few 1e-6.
 //
 // Kernel organisation (one 128 x 256 tile of S per CTA, 192 threads):
-//   warp 0      TMA producer: for each 16-wide K slice loads q_hi, q_lo
-//               (128 rows) and d_hi, d_lo (256 rows) into one pipeline stage
-//               (64-byte swizzle), signalling a "full" mbarrier with the byte count;
-//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators);
-//               one thread issues, per K slice, 2 K-steps x 3 products of
-//               tcgen05.mma.cta_group::1.kind::tf32 (M=128, N=256, K=8) and
+//   warp 0      TMA producer: for each K slice (16 FP32 values, 64-byte swizzle,
+//               four tiles q_hi, q_lo, d_hi, d_lo; or 64 BF16 values, 128-byte
+//               swizzle, two tiles q, d) fills one pipeline stage, signalling a
+//               "full" mbarrier with the byte count;
+//   warp 1      allocates TMEM (two 128 x 256 FP32 accumulators in TF32 mode,
+//               one in BF16 mode); one thread issues, per K slice, 2 K-steps x 3
+//               products of tcgen05.mma.cta_group::1.kind::tf32 (M=128, N=256,
+//               K=8), or 4 K-steps of kind::f16 with BF16 operands (K=16), and
 //               tcgen05.commit to the stage's "empty" mbarrier, finally to the
 //               "accumulator ready" mbarrier;
 //   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns of both
@@ -36,17 +44,41 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BN = 256;
-constexpr int BK = 16;                       // FP32 elements per K slice (64 bytes)
 constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 4;         // 8 KB
-constexpr int B_BYTES = BN * BK * 4;         // 16 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 48 KB
-constexpr int TMEM_COLS = 512;            // main + correction accumulators
-constexpr int ACC_CORR = 256;             // column of the correction accumulator
+constexpr int STAGE_BYTES = 48 * 1024;       // BM + BN rows of 128 bytes of operand data
 constexpr int THREADS = 192;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;    // try_wait polls before giving up (about a second)
 constexpr int GROUP_M = 16;                  // tile raster: 16 row tiles share each column tile
+constexpr int ACC_CORR = 256;                // TMEM column of the correction accumulator (TF32 mode)
+
+// Per-mode layout of a pipeline stage.
+template <bool BF16>
+struct Mode;
+template <>
+struct Mode<false> {                         // three-term TF32
+    static constexpr int BK = 16;            // FP32 elements per K slice (64-byte rows)
+    static constexpr int ROW_BYTES = 64;
+    static constexpr int A_BYTES = BM * ROW_BYTES;   // 8 KB, twice (hi, lo)
+    static constexpr int B_BYTES = BN * ROW_BYTES;   // 16 KB, twice
+    static constexpr int KSTEPS = 2;         // 8 TF32 values (32 bytes) per MMA
+    static constexpr int TMEM_COLS = 512;
+    static constexpr uint64_t LAYOUT = 4;    // 64-byte swizzle
+    static constexpr uint32_t SBO = 512;     // 8 rows x 64 bytes
+};
+template <>
+struct Mode<true> {                          // BF16
+    static constexpr int BK = 64;            // BF16 elements per K slice (128-byte rows)
+    static constexpr int ROW_BYTES = 128;
+    static constexpr int A_BYTES = BM * ROW_BYTES;   // 16 KB
+    static constexpr int B_BYTES = BN * ROW_BYTES;   // 32 KB
+    static constexpr int KSTEPS = 4;         // 16 BF16 values (32 bytes) per MMA
+    static constexpr int TMEM_COLS = 256;
+    static constexpr uint64_t LAYOUT = 2;    // 128-byte swizzle
+    static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
+};
+static_assert(2 * Mode<false>::A_BYTES + 2 * Mode<false>::B_BYTES == STAGE_BYTES, "stage size");
+static_assert(Mode<true>::A_BYTES + Mode<true>::B_BYTES == STAGE_BYTES, "stage size");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -90,25 +122,27 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
-// 64 bytes, 8-row core groups 512 bytes apart (stride byte offset), version 1.
-__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
+// Shared-memory matrix descriptor of a K-major operand tile with rows of
+// ROW_BYTES swizzled in 8-row core groups SBO bytes apart; version 1.  The
+// leading byte offset is unused for swizzled K-major layouts.
+template <bool BF16>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 {
     uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
-    d |= (uint64_t)0 << 16;                             // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(512u >> 4) << 32;                   // stride byte offset
-    d |= (uint64_t)1 << 46;                             // descriptor version
-    d |= (uint64_t)4 << 61;                             // layout: 64-byte swizzle
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);              // start address
+    d |= (uint64_t)(Mode<BF16>::SBO >> 4) << 32;            // stride byte offset
+    d |= (uint64_t)1 << 46;                                 // descriptor version
+    d |= Mode<BF16>::LAYOUT << 61;                          // swizzle mode
     return d;
 }
 
-// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M=128, N=256.
-__host__ __device__ constexpr uint32_t idesc_tf32()
+// Instruction descriptors: D = F32, A and B K-major, M = 128, N = 256;
+// operand format TF32 (kind::tf32) or BF16 (kind::f16).
+__host__ __device__ constexpr uint32_t idesc(uint32_t ab_format)
 {
     return (1u << 4)                      // D format F32
-           | (2u << 7)                    // A format TF32
-           | (2u << 10)                   // B format TF32
+           | (ab_format << 7)             // A format
+           | (ab_format << 10)            // B format
            | ((uint32_t)(BN >> 3) << 17)  // N / 8
            | ((uint32_t)(BM >> 4) << 24); // M / 16
 }
@@ -119,7 +153,16 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc_tf32()), "r"(accumulate));
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(2u)), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(1u)), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
@@ -146,12 +189,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Maps (TF32 mode): q_hi, q_lo, d_hi, d_lo.  (BF16 mode): q, d, and the last
+// two are unused.
+template <bool BF16>
 __global__ void __launch_bounds__(THREADS, 1)
-sim_tc_tf32x3_kernel(const __grid_constant__ CUtensorMap map_qhi, const __grid_constant__ CUtensorMap map_qlo,
-                     const __grid_constant__ CUtensorMap map_dhi, const __grid_constant__ CUtensorMap map_dlo,
-                     float *__restrict__ S, int64_t rows, int64_t n, int32_t k_slices, int64_t ld_s,
-                     int32_t m_tiles, int32_t n_tiles, int32_t *err)
+sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant__ CUtensorMap map_q1,
+              const __grid_constant__ CUtensorMap map_d0, const __grid_constant__ CUtensorMap map_d1,
+              float *__restrict__ S, int64_t rows, int64_t n, int32_t k_slices, int64_t ld_s,
+              int32_t m_tiles, int32_t n_tiles, int32_t *err)
 {
+    using M = Mode<BF16>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
@@ -184,7 +231,7 @@ sim_tc_tf32x3_kernel(const __grid_constant__ CUtensorMap map_qhi, const __grid_c
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS));
+                     "r"(M::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -204,11 +251,16 @@ sim_tc_tf32x3_kernel(const __grid_constant__ CUtensorMap map_qhi, const __grid_c
                 }
                 uint8_t *st = smem + s * STAGE_BYTES;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
-                const int kx = kb * BK;
-                tma_load_2d(st, &map_qhi, &full[s], kx, m0);
-                tma_load_2d(st + A_BYTES, &map_qlo, &full[s], kx, m0);
-                tma_load_2d(st + 2 * A_BYTES, &map_dhi, &full[s], kx, n0);
-                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &map_dlo, &full[s], kx, n0);
+                const int kx = kb * M::BK;
+                if (BF16) {
+                    tma_load_2d(st, &map_q0, &full[s], kx, m0);
+                    tma_load_2d(st + M::A_BYTES, &map_d0, &full[s], kx, n0);
+                } else {
+                    tma_load_2d(st, &map_q0, &full[s], kx, m0);
+                    tma_load_2d(st + M::A_BYTES, &map_q1, &full[s], kx, m0);
+                    tma_load_2d(st + 2 * M::A_BYTES, &map_d0, &full[s], kx, n0);
+                    tma_load_2d(st + 2 * M::A_BYTES + M::B_BYTES, &map_d1, &full[s], kx, n0);
+                }
                 issued = kb + 1;
             }
             if (*abort_flag) {
@@ -231,15 +283,24 @@ sim_tc_tf32x3_kernel(const __grid_constant__ CUtensorMap map_qhi, const __grid_c
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-                const uint32_t a_hi = st, a_lo = st + A_BYTES;
-                const uint32_t b_hi = st + 2 * A_BYTES, b_lo = st + 2 * A_BYTES + B_BYTES;
+                if (BF16) {
+                    const uint32_t a = st, b = st + M::A_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < BK / 8; ++kk) {
-                    const uint32_t off = kk * 32;     // 8 TF32 values = 32 bytes along K
-                    const uint32_t acc = (kb | kk) != 0;
-                    mma_tf32(tmem, smem_desc_sw64(a_hi + off), smem_desc_sw64(b_hi + off), acc);
-                    mma_tf32(tmem + ACC_CORR, smem_desc_sw64(a_hi + off), smem_desc_sw64(b_lo + off), acc);
-                    mma_tf32(tmem + ACC_CORR, smem_desc_sw64(a_lo + off), smem_desc_sw64(b_hi + off), 1u);
+                    for (int kk = 0; kk < M::KSTEPS; ++kk) {
+                        const uint32_t off = kk * 32;     // 16 BF16 values = 32 bytes along K
+                        mma_bf16(tmem, smem_desc<true>(a + off), smem_desc<true>(b + off), (kb | kk) != 0);
+                    }
+                } else {
+                    const uint32_t a_hi = st, a_lo = st + M::A_BYTES;
+                    const uint32_t b_hi = st + 2 * M::A_BYTES, b_lo = st + 2 * M::A_BYTES + M::B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < M::KSTEPS; ++kk) {
+                        const uint32_t off = kk * 32;     // 8 TF32 values = 32 bytes along K
+                        const uint32_t acc = (kb | kk) != 0;
+                        mma_tf32(tmem, smem_desc<false>(a_hi + off), smem_desc<false>(b_hi + off), acc);
+                        mma_tf32(tmem + ACC_CORR, smem_desc<false>(a_hi + off), smem_desc<false>(b_lo + off), acc);
+                        mma_tf32(tmem + ACC_CORR, smem_desc<false>(a_lo + off), smem_desc<false>(b_hi + off), 1u);
+                    }
                 }
                 mma_commit(&empty[s]);
             }
@@ -259,12 +320,15 @@ sim_tc_tf32x3_kernel(const __grid_constant__ CUtensorMap map_qhi, const __grid_c
             const bool vec = (ld_s % 4) == 0;
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
-                float v[32], w[32];
+                float v[32];
                 const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32);
                 tmem_ld32(lane_addr, v);
-                tmem_ld32(lane_addr + ACC_CORR, w);
+                if (!BF16) {
+                    float w[32];
+                    tmem_ld32(lane_addr + ACC_CORR, w);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] += w[i];
+                    for (int i = 0; i < 32; ++i) v[i] += w[i];
+                }
                 const int64_t col0 = (int64_t)n0 + c * 32;
                 if (r < rows) {
                     if (vec && col0 + 32 <= n) {
@@ -284,7 +348,7 @@ sim_tc_tf32x3_kernel(const __grid_constant__ CUtensorMap map_qhi, const __grid_c
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(M::TMEM_COLS));
     }
 }
 
@@ -302,17 +366,53 @@ bool get_encoder()
     return true;
 }
 
-// 2D FP32 tensor [outer, inner] row-major, box [box_outer, BK], 64-byte swizzle.
-bool make_map(CUtensorMap *m, const float *base, int64_t inner, int64_t outer, int box_outer)
+// 2D tensor [outer, inner] row-major (FP32 or BF16), box [box_outer, BK],
+// swizzle matching the mode's row width.
+template <bool BF16>
+bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, int box_outer)
 {
+    using M = Mode<BF16>;
+    const int esize = BF16 ? 2 : 4;
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    cuuint64_t strides[1] = {(cuuint64_t)inner * 4};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_outer};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * esize};
+    cuuint32_t box[2] = {(cuuint32_t)M::BK, (cuuint32_t)box_outer};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+    CUresult r = g_encode(m, BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                          const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          BF16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+template <bool BF16>
+cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void *d1, float *S, int64_t rows,
+                      int64_t n, int32_t dim_pad, int64_t ld_s, int32_t *err, cudaStream_t s)
+{
+    using M = Mode<BF16>;
+    if (rows <= 0 || n <= 0) return cudaSuccess;
+    if (dim_pad % M::BK != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (!get_encoder()) return cudaErrorNotSupported;
+    // TMA: 16-byte aligned bases; row strides are multiples of 16 bytes (dim_pad % 64 == 0)
+    const uintptr_t al = (uintptr_t)q0 | (uintptr_t)d0 | (BF16 ? 0 : ((uintptr_t)q1 | (uintptr_t)d1));
+    if (al & 15u) return cudaErrorMisalignedAddress;
+    CUtensorMap mq0, mq1, md0, md1;
+    if (!make_map<BF16>(&mq0, q0, dim_pad, rows, BM) || !make_map<BF16>(&md0, d0, dim_pad, n, BN))
+        return cudaErrorInvalidValue;
+    if (BF16) {
+        mq1 = mq0;
+        md1 = md0;
+    } else if (!make_map<BF16>(&mq1, q1, dim_pad, rows, BM) || !make_map<BF16>(&md1, d1, dim_pad, n, BN)) {
+        return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaFuncSetAttribute(sim_tc_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const int m_tiles = (int)((rows + BM - 1) / BM);
+    const int n_tiles = (int)((n + BN - 1) / BN);
+    const int64_t tiles = (int64_t)m_tiles * n_tiles;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    sim_tc_kernel<BF16><<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(mq0, mq1, md0, md1, S, rows, n,
+                                                                       dim_pad / M::BK, ld_s, m_tiles, n_tiles, err);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -324,25 +424,14 @@ cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const flo
                                  cudaStream_t s)
 {
     (void)num_sms;
-    if (rows <= 0 || n <= 0) return cudaSuccess;
-    if (dim_pad % BK != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if (!get_encoder()) return cudaErrorNotSupported;
-    // TMA: 16-byte aligned bases and row strides (dim_pad is a multiple of 64 floats)
-    const uintptr_t al = (uintptr_t)q_hi | (uintptr_t)q_lo | (uintptr_t)d_hi | (uintptr_t)d_lo;
-    if (al & 15u) return cudaErrorMisalignedAddress;
-    CUtensorMap mqh, mql, mdh, mdl;
-    if (!make_map(&mqh, q_hi, dim_pad, rows, BM) || !make_map(&mql, q_lo, dim_pad, rows, BM) ||
-        !make_map(&mdh, d_hi, dim_pad, n, BN) || !make_map(&mdl, d_lo, dim_pad, n, BN))
-        return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(sim_tc_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    const int m_tiles = (int)((rows + BM - 1) / BM);
-    const int n_tiles = (int)((n + BN - 1) / BN);
-    const int64_t tiles = (int64_t)m_tiles * n_tiles;
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    sim_tc_tf32x3_kernel<<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(mqh, mql, mdh, mdl, S, rows, n, dim_pad / BK,
-                                                                        ld_s, m_tiles, n_tiles, err);
-    return cudaGetLastError();
+    return launch_tc<false>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, err, s);
+}
+
+cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
+                               int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s)
+{
+    (void)num_sms;
+    return launch_tc<true>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, err, s);
 }
 
 }  // namespace farm

@@ -1,0 +1,84 @@
+"""GPU: the reduced-precision (BF16 + FP32 rescore) path against the FP64 oracle.
+
+The BF16 stage only chooses which candidates get re-scored; every kept rank is
+decided by exact FP32 cosines, so results must match the oracle (same checker
+as the FP32 path) wherever the FP32 top-R of a row lies inside its BF16
+top-C, and Recall@10 against the oracle's top 10 must be at least 0.99.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import parity
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2606_15476_gb300 as F
+    return F
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    c = F.farm_create(0)
+    yield c
+    F.farm_destroy(c)
+
+
+def _run(F, ctx, qb, prec, k=10):
+    h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred,
+                           qb.c_emb, prec)
+    return F.farm_topk(ctx, h, k, qb.n_q)
+
+
+def test_bf16_stage_cosine_error(F, ctx):
+    scenes, qb = synth.workload("site_n20k_d1152")
+    sc = scenes[0]
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    rows = np.concatenate([qb.tgt_emb[:16], qb.c_emb[:16]])
+    got = F.farm_similarity(ctx, 0, rows, sc.n, F.PREC_BF16)
+    errs = np.concatenate([np.abs(got[r] - oracle.cosines(sc, rows[r])) for r in range(rows.shape[0])])
+    # BF16 rounds each operand to 8 significant bits: |error| <= 2^-7 sum|u_k d_k| <= 2^-7
+    assert errs.max() <= 2.0 ** -7
+    assert np.median(errs) < 1e-4
+
+
+def test_bf16_exact_when_every_object_is_rescored(F, ctx):
+    scenes, qb = synth.workload("room_n200_d512")   # n = 200 <= the 256 candidates kept
+    sc = scenes[0]
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    out = _run(F, ctx, qb, F.PREC_BF16)
+    rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"])
+    assert rep.ok(), rep.summary()
+
+
+def test_bf16_recall_at_10_site_scale(F, ctx):
+    scenes, qb = synth.workload("site_n20k_d1152")
+    sc = scenes[0]
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    sub = qb.subset(range(128))
+    out = _run(F, ctx, sub, F.PREC_BF16)
+    ref = oracle.batch(sc, sub, 10)
+    hits = sum(len(set(out["idx"][q].tolist()) & set(ref["idx"][q].tolist())) for q in range(sub.n_q))
+    recall = hits / (10.0 * sub.n_q)
+    assert recall >= 0.99, recall
+    rep = parity.check_topk(sc, sub, 10, out["idx"], out["score"], out["pred"], out["anchor"])
+    assert len(rep.failures) <= max(1, sub.n_q // 100), rep.summary()
+
+
+def test_bf16_matches_fp32_path_on_full_batch(F, ctx):
+    scenes, qb = synth.workload("site_n20k_d1152")
+    sc = scenes[0]
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    a = _run(F, ctx, qb, F.PREC_FP32)
+    b = _run(F, ctx, qb, F.PREC_BF16)
+    same = np.mean([len(set(a["idx"][q].tolist()) & set(b["idx"][q].tolist())) / 10.0 for q in range(qb.n_q)])
+    assert same >= 0.99, same
