@@ -103,6 +103,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(values, dist=None, device=None):
+    """Element-wise max of per-rank timings (ms) over the process group.
+
+    Replicas only: ranks exchange nothing but these timings, after the timed
+    region.  Without a process group the values are returned unchanged."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_rate(n_units_per_rank, world, ms_per_step):
+    """Whole-job throughput: units all ranks processed / the slowest rank's step time."""
+    return world * n_units_per_rank / (ms_per_step * 1e-3)
+
+
 def cpu_baseline(scene, qb, k, n_sample, seed=0):
     """The oracle on a seeded query sample: its rate, and its TopK for recall."""
     import oracle
@@ -226,11 +244,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     stage_ms, launches = F.farm_stage_times(ctx, reset=True)
     F.farm_set_profiling(ctx, False)
-    ms_step = ms / args.steps
+    ms_step = max_over_ranks([ms / args.steps], dist, "cuda" if dist else None)[0]
     if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
         dist.barrier()
 
     # ---- end to end through host buffers (pinned), same steps
@@ -255,10 +270,7 @@ def main():
         step_host()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks([e2e_ms], dist, "cuda" if dist else None)[0]
     h2d = (n_q + n_c) * sc.dim * 4 + 4 * (3 * n_q + 1 + n_c)
     d2h = n_q * K_TOP * (4 + 4 + 16 + 16)
 
@@ -284,7 +296,7 @@ def main():
     achieved = flops_step / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0
 
     line = {
-        "metric": "relational queries/s", "value": world * n_q / (ms_step * 1e-3),
+        "metric": "relational queries/s", "value": job_rate(n_q, world, ms_step),
         "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp32_simt": "f32", "bf16": "bf16"}[args.precision],
@@ -293,7 +305,7 @@ def main():
                    "queries": n_q, "constraint_rows": n_c, "top_k": K_TOP,
                    "precision": args.precision, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (descriptor splits 184 MB + similarity block 1.15 GB)"},
-        "e2e": {"value": world * n_q / (e2e_ms * 1e-3), "unit": "queries/s",
+        "e2e": {"value": job_rate(n_q, world, e2e_ms), "unit": "queries/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "stage_ms_per_step": {"prepare": stage_ms[0] / args.steps, "similarity": gemm_ms,
