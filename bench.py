@@ -176,7 +176,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_simt", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_simt", "bf16", "fp8"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-sample", type=int, default=384)
     ap.add_argument("--ref-queries", type=int, default=64)
@@ -208,7 +208,8 @@ def main():
 
     scenes, qb = synth.workload(args.workload)
     sc = scenes[0]
-    prec = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16}[args.precision]
+    prec = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16,
+            "fp8": F.PREC_FP8}[args.precision]
     stream = torch.cuda.Stream()          # the library and the timing events share it
     torch.cuda.set_stream(stream)
     ctx = F.farm_create(local, stream)
@@ -288,6 +289,10 @@ def main():
         peak = peaks["bf16_tflops_sustained"]
         bound, unit = "tensor", "TFLOP/s"
         peak_note = f"{peak_kind} sustained bf16"
+    elif args.precision == "fp8":
+        peak = peaks["bf16_tflops_sustained"] * (4.5 / 2.25)
+        bound, unit = "tensor", "TFLOP/s"
+        peak_note = f"{peak_kind} sustained bf16 x 4.5/2.25 (FP8 dense)"
     else:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -299,7 +304,7 @@ def main():
         "metric": "relational queries/s", "value": job_rate(n_q, world, ms_step),
         "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp32_simt": "f32", "bf16": "bf16"}[args.precision],
+        "dtype": {"fp32": "f32", "fp32_simt": "f32", "bf16": "bf16", "fp8": "f8e4m3"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "n_objects": sc.n, "dim": sc.dim, "n_views": sc.n_views,
                    "queries": n_q, "constraint_rows": n_c, "top_k": K_TOP,

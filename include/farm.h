@@ -65,6 +65,7 @@ typedef enum {
 typedef enum {
     FARM_PREC_FP32 = 0,       /* FP32-accurate: tcgen05 tensor cores, 3-term split TF32 */
     FARM_PREC_BF16 = 1,       /* BF16 operands, FP32 accumulate, FP32 rescore of the borderline */
+    FARM_PREC_FP8 = 2,        /* FP8-E4M3 operands with per-row scales, FP32 accumulate, FP32 rescore */
     FARM_PREC_FP32_SIMT = 3   /* FP32 FMA on the CUDA cores (independent check path) */
 } farm_precision;
 
@@ -186,8 +187,8 @@ farm_status farm_sync(farm_ctx *ctx);
 
 /*
  * Cosine similarity of n_rows embeddings against every object of a scene,
- * computed by the kernels of `precision` (App. D.2 step 3; FARM_PREC_BF16
- * returns the BF16 stage's approximate cosines):
+ * computed by the kernels of `precision` (App. D.2 step 3; FARM_PREC_BF16 and
+ * FARM_PREC_FP8 return the reduced-precision stage's approximate cosines):
  *   emb [n_rows, dim] FP32, out [n_rows, n] FP32 (host or device per flags).
  */
 farm_status farm_similarity(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb,

@@ -125,6 +125,7 @@ cudaError_t ws_get(farm_ctx *ctx, Buf b, size_t count, T **out)
 void free_scene(Scene &s)
 {
     cudaFree(s.desc32); cudaFree(s.desc_hi); cudaFree(s.desc_lo); cudaFree(s.desc_bf16);
+    cudaFree(s.desc_fp8); cudaFree(s.desc_scale);
     cudaFree(s.cls); cudaFree(s.pos); cudaFree(s.size); cudaFree(s.views);
     s = Scene{};
 }
@@ -177,14 +178,23 @@ farm_status check_device_errors(farm_ctx *ctx)
 struct RowOps {
     float *q32 = nullptr, *qhi = nullptr, *qlo = nullptr;
     uint16_t *qbf = nullptr;
+    uint8_t *qf8 = nullptr;
+    float *qscale = nullptr;
 };
+
+bool reduced_precision(int32_t prec) { return prec == FARM_PREC_BF16 || prec == FARM_PREC_FP8; }
 
 cudaError_t alloc_rows(farm_ctx *ctx, int32_t prec, int64_t rows, int32_t dim_pad, RowOps &r)
 {
     const size_t cnt = (size_t)std::max<int64_t>(rows, 1) * dim_pad;
     cudaError_t e = cudaSuccess;
-    if (prec == FARM_PREC_FP32_SIMT || prec == FARM_PREC_BF16) {
+    if (prec == FARM_PREC_FP32_SIMT || reduced_precision(prec)) {
         if ((e = ws_get(ctx, farm::B_Q32, cnt, &r.q32)) != cudaSuccess) return e;
+    }
+    if (prec == FARM_PREC_FP8) {
+        if ((e = ws_get(ctx, farm::B_QF8, cnt, &r.qf8)) != cudaSuccess) return e;
+        if ((e = ws_get(ctx, farm::B_QSCALE, (size_t)std::max<int64_t>(rows, 1), &r.qscale)) != cudaSuccess)
+            return e;
     }
     if (prec == FARM_PREC_FP32) {
         if ((e = ws_get(ctx, farm::B_QHI, cnt, &r.qhi)) != cudaSuccess) return e;
@@ -217,6 +227,12 @@ farm_status run_similarity(farm_ctx *ctx, int32_t prec, const RowOps &ops, int64
             return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
         LAUNCH(farm::launch_sim_tc_bf16(ops.qbf + off, s.desc_bf16, S, rows, s.n, s.dim_pad, ld_s, c.num_sms,
                                         c.d_err, c.stream));
+        return FARM_OK;
+    case FARM_PREC_FP8:
+        if (!farm::sim_tc_available())
+            return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
+        LAUNCH(farm::launch_sim_tc_fp8(ops.qf8 + off, ops.qscale + r0, s.desc_fp8, s.desc_scale, S, rows, s.n,
+                                       s.dim_pad, ld_s, c.num_sms, c.d_err, c.stream));
         return FARM_OK;
     default:
         return fail(ctx, FARM_EINVAL, "precision not supported by this build");
@@ -367,6 +383,8 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
     if ((e = cudaMalloc(&ns.desc_hi, nd * 4)) != cudaSuccess) return bailmem(e);
     if ((e = cudaMalloc(&ns.desc_lo, nd * 4)) != cudaSuccess) return bailmem(e);
     if ((e = cudaMalloc(&ns.desc_bf16, nd * 2)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.desc_fp8, nd)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.desc_scale, (size_t)n * 4)) != cudaSuccess) return bailmem(e);
     if ((e = cudaMalloc(&ns.cls, (size_t)n * 4)) != cudaSuccess) return bailmem(e);
     if ((e = cudaMalloc(&ns.pos, (size_t)n * 12)) != cudaSuccess) return bailmem(e);
     if ((e = cudaMalloc(&ns.size, (size_t)n * 12)) != cudaSuccess) return bailmem(e);
@@ -385,6 +403,10 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
     if ((e = farm::launch_normalize_rows(d_desc, nullptr, n, dim, ns.dim_pad, ns.desc32, ns.desc_hi,
                                          ns.desc_lo, ns.desc_bf16, c.d_err, farm::kErrBadDesc,
                                          c.stream)) != cudaSuccess)
+        return bailmem(e);
+    ctx->c.launches += 1;
+    if ((e = farm::launch_quantize_fp8_rows(ns.desc32, n, ns.dim_pad, ns.desc_fp8, ns.desc_scale, c.stream)) !=
+        cudaSuccess)
         return bailmem(e);
     if ((e = cudaMemcpyAsync(ns.cls, cls, (size_t)n * 4, kind, c.stream)) != cudaSuccess) return bailmem(e);
     if ((e = cudaMemcpyAsync(ns.pos, box, (size_t)n * 12, kind, c.stream)) != cudaSuccess) return bailmem(e);
@@ -425,7 +447,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     Ctx &c = ctx->c;
     if (!batch_handle) return fail(ctx, FARM_EINVAL, "batch_handle must be non-null");
     if (n_q < 0 || n_q > 0x7fffffff) return fail(ctx, FARM_EINVAL, "n_q out of range");
-    if (precision != FARM_PREC_FP32 && precision != FARM_PREC_BF16 && precision != FARM_PREC_FP32_SIMT)
+    if (precision != FARM_PREC_FP32 && precision != FARM_PREC_BF16 && precision != FARM_PREC_FP32_SIMT &&
+        precision != FARM_PREC_FP8)
         return fail(ctx, FARM_EINVAL, "unknown precision");
     if (n_q > 0 && (!scene_of_q || !tgt_emb || !tgt_cls || !c_off))
         return fail(ctx, FARM_EINVAL, "scene_of_q, tgt_emb, tgt_cls and c_off must be non-null");
@@ -570,7 +593,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     int32_t *bsel_t = nullptr, *bsel_l = nullptr;
     const int32_t cstride_t = bf16_keep_target(p, stride_t, max_n);
     const int32_t cstride_l = bf16_keep_landmark(p, stride_l, max_n);
-    if (precision == FARM_PREC_BF16) {
+    if (reduced_precision(precision)) {
         CK(ws_get(ctx, farm::B_BSEL_T, (size_t)n_q * cstride_t, &bsel_t));
         CK(ws_get(ctx, farm::B_BSEL_L, (size_t)std::max<int64_t>(n_c, 1) * cstride_l, &bsel_l));
     }
@@ -605,6 +628,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     if (n_c > 0)
         LAUNCH(farm::launch_normalize_rows(src_c, d_rowmap + n_q, n_c, dim, dim_pad, ops.q32, ops.qhi, ops.qlo,
                                            ops.qbf, c.d_err, farm::kErrBadRow, c.stream));
+    if (precision == FARM_PREC_FP8)
+        LAUNCH(farm::launch_quantize_fp8_rows(ops.q32, rows_total, dim_pad, ops.qf8, ops.qscale, c.stream));
     mark_end(ctx, m0);
 
     // ---- stages 1-2: similarity and rank selection per scene group, in row chunks
@@ -623,7 +648,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             mark_end(ctx, m1);
             const int64_t ntr = std::max<int64_t>(0, std::min<int64_t>(g.nq - r0, r1 - r0));
             const int m2 = mark_begin(ctx, 2);
-            if (precision != FARM_PREC_BF16) {
+            if (!reduced_precision(precision)) {
                 LAUNCH(farm::launch_select_rows(d_sim, ld, s.n, r1 - r0, ntr, Rs, klm, tsel_idx, tsel_cos,
                                                 g.q0 + r0, stride_t, lsel_idx, g.cp0 + r0 + ntr - g.nq, stride_l,
                                                 c.stream));
@@ -731,7 +756,8 @@ farm_status farm_similarity(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, con
     if (n_rows < 0) return fail(ctx, FARM_EINVAL, "n_rows must be >= 0");
     if (n_rows == 0) return FARM_OK;
     if (!emb || !out) return fail(ctx, FARM_EINVAL, "emb and out must be non-null");
-    if (precision != FARM_PREC_FP32 && precision != FARM_PREC_FP32_SIMT && precision != FARM_PREC_BF16)
+    if (precision != FARM_PREC_FP32 && precision != FARM_PREC_FP32_SIMT && precision != FARM_PREC_BF16 &&
+        precision != FARM_PREC_FP8)
         return fail(ctx, FARM_EINVAL, "unknown precision");
     CK(cudaSetDevice(c.device));
     const Scene &s = c.scenes[scene_id];
@@ -747,6 +773,8 @@ farm_status farm_similarity(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, con
     CK(alloc_rows(ctx, precision, n_rows, s.dim_pad, ops));
     LAUNCH(farm::launch_normalize_rows(src, nullptr, n_rows, s.dim, s.dim_pad, ops.q32, ops.qhi, ops.qlo, ops.qbf,
                                        c.d_err, farm::kErrBadRow, c.stream));
+    if (precision == FARM_PREC_FP8)
+        LAUNCH(farm::launch_quantize_fp8_rows(ops.q32, n_rows, s.dim_pad, ops.qf8, ops.qscale, c.stream));
     float *S = out;
     if (!dev) CK(ws_get(ctx, farm::B_SIM, (size_t)n_rows * s.n, &S));
     farm_status st = run_similarity(ctx, precision, ops, 0, n_rows, s, S, s.n);

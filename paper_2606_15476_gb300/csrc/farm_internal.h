@@ -44,6 +44,8 @@ struct Scene {
     float *desc_hi = nullptr;   // [n, dim_pad] TF32-representable high part
     float *desc_lo = nullptr;   // [n, dim_pad] residual desc32 - desc_hi
     uint16_t *desc_bf16 = nullptr;  // [n, dim_pad] BF16 of desc32
+    uint8_t *desc_fp8 = nullptr;    // [n, dim_pad] E4M3 of desc32 / desc_scale
+    float *desc_scale = nullptr;    // [n] per-row FP8 scale
     int32_t *cls = nullptr;     // [n]
     float *pos = nullptr;       // [3, n] centres (SoA)
     float *size = nullptr;      // [3, n]
@@ -76,6 +78,8 @@ enum Buf {
     B_TOPK,         // int32/float [n_q, k, 10] TopK staging for host outputs
     B_BSEL_T,       // int32 [n_q, C_t] BF16-stage target candidates (before FP32 rescore)
     B_BSEL_L,       // int32 [n_c, C_l] BF16-stage landmark candidates
+    B_QF8,          // uint8 [rows, dim_pad] E4M3 rows
+    B_QSCALE,       // float [rows] their scales
     B_COUNT
 };
 
@@ -124,6 +128,10 @@ cudaError_t launch_normalize_rows(const float *src, const int32_t *dst_rows, int
                                   float *dst_lo, uint16_t *dst_bf16, int32_t *err, int err_bit,
                                   cudaStream_t s);
 
+// E4M3 copy of unit rows with a per-row scale (max|x| / 448).
+cudaError_t launch_quantize_fp8_rows(const float *src, int64_t rows, int32_t dim_pad, uint8_t *dst, float *scale,
+                                     cudaStream_t s);
+
 // Pre-compute the per-view record of kViewStride floats from SoA views.
 cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_views,
                                  float *out, cudaStream_t s);
@@ -140,6 +148,10 @@ cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const flo
 // BF16 operands, FP32 accumulation (first stage of the reduced-precision path).
 cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
                                int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s);
+// FP8 E4M3 operands with per-row scales applied in the epilogue.
+cudaError_t launch_sim_tc_fp8(const uint8_t *q, const float *scale_q, const uint8_t *d, const float *scale_d,
+                              float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, int num_sms,
+                              int32_t *err, cudaStream_t s);
 bool sim_tc_available();
 
 // Per row r of S (rows x n, leading dim ld_s): the R_r largest entries in

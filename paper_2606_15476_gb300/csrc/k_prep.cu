@@ -8,6 +8,7 @@
 // relative per product (the dropped x_lo*y_lo term and the rounding of x_lo
 // are both of that order).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "farm_internal.h"
 
@@ -88,7 +89,39 @@ __global__ void prepare_views_kernel(const float *__restrict__ v, int64_t n, int
     o[6] = rx; o[7] = ry;
 }
 
+// One warp per unit row: scale = max|x| / 448 (the largest finite E4M3
+// value), q = E4M3(x / scale) with saturation.
+__global__ void quantize_fp8_rows_kernel(const float *__restrict__ src, int64_t rows, int32_t dim_pad,
+                                         uint8_t *__restrict__ dst, float *__restrict__ scale)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    const float *x = src + row * (int64_t)dim_pad;
+    float amax = 0.f;
+    for (int k = lane; k < dim_pad; k += 32) amax = fmaxf(amax, fabsf(x[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const float sc = amax > 0.f ? amax / 448.f : 1.f;
+    if (lane == 0) scale[row] = sc;
+    uint8_t *d = dst + row * (int64_t)dim_pad;
+    for (int k = lane; k < dim_pad; k += 32) {
+        const __nv_fp8_e4m3 v(x[k] / sc);
+        d[k] = v.__x;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_quantize_fp8_rows(const float *src, int64_t rows, int32_t dim_pad, uint8_t *dst, float *scale,
+                                     cudaStream_t s)
+{
+    if (rows <= 0) return cudaSuccess;
+    const int warps = 8;
+    quantize_fp8_rows_kernel<<<(unsigned)((rows + warps - 1) / warps), warps * 32, 0, s>>>(src, rows, dim_pad, dst,
+                                                                                             scale);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_normalize_rows(const float *src, const int32_t *dst_rows, int64_t rows,
                                   int32_t dim, int32_t dim_pad, float *dst32, float *dst_hi,

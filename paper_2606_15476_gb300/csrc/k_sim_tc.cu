@@ -1,12 +1,14 @@
 // k_sim_tc.cu -- descriptor similarity on the 5th-generation tensor cores
 // (App. D.2 step 3: the cosine of every query row against every object).
 //
-// Two arithmetic modes share one kernel template:
+// Three arithmetic modes share one kernel template:
 //  * FP32-accurate, three TF32 products:
 //      S[r, j] = <q_r, d_j> ~= q_hi.d_hi + q_hi.d_lo + q_lo.d_hi
-//  * BF16: S[r, j] ~= <bf16(q_r), bf16(d_j)> with FP32 accumulation, the
-//    first stage of the reduced-precision path (its borderline candidates are
-//    re-scored in FP32 afterwards).
+//  * BF16: S[r, j] ~= <bf16(q_r), bf16(d_j)> with FP32 accumulation;
+//  * FP8-E4M3 with per-row scales: S[r, j] ~= s_r t_j <e4m3(q_r/s_r), e4m3(d_j/t_j)>,
+//    the scales applied in the epilogue.
+//  The last two are the first stage of the reduced-precision paths (their
+//  borderline candidates are re-scored in FP32 afterwards).
 //
 // FP32-accurate mode:
 // with x_hi = TF32(x) and x_lo = TF32(x - x_hi) prepared by the normalisation
@@ -52,11 +54,13 @@ constexpr uint32_t WAIT_LIMIT = 1u << 24;    // try_wait polls before giving up 
 constexpr int GROUP_M = 16;                  // tile raster: 16 row tiles share each column tile
 constexpr int ACC_CORR = 256;                // TMEM column of the correction accumulator (TF32 mode)
 
+enum : int { kTf32x3 = 0, kBf16 = 1, kFp8 = 2 };
+
 // Per-mode layout of a pipeline stage.
-template <bool BF16>
+template <int MODE>
 struct Mode;
 template <>
-struct Mode<false> {                         // three-term TF32
+struct Mode<kTf32x3> {                       // three-term TF32
     static constexpr int BK = 16;            // FP32 elements per K slice (64-byte rows)
     static constexpr int ROW_BYTES = 64;
     static constexpr int A_BYTES = BM * ROW_BYTES;   // 8 KB, twice (hi, lo)
@@ -67,7 +71,7 @@ struct Mode<false> {                         // three-term TF32
     static constexpr uint32_t SBO = 512;     // 8 rows x 64 bytes
 };
 template <>
-struct Mode<true> {                          // BF16
+struct Mode<kBf16> {                         // BF16
     static constexpr int BK = 64;            // BF16 elements per K slice (128-byte rows)
     static constexpr int ROW_BYTES = 128;
     static constexpr int A_BYTES = BM * ROW_BYTES;   // 16 KB
@@ -77,8 +81,20 @@ struct Mode<true> {                          // BF16
     static constexpr uint64_t LAYOUT = 2;    // 128-byte swizzle
     static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
 };
-static_assert(2 * Mode<false>::A_BYTES + 2 * Mode<false>::B_BYTES == STAGE_BYTES, "stage size");
-static_assert(Mode<true>::A_BYTES + Mode<true>::B_BYTES == STAGE_BYTES, "stage size");
+template <>
+struct Mode<kFp8> {                          // FP8 E4M3
+    static constexpr int BK = 128;           // FP8 elements per K slice (128-byte rows)
+    static constexpr int ROW_BYTES = 128;
+    static constexpr int A_BYTES = BM * ROW_BYTES;   // 16 KB
+    static constexpr int B_BYTES = BN * ROW_BYTES;   // 32 KB
+    static constexpr int KSTEPS = 4;         // 32 FP8 values (32 bytes) per MMA
+    static constexpr int TMEM_COLS = 256;
+    static constexpr uint64_t LAYOUT = 2;    // 128-byte swizzle
+    static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
+};
+static_assert(2 * Mode<kTf32x3>::A_BYTES + 2 * Mode<kTf32x3>::B_BYTES == STAGE_BYTES, "stage size");
+static_assert(Mode<kBf16>::A_BYTES + Mode<kBf16>::B_BYTES == STAGE_BYTES, "stage size");
+static_assert(Mode<kFp8>::A_BYTES + Mode<kFp8>::B_BYTES == STAGE_BYTES, "stage size");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -125,19 +141,19 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
 // Shared-memory matrix descriptor of a K-major operand tile with rows of
 // ROW_BYTES swizzled in 8-row core groups SBO bytes apart; version 1.  The
 // leading byte offset is unused for swizzled K-major layouts.
-template <bool BF16>
+template <int MODE>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);              // start address
-    d |= (uint64_t)(Mode<BF16>::SBO >> 4) << 32;            // stride byte offset
+    d |= (uint64_t)(Mode<MODE>::SBO >> 4) << 32;            // stride byte offset
     d |= (uint64_t)1 << 46;                                 // descriptor version
-    d |= Mode<BF16>::LAYOUT << 61;                          // swizzle mode
+    d |= Mode<MODE>::LAYOUT << 61;                          // swizzle mode
     return d;
 }
 
 // Instruction descriptors: D = F32, A and B K-major, M = 128, N = 256;
-// operand format TF32 (kind::tf32) or BF16 (kind::f16).
+// operand format TF32 (2, kind::tf32), BF16 (1, kind::f16) or E4M3 (0, kind::f8f6f4).
 __host__ __device__ constexpr uint32_t idesc(uint32_t ab_format)
 {
     return (1u << 4)                      // D format F32
@@ -165,6 +181,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(1u)), "r"(accumulate));
 }
 
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(0u)), "r"(accumulate));
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -189,16 +214,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Maps (TF32 mode): q_hi, q_lo, d_hi, d_lo.  (BF16 mode): q, d, and the last
-// two are unused.
-template <bool BF16>
+// Maps (TF32 mode): q_hi, q_lo, d_hi, d_lo.  (BF16, FP8 modes): q, d, and the
+// last two are unused.  scale_q / scale_d: per-row scales (FP8 mode only).
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant__ CUtensorMap map_q1,
               const __grid_constant__ CUtensorMap map_d0, const __grid_constant__ CUtensorMap map_d1,
               float *__restrict__ S, int64_t rows, int64_t n, int32_t k_slices, int64_t ld_s,
-              int32_t m_tiles, int32_t n_tiles, int32_t *err)
+              int32_t m_tiles, int32_t n_tiles, const float *__restrict__ scale_q,
+              const float *__restrict__ scale_d, int32_t *err)
 {
-    using M = Mode<BF16>;
+    using M = Mode<MODE>;
+    constexpr bool TWO_OPERAND_TILES = MODE != kTf32x3;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
@@ -252,7 +279,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 uint8_t *st = smem + s * STAGE_BYTES;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
                 const int kx = kb * M::BK;
-                if (BF16) {
+                if (TWO_OPERAND_TILES) {
                     tma_load_2d(st, &map_q0, &full[s], kx, m0);
                     tma_load_2d(st + M::A_BYTES, &map_d0, &full[s], kx, n0);
                 } else {
@@ -283,12 +310,15 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-                if (BF16) {
+                if (TWO_OPERAND_TILES) {
                     const uint32_t a = st, b = st + M::A_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < M::KSTEPS; ++kk) {
-                        const uint32_t off = kk * 32;     // 16 BF16 values = 32 bytes along K
-                        mma_bf16(tmem, smem_desc<true>(a + off), smem_desc<true>(b + off), (kb | kk) != 0);
+                        const uint32_t off = kk * 32;     // 32 bytes along K: 16 BF16 or 32 FP8 values
+                        if (MODE == kBf16)
+                            mma_bf16(tmem, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
+                        else
+                            mma_e4m3(tmem, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
                     }
                 } else {
                     const uint32_t a_hi = st, a_lo = st + M::A_BYTES;
@@ -297,9 +327,9 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     for (int kk = 0; kk < M::KSTEPS; ++kk) {
                         const uint32_t off = kk * 32;     // 8 TF32 values = 32 bytes along K
                         const uint32_t acc = (kb | kk) != 0;
-                        mma_tf32(tmem, smem_desc<false>(a_hi + off), smem_desc<false>(b_hi + off), acc);
-                        mma_tf32(tmem + ACC_CORR, smem_desc<false>(a_hi + off), smem_desc<false>(b_lo + off), acc);
-                        mma_tf32(tmem + ACC_CORR, smem_desc<false>(a_lo + off), smem_desc<false>(b_hi + off), 1u);
+                        mma_tf32(tmem, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), acc);
+                        mma_tf32(tmem + ACC_CORR, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_lo + off), acc);
+                        mma_tf32(tmem + ACC_CORR, smem_desc<MODE>(a_lo + off), smem_desc<MODE>(b_hi + off), 1u);
                     }
                 }
                 mma_commit(&empty[s]);
@@ -323,13 +353,18 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 float v[32];
                 const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32);
                 tmem_ld32(lane_addr, v);
-                if (!BF16) {
+                if (MODE == kTf32x3) {
                     float w[32];
                     tmem_ld32(lane_addr + ACC_CORR, w);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] += w[i];
                 }
                 const int64_t col0 = (int64_t)n0 + c * 32;
+                if (MODE == kFp8 && r < rows) {
+                    const float sr = scale_q[r];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] *= sr * (col0 + i < n ? __ldg(scale_d + col0 + i) : 0.f);
+                }
                 if (r < rows) {
                     if (vec && col0 + 32 <= n) {
 #pragma unroll
@@ -368,50 +403,56 @@ bool get_encoder()
 
 // 2D tensor [outer, inner] row-major (FP32 or BF16), box [box_outer, BK],
 // swizzle matching the mode's row width.
-template <bool BF16>
+template <int MODE>
 bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, int box_outer)
 {
-    using M = Mode<BF16>;
-    const int esize = BF16 ? 2 : 4;
+    using M = Mode<MODE>;
+    const int esize = MODE == kTf32x3 ? 4 : (MODE == kBf16 ? 2 : 1);
+    const CUtensorMapDataType dt = MODE == kTf32x3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (MODE == kBf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
     cuuint64_t strides[1] = {(cuuint64_t)inner * esize};
     cuuint32_t box[2] = {(cuuint32_t)M::BK, (cuuint32_t)box_outer};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(m, BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                          const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          BF16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+    CUresult r = g_encode(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          MODE == kTf32x3 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-template <bool BF16>
+template <int MODE>
 cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void *d1, float *S, int64_t rows,
-                      int64_t n, int32_t dim_pad, int64_t ld_s, int32_t *err, cudaStream_t s)
+                      int64_t n, int32_t dim_pad, int64_t ld_s, const float *scale_q, const float *scale_d,
+                      int32_t *err, cudaStream_t s)
 {
-    using M = Mode<BF16>;
+    using M = Mode<MODE>;
+    constexpr bool TWO = MODE != kTf32x3;
     if (rows <= 0 || n <= 0) return cudaSuccess;
     if (dim_pad % M::BK != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (!get_encoder()) return cudaErrorNotSupported;
     // TMA: 16-byte aligned bases; row strides are multiples of 16 bytes (dim_pad % 64 == 0)
-    const uintptr_t al = (uintptr_t)q0 | (uintptr_t)d0 | (BF16 ? 0 : ((uintptr_t)q1 | (uintptr_t)d1));
+    const uintptr_t al = (uintptr_t)q0 | (uintptr_t)d0 | (TWO ? 0 : ((uintptr_t)q1 | (uintptr_t)d1));
     if (al & 15u) return cudaErrorMisalignedAddress;
     CUtensorMap mq0, mq1, md0, md1;
-    if (!make_map<BF16>(&mq0, q0, dim_pad, rows, BM) || !make_map<BF16>(&md0, d0, dim_pad, n, BN))
+    if (MODE == kFp8 && (!scale_q || !scale_d)) return cudaErrorInvalidValue;
+    if (!make_map<MODE>(&mq0, q0, dim_pad, rows, BM) || !make_map<MODE>(&md0, d0, dim_pad, n, BN))
         return cudaErrorInvalidValue;
-    if (BF16) {
+    if (TWO) {
         mq1 = mq0;
         md1 = md0;
-    } else if (!make_map<BF16>(&mq1, q1, dim_pad, rows, BM) || !make_map<BF16>(&md1, d1, dim_pad, n, BN)) {
+    } else if (!make_map<MODE>(&mq1, q1, dim_pad, rows, BM) || !make_map<MODE>(&md1, d1, dim_pad, n, BN)) {
         return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaFuncSetAttribute(sim_tc_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(sim_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int m_tiles = (int)((rows + BM - 1) / BM);
     const int n_tiles = (int)((n + BN - 1) / BN);
     const int64_t tiles = (int64_t)m_tiles * n_tiles;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    sim_tc_kernel<BF16><<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(mq0, mq1, md0, md1, S, rows, n,
-                                                                       dim_pad / M::BK, ld_s, m_tiles, n_tiles, err);
+    sim_tc_kernel<MODE><<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(mq0, mq1, md0, md1, S, rows, n,
+                                                                       dim_pad / M::BK, ld_s, m_tiles, n_tiles,
+                                                                       scale_q, scale_d, err);
     return cudaGetLastError();
 }
 
@@ -424,14 +465,22 @@ cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const flo
                                  cudaStream_t s)
 {
     (void)num_sms;
-    return launch_tc<false>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, err, s);
+    return launch_tc<kTf32x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, err, s);
 }
 
 cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
                                int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s)
 {
     (void)num_sms;
-    return launch_tc<true>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, err, s);
+    return launch_tc<kBf16>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, nullptr, nullptr, err, s);
+}
+
+cudaError_t launch_sim_tc_fp8(const uint8_t *q, const float *scale_q, const uint8_t *d, const float *scale_d,
+                              float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, int num_sms,
+                              int32_t *err, cudaStream_t s)
+{
+    (void)num_sms;
+    return launch_tc<kFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, err, s);
 }
 
 }  // namespace farm

@@ -16,6 +16,7 @@ from . import _build
 
 PREC_FP32 = 0
 PREC_BF16 = 1
+PREC_FP8 = 2
 PREC_FP32_SIMT = 3
 PTR_DEVICE = 1
 N_STAGES = 4

@@ -1,9 +1,11 @@
-"""GPU: the reduced-precision (BF16 + FP32 rescore) path against the FP64 oracle.
+"""GPU: the reduced-precision paths (BF16 or FP8-E4M3, then FP32 rescore)
+against the FP64 oracle.
 
-The BF16 stage only chooses which candidates get re-scored; every kept rank is
-decided by exact FP32 cosines, so results must match the oracle (same checker
-as the FP32 path) wherever the FP32 top-R of a row lies inside its BF16
-top-C, and Recall@10 against the oracle's top 10 must be at least 0.99.
+The reduced-precision stage only chooses which candidates get re-scored; every
+kept rank is decided by exact FP32 cosines, so results must match the oracle
+(same checker as the FP32 path) wherever the FP32 top-R of a row lies inside
+its reduced-precision top-C, and Recall@10 against the oracle's top 10 must be
+at least 0.99.
 """
 import numpy as np
 import pytest
@@ -39,33 +41,46 @@ def _run(F, ctx, qb, prec, k=10):
     return F.farm_topk(ctx, h, k, qb.n_q)
 
 
-def test_bf16_stage_cosine_error(F, ctx):
+REDUCED = ["bf16", "fp8"]
+
+
+def code(F, name):
+    return {"bf16": F.PREC_BF16, "fp8": F.PREC_FP8}[name]
+
+
+@pytest.mark.parametrize("prec,bound,typical", [
+    # BF16 keeps 8 significant bits per operand: |error| <= (2 * 2^-8 + 2^-16) sum|u_k d_k| <= 2^-7
+    ("bf16", 2.0 ** -7, 1e-4),
+    # E4M3 keeps 4: |error| <= (2 * 2^-4 + 2^-8) sum|u_k d_k| <= 0.13
+    ("fp8", 0.13, 5e-3)])
+def test_reduced_stage_cosine_error(F, ctx, prec, bound, typical):
     scenes, qb = synth.workload("site_n20k_d1152")
     sc = scenes[0]
     F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
     rows = np.concatenate([qb.tgt_emb[:16], qb.c_emb[:16]])
-    got = F.farm_similarity(ctx, 0, rows, sc.n, F.PREC_BF16)
+    got = F.farm_similarity(ctx, 0, rows, sc.n, code(F, prec))
     errs = np.concatenate([np.abs(got[r] - oracle.cosines(sc, rows[r])) for r in range(rows.shape[0])])
-    # BF16 rounds each operand to 8 significant bits: |error| <= 2^-7 sum|u_k d_k| <= 2^-7
-    assert errs.max() <= 2.0 ** -7
-    assert np.median(errs) < 1e-4
+    assert errs.max() <= bound
+    assert np.median(errs) < typical
 
 
-def test_bf16_exact_when_every_object_is_rescored(F, ctx):
+@pytest.mark.parametrize("prec", REDUCED)
+def test_reduced_exact_when_every_object_is_rescored(F, ctx, prec):
     scenes, qb = synth.workload("room_n200_d512")   # n = 200 <= the 256 candidates kept
     sc = scenes[0]
     F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
-    out = _run(F, ctx, qb, F.PREC_BF16)
+    out = _run(F, ctx, qb, code(F, prec))
     rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"])
     assert rep.ok(), rep.summary()
 
 
-def test_bf16_recall_at_10_site_scale(F, ctx):
+@pytest.mark.parametrize("prec", REDUCED)
+def test_reduced_recall_at_10_site_scale(F, ctx, prec):
     scenes, qb = synth.workload("site_n20k_d1152")
     sc = scenes[0]
     F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
     sub = qb.subset(range(128))
-    out = _run(F, ctx, sub, F.PREC_BF16)
+    out = _run(F, ctx, sub, code(F, prec))
     ref = oracle.batch(sc, sub, 10)
     hits = sum(len(set(out["idx"][q].tolist()) & set(ref["idx"][q].tolist())) for q in range(sub.n_q))
     recall = hits / (10.0 * sub.n_q)
@@ -74,11 +89,12 @@ def test_bf16_recall_at_10_site_scale(F, ctx):
     assert len(rep.failures) <= max(1, sub.n_q // 100), rep.summary()
 
 
-def test_bf16_matches_fp32_path_on_full_batch(F, ctx):
+@pytest.mark.parametrize("prec", REDUCED)
+def test_reduced_matches_fp32_path_on_full_batch(F, ctx, prec):
     scenes, qb = synth.workload("site_n20k_d1152")
     sc = scenes[0]
     F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
     a = _run(F, ctx, qb, F.PREC_FP32)
-    b = _run(F, ctx, qb, F.PREC_BF16)
+    b = _run(F, ctx, qb, code(F, prec))
     same = np.mean([len(set(a["idx"][q].tolist()) & set(b["idx"][q].tolist())) / 10.0 for q in range(qb.n_q)])
     assert same >= 0.99, same
