@@ -66,7 +66,8 @@ typedef enum {
     FARM_PREC_FP32 = 0,       /* FP32-accurate: tcgen05 tensor cores, 3-term split TF32 */
     FARM_PREC_BF16 = 1,       /* BF16 operands, FP32 accumulate, FP32 rescore of the borderline */
     FARM_PREC_FP8 = 2,        /* FP8-E4M3 operands with per-row scales, FP32 accumulate, FP32 rescore */
-    FARM_PREC_FP32_SIMT = 3   /* FP32 FMA on the CUDA cores (independent check path) */
+    FARM_PREC_FP32_SIMT = 3,  /* FP32 FMA on the CUDA cores (independent check path) */
+    FARM_PREC_LEARNED = 4     /* learned 128-d prefilter (farm_mlp_*), top 512 re-scored in FP32 */
 } farm_precision;
 
 #define FARM_MAX_CONSTRAINTS 4
@@ -84,8 +85,9 @@ typedef enum {
  * k_max is the largest k a later farm_topk may ask for: farm_query_batch keeps
  * only candidates that can still reach the top k_max (see farm_query_batch).
  * rescore (1 .. 512) is the number of candidates per target row the BF16 path
- * re-scores in FP32 (at least the rank bound R of farm_query_batch); landmark
- * rows re-score max(rescore / 4, k_anchor).
+ * re-scores in FP32 (at least the rank bound R of farm_query_batch; the FP8
+ * path keeps twice as many, at most 512); landmark rows re-score a quarter of
+ * that, at least k_anchor.
  */
 typedef struct {
     float mu;
@@ -240,6 +242,48 @@ farm_status farm_candidates(farm_ctx *ctx, uint64_t batch_handle, int32_t *tgt_i
 #define FARM_NOALLOC_SCRATCH_BYTES (32u << 20)
 farm_status farm_rank_rows_noalloc(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb,
                                    int32_t r, int32_t precision, int32_t *out_idx, float *out_cos);
+
+/*
+ * Learned prefilter.  A small network f(x) = normalize(W2 gelu(W1 x + b1) + b2)
+ * (x: a unit row of length dim; W1: hidden x dim; W2: out_dim x hidden; GELU
+ * in its erf form) compresses descriptors and query rows to out_dim values.
+ * With FARM_PREC_LEARNED, farm_query_batch ranks objects by f(q).f(d) (BF16
+ * tensor-core products), keeps the best 512 per target row (128 per landmark
+ * row) and re-scores them with exact FP32 cosines before ranking; the
+ * full-descriptor paths are its fallback and the judge of its recall.
+ * Requirements: 1 <= dim <= 8192, hidden in [64, 4096] and out_dim in
+ * [64, 1024], both multiples of 64; dim equal to the scenes' dim.  The paper
+ * ranks with full embeddings (App. D.2 step 3); this compression is an
+ * addition of this library.
+ *
+ * farm_mlp_set: install weights (host FP32; W1 [hidden, dim], b1 [hidden],
+ *   W2 [out_dim, hidden], b2 [out_dim], row-major).  Scenes' cached
+ *   embeddings are recomputed on their next learned query.
+ * farm_mlp_get: copy the current weights out (any pointer may be NULL).
+ * farm_mlp_loss_grad: for n_pairs (query row xq[i], descriptor xd[i], target
+ *   y[i], weight w[i] (NULL: 1)) rows used as given, writes the loss
+ *   L = sum_i w_i (f(xq_i).f(xd_i) - y_i)^2 / sum_i w_i and its gradient with
+ *   respect to [W1 | b1 | W2 | b2] (grad, hidden*dim + hidden + out_dim*hidden
+ *   + out_dim floats; NULL to skip).  Host pointers; synchronises.
+ * farm_mlp_train: minimises that loss with Adam (lr, betas 0.9/0.999) over
+ *   `epochs` passes of mini-batches of `batch` pairs, shuffled each epoch by
+ *   SplitMix64 from `seed`; pair i joins row pair_row[i] of `rows` ([n_rows,
+ *   dim], host, normalised on the GPU) with object pair_obj[i] of scene
+ *   scene_id.  loss_out[epoch] (nullable) receives the mean batch loss.
+ *   Starts from the installed weights.  Synchronises.
+ * farm_mlp_embed: f of n_rows host rows x (normalised first) into host
+ *   out [n_rows, out_dim], with FP32 CUDA-core kernels (FARM_PREC_FP32_SIMT)
+ *   or the BF16 tensor-core inference path (FARM_PREC_BF16).
+ */
+farm_status farm_mlp_set(farm_ctx *ctx, int32_t dim, int32_t hidden, int32_t out_dim, const float *W1,
+                         const float *b1, const float *W2, const float *b2);
+farm_status farm_mlp_get(farm_ctx *ctx, float *W1, float *b1, float *W2, float *b2);
+farm_status farm_mlp_loss_grad(farm_ctx *ctx, int64_t n_pairs, const float *xq, const float *xd, const float *y,
+                               const float *w, float *loss, float *grad);
+farm_status farm_mlp_train(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *rows, int64_t n_pairs,
+                           const int32_t *pair_row, const int32_t *pair_obj, const float *y, const float *w,
+                           int32_t epochs, int32_t batch, float lr, uint64_t seed, float *loss_out);
+farm_status farm_mlp_embed(farm_ctx *ctx, int64_t n_rows, const float *x, int32_t precision, float *out);
 
 /*
  * Stage timing.  With profiling on, every farm_query_batch records CUDA events

@@ -37,6 +37,7 @@ struct farm_ctx {
 
 namespace farm {
 Ctx *ctx_of(farm_ctx *ctx) { return &ctx->c; }
+cudaError_t ws_alloc(farm_ctx *ctx, Buf b, size_t bytes, void **out);
 }  // namespace farm
 
 namespace {
@@ -113,6 +114,12 @@ cudaError_t ws_get(farm_ctx *ctx, Buf b, size_t bytes, void **out)
     return cudaSuccess;
 }
 
+}  // namespace
+
+cudaError_t farm::ws_alloc(farm_ctx *ctx, Buf b, size_t bytes, void **out) { return ws_get(ctx, b, bytes, out); }
+
+namespace {
+
 template <class T>
 cudaError_t ws_get(farm_ctx *ctx, Buf b, size_t count, T **out)
 {
@@ -125,7 +132,7 @@ cudaError_t ws_get(farm_ctx *ctx, Buf b, size_t count, T **out)
 void free_scene(Scene &s)
 {
     cudaFree(s.desc32); cudaFree(s.desc_hi); cudaFree(s.desc_lo); cudaFree(s.desc_bf16);
-    cudaFree(s.desc_fp8); cudaFree(s.desc_scale);
+    cudaFree(s.desc_fp8); cudaFree(s.desc_scale); cudaFree(s.comp);
     cudaFree(s.cls); cudaFree(s.pos); cudaFree(s.size); cudaFree(s.views);
     s = Scene{};
 }
@@ -180,9 +187,13 @@ struct RowOps {
     uint16_t *qbf = nullptr;
     uint8_t *qf8 = nullptr;
     float *qscale = nullptr;
+    uint16_t *qcomp = nullptr;   // learned embeddings of the rows
 };
 
-bool reduced_precision(int32_t prec) { return prec == FARM_PREC_BF16 || prec == FARM_PREC_FP8; }
+bool reduced_precision(int32_t prec)
+{
+    return prec == FARM_PREC_BF16 || prec == FARM_PREC_FP8 || prec == FARM_PREC_LEARNED;
+}
 
 cudaError_t alloc_rows(farm_ctx *ctx, int32_t prec, int64_t rows, int32_t dim_pad, RowOps &r)
 {
@@ -190,6 +201,13 @@ cudaError_t alloc_rows(farm_ctx *ctx, int32_t prec, int64_t rows, int32_t dim_pa
     cudaError_t e = cudaSuccess;
     if (prec == FARM_PREC_FP32_SIMT || reduced_precision(prec)) {
         if ((e = ws_get(ctx, farm::B_Q32, cnt, &r.q32)) != cudaSuccess) return e;
+    }
+    if (prec == FARM_PREC_BF16 || prec == FARM_PREC_LEARNED) {
+        if ((e = ws_get(ctx, farm::B_QBF, cnt, &r.qbf)) != cudaSuccess) return e;
+    }
+    if (prec == FARM_PREC_LEARNED) {
+        const size_t ccnt = (size_t)std::max<int64_t>(rows, 1) * ctx->c.mlp.P;
+        if ((e = ws_get(ctx, farm::B_QCOMP, ccnt, &r.qcomp)) != cudaSuccess) return e;
     }
     if (prec == FARM_PREC_FP8) {
         if ((e = ws_get(ctx, farm::B_QF8, cnt, &r.qf8)) != cudaSuccess) return e;
@@ -199,9 +217,6 @@ cudaError_t alloc_rows(farm_ctx *ctx, int32_t prec, int64_t rows, int32_t dim_pa
     if (prec == FARM_PREC_FP32) {
         if ((e = ws_get(ctx, farm::B_QHI, cnt, &r.qhi)) != cudaSuccess) return e;
         if ((e = ws_get(ctx, farm::B_QLO, cnt, &r.qlo)) != cudaSuccess) return e;
-    }
-    if (prec == FARM_PREC_BF16) {
-        if ((e = ws_get(ctx, farm::B_QBF, cnt, &r.qbf)) != cudaSuccess) return e;
     }
     return e;
 }
@@ -228,6 +243,12 @@ farm_status run_similarity(farm_ctx *ctx, int32_t prec, const RowOps &ops, int64
         LAUNCH(farm::launch_sim_tc_bf16(ops.qbf + off, s.desc_bf16, S, rows, s.n, s.dim_pad, ld_s, c.num_sms,
                                         c.d_err, c.stream));
         return FARM_OK;
+    case FARM_PREC_LEARNED:
+        if (!farm::sim_tc_available())
+            return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
+        LAUNCH(farm::launch_sim_tc_bf16(ops.qcomp + r0 * c.mlp.P, s.comp, S, rows, s.n, c.mlp.P, ld_s, c.num_sms,
+                                        c.d_err, c.stream));
+        return FARM_OK;
     case FARM_PREC_FP8:
         if (!farm::sim_tc_available())
             return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
@@ -239,14 +260,21 @@ farm_status run_similarity(farm_ctx *ctx, int32_t prec, const RowOps &ops, int64
     }
 }
 
-// Candidates kept per row by the BF16 stage before the FP32 rescore.
-int32_t bf16_keep_target(const farm_params &p, int32_t R, int64_t n)
+// Candidates kept per row by the reduced-precision stage before the FP32
+// rescore: `rescore` for BF16 target rows, twice that for FP8 (whose E4M3
+// operands carry 4 significant bits against BF16's 8), at most 512; landmark
+// rows keep a quarter of it, at least K_a.
+int32_t reduced_keep_target(const farm_params &p, int32_t prec, int32_t R, int64_t n)
 {
-    return (int32_t)std::min<int64_t>(std::max<int32_t>(p.rescore, R), n);
+    if (prec == FARM_PREC_LEARNED) return (int32_t)std::min<int64_t>(farm::kMaxTargetCands, n);
+    const int32_t c = std::min<int32_t>(prec == FARM_PREC_FP8 ? 2 * p.rescore : p.rescore, farm::kMaxTargetCands);
+    return (int32_t)std::min<int64_t>(std::max<int32_t>(c, R), n);
 }
-int32_t bf16_keep_landmark(const farm_params &p, int32_t klm, int64_t n)
+int32_t reduced_keep_landmark(const farm_params &p, int32_t prec, int32_t klm, int64_t n)
 {
-    return (int32_t)std::min<int64_t>(std::max<int32_t>(p.rescore / 4, klm), n);
+    const int32_t c = prec == FARM_PREC_LEARNED ? farm::kMaxTargetCands / 4
+                                                : (prec == FARM_PREC_FP8 ? 2 * p.rescore : p.rescore) / 4;
+    return (int32_t)std::min<int64_t>(std::max<int32_t>(std::min<int32_t>(c, farm::kMaxAnchorCands), klm), n);
 }
 
 }  // namespace
@@ -287,6 +315,9 @@ farm_status farm_destroy(farm_ctx *ctx)
     for (int b = 0; b < farm::B_COUNT; ++b) cudaFree(c.ws.ptr[b]);
     cudaFree(c.d_err);
     cudaFree(ctx->d_scenes);
+    cudaFree(c.mlp.params);
+    cudaFree(c.mlp.w1b);
+    cudaFree(c.mlp.w2b);
     if (c.h_err) cudaFreeHost(c.h_err);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
@@ -448,8 +479,10 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     if (!batch_handle) return fail(ctx, FARM_EINVAL, "batch_handle must be non-null");
     if (n_q < 0 || n_q > 0x7fffffff) return fail(ctx, FARM_EINVAL, "n_q out of range");
     if (precision != FARM_PREC_FP32 && precision != FARM_PREC_BF16 && precision != FARM_PREC_FP32_SIMT &&
-        precision != FARM_PREC_FP8)
+        precision != FARM_PREC_FP8 && precision != FARM_PREC_LEARNED)
         return fail(ctx, FARM_EINVAL, "unknown precision");
+    if (precision == FARM_PREC_LEARNED && !c.mlp.set)
+        return fail(ctx, FARM_ESTATE, "FARM_PREC_LEARNED needs prefilter weights (farm_mlp_set or farm_mlp_train)");
     if (n_q > 0 && (!scene_of_q || !tgt_emb || !tgt_cls || !c_off))
         return fail(ctx, FARM_EINVAL, "scene_of_q, tgt_emb, tgt_cls and c_off must be non-null");
     const bool dev = (flags & FARM_PTR_DEVICE) != 0;
@@ -469,6 +502,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             const Scene &s = c.scenes[sid];
             if (dim < 0) dim = s.dim;
             if (s.dim != dim) return fail(ctx, FARM_EINVAL, "all scenes of a batch must share dim");
+            if (precision == FARM_PREC_LEARNED && s.dim != c.mlp.D)
+                return fail(ctx, FARM_EINVAL, "the prefilter network's input length differs from the scene's dim");
             min_n = std::min(min_n, s.n);
             max_n = std::max(max_n, s.n);
         }
@@ -591,8 +626,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     RowOps ops;
     CK(alloc_rows(ctx, precision, rows_total, dim_pad, ops));
     int32_t *bsel_t = nullptr, *bsel_l = nullptr;
-    const int32_t cstride_t = bf16_keep_target(p, stride_t, max_n);
-    const int32_t cstride_l = bf16_keep_landmark(p, stride_l, max_n);
+    const int32_t cstride_t = reduced_keep_target(p, precision, stride_t, max_n);
+    const int32_t cstride_l = reduced_keep_landmark(p, precision, stride_l, max_n);
     if (reduced_precision(precision)) {
         CK(ws_get(ctx, farm::B_BSEL_T, (size_t)n_q * cstride_t, &bsel_t));
         CK(ws_get(ctx, farm::B_BSEL_L, (size_t)std::max<int64_t>(n_c, 1) * cstride_l, &bsel_l));
@@ -630,6 +665,10 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                                            ops.qbf, c.d_err, farm::kErrBadRow, c.stream));
     if (precision == FARM_PREC_FP8)
         LAUNCH(farm::launch_quantize_fp8_rows(ops.q32, rows_total, dim_pad, ops.qf8, ops.qscale, c.stream));
+    if (precision == FARM_PREC_LEARNED) {
+        for (const auto &g : groups) CK(farm::learned_refresh_scene(ctx, g.sid));
+        CK(farm::learned_embed_rows(ctx, ops.qbf, rows_total, ops.qcomp));
+    }
     mark_end(ctx, m0);
 
     // ---- stages 1-2: similarity and rank selection per scene group, in row chunks
@@ -653,8 +692,9 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                                                 g.q0 + r0, stride_t, lsel_idx, g.cp0 + r0 + ntr - g.nq, stride_l,
                                                 c.stream));
             } else {
-                // BF16 stage keeps C candidates per row; FP32 rescore keeps R (or K_a) of them
-                const int32_t Ct = bf16_keep_target(p, Rs, s.n), Cl = bf16_keep_landmark(p, klm, s.n);
+                // the reduced-precision stage keeps C candidates per row; the FP32 rescore keeps R (or K_a)
+                const int32_t Ct = reduced_keep_target(p, precision, Rs, s.n);
+                const int32_t Cl = reduced_keep_landmark(p, precision, klm, s.n);
                 const int64_t lrow0 = g.cp0 + r0 + ntr - g.nq;
                 LAUNCH(farm::launch_select_rows(d_sim, ld, s.n, r1 - r0, ntr, Ct, Cl, bsel_t, nullptr, g.q0 + r0,
                                                 cstride_t, bsel_l, lrow0, cstride_l, c.stream));

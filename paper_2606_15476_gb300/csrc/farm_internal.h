@@ -46,6 +46,8 @@ struct Scene {
     uint16_t *desc_bf16 = nullptr;  // [n, dim_pad] BF16 of desc32
     uint8_t *desc_fp8 = nullptr;    // [n, dim_pad] E4M3 of desc32 / desc_scale
     float *desc_scale = nullptr;    // [n] per-row FP8 scale
+    uint16_t *comp = nullptr;       // [n, P] BF16 learned embeddings f(d) (cache)
+    uint64_t comp_version = 0;      // Mlp::version the cache was computed with
     int32_t *cls = nullptr;     // [n]
     float *pos = nullptr;       // [3, n] centres (SoA)
     float *size = nullptr;      // [3, n]
@@ -80,12 +82,33 @@ enum Buf {
     B_BSEL_L,       // int32 [n_c, C_l] BF16-stage landmark candidates
     B_QF8,          // uint8 [rows, dim_pad] E4M3 rows
     B_QSCALE,       // float [rows] their scales
+    B_QCOMP,        // bf16 [rows, P] learned embeddings of the rows
+    B_MLP_H,        // float [chunk, H] pre-activations (inference)
+    B_MLP_A,        // float [chunk, H] activations
+    B_MLP_AB,       // bf16 [chunk, H]
+    B_MLP_Z,        // float [chunk, P]
+    B_MLP_E,        // float [chunk, P]
     B_COUNT
 };
 
 // Per-query metadata row (int32 x 8) consumed by the compose kernel.
 enum QMeta {
     QM_SCENE = 0, QM_CLS, QM_M, QM_C0, QM_PRED01, QM_PRED23, QM_R, QM_KLM
+};
+
+// The learned prefilter f(x) = normalize(W2 gelu(W1 x + b1) + b2).
+struct Mlp {
+    bool set = false;
+    int32_t D = 0, H = 0, P = 0, D_pad = 0;
+    float *params = nullptr;      // FP32 [W1 (H x D) | b1 (H) | W2 (P x H) | b2 (P)]
+    uint16_t *w1b = nullptr;      // BF16 [H, D_pad], zero padded
+    uint16_t *w2b = nullptr;      // BF16 [P, H]
+    uint64_t version = 0;         // bumped whenever the weights change
+    int64_t count() const { return (int64_t)H * D + H + (int64_t)P * H + P; }
+    float *W1() const { return params; }
+    float *b1() const { return params + (int64_t)H * D; }
+    float *W2() const { return b1() + H; }
+    float *b2() const { return W2() + (int64_t)P * H; }
 };
 
 struct Ctx {
@@ -112,7 +135,35 @@ struct Ctx {
     double stage_ms[FARM_N_STAGES] = {};
     int64_t launches = 0;
     int num_sms = 0;
+    Mlp mlp;
 };
+
+// ---- learned prefilter (k_mlp.cu) ----
+cudaError_t mlp_gemm(bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda, const float *B,
+                     int ldb, float beta, float *C, int ldc, cudaStream_t s);
+cudaError_t mlp_bias_gelu(float *h, const float *b, float *a, int64_t rows, int cols, cudaStream_t s);
+cudaError_t mlp_bias_normalize(float *z, const float *b, float *e, float *norm, int64_t rows, int cols,
+                               cudaStream_t s);
+cudaError_t mlp_pair_loss(const float *eq, const float *ed, const float *y, const float *w, float wsum, int64_t pairs,
+                          int cols, float *deq, float *ded, float *loss, cudaStream_t s);
+cudaError_t mlp_normalize_backward(const float *e, const float *norm, float *de, int64_t rows, int cols,
+                                   cudaStream_t s);
+cudaError_t mlp_gelu_backward(const float *h, float *da, int64_t count, cudaStream_t s);
+cudaError_t mlp_colsum(const float *x, int64_t rows, int cols, float *out, bool accumulate, cudaStream_t s);
+cudaError_t mlp_gather_rows(const float *src, int lds, const int32_t *idx, int64_t rows, int cols, float *dst,
+                            cudaStream_t s);
+cudaError_t mlp_adam(float *p, const float *g, float *m, float *v, int64_t count, float lr, int t, cudaStream_t s);
+cudaError_t mlp_to_bf16(const float *x, int64_t count, uint16_t *y, cudaStream_t s);
+
+// Grow-only workspace buffer of the context (synchronises before a regrow).
+cudaError_t ws_alloc(farm_ctx *ctx, Buf b, size_t bytes, void **out);
+
+// Learned embeddings f(x) of BF16 unit rows xb [rows, D_pad] into BF16
+// out [rows, P], on the tensor cores, in chunks (the prefilter's host code).
+cudaError_t learned_embed_rows(farm_ctx *ctx, const uint16_t *xb, int64_t rows, uint16_t *out);
+// Recompute a scene's cached learned embeddings if the weights changed.
+cudaError_t learned_refresh_scene(farm_ctx *ctx, int32_t scene_id);
+
 
 // The internal state behind a public farm_ctx handle.
 Ctx *ctx_of(farm_ctx *ctx);

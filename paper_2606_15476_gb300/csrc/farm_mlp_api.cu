@@ -1,0 +1,456 @@
+// farm_mlp_api.cu -- the learned descriptor prefilter: weights, training on
+// the GPU, loss/gradient evaluation, and tensor-core inference.
+//
+// f(x) = normalize(W2 gelu(W1 x + b1) + b2) maps a unit descriptor or query
+// row (length D) to a unit vector of length P (128 by default).  Trained on
+// (query row, object descriptor, oracle cosine y) pairs with the weighted
+// squared error of f(q).f(d) against y, it replaces the full-length similarity
+// stage by a P-length one whose best candidates are then re-scored exactly in
+// FP32 (the plain full-descriptor path stays the fallback and the judge of
+// its recall).  Training runs FP32 forward/backward kernels on the CUDA cores
+// with Adam; inference runs both layers as BF16 tensor-core products.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "farm_internal.h"
+
+using farm::Ctx;
+using farm::Mlp;
+
+namespace {
+
+farm_status fail(Ctx &c, farm_status st, const std::string &msg)
+{
+    c.err = msg;
+    return st;
+}
+
+#define MCK(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? FARM_ENOMEM : FARM_ECUDA,             \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+#define MLAUNCH(call)     \
+    do {                  \
+        c.launches += 1;  \
+        MCK(call);        \
+    } while (0)
+
+constexpr int64_t kEmbedChunk = 16384;   // rows per inference chunk
+
+// SplitMix64 (Steele, Lea, Flood 2014) for the per-epoch shuffle.
+uint64_t splitmix64(uint64_t &x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Device scratch for training and loss/gradient evaluation (one allocation).
+struct TrainBufs {
+    float *base = nullptr;
+    float *xq, *xd, *hq, *hd, *aq, *ad, *zq, *zd, *eq, *ed, *nq, *nd, *da, *grad, *m, *v, *loss, *y, *w;
+    int32_t *iq, *id;
+    size_t bytes = 0;
+};
+
+cudaError_t train_alloc(TrainBufs &t, const Mlp &M, int64_t B, int64_t loss_slots)
+{
+    const int64_t D = M.D, H = M.H, P = M.P, cnt = M.count();
+    const int64_t floats = 2 * B * D + 4 * B * H + 4 * B * P + 2 * B + B * H + 3 * cnt + loss_slots + 2 * B;
+    t.bytes = (size_t)floats * 4 + (size_t)2 * B * 4 + 1024;
+    cudaError_t e = cudaMalloc(&t.base, t.bytes);
+    if (e != cudaSuccess) return e;
+    float *p = t.base;
+    auto take = [&](int64_t n) { float *r = p; p += (n + 63) / 64 * 64; return r; };
+    t.xq = take(B * D); t.xd = take(B * D);
+    t.hq = take(B * H); t.hd = take(B * H); t.aq = take(B * H); t.ad = take(B * H);
+    t.zq = take(B * P); t.zd = take(B * P); t.eq = take(B * P); t.ed = take(B * P);
+    t.nq = take(B); t.nd = take(B); t.da = take(B * H);
+    t.grad = take(cnt); t.m = take(cnt); t.v = take(cnt);
+    t.loss = take(loss_slots); t.y = take(B); t.w = take(B);
+    t.iq = reinterpret_cast<int32_t *>(take(B));
+    t.id = reinterpret_cast<int32_t *>(take(B));
+    return cudaSuccess;
+}
+
+// Forward of b rows X [b, D] (lda D): h, a, z kept, e = f(X), norm.
+cudaError_t forward(const Mlp &M, const float *X, int64_t b, float *h, float *a, float *z, float *e, float *nrm,
+                    cudaStream_t s, int64_t &launches)
+{
+    cudaError_t r;
+    launches += 4;
+    if ((r = farm::mlp_gemm(false, false, (int)b, M.H, M.D, 1.f, X, M.D, M.W1(), M.D, 0.f, h, M.H, s))) return r;
+    if ((r = farm::mlp_bias_gelu(h, M.b1(), a, b, M.H, s))) return r;
+    if ((r = farm::mlp_gemm(false, false, (int)b, M.P, M.H, 1.f, a, M.H, M.W2(), M.H, 0.f, z, M.P, s))) return r;
+    return farm::mlp_bias_normalize(z, M.b2(), e, nrm, b, M.P, s);
+}
+
+// Backward of one tower given de (overwritten) into grad (beta 0: set, 1: add).
+cudaError_t backward(const Mlp &M, const float *X, int64_t b, float *h, const float *a, const float *e,
+                     const float *nrm, float *de, float *da, float *grad, float beta, cudaStream_t s,
+                     int64_t &launches)
+{
+    const int64_t D = M.D, H = M.H, P = M.P;
+    float *gW1 = grad, *gb1 = grad + H * D, *gW2 = gb1 + H, *gb2 = gW2 + P * H;
+    cudaError_t r;
+    launches += 8;
+    if ((r = farm::mlp_normalize_backward(e, nrm, de, b, (int)P, s))) return r;
+    if ((r = farm::mlp_gemm(true, true, (int)P, (int)H, (int)b, 1.f, de, (int)P, a, (int)H, beta, gW2, (int)H, s)))
+        return r;
+    if ((r = farm::mlp_colsum(de, b, (int)P, gb2, beta != 0.f, s))) return r;
+    if ((r = farm::mlp_gemm(false, true, (int)b, (int)H, (int)P, 1.f, de, (int)P, M.W2(), (int)H, 0.f, da, (int)H, s)))
+        return r;
+    if ((r = farm::mlp_gelu_backward(h, da, b * H, s))) return r;
+    if ((r = farm::mlp_gemm(true, true, (int)H, (int)D, (int)b, 1.f, da, (int)H, X, (int)D, beta, gW1, (int)D, s)))
+        return r;
+    return farm::mlp_colsum(da, b, (int)H, gb1, beta != 0.f, s);
+}
+
+cudaError_t refresh_bf16_weights(Ctx &c)
+{
+    Mlp &M = c.mlp;
+    // BF16 copies for the tensor-core inference: W1 padded to D_pad columns
+    std::vector<float> w1((size_t)M.H * M.D);
+    cudaError_t e = cudaMemcpyAsync(w1.data(), M.W1(), w1.size() * 4, cudaMemcpyDeviceToHost, c.stream);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+    std::vector<float> w1p((size_t)M.H * M.D_pad, 0.f);
+    for (int64_t i = 0; i < M.H; ++i) std::memcpy(&w1p[i * M.D_pad], &w1[i * M.D], (size_t)M.D * 4);
+    float *tmp = nullptr;
+    if ((e = cudaMalloc(&tmp, w1p.size() * 4)) != cudaSuccess) return e;
+    e = cudaMemcpyAsync(tmp, w1p.data(), w1p.size() * 4, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = farm::mlp_to_bf16(tmp, (int64_t)w1p.size(), M.w1b, c.stream);
+    if (e == cudaSuccess) e = farm::mlp_to_bf16(M.W2(), (int64_t)M.P * M.H, M.w2b, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    cudaFree(tmp);
+    c.launches += 2;
+    M.version += 1;
+    return e;
+}
+
+}  // namespace
+
+cudaError_t farm::learned_embed_rows(farm_ctx *ctx, const uint16_t *xb, int64_t rows, uint16_t *out)
+{
+    Ctx &c = *ctx_of(ctx);
+    const Mlp &M = c.mlp;
+    const int64_t chunk = std::min<int64_t>(rows, kEmbedChunk);
+    void *h, *a, *ab, *z, *e;
+    cudaError_t r;
+    if ((r = ws_alloc(ctx, B_MLP_H, (size_t)chunk * M.H * 4, &h))) return r;
+    if ((r = ws_alloc(ctx, B_MLP_A, (size_t)chunk * M.H * 4, &a))) return r;
+    if ((r = ws_alloc(ctx, B_MLP_AB, (size_t)chunk * M.H * 2, &ab))) return r;
+    if ((r = ws_alloc(ctx, B_MLP_Z, (size_t)chunk * M.P * 4, &z))) return r;
+    if ((r = ws_alloc(ctx, B_MLP_E, (size_t)chunk * M.P * 4, &e))) return r;
+    for (int64_t r0 = 0; r0 < rows; r0 += chunk) {
+        const int64_t b = std::min(chunk, rows - r0);
+        c.launches += 6;
+        if ((r = launch_sim_tc_bf16(xb + r0 * M.D_pad, M.w1b, (float *)h, b, M.H, M.D_pad, M.H, c.num_sms, c.d_err,
+                                    c.stream)))
+            return r;
+        if ((r = mlp_bias_gelu((float *)h, M.b1(), (float *)a, b, M.H, c.stream))) return r;
+        if ((r = mlp_to_bf16((float *)a, b * M.H, (uint16_t *)ab, c.stream))) return r;
+        if ((r = launch_sim_tc_bf16((uint16_t *)ab, M.w2b, (float *)z, b, M.P, M.H, M.P, c.num_sms, c.d_err,
+                                    c.stream)))
+            return r;
+        if ((r = mlp_bias_normalize((float *)z, M.b2(), (float *)e, nullptr, b, M.P, c.stream))) return r;
+        if ((r = mlp_to_bf16((float *)e, b * M.P, out + r0 * M.P, c.stream))) return r;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t farm::learned_refresh_scene(farm_ctx *ctx, int32_t scene_id)
+{
+    Ctx &c = *ctx_of(ctx);
+    Scene &s = c.scenes[scene_id];
+    if (s.comp && s.comp_version == c.mlp.version) return cudaSuccess;
+    cudaError_t r;
+    if (!s.comp) {
+        if ((r = cudaStreamSynchronize(c.stream))) return r;
+        if ((r = cudaMalloc(&s.comp, (size_t)s.n * c.mlp.P * 2))) return r;
+    }
+    if ((r = learned_embed_rows(ctx, s.desc_bf16, s.n, s.comp))) return r;
+    s.comp_version = c.mlp.version;
+    return cudaSuccess;
+}
+
+extern "C" {
+
+farm_status farm_mlp_set(farm_ctx *ctx, int32_t dim, int32_t hidden, int32_t out_dim, const float *W1,
+                         const float *b1, const float *W2, const float *b2)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = *farm::ctx_of(ctx);
+    if (dim < 1 || dim > 8192 || hidden < 64 || hidden > 4096 || hidden % 64 || out_dim < 64 || out_dim > 1024 ||
+        out_dim % 64)
+        return fail(c, FARM_EINVAL, "farm_mlp_set: need 1 <= dim <= 8192, hidden in [64, 4096] and out_dim in "
+                                    "[64, 1024], both multiples of 64");
+    if (!W1 || !b1 || !W2 || !b2) return fail(c, FARM_EINVAL, "farm_mlp_set: weights must be non-null");
+    MCK(cudaSetDevice(c.device));
+    Mlp &M = c.mlp;
+    Mlp nm;
+    nm.D = dim; nm.H = hidden; nm.P = out_dim;
+    nm.D_pad = (dim + farm::kDimAlign - 1) / farm::kDimAlign * farm::kDimAlign;
+    const int64_t cnt = nm.count();
+    std::vector<float> host((size_t)cnt);
+    std::memcpy(host.data(), W1, (size_t)nm.H * nm.D * 4);
+    std::memcpy(host.data() + (size_t)nm.H * nm.D, b1, (size_t)nm.H * 4);
+    std::memcpy(host.data() + (size_t)nm.H * nm.D + nm.H, W2, (size_t)nm.P * nm.H * 4);
+    std::memcpy(host.data() + (size_t)nm.H * nm.D + nm.H + (size_t)nm.P * nm.H, b2, (size_t)nm.P * 4);
+    for (float x : host)
+        if (!std::isfinite(x)) return fail(c, FARM_EINVAL, "farm_mlp_set: non-finite weight");
+    MCK(cudaStreamSynchronize(c.stream));
+    if (M.set && (M.D != nm.D || M.H != nm.H || M.P != nm.P)) {
+        cudaFree(M.params); cudaFree(M.w1b); cudaFree(M.w2b);
+        M.params = nullptr; M.w1b = nullptr; M.w2b = nullptr;
+        M.set = false;
+    }
+    if (!M.set) {
+        MCK(cudaMalloc(&M.params, (size_t)cnt * 4));
+        MCK(cudaMalloc(&M.w1b, (size_t)nm.H * nm.D_pad * 2));
+        MCK(cudaMalloc(&M.w2b, (size_t)nm.P * nm.H * 2));
+        M.D = nm.D; M.H = nm.H; M.P = nm.P; M.D_pad = nm.D_pad;
+        // shape change: every scene cache is stale
+        for (auto &s : c.scenes)
+            if (s.comp) { cudaFree(s.comp); s.comp = nullptr; }
+    }
+    MCK(cudaMemcpyAsync(M.params, host.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, c.stream));
+    M.set = true;
+    MCK(refresh_bf16_weights(c));
+    return FARM_OK;
+}
+
+farm_status farm_mlp_get(farm_ctx *ctx, float *W1, float *b1, float *W2, float *b2)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = *farm::ctx_of(ctx);
+    const Mlp &M = c.mlp;
+    if (!M.set) return fail(c, FARM_ESTATE, "farm_mlp_get: no weights set");
+    MCK(cudaSetDevice(c.device));
+    if (W1) MCK(cudaMemcpyAsync(W1, M.W1(), (size_t)M.H * M.D * 4, cudaMemcpyDeviceToHost, c.stream));
+    if (b1) MCK(cudaMemcpyAsync(b1, M.b1(), (size_t)M.H * 4, cudaMemcpyDeviceToHost, c.stream));
+    if (W2) MCK(cudaMemcpyAsync(W2, M.W2(), (size_t)M.P * M.H * 4, cudaMemcpyDeviceToHost, c.stream));
+    if (b2) MCK(cudaMemcpyAsync(b2, M.b2(), (size_t)M.P * 4, cudaMemcpyDeviceToHost, c.stream));
+    MCK(cudaStreamSynchronize(c.stream));
+    return FARM_OK;
+}
+
+farm_status farm_mlp_loss_grad(farm_ctx *ctx, int64_t n_pairs, const float *xq, const float *xd, const float *y,
+                               const float *w, float *loss, float *grad)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = *farm::ctx_of(ctx);
+    const Mlp &M = c.mlp;
+    if (!M.set) return fail(c, FARM_ESTATE, "farm_mlp_loss_grad: no weights set");
+    if (n_pairs < 1 || n_pairs > (1 << 20) || !xq || !xd || !y || !loss)
+        return fail(c, FARM_EINVAL, "farm_mlp_loss_grad: bad arguments");
+    MCK(cudaSetDevice(c.device));
+    double wsum = 0.0;
+    for (int64_t i = 0; i < n_pairs; ++i) wsum += w ? (double)w[i] : 1.0;
+    if (!(wsum > 0.0)) return fail(c, FARM_EINVAL, "farm_mlp_loss_grad: weights sum to zero");
+    TrainBufs t;
+    MCK(train_alloc(t, M, n_pairs, 1));
+    auto done = [&](farm_status st) { cudaFree(t.base); return st; };
+    cudaError_t e = cudaSuccess;
+    const size_t xb = (size_t)n_pairs * M.D * 4;
+    int64_t L = 0;
+    if (!e) e = cudaMemcpyAsync(t.xq, xq, xb, cudaMemcpyHostToDevice, c.stream);
+    if (!e) e = cudaMemcpyAsync(t.xd, xd, xb, cudaMemcpyHostToDevice, c.stream);
+    if (!e) e = cudaMemcpyAsync(t.y, y, (size_t)n_pairs * 4, cudaMemcpyHostToDevice, c.stream);
+    if (!e && w) e = cudaMemcpyAsync(t.w, w, (size_t)n_pairs * 4, cudaMemcpyHostToDevice, c.stream);
+    if (!e) e = cudaMemsetAsync(t.loss, 0, 4, c.stream);
+    if (!e) e = forward(M, t.xq, n_pairs, t.hq, t.aq, t.zq, t.eq, t.nq, c.stream, L);
+    if (!e) e = forward(M, t.xd, n_pairs, t.hd, t.ad, t.zd, t.ed, t.nd, c.stream, L);
+    // de of both towers into zq / zd (the pre-normalisation values are no longer needed)
+    if (!e) e = farm::mlp_pair_loss(t.eq, t.ed, t.y, w ? t.w : nullptr, (float)wsum, n_pairs, M.P, t.zq, t.zd,
+                                    t.loss, c.stream);
+    if (!e) e = backward(M, t.xq, n_pairs, t.hq, t.aq, t.eq, t.nq, t.zq, t.da, t.grad, 0.f, c.stream, L);
+    if (!e) e = backward(M, t.xd, n_pairs, t.hd, t.ad, t.ed, t.nd, t.zd, t.da, t.grad, 1.f, c.stream, L);
+    if (!e) e = cudaMemcpyAsync(loss, t.loss, 4, cudaMemcpyDeviceToHost, c.stream);
+    if (!e && grad) e = cudaMemcpyAsync(grad, t.grad, (size_t)M.count() * 4, cudaMemcpyDeviceToHost, c.stream);
+    if (!e) e = cudaStreamSynchronize(c.stream);
+    c.launches += L + 1;
+    if (e) return done(fail(c, FARM_ECUDA, std::string("farm_mlp_loss_grad: ") + cudaGetErrorString(e)));
+    return done(FARM_OK);
+}
+
+farm_status farm_mlp_train(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *rows, int64_t n_pairs,
+                           const int32_t *pair_row, const int32_t *pair_obj, const float *y, const float *w,
+                           int32_t epochs, int32_t batch, float lr, uint64_t seed, float *loss_out)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = *farm::ctx_of(ctx);
+    Mlp &M = c.mlp;
+    if (!M.set) return fail(c, FARM_ESTATE, "farm_mlp_train: set initial weights with farm_mlp_set first");
+    if (scene_id < 0 || scene_id >= (int32_t)c.scenes.size() || !c.scenes[scene_id].present)
+        return fail(c, FARM_EINVAL, "farm_mlp_train: unknown scene");
+    const farm::Scene &s = c.scenes[scene_id];
+    if (s.dim != M.D) return fail(c, FARM_EINVAL, "farm_mlp_train: scene dim differs from the network's");
+    if (n_rows < 1 || !rows || n_pairs < 1 || !pair_row || !pair_obj || !y || epochs < 1 || batch < 1 ||
+        batch > (1 << 16) || !(lr > 0.f))
+        return fail(c, FARM_EINVAL, "farm_mlp_train: bad arguments");
+    for (int64_t i = 0; i < n_pairs; ++i)
+        if (pair_row[i] < 0 || pair_row[i] >= n_rows || pair_obj[i] < 0 || pair_obj[i] >= s.n ||
+            !std::isfinite(y[i]) || (w && !(w[i] >= 0.f)))
+            return fail(c, FARM_EINVAL, "farm_mlp_train: pair " + std::to_string(i) + " out of range");
+    MCK(cudaSetDevice(c.device));
+    const int64_t B = std::min<int64_t>(batch, n_pairs);
+    const int64_t steps = (n_pairs + B - 1) / B;
+    TrainBufs t;
+    MCK(train_alloc(t, M, B, steps * (int64_t)epochs));
+    float *qn = nullptr;       // normalised training rows [n_rows, D]
+    float *raw = nullptr;
+    int32_t *d_pr = nullptr, *d_po = nullptr;
+    float *d_y = nullptr, *d_w = nullptr;
+    auto done = [&](farm_status st) {
+        cudaStreamSynchronize(c.stream);
+        cudaFree(t.base); cudaFree(qn); cudaFree(raw); cudaFree(d_pr); cudaFree(d_po); cudaFree(d_y); cudaFree(d_w);
+        return st;
+    };
+    cudaError_t e = cudaSuccess;
+    if (!e) e = cudaMalloc(&qn, (size_t)n_rows * M.D * 4);
+    if (!e) e = cudaMalloc(&raw, (size_t)n_rows * M.D * 4);
+    if (!e) e = cudaMalloc(&d_pr, (size_t)n_pairs * 4);
+    if (!e) e = cudaMalloc(&d_po, (size_t)n_pairs * 4);
+    if (!e) e = cudaMalloc(&d_y, (size_t)n_pairs * 4);
+    if (!e) e = cudaMalloc(&d_w, (size_t)n_pairs * 4);
+    if (!e) e = cudaMemcpyAsync(raw, rows, (size_t)n_rows * M.D * 4, cudaMemcpyHostToDevice, c.stream);
+    if (!e) e = farm::launch_normalize_rows(raw, nullptr, n_rows, M.D, M.D, qn, nullptr, nullptr, nullptr, c.d_err,
+                                            farm::kErrBadRow, c.stream);
+    if (!e) e = cudaMemsetAsync(t.m, 0, (size_t)M.count() * 4, c.stream);
+    if (!e) e = cudaMemsetAsync(t.v, 0, (size_t)M.count() * 4, c.stream);
+    if (!e) e = cudaMemsetAsync(t.loss, 0, (size_t)steps * epochs * 4, c.stream);
+    if (e) return done(fail(c, FARM_ECUDA, std::string("farm_mlp_train: ") + cudaGetErrorString(e)));
+    std::vector<int32_t> perm((size_t)n_pairs), pr((size_t)n_pairs), po((size_t)n_pairs);
+    std::vector<float> py((size_t)n_pairs), pw((size_t)n_pairs);
+    for (int64_t i = 0; i < n_pairs; ++i) perm[i] = (int32_t)i;
+    uint64_t st = seed;
+    int64_t L = 0;
+    int t_adam = 0;
+    for (int32_t ep = 0; ep < epochs && !e; ++ep) {
+        for (int64_t i = n_pairs - 1; i > 0; --i) {
+            const int64_t j = (int64_t)(splitmix64(st) % (uint64_t)(i + 1));
+            std::swap(perm[i], perm[j]);
+        }
+        for (int64_t i = 0; i < n_pairs; ++i) {
+            pr[i] = pair_row[perm[i]];
+            po[i] = pair_obj[perm[i]];
+            py[i] = y[perm[i]];
+            pw[i] = w ? w[perm[i]] : 1.f;
+        }
+        // the previous epoch's kernels may still read the device copies
+        e = cudaStreamSynchronize(c.stream);
+        if (!e) e = cudaMemcpyAsync(d_pr, pr.data(), (size_t)n_pairs * 4, cudaMemcpyHostToDevice, c.stream);
+        if (!e) e = cudaMemcpyAsync(d_po, po.data(), (size_t)n_pairs * 4, cudaMemcpyHostToDevice, c.stream);
+        if (!e) e = cudaMemcpyAsync(d_y, py.data(), (size_t)n_pairs * 4, cudaMemcpyHostToDevice, c.stream);
+        if (!e) e = cudaMemcpyAsync(d_w, pw.data(), (size_t)n_pairs * 4, cudaMemcpyHostToDevice, c.stream);
+        for (int64_t sidx = 0; sidx < steps && !e; ++sidx) {
+            const int64_t off = sidx * B;
+            const int64_t b = std::min(B, n_pairs - off);
+            double wsum = 0.0;
+            for (int64_t i = 0; i < b; ++i) wsum += pw[off + i];
+            if (!(wsum > 0.0)) continue;
+            float *lslot = t.loss + (int64_t)ep * steps + sidx;
+            L += 3;
+            e = farm::mlp_gather_rows(qn, M.D, d_pr + off, b, M.D, t.xq, c.stream);
+            if (!e) e = farm::mlp_gather_rows(s.desc32, s.dim_pad, d_po + off, b, M.D, t.xd, c.stream);
+            if (!e) e = forward(M, t.xq, b, t.hq, t.aq, t.zq, t.eq, t.nq, c.stream, L);
+            if (!e) e = forward(M, t.xd, b, t.hd, t.ad, t.zd, t.ed, t.nd, c.stream, L);
+            if (!e) e = farm::mlp_pair_loss(t.eq, t.ed, d_y + off, d_w + off, (float)wsum, b, M.P, t.zq, t.zd, lslot,
+                                            c.stream);
+            if (!e) e = backward(M, t.xq, b, t.hq, t.aq, t.eq, t.nq, t.zq, t.da, t.grad, 0.f, c.stream, L);
+            if (!e) e = backward(M, t.xd, b, t.hd, t.ad, t.ed, t.nd, t.zd, t.da, t.grad, 1.f, c.stream, L);
+            if (!e) e = farm::mlp_adam(M.params, t.grad, t.m, t.v, M.count(), lr, ++t_adam, c.stream);
+        }
+    }
+    c.launches += L;
+    if (!e && loss_out) {
+        std::vector<float> ls((size_t)steps * epochs);
+        e = cudaMemcpyAsync(ls.data(), t.loss, ls.size() * 4, cudaMemcpyDeviceToHost, c.stream);
+        if (!e) e = cudaStreamSynchronize(c.stream);
+        for (int32_t ep = 0; ep < epochs && !e; ++ep) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < steps; ++i) acc += ls[(size_t)ep * steps + i];
+            loss_out[ep] = (float)(acc / (double)steps);
+        }
+    }
+    if (!e) e = refresh_bf16_weights(c);
+    if (e) return done(fail(c, FARM_ECUDA, std::string("farm_mlp_train: ") + cudaGetErrorString(e)));
+    return done(FARM_OK);
+}
+
+farm_status farm_mlp_embed(farm_ctx *ctx, int64_t n_rows, const float *x, int32_t precision, float *out)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = *farm::ctx_of(ctx);
+    const Mlp &M = c.mlp;
+    if (!M.set) return fail(c, FARM_ESTATE, "farm_mlp_embed: no weights set");
+    if (n_rows < 0 || (n_rows > 0 && (!x || !out))) return fail(c, FARM_EINVAL, "farm_mlp_embed: bad arguments");
+    if (precision != FARM_PREC_FP32_SIMT && precision != FARM_PREC_BF16)
+        return fail(c, FARM_EINVAL, "farm_mlp_embed: precision must be FARM_PREC_FP32_SIMT or FARM_PREC_BF16");
+    if (n_rows == 0) return FARM_OK;
+    MCK(cudaSetDevice(c.device));
+    float *raw = nullptr, *xn = nullptr, *h = nullptr, *a = nullptr, *z = nullptr, *e32 = nullptr;
+    uint16_t *xb = nullptr, *eb = nullptr;
+    auto done = [&](farm_status st) {
+        cudaStreamSynchronize(c.stream);
+        cudaFree(raw); cudaFree(xn); cudaFree(h); cudaFree(a); cudaFree(z); cudaFree(e32); cudaFree(xb); cudaFree(eb);
+        return st;
+    };
+    cudaError_t e = cudaMalloc(&raw, (size_t)n_rows * M.D * 4);
+    if (!e) e = cudaMemcpyAsync(raw, x, (size_t)n_rows * M.D * 4, cudaMemcpyHostToDevice, c.stream);
+    if (precision == FARM_PREC_FP32_SIMT) {
+        if (!e) e = cudaMalloc(&xn, (size_t)n_rows * M.D * 4);
+        if (!e) e = cudaMalloc(&h, (size_t)n_rows * M.H * 4);
+        if (!e) e = cudaMalloc(&a, (size_t)n_rows * M.H * 4);
+        if (!e) e = cudaMalloc(&z, (size_t)n_rows * M.P * 4);
+        if (!e) e = cudaMalloc(&e32, (size_t)n_rows * M.P * 4);
+        if (!e) e = farm::launch_normalize_rows(raw, nullptr, n_rows, M.D, M.D, xn, nullptr, nullptr, nullptr, c.d_err,
+                                                farm::kErrBadRow, c.stream);
+        int64_t L = 1;
+        if (!e) e = forward(M, xn, n_rows, h, a, z, e32, nullptr, c.stream, L);
+        c.launches += L;
+        if (!e) e = cudaMemcpyAsync(out, e32, (size_t)n_rows * M.P * 4, cudaMemcpyDeviceToHost, c.stream);
+    } else {
+        if (!e) e = cudaMalloc(&xb, (size_t)n_rows * M.D_pad * 2);
+        if (!e) e = cudaMalloc(&eb, (size_t)n_rows * M.P * 2);
+        if (!e) e = cudaMalloc(&e32, (size_t)n_rows * M.P * 4);
+        if (!e) e = farm::launch_normalize_rows(raw, nullptr, n_rows, M.D, M.D_pad, nullptr, nullptr, nullptr, xb,
+                                                c.d_err, farm::kErrBadRow, c.stream);
+        c.launches += 1;
+        if (!e) e = farm::learned_embed_rows(ctx, xb, n_rows, eb);
+        // widen the BF16 embeddings for the caller
+        std::vector<uint16_t> hb;
+        if (!e) {
+            hb.resize((size_t)n_rows * M.P);
+            e = cudaMemcpyAsync(hb.data(), eb, hb.size() * 2, cudaMemcpyDeviceToHost, c.stream);
+        }
+        if (!e) e = cudaStreamSynchronize(c.stream);
+        if (!e)
+            for (size_t i = 0; i < hb.size(); ++i) {
+                const uint32_t u = (uint32_t)hb[i] << 16;
+                std::memcpy(out + i, &u, 4);
+            }
+    }
+    if (!e) e = cudaStreamSynchronize(c.stream);
+    if (e) return done(fail(c, FARM_ECUDA, std::string("farm_mlp_embed: ") + cudaGetErrorString(e)));
+    farm_status st = FARM_OK;
+    if (c.h_err) {
+        cudaMemcpy(c.h_err, c.d_err, 4, cudaMemcpyDeviceToHost);
+        if (*c.h_err) {
+            cudaMemset(c.d_err, 0, 4);
+            st = fail(c, FARM_EINVAL, "farm_mlp_embed: a row has zero or non-finite norm");
+        }
+    }
+    return done(st);
+}
+
+}  // extern "C"

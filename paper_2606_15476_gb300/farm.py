@@ -18,6 +18,7 @@ PREC_FP32 = 0
 PREC_BF16 = 1
 PREC_FP8 = 2
 PREC_FP32_SIMT = 3
+PREC_LEARNED = 4
 PTR_DEVICE = 1
 N_STAGES = 4
 STATUS = {0: "FARM_OK", 1: "FARM_EINVAL", 2: "FARM_ENOMEM", 3: "FARM_ECUDA", 4: "FARM_ESTATE",
@@ -54,6 +55,11 @@ def _load():
         "farm_similarity": (C.c_int, [P, I32, I64, P, I32, P, U32]),
         "farm_candidates": (C.c_int, [P, U64, P, P, P, P]),
         "farm_rank_rows_noalloc": (C.c_int, [P, I32, I64, P, I32, I32, P, P]),
+        "farm_mlp_set": (C.c_int, [P, I32, I32, I32, P, P, P, P]),
+        "farm_mlp_get": (C.c_int, [P, P, P, P, P]),
+        "farm_mlp_loss_grad": (C.c_int, [P, I64, P, P, P, P, P, P]),
+        "farm_mlp_train": (C.c_int, [P, I32, I64, P, I64, P, P, P, P, I32, I32, C.c_float, U64, P]),
+        "farm_mlp_embed": (C.c_int, [P, I64, P, I32, P]),
         "farm_set_profiling": (C.c_int, [P, I32]),
         "farm_stage_times": (C.c_int, [P, P, P, I32]),
         "farm_last_error": (C.c_char_p, [P]),
@@ -72,8 +78,9 @@ _lib = _load()
 def exported_symbols():
     return ["farm_default_params", "farm_create", "farm_destroy", "farm_memory_upload",
             "farm_query_batch", "farm_topk", "farm_sync", "farm_similarity", "farm_candidates",
-            "farm_rank_rows_noalloc", "farm_set_profiling", "farm_stage_times", "farm_last_error",
-            "farm_version"]
+            "farm_rank_rows_noalloc", "farm_mlp_set", "farm_mlp_get", "farm_mlp_loss_grad",
+            "farm_mlp_train", "farm_mlp_embed", "farm_set_profiling", "farm_stage_times",
+            "farm_last_error", "farm_version"]
 
 
 def _is_cuda_tensor(x) -> bool:
@@ -239,6 +246,68 @@ def farm_rank_rows_noalloc(ctx, scene_id: int, emb, r: int, precision: int, out_
                                          C.c_void_p(out_idx.data_ptr()),
                                          None if out_cos is None else C.c_void_p(out_cos.data_ptr())))
     return out_idx, out_cos
+
+
+def _host(x, dtype):
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def farm_mlp_set(ctx, W1, b1, W2, b2) -> None:
+    W1, p1 = _host(W1, np.float32)
+    b1, p2 = _host(b1, np.float32)
+    W2, p3 = _host(W2, np.float32)
+    b2, p4 = _host(b2, np.float32)
+    hidden, dim = W1.shape
+    out_dim = W2.shape[0]
+    _ck(ctx, _lib.farm_mlp_set(ctx, int(dim), int(hidden), int(out_dim), p1, p2, p3, p4))
+
+
+def farm_mlp_get(ctx, dim: int, hidden: int, out_dim: int):
+    W1 = np.zeros((hidden, dim), np.float32)
+    b1 = np.zeros(hidden, np.float32)
+    W2 = np.zeros((out_dim, hidden), np.float32)
+    b2 = np.zeros(out_dim, np.float32)
+    _ck(ctx, _lib.farm_mlp_get(ctx, W1.ctypes.data_as(C.c_void_p), b1.ctypes.data_as(C.c_void_p),
+                               W2.ctypes.data_as(C.c_void_p), b2.ctypes.data_as(C.c_void_p)))
+    return W1, b1, W2, b2
+
+
+def farm_mlp_loss_grad(ctx, xq, xd, y, w, n_params: int):
+    xq, pq = _host(xq, np.float32)
+    xd, pd = _host(xd, np.float32)
+    y, py = _host(y, np.float32)
+    wp = None
+    if w is not None:
+        w, wp = _host(w, np.float32)
+    loss = np.zeros(1, np.float32)
+    grad = np.zeros(n_params, np.float32)
+    _ck(ctx, _lib.farm_mlp_loss_grad(ctx, int(xq.shape[0]), pq, pd, py, wp, loss.ctypes.data_as(C.c_void_p),
+                                     grad.ctypes.data_as(C.c_void_p)))
+    return float(loss[0]), grad
+
+
+def farm_mlp_train(ctx, scene_id: int, rows, pair_row, pair_obj, y, w=None, epochs: int = 1,
+                   batch: int = 4096, lr: float = 1e-3, seed: int = 0):
+    rows, pr = _host(rows, np.float32)
+    a, pa = _host(pair_row, np.int32)
+    o, po = _host(pair_obj, np.int32)
+    yy, py = _host(y, np.float32)
+    wp = None
+    if w is not None:
+        ww, wp = _host(w, np.float32)
+    losses = np.zeros(epochs, np.float32)
+    _ck(ctx, _lib.farm_mlp_train(ctx, int(scene_id), int(rows.shape[0]), pr, int(a.shape[0]), pa, po, py, wp,
+                                 int(epochs), int(batch), C.c_float(lr), C.c_uint64(seed),
+                                 losses.ctypes.data_as(C.c_void_p)))
+    return losses
+
+
+def farm_mlp_embed(ctx, x, out_dim: int, precision: int = PREC_FP32_SIMT):
+    x, px = _host(x, np.float32)
+    out = np.zeros((x.shape[0], out_dim), np.float32)
+    _ck(ctx, _lib.farm_mlp_embed(ctx, int(x.shape[0]), px, int(precision), out.ctypes.data_as(C.c_void_p)))
+    return out
 
 
 def farm_set_profiling(ctx, on: bool) -> None:
