@@ -54,12 +54,6 @@ struct Scene {
     float *views = nullptr;     // [n, n_views, kViewStride]
 };
 
-struct Workspace {
-    // grow-only device buffers (bytes recorded alongside)
-    void *ptr[24] = {};
-    size_t bytes[24] = {};
-};
-
 enum Buf {
     B_RAW = 0,      // raw embedding rows as given [n_q + n_c, dim]
     B_Q32,          // normalised rows [rows, dim_pad]
@@ -89,6 +83,12 @@ enum Buf {
     B_MLP_Z,        // float [chunk, P]
     B_MLP_E,        // float [chunk, P]
     B_COUNT
+};
+
+struct Workspace {
+    // grow-only device buffers, one per Buf (bytes recorded alongside)
+    void *ptr[B_COUNT] = {};
+    size_t bytes[B_COUNT] = {};
 };
 
 // Per-query metadata row (int32 x 8) consumed by the compose kernel.
@@ -131,7 +131,6 @@ struct Ctx {
     int32_t batch_min_n = 0;      // smallest scene size in the batch
     // profiling
     bool profiling = false;
-    cudaEvent_t ev[8] = {};
     double stage_ms[FARM_N_STAGES] = {};
     int64_t launches = 0;
     int num_sms = 0;

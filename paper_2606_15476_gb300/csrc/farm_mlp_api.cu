@@ -57,27 +57,25 @@ uint64_t splitmix64(uint64_t &x)
 struct TrainBufs {
     float *base = nullptr;
     float *xq, *xd, *hq, *hd, *aq, *ad, *zq, *zd, *eq, *ed, *nq, *nd, *da, *grad, *m, *v, *loss, *y, *w;
-    int32_t *iq, *id;
-    size_t bytes = 0;
 };
 
 cudaError_t train_alloc(TrainBufs &t, const Mlp &M, int64_t B, int64_t loss_slots)
 {
     const int64_t D = M.D, H = M.H, P = M.P, cnt = M.count();
-    const int64_t floats = 2 * B * D + 4 * B * H + 4 * B * P + 2 * B + B * H + 3 * cnt + loss_slots + 2 * B;
-    t.bytes = (size_t)floats * 4 + (size_t)2 * B * 4 + 1024;
-    cudaError_t e = cudaMalloc(&t.base, t.bytes);
+    const int64_t sizes[] = {B * D, B * D, B * H, B * H, B * H, B * H, B * P, B * P, B * P, B * P,
+                             B,     B,     B * H, cnt,   cnt,   cnt,   loss_slots, B, B};
+    float **dst[] = {&t.xq, &t.xd, &t.hq, &t.hd, &t.aq, &t.ad, &t.zq, &t.zd, &t.eq, &t.ed,
+                     &t.nq, &t.nd, &t.da, &t.grad, &t.m, &t.v, &t.loss, &t.y, &t.w};
+    auto rounded = [](int64_t n) { return (n + 63) / 64 * 64; };   // 256-byte aligned sub-arrays
+    int64_t total = 0;
+    for (int64_t n : sizes) total += rounded(n);
+    cudaError_t e = cudaMalloc(&t.base, (size_t)total * sizeof(float));
     if (e != cudaSuccess) return e;
     float *p = t.base;
-    auto take = [&](int64_t n) { float *r = p; p += (n + 63) / 64 * 64; return r; };
-    t.xq = take(B * D); t.xd = take(B * D);
-    t.hq = take(B * H); t.hd = take(B * H); t.aq = take(B * H); t.ad = take(B * H);
-    t.zq = take(B * P); t.zd = take(B * P); t.eq = take(B * P); t.ed = take(B * P);
-    t.nq = take(B); t.nd = take(B); t.da = take(B * H);
-    t.grad = take(cnt); t.m = take(cnt); t.v = take(cnt);
-    t.loss = take(loss_slots); t.y = take(B); t.w = take(B);
-    t.iq = reinterpret_cast<int32_t *>(take(B));
-    t.id = reinterpret_cast<int32_t *>(take(B));
+    for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
+        *dst[i] = p;
+        p += rounded(sizes[i]);
+    }
     return cudaSuccess;
 }
 
