@@ -20,7 +20,8 @@
 // truncation errors are about 2^-11 smaller; the epilogue adds the two in
 // IEEE FP32.  Measured against FP64 this keeps cosines within a few 1e-6.
 //
-// Kernel organisation (one 128 x 256 tile of S per CTA, 192 threads):
+// Kernel organisation (persistent: one CTA of 192 threads per SM walks the
+// 128 x 256 tiles of S):
 //   warp 0      TMA producer: for each K slice (16 FP32 values, 64-byte swizzle,
 //               four tiles q_hi, q_lo, d_hi, d_lo; or 64 BF16 values, 128-byte
 //               swizzle, two tiles q, d) fills one pipeline stage, signalling a
@@ -31,11 +32,14 @@
 //               K=8), or 4 K-steps of kind::f16 with BF16 operands (K=16), and
 //               tcgen05.commit to the stage's "empty" mbarrier, finally to the
 //               "accumulator ready" mbarrier;
-//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns of both
-//               accumulators at a time, add, store the rows of S (bounds-checked).
+//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns at a time (TF32
+//               mode: of both accumulators, added), store the rows of S
+//               (bounds-checked), then release the accumulator.
 // Four pipeline stages of 48 KB each.  Every mbarrier wait is bounded: on
 // expiry the kernel raises the error flag, stops issuing work, waits (bounded)
 // for the copies it issued, frees its TMEM and returns.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -214,6 +218,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Tile id -> (first row, first column) under the grouped raster: GROUP_M row
+// tiles share each column tile so a descriptor tile is read from HBM about
+// once per group.
+__device__ __forceinline__ void tile_origin(int tile, int m_tiles, int n_tiles, int &m0, int &n0)
+{
+    const int per_group = GROUP_M * n_tiles;
+    const int g = tile / per_group;
+    const int first_m = g * GROUP_M;
+    const int gm = min(GROUP_M, m_tiles - first_m);
+    const int in_g = tile - g * per_group;
+    m0 = (first_m + in_g % gm) * BM;
+    n0 = (in_g / gm) * BN;
+}
+
+// Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// The shared-memory pipeline runs on across tiles.  Two-operand modes (BF16,
+// FP8) keep two accumulators in the 512 TMEM columns, so the epilogue of one
+// tile overlaps the MMAs of the next (acc_full / acc_empty mbarriers); the
+// TF32 mode needs both halves of TMEM for its main and correction
+// accumulators and drains before the next tile's MMAs start, while the
+// producer already prefetches that tile's first stages.
 // Maps (TF32 mode): q_hi, q_lo, d_hi, d_lo.  (BF16, FP8 modes): q, d, and the
 // last two are unused.  scale_q / scale_d: per-row scales (FP8 mode only).
 template <int MODE>
@@ -226,39 +256,35 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
 {
     using M = Mode<MODE>;
     constexpr bool TWO_OPERAND_TILES = MODE != kTf32x3;
+    constexpr int NACC = TWO_OPERAND_TILES ? 2 : 1;
+    constexpr uint32_t TMEM_ALLOC = 512;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *acc_ready = empty + STAGES;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_ready + 1);
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    // grouped raster over (m tile, n tile)
-    const int tile = blockIdx.x;
-    const int per_group = GROUP_M * n_tiles;
-    const int g = tile / per_group;
-    const int first_m = g * GROUP_M;
-    const int gm = min(GROUP_M, m_tiles - first_m);
-    const int in_g = tile - g * per_group;
-    const int mt = first_m + in_g % gm;
-    const int nt = in_g / gm;
-    const int m0 = mt * BM, n0 = nt * BN;
+    const int total = m_tiles * n_tiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(acc_ready, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);     // one arrival per epilogue warp
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(M::TMEM_COLS));
+                     "r"(TMEM_ALLOC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -268,90 +294,109 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < k_slices; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-                if (!mbar_wait(&empty[s], ph ^ 1u) || *abort_flag) {
-                    *abort_flag = 1;
-                    break;
+            uint32_t it = 0;
+            for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x) {
+                int m0, n0;
+                tile_origin(tile, m_tiles, n_tiles, m0, n0);
+                for (int kb = 0; kb < k_slices; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u) || *abort_flag) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    const int kx = kb * M::BK;
+                    if (TWO_OPERAND_TILES) {
+                        tma_load_2d(st, &map_q0, &full[s], kx, m0);
+                        tma_load_2d(st + M::A_BYTES, &map_d0, &full[s], kx, n0);
+                    } else {
+                        tma_load_2d(st, &map_q0, &full[s], kx, m0);
+                        tma_load_2d(st + M::A_BYTES, &map_q1, &full[s], kx, m0);
+                        tma_load_2d(st + 2 * M::A_BYTES, &map_d0, &full[s], kx, n0);
+                        tma_load_2d(st + 2 * M::A_BYTES + M::B_BYTES, &map_d1, &full[s], kx, n0);
+                    }
                 }
-                uint8_t *st = smem + s * STAGE_BYTES;
-                mbar_expect_tx(&full[s], STAGE_BYTES);
-                const int kx = kb * M::BK;
-                if (TWO_OPERAND_TILES) {
-                    tma_load_2d(st, &map_q0, &full[s], kx, m0);
-                    tma_load_2d(st + M::A_BYTES, &map_d0, &full[s], kx, n0);
-                } else {
-                    tma_load_2d(st, &map_q0, &full[s], kx, m0);
-                    tma_load_2d(st + M::A_BYTES, &map_q1, &full[s], kx, m0);
-                    tma_load_2d(st + 2 * M::A_BYTES, &map_d0, &full[s], kx, n0);
-                    tma_load_2d(st + 2 * M::A_BYTES + M::B_BYTES, &map_d1, &full[s], kx, n0);
-                }
-                issued = kb + 1;
             }
             if (*abort_flag) {
                 // let the copies already issued land before shared memory is released
-                for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-                    mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u);
+                for (uint32_t j = (it > (uint32_t)STAGES ? it - STAGES : 0u); j < it; ++j)
+                    mbar_wait(&full[j % STAGES], (j / STAGES) & 1u);
                 atomicOr(err, kErrTimeout);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            bool ok = true;
-            for (int kb = 0; kb < k_slices; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-                if (!mbar_wait(&full[s], ph) || *abort_flag) {
+            uint32_t it = 0, tc = 0;
+            for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x, ++tc) {
+                const uint32_t buf = tc % NACC, use = tc / NACC;
+                if (!mbar_wait(&acc_empty[buf], (use & 1u) ^ 1u) || *abort_flag) {
                     *abort_flag = 1;
-                    ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-                if (TWO_OPERAND_TILES) {
-                    const uint32_t a = st, b = st + M::A_BYTES;
-#pragma unroll
-                    for (int kk = 0; kk < M::KSTEPS; ++kk) {
-                        const uint32_t off = kk * 32;     // 32 bytes along K: 16 BF16 or 32 FP8 values
-                        if (MODE == kBf16)
-                            mma_bf16(tmem, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
-                        else
-                            mma_e4m3(tmem, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
+                const uint32_t acc = tmem + (TWO_OPERAND_TILES ? buf * 256u : 0u);
+                for (int kb = 0; kb < k_slices; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1u;
+                    if (!mbar_wait(&full[s], ph) || *abort_flag) {
+                        *abort_flag = 1;
+                        break;
                     }
-                } else {
-                    const uint32_t a_hi = st, a_lo = st + M::A_BYTES;
-                    const uint32_t b_hi = st + 2 * M::A_BYTES, b_lo = st + 2 * M::A_BYTES + M::B_BYTES;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+                    if (TWO_OPERAND_TILES) {
+                        const uint32_t a = st, b = st + M::A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < M::KSTEPS; ++kk) {
-                        const uint32_t off = kk * 32;     // 8 TF32 values = 32 bytes along K
-                        const uint32_t acc = (kb | kk) != 0;
-                        mma_tf32(tmem, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), acc);
-                        mma_tf32(tmem + ACC_CORR, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_lo + off), acc);
-                        mma_tf32(tmem + ACC_CORR, smem_desc<MODE>(a_lo + off), smem_desc<MODE>(b_hi + off), 1u);
+                        for (int kk = 0; kk < M::KSTEPS; ++kk) {
+                            const uint32_t off = kk * 32;     // 32 bytes along K: 16 BF16 or 32 FP8 values
+                            if (MODE == kBf16)
+                                mma_bf16(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
+                            else
+                                mma_e4m3(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
+                        }
+                    } else {
+                        const uint32_t a_hi = st, a_lo = st + M::A_BYTES;
+                        const uint32_t b_hi = st + 2 * M::A_BYTES, b_lo = st + 2 * M::A_BYTES + M::B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < M::KSTEPS; ++kk) {
+                            const uint32_t off = kk * 32;     // 8 TF32 values = 32 bytes along K
+                            const uint32_t first = (kb | kk) != 0;
+                            mma_tf32(acc, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), first);
+                            mma_tf32(acc + ACC_CORR, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_lo + off), first);
+                            mma_tf32(acc + ACC_CORR, smem_desc<MODE>(a_lo + off), smem_desc<MODE>(b_hi + off), 1u);
+                        }
                     }
+                    mma_commit(&empty[s]);
                 }
-                mma_commit(&empty[s]);
+                if (*abort_flag) break;
+                mma_commit(&acc_full[buf]);
             }
-            if (ok) mma_commit(acc_ready);
-            else atomicOr(err, kErrTimeout);
+            if (*abort_flag) atomicOr(err, kErrTimeout);
         }
     } else {
         // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
         const int quad = warp & 3;
-        const bool ready = mbar_wait(acc_ready, 0u) && !*abort_flag;
-        if (!ready) *abort_flag = 1;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (ready) {
-            const int r_local = quad * 32 + lane;
-            const int64_t r = (int64_t)m0 + r_local;
+        uint32_t tc = 0;
+        for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++tc) {
+            const uint32_t buf = tc % NACC, use = tc / NACC;
+            if (!mbar_wait(&acc_full[buf], use & 1u) || *abort_flag) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            int m0, n0;
+            tile_origin(tile, m_tiles, n_tiles, m0, n0);
+            const int64_t r = (int64_t)m0 + quad * 32 + lane;
             float *srow = S + r * ld_s;
             const bool vec = (ld_s % 4) == 0;
+            const float sr = (MODE == kFp8 && r < rows) ? scale_q[r] : 1.f;
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
-                const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32);
+                const uint32_t lane_addr = tmem + (TWO_OPERAND_TILES ? buf * 256u : 0u) +
+                                           ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32);
                 tmem_ld32(lane_addr, v);
                 if (MODE == kTf32x3) {
                     float w[32];
@@ -361,7 +406,6 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 }
                 const int64_t col0 = (int64_t)n0 + c * 32;
                 if (MODE == kFp8 && r < rows) {
-                    const float sr = scale_q[r];
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] *= sr * (col0 + i < n ? __ldg(scale_d + col0 + i) : 0.f);
                 }
@@ -377,13 +421,16 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(M::TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_ALLOC));
     }
 }
 
@@ -424,7 +471,7 @@ bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, in
 template <int MODE>
 cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void *d1, float *S, int64_t rows,
                       int64_t n, int32_t dim_pad, int64_t ld_s, const float *scale_q, const float *scale_d,
-                      int32_t *err, cudaStream_t s)
+                      int num_sms, int32_t *err, cudaStream_t s)
 {
     using M = Mode<MODE>;
     constexpr bool TWO = MODE != kTf32x3;
@@ -450,7 +497,8 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     const int n_tiles = (int)((n + BN - 1) / BN);
     const int64_t tiles = (int64_t)m_tiles * n_tiles;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    sim_tc_kernel<MODE><<<(unsigned)tiles, THREADS, SMEM_BYTES, s>>>(mq0, mq1, md0, md1, S, rows, n,
+    const int grid = (int)std::min<int64_t>(tiles, std::max(num_sms, 1));
+    sim_tc_kernel<MODE><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(mq0, mq1, md0, md1, S, rows, n,
                                                                        dim_pad / M::BK, ld_s, m_tiles, n_tiles,
                                                                        scale_q, scale_d, err);
     return cudaGetLastError();
@@ -464,23 +512,20 @@ cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const flo
                                  int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err,
                                  cudaStream_t s)
 {
-    (void)num_sms;
-    return launch_tc<kTf32x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, err, s);
+    return launch_tc<kTf32x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, num_sms, err, s);
 }
 
 cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
                                int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s)
 {
-    (void)num_sms;
-    return launch_tc<kBf16>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, nullptr, nullptr, err, s);
+    return launch_tc<kBf16>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, nullptr, nullptr, num_sms, err, s);
 }
 
 cudaError_t launch_sim_tc_fp8(const uint8_t *q, const float *scale_q, const uint8_t *d, const float *scale_d,
                               float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, int num_sms,
                               int32_t *err, cudaStream_t s)
 {
-    (void)num_sms;
-    return launch_tc<kFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, err, s);
+    return launch_tc<kFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, num_sms, err, s);
 }
 
 }  // namespace farm

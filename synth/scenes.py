@@ -167,17 +167,16 @@ def make_scene(seed: int, n: int, dim: int, extent=(10.0, 10.0, 3.0),
                  noise_sigma=sigma)
 
 
-def _plant_landmark(rng, centers, e, pred, radius=5.0):
+def _plant_landmark(rng, centers, e, pred, tree, radius=5.0):
     """Pick a landmark object for constraint `pred` on planted target `e`.
 
     Prefers objects within `radius` metres; among them, for above (0) a lower
     centre, for below (1) a higher centre, for near (4) one within 1 m; for
     left/right (2, 3) any neighbour.  Falls back to any other object.
+    `tree` is a KD-tree over the centres (neighbour lookup only).
     """
     n = centers.shape[0]
-    d = centers - centers[e]
-    dist2 = np.einsum("ij,ij->i", d, d)
-    cand = np.flatnonzero(dist2 <= radius * radius)
+    cand = np.asarray(sorted(tree.query_ball_point(centers[e], radius)), dtype=np.int64)
     cand = cand[cand != e]
     if cand.size == 0:
         others = np.flatnonzero(np.arange(n) != e)
@@ -187,7 +186,8 @@ def _plant_landmark(rng, centers, e, pred, radius=5.0):
     elif pred == 1:
         pref = cand[centers[cand, 2] > centers[e, 2]]
     elif pred == 4:
-        pref = cand[dist2[cand] <= 1.0]
+        d = centers[cand] - centers[e]
+        pref = cand[np.einsum("ij,ij->i", d, d) <= 1.0]
     else:
         pref = cand
     pool = pref if pref.size else cand
@@ -231,9 +231,11 @@ def make_queries(seed: int, scene: Scene, n_q: int, m_choices=(2,),
     n_c = int(c_off[-1])
     preds = rng.integers(0, N_PRED, size=n_c)
     lms = np.zeros(n_c, np.int64)
+    from scipy.spatial import cKDTree
+    tree = cKDTree(centers)
     for q in range(n_q):
         for c in range(c_off[q], c_off[q + 1]):
-            lms[c] = _plant_landmark(rng, centers, int(targets[q]), int(preds[c]))
+            lms[c] = _plant_landmark(rng, centers, int(targets[q]), int(preds[c]), tree)
     c_emb = cent[scene.cls[lms]] + sigma * rng.standard_normal((n_c, dim))
     tgt_cls = scene.cls[targets].astype(np.int32) if with_class else np.full(n_q, -1, np.int32)
     return QueryBatch(tgt_emb=np.ascontiguousarray(tgt_emb.astype(np.float32)),
