@@ -121,18 +121,64 @@ def job_rate(n_units_per_rank, world, ms_per_step):
     return world * n_units_per_rank / (ms_per_step * 1e-3)
 
 
-def cpu_baseline(scene, qb, k, n_sample, seed=0):
+def cpu_baseline(scenes, qb, k, n_sample, seed=0):
     """The oracle on a seeded query sample: its rate, and its TopK for recall."""
     import oracle
     qs = np.sort(np.random.default_rng(seed).choice(qb.n_q, size=min(n_sample, qb.n_q), replace=False))
-    sub = qb.subset(qs)
+    ref = np.zeros((len(qs), k), np.int64)
     t0 = time.perf_counter()
-    ref = oracle.batch(scene, sub, k)
+    for sid in np.unique(qb.scene_of_q[qs]):
+        pos = np.flatnonzero(qb.scene_of_q[qs] == sid)
+        out = oracle.batch(scenes[int(sid)], qb.subset(qs[pos]), k)
+        ref[pos] = out["idx"]
     dt = time.perf_counter() - t0
-    return {"value": sub.n_q / dt, "unit": "queries/s", "cores": oracle.num_threads(),
+    return {"value": len(qs) / dt, "unit": "queries/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": f"{sub.n_q} of the {qb.n_q} queries (seeded), FP64 oracle, OpenMP over "
-                      f"queries, {dt:.1f} s wall"}, qs, ref["idx"]
+            "sample": f"{len(qs)} of the {qb.n_q} queries (seeded), FP64 oracle, OpenMP over "
+                      f"queries, {dt:.1f} s wall"}, qs, ref
+
+
+def similarity_flops(scenes, qb):
+    """2 D N per (row, object) over every scene's rows: the algorithmic work of the similarity stage."""
+    rows = np.bincount(qb.scene_of_q, minlength=len(scenes)).astype(np.float64)
+    m = np.diff(qb.c_off.astype(np.int64))
+    rows += np.bincount(qb.scene_of_q, weights=m, minlength=len(scenes))
+    return float(sum(2.0 * rows[i] * sc.n * sc.dim for i, sc in enumerate(scenes)))
+
+
+def train_prefilter(F, ctx, scenes, seed=0, n_rows=2000, top=256, rand=768, epochs=2):
+    """Self-supervised training of the learned prefilter on the uploaded memory:
+    proxy queries are a sample of each scene's descriptors, paired with their
+    best objects by the library's FP32-accurate cosine and with random ones
+    (2,048,000 pairs at the defaults)."""
+    rng = np.random.default_rng(seed)
+    D, H, P = scenes[0].dim, 512, 128
+    params = [(rng.standard_normal((H, D)) / np.sqrt(D)).astype(np.float32),
+              (0.05 * rng.standard_normal(H)).astype(np.float32),
+              (rng.standard_normal((P, H)) / np.sqrt(H)).astype(np.float32),
+              (0.05 * rng.standard_normal(P)).astype(np.float32)]
+    F.farm_mlp_set(ctx, *params)
+    sc = scenes[0]
+    idx = rng.choice(sc.n, min(n_rows, sc.n), replace=False)
+    rows = sc.desc[idx]
+    pr_l, po_l, y_l, w_l = [], [], [], []
+    for c0 in range(0, len(rows), 256):
+        blk = rows[c0:c0 + 256]
+        S = F.farm_similarity(ctx, 0, blk, sc.n, F.PREC_FP32)
+        t = np.argpartition(-S, min(top, sc.n - 1), axis=1)[:, :top]
+        r = rng.integers(0, sc.n, size=(len(blk), rand))
+        objs = np.concatenate([t, r], axis=1)
+        pr = np.repeat(np.arange(c0, c0 + len(blk)), objs.shape[1])
+        po = objs.ravel()
+        pr_l.append(pr); po_l.append(po)
+        y_l.append(S[pr - c0, po])
+        w_l.append(np.concatenate([np.full((len(blk), top), 4.0), np.ones((len(blk), rand))], axis=1).ravel())
+    pr, po = np.concatenate(pr_l).astype(np.int32), np.concatenate(po_l).astype(np.int32)
+    y, w = np.concatenate(y_l).astype(np.float32), np.concatenate(w_l).astype(np.float32)
+    t0 = time.perf_counter()
+    losses = F.farm_mlp_train(ctx, 0, rows, pr, po, y, w, epochs=epochs, batch=4096, lr=1e-3, seed=seed + 1)
+    return {"pairs": int(len(y)), "epochs": epochs, "seconds": time.perf_counter() - t0,
+            "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1])}
 
 
 def run_reference(args):
@@ -147,12 +193,18 @@ def run_reference(args):
     sc = scenes[0]
     n_per_step = args.ref_queries
     rng = np.random.default_rng(1)
+
+    def one_step(count):
+        qs = np.sort(rng.choice(qb.n_q, size=count, replace=False))
+        for sid in np.unique(qb.scene_of_q[qs]):
+            pos = qs[qb.scene_of_q[qs] == sid]
+            oracle.batch(scenes[int(sid)], qb.subset(pos), K_TOP)
+
     for _ in range(args.warmup):
-        oracle.batch(sc, qb.subset(rng.choice(qb.n_q, size=8, replace=False)), K_TOP)
+        one_step(8)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        sub = qb.subset(np.sort(rng.choice(qb.n_q, size=n_per_step, replace=False)))
-        oracle.batch(sc, sub, K_TOP)
+        one_step(n_per_step)
     dt = time.perf_counter() - t0
     value = n_per_step * args.steps / dt
     line = {
@@ -160,7 +212,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n_objects": sc.n, "dim": sc.dim,
+        "config": {"workload": args.workload, "scenes": len(scenes),
+                   "n_objects": int(sum(x.n for x in scenes)), "dim": sc.dim,
                    "queries_per_step": n_per_step, "top_k": K_TOP},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": oracle.num_threads(),
                          "kind": "oracle",
@@ -176,7 +229,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_simt", "bf16", "fp8"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_simt", "bf16", "fp8", "learned"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-sample", type=int, default=384)
     ap.add_argument("--ref-queries", type=int, default=64)
@@ -209,11 +262,13 @@ def main():
     scenes, qb = synth.workload(args.workload)
     sc = scenes[0]
     prec = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16,
-            "fp8": F.PREC_FP8}[args.precision]
+            "fp8": F.PREC_FP8, "learned": F.PREC_LEARNED}[args.precision]
     stream = torch.cuda.Stream()          # the library and the timing events share it
     torch.cuda.set_stream(stream)
     ctx = F.farm_create(local, stream)
-    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    for sid, scn in enumerate(scenes):
+        F.farm_memory_upload(ctx, sid, scn.desc, scn.cls, scn.box, scn.views)
+    training = train_prefilter(F, ctx, scenes) if args.precision == "learned" else None
     n_q, n_c = qb.n_q, qb.n_c
     d_tgt = torch.from_numpy(qb.tgt_emb).cuda()
     d_cemb = torch.from_numpy(qb.c_emb).cuda()
@@ -277,8 +332,10 @@ def main():
 
     # ---- roofline of the similarity contraction (stage 1), measured over the timed region
     peaks, peak_kind = _peaks()
-    rows = n_q + n_c
-    flops_step = 2.0 * rows * sc.n * sc.dim
+    flops_step = similarity_flops(scenes, qb)
+    if args.precision == "learned":
+        # the similarity stage works in the 128-d embedding space
+        flops_step *= 128.0 / sc.dim
     gemm_ms = stage_ms[1] / args.steps
     if args.precision == "fp32":
         # three TF32 products per FP32-accurate product; TF32 peak = bf16 peak x (1.1 / 2.25)
@@ -289,6 +346,10 @@ def main():
         peak = peaks["bf16_tflops_sustained"]
         bound, unit = "tensor", "TFLOP/s"
         peak_note = f"{peak_kind} sustained bf16"
+    elif args.precision == "learned":
+        peak = peaks["bf16_tflops_sustained"]
+        bound, unit = "tensor", "TFLOP/s"
+        peak_note = f"{peak_kind} sustained bf16 (128-d learned embeddings)"
     elif args.precision == "fp8":
         peak = peaks["bf16_tflops_sustained"] * (4.5 / 2.25)
         bound, unit = "tensor", "TFLOP/s"
@@ -304,12 +365,14 @@ def main():
         "metric": "relational queries/s", "value": job_rate(n_q, world, ms_step),
         "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp32_simt": "f32", "bf16": "bf16", "fp8": "f8e4m3"}[args.precision],
+        "dtype": {"fp32": "f32", "fp32_simt": "f32", "bf16": "bf16", "fp8": "f8e4m3",
+                  "learned": "bf16"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": args.workload, "n_objects": sc.n, "dim": sc.dim, "n_views": sc.n_views,
+        "config": {"workload": args.workload, "scenes": len(scenes),
+                   "n_objects": int(sum(x.n for x in scenes)), "dim": sc.dim, "n_views": sc.n_views,
                    "queries": n_q, "constraint_rows": n_c, "top_k": K_TOP,
                    "precision": args.precision, "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (descriptor splits 184 MB + similarity block 1.15 GB)"},
+                   "l2": "inputs larger than L2 (descriptor copies and the similarity block exceed 129 MB)"},
         "e2e": {"value": job_rate(n_q, world, e2e_ms), "unit": "queries/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -323,11 +386,13 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        base, qs, ref_idx = cpu_baseline(sc, qb, K_TOP, args.cpu_sample)
+        base, qs, ref_idx = cpu_baseline(scenes, qb, K_TOP, args.cpu_sample)
         line["cpu_baseline"] = base
         got = h_out["idx"][qs]
         hits = sum(len(set(got[i].tolist()) & set(ref_idx[i].tolist())) for i in range(len(qs)))
         line["recall_at_10_vs_oracle"] = {"value": hits / (K_TOP * len(qs)), "queries": int(len(qs))}
+    if training:
+        line["prefilter_training"] = training
     F.farm_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
