@@ -87,7 +87,12 @@ typedef enum {
  * rescore (1 .. 512) is the number of candidates per target row the BF16 path
  * re-scores in FP32 (at least the rank bound R of farm_query_batch; the FP8
  * path keeps twice as many, at most 512); landmark rows re-score a quarter of
- * that, at least k_anchor.
+ * that, at least k_anchor.  Of those, only the borderline ones are re-scored:
+ * candidates whose reduced-precision cosine lies within rescore_band (>= 0) of
+ * the R-th (or K_a-th) reduced-precision value, 16 times that band for FP8
+ * (four fewer significant bits); farm_default_params sets 2e-3, about thirty
+ * standard deviations of the BF16 stage's cosine error on unit descriptors
+ * of length 1152.
  */
 typedef struct {
     float mu;
@@ -100,9 +105,10 @@ typedef struct {
     int32_t k_anchor;
     int32_t k_max;
     int32_t rescore;
+    float rescore_band;
 } farm_params;
 
-/* Fills *p with the defaults above (k_max = 10, rescore = 256). */
+/* Fills *p with the defaults above (k_max = 10, rescore = 256, rescore_band = 2e-3). */
 void farm_default_params(farm_params *p);
 
 /*

@@ -90,6 +90,7 @@ bool params_ok(const farm_params &p, std::string &why)
         return false;
     }
     if (p.rescore < 1 || p.rescore > farm::kMaxTargetCands) { why = "rescore must lie in [1, 512]"; return false; }
+    if (!(p.rescore_band >= 0.f) || !std::isfinite(p.rescore_band)) { why = "rescore_band must be >= 0"; return false; }
     return true;
 }
 
@@ -300,6 +301,7 @@ void farm_default_params(farm_params *p)
     p->k_anchor = 16;
     p->k_max = 10;
     p->rescore = 256;
+    p->rescore_band = 2e-3f;
 }
 
 const char *farm_last_error(farm_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
@@ -626,11 +628,16 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     RowOps ops;
     CK(alloc_rows(ctx, precision, rows_total, dim_pad, ops));
     int32_t *bsel_t = nullptr, *bsel_l = nullptr;
+    float *bsel_tv = nullptr, *bsel_lv = nullptr;
     const int32_t cstride_t = reduced_keep_target(p, precision, stride_t, max_n);
     const int32_t cstride_l = reduced_keep_landmark(p, precision, stride_l, max_n);
     if (reduced_precision(precision)) {
         CK(ws_get(ctx, farm::B_BSEL_T, (size_t)n_q * cstride_t, &bsel_t));
         CK(ws_get(ctx, farm::B_BSEL_L, (size_t)std::max<int64_t>(n_c, 1) * cstride_l, &bsel_l));
+        if (precision != FARM_PREC_LEARNED) {
+            CK(ws_get(ctx, farm::B_BSEL_TV, (size_t)n_q * cstride_t, &bsel_tv));
+            CK(ws_get(ctx, farm::B_BSEL_LV, (size_t)std::max<int64_t>(n_c, 1) * cstride_l, &bsel_lv));
+        }
     }
     int64_t max_ld = 0, max_rows = 0;
     for (const auto &g : groups) {
@@ -696,16 +703,17 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                 const int32_t Ct = reduced_keep_target(p, precision, Rs, s.n);
                 const int32_t Cl = reduced_keep_landmark(p, precision, klm, s.n);
                 const int64_t lrow0 = g.cp0 + r0 + ntr - g.nq;
-                LAUNCH(farm::launch_select_rows(d_sim, ld, s.n, r1 - r0, ntr, Ct, Cl, bsel_t, nullptr, g.q0 + r0,
-                                                cstride_t, bsel_l, lrow0, cstride_l, c.stream));
+                LAUNCH(farm::launch_select_rows_ex(d_sim, ld, s.n, r1 - r0, ntr, Ct, Cl, bsel_t, bsel_tv, g.q0 + r0,
+                                                   cstride_t, bsel_l, bsel_lv, lrow0, cstride_l, c.stream));
+                const float band = precision == FARM_PREC_FP8 ? 16.f * p.rescore_band : p.rescore_band;
                 if (ntr > 0)
-                    LAUNCH(farm::launch_rescore(ops.q32, g.row0 + r0, dim_pad, s.desc32, bsel_t, Ct, cstride_t,
-                                                g.q0 + r0, ntr, Rs, tsel_idx, tsel_cos, stride_t, g.q0 + r0,
-                                                c.stream));
+                    LAUNCH(farm::launch_rescore(ops.q32, g.row0 + r0, dim_pad, s.desc32, bsel_t, bsel_tv, band, Ct,
+                                                cstride_t, g.q0 + r0, ntr, Rs, tsel_idx, tsel_cos, stride_t,
+                                                g.q0 + r0, c.stream));
                 if (r1 - r0 - ntr > 0)
-                    LAUNCH(farm::launch_rescore(ops.q32, g.row0 + r0 + ntr, dim_pad, s.desc32, bsel_l, Cl, cstride_l,
-                                                lrow0, r1 - r0 - ntr, klm, lsel_idx, nullptr, stride_l, lrow0,
-                                                c.stream));
+                    LAUNCH(farm::launch_rescore(ops.q32, g.row0 + r0 + ntr, dim_pad, s.desc32, bsel_l, bsel_lv, band,
+                                                Cl, cstride_l, lrow0, r1 - r0 - ntr, klm, lsel_idx, nullptr, stride_l,
+                                                lrow0, c.stream));
             }
             mark_end(ctx, m2);
         }

@@ -74,6 +74,8 @@ enum Buf {
     B_TOPK,         // int32/float [n_q, k, 10] TopK staging for host outputs
     B_BSEL_T,       // int32 [n_q, C_t] BF16-stage target candidates (before FP32 rescore)
     B_BSEL_L,       // int32 [n_c, C_l] BF16-stage landmark candidates
+    B_BSEL_TV,      // float [n_q, C_t] their reduced-precision values
+    B_BSEL_LV,      // float [n_c, C_l]
     B_QF8,          // uint8 [rows, dim_pad] E4M3 rows
     B_QSCALE,       // float [rows] their scales
     B_QCOMP,        // bf16 [rows, P] learned embeddings of the rows
@@ -215,6 +217,13 @@ cudaError_t launch_select_rows(const float *S, int64_t ld_s, int64_t n, int64_t 
                                int32_t stride_t, int32_t *lsel_idx, int64_t lsel_row0,
                                int32_t stride_l, cudaStream_t s);
 
+// As launch_select_rows, also writing the landmark rows' values to lsel_cos
+// (same layout as lsel_idx; nullable).
+cudaError_t launch_select_rows_ex(const float *S, int64_t ld_s, int64_t n, int64_t rows, int64_t n_tgt_rows,
+                                  int32_t r_tgt, int32_t k_lm, int32_t *tsel_idx, float *tsel_cos, int64_t tsel_row0,
+                                  int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int64_t lsel_row0,
+                                  int32_t stride_l, cudaStream_t s);
+
 // Device-side view of one scene, indexed by scene id in a device table.
 struct SceneDev {
     const float *pos;       // [3, n]
@@ -227,11 +236,14 @@ struct SceneDev {
 
 // Re-score C candidates per row with exact FP32 dot products of unit rows and
 // keep the R best in rank order: row r (of `rows`) uses Q32 row q_row0 + r,
-// candidates cand[(cand_row0 + r) * cand_stride + c], writes
-// out_idx/out_cos[(out_row0 + r) * out_stride + i] (-1 / 0 past R).
+// candidates cand[(cand_row0 + r) * cand_stride + c] (descending by their
+// reduced-precision values cand_val, same layout; nullable), writes
+// out_idx/out_cos[(out_row0 + r) * out_stride + i] (-1 / 0 past R).  With
+// cand_val, candidates more than `band` below the R-th value are skipped.
 cudaError_t launch_rescore(const float *Q32, int64_t q_row0, int32_t dim_pad, const float *D32, const int32_t *cand,
-                           int32_t C, int32_t cand_stride, int64_t cand_row0, int64_t rows, int32_t R,
-                           int32_t *out_idx, float *out_cos, int32_t out_stride, int64_t out_row0, cudaStream_t s);
+                           const float *cand_val, float band, int32_t C, int32_t cand_stride, int64_t cand_row0,
+                           int64_t rows, int32_t R, int32_t *out_idx, float *out_cos, int32_t out_stride,
+                           int64_t out_row0, cudaStream_t s);
 
 struct ComposeArgs {
     int64_t n_q;

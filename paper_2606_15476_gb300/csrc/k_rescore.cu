@@ -7,9 +7,14 @@
 // result equals the FP32 path's list whenever the FP32 top R lie within the
 // BF16 top C.
 //
+// Only the borderline candidates are re-scored: with the reduced-precision
+// values of the (descending) candidate list at hand, a candidate whose value
+// lies more than `band` below the R-th value is skipped (it would need an
+// arithmetic error above the band to belong to the top R).
+//
 // One CTA per row: the row is staged in shared memory, each warp takes
 // candidates in turn (lanes stride the descriptor in float4, then a shuffle
-// reduction), and a bitonic sort over (cosine key, index) orders the C scores.
+// reduction), and a bitonic sort over (cosine key, index) orders the scores.
 #include "farm_internal.h"
 
 namespace farm {
@@ -32,8 +37,9 @@ __device__ __forceinline__ float key_value(uint32_t k)
 
 __global__ void __launch_bounds__(TH)
 rescore_kernel(const float *__restrict__ Q32, int64_t q_row0, int32_t dim_pad, const float *__restrict__ D32,
-               const int32_t *__restrict__ cand, int32_t C, int32_t cand_stride, int64_t cand_row0, int32_t R,
-               int32_t *__restrict__ out_idx, float *__restrict__ out_cos, int32_t out_stride, int64_t out_row0)
+               const int32_t *__restrict__ cand, const float *__restrict__ cand_val, float band, int32_t C,
+               int32_t cand_stride, int64_t cand_row0, int32_t R, int32_t *__restrict__ out_idx,
+               float *__restrict__ out_cos, int32_t out_stride, int64_t out_row0)
 {
     extern __shared__ float4 q4[];
     __shared__ uint64_t key[SORT_MAX];
@@ -44,7 +50,13 @@ rescore_kernel(const float *__restrict__ Q32, int64_t q_row0, int32_t dim_pad, c
     for (int i = tid; i < nv; i += TH) q4[i] = src[i];
     __syncthreads();
     const int32_t *cr = cand + (cand_row0 + r) * (int64_t)cand_stride;
+    const float *cv = cand_val ? cand_val + (cand_row0 + r) * (int64_t)cand_stride : nullptr;
+    const float thr = cv ? cv[R - 1] - band : 0.f;
     for (int c = warp; c < C; c += TH / 32) {
+        if (cv && cv[c] < thr) {
+            if (lane == 0) key[c] = 0ull;
+            continue;
+        }
         const int32_t e = cr[c];
         const float4 *dp = reinterpret_cast<const float4 *>(D32 + (int64_t)e * dim_pad);
         float acc = 0.f;
@@ -92,8 +104,9 @@ rescore_kernel(const float *__restrict__ Q32, int64_t q_row0, int32_t dim_pad, c
 }  // namespace
 
 cudaError_t launch_rescore(const float *Q32, int64_t q_row0, int32_t dim_pad, const float *D32, const int32_t *cand,
-                           int32_t C, int32_t cand_stride, int64_t cand_row0, int64_t rows, int32_t R,
-                           int32_t *out_idx, float *out_cos, int32_t out_stride, int64_t out_row0, cudaStream_t s)
+                           const float *cand_val, float band, int32_t C, int32_t cand_stride, int64_t cand_row0,
+                           int64_t rows, int32_t R, int32_t *out_idx, float *out_cos, int32_t out_stride,
+                           int64_t out_row0, cudaStream_t s)
 {
     if (rows <= 0) return cudaSuccess;
     if (C < 1 || C > SORT_MAX || R < 1 || R > C || R > out_stride || dim_pad % 4 != 0) return cudaErrorInvalidValue;
@@ -102,8 +115,8 @@ cudaError_t launch_rescore(const float *Q32, int64_t q_row0, int32_t dim_pad, co
         cudaError_t e = cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    rescore_kernel<<<(unsigned)rows, TH, smem, s>>>(Q32, q_row0, dim_pad, D32, cand, C, cand_stride, cand_row0, R,
-                                                    out_idx, out_cos, out_stride, out_row0);
+    rescore_kernel<<<(unsigned)rows, TH, smem, s>>>(Q32, q_row0, dim_pad, D32, cand, cand_val, band, C, cand_stride,
+                                                    cand_row0, R, out_idx, out_cos, out_stride, out_row0);
     return cudaGetLastError();
 }
 

@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(TH)
 select_rows_global_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, int64_t n_tgt_rows,
                    int32_t r_tgt, int32_t k_lm, int32_t *__restrict__ tsel_idx,
                    float *__restrict__ tsel_cos, int64_t tsel_row0, int32_t stride_t,
-                   int32_t *__restrict__ lsel_idx, int64_t lsel_row0, int32_t stride_l)
+                   int32_t *__restrict__ lsel_idx, float *__restrict__ lsel_cos, int64_t lsel_row0,
+                   int32_t stride_l)
 {
     __shared__ uint32_t hist[256];
     __shared__ uint64_t cand[SORT_MAX];
@@ -165,8 +166,11 @@ select_rows_global_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, 
         }
     } else {
         int32_t *oi = lsel_idx + (lsel_row0 + (r - n_tgt_rows)) * (int64_t)stride_l;
-        for (int i = tid; i < stride_l; i += TH)
+        float *oc = lsel_cos ? lsel_cos + (lsel_row0 + (r - n_tgt_rows)) * (int64_t)stride_l : nullptr;
+        for (int i = tid; i < stride_l; i += TH) {
             oi[i] = i < R ? (int32_t)(0xffffffffu - (uint32_t)(cand[i] & 0xffffffffu)) : -1;
+            if (oc) oc[i] = i < R ? key_value((uint32_t)(cand[i] >> 32)) : 0.f;
+        }
     }
 }
 
@@ -209,26 +213,23 @@ __device__ __forceinline__ void find_bucket(const uint32_t *hist, uint32_t remai
     __syncthreads();
 }
 
-// Bitonic sort of P (a power of two <= 2 TH) 64-bit keys in shared memory,
-// descending; thread t handles elements t and t + TH.  Stages whose partners
-// lie in the same 32-element block synchronise the warp only.
+// Bitonic sort of P (a power of two <= TH) 64-bit keys in shared memory,
+// descending, one element per thread.  Stages whose partners lie in the same
+// warp synchronise the warp only.
 __device__ __forceinline__ void bitonic_desc(uint64_t *cand, int P)
 {
+    const int i = threadIdx.x;
     int prev_j = TH;
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j >= 32 || prev_j >= 32) __syncthreads();
             else __syncwarp();
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int i = threadIdx.x + h * TH;
-                if (i < P) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const uint64_t a = cand[i], b = cand[ixj];
-                        const bool desc = (i & k) == 0;
-                        if (desc ? (a < b) : (a > b)) { cand[i] = b; cand[ixj] = a; }
-                    }
+            if (i < P) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = cand[i], b = cand[ixj];
+                    const bool desc = (i & k) == 0;
+                    if (desc ? (a < b) : (a > b)) { cand[i] = b; cand[ixj] = a; }
                 }
             }
             prev_j = j;
@@ -237,32 +238,18 @@ __device__ __forceinline__ void bitonic_desc(uint64_t *cand, int P)
     __syncthreads();
 }
 
-// Block-wide sum of one value per thread (result in every thread).
-__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t *wsum)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = __reduce_add_sync(0xffffffffu, v);
-    __syncthreads();
-    if (lane == 0) wsum[warp] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    for (int w = 0; w < TH / 32; ++w) t += wsum[w];
-    return t;
-}
-
-constexpr int kCandMax = 2 * TH;   // candidates the sampled threshold may admit
-
 constexpr int kVecHalf = kRowSmemMax / 8 / TH;   // float4 loads per thread per batch (two batches)
 
 __global__ void __launch_bounds__(TH, 2)
 select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, int64_t n_tgt_rows,
                         int32_t r_tgt, int32_t k_lm, int32_t *__restrict__ tsel_idx,
                         float *__restrict__ tsel_cos, int64_t tsel_row0, int32_t stride_t,
-                        int32_t *__restrict__ lsel_idx, int64_t lsel_row0, int32_t stride_l)
+                        int32_t *__restrict__ lsel_idx, float *__restrict__ lsel_cos, int64_t lsel_row0,
+                   int32_t stride_l)
 {
     extern __shared__ uint32_t keys[];
     __shared__ uint32_t hist[2048];
-    __shared__ uint64_t cand[kCandMax];
+    __shared__ uint64_t cand[SORT_MAX];
     __shared__ uint32_t wsum[TH / 32];
     __shared__ uint32_t s_bin, s_rem, s_cnt;
     __shared__ int s_app, s_warp[TH / 32];
@@ -274,7 +261,10 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
     const int R = is_tgt ? r_tgt : k_lm;
     const int n4 = n & ~3;
 
-    // stage the row as order keys, loads issued in two batches
+    // issue the row's loads in two batches of kVecHalf float4 per thread, then
+    // histogram the top 11 bits of each key
+    for (int i = tid; i < 2048; i += TH) hist[i] = 0;
+    __syncthreads();
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         float4 buf[kVecHalf];
@@ -286,140 +276,99 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
 #pragma unroll
         for (int u = 0; u < kVecHalf; ++u) {
             const int i = ((half * kVecHalf + u) * TH + tid) * 4;
-            if (i < n4)
-                *reinterpret_cast<uint4 *>(keys + i) = make_uint4(order_key(buf[u].x), order_key(buf[u].y),
-                                                                 order_key(buf[u].z), order_key(buf[u].w));
+            if (i < n4) {
+                const uint4 k = make_uint4(order_key(buf[u].x), order_key(buf[u].y), order_key(buf[u].z),
+                                           order_key(buf[u].w));
+                *reinterpret_cast<uint4 *>(keys + i) = k;
+                atomicAdd(&hist[k.x >> 21], 1u);
+                atomicAdd(&hist[k.y >> 21], 1u);
+                atomicAdd(&hist[k.z >> 21], 1u);
+                atomicAdd(&hist[k.w >> 21], 1u);
+            }
         }
     }
-    if (tid < n - n4) keys[n4 + tid] = order_key(row[n4 + tid]);
-    __syncthreads();
-    const int nv = (n + 3) >> 2;   // uint4 groups (the tail group is masked by index)
-
-    // Threshold from a strided sample of TH keys: its k-th largest, with k
-    // chosen so that about 4R keys of the row reach it.  Every key at or above
-    // it is a candidate; the R best candidates are the row's top R whenever at
-    // least R keys reach the threshold.  Short rows take every key.
-    uint32_t tau = 0;
-    if (n > kCandMax) {
-        cand[tid] = (uint64_t)keys[(int)(((int64_t)tid * n) / TH)] << 32;
-        bitonic_desc(cand, TH);
-        const int k = min(TH, max((4 * R * TH + n - 1) / n, 4) + 1);
-        tau = (uint32_t)(cand[k - 1] >> 32);
-        __syncthreads();
+    if (tid < n - n4) {
+        const uint32_t k = order_key(row[n4 + tid]);
+        keys[n4 + tid] = k;
+        atomicAdd(&hist[k >> 21], 1u);
     }
-    uint32_t mine = 0;
+    __syncthreads();
+    find_bucket<2048>(hist, (uint32_t)R, wsum, &s_bin, &s_rem, &s_cnt);
+    const uint32_t b1 = s_bin;
+    uint32_t remaining = s_rem;
+    const int nv = (n + 3) >> 2;   // uint4 groups (the tail group is masked by index)
+    // second digit: bits 10..20 among keys whose top digit is b1
+    for (int i = tid; i < 2048; i += TH) hist[i] = 0;
+    __syncthreads();
     for (int g = tid; g < nv; g += TH) {
         const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
-        mine += (4 * g + 0 < n && k.x >= tau) + (4 * g + 1 < n && k.y >= tau) + (4 * g + 2 < n && k.z >= tau) +
-                (4 * g + 3 < n && k.w >= tau);
+        const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (4 * g + c < n && (kk[c] >> 21) == b1) atomicAdd(&hist[(kk[c] >> 10) & 2047u], 1u);
     }
-    const uint32_t cnt = block_sum(mine, wsum);
+    __syncthreads();
+    find_bucket<2048>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
+    const uint32_t p2 = (b1 << 11) | s_bin;     // top 22 bits
+    remaining = s_rem;
+    // third digit: bits 0..9
+    for (int i = tid; i < 1024; i += TH) hist[i] = 0;
+    __syncthreads();
+    for (int g = tid; g < nv; g += TH) {
+        const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
+        const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (4 * g + c < n && (kk[c] >> 10) == p2) atomicAdd(&hist[kk[c] & 1023u], 1u);
+    }
+    __syncthreads();
+    find_bucket<1024>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
+    const uint32_t T = (p2 << 10) | s_bin;
+    remaining = s_rem;
+    const bool take_all_eq = s_cnt == remaining;
+    const int n_gt = R - (int)remaining;
 
-    if (cnt >= (uint32_t)R && cnt <= (uint32_t)kCandMax) {
-        if (tid == 0) s_app = 0;
-        __syncthreads();
-        for (int g = tid; g < nv; g += TH) {
-            const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
-            const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+    if (tid == 0) s_app = 0;
+    __syncthreads();
+    for (int g = tid; g < nv; g += TH) {
+        const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
+        const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int i = 4 * g + c;
-                if (i < n && kk[c] >= tau) {
-                    const int pos = atomicAdd(&s_app, 1);
-                    cand[pos] = ((uint64_t)kk[c] << 32) | (uint64_t)(0xffffffffu - (uint32_t)i);
-                }
+        for (int c = 0; c < 4; ++c) {
+            const int i = 4 * g + c;
+            if (i < n && (kk[c] > T || (take_all_eq && kk[c] == T))) {
+                const int pos = atomicAdd(&s_app, 1);
+                cand[pos] = ((uint64_t)kk[c] << 32) | (uint64_t)(0xffffffffu - (uint32_t)i);
             }
         }
-        __syncthreads();
-        int P = 1;
-        while (P < (int)cnt) P <<= 1;
-        for (int i = (int)cnt + tid; i < P; i += TH) cand[i] = 0ull;
-        bitonic_desc(cand, P);
-    } else {
-        // radix select on the staged keys: 11/11/10-bit digits
-        for (int i = tid; i < 2048; i += TH) hist[i] = 0;
-        __syncthreads();
-        for (int g = tid; g < nv; g += TH) {
-            const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
-            const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (4 * g + c < n) atomicAdd(&hist[kk[c] >> 21], 1u);
-        }
-        __syncthreads();
-        find_bucket<2048>(hist, (uint32_t)R, wsum, &s_bin, &s_rem, &s_cnt);
-        const uint32_t b1 = s_bin;
-        uint32_t remaining = s_rem;
-        for (int i = tid; i < 2048; i += TH) hist[i] = 0;
-        __syncthreads();
-        for (int g = tid; g < nv; g += TH) {
-            const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
-            const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (4 * g + c < n && (kk[c] >> 21) == b1) atomicAdd(&hist[(kk[c] >> 10) & 2047u], 1u);
-        }
-        __syncthreads();
-        find_bucket<2048>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
-        const uint32_t p2 = (b1 << 11) | s_bin;     // top 22 bits
-        remaining = s_rem;
-        for (int i = tid; i < 1024; i += TH) hist[i] = 0;
-        __syncthreads();
-        for (int g = tid; g < nv; g += TH) {
-            const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
-            const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (4 * g + c < n && (kk[c] >> 10) == p2) atomicAdd(&hist[kk[c] & 1023u], 1u);
-        }
-        __syncthreads();
-        find_bucket<1024>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
-        const uint32_t T = (p2 << 10) | s_bin;
-        remaining = s_rem;
-        const bool take_all_eq = s_cnt == remaining;
-        const int n_gt = R - (int)remaining;
-        if (tid == 0) s_app = 0;
-        __syncthreads();
-        for (int g = tid; g < nv; g += TH) {
-            const uint4 k = reinterpret_cast<const uint4 *>(keys)[g];
-            const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int i = 4 * g + c;
-                if (i < n && (kk[c] > T || (take_all_eq && kk[c] == T))) {
-                    const int pos = atomicAdd(&s_app, 1);
-                    cand[pos] = ((uint64_t)kk[c] << 32) | (uint64_t)(0xffffffffu - (uint32_t)i);
-                }
-            }
-        }
-        __syncthreads();
-        if (!take_all_eq) {
-            int taken = 0;
-            for (int base = 0; base < n && taken < (int)remaining; base += TH) {
-                const int j = base + tid;
-                const bool eq = j < n && keys[j] == T;
-                const unsigned bal = __ballot_sync(0xffffffffu, eq);
-                if (lane == 0) s_warp[warp] = __popc(bal);
-                __syncthreads();
-                int off = 0, tot = 0;
-                for (int w = 0; w < TH / 32; ++w) {
-                    if (w < warp) off += s_warp[w];
-                    tot += s_warp[w];
-                }
-                if (eq) {
-                    const int pos = taken + off + __popc(bal & ((1u << lane) - 1u));
-                    if (pos < (int)remaining)
-                        cand[n_gt + pos] = ((uint64_t)T << 32) | (uint64_t)(0xffffffffu - (uint32_t)j);
-                }
-                taken += tot;
-                __syncthreads();
-            }
-        }
-        int P = 1;
-        while (P < R) P <<= 1;
-        for (int i = R + tid; i < P; i += TH) cand[i] = 0ull;
-        bitonic_desc(cand, P);
     }
+    __syncthreads();
+    if (!take_all_eq) {
+        int taken = 0;
+        for (int base = 0; base < n && taken < (int)remaining; base += TH) {
+            const int j = base + tid;
+            const bool eq = j < n && keys[j] == T;
+            const unsigned bal = __ballot_sync(0xffffffffu, eq);
+            if (lane == 0) s_warp[warp] = __popc(bal);
+            __syncthreads();
+            int off = 0, tot = 0;
+            for (int w = 0; w < TH / 32; ++w) {
+                if (w < warp) off += s_warp[w];
+                tot += s_warp[w];
+            }
+            if (eq) {
+                const int pos = taken + off + __popc(bal & ((1u << lane) - 1u));
+                if (pos < (int)remaining)
+                    cand[n_gt + pos] = ((uint64_t)T << 32) | (uint64_t)(0xffffffffu - (uint32_t)j);
+            }
+            taken += tot;
+            __syncthreads();
+        }
+    }
+    int P = 1;
+    while (P < R) P <<= 1;
+    for (int i = R + tid; i < P; i += TH) cand[i] = 0ull;
+    bitonic_desc(cand, P);
     if (is_tgt) {
         int32_t *oi = tsel_idx + (tsel_row0 + r) * (int64_t)stride_t;
         float *oc = tsel_cos ? tsel_cos + (tsel_row0 + r) * (int64_t)stride_t : nullptr;
@@ -435,18 +384,20 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
         }
     } else {
         int32_t *oi = lsel_idx + (lsel_row0 + (r - n_tgt_rows)) * (int64_t)stride_l;
-        for (int i = tid; i < stride_l; i += TH)
+        float *oc = lsel_cos ? lsel_cos + (lsel_row0 + (r - n_tgt_rows)) * (int64_t)stride_l : nullptr;
+        for (int i = tid; i < stride_l; i += TH) {
             oi[i] = i < R ? (int32_t)(0xffffffffu - (uint32_t)(cand[i] & 0xffffffffu)) : -1;
+            if (oc) oc[i] = i < R ? key_value((uint32_t)(cand[i] >> 32)) : 0.f;
+        }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_select_rows(const float *S, int64_t ld_s, int64_t n, int64_t rows,
-                               int64_t n_tgt_rows, int32_t r_tgt, int32_t k_lm,
-                               int32_t *tsel_idx, float *tsel_cos, int64_t tsel_row0,
-                               int32_t stride_t, int32_t *lsel_idx, int64_t lsel_row0,
-                               int32_t stride_l, cudaStream_t s)
+cudaError_t launch_select_rows_ex(const float *S, int64_t ld_s, int64_t n, int64_t rows, int64_t n_tgt_rows,
+                                  int32_t r_tgt, int32_t k_lm, int32_t *tsel_idx, float *tsel_cos, int64_t tsel_row0,
+                                  int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int64_t lsel_row0,
+                                  int32_t stride_l, cudaStream_t s)
 {
     if (rows <= 0) return cudaSuccess;
     if (r_tgt < 1 || r_tgt > SORT_MAX || r_tgt > n || k_lm < 1 || k_lm > kMaxAnchorCands ||
@@ -459,13 +410,23 @@ cudaError_t launch_select_rows(const float *S, int64_t ld_s, int64_t n, int64_t 
         if (e != cudaSuccess) return e;
         select_rows_smem_kernel<<<(unsigned)rows, TH, smem, s>>>(S, ld_s, (int32_t)n, n_tgt_rows, r_tgt, k_lm,
                                                                   tsel_idx, tsel_cos, tsel_row0, stride_t,
-                                                                  lsel_idx, lsel_row0, stride_l);
+                                                                  lsel_idx, lsel_cos, lsel_row0, stride_l);
     } else {
         select_rows_global_kernel<<<(unsigned)rows, TH, 0, s>>>(S, ld_s, (int32_t)n, n_tgt_rows, r_tgt, k_lm,
                                                                  tsel_idx, tsel_cos, tsel_row0, stride_t,
-                                                                 lsel_idx, lsel_row0, stride_l);
+                                                                 lsel_idx, lsel_cos, lsel_row0, stride_l);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_select_rows(const float *S, int64_t ld_s, int64_t n, int64_t rows,
+                               int64_t n_tgt_rows, int32_t r_tgt, int32_t k_lm,
+                               int32_t *tsel_idx, float *tsel_cos, int64_t tsel_row0,
+                               int32_t stride_t, int32_t *lsel_idx, int64_t lsel_row0,
+                               int32_t stride_l, cudaStream_t s)
+{
+    return launch_select_rows_ex(S, ld_s, n, rows, n_tgt_rows, r_tgt, k_lm, tsel_idx, tsel_cos, tsel_row0, stride_t,
+                                 lsel_idx, nullptr, lsel_row0, stride_l, s);
 }
 
 }  // namespace farm
