@@ -48,7 +48,13 @@ class _Scene(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile farm_oracle.c into a shared library (gcc, -O2, OpenMP)."""
+    """Compile farm_oracle.c into a shared library (gcc, -O2, OpenMP).
+
+    FARM_ORACLE_LIB names a prebuilt library to use instead (the mutation
+    tests point it at copies of the oracle with planted mistakes)."""
+    alt = os.environ.get("FARM_ORACLE_LIB")
+    if alt:
+        return alt
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):

@@ -1,0 +1,49 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/farm_oracle.c (on the CPU),
+compiles it, and runs the pin suite against it in a subprocess: the suite must
+fail.  A pin set that passes a planted mistake is not pinning that part.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "farm_oracle.c")
+
+MUTANTS = {
+    "above_sign": ("return orc_sigmoid(dz / p->tau_v);", "return orc_sigmoid(-dz / p->tau_v);"),
+    "near_width": ("exp(-d2 / (2.0 * p->sigma_near * p->sigma_near))", "exp(-d2 / (p->sigma_near * p->sigma_near))"),
+    "left_right_sign": ("acc += orc_sigmoid(sign * (ua - ue) / p->tau_h);",
+                        "acc += orc_sigmoid(sign * (ue - ua) / p->tau_h);"),
+    "view_validity_or": ("if (!(Ze > p->z_min && Za > p->z_min)) continue;",
+                         "if (!(Ze > p->z_min || Za > p->z_min)) continue;"),
+    "rank_tie_reversed": ("    return a < b;\n}", "    return a > b;\n}"),
+    "rank_off_by_one": ("ssem[j] = class_factor(s, p, c_t, j) / (p->mu + (double)rank[j]);",
+                        "ssem[j] = class_factor(s, p, c_t, j) / (p->mu + (double)rank[j] - 1.0);"),
+    "class_factor_inverted": ("return (c_t >= 0 && s->cls[j] != c_t) ? p->class_mis : 1.0;",
+                              "return (c_t >= 0 && s->cls[j] == c_t) ? p->class_mis : 1.0;"),
+    "landmark_may_be_target": ("                if (a == e) continue;\n                double r = orc_relation(s, p, preds[i], e, a);\n                if (arg < 0",
+                               "                double r = orc_relation(s, p, preds[i], e, a);\n                if (arg < 0"),
+    "product_not_geometric_mean": ("gbar = zero ? 0.0 : exp(lsum / (double)m);", "gbar = zero ? 0.0 : exp(lsum);"),
+    "full_product_not_blend": ("return s_sem * ((1.0 - p->w) + p->w * gbar);", "return s_sem * gbar;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    mutant = tmp_path / "mutant.c"
+    mutant.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(lib), str(mutant), "-lm"],
+                   check=True)
+    env = dict(os.environ, FARM_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins pass with mutant {name}:\n{r.stdout[-2000:]}"
