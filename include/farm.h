@@ -194,6 +194,13 @@ farm_status farm_topk(farm_ctx *ctx, uint64_t batch_handle, int32_t k, int32_t *
 farm_status farm_sync(farm_ctx *ctx);
 
 /*
+ * Object count n and descriptor length dim of an uploaded scene, for sizing
+ * the output of farm_similarity (n_rows x n floats).  Either pointer may be
+ * NULL.  FARM_EINVAL for a scene id that holds no scene.
+ */
+farm_status farm_scene_info(farm_ctx *ctx, int32_t scene_id, int64_t *n, int32_t *dim);
+
+/*
  * Cosine similarity of n_rows embeddings against every object of a scene,
  * computed by the kernels of `precision` (App. D.2 step 3; FARM_PREC_BF16 and
  * FARM_PREC_FP8 return the reduced-precision stage's approximate cosines):

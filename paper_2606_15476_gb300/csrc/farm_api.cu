@@ -28,6 +28,8 @@ struct farm_ctx {
     // pinned staging for per-batch metadata
     int32_t *h_stage = nullptr;
     size_t h_stage_n = 0;
+    farm::Piece *h_pieces = nullptr;  // pinned staging of the batch's piece tables
+    size_t h_pieces_n = 0;
     cudaEvent_t stage_done = nullptr;
     // profiling marks
     struct Mark { int stage; cudaEvent_t a, b; };
@@ -322,6 +324,7 @@ farm_status farm_destroy(farm_ctx *ctx)
     cudaFree(c.mlp.w2b);
     if (c.h_err) cudaFreeHost(c.h_err);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->h_pieces) cudaFreeHost(ctx->h_pieces);
     if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
     for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
@@ -639,21 +642,121 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             CK(ws_get(ctx, farm::B_BSEL_LV, (size_t)std::max<int64_t>(n_c, 1) * cstride_l, &bsel_lv));
         }
     }
-    int64_t max_ld = 0, max_rows = 0;
+    // ---- similarity batches: row ranges ("pieces") of the scene groups are
+    //      laid end to end in S while they fit kSimCapBytes; each batch takes
+    //      one similarity launch per piece and one grouped select (+ chunk
+    //      merge) (+ FP32 rescore) launch over all of its pieces
+    struct Batch { size_t p0 = 0, np = 0; int64_t s_floats = 0, rows = 0, blocks = 0, tmp = 0;
+                   int32_t smem_sel = 1, smem_merge = 0; bool chunked = false; };
+    std::vector<farm::Piece> pieces;
+    std::vector<int32_t> piece_sid;
+    std::vector<Batch> batches;
+    const bool reduced = reduced_precision(precision);
+    int32_t tmp_stride = 4;
     for (const auto &g : groups) {
-        const int64_t ld = round_up(c.scenes[g.sid].n, 32);
-        max_ld = std::max(max_ld, ld);
-        max_rows = std::max(max_rows, g.nq + g.nc);
+        const Scene &s = c.scenes[g.sid];
+        const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
+        const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
+        const int32_t kt = reduced ? reduced_keep_target(p, precision, Rs, s.n) : Rs;
+        const int32_t kl = reduced ? reduced_keep_landmark(p, precision, klm, s.n) : klm;
+        if (s.n > farm::kSelectRowMax) tmp_stride = std::max<int32_t>(tmp_stride, (int32_t)round_up(std::max(kt, kl), 4));
     }
-    const int64_t chunk_rows = std::max<int64_t>(1, std::min<int64_t>(max_rows, (int64_t)(kSimCapBytes / (max_ld * 4))));
-    float *d_sim;
-    CK(ws_get(ctx, farm::B_SIM, (size_t)chunk_rows * max_ld, &d_sim));
+    for (const auto &g : groups) {
+        const Scene &s = c.scenes[g.sid];
+        const int64_t ld = round_up(s.n, 32);
+        const int64_t rows_g = g.nq + g.nc;
+        const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
+        const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
+        const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows_g, (int64_t)(kSimCapBytes / (ld * 4))));
+        // long rows: column chunks of at most kSelectRowMax entries, merged after
+        int32_t chunks = 1, chunk_len = (int32_t)s.n;
+        bool global_select = false;
+        if (s.n > farm::kSelectRowMax) {
+            const int64_t c0 = (s.n + farm::kSelectRowMax - 1) / farm::kSelectRowMax;
+            chunk_len = (int32_t)round_up((s.n + c0 - 1) / c0, 32);
+            chunks = (int32_t)((s.n + chunk_len - 1) / chunk_len);
+            global_select = (int64_t)chunks * tmp_stride > farm::kSelectRowMax;
+        }
+        for (int64_t r0 = 0; r0 < rows_g; r0 += chunk) {
+            const int64_t r1 = std::min(rows_g, r0 + chunk);
+            const int64_t nr = r1 - r0;
+            if (batches.empty() || (batches.back().np > 0 && (batches.back().s_floats + nr * ld) * 4 > (int64_t)kSimCapBytes)) {
+                Batch bt;
+                bt.p0 = pieces.size();
+                batches.push_back(bt);
+            }
+            Batch &bt = batches.back();
+            farm::Piece pc{};
+            pc.d32 = s.desc32;
+            pc.s_off = bt.s_floats;
+            pc.row_begin = bt.rows;
+            pc.block_begin = bt.blocks;
+            pc.q_row0 = g.row0 + r0;
+            pc.ntr = (int32_t)std::max<int64_t>(0, std::min<int64_t>(g.nq - r0, nr));
+            pc.t_row0 = g.q0 + r0;
+            pc.l_row0 = g.cp0 + r0 + pc.ntr - g.nq;
+            pc.rows = (int32_t)nr;
+            pc.n = (int32_t)s.n;
+            pc.ld = (int32_t)ld;
+            pc.R = Rs;
+            pc.klm = klm;
+            pc.keep_t = reduced ? reduced_keep_target(p, precision, Rs, s.n) : Rs;
+            pc.keep_l = reduced ? reduced_keep_landmark(p, precision, klm, s.n) : klm;
+            pc.chunks = global_select ? 1 : chunks;
+            pc.chunk_len = global_select ? (int32_t)s.n : chunk_len;
+            pc.tmp_off = -1;
+            if (global_select) {
+                pc.chunks = 0;   // selected by the per-piece global-memory kernel; no grouped blocks
+            } else {
+                bt.blocks += nr * pc.chunks;
+                bt.smem_sel = std::max(bt.smem_sel, pc.chunk_len);
+                if (pc.chunks > 1) {
+                    pc.tmp_off = bt.tmp;
+                    bt.tmp += nr * pc.chunks * tmp_stride;
+                    bt.chunked = true;
+                    bt.smem_merge = std::max(bt.smem_merge, pc.chunks * tmp_stride);
+                }
+            }
+            bt.s_floats += nr * ld;
+            bt.rows += nr;
+            bt.np += 1;
+            pieces.push_back(pc);
+            piece_sid.push_back(g.sid);
+        }
+    }
+    int64_t s_need = 1, tmp_need = 4;
+    for (const auto &bt : batches) {
+        s_need = std::max(s_need, bt.s_floats);
+        tmp_need = std::max(tmp_need, bt.tmp);
+    }
+    float *d_sim, *tmp_val = nullptr;
+    int32_t *tmp_idx = nullptr;
+    farm::Piece *d_pieces;
+    CK(ws_get(ctx, farm::B_SIM, (size_t)s_need, &d_sim));
+    CK(ws_get(ctx, farm::B_PIECES, pieces.size(), &d_pieces));
+    bool any_chunked = false;
+    for (const auto &bt : batches) any_chunked |= bt.chunked;
+    if (any_chunked) {
+        CK(ws_get(ctx, farm::B_CHUNK_IDX, (size_t)tmp_need, &tmp_idx));
+        CK(ws_get(ctx, farm::B_CHUNK_VAL, (size_t)tmp_need, &tmp_val));
+    }
+    if (ctx->h_pieces_n < pieces.size()) {
+        if (ctx->h_pieces) cudaFreeHost(ctx->h_pieces);
+        ctx->h_pieces = nullptr;
+        ctx->h_pieces_n = 0;
+        CK(cudaHostAlloc(&ctx->h_pieces, pieces.size() * sizeof(farm::Piece) * 5 / 4 + sizeof(farm::Piece),
+                         cudaHostAllocDefault));
+        ctx->h_pieces_n = pieces.size() * 5 / 4 + 1;
+    }
+    std::memcpy(ctx->h_pieces, pieces.data(), pieces.size() * sizeof(farm::Piece));
 
     // ---- stage 0: inputs and normalisation
     const int m0 = mark_begin(ctx, 0);
     CK(cudaMemcpyAsync(d_rowmap, h_rowmap, (size_t)(n_q + n_c) * 4, cudaMemcpyHostToDevice, c.stream));
     CK(cudaMemcpyAsync(d_perm, h_perm, (size_t)n_q * 4, cudaMemcpyHostToDevice, c.stream));
     CK(cudaMemcpyAsync(d_meta, h_meta, (size_t)n_q * 8 * 4, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(d_pieces, ctx->h_pieces, pieces.size() * sizeof(farm::Piece), cudaMemcpyHostToDevice,
+                       c.stream));
     CK(cudaEventRecord(ctx->stage_done, c.stream));
     const float *src_t = tgt_emb, *src_c = c_emb;
     if (!dev) {
@@ -678,45 +781,42 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     }
     mark_end(ctx, m0);
 
-    // ---- stages 1-2: similarity and rank selection per scene group, in row chunks
-    for (const auto &g : groups) {
-        const Scene &s = c.scenes[g.sid];
-        const int64_t ld = round_up(s.n, 32);
-        const int64_t rows_g = g.nq + g.nc;
-        const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
-        const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
-        const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows_g, (int64_t)(kSimCapBytes / (ld * 4))));
-        for (int64_t r0 = 0; r0 < rows_g; r0 += chunk) {
-            const int64_t r1 = std::min(rows_g, r0 + chunk);
-            const int m1 = mark_begin(ctx, 1);
-            farm_status st = run_similarity(ctx, precision, ops, g.row0 + r0, r1 - r0, s, d_sim, ld);
+    // ---- stages 1-2: similarity per piece, then the batch's rank selection
+    int32_t *sel_ti = reduced ? bsel_t : tsel_idx, *sel_li = reduced ? bsel_l : lsel_idx;
+    float *sel_tc = reduced ? bsel_tv : tsel_cos, *sel_lc = reduced ? bsel_lv : nullptr;
+    const int32_t sel_st = reduced ? cstride_t : stride_t, sel_sl = reduced ? cstride_l : stride_l;
+    for (const auto &bt : batches) {
+        const int m1 = mark_begin(ctx, 1);
+        for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
+            const farm::Piece &pc = pieces[k];
+            farm_status st = run_similarity(ctx, precision, ops, pc.q_row0, pc.rows, c.scenes[piece_sid[k]],
+                                            d_sim + pc.s_off, pc.ld);
             if (st != FARM_OK) return st;
-            mark_end(ctx, m1);
-            const int64_t ntr = std::max<int64_t>(0, std::min<int64_t>(g.nq - r0, r1 - r0));
-            const int m2 = mark_begin(ctx, 2);
-            if (!reduced_precision(precision)) {
-                LAUNCH(farm::launch_select_rows(d_sim, ld, s.n, r1 - r0, ntr, Rs, klm, tsel_idx, tsel_cos,
-                                                g.q0 + r0, stride_t, lsel_idx, g.cp0 + r0 + ntr - g.nq, stride_l,
-                                                c.stream));
-            } else {
-                // the reduced-precision stage keeps C candidates per row; the FP32 rescore keeps R (or K_a)
-                const int32_t Ct = reduced_keep_target(p, precision, Rs, s.n);
-                const int32_t Cl = reduced_keep_landmark(p, precision, klm, s.n);
-                const int64_t lrow0 = g.cp0 + r0 + ntr - g.nq;
-                LAUNCH(farm::launch_select_rows_ex(d_sim, ld, s.n, r1 - r0, ntr, Ct, Cl, bsel_t, bsel_tv, g.q0 + r0,
-                                                   cstride_t, bsel_l, bsel_lv, lrow0, cstride_l, c.stream));
-                const float band = precision == FARM_PREC_FP8 ? 16.f * p.rescore_band : p.rescore_band;
-                if (ntr > 0)
-                    LAUNCH(farm::launch_rescore(ops.q32, g.row0 + r0, dim_pad, s.desc32, bsel_t, bsel_tv, band, Ct,
-                                                cstride_t, g.q0 + r0, ntr, Rs, tsel_idx, tsel_cos, stride_t,
-                                                g.q0 + r0, c.stream));
-                if (r1 - r0 - ntr > 0)
-                    LAUNCH(farm::launch_rescore(ops.q32, g.row0 + r0 + ntr, dim_pad, s.desc32, bsel_l, bsel_lv, band,
-                                                Cl, cstride_l, lrow0, r1 - r0 - ntr, klm, lsel_idx, nullptr, stride_l,
-                                                lrow0, c.stream));
-            }
-            mark_end(ctx, m2);
         }
+        mark_end(ctx, m1);
+        const int m2 = mark_begin(ctx, 2);
+        const farm::Piece *dp = d_pieces + bt.p0;
+        if (bt.blocks > 0)
+            LAUNCH(farm::launch_select_grouped(d_sim, dp, (int32_t)bt.np, bt.blocks, bt.smem_sel, sel_ti, sel_tc,
+                                               sel_st, sel_li, sel_lc, sel_sl, tmp_idx, tmp_val, tmp_stride,
+                                               c.stream));
+        if (bt.chunked)
+            LAUNCH(farm::launch_merge_chunks(dp, (int32_t)bt.np, bt.rows, bt.smem_merge, tmp_idx, tmp_val, tmp_stride,
+                                             sel_ti, sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.stream));
+        for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
+            const farm::Piece &pc = pieces[k];
+            if (pc.chunks != 0) continue;
+            LAUNCH(farm::launch_select_rows_ex(d_sim + pc.s_off, pc.ld, pc.n, pc.rows, pc.ntr, pc.keep_t, pc.keep_l,
+                                               sel_ti, sel_tc, pc.t_row0, sel_st, sel_li, sel_lc, pc.l_row0, sel_sl,
+                                               c.stream));
+        }
+        if (reduced) {
+            const float band = precision == FARM_PREC_FP8 ? 16.f * p.rescore_band : p.rescore_band;
+            LAUNCH(farm::launch_rescore_grouped(dp, (int32_t)bt.np, bt.rows, ops.q32, dim_pad, bsel_t, bsel_tv,
+                                                cstride_t, bsel_l, bsel_lv, cstride_l, band, tsel_idx, tsel_cos,
+                                                stride_t, lsel_idx, stride_l, c.stream));
+        }
+        mark_end(ctx, m2);
     }
 
     // ---- stage 3: relations, composite, sort
@@ -792,6 +892,17 @@ farm_status farm_sync(farm_ctx *ctx)
     if (!ctx) return FARM_EINVAL;
     CK(cudaSetDevice(ctx->c.device));
     return check_device_errors(ctx);
+}
+
+farm_status farm_scene_info(farm_ctx *ctx, int32_t scene_id, int64_t *n, int32_t *dim)
+{
+    if (!ctx) return FARM_EINVAL;
+    const Ctx &c = ctx->c;
+    if (scene_id < 0 || scene_id >= kMaxScenes || !c.scenes[scene_id].present)
+        return fail(ctx, FARM_EINVAL, "unknown scene");
+    if (n) *n = c.scenes[scene_id].n;
+    if (dim) *dim = c.scenes[scene_id].dim;
+    return FARM_OK;
 }
 
 farm_status farm_similarity(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb, int32_t precision,

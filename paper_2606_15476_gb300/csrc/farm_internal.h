@@ -84,6 +84,9 @@ enum Buf {
     B_MLP_AB,       // bf16 [chunk, H]
     B_MLP_Z,        // float [chunk, P]
     B_MLP_E,        // float [chunk, P]
+    B_PIECES,       // Piece tables of the batch's grouped launches
+    B_CHUNK_IDX,    // int32 chunk lists of long rows (select, then merge)
+    B_CHUNK_VAL,    // float their values
     B_COUNT
 };
 
@@ -223,6 +226,78 @@ cudaError_t launch_select_rows_ex(const float *S, int64_t ld_s, int64_t n, int64
                                   int32_t r_tgt, int32_t k_lm, int32_t *tsel_idx, float *tsel_cos, int64_t tsel_row0,
                                   int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int64_t lsel_row0,
                                   int32_t stride_l, cudaStream_t s);
+
+// One scene's block of rows within a grouped select / merge / rescore
+// launch.  The block's rows are rows [row_begin, row_begin + rows) of the
+// launch, stored at S + s_off with leading dimension ld; the first ntr are
+// target rows.  A row longer than the shared-memory limit is selected in
+// `chunks` column chunks of chunk_len entries, whose lists (tmp_stride
+// entries each, rows at tmp + tmp_off + i * chunks * tmp_stride) are merged
+// afterwards.  Pieces of a launch are ordered by row_begin and block_begin.
+struct Piece {
+    const float *d32;       // the scene's unit FP32 descriptors (rescore)
+    int64_t s_off;          // offset of the block's first row in S (floats)
+    int64_t row_begin;      // first launch row of the block
+    int64_t block_begin;    // first select block (rows x chunks before it)
+    int64_t q_row0;         // row of the block's first row in the normalised operand rows
+    int64_t t_row0;         // list row of the first target row
+    int64_t l_row0;         // list row of the first landmark row
+    int64_t tmp_off;        // chunk-list offset of the first row (entries)
+    int32_t rows, ntr, n, ld;
+    int32_t keep_t, keep_l; // list lengths the select keeps (R / K_a, or the rescore's C)
+    int32_t R, klm;         // list lengths after a rescore
+    int32_t chunks, chunk_len;
+};
+
+// Grouped select over `pieces` (device; n_pieces entries) in one launch of
+// total_blocks = sum of rows x chunks blocks.  Unchunked rows write their
+// lists to (t|l)sel_(idx|cos) rows t_row0 + i / l_row0 + i - ntr (strides
+// stride_t / stride_l; the cos pointers may be null); chunked rows write
+// their chunk lists to tmp_(idx|val).  smem_n: the longest row or chunk of
+// the launch, <= kSelectRowMax.  S + s_off and ld keep rows 16-byte aligned.
+cudaError_t launch_select_grouped(const float *S, const Piece *pieces, int32_t n_pieces, int64_t total_blocks,
+                                  int32_t smem_n, int32_t *tsel_idx, float *tsel_cos, int32_t stride_t,
+                                  int32_t *lsel_idx, float *lsel_cos, int32_t stride_l, int32_t *tmp_idx,
+                                  float *tmp_val, int32_t tmp_stride, cudaStream_t s);
+// Merge the chunk lists of chunked rows into their final lists (one block per
+// launch row; rows of unchunked pieces return at once).  smem_n: the longest
+// merged list, chunks x tmp_stride, <= kSelectRowMax.
+cudaError_t launch_merge_chunks(const Piece *pieces, int32_t n_pieces, int64_t total_rows, int32_t smem_n,
+                                const int32_t *tmp_idx, const float *tmp_val, int32_t tmp_stride,
+                                int32_t *tsel_idx, float *tsel_cos, int32_t stride_t, int32_t *lsel_idx,
+                                float *lsel_cos, int32_t stride_l, cudaStream_t s);
+// Grouped FP32 rescore (one block per launch row): the keep_t / keep_l
+// candidates of bsel_* (strides cstride_t / cstride_l; values nullable, then
+// no band skip) against the normalised rows Q32 -> the R / klm best in rank
+// order into tsel_idx / tsel_cos and lsel_idx.
+cudaError_t launch_rescore_grouped(const Piece *pieces, int32_t n_pieces, int64_t total_rows, const float *Q32,
+                                   int32_t dim_pad, const int32_t *bsel_t, const float *bsel_tv, int32_t cstride_t,
+                                   const int32_t *bsel_l, const float *bsel_lv, int32_t cstride_l, float band,
+                                   int32_t *tsel_idx, float *tsel_cos, int32_t stride_t, int32_t *lsel_idx,
+                                   int32_t stride_l, cudaStream_t s);
+constexpr int kSelectRowMax = 24576;    // longest row the shared-memory select stages
+
+#ifdef __CUDACC__
+// The last piece whose begin(piece) <= b, for a table ordered by that field
+// (binary search by thread 0, broadcast through shared memory; every thread
+// of the block must call it).
+template <class F>
+__device__ __forceinline__ int find_piece(const Piece *pieces, int n_pieces, int64_t b, F begin)
+{
+    __shared__ int s_piece;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_pieces - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (begin(pieces[mid]) <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        s_piece = lo;
+    }
+    __syncthreads();
+    return s_piece;
+}
+#endif
 
 // Device-side view of one scene, indexed by scene id in a device table.
 struct SceneDev {

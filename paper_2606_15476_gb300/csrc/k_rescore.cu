@@ -35,22 +35,20 @@ __device__ __forceinline__ float key_value(uint32_t k)
     return __uint_as_float(u);
 }
 
-__global__ void __launch_bounds__(TH)
-rescore_kernel(const float *__restrict__ Q32, int64_t q_row0, int32_t dim_pad, const float *__restrict__ D32,
-               const int32_t *__restrict__ cand, const float *__restrict__ cand_val, float band, int32_t C,
-               int32_t cand_stride, int64_t cand_row0, int32_t R, int32_t *__restrict__ out_idx,
-               float *__restrict__ out_cos, int32_t out_stride, int64_t out_row0)
+// One row: the C candidates cr (values cv, nullable) against the unit row q
+// (global, dim_pad floats) -> the R best in rank order into oi / oc.
+__device__ __forceinline__ void rescore_row(const float *__restrict__ q, int32_t dim_pad,
+                                            const float *__restrict__ D32, const int32_t *__restrict__ cr,
+                                            const float *__restrict__ cv, float band, int32_t C, int32_t R,
+                                            int32_t *__restrict__ oi, float *__restrict__ oc, int32_t out_stride)
 {
     extern __shared__ float4 q4[];
     __shared__ uint64_t key[SORT_MAX];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t r = blockIdx.x;
     const int nv = dim_pad / 4;
-    const float4 *src = reinterpret_cast<const float4 *>(Q32 + (q_row0 + r) * (int64_t)dim_pad);
+    const float4 *src = reinterpret_cast<const float4 *>(q);
     for (int i = tid; i < nv; i += TH) q4[i] = src[i];
     __syncthreads();
-    const int32_t *cr = cand + (cand_row0 + r) * (int64_t)cand_stride;
-    const float *cv = cand_val ? cand_val + (cand_row0 + r) * (int64_t)cand_stride : nullptr;
     const float thr = cv ? cv[R - 1] - band : 0.f;
     for (int c = warp; c < C; c += TH / 32) {
         if (cv && cv[c] < thr) {
@@ -88,8 +86,6 @@ rescore_kernel(const float *__restrict__ Q32, int64_t q_row0, int32_t dim_pad, c
             __syncthreads();
         }
     }
-    int32_t *oi = out_idx + (out_row0 + r) * (int64_t)out_stride;
-    float *oc = out_cos ? out_cos + (out_row0 + r) * (int64_t)out_stride : nullptr;
     for (int i = tid; i < out_stride; i += TH) {
         if (i < R) {
             oi[i] = (int32_t)(0xffffffffu - (uint32_t)(key[i] & 0xffffffffu));
@@ -98,6 +94,42 @@ rescore_kernel(const float *__restrict__ Q32, int64_t q_row0, int32_t dim_pad, c
             oi[i] = -1;
             if (oc) oc[i] = 0.f;
         }
+    }
+}
+
+__global__ void __launch_bounds__(TH)
+rescore_kernel(const float *__restrict__ Q32, int64_t q_row0, int32_t dim_pad, const float *__restrict__ D32,
+               const int32_t *__restrict__ cand, const float *__restrict__ cand_val, float band, int32_t C,
+               int32_t cand_stride, int64_t cand_row0, int32_t R, int32_t *__restrict__ out_idx,
+               float *__restrict__ out_cos, int32_t out_stride, int64_t out_row0)
+{
+    const int64_t r = blockIdx.x;
+    const int64_t co = (cand_row0 + r) * (int64_t)cand_stride, oo = (out_row0 + r) * (int64_t)out_stride;
+    rescore_row(Q32 + (q_row0 + r) * (int64_t)dim_pad, dim_pad, D32, cand + co, cand_val ? cand_val + co : nullptr,
+                band, C, R, out_idx + oo, out_cos ? out_cos + oo : nullptr, out_stride);
+}
+
+// Grouped rescore: block -> (piece, row) through the piece table.
+__global__ void __launch_bounds__(TH)
+rescore_grouped_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, const float *__restrict__ Q32,
+                       int32_t dim_pad, const int32_t *__restrict__ bsel_t, const float *__restrict__ bsel_tv,
+                       int32_t cstride_t, const int32_t *__restrict__ bsel_l, const float *__restrict__ bsel_lv,
+                       int32_t cstride_l, float band, int32_t *__restrict__ tsel_idx, float *__restrict__ tsel_cos,
+                       int32_t stride_t, int32_t *__restrict__ lsel_idx, int32_t stride_l)
+{
+    const int64_t r = blockIdx.x;
+    const Piece pc = pieces[find_piece(pieces, n_pieces, r, [](const Piece &x) { return x.row_begin; })];
+    const int i = (int)(r - pc.row_begin);
+    const float *q = Q32 + (pc.q_row0 + i) * (int64_t)dim_pad;
+    if (i < pc.ntr) {
+        const int64_t co = (pc.t_row0 + i) * (int64_t)cstride_t, oo = (pc.t_row0 + i) * (int64_t)stride_t;
+        rescore_row(q, dim_pad, pc.d32, bsel_t + co, bsel_tv ? bsel_tv + co : nullptr, band, pc.keep_t, pc.R,
+                    tsel_idx + oo, tsel_cos ? tsel_cos + oo : nullptr, stride_t);
+    } else {
+        const int64_t l = pc.l_row0 + (i - pc.ntr);
+        const int64_t co = l * (int64_t)cstride_l;
+        rescore_row(q, dim_pad, pc.d32, bsel_l + co, bsel_lv ? bsel_lv + co : nullptr, band, pc.keep_l, pc.klm,
+                    lsel_idx + l * (int64_t)stride_l, nullptr, stride_l);
     }
 }
 
@@ -117,6 +149,27 @@ cudaError_t launch_rescore(const float *Q32, int64_t q_row0, int32_t dim_pad, co
     }
     rescore_kernel<<<(unsigned)rows, TH, smem, s>>>(Q32, q_row0, dim_pad, D32, cand, cand_val, band, C, cand_stride,
                                                     cand_row0, R, out_idx, out_cos, out_stride, out_row0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescore_grouped(const Piece *pieces, int32_t n_pieces, int64_t total_rows, const float *Q32,
+                                   int32_t dim_pad, const int32_t *bsel_t, const float *bsel_tv, int32_t cstride_t,
+                                   const int32_t *bsel_l, const float *bsel_lv, int32_t cstride_l, float band,
+                                   int32_t *tsel_idx, float *tsel_cos, int32_t stride_t, int32_t *lsel_idx,
+                                   int32_t stride_l, cudaStream_t s)
+{
+    if (total_rows <= 0) return cudaSuccess;
+    if (n_pieces < 1 || total_rows > 0x7fffffff || dim_pad % 4 != 0 || cstride_t > SORT_MAX || cstride_l > SORT_MAX)
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)dim_pad * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(rescore_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    rescore_grouped_kernel<<<(unsigned)total_rows, TH, smem, s>>>(pieces, n_pieces, Q32, dim_pad, bsel_t, bsel_tv,
+                                                                  cstride_t, bsel_l, bsel_lv, cstride_l, band,
+                                                                  tsel_idx, tsel_cos, stride_t, lsel_idx, stride_l);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ namespace {
 
 constexpr int TH = 512;
 constexpr int SORT_MAX = kMaxTargetCands;   // >= kMaxAnchorCands
-constexpr int kRowSmemMax = 24576;          // entries staged in shared memory (96 KB)
+constexpr int kRowSmemMax = kSelectRowMax;  // entries staged in shared memory (96 KB)
 
 __device__ __forceinline__ uint32_t order_key(float f)
 {
@@ -37,6 +37,26 @@ __device__ __forceinline__ float key_value(uint32_t k)
 {
     const uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
     return __uint_as_float(u);
+}
+
+// Rank-ordered (key, ~position) list -> indices / values [0, stride); the
+// object index of position p is idx_map[p] when idx_map is given, else
+// idx_base + p.  Entries past R hold index -1 and value pad.
+__device__ __forceinline__ void write_list(const uint64_t *cand, int R, int32_t idx_base,
+                                           const int32_t *__restrict__ idx_map, int32_t *__restrict__ oi,
+                                           float *__restrict__ oc, int stride, float pad)
+{
+    for (int i = threadIdx.x; i < stride; i += TH) {
+        if (i < R) {
+            const uint64_t c = cand[i];
+            const int32_t pos = (int32_t)(0xffffffffu - (uint32_t)(c & 0xffffffffu));
+            oi[i] = idx_map ? idx_map[pos] : idx_base + pos;
+            if (oc) oc[i] = key_value((uint32_t)(c >> 32));
+        } else {
+            oi[i] = -1;
+            if (oc) oc[i] = pad;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(TH)
@@ -152,25 +172,12 @@ select_rows_global_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, 
         }
     }
     if (is_tgt) {
-        int32_t *oi = tsel_idx + (tsel_row0 + r) * (int64_t)stride_t;
-        float *oc = tsel_cos ? tsel_cos + (tsel_row0 + r) * (int64_t)stride_t : nullptr;
-        for (int i = tid; i < stride_t; i += TH) {
-            if (i < R) {
-                const uint64_t c = cand[i];
-                oi[i] = (int32_t)(0xffffffffu - (uint32_t)(c & 0xffffffffu));
-                if (oc) oc[i] = key_value((uint32_t)(c >> 32));
-            } else {
-                oi[i] = -1;
-                if (oc) oc[i] = 0.f;
-            }
-        }
+        write_list(cand, R, 0, nullptr, tsel_idx + (tsel_row0 + r) * (int64_t)stride_t,
+                   tsel_cos ? tsel_cos + (tsel_row0 + r) * (int64_t)stride_t : nullptr, stride_t, 0.f);
     } else {
-        int32_t *oi = lsel_idx + (lsel_row0 + (r - n_tgt_rows)) * (int64_t)stride_l;
-        float *oc = lsel_cos ? lsel_cos + (lsel_row0 + (r - n_tgt_rows)) * (int64_t)stride_l : nullptr;
-        for (int i = tid; i < stride_l; i += TH) {
-            oi[i] = i < R ? (int32_t)(0xffffffffu - (uint32_t)(cand[i] & 0xffffffffu)) : -1;
-            if (oc) oc[i] = i < R ? key_value((uint32_t)(cand[i] >> 32)) : 0.f;
-        }
+        const int64_t l = lsel_row0 + (r - n_tgt_rows);
+        write_list(cand, R, 0, nullptr, lsel_idx + l * (int64_t)stride_l,
+                   lsel_cos ? lsel_cos + l * (int64_t)stride_l : nullptr, stride_l, 0.f);
     }
 }
 
@@ -240,12 +247,15 @@ __device__ __forceinline__ void bitonic_desc(uint64_t *cand, int P)
 
 constexpr int kVecHalf = kRowSmemMax / 8 / TH;   // float4 loads per thread per batch (two batches)
 
-__global__ void __launch_bounds__(TH, 2)
-select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, int64_t n_tgt_rows,
-                        int32_t r_tgt, int32_t k_lm, int32_t *__restrict__ tsel_idx,
-                        float *__restrict__ tsel_cos, int64_t tsel_row0, int32_t stride_t,
-                        int32_t *__restrict__ lsel_idx, float *__restrict__ lsel_cos, int64_t lsel_row0,
-                   int32_t stride_l)
+// The R largest entries of one row (n <= kRowSmemMax, `row` 16-byte
+// aligned) staged in shared memory (`keys`, dynamic), written in rank order
+// to oi / oc (nullable) [0, out_stride) as write_list maps positions.  Among
+// equal values the lower position comes first, so a row whose position order
+// agrees with object-index order among equal values (a row of S, or chunk
+// lists laid end to end) yields the rank order of the definition.
+__device__ __forceinline__ void select_row_smem(const float *__restrict__ row, int n, int R, int32_t idx_base,
+                                                const int32_t *__restrict__ idx_map, int32_t *__restrict__ oi,
+                                                float *__restrict__ oc, int out_stride, float pad)
 {
     extern __shared__ uint32_t keys[];
     __shared__ uint32_t hist[2048];
@@ -255,10 +265,6 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
     __shared__ int s_app, s_warp[TH / 32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t r = blockIdx.x;
-    const float *row = S + r * ld_s;
-    const bool is_tgt = r < n_tgt_rows;
-    const int R = is_tgt ? r_tgt : k_lm;
     const int n4 = n & ~3;
 
     // issue the row's loads in two batches of kVecHalf float4 per thread, then
@@ -369,27 +375,90 @@ select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, in
     while (P < R) P <<= 1;
     for (int i = R + tid; i < P; i += TH) cand[i] = 0ull;
     bitonic_desc(cand, P);
+    write_list(cand, R, idx_base, idx_map, oi, oc, out_stride, pad);
+    __syncthreads();   // the shared arrays are reused by the block's next call
+}
+
+__global__ void __launch_bounds__(TH, 2)
+select_rows_smem_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, int64_t n_tgt_rows,
+                        int32_t r_tgt, int32_t k_lm, int32_t *__restrict__ tsel_idx,
+                        float *__restrict__ tsel_cos, int64_t tsel_row0, int32_t stride_t,
+                        int32_t *__restrict__ lsel_idx, float *__restrict__ lsel_cos, int64_t lsel_row0,
+                        int32_t stride_l)
+{
+    const int64_t r = blockIdx.x;
+    const bool is_tgt = r < n_tgt_rows;
     if (is_tgt) {
-        int32_t *oi = tsel_idx + (tsel_row0 + r) * (int64_t)stride_t;
-        float *oc = tsel_cos ? tsel_cos + (tsel_row0 + r) * (int64_t)stride_t : nullptr;
-        for (int i = tid; i < stride_t; i += TH) {
-            if (i < R) {
-                const uint64_t c = cand[i];
-                oi[i] = (int32_t)(0xffffffffu - (uint32_t)(c & 0xffffffffu));
-                if (oc) oc[i] = key_value((uint32_t)(c >> 32));
-            } else {
-                oi[i] = -1;
-                if (oc) oc[i] = 0.f;
-            }
+        select_row_smem(S + r * ld_s, n, r_tgt, 0, nullptr, tsel_idx + (tsel_row0 + r) * (int64_t)stride_t,
+                        tsel_cos ? tsel_cos + (tsel_row0 + r) * (int64_t)stride_t : nullptr, stride_t, 0.f);
+    } else {
+        const int64_t l = lsel_row0 + (r - n_tgt_rows);
+        select_row_smem(S + r * ld_s, n, k_lm, 0, nullptr, lsel_idx + l * (int64_t)stride_l,
+                        lsel_cos ? lsel_cos + l * (int64_t)stride_l : nullptr, stride_l, 0.f);
+    }
+}
+
+// Grouped select: block -> (piece, row, chunk) through the piece table.
+__global__ void __launch_bounds__(TH, 2)
+select_grouped_kernel(const float *__restrict__ S, const Piece *__restrict__ pieces, int32_t n_pieces,
+                      int32_t *__restrict__ tsel_idx, float *__restrict__ tsel_cos, int32_t stride_t,
+                      int32_t *__restrict__ lsel_idx, float *__restrict__ lsel_cos, int32_t stride_l,
+                      int32_t *__restrict__ tmp_idx, float *__restrict__ tmp_val, int32_t tmp_stride)
+{
+    const int64_t b = blockIdx.x;
+    const Piece pc = pieces[find_piece(pieces, n_pieces, b, [](const Piece &x) { return x.block_begin; })];
+    const int64_t local = b - pc.block_begin;
+    const int i = (int)(local / pc.chunks), c = (int)(local % pc.chunks);
+    const bool is_tgt = i < pc.ntr;
+    const int R = is_tgt ? pc.keep_t : pc.keep_l;
+    const float *row = S + pc.s_off + (int64_t)i * pc.ld;
+    if (pc.chunks == 1) {
+        if (is_tgt) {
+            const int64_t o = (pc.t_row0 + i) * (int64_t)stride_t;
+            select_row_smem(row, pc.n, R, 0, nullptr, tsel_idx + o, tsel_cos ? tsel_cos + o : nullptr, stride_t, 0.f);
+        } else {
+            const int64_t o = (pc.l_row0 + (i - pc.ntr)) * (int64_t)stride_l;
+            select_row_smem(row, pc.n, R, 0, nullptr, lsel_idx + o, lsel_cos ? lsel_cos + o : nullptr, stride_l, 0.f);
         }
     } else {
-        int32_t *oi = lsel_idx + (lsel_row0 + (r - n_tgt_rows)) * (int64_t)stride_l;
-        float *oc = lsel_cos ? lsel_cos + (lsel_row0 + (r - n_tgt_rows)) * (int64_t)stride_l : nullptr;
-        for (int i = tid; i < stride_l; i += TH) {
-            oi[i] = i < R ? (int32_t)(0xffffffffu - (uint32_t)(cand[i] & 0xffffffffu)) : -1;
-            if (oc) oc[i] = i < R ? key_value((uint32_t)(cand[i] >> 32)) : 0.f;
-        }
+        const int c0 = c * pc.chunk_len;
+        const int len = min(pc.chunk_len, pc.n - c0);
+        const int64_t o = pc.tmp_off + ((int64_t)i * pc.chunks + c) * tmp_stride;
+        select_row_smem(row + c0, len, min(R, len), c0, nullptr, tmp_idx + o, tmp_val + o, tmp_stride,
+                        -__int_as_float(0x7f800000));
     }
+}
+
+// Merge of a chunked row: its chunk lists, laid end to end in chunk order,
+// list equal values in object-index order, so a select over them with
+// position -> index through tmp_idx gives the row's rank order.
+__global__ void __launch_bounds__(TH, 2)
+merge_chunks_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, const int32_t *__restrict__ tmp_idx,
+                    const float *__restrict__ tmp_val, int32_t tmp_stride, int32_t *__restrict__ tsel_idx,
+                    float *__restrict__ tsel_cos, int32_t stride_t, int32_t *__restrict__ lsel_idx,
+                    float *__restrict__ lsel_cos, int32_t stride_l)
+{
+    const int64_t r = blockIdx.x;
+    const Piece pc = pieces[find_piece(pieces, n_pieces, r, [](const Piece &x) { return x.row_begin; })];
+    if (pc.chunks <= 1) return;   // unchunked rows (1) and rows of the global-memory select (0)
+    const int i = (int)(r - pc.row_begin);
+    const int M = pc.chunks * tmp_stride;
+    const int64_t o = pc.tmp_off + (int64_t)i * M;
+    if (i < pc.ntr) {
+        const int64_t w = (pc.t_row0 + i) * (int64_t)stride_t;
+        select_row_smem(tmp_val + o, M, pc.keep_t, 0, tmp_idx + o, tsel_idx + w, tsel_cos ? tsel_cos + w : nullptr,
+                        stride_t, 0.f);
+    } else {
+        const int64_t w = (pc.l_row0 + (i - pc.ntr)) * (int64_t)stride_l;
+        select_row_smem(tmp_val + o, M, pc.keep_l, 0, tmp_idx + o, lsel_idx + w, lsel_cos ? lsel_cos + w : nullptr,
+                        stride_l, 0.f);
+    }
+}
+
+cudaError_t set_smem(const void *fn, int32_t smem_n, size_t *bytes)
+{
+    *bytes = (size_t)((smem_n + 3) & ~3) * sizeof(uint32_t);
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes);
 }
 
 }  // namespace
@@ -427,6 +496,41 @@ cudaError_t launch_select_rows(const float *S, int64_t ld_s, int64_t n, int64_t 
 {
     return launch_select_rows_ex(S, ld_s, n, rows, n_tgt_rows, r_tgt, k_lm, tsel_idx, tsel_cos, tsel_row0, stride_t,
                                  lsel_idx, nullptr, lsel_row0, stride_l, s);
+}
+
+cudaError_t launch_select_grouped(const float *S, const Piece *pieces, int32_t n_pieces, int64_t total_blocks,
+                                  int32_t smem_n, int32_t *tsel_idx, float *tsel_cos, int32_t stride_t,
+                                  int32_t *lsel_idx, float *lsel_cos, int32_t stride_l, int32_t *tmp_idx,
+                                  float *tmp_val, int32_t tmp_stride, cudaStream_t s)
+{
+    if (total_blocks <= 0) return cudaSuccess;
+    if (n_pieces < 1 || smem_n < 1 || smem_n > kRowSmemMax || total_blocks > 0x7fffffff || (tmp_stride & 3) != 0 ||
+        ((uintptr_t)S & 15u) != 0)
+        return cudaErrorInvalidValue;
+    size_t smem = 0;
+    cudaError_t e = set_smem((const void *)select_grouped_kernel, smem_n, &smem);
+    if (e != cudaSuccess) return e;
+    select_grouped_kernel<<<(unsigned)total_blocks, TH, smem, s>>>(S, pieces, n_pieces, tsel_idx, tsel_cos,
+                                                                   stride_t, lsel_idx, lsel_cos, stride_l, tmp_idx,
+                                                                   tmp_val, tmp_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_chunks(const Piece *pieces, int32_t n_pieces, int64_t total_rows, int32_t smem_n,
+                                const int32_t *tmp_idx, const float *tmp_val, int32_t tmp_stride,
+                                int32_t *tsel_idx, float *tsel_cos, int32_t stride_t, int32_t *lsel_idx,
+                                float *lsel_cos, int32_t stride_l, cudaStream_t s)
+{
+    if (total_rows <= 0) return cudaSuccess;
+    if (n_pieces < 1 || smem_n < 1 || smem_n > kRowSmemMax || total_rows > 0x7fffffff || (tmp_stride & 3) != 0)
+        return cudaErrorInvalidValue;
+    size_t smem = 0;
+    cudaError_t e = set_smem((const void *)merge_chunks_kernel, smem_n, &smem);
+    if (e != cudaSuccess) return e;
+    merge_chunks_kernel<<<(unsigned)total_rows, TH, smem, s>>>(pieces, n_pieces, tmp_idx, tmp_val, tmp_stride,
+                                                               tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos,
+                                                               stride_l);
+    return cudaGetLastError();
 }
 
 }  // namespace farm

@@ -476,7 +476,10 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     using M = Mode<MODE>;
     constexpr bool TWO = MODE != kTf32x3;
     if (rows <= 0 || n <= 0) return cudaSuccess;
-    if (dim_pad % M::BK != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    // rows are padded to kDimAlign (64) elements; the FP8 K slice (128 bytes)
+    // may run past the row end, where the tensor map's bounds fill zeros
+    if (dim_pad % kDimAlign != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const int k_blocks = (dim_pad + M::BK - 1) / M::BK;
     if (!get_encoder()) return cudaErrorNotSupported;
     // TMA: 16-byte aligned bases; row strides are multiples of 16 bytes (dim_pad % 64 == 0)
     const uintptr_t al = (uintptr_t)q0 | (uintptr_t)d0 | (TWO ? 0 : ((uintptr_t)q1 | (uintptr_t)d1));
@@ -499,7 +502,7 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<int64_t>(tiles, std::max(num_sms, 1));
     sim_tc_kernel<MODE><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(mq0, mq1, md0, md1, S, rows, n,
-                                                                       dim_pad / M::BK, ld_s, m_tiles, n_tiles,
+                                                                       k_blocks, ld_s, m_tiles, n_tiles,
                                                                        scale_q, scale_d, err);
     return cudaGetLastError();
 }

@@ -53,6 +53,7 @@ def _load():
         "farm_topk": (C.c_int, [P, U64, I32, P, P, P, P, U32]),
         "farm_sync": (C.c_int, [P]),
         "farm_similarity": (C.c_int, [P, I32, I64, P, I32, P, U32]),
+        "farm_scene_info": (C.c_int, [P, I32, P, P]),
         "farm_candidates": (C.c_int, [P, U64, P, P, P, P]),
         "farm_rank_rows_noalloc": (C.c_int, [P, I32, I64, P, I32, I32, P, P]),
         "farm_mlp_set": (C.c_int, [P, I32, I32, I32, P, P, P, P]),
@@ -77,7 +78,8 @@ _lib = _load()
 
 def exported_symbols():
     return ["farm_default_params", "farm_create", "farm_destroy", "farm_memory_upload",
-            "farm_query_batch", "farm_topk", "farm_sync", "farm_similarity", "farm_candidates",
+            "farm_query_batch", "farm_topk", "farm_sync", "farm_similarity", "farm_scene_info",
+            "farm_candidates",
             "farm_rank_rows_noalloc", "farm_mlp_set", "farm_mlp_get", "farm_mlp_loss_grad",
             "farm_mlp_train", "farm_mlp_embed", "farm_set_profiling", "farm_stage_times",
             "farm_last_error", "farm_version"]
@@ -209,11 +211,31 @@ def farm_sync(ctx) -> None:
     _ck(ctx, _lib.farm_sync(ctx))
 
 
+def farm_scene_info(ctx, scene_id: int):
+    """(n, dim) of an uploaded scene."""
+    n = C.c_int64()
+    dim = C.c_int32()
+    _ck(ctx, _lib.farm_scene_info(ctx, int(scene_id), C.byref(n), C.byref(dim)))
+    return int(n.value), int(dim.value)
+
+
 def farm_similarity(ctx, scene_id: int, emb, n: int, precision: int = PREC_FP32, out=None):
+    """Cosines [rows, n] of `emb` against scene `scene_id`; n must be the
+    scene's object count (checked against the library's record)."""
     e = _Arr(emb, np.float32, "emb")
     rows = int(emb.shape[0])
+    n_scene, _ = farm_scene_info(ctx, scene_id)
+    if int(n) != n_scene:
+        raise FarmError(1, f"n = {n} but scene {scene_id} holds {n_scene} objects")
     if out is None:
         out = np.zeros((rows, n), np.float32)
+    if _is_cuda_tensor(out):
+        import torch
+        ok = out.dtype == torch.float32 and out.is_contiguous()
+    else:
+        ok = isinstance(out, np.ndarray) and out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
+    if not ok or tuple(out.shape) != (rows, n):
+        raise FarmError(1, f"out must be a contiguous FP32 array of shape ({rows}, {n})")
     dev = _is_cuda_tensor(out)
     if dev != e.device:
         raise FarmError(1, "emb and out must both be host or both be device")

@@ -1,0 +1,161 @@
+"""GPU: the grouped rank selection (one launch over every scene piece of a
+batch) and the column-chunked selection of rows longer than 24,576 objects
+(per-chunk lists, then a merge), against the FP64 oracle.
+
+Scene sizes straddle the chunking limit: 24,576 objects (one chunk, the
+largest row staged whole), 24,577 (two chunks, ragged) and 61,003 (three
+chunks, ragged, not a multiple of 32), next to small scenes, with the
+queries of all scenes interleaved in one batch.  Duplicated descriptor rows
+put exact cosine ties on both sides of every chunk boundary, where the rank
+order must still take the lower object index first.
+"""
+import numpy as np
+import pytest
+
+from oracle import parity
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DIM = 64
+SIZES = {30: 61003, 31: 300, 32: 24577, 33: 24576, 34: 57}
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2606_15476_gb300 as F
+    return F
+
+
+def _scene_with_ties(sid, n):
+    sc = synth.make_scene(sid, n, DIM, extent=(30.0, 30.0, 4.0), n_classes=8, n_views=3)
+    if n > 1000:
+        # copy a few rows onto indices on the far side of the chunk boundaries
+        rng = np.random.default_rng(sid)
+        src = rng.choice(n // 3, size=24, replace=False)
+        dst = n - 1 - rng.choice(n // 3, size=24, replace=False)
+        sc.desc[dst] = sc.desc[src]
+        mid = n // 2
+        sc.desc[mid - 3:mid + 3] = sc.desc[7]
+    return sc
+
+
+@pytest.fixture(scope="module")
+def world(F):
+    ctx = F.farm_create(0)
+    scenes = {}
+    parts = []
+    for sid, n in SIZES.items():
+        sc = _scene_with_ties(sid, n)
+        F.farm_memory_upload(ctx, sid, sc.desc, sc.cls, sc.box, sc.views)
+        scenes[sid] = sc
+        nq = 24 if n > 1000 else 12
+        qb = synth.make_queries(sid + 700, sc, nq, m_choices=(0, 1, 2, 3, 4), scene_id=sid)
+        if n > 1000:
+            # targets that are exactly a duplicated descriptor: tied top ranks
+            qb.tgt_emb[:3] = sc.desc[[7, n // 2, n - 1]]
+        parts.append(qb)
+    qb = synth.scenes.concat_batches(parts)
+    qb = qb.subset(np.random.default_rng(5).permutation(qb.n_q))
+    yield ctx, scenes, qb
+    F.farm_destroy(ctx)
+
+
+def _run(F, ctx, qb, prec, k=10):
+    h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred,
+                           qb.c_emb, prec)
+    return h, F.farm_topk(ctx, h, k, qb.n_q)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_simt"])
+def test_mixed_batch_matches_oracle(F, world, prec):
+    ctx, scenes, qb = world
+    code = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT}[prec]
+    h, out = _run(F, ctx, qb, code)
+    t, l = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
+    for sid, sc in scenes.items():
+        qs = np.flatnonzero(qb.scene_of_q == sid)
+        sub = qb.subset(qs)
+        k = min(10, sc.n)
+        rep = parity.check_topk(sc, sub, k, out["idx"][qs, :k], out["score"][qs, :k],
+                                out["pred"][qs, :k], out["anchor"][qs, :k])
+        assert rep.ok(), (sid, rep.summary())
+        cq = np.concatenate([np.arange(qb.c_off[q], qb.c_off[q + 1]) for q in qs]).astype(np.int64)
+        fails = parity.check_candidates(sc, sub, t[qs], l[cq] if cq.size else l[:0])
+        assert not fails, (sid, fails[:3])
+
+
+def test_chunked_rows_list_ties_in_index_order(F, world):
+    """Rows whose leading ranks are exact ties spread over several chunks."""
+    ctx, scenes, qb = world
+    h, _ = _run(F, ctx, qb, F.PREC_FP32)
+    t, _ = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
+    checked = 0
+    for q in range(qb.n_q):
+        sc = scenes[int(qb.scene_of_q[q])]
+        if sc.n <= 1000:
+            continue
+        u = qb.tgt_emb[q]
+        for j in (7, sc.n // 2, sc.n - 1):
+            if np.array_equal(u, sc.desc[j]):
+                # every object with this exact descriptor, in index order, heads the list
+                same = np.flatnonzero(np.all(sc.desc == sc.desc[j], axis=1))
+                assert t[q, :same.size].tolist() == same.tolist(), (q, j)
+                checked += 1
+    assert checked >= 6
+
+
+def test_bf16_on_mixed_batch(F, world):
+    """BF16 through the grouped select and grouped rescore: the same TopK as
+    the FP32 path (Recall@10 >= 0.99 over the batch)."""
+    ctx, scenes, qb = world
+    _, ref = _run(F, ctx, qb, F.PREC_FP32)
+    _, out = _run(F, ctx, qb, F.PREC_BF16)
+    hits = total = 0
+    for q in range(qb.n_q):
+        k = min(10, scenes[int(qb.scene_of_q[q])].n)
+        hits += len(set(ref["idx"][q, :k].tolist()) & set(out["idx"][q, :k].tolist()))
+        total += k
+    assert hits / total >= 0.99, hits / total
+    assert np.all(np.diff(out["score"], axis=1) <= 0)
+
+
+def test_fp8_lists_are_in_exact_rank_order(F, world):
+    """FP8 through the grouped launches.  In these scenes the leading 512
+    cosines of a row span well under 0.01 while E4M3 operands at dim 64 err
+    by up to about 0.03, so the FP8 stage cannot find the FP32 top ranks
+    (recall is not asserted); what the grouped FP32 rescore guarantees is
+    checked instead: every list holds distinct objects in exact-cosine rank
+    order."""
+    ctx, scenes, qb = world
+    h, out = _run(F, ctx, qb, F.PREC_FP8)
+    t, _ = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
+    for q in range(qb.n_q):
+        sc = scenes[int(qb.scene_of_q[q])]
+        row = t[q][t[q] >= 0]
+        assert row.size == min(sc.n, t.shape[1]) and np.unique(row).size == row.size, q
+        u = qb.tgt_emb[q].astype(np.float64)
+        d = sc.desc[row].astype(np.float64)
+        cos = d @ u / (np.linalg.norm(d, axis=1) * np.linalg.norm(u))
+        assert np.all(np.diff(cos) <= 2e-5), q
+    assert np.all(np.diff(out["score"], axis=1) <= 0)
+
+
+def test_scene_info_guards_similarity_output(F, world):
+    ctx, scenes, qb = world
+    for sid, sc in scenes.items():
+        assert F.farm_scene_info(ctx, sid) == (sc.n, DIM)
+    with pytest.raises(F.FarmError):
+        F.farm_scene_info(ctx, 99)
+    rows = qb.tgt_emb[:2]
+    with pytest.raises(F.FarmError):
+        F.farm_similarity(ctx, 30, rows, 2, F.PREC_FP8)          # n is not the scene's size
+    with pytest.raises(F.FarmError):
+        F.farm_similarity(ctx, 30, rows, scenes[30].n, F.PREC_FP8, out=np.zeros((2, 5), np.float32))
+    S = F.farm_similarity(ctx, 30, rows, scenes[30].n, F.PREC_FP8)
+    assert S.shape == (2, scenes[30].n) and np.isfinite(S).all()
