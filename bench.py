@@ -338,10 +338,10 @@ def main():
         flops_step *= 128.0 / sc.dim
     gemm_ms = stage_ms[1] / args.steps
     if args.precision == "fp32":
-        # three TF32 products per FP32-accurate product; TF32 peak = bf16 peak x (1.1 / 2.25)
-        peak = peaks["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
+        # three FP16 products per FP32-accurate product; FP16 dense peak = bf16 dense peak
+        peak = peaks["bf16_tflops_sustained"] / 3.0
         bound, unit = "tensor", "TFLOP/s"
-        peak_note = f"{peak_kind} sustained bf16 x 1.1/2.25 (TF32) / 3 (three-term split)"
+        peak_note = f"{peak_kind} sustained bf16 (= fp16 dense) / 3 (three-term FP16 split)"
     elif args.precision == "bf16":
         peak = peaks["bf16_tflops_sustained"]
         bound, unit = "tensor", "TFLOP/s"

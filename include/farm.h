@@ -63,7 +63,7 @@ typedef enum {
 
 /* Arithmetic of the descriptor-similarity stage (App. D.2 step 3). */
 typedef enum {
-    FARM_PREC_FP32 = 0,       /* FP32-accurate: tcgen05 tensor cores, 3-term split TF32 */
+    FARM_PREC_FP32 = 0,       /* FP32-accurate: tcgen05 tensor cores, 3-term FP16 split (22-bit operands) */
     FARM_PREC_BF16 = 1,       /* BF16 operands, FP32 accumulate, FP32 rescore of the borderline */
     FARM_PREC_FP8 = 2,        /* FP8-E4M3 operands with per-row scales, FP32 accumulate, FP32 rescore */
     FARM_PREC_FP32_SIMT = 3,  /* FP32 FMA on the CUDA cores (independent check path) */

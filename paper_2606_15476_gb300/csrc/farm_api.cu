@@ -186,7 +186,8 @@ farm_status check_device_errors(farm_ctx *ctx)
 
 // Normalised operand rows for `prec` into the workspace; returns pointers.
 struct RowOps {
-    float *q32 = nullptr, *qhi = nullptr, *qlo = nullptr;
+    float *q32 = nullptr;
+    uint16_t *qhi = nullptr, *qlo = nullptr;
     uint16_t *qbf = nullptr;
     uint8_t *qf8 = nullptr;
     float *qscale = nullptr;
@@ -237,8 +238,8 @@ farm_status run_similarity(farm_ctx *ctx, int32_t prec, const RowOps &ops, int64
     case FARM_PREC_FP32:
         if (!farm::sim_tc_available())
             return fail(ctx, FARM_EINVAL, "the tensor-core FP32 similarity path is not built");
-        LAUNCH(farm::launch_sim_tc_tf32x3(ops.qhi + off, ops.qlo + off, s.desc_hi, s.desc_lo, S,
-                                          rows, s.n, s.dim_pad, ld_s, c.num_sms, c.d_err, c.stream));
+        LAUNCH(farm::launch_sim_tc_f16x3(ops.qhi + off, ops.qlo + off, s.desc_hi, s.desc_lo, S,
+                                         rows, s.n, s.dim_pad, ld_s, c.num_sms, c.d_err, c.stream));
         return FARM_OK;
     case FARM_PREC_BF16:
         if (!farm::sim_tc_available())
@@ -416,8 +417,8 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
     };
     cudaError_t e;
     if ((e = cudaMalloc(&ns.desc32, nd * 4)) != cudaSuccess) return bailmem(e);
-    if ((e = cudaMalloc(&ns.desc_hi, nd * 4)) != cudaSuccess) return bailmem(e);
-    if ((e = cudaMalloc(&ns.desc_lo, nd * 4)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.desc_hi, nd * 2)) != cudaSuccess) return bailmem(e);
+    if ((e = cudaMalloc(&ns.desc_lo, nd * 2)) != cudaSuccess) return bailmem(e);
     if ((e = cudaMalloc(&ns.desc_bf16, nd * 2)) != cudaSuccess) return bailmem(e);
     if ((e = cudaMalloc(&ns.desc_fp8, nd)) != cudaSuccess) return bailmem(e);
     if ((e = cudaMalloc(&ns.desc_scale, (size_t)n * 4)) != cudaSuccess) return bailmem(e);

@@ -41,8 +41,8 @@ struct Scene {
     int32_t dim_pad = 0;
     int32_t n_views = 0;
     float *desc32 = nullptr;    // [n, dim_pad] unit rows, FP32
-    float *desc_hi = nullptr;   // [n, dim_pad] TF32-representable high part
-    float *desc_lo = nullptr;   // [n, dim_pad] residual desc32 - desc_hi
+    uint16_t *desc_hi = nullptr;    // [n, dim_pad] FP16 high part of desc32
+    uint16_t *desc_lo = nullptr;    // [n, dim_pad] FP16 of 2^11 (desc32 - desc_hi)
     uint16_t *desc_bf16 = nullptr;  // [n, dim_pad] BF16 of desc32
     uint8_t *desc_fp8 = nullptr;    // [n, dim_pad] E4M3 of desc32 / desc_scale
     float *desc_scale = nullptr;    // [n] per-row FP8 scale
@@ -57,8 +57,8 @@ struct Scene {
 enum Buf {
     B_RAW = 0,      // raw embedding rows as given [n_q + n_c, dim]
     B_Q32,          // normalised rows [rows, dim_pad]
-    B_QHI,          // TF32 high part
-    B_QLO,          // TF32 residual
+    B_QHI,          // FP16 high part
+    B_QLO,          // FP16 scaled residual
     B_QBF,          // BF16 rows
     B_SIM,          // similarity block [rows_chunk, n]
     B_ROWMAP,       // int32 [n_q + n_c] planned row of each source row
@@ -175,12 +175,12 @@ Ctx *ctx_of(farm_ctx *ctx);
 // ---- kernel launchers (each returns cudaGetLastError() after launching) ----
 
 // Unit-normalise `rows` rows of length dim into dst rows of length dim_pad
-// (zero tail); optionally also write the TF32 split and BF16 copies.  Rows
+// (zero tail); optionally also write the FP16 split and BF16 copies.  Rows
 // with zero or non-finite norm set err_bit in *err and are written as zeros.
 // dst_rows: optional int32 [rows] scatter map (src row r goes to dst row dst_rows[r]).
 cudaError_t launch_normalize_rows(const float *src, const int32_t *dst_rows, int64_t rows,
-                                  int32_t dim, int32_t dim_pad, float *dst32, float *dst_hi,
-                                  float *dst_lo, uint16_t *dst_bf16, int32_t *err, int err_bit,
+                                  int32_t dim, int32_t dim_pad, float *dst32, uint16_t *dst_hi,
+                                  uint16_t *dst_lo, uint16_t *dst_bf16, int32_t *err, int err_bit,
                                   cudaStream_t s);
 
 // E4M3 copy of unit rows with a per-row scale (max|x| / 448).
@@ -195,11 +195,11 @@ cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_vi
 cudaError_t launch_sim_simt(const float *q, const float *d, float *S, int64_t rows, int64_t n,
                             int32_t dim_pad, int64_t ld_s, cudaStream_t s);
 
-// Same product on the tensor cores with three TF32 terms (hi*hi + hi*lo + lo*hi).
-cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const float *d_hi,
-                                 const float *d_lo, float *S, int64_t rows, int64_t n,
-                                 int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err,
-                                 cudaStream_t s);
+// Same product on the tensor cores with three FP16 terms,
+// hi*hi + 2^-11 (hi*lo + lo*hi), from the split the normalisation writes.
+cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, const uint16_t *d_hi,
+                                const uint16_t *d_lo, float *S, int64_t rows, int64_t n, int32_t dim_pad,
+                                int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s);
 // BF16 operands, FP32 accumulation (first stage of the reduced-precision path).
 cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
                                int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s);

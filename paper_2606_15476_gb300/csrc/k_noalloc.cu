@@ -57,7 +57,7 @@ extern "C" farm_status farm_rank_rows_noalloc(farm_ctx *ctx, int32_t scene_id, i
     const farm::Scene &s = c.scenes[scene_id];
     if (r < 1 || r > farm::kMaxTargetCands || r > s.n)
         return fail(FARM_EINVAL, "farm_rank_rows_noalloc: r must lie in [1, min(512, n)]");
-    // scratch layout: normalised rows (one FP32 copy, or the TF32 hi and lo
+    // scratch layout: normalised rows (one FP32 copy, or the FP16 hi and lo
     // parts), then the similarity block [n_rows, round32(n)]
     const int64_t ld = (s.n + 31) / 32 * 32;
     const size_t row_bytes = farm::align256((size_t)n_rows * s.dim_pad * sizeof(float));
@@ -89,13 +89,14 @@ extern "C" farm_status farm_rank_rows_noalloc(farm_ctx *ctx, int32_t scene_id, i
     // every scratch entry read below is written earlier in this call: no clearing needed
     if (precision == FARM_PREC_FP32) {
         c.launches += 1;
-        e = farm::launch_normalize_rows(emb, nullptr, n_rows, s.dim, s.dim_pad, nullptr, q0, q1, nullptr, c.d_err,
+        uint16_t *h0 = reinterpret_cast<uint16_t *>(q0), *h1 = reinterpret_cast<uint16_t *>(q1);
+        e = farm::launch_normalize_rows(emb, nullptr, n_rows, s.dim, s.dim_pad, nullptr, h0, h1, nullptr, c.d_err,
                                         farm::kErrBadRow, c.stream);
         if (e != cudaSuccess) return fail(FARM_ECUDA, cudaGetErrorString(e));
         if (!farm::sim_tc_available()) return fail(FARM_EINVAL, "the tensor-core FP32 similarity path is not built");
         c.launches += 1;
-        e = farm::launch_sim_tc_tf32x3(q0, q1, s.desc_hi, s.desc_lo, S, n_rows, s.n, s.dim_pad, ld, c.num_sms,
-                                       c.d_err, c.stream);
+        e = farm::launch_sim_tc_f16x3(h0, h1, s.desc_hi, s.desc_lo, S, n_rows, s.n, s.dim_pad, ld, c.num_sms,
+                                      c.d_err, c.stream);
     } else {
         c.launches += 1;
         e = farm::launch_normalize_rows(emb, nullptr, n_rows, s.dim, s.dim_pad, q0, nullptr, nullptr, nullptr,

@@ -3,11 +3,14 @@
 // Descriptors and query embeddings enter the similarity stage (App. D.2
 // step 3) as unit vectors, so a dot product is the cosine.  For the
 // FP32-accurate tensor-core path every unit row x is also stored as
-//   x_hi = x rounded to TF32 (11 significant bits),  x_lo = TF32(x - x_hi),
-// so that x_hi*y_hi + x_hi*y_lo + x_lo*y_hi reproduces x*y to about 2^-21
-// relative per product (the dropped x_lo*y_lo term and the rounding of x_lo
-// are both of that order).
+//   x_hi = FP16(x)  (11 significant bits),  x_lo = FP16(2^11 (x - x_hi)),
+// so that x_hi*y_hi + 2^-11 (x_hi*y_lo + x_lo*y_hi) reproduces x*y to about
+// 2^-22 relative per product (the dropped x_lo*y_lo term and the rounding of
+// x_lo are both of that order).  x - x_hi is exact in FP32 and the power-of-two
+// scale is exact; it lifts the residual out of FP16's subnormal range.  Unit
+// rows have |x| <= 1, far inside FP16's range.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include "farm_internal.h"
@@ -15,18 +18,13 @@
 namespace farm {
 namespace {
 
-__device__ __forceinline__ float tf32_round(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
+__device__ __forceinline__ uint16_t half_bits(__half h) { return *reinterpret_cast<uint16_t *>(&h); }
 
 // One warp per row.
 __global__ void normalize_rows_kernel(const float *__restrict__ src, const int32_t *__restrict__ dst_rows,
                                       int64_t rows, int32_t dim, int32_t dim_pad,
-                                      float *__restrict__ dst32, float *__restrict__ dst_hi,
-                                      float *__restrict__ dst_lo, uint16_t *__restrict__ dst_bf16,
+                                      float *__restrict__ dst32, uint16_t *__restrict__ dst_hi,
+                                      uint16_t *__restrict__ dst_lo, uint16_t *__restrict__ dst_bf16,
                                       int32_t *err, int err_bit)
 {
     const int lane = threadIdx.x & 31;
@@ -46,9 +44,9 @@ __global__ void normalize_rows_kernel(const float *__restrict__ src, const int32
         float v = (k < dim && !bad) ? x[k] / nrm : 0.f;
         if (dst32) dst32[base + k] = v;
         if (dst_hi) {
-            float hi = tf32_round(v);
-            dst_hi[base + k] = hi;
-            dst_lo[base + k] = tf32_round(v - hi);
+            const __half hi = __float2half_rn(v);
+            dst_hi[base + k] = half_bits(hi);
+            dst_lo[base + k] = half_bits(__float2half_rn((v - __half2float(hi)) * 2048.f));
         }
         if (dst_bf16) {
             __nv_bfloat16 b = __float2bfloat16_rn(v);
@@ -124,8 +122,8 @@ cudaError_t launch_quantize_fp8_rows(const float *src, int64_t rows, int32_t dim
 }
 
 cudaError_t launch_normalize_rows(const float *src, const int32_t *dst_rows, int64_t rows,
-                                  int32_t dim, int32_t dim_pad, float *dst32, float *dst_hi,
-                                  float *dst_lo, uint16_t *dst_bf16, int32_t *err, int err_bit,
+                                  int32_t dim, int32_t dim_pad, float *dst32, uint16_t *dst_hi,
+                                  uint16_t *dst_lo, uint16_t *dst_bf16, int32_t *err, int err_bit,
                                   cudaStream_t s)
 {
     if (rows <= 0) return cudaSuccess;

@@ -2,39 +2,45 @@
 // (App. D.2 step 3: the cosine of every query row against every object).
 //
 // Three arithmetic modes share one kernel template:
-//  * FP32-accurate, three TF32 products:
-//      S[r, j] = <q_r, d_j> ~= q_hi.d_hi + q_hi.d_lo + q_lo.d_hi
+//  * FP32-accurate, three FP16 products with a scaled residual:
+//      S[r, j] = <q_r, d_j> ~= q_hi.d_hi + 2^-11 (q_hi.d_lo + q_lo.d_hi)
 //  * BF16: S[r, j] ~= <bf16(q_r), bf16(d_j)> with FP32 accumulation;
 //  * FP8-E4M3 with per-row scales: S[r, j] ~= s_r t_j <e4m3(q_r/s_r), e4m3(d_j/t_j)>,
 //    the scales applied in the epilogue.
 //  The last two are the first stage of the reduced-precision paths (their
 //  borderline candidates are re-scored in FP32 afterwards).
 //
-// FP32-accurate mode:
-// with x_hi = TF32(x) and x_lo = TF32(x - x_hi) prepared by the normalisation
-// kernel.  The dropped x_lo*y_lo term and the rounding of x_lo are each about
-// 2^-21 of |x*y|.  The tensor cores' FP32 accumulation truncates: every MMA
-// step adds an error of up to one unit in the last place of the running sum,
-// so the large products q_hi.d_hi accumulate in one tensor-memory (TMEM)
-// accumulator and the two small correction products in a second one, whose
-// truncation errors are about 2^-11 smaller; the epilogue adds the two in
-// IEEE FP32.  Measured against FP64 this keeps cosines within a few 1e-6.
+// FP32-accurate mode (the split of Ootomo and Yokota, "Recovering single
+// precision accuracy from Tensor Cores while surpassing the FP32 theoretical
+// peak performance", IJHPCA 2022): with x_hi = FP16(x) and
+// x_lo = FP16(2^11 (x - x_hi)) prepared by the normalisation kernel, each
+// operand keeps 22 significant bits; the dropped x_lo*y_lo term and the
+// rounding of x_lo are each about 2^-22 of |x*y|.  The 2^11 scale keeps the
+// residual in FP16's normal range.  The tensor cores' FP32 accumulation
+// truncates: every MMA step adds an error of up to one unit in the last place
+// of the running sum, so the large products q_hi.d_hi accumulate in one
+// tensor-memory (TMEM) accumulator and the two scaled correction products in
+// a second one; the epilogue adds 2^-11 times the second to the first in IEEE
+// FP32.  FP16 products run at twice the TF32 rate and the operands take half
+// the bytes of a TF32 split.
 //
 // Kernel organisation (persistent: one CTA of 192 threads per SM walks the
 // 128 x 256 tiles of S):
-//   warp 0      TMA producer: for each K slice (16 FP32 values, 64-byte swizzle,
-//               four tiles q_hi, q_lo, d_hi, d_lo; or 64 BF16 values, 128-byte
-//               swizzle, two tiles q, d) fills one pipeline stage, signalling a
-//               "full" mbarrier with the byte count;
-//   warp 1      allocates TMEM (two 128 x 256 FP32 accumulators in TF32 mode,
-//               one in BF16 mode); one thread issues, per K slice, 2 K-steps x 3
-//               products of tcgen05.mma.cta_group::1.kind::tf32 (M=128, N=256,
-//               K=8), or 4 K-steps of kind::f16 with BF16 operands (K=16), and
-//               tcgen05.commit to the stage's "empty" mbarrier, finally to the
-//               "accumulator ready" mbarrier;
-//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns at a time (TF32
-//               mode: of both accumulators, added), store the rows of S
-//               (bounds-checked), then release the accumulator.
+//   warp 0      TMA producer: for each K slice (32 FP16 values, 64-byte swizzle,
+//               four tiles q_hi, q_lo, d_hi, d_lo; or 64 BF16 / 128 FP8 values,
+//               128-byte swizzle, two tiles q, d) fills one pipeline stage,
+//               signalling a "full" mbarrier with the byte count;
+//   warp 1      allocates TMEM (main and correction 128 x 256 FP32
+//               accumulators in the FP32-accurate mode, two alternating tile
+//               accumulators otherwise); one thread issues, per K slice,
+//               2 K-steps x 3 products of tcgen05.mma.cta_group::1.kind::f16
+//               with FP16 operands (M=128, N=256, K=16), or 4 K-steps of
+//               kind::f16 (BF16) / kind::f8f6f4 (E4M3), and tcgen05.commit to
+//               the stage's "empty" mbarrier, finally to the "accumulator
+//               ready" mbarrier;
+//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns at a time (FP32-
+//               accurate mode: of both accumulators, combined), store the rows
+//               of S (bounds-checked), then release the accumulator.
 // Four pipeline stages of 48 KB each.  Every mbarrier wait is bounded: on
 // expiry the kernel raises the error flag, stops issuing work, waits (bounded)
 // for the copies it issued, frees its TMEM and returns.
@@ -56,20 +62,21 @@ constexpr int THREADS = 192;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;    // try_wait polls before giving up (about a second)
 constexpr int GROUP_M = 16;                  // tile raster: 16 row tiles share each column tile
-constexpr int ACC_CORR = 256;                // TMEM column of the correction accumulator (TF32 mode)
+constexpr int ACC_CORR = 256;                // TMEM column of the correction accumulator (FP16x3 mode)
+constexpr float RESID_SCALE_INV = 1.f / 2048.f;   // the residual operands carry a factor 2^11
 
-enum : int { kTf32x3 = 0, kBf16 = 1, kFp8 = 2 };
+enum : int { kF16x3 = 0, kBf16 = 1, kFp8 = 2 };
 
 // Per-mode layout of a pipeline stage.
 template <int MODE>
 struct Mode;
 template <>
-struct Mode<kTf32x3> {                       // three-term TF32
-    static constexpr int BK = 16;            // FP32 elements per K slice (64-byte rows)
+struct Mode<kF16x3> {                        // three-term FP16 with scaled residuals
+    static constexpr int BK = 32;            // FP16 elements per K slice (64-byte rows)
     static constexpr int ROW_BYTES = 64;
     static constexpr int A_BYTES = BM * ROW_BYTES;   // 8 KB, twice (hi, lo)
     static constexpr int B_BYTES = BN * ROW_BYTES;   // 16 KB, twice
-    static constexpr int KSTEPS = 2;         // 8 TF32 values (32 bytes) per MMA
+    static constexpr int KSTEPS = 2;         // 16 FP16 values (32 bytes) per MMA
     static constexpr int TMEM_COLS = 512;
     static constexpr uint64_t LAYOUT = 4;    // 64-byte swizzle
     static constexpr uint32_t SBO = 512;     // 8 rows x 64 bytes
@@ -96,7 +103,7 @@ struct Mode<kFp8> {                          // FP8 E4M3
     static constexpr uint64_t LAYOUT = 2;    // 128-byte swizzle
     static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
 };
-static_assert(2 * Mode<kTf32x3>::A_BYTES + 2 * Mode<kTf32x3>::B_BYTES == STAGE_BYTES, "stage size");
+static_assert(2 * Mode<kF16x3>::A_BYTES + 2 * Mode<kF16x3>::B_BYTES == STAGE_BYTES, "stage size");
 static_assert(Mode<kBf16>::A_BYTES + Mode<kBf16>::B_BYTES == STAGE_BYTES, "stage size");
 static_assert(Mode<kFp8>::A_BYTES + Mode<kFp8>::B_BYTES == STAGE_BYTES, "stage size");
 
@@ -157,7 +164,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 }
 
 // Instruction descriptors: D = F32, A and B K-major, M = 128, N = 256;
-// operand format TF32 (2, kind::tf32), BF16 (1, kind::f16) or E4M3 (0, kind::f8f6f4).
+// operand format FP16 (0, kind::f16), BF16 (1, kind::f16) or E4M3 (0, kind::f8f6f4).
 __host__ __device__ constexpr uint32_t idesc(uint32_t ab_format)
 {
     return (1u << 4)                      // D format F32
@@ -167,13 +174,13 @@ __host__ __device__ constexpr uint32_t idesc(uint32_t ab_format)
            | ((uint32_t)(BM >> 4) << 24); // M / 16
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(2u)), "r"(accumulate));
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(0u)), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
@@ -241,10 +248,10 @@ __device__ __forceinline__ void tile_origin(int tile, int m_tiles, int n_tiles, 
 // The shared-memory pipeline runs on across tiles.  Two-operand modes (BF16,
 // FP8) keep two accumulators in the 512 TMEM columns, so the epilogue of one
 // tile overlaps the MMAs of the next (acc_full / acc_empty mbarriers); the
-// TF32 mode needs both halves of TMEM for its main and correction
+// FP16x3 mode needs both halves of TMEM for its main and correction
 // accumulators and drains before the next tile's MMAs start, while the
 // producer already prefetches that tile's first stages.
-// Maps (TF32 mode): q_hi, q_lo, d_hi, d_lo.  (BF16, FP8 modes): q, d, and the
+// Maps (FP16x3 mode): q_hi, q_lo, d_hi, d_lo.  (BF16, FP8 modes): q, d, and the
 // last two are unused.  scale_q / scale_d: per-row scales (FP8 mode only).
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -255,7 +262,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
               const float *__restrict__ scale_d, int32_t *err)
 {
     using M = Mode<MODE>;
-    constexpr bool TWO_OPERAND_TILES = MODE != kTf32x3;
+    constexpr bool TWO_OPERAND_TILES = MODE != kF16x3;
     constexpr int NACC = TWO_OPERAND_TILES ? 2 : 1;
     constexpr uint32_t TMEM_ALLOC = 512;
     extern __shared__ uint8_t smem_raw[];
@@ -361,11 +368,11 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                         const uint32_t b_hi = st + 2 * M::A_BYTES, b_lo = st + 2 * M::A_BYTES + M::B_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < M::KSTEPS; ++kk) {
-                            const uint32_t off = kk * 32;     // 8 TF32 values = 32 bytes along K
+                            const uint32_t off = kk * 32;     // 16 FP16 values = 32 bytes along K
                             const uint32_t first = (kb | kk) != 0;
-                            mma_tf32(acc, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), first);
-                            mma_tf32(acc + ACC_CORR, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_lo + off), first);
-                            mma_tf32(acc + ACC_CORR, smem_desc<MODE>(a_lo + off), smem_desc<MODE>(b_hi + off), 1u);
+                            mma_f16(acc, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), first);
+                            mma_f16(acc + ACC_CORR, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_lo + off), first);
+                            mma_f16(acc + ACC_CORR, smem_desc<MODE>(a_lo + off), smem_desc<MODE>(b_hi + off), 1u);
                         }
                     }
                     mma_commit(&empty[s]);
@@ -398,11 +405,11 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 const uint32_t lane_addr = tmem + (TWO_OPERAND_TILES ? buf * 256u : 0u) +
                                            ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32);
                 tmem_ld32(lane_addr, v);
-                if (MODE == kTf32x3) {
+                if (MODE == kF16x3) {
                     float w[32];
                     tmem_ld32(lane_addr + ACC_CORR, w);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] += w[i];
+                    for (int i = 0; i < 32; ++i) v[i] = fmaf(w[i], RESID_SCALE_INV, v[i]);
                 }
                 const int64_t col0 = (int64_t)n0 + c * 32;
                 if (MODE == kFp8 && r < rows) {
@@ -448,14 +455,14 @@ bool get_encoder()
     return true;
 }
 
-// 2D tensor [outer, inner] row-major (FP32 or BF16), box [box_outer, BK],
-// swizzle matching the mode's row width.
+// 2D tensor [outer, inner] row-major (FP16, BF16 or FP8 bytes), box
+// [box_outer, BK], swizzle matching the mode's row width.
 template <int MODE>
 bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, int box_outer)
 {
     using M = Mode<MODE>;
-    const int esize = MODE == kTf32x3 ? 4 : (MODE == kBf16 ? 2 : 1);
-    const CUtensorMapDataType dt = MODE == kTf32x3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+    const int esize = MODE == kFp8 ? 1 : 2;
+    const CUtensorMapDataType dt = MODE == kF16x3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : (MODE == kBf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
     cuuint64_t strides[1] = {(cuuint64_t)inner * esize};
@@ -463,7 +470,7 @@ bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, in
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          MODE == kTf32x3 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                          MODE == kF16x3 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -474,7 +481,7 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
                       int num_sms, int32_t *err, cudaStream_t s)
 {
     using M = Mode<MODE>;
-    constexpr bool TWO = MODE != kTf32x3;
+    constexpr bool TWO = MODE != kF16x3;
     if (rows <= 0 || n <= 0) return cudaSuccess;
     // rows are padded to kDimAlign (64) elements; the FP8 K slice (128 bytes)
     // may run past the row end, where the tensor map's bounds fill zeros
@@ -511,11 +518,11 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
 
 bool sim_tc_available() { return get_encoder(); }
 
-cudaError_t launch_sim_tc_tf32x3(const float *q_hi, const float *q_lo, const float *d_hi, const float *d_lo, float *S,
-                                 int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err,
-                                 cudaStream_t s)
+cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, const uint16_t *d_hi,
+                                const uint16_t *d_lo, float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s,
+                                int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kTf32x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, num_sms, err, s);
+    return launch_tc<kF16x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, num_sms, err, s);
 }
 
 cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
