@@ -194,6 +194,17 @@ farm_status farm_topk(farm_ctx *ctx, uint64_t batch_handle, int32_t k, int32_t *
 farm_status farm_sync(farm_ctx *ctx);
 
 /*
+ * Rows that the thresholded rank selection of the tensor-core paths handed
+ * to its exact fallback since the context was created (or last reset).  The
+ * threshold comes from per-tile maxima of the similarity block; a row whose
+ * entries at or above it overflow the candidate buffer (many exact ties, or
+ * top-ranked objects crowded into a few 256-object tiles) is selected by a
+ * slower exact radix select.  Results are exact either way.  Synchronises the
+ * context's stream; reset != 0 zeroes the count afterwards.
+ */
+farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t reset);
+
+/*
  * Object count n and descriptor length dim of an uploaded scene, for sizing
  * the output of farm_similarity (n_rows x n floats).  Either pointer may be
  * NULL.  FARM_EINVAL for a scene id that holds no scene.

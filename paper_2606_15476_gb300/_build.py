@@ -32,7 +32,7 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + \
+    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))) + \
         [os.path.join(HERE, "..", "include", "farm.h"), __file__]
 
 

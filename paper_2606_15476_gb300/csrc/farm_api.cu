@@ -227,7 +227,7 @@ cudaError_t alloc_rows(farm_ctx *ctx, int32_t prec, int64_t rows, int32_t dim_pa
 
 // S rows [r0, r0 + rows) of the planned row space against scene s.
 farm_status run_similarity(farm_ctx *ctx, int32_t prec, const RowOps &ops, int64_t r0,
-                           int64_t rows, const Scene &s, float *S, int64_t ld_s)
+                           int64_t rows, const Scene &s, float *S, int64_t ld_s, float *tops = nullptr)
 {
     Ctx &c = ctx->c;
     const int64_t off = r0 * s.dim_pad;
@@ -239,25 +239,25 @@ farm_status run_similarity(farm_ctx *ctx, int32_t prec, const RowOps &ops, int64
         if (!farm::sim_tc_available())
             return fail(ctx, FARM_EINVAL, "the tensor-core FP32 similarity path is not built");
         LAUNCH(farm::launch_sim_tc_f16x3(ops.qhi + off, ops.qlo + off, s.desc_hi, s.desc_lo, S,
-                                         rows, s.n, s.dim_pad, ld_s, c.num_sms, c.d_err, c.stream));
+                                         rows, s.n, s.dim_pad, ld_s, tops, c.num_sms, c.d_err, c.stream));
         return FARM_OK;
     case FARM_PREC_BF16:
         if (!farm::sim_tc_available())
             return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
-        LAUNCH(farm::launch_sim_tc_bf16(ops.qbf + off, s.desc_bf16, S, rows, s.n, s.dim_pad, ld_s, c.num_sms,
+        LAUNCH(farm::launch_sim_tc_bf16(ops.qbf + off, s.desc_bf16, S, rows, s.n, s.dim_pad, ld_s, tops, c.num_sms,
                                         c.d_err, c.stream));
         return FARM_OK;
     case FARM_PREC_LEARNED:
         if (!farm::sim_tc_available())
             return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
-        LAUNCH(farm::launch_sim_tc_bf16(ops.qcomp + r0 * c.mlp.P, s.comp, S, rows, s.n, c.mlp.P, ld_s, c.num_sms,
+        LAUNCH(farm::launch_sim_tc_bf16(ops.qcomp + r0 * c.mlp.P, s.comp, S, rows, s.n, c.mlp.P, ld_s, tops, c.num_sms,
                                         c.d_err, c.stream));
         return FARM_OK;
     case FARM_PREC_FP8:
         if (!farm::sim_tc_available())
             return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
         LAUNCH(farm::launch_sim_tc_fp8(ops.qf8 + off, ops.qscale + r0, s.desc_fp8, s.desc_scale, S, rows, s.n,
-                                       s.dim_pad, ld_s, c.num_sms, c.d_err, c.stream));
+                                       s.dim_pad, ld_s, tops, c.num_sms, c.d_err, c.stream));
         return FARM_OK;
     default:
         return fail(ctx, FARM_EINVAL, "precision not supported by this build");
@@ -319,6 +319,7 @@ farm_status farm_destroy(farm_ctx *ctx)
         if (s.present) free_scene(s);
     for (int b = 0; b < farm::B_COUNT; ++b) cudaFree(c.ws.ptr[b]);
     cudaFree(c.d_err);
+    cudaFree(c.d_fallback);
     cudaFree(ctx->d_scenes);
     cudaFree(c.mlp.params);
     cudaFree(c.mlp.w1b);
@@ -363,6 +364,8 @@ farm_status farm_create(farm_ctx **out, int device, void *cuda_stream, const far
     }
     if (cudaMalloc(&c.d_err, sizeof(int32_t)) != cudaSuccess) return bail(FARM_ENOMEM);
     if (cudaMemset(c.d_err, 0, sizeof(int32_t)) != cudaSuccess) return bail(FARM_ECUDA);
+    if (cudaMalloc(&c.d_fallback, sizeof(int32_t)) != cudaSuccess) return bail(FARM_ENOMEM);
+    if (cudaMemset(c.d_fallback, 0, sizeof(int32_t)) != cudaSuccess) return bail(FARM_ECUDA);
     if (cudaHostAlloc(&c.h_err, sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) return bail(FARM_ENOMEM);
     if (cudaMalloc(&ctx->d_scenes, kMaxScenes * sizeof(SceneDev)) != cudaSuccess) return bail(FARM_ENOMEM);
     if (cudaMemset(ctx->d_scenes, 0, kMaxScenes * sizeof(SceneDev)) != cudaSuccess) return bail(FARM_ECUDA);
@@ -645,14 +648,19 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     }
     // ---- similarity batches: row ranges ("pieces") of the scene groups are
     //      laid end to end in S while they fit kSimCapBytes; each batch takes
-    //      one similarity launch per piece and one grouped select (+ chunk
-    //      merge) (+ FP32 rescore) launch over all of its pieces
-    struct Batch { size_t p0 = 0, np = 0; int64_t s_floats = 0, rows = 0, blocks = 0, tmp = 0;
-                   int32_t smem_sel = 1, smem_merge = 0; bool chunked = false; };
+    //      one similarity launch per piece, then the rank selection: on the
+    //      tensor-core paths the thresholded select (from the 32-object group
+    //      maxima the similarity epilogue writes) for every row with at least
+    //      as many groups as its list length, the shared-memory select (+ chunk
+    //      merge) for the others; then one FP32 rescore launch on the
+    //      reduced-precision paths
+    struct Batch { size_t p0 = 0, np = 0; int64_t s_floats = 0, rows = 0, blocks = 0, tblocks = 0, tmp = 0,
+                   tops = 0; int32_t smem_sel = 1, smem_merge = 0, max_union = 1; bool chunked = false; };
     std::vector<farm::Piece> pieces;
     std::vector<int32_t> piece_sid;
     std::vector<Batch> batches;
     const bool reduced = reduced_precision(precision);
+    const bool tile_tops = precision != FARM_PREC_FP32_SIMT;
     int32_t tmp_stride = 4;
     for (const auto &g : groups) {
         const Scene &s = c.scenes[g.sid];
@@ -669,7 +677,9 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
         const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
         const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows_g, (int64_t)(kSimCapBytes / (ld * 4))));
-        // long rows: column chunks of at most kSelectRowMax entries, merged after
+        const int64_t n_tiles = (s.n + farm::kSimTileN - 1) / farm::kSimTileN;
+        const int32_t uni = (int32_t)std::min<int64_t>(n_tiles * farm::kTileTop, 8192);
+        // long rows of the shared-memory select: column chunks, merged after
         int32_t chunks = 1, chunk_len = (int32_t)s.n;
         bool global_select = false;
         if (s.n > farm::kSelectRowMax) {
@@ -692,6 +702,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             pc.s_off = bt.s_floats;
             pc.row_begin = bt.rows;
             pc.block_begin = bt.blocks;
+            pc.tblock_begin = bt.tblocks;
             pc.q_row0 = g.row0 + r0;
             pc.ntr = (int32_t)std::max<int64_t>(0, std::min<int64_t>(g.nq - r0, nr));
             pc.t_row0 = g.q0 + r0;
@@ -703,17 +714,27 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             pc.klm = klm;
             pc.keep_t = reduced ? reduced_keep_target(p, precision, Rs, s.n) : Rs;
             pc.keep_l = reduced ? reduced_keep_landmark(p, precision, klm, s.n) : klm;
-            pc.chunks = global_select ? 1 : chunks;
-            pc.chunk_len = global_select ? (int32_t)s.n : chunk_len;
             pc.tmp_off = -1;
-            if (global_select) {
-                pc.chunks = 0;   // selected by the per-piece global-memory kernel; no grouped blocks
-            } else {
-                bt.blocks += nr * pc.chunks;
+            pc.tops_off = -1;
+            // rows [0, th0): shared-memory select; rows [th0, rows): thresholded select
+            pc.th0 = pc.rows;
+            if (tile_tops) {
+                pc.th0 = uni >= pc.keep_t ? 0 : (uni >= pc.keep_l ? pc.ntr : pc.rows);
+                pc.tops_off = bt.tops;
+                bt.tops += nr * n_tiles * farm::kTileTop;
+                if (pc.th0 < pc.rows) {
+                    bt.tblocks += pc.rows - pc.th0;
+                    bt.max_union = std::max(bt.max_union, uni);
+                }
+            }
+            pc.chunks = global_select ? 0 : chunks;
+            pc.chunk_len = global_select ? (int32_t)s.n : chunk_len;
+            if (pc.th0 > 0 && !global_select) {
+                bt.blocks += (int64_t)pc.th0 * pc.chunks;
                 bt.smem_sel = std::max(bt.smem_sel, pc.chunk_len);
                 if (pc.chunks > 1) {
                     pc.tmp_off = bt.tmp;
-                    bt.tmp += nr * pc.chunks * tmp_stride;
+                    bt.tmp += (int64_t)pc.th0 * pc.chunks * tmp_stride;
                     bt.chunked = true;
                     bt.smem_merge = std::max(bt.smem_merge, pc.chunks * tmp_stride);
                 }
@@ -725,15 +746,17 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             piece_sid.push_back(g.sid);
         }
     }
-    int64_t s_need = 1, tmp_need = 4;
+    int64_t s_need = 1, tmp_need = 4, tops_need = 4;
     for (const auto &bt : batches) {
         s_need = std::max(s_need, bt.s_floats);
         tmp_need = std::max(tmp_need, bt.tmp);
+        tops_need = std::max(tops_need, bt.tops);
     }
-    float *d_sim, *tmp_val = nullptr;
+    float *d_sim, *tmp_val = nullptr, *d_tops = nullptr;
     int32_t *tmp_idx = nullptr;
     farm::Piece *d_pieces;
     CK(ws_get(ctx, farm::B_SIM, (size_t)s_need, &d_sim));
+    if (tile_tops) CK(ws_get(ctx, farm::B_TOPS, (size_t)tops_need, &d_tops));
     CK(ws_get(ctx, farm::B_PIECES, pieces.size(), &d_pieces));
     bool any_chunked = false;
     for (const auto &bt : batches) any_chunked |= bt.chunked;
@@ -791,7 +814,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
             const farm::Piece &pc = pieces[k];
             farm_status st = run_similarity(ctx, precision, ops, pc.q_row0, pc.rows, c.scenes[piece_sid[k]],
-                                            d_sim + pc.s_off, pc.ld);
+                                            d_sim + pc.s_off, pc.ld, tile_tops ? d_tops + pc.tops_off : nullptr);
             if (st != FARM_OK) return st;
         }
         mark_end(ctx, m1);
@@ -804,10 +827,13 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         if (bt.chunked)
             LAUNCH(farm::launch_merge_chunks(dp, (int32_t)bt.np, bt.rows, bt.smem_merge, tmp_idx, tmp_val, tmp_stride,
                                              sel_ti, sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.stream));
+        if (bt.tblocks > 0)
+            LAUNCH(farm::launch_select_thresh(d_sim, d_tops, dp, (int32_t)bt.np, bt.tblocks, bt.max_union, sel_ti,
+                                              sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.d_fallback, c.stream));
         for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
             const farm::Piece &pc = pieces[k];
-            if (pc.chunks != 0) continue;
-            LAUNCH(farm::launch_select_rows_ex(d_sim + pc.s_off, pc.ld, pc.n, pc.rows, pc.ntr, pc.keep_t, pc.keep_l,
+            if (pc.chunks != 0 || pc.th0 == 0) continue;
+            LAUNCH(farm::launch_select_rows_ex(d_sim + pc.s_off, pc.ld, pc.n, pc.th0, pc.ntr, pc.keep_t, pc.keep_l,
                                                sel_ti, sel_tc, pc.t_row0, sel_st, sel_li, sel_lc, pc.l_row0, sel_sl,
                                                c.stream));
         }
@@ -973,6 +999,22 @@ farm_status farm_candidates(farm_ctx *ctx, uint64_t batch_handle, int32_t *tgt_i
         for (int64_t i = 0; i < n_c; ++i)
             std::memcpy(lm_idx + i * c.batch_klm, l.data() + (size_t)ctx->h_cplan[i] * c.batch_klm,
                         (size_t)c.batch_klm * 4);
+    return FARM_OK;
+}
+
+farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t reset)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    CK(cudaSetDevice(c.device));
+    int32_t v = 0;
+    CK(cudaMemcpyAsync(&v, c.d_fallback, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    if (rows_out) *rows_out = v;
+    if (reset) {
+        CK(cudaMemsetAsync(c.d_fallback, 0, sizeof(int32_t), c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+    }
     return FARM_OK;
 }
 

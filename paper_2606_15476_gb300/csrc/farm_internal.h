@@ -87,6 +87,7 @@ enum Buf {
     B_PIECES,       // Piece tables of the batch's grouped launches
     B_CHUNK_IDX,    // int32 chunk lists of long rows (select, then merge)
     B_CHUNK_VAL,    // float their values
+    B_TOPS,         // float per-row tile maxima of the tensor-core similarity (thresholded select)
     B_COUNT
 };
 
@@ -125,6 +126,7 @@ struct Ctx {
     std::vector<Scene> scenes;
     Workspace ws;
     int32_t *d_err = nullptr;     // device error word
+    int32_t *d_fallback = nullptr;  // rows the thresholded select handed to its exact fallback
     int32_t *h_err = nullptr;     // pinned host mirror
     // batch state
     uint64_t batch_gen = 0;
@@ -195,18 +197,28 @@ cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_vi
 cudaError_t launch_sim_simt(const float *q, const float *d, float *S, int64_t rows, int64_t n,
                             int32_t dim_pad, int64_t ld_s, cudaStream_t s);
 
+// The tensor-core kernels work on column tiles of kSimTileN objects.  With a
+// non-null `tops` ([rows, ceil(n / kSimTileN), kTileTop] FP32, 16-byte
+// aligned) the epilogue also writes, per row, the maximum of every group of
+// 32 consecutive objects (kTileTop groups per tile; -inf for a group past the
+// row end): entries of the row, so their R-th largest value bounds the row's
+// R-th largest from below (the thresholded select uses it).
+constexpr int kSimTileN = 256;
+constexpr int kTileTop = 8;
+
 // Same product on the tensor cores with three FP16 terms,
 // hi*hi + 2^-11 (hi*lo + lo*hi), from the split the normalisation writes.
 cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, const uint16_t *d_hi,
                                 const uint16_t *d_lo, float *S, int64_t rows, int64_t n, int32_t dim_pad,
-                                int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s);
+                                int64_t ld_s, float *tops, int num_sms, int32_t *err, cudaStream_t s);
 // BF16 operands, FP32 accumulation (first stage of the reduced-precision path).
 cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
-                               int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s);
+                               int32_t dim_pad, int64_t ld_s, float *tops, int num_sms, int32_t *err,
+                               cudaStream_t s);
 // FP8 E4M3 operands with per-row scales applied in the epilogue.
 cudaError_t launch_sim_tc_fp8(const uint8_t *q, const float *scale_q, const uint8_t *d, const float *scale_d,
-                              float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, int num_sms,
-                              int32_t *err, cudaStream_t s);
+                              float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, float *tops,
+                              int num_sms, int32_t *err, cudaStream_t s);
 bool sim_tc_available();
 
 // Per row r of S (rows x n, leading dim ld_s): the R_r largest entries in
@@ -230,23 +242,30 @@ cudaError_t launch_select_rows_ex(const float *S, int64_t ld_s, int64_t n, int64
 // One scene's block of rows within a grouped select / merge / rescore
 // launch.  The block's rows are rows [row_begin, row_begin + rows) of the
 // launch, stored at S + s_off with leading dimension ld; the first ntr are
-// target rows.  A row longer than the shared-memory limit is selected in
+// target rows.  Rows [0, th0) are selected by the shared-memory select
+// (launch_select_grouped, blocks from block_begin), rows [th0, rows) by the
+// thresholded select (launch_select_thresh, blocks from tblock_begin, tile
+// maxima at tops + tops_off, rows of ceil(n / kSimTileN) * kTileTop values).
+// A row of the shared-memory select longer than its limit is selected in
 // `chunks` column chunks of chunk_len entries, whose lists (tmp_stride
 // entries each, rows at tmp + tmp_off + i * chunks * tmp_stride) are merged
-// afterwards.  Pieces of a launch are ordered by row_begin and block_begin.
+// afterwards.  Pieces of a launch are ordered by every *_begin field.
 struct Piece {
     const float *d32;       // the scene's unit FP32 descriptors (rescore)
     int64_t s_off;          // offset of the block's first row in S (floats)
     int64_t row_begin;      // first launch row of the block
-    int64_t block_begin;    // first select block (rows x chunks before it)
+    int64_t block_begin;    // first shared-memory-select block (th0 x chunks blocks)
+    int64_t tblock_begin;   // first thresholded-select block (rows - th0 blocks)
     int64_t q_row0;         // row of the block's first row in the normalised operand rows
     int64_t t_row0;         // list row of the first target row
     int64_t l_row0;         // list row of the first landmark row
     int64_t tmp_off;        // chunk-list offset of the first row (entries)
+    int64_t tops_off;       // tile-maxima offset of the first row (floats)
     int32_t rows, ntr, n, ld;
     int32_t keep_t, keep_l; // list lengths the select keeps (R / K_a, or the rescore's C)
     int32_t R, klm;         // list lengths after a rescore
     int32_t chunks, chunk_len;
+    int32_t th0, pad0;
 };
 
 // Grouped select over `pieces` (device; n_pieces entries) in one launch of
@@ -266,6 +285,16 @@ cudaError_t launch_merge_chunks(const Piece *pieces, int32_t n_pieces, int64_t t
                                 const int32_t *tmp_idx, const float *tmp_val, int32_t tmp_stride,
                                 int32_t *tsel_idx, float *tsel_cos, int32_t stride_t, int32_t *lsel_idx,
                                 float *lsel_cos, int32_t stride_l, cudaStream_t s);
+// Thresholded select of rows [th0, rows) of every piece (one block per row,
+// total_blocks of them), from the tile maxima `tops` the tensor-core
+// similarity kernel wrote; each row needs ceil(n / kSimTileN) * kTileTop >=
+// its list length.  max_union: the largest such union of the launch.  Rows
+// whose candidates overflow fall back to an exact global-memory select and
+// are counted in *n_fallback (device).  Outputs as launch_select_grouped.
+cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,
+                                 int64_t total_blocks, int32_t max_union, int32_t *tsel_idx, float *tsel_cos,
+                                 int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
+                                 int32_t *n_fallback, cudaStream_t s);
 // Grouped FP32 rescore (one block per launch row): the keep_t / keep_l
 // candidates of bsel_* (strides cstride_t / cstride_l; values nullable, then
 // no band skip) against the normalised rows Q32 -> the R / klm best in rank

@@ -151,12 +151,12 @@ cudaError_t farm::learned_embed_rows(farm_ctx *ctx, const uint16_t *xb, int64_t 
     for (int64_t r0 = 0; r0 < rows; r0 += chunk) {
         const int64_t b = std::min(chunk, rows - r0);
         c.launches += 6;
-        if ((r = launch_sim_tc_bf16(xb + r0 * M.D_pad, M.w1b, (float *)h, b, M.H, M.D_pad, M.H, c.num_sms, c.d_err,
+        if ((r = launch_sim_tc_bf16(xb + r0 * M.D_pad, M.w1b, (float *)h, b, M.H, M.D_pad, M.H, nullptr, c.num_sms, c.d_err,
                                     c.stream)))
             return r;
         if ((r = mlp_bias_gelu((float *)h, M.b1(), (float *)a, b, M.H, c.stream))) return r;
         if ((r = mlp_to_bf16((float *)a, b * M.H, (uint16_t *)ab, c.stream))) return r;
-        if ((r = launch_sim_tc_bf16((uint16_t *)ab, M.w2b, (float *)z, b, M.P, M.H, M.P, c.num_sms, c.d_err,
+        if ((r = launch_sim_tc_bf16((uint16_t *)ab, M.w2b, (float *)z, b, M.P, M.H, M.P, nullptr, c.num_sms, c.d_err,
                                     c.stream)))
             return r;
         if ((r = mlp_bias_normalize((float *)z, M.b2(), (float *)e, nullptr, b, M.P, c.stream))) return r;

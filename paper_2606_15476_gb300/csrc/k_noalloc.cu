@@ -95,7 +95,7 @@ extern "C" farm_status farm_rank_rows_noalloc(farm_ctx *ctx, int32_t scene_id, i
         if (e != cudaSuccess) return fail(FARM_ECUDA, cudaGetErrorString(e));
         if (!farm::sim_tc_available()) return fail(FARM_EINVAL, "the tensor-core FP32 similarity path is not built");
         c.launches += 1;
-        e = farm::launch_sim_tc_f16x3(h0, h1, s.desc_hi, s.desc_lo, S, n_rows, s.n, s.dim_pad, ld, c.num_sms,
+        e = farm::launch_sim_tc_f16x3(h0, h1, s.desc_hi, s.desc_lo, S, n_rows, s.n, s.dim_pad, ld, nullptr, c.num_sms,
                                       c.d_err, c.stream);
     } else {
         c.launches += 1;

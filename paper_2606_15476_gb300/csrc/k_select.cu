@@ -18,212 +18,45 @@
 // Rows of up to kRowSmemMax entries are staged once in shared memory (two
 // CTAs per SM) and take three passes with 11/11/10-bit digits over shared
 // memory; longer rows stay in global memory (four 8-bit passes, L2-resident).
-#include "farm_internal.h"
+#include "select_common.cuh"
 
 namespace farm {
 namespace {
+
+using namespace sel;
 
 constexpr int TH = 512;
 constexpr int SORT_MAX = kMaxTargetCands;   // >= kMaxAnchorCands
 constexpr int kRowSmemMax = kSelectRowMax;  // entries staged in shared memory (96 KB)
 
-__device__ __forceinline__ uint32_t order_key(float f)
-{
-    const uint32_t u = __float_as_uint(f + 0.0f);   // -0 -> +0
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-
-__device__ __forceinline__ float key_value(uint32_t k)
-{
-    const uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
-    return __uint_as_float(u);
-}
-
-// Rank-ordered (key, ~position) list -> indices / values [0, stride); the
-// object index of position p is idx_map[p] when idx_map is given, else
-// idx_base + p.  Entries past R hold index -1 and value pad.
-__device__ __forceinline__ void write_list(const uint64_t *cand, int R, int32_t idx_base,
-                                           const int32_t *__restrict__ idx_map, int32_t *__restrict__ oi,
-                                           float *__restrict__ oc, int stride, float pad)
-{
-    for (int i = threadIdx.x; i < stride; i += TH) {
-        if (i < R) {
-            const uint64_t c = cand[i];
-            const int32_t pos = (int32_t)(0xffffffffu - (uint32_t)(c & 0xffffffffu));
-            oi[i] = idx_map ? idx_map[pos] : idx_base + pos;
-            if (oc) oc[i] = key_value((uint32_t)(c >> 32));
-        } else {
-            oi[i] = -1;
-            if (oc) oc[i] = pad;
-        }
-    }
-}
-
 __global__ void __launch_bounds__(TH)
 select_rows_global_kernel(const float *__restrict__ S, int64_t ld_s, int32_t n, int64_t n_tgt_rows,
-                   int32_t r_tgt, int32_t k_lm, int32_t *__restrict__ tsel_idx,
-                   float *__restrict__ tsel_cos, int64_t tsel_row0, int32_t stride_t,
-                   int32_t *__restrict__ lsel_idx, float *__restrict__ lsel_cos, int64_t lsel_row0,
-                   int32_t stride_l)
+                          int32_t r_tgt, int32_t k_lm, int32_t *__restrict__ tsel_idx,
+                          float *__restrict__ tsel_cos, int64_t tsel_row0, int32_t stride_t,
+                          int32_t *__restrict__ lsel_idx, float *__restrict__ lsel_cos, int64_t lsel_row0,
+                          int32_t stride_l)
 {
     __shared__ uint32_t hist[256];
     __shared__ uint64_t cand[SORT_MAX];
-    __shared__ uint32_t s_prefix;
-    __shared__ int s_remaining, s_cnt, s_warp[TH / 32];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ int s_misc[TH / 32 + 3];
     const int64_t r = blockIdx.x;
     const float *row = S + r * ld_s;
-    const bool is_tgt = r < n_tgt_rows;
-    const int R = is_tgt ? r_tgt : k_lm;
-
-    uint32_t prefix = 0, mask = 0;
-    int remaining = R;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int i = tid; i < 256; i += TH) hist[i] = 0;
-        __syncthreads();
-        for (int j = tid; j < n; j += TH) {
-            const uint32_t k = order_key(row[j]);
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        if (warp == 0) {
-            // suffix sums over 256 buckets: lane l owns buckets 255-8l .. 248-8l
-            uint32_t loc[8], sum = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { loc[i] = hist[255 - (lane * 8 + i)]; sum += loc[i]; }
-            uint32_t incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            uint32_t before = incl - sum;   // entries in higher buckets than this lane's
-            // the lane whose range crosses `remaining` finds the bucket
-            if (before < (uint32_t)remaining && incl >= (uint32_t)remaining) {
-                uint32_t cum = before;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (cum + loc[i] >= (uint32_t)remaining) {
-                        const uint32_t b = 255u - (uint32_t)(lane * 8 + i);
-                        s_prefix = prefix | (b << shift);
-                        s_remaining = remaining - (int)cum;
-                        break;
-                    }
-                    cum += loc[i];
-                }
-            }
-        }
-        __syncthreads();
-        prefix = s_prefix;
-        remaining = s_remaining;
-        mask |= 255u << shift;
-    }
-    const uint32_t T = prefix;
-    const int n_gt = R - remaining;   // entries strictly above T, all kept
-
-    if (tid == 0) s_cnt = 0;
-    __syncthreads();
-    for (int j = tid; j < n; j += TH) {
-        const uint32_t k = order_key(row[j]);
-        if (k > T) {
-            const int pos = atomicAdd(&s_cnt, 1);
-            cand[pos] = ((uint64_t)k << 32) | (uint64_t)(0xffffffffu - (uint32_t)j);
-        }
-    }
-    __syncthreads();
-    // the first `remaining` entries equal to T, in index order
-    int taken = 0;
-    for (int base = 0; base < n && taken < remaining; base += TH) {
-        const int j = base + tid;
-        const bool eq = j < n && order_key(row[j]) == T;
-        const unsigned bal = __ballot_sync(0xffffffffu, eq);
-        if (lane == 0) s_warp[warp] = __popc(bal);
-        __syncthreads();
-        int off = 0, tot = 0;
-        for (int w = 0; w < TH / 32; ++w) {
-            if (w < warp) off += s_warp[w];
-            tot += s_warp[w];
-        }
-        if (eq) {
-            const int pos = taken + off + __popc(bal & ((1u << lane) - 1u));
-            if (pos < remaining)
-                cand[n_gt + pos] = ((uint64_t)T << 32) | (uint64_t)(0xffffffffu - (uint32_t)j);
-        }
-        taken += tot;
-        __syncthreads();
-    }
-    // bitonic sort, descending, over the next power of two >= R
-    int P = 1;
-    while (P < R) P <<= 1;
-    for (int i = R + tid; i < P; i += TH) cand[i] = 0ull;
-    __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < P; i += TH) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t a = cand[i], b = cand[ixj];
-                    const bool desc = (i & k) == 0;
-                    if (desc ? (a < b) : (a > b)) { cand[i] = b; cand[ixj] = a; }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (is_tgt) {
-        write_list(cand, R, 0, nullptr, tsel_idx + (tsel_row0 + r) * (int64_t)stride_t,
-                   tsel_cos ? tsel_cos + (tsel_row0 + r) * (int64_t)stride_t : nullptr, stride_t, 0.f);
+    if (r < n_tgt_rows) {
+        const int64_t o = (tsel_row0 + r) * (int64_t)stride_t;
+        select_row_global<TH>(row, n, r_tgt, cand, hist, s_misc, tsel_idx + o, tsel_cos ? tsel_cos + o : nullptr,
+                              stride_t, 0.f);
     } else {
-        const int64_t l = lsel_row0 + (r - n_tgt_rows);
-        write_list(cand, R, 0, nullptr, lsel_idx + l * (int64_t)stride_l,
-                   lsel_cos ? lsel_cos + l * (int64_t)stride_l : nullptr, stride_l, 0.f);
+        const int64_t o = (lsel_row0 + (r - n_tgt_rows)) * (int64_t)stride_l;
+        select_row_global<TH>(row, n, k_lm, cand, hist, s_misc, lsel_idx + o, lsel_cos ? lsel_cos + o : nullptr,
+                              stride_l, 0.f);
     }
 }
 
-
-// Descending bucket search over NB bins: the bin holding the `remaining`-th
-// largest entry, how many of its entries are still needed, and its count.
-template <int NB>
-__device__ __forceinline__ void find_bucket(const uint32_t *hist, uint32_t remaining, uint32_t *wsum,
-                                            uint32_t *s_bin, uint32_t *s_rem, uint32_t *s_cnt)
-{
-    constexpr int BPT = NB / TH;    // bins per thread, highest bins to thread 0
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t loc[BPT], sum = 0;
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) { loc[i] = hist[NB - 1 - (tid * BPT + i)]; sum += loc[i]; }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    uint32_t wbase = 0;
-    for (int w = 0; w < warp; ++w) wbase += wsum[w];
-    const uint32_t before = wbase + incl - sum;
-    if (before < remaining && before + sum >= remaining) {
-        uint32_t cum = before;
-#pragma unroll
-        for (int i = 0; i < BPT; ++i) {
-            if (cum + loc[i] >= remaining) {
-                *s_bin = (uint32_t)(NB - 1 - (tid * BPT + i));
-                *s_rem = remaining - cum;
-                *s_cnt = loc[i];
-                break;
-            }
-            cum += loc[i];
-        }
-    }
-    __syncthreads();
-}
 
 // Bitonic sort of P (a power of two <= TH) 64-bit keys in shared memory,
 // descending, one element per thread.  Stages whose partners lie in the same
 // warp synchronise the warp only.
-__device__ __forceinline__ void bitonic_desc(uint64_t *cand, int P)
+__device__ __forceinline__ void bitonic_desc_warp(uint64_t *cand, int P)
 {
     const int i = threadIdx.x;
     int prev_j = TH;
@@ -299,7 +132,7 @@ __device__ __forceinline__ void select_row_smem(const float *__restrict__ row, i
         atomicAdd(&hist[k >> 21], 1u);
     }
     __syncthreads();
-    find_bucket<2048>(hist, (uint32_t)R, wsum, &s_bin, &s_rem, &s_cnt);
+    find_bucket<2048, TH>(hist, (uint32_t)R, wsum, &s_bin, &s_rem, &s_cnt);
     const uint32_t b1 = s_bin;
     uint32_t remaining = s_rem;
     const int nv = (n + 3) >> 2;   // uint4 groups (the tail group is masked by index)
@@ -314,7 +147,7 @@ __device__ __forceinline__ void select_row_smem(const float *__restrict__ row, i
             if (4 * g + c < n && (kk[c] >> 21) == b1) atomicAdd(&hist[(kk[c] >> 10) & 2047u], 1u);
     }
     __syncthreads();
-    find_bucket<2048>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
+    find_bucket<2048, TH>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
     const uint32_t p2 = (b1 << 11) | s_bin;     // top 22 bits
     remaining = s_rem;
     // third digit: bits 0..9
@@ -328,7 +161,7 @@ __device__ __forceinline__ void select_row_smem(const float *__restrict__ row, i
             if (4 * g + c < n && (kk[c] >> 10) == p2) atomicAdd(&hist[kk[c] & 1023u], 1u);
     }
     __syncthreads();
-    find_bucket<1024>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
+    find_bucket<1024, TH>(hist, remaining, wsum, &s_bin, &s_rem, &s_cnt);
     const uint32_t T = (p2 << 10) | s_bin;
     remaining = s_rem;
     const bool take_all_eq = s_cnt == remaining;
@@ -344,7 +177,7 @@ __device__ __forceinline__ void select_row_smem(const float *__restrict__ row, i
             const int i = 4 * g + c;
             if (i < n && (kk[c] > T || (take_all_eq && kk[c] == T))) {
                 const int pos = atomicAdd(&s_app, 1);
-                cand[pos] = ((uint64_t)kk[c] << 32) | (uint64_t)(0xffffffffu - (uint32_t)i);
+                cand[pos] = cand_word(kk[c], i);
             }
         }
     }
@@ -365,7 +198,7 @@ __device__ __forceinline__ void select_row_smem(const float *__restrict__ row, i
             if (eq) {
                 const int pos = taken + off + __popc(bal & ((1u << lane) - 1u));
                 if (pos < (int)remaining)
-                    cand[n_gt + pos] = ((uint64_t)T << 32) | (uint64_t)(0xffffffffu - (uint32_t)j);
+                    cand[n_gt + pos] = cand_word(T, j);
             }
             taken += tot;
             __syncthreads();
@@ -374,8 +207,8 @@ __device__ __forceinline__ void select_row_smem(const float *__restrict__ row, i
     int P = 1;
     while (P < R) P <<= 1;
     for (int i = R + tid; i < P; i += TH) cand[i] = 0ull;
-    bitonic_desc(cand, P);
-    write_list(cand, R, idx_base, idx_map, oi, oc, out_stride, pad);
+    bitonic_desc_warp(cand, P);
+    write_list<TH>(cand, R, idx_base, idx_map, oi, oc, out_stride, pad);
     __syncthreads();   // the shared arrays are reused by the block's next call
 }
 
@@ -440,8 +273,8 @@ merge_chunks_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, const in
 {
     const int64_t r = blockIdx.x;
     const Piece pc = pieces[find_piece(pieces, n_pieces, r, [](const Piece &x) { return x.row_begin; })];
-    if (pc.chunks <= 1) return;   // unchunked rows (1) and rows of the global-memory select (0)
     const int i = (int)(r - pc.row_begin);
+    if (pc.chunks <= 1 || i >= pc.th0) return;   // unchunked rows, rows of the per-piece or thresholded select
     const int M = pc.chunks * tmp_stride;
     const int64_t o = pc.tmp_off + (int64_t)i * M;
     if (i < pc.ntr) {

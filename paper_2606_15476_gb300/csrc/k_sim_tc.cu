@@ -55,7 +55,8 @@ namespace farm {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 256;
+constexpr int BN = kSimTileN;
+static_assert(BN / 32 == kTileTop, "one tile maximum per 32-column group");
 constexpr int STAGES = 4;
 constexpr int STAGE_BYTES = 48 * 1024;       // BM + BN rows of 128 bytes of operand data
 constexpr int THREADS = 192;
@@ -259,7 +260,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
               const __grid_constant__ CUtensorMap map_d0, const __grid_constant__ CUtensorMap map_d1,
               float *__restrict__ S, int64_t rows, int64_t n, int32_t k_slices, int64_t ld_s,
               int32_t m_tiles, int32_t n_tiles, const float *__restrict__ scale_q,
-              const float *__restrict__ scale_d, int32_t *err)
+              const float *__restrict__ scale_d, float *__restrict__ tops, int32_t *err)
 {
     using M = Mode<MODE>;
     constexpr bool TWO_OPERAND_TILES = MODE != kF16x3;
@@ -399,7 +400,9 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             float *srow = S + r * ld_s;
             const bool vec = (ld_s % 4) == 0;
             const float sr = (MODE == kFp8 && r < rows) ? scale_q[r] : 1.f;
-#pragma unroll 1
+            const bool keep_tops = tops != nullptr && r < rows;
+            float gmax[BN / 32];     // maximum of each 32-column group of row r in this tile
+#pragma unroll
             for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
                 const uint32_t lane_addr = tmem + (TWO_OPERAND_TILES ? buf * 256u : 0u) +
@@ -416,6 +419,18 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] *= sr * (col0 + i < n ? __ldg(scale_d + col0 + i) : 0.f);
                 }
+                if (keep_tops) {
+                    float m = -__int_as_float(0x7f800000);
+                    if (col0 + 32 <= n) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) m = fmaxf(m, v[i]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (col0 + i < n) m = fmaxf(m, v[i]);
+                    }
+                    gmax[c] = m;
+                }
                 if (r < rows) {
                     if (vec && col0 + 32 <= n) {
 #pragma unroll
@@ -427,6 +442,12 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                             if (col0 + i < n) srow[col0 + i] = v[i];
                     }
                 }
+            }
+            if (keep_tops) {
+                float4 *tp = reinterpret_cast<float4 *>(tops + (r * n_tiles + n0 / BN) * kTileTop);
+#pragma unroll
+                for (int j = 0; j < kTileTop; j += 4)
+                    tp[j / 4] = make_float4(gmax[j], gmax[j + 1], gmax[j + 2], gmax[j + 3]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
@@ -478,7 +499,7 @@ bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, in
 template <int MODE>
 cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void *d1, float *S, int64_t rows,
                       int64_t n, int32_t dim_pad, int64_t ld_s, const float *scale_q, const float *scale_d,
-                      int num_sms, int32_t *err, cudaStream_t s)
+                      float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
     using M = Mode<MODE>;
     constexpr bool TWO = MODE != kF16x3;
@@ -510,7 +531,7 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     const int grid = (int)std::min<int64_t>(tiles, std::max(num_sms, 1));
     sim_tc_kernel<MODE><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(mq0, mq1, md0, md1, S, rows, n,
                                                                        k_blocks, ld_s, m_tiles, n_tiles,
-                                                                       scale_q, scale_d, err);
+                                                                       scale_q, scale_d, tops, err);
     return cudaGetLastError();
 }
 
@@ -520,22 +541,23 @@ bool sim_tc_available() { return get_encoder(); }
 
 cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, const uint16_t *d_hi,
                                 const uint16_t *d_lo, float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s,
-                                int num_sms, int32_t *err, cudaStream_t s)
+                                float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kF16x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, num_sms, err, s);
+    return launch_tc<kF16x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms, err,
+                             s);
 }
 
 cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
-                               int32_t dim_pad, int64_t ld_s, int num_sms, int32_t *err, cudaStream_t s)
+                               int32_t dim_pad, int64_t ld_s, float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kBf16>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, nullptr, nullptr, num_sms, err, s);
+    return launch_tc<kBf16>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms, err, s);
 }
 
 cudaError_t launch_sim_tc_fp8(const uint8_t *q, const float *scale_q, const uint8_t *d, const float *scale_d,
-                              float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, int num_sms,
-                              int32_t *err, cudaStream_t s)
+                              float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, float *tops,
+                              int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, num_sms, err, s);
+    return launch_tc<kFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, tops, num_sms, err, s);
 }
 
 }  // namespace farm

@@ -54,6 +54,7 @@ def _load():
         "farm_sync": (C.c_int, [P]),
         "farm_similarity": (C.c_int, [P, I32, I64, P, I32, P, U32]),
         "farm_scene_info": (C.c_int, [P, I32, P, P]),
+        "farm_select_fallbacks": (C.c_int, [P, P, I32]),
         "farm_candidates": (C.c_int, [P, U64, P, P, P, P]),
         "farm_rank_rows_noalloc": (C.c_int, [P, I32, I64, P, I32, I32, P, P]),
         "farm_mlp_set": (C.c_int, [P, I32, I32, I32, P, P, P, P]),
@@ -79,6 +80,7 @@ _lib = _load()
 def exported_symbols():
     return ["farm_default_params", "farm_create", "farm_destroy", "farm_memory_upload",
             "farm_query_batch", "farm_topk", "farm_sync", "farm_similarity", "farm_scene_info",
+            "farm_select_fallbacks",
             "farm_candidates",
             "farm_rank_rows_noalloc", "farm_mlp_set", "farm_mlp_get", "farm_mlp_loss_grad",
             "farm_mlp_train", "farm_mlp_embed", "farm_set_profiling", "farm_stage_times",
@@ -209,6 +211,13 @@ def farm_topk(ctx, handle: int, k: int, n_q: int, out_idx=None, out_score=None, 
 
 def farm_sync(ctx) -> None:
     _ck(ctx, _lib.farm_sync(ctx))
+
+
+def farm_select_fallbacks(ctx, reset: bool = False) -> int:
+    """Rows the thresholded select handed to its exact fallback (see farm.h)."""
+    v = C.c_int64()
+    _ck(ctx, _lib.farm_select_fallbacks(ctx, C.byref(v), 1 if reset else 0))
+    return int(v.value)
 
 
 def farm_scene_info(ctx, scene_id: int):

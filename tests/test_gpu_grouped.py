@@ -159,3 +159,89 @@ def test_scene_info_guards_similarity_output(F, world):
         F.farm_similarity(ctx, 30, rows, scenes[30].n, F.PREC_FP8, out=np.zeros((2, 5), np.float32))
     S = F.farm_similarity(ctx, 30, rows, scenes[30].n, F.PREC_FP8)
     assert S.shape == (2, scenes[30].n) and np.isfinite(S).all()
+
+
+# ---- thresholded select: adversarial layouts ------------------------------------
+
+def _one_query(sc, tgt, m_preds, lm_embs, sid):
+    from synth import QueryBatch
+    m = len(m_preds)
+    return QueryBatch(tgt_emb=tgt[None, :].astype(np.float32), tgt_cls=np.array([-1], np.int32),
+                      c_off=np.array([0, m], np.int32), c_pred=np.asarray(m_preds, np.int32),
+                      c_emb=np.asarray(lm_embs, np.float32).reshape(m, sc.desc.shape[1]),
+                      scene_of_q=np.array([sid], np.int32))
+
+
+def test_exact_ties_beyond_the_candidate_buffer_take_the_exact_fallback(F):
+    """3,500 objects with one identical descriptor equal to the query: every
+    tied entry passes the tile-maxima threshold, the 2,048-word candidate
+    buffer overflows, and the exact fallback must list the first R tied
+    objects in index order."""
+    ctx = F.farm_create(0)
+    try:
+        sc = synth.make_scene(40, 12000, DIM, extent=(30.0, 30.0, 4.0), n_classes=8, n_views=3)
+        e = sc.desc[1000].copy()
+        sc.desc[1000:4500] = e
+        F.farm_memory_upload(ctx, 40, sc.desc, sc.cls, sc.box, sc.views)
+        qb = _one_query(sc, e, [0, 4], [e, sc.desc[7]], 40)
+        F.farm_select_fallbacks(ctx, reset=True)
+        h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred,
+                               qb.c_emb, F.PREC_FP32)
+        t, l = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
+        assert F.farm_select_fallbacks(ctx) >= 2     # the target row and the first landmark row
+        R = t.shape[1]
+        assert t[0].tolist() == list(range(1000, 1000 + R))
+        assert l[0].tolist() == list(range(1000, 1000 + l.shape[1]))
+        fails = parity.check_candidates(sc, qb, t, l)
+        assert not fails, fails[:3]
+    finally:
+        F.farm_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_top_ranks_crowded_into_one_tile(F, prec):
+    """The 300 best objects are objects 0-299: ten 32-object groups, so only
+    ten of them enter the threshold's set of group maxima; the threshold is
+    loose, many more candidates pass, and the lists must still be exact."""
+    ctx = F.farm_create(0)
+    try:
+        rng = np.random.default_rng(41)
+        sc = synth.make_scene(41, 6000, DIM, extent=(30.0, 30.0, 4.0), n_classes=8, n_views=3)
+        e = rng.standard_normal(DIM).astype(np.float32)
+        e /= np.linalg.norm(e)
+        near = e + 0.05 * rng.standard_normal((300, DIM)).astype(np.float32)
+        sc.desc[:300] = near / np.linalg.norm(near, axis=1, keepdims=True)
+        F.farm_memory_upload(ctx, 41, sc.desc, sc.cls, sc.box, sc.views)
+        qb = _one_query(sc, e, [1, 4], [sc.desc[5000], e], 41)
+        F.farm_select_fallbacks(ctx, reset=True)
+        code = {"fp32": F.PREC_FP32, "bf16": F.PREC_BF16}[prec]
+        h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred,
+                               qb.c_emb, code)
+        out = F.farm_topk(ctx, h, 10, qb.n_q)
+        t, l = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
+        assert F.farm_select_fallbacks(ctx) == 0
+        assert set(t[0].tolist()) <= set(range(300))
+        fails = parity.check_candidates(sc, qb, t, l)
+        assert not fails, fails[:3]
+        rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"])
+        assert rep.ok(), rep.summary()
+    finally:
+        F.farm_destroy(ctx)
+
+
+def test_no_fallback_on_the_site_scene(F):
+    """The 20,000-object site scene: no row of the full 4,096-query batch needs
+    the exact fallback."""
+    scenes, qb = synth.workload("site_n20k_d1152")
+    sc = scenes[0]
+    ctx = F.farm_create(0)
+    try:
+        F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+        for code in (F.PREC_FP32, F.PREC_BF16):
+            F.farm_select_fallbacks(ctx, reset=True)
+            h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred,
+                                   qb.c_emb, code)
+            F.farm_topk(ctx, h, 10, qb.n_q)
+            assert F.farm_select_fallbacks(ctx) == 0, code
+    finally:
+        F.farm_destroy(ctx)
