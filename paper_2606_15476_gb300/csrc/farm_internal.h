@@ -296,9 +296,12 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
                                  int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
                                  int32_t *n_fallback, cudaStream_t s);
 // Grouped FP32 rescore (one block per launch row): the keep_t / keep_l
-// candidates of bsel_* (strides cstride_t / cstride_l; values nullable, then
-// no band skip) against the normalised rows Q32 -> the R / klm best in rank
-// order into tsel_idx / tsel_cos and lsel_idx.
+// candidates of bsel_* (strides cstride_t / cstride_l; descending by their
+// reduced-precision values bsel_tv / bsel_lv, nullable) are re-scored with
+// exact FP32 dot products of the unit rows Q32 and the descriptors d32, and
+// the R / klm best in rank order go to tsel_idx / tsel_cos and lsel_idx (-1 /
+// 0 past the list).  With values, a candidate more than `band` below the
+// list's last kept value is skipped.
 cudaError_t launch_rescore_grouped(const Piece *pieces, int32_t n_pieces, int64_t total_rows, const float *Q32,
                                    int32_t dim_pad, const int32_t *bsel_t, const float *bsel_tv, int32_t cstride_t,
                                    const int32_t *bsel_l, const float *bsel_lv, int32_t cstride_l, float band,
@@ -337,17 +340,6 @@ struct SceneDev {
     int32_t n_views;
     int32_t pad;
 };
-
-// Re-score C candidates per row with exact FP32 dot products of unit rows and
-// keep the R best in rank order: row r (of `rows`) uses Q32 row q_row0 + r,
-// candidates cand[(cand_row0 + r) * cand_stride + c] (descending by their
-// reduced-precision values cand_val, same layout; nullable), writes
-// out_idx/out_cos[(out_row0 + r) * out_stride + i] (-1 / 0 past R).  With
-// cand_val, candidates more than `band` below the R-th value are skipped.
-cudaError_t launch_rescore(const float *Q32, int64_t q_row0, int32_t dim_pad, const float *D32, const int32_t *cand,
-                           const float *cand_val, float band, int32_t C, int32_t cand_stride, int64_t cand_row0,
-                           int64_t rows, int32_t R, int32_t *out_idx, float *out_cos, int32_t out_stride,
-                           int64_t out_row0, cudaStream_t s);
 
 struct ComposeArgs {
     int64_t n_q;

@@ -12,9 +12,10 @@
 // lies more than `band` below the R-th value is skipped (it would need an
 // arithmetic error above the band to belong to the top R).
 //
-// One CTA per row: the row is staged in shared memory, each warp takes
-// candidates in turn (lanes stride the descriptor in float4, then a shuffle
-// reduction), and a bitonic sort over (cosine key, index) orders the scores.
+// One CTA per row: the row is staged in shared memory, each warp takes two
+// candidates at a time (lanes stride both descriptors in float4 with four
+// loads of each in flight, then shuffle reductions), and a bitonic sort over
+// (cosine key, index) orders the scores.
 #include "farm_internal.h"
 
 namespace farm {
@@ -50,24 +51,56 @@ __device__ __forceinline__ void rescore_row(const float *__restrict__ q, int32_t
     for (int i = tid; i < nv; i += TH) q4[i] = src[i];
     __syncthreads();
     const float thr = cv ? cv[R - 1] - band : 0.f;
-    for (int c = warp; c < C; c += TH / 32) {
-        if (cv && cv[c] < thr) {
-            if (lane == 0) key[c] = 0ull;
+    // two candidates per warp step, four float4 loads of each in flight per lane
+    for (int c0 = 2 * warp; c0 < C; c0 += 2 * (TH / 32)) {
+        const int c1 = c0 + 1;
+        const bool do0 = !(cv && cv[c0] < thr);
+        const bool do1 = c1 < C && !(cv && cv[c1] < thr);
+        if (!do0 && !do1) {
+            if (lane == 0) {
+                key[c0] = 0ull;
+                if (c1 < C) key[c1] = 0ull;
+            }
             continue;
         }
-        const int32_t e = cr[c];
-        const float4 *dp = reinterpret_cast<const float4 *>(D32 + (int64_t)e * dim_pad);
-        float acc = 0.f;
-        for (int i = lane; i < nv; i += 32) {
-            const float4 a = q4[i], b = __ldg(dp + i);
-            acc = fmaf(a.x, b.x, acc);
-            acc = fmaf(a.y, b.y, acc);
-            acc = fmaf(a.z, b.z, acc);
-            acc = fmaf(a.w, b.w, acc);
+        const int32_t e0 = do0 ? cr[c0] : 0, e1 = do1 ? cr[c1] : 0;
+        const float4 *p0 = reinterpret_cast<const float4 *>(D32 + (int64_t)e0 * dim_pad);
+        const float4 *p1 = reinterpret_cast<const float4 *>(D32 + (int64_t)e1 * dim_pad);
+        float a0 = 0.f, a1 = 0.f;
+        for (int base = 0; base < nv; base += 4 * 32) {
+            float4 x0[4], x1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = base + u * 32 + lane;
+                const bool in = i < nv;
+                x0[u] = (in && do0) ? __ldg(p0 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                x1[u] = (in && do1) ? __ldg(p1 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = base + u * 32 + lane;
+                if (i < nv) {
+                    const float4 q = q4[i];
+                    a0 = fmaf(q.x, x0[u].x, a0);
+                    a0 = fmaf(q.y, x0[u].y, a0);
+                    a0 = fmaf(q.z, x0[u].z, a0);
+                    a0 = fmaf(q.w, x0[u].w, a0);
+                    a1 = fmaf(q.x, x1[u].x, a1);
+                    a1 = fmaf(q.y, x1[u].y, a1);
+                    a1 = fmaf(q.z, x1[u].z, a1);
+                    a1 = fmaf(q.w, x1[u].w, a1);
+                }
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) key[c] = ((uint64_t)order_key(acc) << 32) | (uint64_t)(0xffffffffu - (uint32_t)e);
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        }
+        if (lane == 0) {
+            key[c0] = do0 ? ((uint64_t)order_key(a0) << 32) | (uint64_t)(0xffffffffu - (uint32_t)e0) : 0ull;
+            if (c1 < C) key[c1] = do1 ? ((uint64_t)order_key(a1) << 32) | (uint64_t)(0xffffffffu - (uint32_t)e1) : 0ull;
+        }
     }
     int P = 1;
     while (P < C) P <<= 1;
@@ -97,18 +130,6 @@ __device__ __forceinline__ void rescore_row(const float *__restrict__ q, int32_t
     }
 }
 
-__global__ void __launch_bounds__(TH)
-rescore_kernel(const float *__restrict__ Q32, int64_t q_row0, int32_t dim_pad, const float *__restrict__ D32,
-               const int32_t *__restrict__ cand, const float *__restrict__ cand_val, float band, int32_t C,
-               int32_t cand_stride, int64_t cand_row0, int32_t R, int32_t *__restrict__ out_idx,
-               float *__restrict__ out_cos, int32_t out_stride, int64_t out_row0)
-{
-    const int64_t r = blockIdx.x;
-    const int64_t co = (cand_row0 + r) * (int64_t)cand_stride, oo = (out_row0 + r) * (int64_t)out_stride;
-    rescore_row(Q32 + (q_row0 + r) * (int64_t)dim_pad, dim_pad, D32, cand + co, cand_val ? cand_val + co : nullptr,
-                band, C, R, out_idx + oo, out_cos ? out_cos + oo : nullptr, out_stride);
-}
-
 // Grouped rescore: block -> (piece, row) through the piece table.
 __global__ void __launch_bounds__(TH)
 rescore_grouped_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, const float *__restrict__ Q32,
@@ -134,23 +155,6 @@ rescore_grouped_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, const
 }
 
 }  // namespace
-
-cudaError_t launch_rescore(const float *Q32, int64_t q_row0, int32_t dim_pad, const float *D32, const int32_t *cand,
-                           const float *cand_val, float band, int32_t C, int32_t cand_stride, int64_t cand_row0,
-                           int64_t rows, int32_t R, int32_t *out_idx, float *out_cos, int32_t out_stride,
-                           int64_t out_row0, cudaStream_t s)
-{
-    if (rows <= 0) return cudaSuccess;
-    if (C < 1 || C > SORT_MAX || R < 1 || R > C || R > out_stride || dim_pad % 4 != 0) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)dim_pad * sizeof(float);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    rescore_kernel<<<(unsigned)rows, TH, smem, s>>>(Q32, q_row0, dim_pad, D32, cand, cand_val, band, C, cand_stride,
-                                                    cand_row0, R, out_idx, out_cos, out_stride, out_row0);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_rescore_grouped(const Piece *pieces, int32_t n_pieces, int64_t total_rows, const float *Q32,
                                    int32_t dim_pad, const int32_t *bsel_t, const float *bsel_tv, int32_t cstride_t,

@@ -72,7 +72,11 @@ select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops
     __syncthreads();
     const uint32_t T = kth_key<TT>(ukeys, U, R, hist, wsum, s3);
 
-    // one pass over the row: every entry with key >= T
+    // one pass over the row: every entry with key >= T.  tau = key_value(T)
+    // is the union value itself (never -0), and for non-NaN x, x >= tau holds
+    // exactly when order_key(x) >= T, so the pass compares floats and builds
+    // keys only for the entries it keeps.
+    const float tau = key_value(T);
     if (tid == 0) s_cnt = 0;
     __syncthreads();
     const int n4 = n >> 2;
@@ -91,19 +95,18 @@ select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops
             const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const uint32_t k = order_key(x[c]);
-                if (k >= T) {
+                if (x[c] >= tau) {
                     const int pos = atomicAdd(&s_cnt, 1);
-                    if (pos < CAP) cand[pos] = cand_word(k, 4 * g + c);
+                    if (pos < CAP) cand[pos] = cand_word(order_key(x[c]), 4 * g + c);
                 }
             }
         }
     }
     for (int j = 4 * n4 + tid; j < n; j += TT) {
-        const uint32_t k = order_key(__ldcs(row + j));
-        if (k >= T) {
+        const float x = __ldcs(row + j);
+        if (x >= tau) {
             const int pos = atomicAdd(&s_cnt, 1);
-            if (pos < CAP) cand[pos] = cand_word(k, j);
+            if (pos < CAP) cand[pos] = cand_word(order_key(x), j);
         }
     }
     __syncthreads();
