@@ -28,8 +28,8 @@ struct farm_ctx {
     // pinned staging for per-batch metadata
     int32_t *h_stage = nullptr;
     size_t h_stage_n = 0;
-    farm::Piece *h_pieces = nullptr;  // pinned staging of the batch's piece tables
-    size_t h_pieces_n = 0;
+    uint8_t *h_blob = nullptr;        // pinned staging of the batch's piece tables and tensor maps
+    size_t h_blob_n = 0;
     cudaEvent_t stage_done = nullptr;
     // profiling marks
     struct Mark { int stage; cudaEvent_t a, b; };
@@ -326,7 +326,7 @@ farm_status farm_destroy(farm_ctx *ctx)
     cudaFree(c.mlp.w2b);
     if (c.h_err) cudaFreeHost(c.h_err);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-    if (ctx->h_pieces) cudaFreeHost(ctx->h_pieces);
+    if (ctx->h_blob) cudaFreeHost(ctx->h_blob);
     if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
     for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
@@ -677,8 +677,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
         const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
         const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows_g, (int64_t)(kSimCapBytes / (ld * 4))));
-        const int64_t n_tiles = (s.n + farm::kSimTileN - 1) / farm::kSimTileN;
-        const int32_t uni = (int32_t)std::min<int64_t>(n_tiles * farm::kTileTop, 8192);
+        const int32_t uni = (int32_t)std::min<int64_t>(farm::group_count(s.n), 8192);
         // long rows of the shared-memory select: column chunks, merged after
         int32_t chunks = 1, chunk_len = (int32_t)s.n;
         bool global_select = false;
@@ -721,7 +720,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             if (tile_tops) {
                 pc.th0 = uni >= pc.keep_t ? 0 : (uni >= pc.keep_l ? pc.ntr : pc.rows);
                 pc.tops_off = bt.tops;
-                bt.tops += nr * n_tiles * farm::kTileTop;
+                bt.tops += nr * farm::group_stride(s.n);
                 if (pc.th0 < pc.rows) {
                     bt.tblocks += pc.rows - pc.th0;
                     bt.max_union = std::max(bt.max_union, uni);
@@ -754,33 +753,92 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     }
     float *d_sim, *tmp_val = nullptr, *d_tops = nullptr;
     int32_t *tmp_idx = nullptr;
-    farm::Piece *d_pieces;
     CK(ws_get(ctx, farm::B_SIM, (size_t)s_need, &d_sim));
     if (tile_tops) CK(ws_get(ctx, farm::B_TOPS, (size_t)tops_need, &d_tops));
-    CK(ws_get(ctx, farm::B_PIECES, pieces.size(), &d_pieces));
     bool any_chunked = false;
     for (const auto &bt : batches) any_chunked |= bt.chunked;
     if (any_chunked) {
         CK(ws_get(ctx, farm::B_CHUNK_IDX, (size_t)tmp_need, &tmp_idx));
         CK(ws_get(ctx, farm::B_CHUNK_VAL, (size_t)tmp_need, &tmp_val));
     }
-    if (ctx->h_pieces_n < pieces.size()) {
-        if (ctx->h_pieces) cudaFreeHost(ctx->h_pieces);
-        ctx->h_pieces = nullptr;
-        ctx->h_pieces_n = 0;
-        CK(cudaHostAlloc(&ctx->h_pieces, pieces.size() * sizeof(farm::Piece) * 5 / 4 + sizeof(farm::Piece),
-                         cudaHostAllocDefault));
-        ctx->h_pieces_n = pieces.size() * 5 / 4 + 1;
+    // tensor-core similarity: one grouped launch per batch over its pieces;
+    // each scene's two B tensor maps are encoded once per call
+    int sim_mode = -1;
+    if (precision == FARM_PREC_FP32) sim_mode = farm::kSimF16x3;
+    else if (precision == FARM_PREC_BF16 || precision == FARM_PREC_LEARNED) sim_mode = farm::kSimBf16;
+    else if (precision == FARM_PREC_FP8) sim_mode = farm::kSimFp8;
+    if (sim_mode >= 0 && !farm::sim_tc_available())
+        return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
+    std::vector<int32_t> map_of_scene;
+    std::vector<int32_t> map_scenes;
+    if (precision == FARM_PREC_LEARNED)     // (re)computes the scenes' learned embeddings the maps point at
+        for (const auto &g : groups) CK(farm::learned_refresh_scene(ctx, g.sid));
+    if (sim_mode >= 0) {
+        map_of_scene.assign(kMaxScenes, -1);
+        for (const auto &g : groups)
+            if (map_of_scene[g.sid] < 0) {
+                map_of_scene[g.sid] = (int32_t)map_scenes.size();
+                map_scenes.push_back(g.sid);
+            }
     }
-    std::memcpy(ctx->h_pieces, pieces.data(), pieces.size() * sizeof(farm::Piece));
+    // device blob: select pieces | GEMM pieces | tensor maps (128-byte aligned sections)
+    const size_t off_gp = round_up((int64_t)(pieces.size() * sizeof(farm::Piece)), 128);
+    const size_t off_maps = off_gp + round_up((int64_t)(pieces.size() * sizeof(farm::GemmPiece)), 128);
+    const size_t blob_bytes = off_maps + map_scenes.size() * 2 * farm::kTensorMapBytes;
+    uint8_t *d_blob;
+    CK(ws_get(ctx, farm::B_PIECES, blob_bytes, &d_blob));
+    if (ctx->h_blob_n < blob_bytes) {
+        if (ctx->h_blob) cudaFreeHost(ctx->h_blob);
+        ctx->h_blob = nullptr;
+        ctx->h_blob_n = 0;
+        CK(cudaHostAlloc(&ctx->h_blob, blob_bytes * 5 / 4 + 256, cudaHostAllocDefault));
+        ctx->h_blob_n = blob_bytes * 5 / 4 + 256;
+    }
+    farm::Piece *d_pieces = reinterpret_cast<farm::Piece *>(d_blob);
+    farm::GemmPiece *d_gpieces = reinterpret_cast<farm::GemmPiece *>(d_blob + off_gp);
+    std::memcpy(ctx->h_blob, pieces.data(), pieces.size() * sizeof(farm::Piece));
+    std::vector<int64_t> batch_tiles(batches.size(), 0);
+    if (sim_mode >= 0) {
+        farm::GemmPiece *hg = reinterpret_cast<farm::GemmPiece *>(ctx->h_blob + off_gp);
+        for (size_t b = 0; b < batches.size(); ++b) {
+            int64_t tiles = 0;
+            for (size_t k = batches[b].p0; k < batches[b].p0 + batches[b].np; ++k) {
+                const farm::Piece &pc = pieces[k];
+                const Scene &sc = c.scenes[piece_sid[k]];
+                farm::GemmPiece gp{};
+                gp.q_row0 = pc.q_row0;
+                gp.s_off = pc.s_off;
+                gp.tops_off = tile_tops ? pc.tops_off : -1;
+                gp.scale_d = sim_mode == farm::kSimFp8 ? sc.desc_scale : nullptr;
+                gp.bmap = d_blob + off_maps + (size_t)map_of_scene[piece_sid[k]] * 2 * farm::kTensorMapBytes;
+                gp.rows = pc.rows;
+                gp.n = pc.n;
+                gp.ld = pc.ld;
+                gp.tile_begin = (int32_t)tiles;
+                tiles += farm::sim_cluster_tiles(pc.rows, pc.n);
+                hg[k] = gp;
+            }
+            if (tiles > 0x7fffffffLL) return fail(ctx, FARM_EINVAL, "similarity batch exceeds 2^31 tiles");
+            batch_tiles[b] = tiles;
+        }
+        for (size_t m = 0; m < map_scenes.size(); ++m) {
+            const Scene &sc = c.scenes[map_scenes[m]];
+            void *out = ctx->h_blob + off_maps + m * 2 * farm::kTensorMapBytes;
+            bool ok;
+            if (precision == FARM_PREC_FP32) ok = farm::sim_tc_encode_b(sim_mode, out, sc.desc_hi, sc.desc_lo, sc.n, sc.dim_pad);
+            else if (precision == FARM_PREC_BF16) ok = farm::sim_tc_encode_b(sim_mode, out, sc.desc_bf16, nullptr, sc.n, sc.dim_pad);
+            else if (precision == FARM_PREC_LEARNED) ok = farm::sim_tc_encode_b(sim_mode, out, sc.comp, nullptr, sc.n, c.mlp.P);
+            else ok = farm::sim_tc_encode_b(sim_mode, out, sc.desc_fp8, nullptr, sc.n, sc.dim_pad);
+            if (!ok) return fail(ctx, FARM_ECUDA, "tensor map encoding failed for scene " + std::to_string(map_scenes[m]));
+        }
+    }
 
     // ---- stage 0: inputs and normalisation
     const int m0 = mark_begin(ctx, 0);
     CK(cudaMemcpyAsync(d_rowmap, h_rowmap, (size_t)(n_q + n_c) * 4, cudaMemcpyHostToDevice, c.stream));
     CK(cudaMemcpyAsync(d_perm, h_perm, (size_t)n_q * 4, cudaMemcpyHostToDevice, c.stream));
     CK(cudaMemcpyAsync(d_meta, h_meta, (size_t)n_q * 8 * 4, cudaMemcpyHostToDevice, c.stream));
-    CK(cudaMemcpyAsync(d_pieces, ctx->h_pieces, pieces.size() * sizeof(farm::Piece), cudaMemcpyHostToDevice,
-                       c.stream));
+    CK(cudaMemcpyAsync(d_blob, ctx->h_blob, blob_bytes, cudaMemcpyHostToDevice, c.stream));
     CK(cudaEventRecord(ctx->stage_done, c.stream));
     const float *src_t = tgt_emb, *src_c = c_emb;
     if (!dev) {
@@ -799,23 +857,35 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                                            ops.qbf, c.d_err, farm::kErrBadRow, c.stream));
     if (precision == FARM_PREC_FP8)
         LAUNCH(farm::launch_quantize_fp8_rows(ops.q32, rows_total, dim_pad, ops.qf8, ops.qscale, c.stream));
-    if (precision == FARM_PREC_LEARNED) {
-        for (const auto &g : groups) CK(farm::learned_refresh_scene(ctx, g.sid));
-        CK(farm::learned_embed_rows(ctx, ops.qbf, rows_total, ops.qcomp));
-    }
+    if (precision == FARM_PREC_LEARNED) CK(farm::learned_embed_rows(ctx, ops.qbf, rows_total, ops.qcomp));
     mark_end(ctx, m0);
 
     // ---- stages 1-2: similarity per piece, then the batch's rank selection
     int32_t *sel_ti = reduced ? bsel_t : tsel_idx, *sel_li = reduced ? bsel_l : lsel_idx;
     float *sel_tc = reduced ? bsel_tv : tsel_cos, *sel_lc = reduced ? bsel_lv : nullptr;
     const int32_t sel_st = reduced ? cstride_t : stride_t, sel_sl = reduced ? cstride_l : stride_l;
-    for (const auto &bt : batches) {
+    for (size_t b = 0; b < batches.size(); ++b) {
+        const Batch &bt = batches[b];
         const int m1 = mark_begin(ctx, 1);
-        for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
-            const farm::Piece &pc = pieces[k];
-            farm_status st = run_similarity(ctx, precision, ops, pc.q_row0, pc.rows, c.scenes[piece_sid[k]],
-                                            d_sim + pc.s_off, pc.ld, tile_tops ? d_tops + pc.tops_off : nullptr);
-            if (st != FARM_OK) return st;
+        if (sim_mode >= 0) {
+            const void *q0, *q1 = nullptr;
+            int32_t kdim = dim_pad;
+            int64_t q_rows = rows_total;
+            if (precision == FARM_PREC_FP32) { q0 = ops.qhi; q1 = ops.qlo; }
+            else if (precision == FARM_PREC_BF16) q0 = ops.qbf;
+            else if (precision == FARM_PREC_LEARNED) { q0 = ops.qcomp; kdim = c.mlp.P; }
+            else q0 = ops.qf8;
+            LAUNCH(farm::launch_sim_tc_grouped(sim_mode, q0, q1, q_rows, kdim, d_gpieces + bt.p0, (int32_t)bt.np,
+                                               batch_tiles[b], d_sim, tile_tops ? d_tops : nullptr,
+                                               precision == FARM_PREC_FP8 ? ops.qscale : nullptr, c.num_sms, c.d_err,
+                                               c.stream));
+        } else {
+            for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
+                const farm::Piece &pc = pieces[k];
+                farm_status st = run_similarity(ctx, precision, ops, pc.q_row0, pc.rows, c.scenes[piece_sid[k]],
+                                                d_sim + pc.s_off, pc.ld, nullptr);
+                if (st != FARM_OK) return st;
+            }
         }
         mark_end(ctx, m1);
         const int m2 = mark_begin(ctx, 2);

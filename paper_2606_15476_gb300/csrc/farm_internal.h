@@ -197,17 +197,59 @@ cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_vi
 cudaError_t launch_sim_simt(const float *q, const float *d, float *S, int64_t rows, int64_t n,
                             int32_t dim_pad, int64_t ld_s, cudaStream_t s);
 
-// The tensor-core kernels work on column tiles of kSimTileN objects.  With a
-// non-null `tops` ([rows, ceil(n / kSimTileN), kTileTop] FP32, 16-byte
-// aligned) the epilogue also writes, per row, the maximum of every group of
-// 32 consecutive objects (kTileTop groups per tile; -inf for a group past the
-// row end): entries of the row, so their R-th largest value bounds the row's
-// R-th largest from below (the thresholded select uses it).
+// Tiles of the tensor-core similarity kernels: kSimTileM query rows x
+// kSimTileN objects per CTA, kSimCluster vertically adjacent CTAs per cluster
+// sharing one descriptor tile.
+constexpr int kSimTileM = 128;
 constexpr int kSimTileN = 256;
-constexpr int kTileTop = 8;
+constexpr int kSimCluster = 2;
+enum SimMode { kSimF16x3 = 0, kSimBf16 = 1, kSimFp8 = 2 };
 
-// Same product on the tensor cores with three FP16 terms,
-// hi*hi + 2^-11 (hi*lo + lo*hi), from the split the normalisation writes.
+// Group maxima: with a non-null `tops` the similarity epilogue also writes,
+// per row, the maximum of every group of 32 consecutive objects (-inf for
+// positions past the row end), group_stride(n) floats per row, 16-byte
+// aligned.  They are entries of the row, so their R-th largest value bounds
+// the row's R-th largest from below (the thresholded select uses it).
+__host__ __device__ constexpr int64_t group_count(int64_t n) { return (n + 31) / 32; }
+__host__ __device__ constexpr int64_t group_stride(int64_t n) { return (group_count(n) + 7) / 8 * 8; }
+
+// One block of query rows against one scene in a grouped similarity launch.
+struct GemmPiece {
+    int64_t q_row0;          // first row of the block in the operand arrays
+    int64_t s_off;           // S offset of the block's first row (floats; a multiple of 4)
+    int64_t tops_off;        // group-maxima offset of the first row (floats, a multiple of 8); -1: none
+    const float *scale_d;    // FP8 per-object scales of the scene
+    const void *bmap;        // the scene's two B tensor maps (device memory, 64-byte aligned)
+    int32_t rows, n, ld;     // rows of the block, objects, leading dimension of S
+    int32_t tile_begin;      // first cluster tile of the block in the launch
+};
+constexpr size_t kTensorMapBytes = 128;
+
+// Cluster tiles of one block of `rows` rows against `n` objects.
+inline int64_t sim_cluster_tiles(int64_t rows, int64_t n)
+{
+    const int64_t mt = (rows + kSimTileM - 1) / kSimTileM;
+    return (mt + kSimCluster - 1) / kSimCluster * ((n + kSimTileN - 1) / kSimTileN);
+}
+
+// The two B tensor maps (hi / lo, or the one operand twice) of a scene's
+// descriptor operand in `mode`, written to host memory `out`
+// (2 * kTensorMapBytes, 64-byte aligned).  False when the encoder fails.
+bool sim_tc_encode_b(int mode, void *out, const void *d0, const void *d1, int64_t n, int32_t dim_pad);
+
+// Grouped launch: every piece of the device table `pieces` (n_pieces,
+// ordered by tile_begin; total_tiles cluster tiles) against its scene, the
+// query operands q0 / q1 ([rows_total, dim_pad] in the mode's element type)
+// and FP8 row scales scale_q.  S and tops are the bases the pieces' offsets
+// refer to (tops nullable).
+cudaError_t launch_sim_tc_grouped(int mode, const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
+                                  const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S,
+                                  float *tops, const float *scale_q, int num_sms, int32_t *err, cudaStream_t s);
+
+// One problem (rows x n, S leading dimension ld_s, group maxima at tops with
+// group_stride(n) floats per row, nullable) on the tensor cores.
+// Three FP16 terms, hi*hi + 2^-11 (hi*lo + lo*hi), from the split the
+// normalisation writes.
 cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, const uint16_t *d_hi,
                                 const uint16_t *d_lo, float *S, int64_t rows, int64_t n, int32_t dim_pad,
                                 int64_t ld_s, float *tops, int num_sms, int32_t *err, cudaStream_t s);
@@ -244,8 +286,8 @@ cudaError_t launch_select_rows_ex(const float *S, int64_t ld_s, int64_t n, int64
 // launch, stored at S + s_off with leading dimension ld; the first ntr are
 // target rows.  Rows [0, th0) are selected by the shared-memory select
 // (launch_select_grouped, blocks from block_begin), rows [th0, rows) by the
-// thresholded select (launch_select_thresh, blocks from tblock_begin, tile
-// maxima at tops + tops_off, rows of ceil(n / kSimTileN) * kTileTop values).
+// thresholded select (launch_select_thresh, blocks from tblock_begin, group
+// maxima at tops + tops_off, group_stride(n) floats per row).
 // A row of the shared-memory select longer than its limit is selected in
 // `chunks` column chunks of chunk_len entries, whose lists (tmp_stride
 // entries each, rows at tmp + tmp_off + i * chunks * tmp_stride) are merged
@@ -260,7 +302,7 @@ struct Piece {
     int64_t t_row0;         // list row of the first target row
     int64_t l_row0;         // list row of the first landmark row
     int64_t tmp_off;        // chunk-list offset of the first row (entries)
-    int64_t tops_off;       // tile-maxima offset of the first row (floats)
+    int64_t tops_off;       // group-maxima offset of the first row (floats)
     int32_t rows, ntr, n, ld;
     int32_t keep_t, keep_l; // list lengths the select keeps (R / K_a, or the rescore's C)
     int32_t R, klm;         // list lengths after a rescore
@@ -286,9 +328,9 @@ cudaError_t launch_merge_chunks(const Piece *pieces, int32_t n_pieces, int64_t t
                                 int32_t *tsel_idx, float *tsel_cos, int32_t stride_t, int32_t *lsel_idx,
                                 float *lsel_cos, int32_t stride_l, cudaStream_t s);
 // Thresholded select of rows [th0, rows) of every piece (one block per row,
-// total_blocks of them), from the tile maxima `tops` the tensor-core
-// similarity kernel wrote; each row needs ceil(n / kSimTileN) * kTileTop >=
-// its list length.  max_union: the largest such union of the launch.  Rows
+// total_blocks of them), from the group maxima `tops` the tensor-core
+// similarity kernel wrote; each row needs group_count(n) >= its list length.
+// max_union: the largest group count of the launch (at most 8,192 are used).  Rows
 // whose candidates overflow fall back to an exact global-memory select and
 // are counted in *n_fallback (device).  Outputs as launch_select_grouped.
 cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,

@@ -63,11 +63,10 @@ select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops
     }
     const int n = pc.n;
     const float *row = S + pc.s_off + (int64_t)i * pc.ld;
-    const int n_tiles = (n + kSimTileN - 1) / kSimTileN;
-    const int U = min(n_tiles * kTileTop, UNION_MAX);
+    const int U = (int)min(group_count(n), (int64_t)UNION_MAX);
 
     // tau: the R-th largest key of the group maxima (the planner routes rows with U < R elsewhere)
-    const float *tp = tops + pc.tops_off + (int64_t)i * n_tiles * kTileTop;
+    const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(n);
     for (int j = tid; j < U; j += TT) ukeys[j] = order_key(__ldg(tp + j));
     __syncthreads();
     const uint32_t T = kth_key<TT>(ukeys, U, R, hist, wsum, s3);

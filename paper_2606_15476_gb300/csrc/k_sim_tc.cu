@@ -54,25 +54,25 @@
 namespace farm {
 namespace {
 
-constexpr int BM = 128;
+constexpr int BM = kSimTileM;
 constexpr int BN = kSimTileN;
-static_assert(BN / 32 == kTileTop, "one tile maximum per 32-column group");
+static_assert(BN % 128 == 0, "group maxima are stored four at a time");
 constexpr int STAGES = 4;
 constexpr int STAGE_BYTES = 48 * 1024;       // BM + BN rows of 128 bytes of operand data
 constexpr int THREADS = 192;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;    // try_wait polls before giving up (about a second)
-constexpr int GROUP_M = 16;                  // tile raster: 16 row tiles share each column tile
+constexpr int GROUP_M = 8;                   // tile raster: 8 cluster rows (16 row tiles) share each column tile
+constexpr int CM = kSimCluster;              // CTAs per cluster: vertically adjacent tiles sharing one B tile
 constexpr int ACC_CORR = 256;                // TMEM column of the correction accumulator (FP16x3 mode)
 constexpr float RESID_SCALE_INV = 1.f / 2048.f;   // the residual operands carry a factor 2^11
 
-enum : int { kF16x3 = 0, kBf16 = 1, kFp8 = 2 };
 
 // Per-mode layout of a pipeline stage.
 template <int MODE>
 struct Mode;
 template <>
-struct Mode<kF16x3> {                        // three-term FP16 with scaled residuals
+struct Mode<kSimF16x3> {                        // three-term FP16 with scaled residuals
     static constexpr int BK = 32;            // FP16 elements per K slice (64-byte rows)
     static constexpr int ROW_BYTES = 64;
     static constexpr int A_BYTES = BM * ROW_BYTES;   // 8 KB, twice (hi, lo)
@@ -83,7 +83,7 @@ struct Mode<kF16x3> {                        // three-term FP16 with scaled resi
     static constexpr uint32_t SBO = 512;     // 8 rows x 64 bytes
 };
 template <>
-struct Mode<kBf16> {                         // BF16
+struct Mode<kSimBf16> {                         // BF16
     static constexpr int BK = 64;            // BF16 elements per K slice (128-byte rows)
     static constexpr int ROW_BYTES = 128;
     static constexpr int A_BYTES = BM * ROW_BYTES;   // 16 KB
@@ -94,7 +94,7 @@ struct Mode<kBf16> {                         // BF16
     static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
 };
 template <>
-struct Mode<kFp8> {                          // FP8 E4M3
+struct Mode<kSimFp8> {                          // FP8 E4M3
     static constexpr int BK = 128;           // FP8 elements per K slice (128-byte rows)
     static constexpr int ROW_BYTES = 128;
     static constexpr int A_BYTES = BM * ROW_BYTES;   // 16 KB
@@ -104,9 +104,9 @@ struct Mode<kFp8> {                          // FP8 E4M3
     static constexpr uint64_t LAYOUT = 2;    // 128-byte swizzle
     static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
 };
-static_assert(2 * Mode<kF16x3>::A_BYTES + 2 * Mode<kF16x3>::B_BYTES == STAGE_BYTES, "stage size");
-static_assert(Mode<kBf16>::A_BYTES + Mode<kBf16>::B_BYTES == STAGE_BYTES, "stage size");
-static_assert(Mode<kFp8>::A_BYTES + Mode<kFp8>::B_BYTES == STAGE_BYTES, "stage size");
+static_assert(2 * Mode<kSimF16x3>::A_BYTES + 2 * Mode<kSimF16x3>::B_BYTES == STAGE_BYTES, "stage size");
+static_assert(Mode<kSimBf16>::A_BYTES + Mode<kSimBf16>::B_BYTES == STAGE_BYTES, "stage size");
+static_assert(Mode<kSimFp8>::A_BYTES + Mode<kSimFp8>::B_BYTES == STAGE_BYTES, "stage size");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -148,6 +148,32 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
         ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
         : "memory");
+}
+
+// The same copy delivered to the same shared-memory offset of every CTA in
+// cta_mask, signalling each destination CTA's mbarrier at the offset of `bar`.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                               uint16_t cta_mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4}], [%2], %5;"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1),
+          "h"(cta_mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor of a K-major operand tile with rows of
@@ -208,6 +234,15 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
+// Commit whose arrival lands on the mbarrier at the offset of `bar` in every
+// CTA of cta_mask.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t cta_mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(smem_u32(bar)), "h"(cta_mask)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 {
     uint32_t r[32];
@@ -231,39 +266,74 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Tile id -> (first row, first column) under the grouped raster: GROUP_M row
-// tiles share each column tile so a descriptor tile is read from HBM about
-// once per group.
-__device__ __forceinline__ void tile_origin(int tile, int m_tiles, int n_tiles, int &m0, int &n0)
+// Cluster tile id -> this CTA's (first row, first column).  A cluster tile is
+// CM vertically adjacent row tiles (CTA rank r takes the r-th) of one column
+// tile; under the grouped raster GROUP_M cluster rows share each column tile
+// so a descriptor tile is read from HBM about once per group.
+__device__ __forceinline__ void tile_origin(int tile, int m_super, int n_tiles, uint32_t rank, int &m0, int &n0)
 {
     const int per_group = GROUP_M * n_tiles;
     const int g = tile / per_group;
     const int first_m = g * GROUP_M;
-    const int gm = min(GROUP_M, m_tiles - first_m);
+    const int gm = min(GROUP_M, m_super - first_m);
     const int in_g = tile - g * per_group;
-    m0 = (first_m + in_g % gm) * BM;
+    m0 = ((first_m + in_g % gm) * CM + (int)rank) * BM;
     n0 = (in_g / gm) * BN;
 }
 
-// Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// The shared-memory pipeline runs on across tiles.  Two-operand modes (BF16,
+// Persistent, in clusters of CM CTAs: cluster c walks cluster tiles c,
+// c + (number of clusters), ...; its CTAs compute vertically adjacent tiles of
+// one column tile in lockstep.  Each CTA loads its own A tile and 1/CM of the
+// shared B tile, multicast to every CTA of the cluster, so a stage is full
+// when the CTA's own A and all CM parts of B have landed; a stage is free
+// again when the MMAs of every CTA have consumed it (the "empty" mbarrier
+// counts CM multicast commits).  The shared-memory pipeline runs on across
+// tiles.  Two-operand modes (BF16,
 // FP8) keep two accumulators in the 512 TMEM columns, so the epilogue of one
 // tile overlaps the MMAs of the next (acc_full / acc_empty mbarriers); the
 // FP16x3 mode needs both halves of TMEM for its main and correction
 // accumulators and drains before the next tile's MMAs start, while the
 // producer already prefetches that tile's first stages.
-// Maps (FP16x3 mode): q_hi, q_lo, d_hi, d_lo.  (BF16, FP8 modes): q, d, and the
-// last two are unused.  scale_q / scale_d: per-row scales (FP8 mode only).
-template <int MODE>
+// A launch covers either one problem (`single`, its B maps map_d0 / map_d1)
+// or, GROUPED, the pieces of a device table: blocks of query rows against
+// different scenes, with their B maps in device memory, numbered by cluster
+// tile (tile_begin) so that every role finds its piece by binary search.
+// Maps (FP16x3 mode): q_hi, q_lo, d_hi, d_lo.  (BF16, FP8 modes): q, d, and
+// the second of each pair is unused.  scale_q: per-row scales of the query
+// rows, pieces' scale_d: per-object scales (FP8 mode only).
+template <bool GROUPED>
+__device__ __forceinline__ GemmPiece piece_of(int tile, const GemmPiece *pieces, int n_pieces,
+                                              const GemmPiece &single)
+{
+    if (!GROUPED) return single;
+    int lo = 0, hi = n_pieces - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pieces[mid].tile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return pieces[lo];
+}
+
+// This CTA's tile of cluster tile `tile` within piece pc: first row (local
+// to the piece) and first column.
+__device__ __forceinline__ void piece_tile(const GemmPiece &pc, int tile, uint32_t rank, int &m0, int &n0)
+{
+    const int m_tiles = (pc.rows + BM - 1) / BM;
+    const int n_tiles = (pc.n + BN - 1) / BN;
+    tile_origin(tile - pc.tile_begin, (m_tiles + CM - 1) / CM, n_tiles, rank, m0, n0);
+}
+
+template <int MODE, bool GROUPED>
 __global__ void __launch_bounds__(THREADS, 1)
 sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant__ CUtensorMap map_q1,
               const __grid_constant__ CUtensorMap map_d0, const __grid_constant__ CUtensorMap map_d1,
-              float *__restrict__ S, int64_t rows, int64_t n, int32_t k_slices, int64_t ld_s,
-              int32_t m_tiles, int32_t n_tiles, const float *__restrict__ scale_q,
-              const float *__restrict__ scale_d, float *__restrict__ tops, int32_t *err)
+              const GemmPiece *__restrict__ pieces, int32_t n_pieces, const GemmPiece single,
+              float *__restrict__ S, float *__restrict__ tops, int32_t k_slices, int32_t total,
+              const float *__restrict__ scale_q, int32_t *err)
 {
     using M = Mode<MODE>;
-    constexpr bool TWO_OPERAND_TILES = MODE != kF16x3;
+    constexpr bool TWO_OPERAND_TILES = MODE != kSimF16x3;
     constexpr int NACC = TWO_OPERAND_TILES ? 2 : 1;
     constexpr uint32_t TMEM_ALLOC = 512;
     extern __shared__ uint8_t smem_raw[];
@@ -276,12 +346,15 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int total = m_tiles * n_tiles;
+    const uint32_t rank = cluster_rank();
+    const int cluster_id = blockIdx.x / CM, n_clusters = gridDim.x / CM;
+    constexpr uint16_t ALL_CTAS = (uint16_t)((1u << CM) - 1u);
+    constexpr int B_PART = M::B_BYTES / CM;   // bytes of this CTA's share of a B tile
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], CM);    // one multicast commit from each CTA's MMA issuer
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -296,16 +369,20 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    cluster_sync();    // every CTA's mbarriers are initialised before any multicast reaches them
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
         if (lane == 0) {
             uint32_t it = 0;
-            for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x) {
+            for (int tile = cluster_id; tile < total && !*abort_flag; tile += n_clusters) {
+                const GemmPiece pc = piece_of<GROUPED>(tile, pieces, n_pieces, single);
                 int m0, n0;
-                tile_origin(tile, m_tiles, n_tiles, m0, n0);
+                piece_tile(pc, tile, rank, m0, n0);
+                const int qa = (int)(pc.q_row0 + m0);     // A rows: the piece's rows in the operand arrays
+                const CUtensorMap *bmap0 = GROUPED ? static_cast<const CUtensorMap *>(pc.bmap) : &map_d0;
+                const CUtensorMap *bmap1 = GROUPED ? static_cast<const CUtensorMap *>(pc.bmap) + 1 : &map_d1;
                 for (int kb = 0; kb < k_slices; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1u;
@@ -316,14 +393,16 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     uint8_t *st = smem + s * STAGE_BYTES;
                     mbar_expect_tx(&full[s], STAGE_BYTES);
                     const int kx = kb * M::BK;
+                    const int nb = n0 + (int)rank * (BN / CM);   // first B row of this CTA's share
                     if (TWO_OPERAND_TILES) {
-                        tma_load_2d(st, &map_q0, &full[s], kx, m0);
-                        tma_load_2d(st + M::A_BYTES, &map_d0, &full[s], kx, n0);
+                        tma_load_2d(st, &map_q0, &full[s], kx, qa);
+                        tma_load_2d_mc(st + M::A_BYTES + rank * B_PART, bmap0, &full[s], kx, nb, ALL_CTAS);
                     } else {
-                        tma_load_2d(st, &map_q0, &full[s], kx, m0);
-                        tma_load_2d(st + M::A_BYTES, &map_q1, &full[s], kx, m0);
-                        tma_load_2d(st + 2 * M::A_BYTES, &map_d0, &full[s], kx, n0);
-                        tma_load_2d(st + 2 * M::A_BYTES + M::B_BYTES, &map_d1, &full[s], kx, n0);
+                        tma_load_2d(st, &map_q0, &full[s], kx, qa);
+                        tma_load_2d(st + M::A_BYTES, &map_q1, &full[s], kx, qa);
+                        tma_load_2d_mc(st + 2 * M::A_BYTES + rank * B_PART, bmap0, &full[s], kx, nb, ALL_CTAS);
+                        tma_load_2d_mc(st + 2 * M::A_BYTES + M::B_BYTES + rank * B_PART, bmap1, &full[s], kx, nb,
+                                       ALL_CTAS);
                     }
                 }
             }
@@ -337,7 +416,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     } else if (warp == 1) {
         if (lane == 0) {
             uint32_t it = 0, tc = 0;
-            for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x, ++tc) {
+            for (int tile = cluster_id; tile < total && !*abort_flag; tile += n_clusters, ++tc) {
                 const uint32_t buf = tc % NACC, use = tc / NACC;
                 if (!mbar_wait(&acc_empty[buf], (use & 1u) ^ 1u) || *abort_flag) {
                     *abort_flag = 1;
@@ -359,7 +438,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
 #pragma unroll
                         for (int kk = 0; kk < M::KSTEPS; ++kk) {
                             const uint32_t off = kk * 32;     // 32 bytes along K: 16 BF16 or 32 FP8 values
-                            if (MODE == kBf16)
+                            if (MODE == kSimBf16)
                                 mma_bf16(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
                             else
                                 mma_e4m3(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
@@ -376,7 +455,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                             mma_f16(acc + ACC_CORR, smem_desc<MODE>(a_lo + off), smem_desc<MODE>(b_hi + off), 1u);
                         }
                     }
-                    mma_commit(&empty[s]);
+                    mma_commit_mc(&empty[s], ALL_CTAS);
                 }
                 if (*abort_flag) break;
                 mma_commit(&acc_full[buf]);
@@ -387,20 +466,24 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
         // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
         const int quad = warp & 3;
         uint32_t tc = 0;
-        for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++tc) {
+        for (int tile = cluster_id; tile < total; tile += n_clusters, ++tc) {
             const uint32_t buf = tc % NACC, use = tc / NACC;
             if (!mbar_wait(&acc_full[buf], use & 1u) || *abort_flag) {
                 *abort_flag = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
+            const GemmPiece pc = piece_of<GROUPED>(tile, pieces, n_pieces, single);
             int m0, n0;
-            tile_origin(tile, m_tiles, n_tiles, m0, n0);
-            const int64_t r = (int64_t)m0 + quad * 32 + lane;
-            float *srow = S + r * ld_s;
-            const bool vec = (ld_s % 4) == 0;
-            const float sr = (MODE == kFp8 && r < rows) ? scale_q[r] : 1.f;
-            const bool keep_tops = tops != nullptr && r < rows;
+            piece_tile(pc, tile, rank, m0, n0);
+            const int64_t r = (int64_t)m0 + quad * 32 + lane;    // row within the piece
+            const int64_t rows = pc.rows, n = pc.n;
+            const bool live = r < rows;
+            float *srow = S + pc.s_off + r * pc.ld;
+            const bool vec = (pc.ld % 4) == 0;
+            const float sr = (MODE == kSimFp8 && live) ? scale_q[pc.q_row0 + r] : 1.f;
+            const float *__restrict__ scale_d = pc.scale_d;
+            const bool keep_tops = tops != nullptr && pc.tops_off >= 0 && live;
             float gmax[BN / 32];     // maximum of each 32-column group of row r in this tile
 #pragma unroll
             for (int c = 0; c < BN / 32; ++c) {
@@ -408,14 +491,14 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 const uint32_t lane_addr = tmem + (TWO_OPERAND_TILES ? buf * 256u : 0u) +
                                            ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32);
                 tmem_ld32(lane_addr, v);
-                if (MODE == kF16x3) {
+                if (MODE == kSimF16x3) {
                     float w[32];
                     tmem_ld32(lane_addr + ACC_CORR, w);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] = fmaf(w[i], RESID_SCALE_INV, v[i]);
                 }
                 const int64_t col0 = (int64_t)n0 + c * 32;
-                if (MODE == kFp8 && r < rows) {
+                if (MODE == kSimFp8 && live) {
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] *= sr * (col0 + i < n ? __ldg(scale_d + col0 + i) : 0.f);
                 }
@@ -431,7 +514,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     }
                     gmax[c] = m;
                 }
-                if (r < rows) {
+                if (live) {
                     if (vec && col0 + 32 <= n) {
 #pragma unroll
                         for (int i = 0; i < 32; i += 4)
@@ -444,9 +527,9 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 }
             }
             if (keep_tops) {
-                float4 *tp = reinterpret_cast<float4 *>(tops + (r * n_tiles + n0 / BN) * kTileTop);
+                float4 *tp = reinterpret_cast<float4 *>(tops + pc.tops_off + r * group_stride(n) + n0 / 32);
 #pragma unroll
-                for (int j = 0; j < kTileTop; j += 4)
+                for (int j = 0; j < BN / 32; j += 4)
                     tp[j / 4] = make_float4(gmax[j], gmax[j + 1], gmax[j + 2], gmax[j + 3]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -455,7 +538,8 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    __syncwarp();      // warps 0 and 1 ran their roles on lane 0 only
+    cluster_sync();    // no CTA leaves while a peer's copies or commits may still target its shared memory
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_ALLOC));
@@ -482,18 +566,73 @@ template <int MODE>
 bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, int box_outer)
 {
     using M = Mode<MODE>;
-    const int esize = MODE == kFp8 ? 1 : 2;
-    const CUtensorMapDataType dt = MODE == kF16x3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                   : (MODE == kBf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+    const int esize = MODE == kSimFp8 ? 1 : 2;
+    const CUtensorMapDataType dt = MODE == kSimF16x3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : (MODE == kSimBf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
     cuuint64_t strides[1] = {(cuuint64_t)inner * esize};
     cuuint32_t box[2] = {(cuuint32_t)M::BK, (cuuint32_t)box_outer};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          MODE == kF16x3 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                          MODE == kSimF16x3 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+// Launch with the cluster attribute and a persistent grid of as many clusters
+// as can be resident at once (a GPC with an odd number of free SMs cannot
+// hold a whole cluster on its last SM); the count is cached per device,
+// mode and kind (concurrent first calls compute the same value).
+template <int MODE, bool GROUPED>
+cudaError_t launch_impl(const CUtensorMap &mq0, const CUtensorMap &mq1, const CUtensorMap &md0,
+                        const CUtensorMap &md1, const GemmPiece *pieces, int32_t n_pieces, const GemmPiece &single,
+                        float *S, float *tops, int32_t k_slices, int64_t total_tiles, const float *scale_q,
+                        int num_sms, int32_t *err, cudaStream_t s)
+{
+    if (total_tiles <= 0) return cudaSuccess;
+    if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(sim_tc_kernel<MODE, GROUPED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CM;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int resident[64][3][2] = {};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    int *slot = dev >= 0 && dev < 64 ? &resident[dev][MODE][GROUPED ? 1 : 0] : nullptr;
+    int nc = slot ? *slot : 0;
+    if (nc == 0) {
+        cfg.gridDim = dim3((unsigned)(std::max(num_sms / CM, 1) * CM));
+        if (cudaOccupancyMaxActiveClusters(&nc, sim_tc_kernel<MODE, GROUPED>, &cfg) != cudaSuccess || nc < 1) {
+            (void)cudaGetLastError();    // the query's error is not the launch's
+            nc = std::max(num_sms / CM, 1);
+        }
+        if (slot) *slot = nc;
+    }
+    const int clusters = (int)std::min<int64_t>(total_tiles, nc);
+    cfg.gridDim = dim3((unsigned)(clusters * CM));
+    e = cudaLaunchKernelEx(&cfg, sim_tc_kernel<MODE, GROUPED>, mq0, mq1, md0, md1, pieces, n_pieces, single, S, tops,
+                           k_slices, (int32_t)total_tiles, scale_q, err);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// Rows are padded to kDimAlign (64) elements; the FP8 K slice (128 bytes) may
+// run past the row end, where the tensor map's bounds fill zeros.
+template <int MODE>
+int32_t k_slices_of(int32_t dim_pad)
+{
+    return (dim_pad + Mode<MODE>::BK - 1) / Mode<MODE>::BK;
 }
 
 template <int MODE>
@@ -501,63 +640,121 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
                       int64_t n, int32_t dim_pad, int64_t ld_s, const float *scale_q, const float *scale_d,
                       float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
-    using M = Mode<MODE>;
-    constexpr bool TWO = MODE != kF16x3;
+    constexpr bool TWO = MODE != kSimF16x3;
     if (rows <= 0 || n <= 0) return cudaSuccess;
-    // rows are padded to kDimAlign (64) elements; the FP8 K slice (128 bytes)
-    // may run past the row end, where the tensor map's bounds fill zeros
-    if (dim_pad % kDimAlign != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL) return cudaErrorInvalidValue;
-    const int k_blocks = (dim_pad + M::BK - 1) / M::BK;
+    if (dim_pad % kDimAlign != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL || ld_s < n) return cudaErrorInvalidValue;
     if (!get_encoder()) return cudaErrorNotSupported;
     // TMA: 16-byte aligned bases; row strides are multiples of 16 bytes (dim_pad % 64 == 0)
     const uintptr_t al = (uintptr_t)q0 | (uintptr_t)d0 | (TWO ? 0 : ((uintptr_t)q1 | (uintptr_t)d1));
     if (al & 15u) return cudaErrorMisalignedAddress;
+    if (tops && ((uintptr_t)tops & 15u)) return cudaErrorMisalignedAddress;
+    if (MODE == kSimFp8 && (!scale_q || !scale_d)) return cudaErrorInvalidValue;
     CUtensorMap mq0, mq1, md0, md1;
-    if (MODE == kFp8 && (!scale_q || !scale_d)) return cudaErrorInvalidValue;
-    if (!make_map<MODE>(&mq0, q0, dim_pad, rows, BM) || !make_map<MODE>(&md0, d0, dim_pad, n, BN))
+    if (!make_map<MODE>(&mq0, q0, dim_pad, rows, BM) || !make_map<MODE>(&md0, d0, dim_pad, n, BN / CM))
         return cudaErrorInvalidValue;
     if (TWO) {
         mq1 = mq0;
         md1 = md0;
-    } else if (!make_map<MODE>(&mq1, q1, dim_pad, rows, BM) || !make_map<MODE>(&md1, d1, dim_pad, n, BN)) {
+    } else if (!make_map<MODE>(&mq1, q1, dim_pad, rows, BM) || !make_map<MODE>(&md1, d1, dim_pad, n, BN / CM)) {
         return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaFuncSetAttribute(sim_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    const int m_tiles = (int)((rows + BM - 1) / BM);
-    const int n_tiles = (int)((n + BN - 1) / BN);
-    const int64_t tiles = (int64_t)m_tiles * n_tiles;
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const int grid = (int)std::min<int64_t>(tiles, std::max(num_sms, 1));
-    sim_tc_kernel<MODE><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(mq0, mq1, md0, md1, S, rows, n,
-                                                                       k_blocks, ld_s, m_tiles, n_tiles,
-                                                                       scale_q, scale_d, tops, err);
-    return cudaGetLastError();
+    GemmPiece single{};
+    single.q_row0 = 0;
+    single.s_off = 0;
+    single.tops_off = tops ? 0 : -1;
+    single.scale_d = scale_d;
+    single.bmap = nullptr;
+    single.rows = (int32_t)rows;
+    single.n = (int32_t)n;
+    single.ld = (int32_t)ld_s;
+    single.tile_begin = 0;
+    if (ld_s > 0x7fffffffLL) return cudaErrorInvalidValue;
+    return launch_impl<MODE, false>(mq0, mq1, md0, md1, nullptr, 1, single, S, tops, k_slices_of<MODE>(dim_pad),
+                                    sim_cluster_tiles(rows, n), scale_q, num_sms, err, s);
+}
+
+template <int MODE>
+cudaError_t launch_grouped(const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
+                           const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S, float *tops,
+                           const float *scale_q, int num_sms, int32_t *err, cudaStream_t s)
+{
+    constexpr bool TWO = MODE != kSimF16x3;
+    if (total_tiles <= 0) return cudaSuccess;
+    if (n_pieces < 1 || rows_total < 1 || rows_total > 0x7fffffffLL || dim_pad % kDimAlign != 0 || !pieces)
+        return cudaErrorInvalidValue;
+    if (!get_encoder()) return cudaErrorNotSupported;
+    const uintptr_t al = (uintptr_t)q0 | (TWO ? 0 : (uintptr_t)q1) | (uintptr_t)S | (tops ? (uintptr_t)tops : 0);
+    if (al & 15u) return cudaErrorMisalignedAddress;
+    if (MODE == kSimFp8 && !scale_q) return cudaErrorInvalidValue;
+    CUtensorMap mq0, mq1;
+    if (!make_map<MODE>(&mq0, q0, dim_pad, rows_total, BM)) return cudaErrorInvalidValue;
+    if (TWO) mq1 = mq0;
+    else if (!make_map<MODE>(&mq1, q1, dim_pad, rows_total, BM)) return cudaErrorInvalidValue;
+    GemmPiece unused{};
+    // the B maps of the pieces live in device memory; map_d0 / map_d1 are unused
+    return launch_impl<MODE, true>(mq0, mq1, mq0, mq1, pieces, n_pieces, unused, S, tops, k_slices_of<MODE>(dim_pad),
+                                   total_tiles, scale_q, num_sms, err, s);
 }
 
 }  // namespace
 
 bool sim_tc_available() { return get_encoder(); }
 
+bool sim_tc_encode_b(int mode, void *out, const void *d0, const void *d1, int64_t n, int32_t dim_pad)
+{
+    if (!get_encoder() || n < 1 || (reinterpret_cast<uintptr_t>(out) & 63u)) return false;
+    CUtensorMap *m = static_cast<CUtensorMap *>(out);
+    static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
+    switch (mode) {
+    case kSimF16x3:
+        return make_map<kSimF16x3>(&m[0], d0, dim_pad, n, BN / CM) && make_map<kSimF16x3>(&m[1], d1, dim_pad, n, BN / CM);
+    case kSimBf16:
+        return make_map<kSimBf16>(&m[0], d0, dim_pad, n, BN / CM) && make_map<kSimBf16>(&m[1], d0, dim_pad, n, BN / CM);
+    case kSimFp8:
+        return make_map<kSimFp8>(&m[0], d0, dim_pad, n, BN / CM) && make_map<kSimFp8>(&m[1], d0, dim_pad, n, BN / CM);
+    default:
+        return false;
+    }
+}
+
+cudaError_t launch_sim_tc_grouped(int mode, const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
+                                  const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S,
+                                  float *tops, const float *scale_q, int num_sms, int32_t *err, cudaStream_t s)
+{
+    switch (mode) {
+    case kSimF16x3:
+        return launch_grouped<kSimF16x3>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops, scale_q,
+                                      num_sms, err, s);
+    case kSimBf16:
+        return launch_grouped<kSimBf16>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops, scale_q,
+                                     num_sms, err, s);
+    case kSimFp8:
+        return launch_grouped<kSimFp8>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops, scale_q,
+                                    num_sms, err, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, const uint16_t *d_hi,
                                 const uint16_t *d_lo, float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s,
                                 float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kF16x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms, err,
+    return launch_tc<kSimF16x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms, err,
                              s);
 }
 
 cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
                                int32_t dim_pad, int64_t ld_s, float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kBf16>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms, err, s);
+    return launch_tc<kSimBf16>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms, err, s);
 }
 
 cudaError_t launch_sim_tc_fp8(const uint8_t *q, const float *scale_q, const uint8_t *d, const float *scale_d,
                               float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, float *tops,
                               int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, tops, num_sms, err, s);
+    return launch_tc<kSimFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, tops, num_sms, err, s);
 }
 
 }  // namespace farm
