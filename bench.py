@@ -59,6 +59,8 @@ class ClockSampler:
         self.lines = []
 
     def __enter__(self):
+        if self.index < 0:          # not sampled
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
@@ -234,6 +236,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=384)
     ap.add_argument("--ref-queries", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="run the timed steps directly instead of as CUDA graphs (FARM_GRAPH)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -277,30 +281,45 @@ def main():
     o_pred = torch.empty((n_q, K_TOP, 4), dtype=torch.float32, device="cuda")
     o_anc = torch.empty((n_q, K_TOP, 4), dtype=torch.int32, device="cuda")
 
-    def step_device():
-        h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec)
+    graph = not args.no_graph
+
+    def step_device(use_graph=graph):
+        h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec,
+                               graph=use_graph)
         F.farm_topk(ctx, h, K_TOP, n_q, o_idx, o_score, o_pred, o_anc)
+
+    def timed(fn, sample_clocks):
+        """K steps between CUDA events on the library's stream, barrier and synchronize on both sides."""
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local if sample_clocks else -1) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        F.farm_sync(ctx)
+        return ev0.elapsed_time(ev1), clk
 
     for _ in range(args.warmup):
         step_device()
     F.farm_sync(ctx)
     F.farm_stage_times(ctx, reset=True)
-    F.farm_set_profiling(ctx, True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step_device()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    F.farm_sync(ctx)
-    ms = ev0.elapsed_time(ev1)
-    stage_ms, launches = F.farm_stage_times(ctx, reset=True)
-    F.farm_set_profiling(ctx, False)
+    ms, clk = timed(step_device, True)
+    _, launches = F.farm_stage_times(ctx, reset=True)
     ms_step = max_over_ranks([ms / args.steps], dist, "cuda" if dist else None)[0]
+    # the same steps run directly with the library's stage events: the stage
+    # breakdown and the similarity kernel's time for the roofline
+    for _ in range(min(args.warmup, 3)):
+        step_device(False)
+    F.farm_sync(ctx)
+    F.farm_stage_times(ctx, reset=True)
+    F.farm_set_profiling(ctx, True)
+    ms_prof, _ = timed(lambda: step_device(False), False)
+    stage_ms, _ = F.farm_stage_times(ctx, reset=True)
+    F.farm_set_profiling(ctx, False)
     if dist:
         dist.barrier()
 
@@ -313,7 +332,8 @@ def main():
                  anchor=torch.empty((n_q, K_TOP, 4), dtype=torch.int32).pin_memory().numpy())
 
     def step_host():
-        h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec)
+        h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec,
+                               graph=graph)
         F.farm_topk(ctx, h, K_TOP, n_q, h_out["idx"], h_out["score"], h_out["pred"], h_out["anchor"])
 
     for _ in range(args.warmup):
@@ -372,12 +392,14 @@ def main():
                    "n_objects": int(sum(x.n for x in scenes)), "dim": sc.dim, "n_views": sc.n_views,
                    "queries": n_q, "constraint_rows": n_c, "top_k": K_TOP,
                    "precision": args.precision, "parallelism": f"replicas{world}",
+                   "cuda_graph": graph,
                    "l2": "inputs larger than L2 (descriptor copies and the similarity block exceed 129 MB)"},
         "e2e": {"value": job_rate(n_q, world, e2e_ms), "unit": "queries/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "stage_ms_per_step": {"prepare": stage_ms[0] / args.steps, "similarity": gemm_ms,
-                              "select": stage_ms[2] / args.steps, "compose": stage_ms[3] / args.steps},
+                              "select": stage_ms[2] / args.steps, "compose": stage_ms[3] / args.steps,
+                              "direct_ms_per_step": ms_prof / args.steps},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": achieved / peak if peak else None, "traffic": None,
                      "kernel": "similarity", "peak_source": peak_note},

@@ -75,6 +75,7 @@ typedef enum {
 
 /* flags */
 #define FARM_PTR_DEVICE 1u    /* the call's array arguments are device pointers */
+#define FARM_GRAPH 2u         /* farm_query_batch: run the batch's device work as a CUDA graph (see there) */
 
 /*
  * The method's constants.  mu = 5 (reciprocal-rank offset), w = 0.5 (blend
@@ -159,12 +160,26 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
  *   c_emb      [n_c, dim]  FP32 landmark embeddings
  *   precision  a farm_precision value
  *   flags      FARM_PTR_DEVICE: tgt_emb and c_emb are device pointers (the
- *              other arrays are always host memory)
+ *              other arrays are always host memory).
+ *              FARM_GRAPH: the batch's device work (staging copies, row
+ *              normalisation, similarity, rank selection, rescore, relations
+ *              and composite) runs as a CUDA graph.  Graphs are cached by the
+ *              batch's shape: precision, n_q, n_c, and the scenes in order of
+ *              first use with each one's query and constraint counts, and, for
+ *              device embeddings, their addresses.  A batch of a cached shape
+ *              replays the graph; the host still plans each call (query order,
+ *              metadata).  Host embeddings are copied into library buffers
+ *              before the graph runs; device embeddings are read in place, so
+ *              a caller that reuses its buffers replays without copies.
+ *              Re-uploading a scene, changing the prefilter weights or growing
+ *              a work buffer starts new captures.  At most 8 graphs are kept
+ *              (least recently used go).
  *   batch_handle  receives the handle that farm_topk takes
  * Only target candidates whose rank r can still place them in the top k_max
  * are scored: a candidate scores at most 1/(mu + r) while k_max objects score
  * at least (1 - w) * class_mis / (mu + k_max), so candidates of rank above
- * R = floor((mu + k_max) / ((1 - w) * class_mis) - mu) + 1 (96 at the defaults)
+ * R = floor((mu + k_max) / ((1 - w) * class_mis) - mu) + 1 (95 with the default
+ * single-precision constants: 0.3f is slightly above 0.3)
  * cannot enter the result.  The result is the same as scoring every object.
  * A new farm_query_batch call invalidates the previous handle.
  */

@@ -31,6 +31,11 @@ struct farm_ctx {
     uint8_t *h_blob = nullptr;        // pinned staging of the batch's piece tables and tensor maps
     size_t h_blob_n = 0;
     cudaEvent_t stage_done = nullptr;
+    // CUDA graphs of batch shapes (FARM_GRAPH), least recently used evicted
+    struct GraphEntry { std::vector<int64_t> key; cudaGraphExec_t exec = nullptr; int64_t launches = 0; uint64_t used = 0; };
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_clock = 0;
+    bool capturing = false;
     // profiling marks
     struct Mark { int stage; cudaEvent_t a, b; };
     std::vector<Mark> marks;
@@ -112,6 +117,7 @@ cudaError_t ws_get(farm_ctx *ctx, Buf b, size_t bytes, void **out)
         cudaError_t e = cudaMalloc(&ws.ptr[b], grow);
         if (e != cudaSuccess) return e;
         ws.bytes[b] = grow;
+        ctx->c.ws_gen += 1;     // captured graphs that use the old buffer no longer match
     }
     *out = ws.ptr[b];
     return cudaSuccess;
@@ -142,7 +148,7 @@ void free_scene(Scene &s)
 
 int mark_begin(farm_ctx *ctx, int stage)
 {
-    if (!ctx->c.profiling) return -1;
+    if (!ctx->c.profiling || ctx->capturing) return -1;
     cudaEvent_t a, b;
     if (ctx->pool.size() >= 2) {
         a = ctx->pool.back(); ctx->pool.pop_back();
@@ -330,6 +336,7 @@ farm_status farm_destroy(farm_ctx *ctx)
     if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
     for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
     delete ctx;
     return FARM_OK;
@@ -475,6 +482,7 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
     ns.present = true;
     s = ns;
     c.batch_valid = false;
+    c.scene_gen += 1;
     return FARM_OK;
 }
 
@@ -495,6 +503,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     if (n_q > 0 && (!scene_of_q || !tgt_emb || !tgt_cls || !c_off))
         return fail(ctx, FARM_EINVAL, "scene_of_q, tgt_emb, tgt_cls and c_off must be non-null");
     const bool dev = (flags & FARM_PTR_DEVICE) != 0;
+    const bool graph = (flags & FARM_GRAPH) != 0;
     int64_t n_c = 0;
     int32_t dim = -1;
     int64_t min_n = INT64_MAX, max_n = 0;
@@ -646,6 +655,15 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             CK(ws_get(ctx, farm::B_BSEL_LV, (size_t)std::max<int64_t>(n_c, 1) * cstride_l, &bsel_lv));
         }
     }
+    if (!dev) CK(ws_get(ctx, farm::B_RAW, (size_t)(n_q + n_c) * dim, &d_raw));
+    if (graph && precision == FARM_PREC_LEARNED) CK(farm::learned_reserve(ctx, rows_total));
+    auto copy_inputs = [&](cudaMemcpyKind kind) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(d_raw, tgt_emb, (size_t)n_q * dim * 4, kind, c.stream);
+        if (e == cudaSuccess && n_c > 0)
+            e = cudaMemcpyAsync(d_raw + (size_t)n_q * dim, c_emb, (size_t)n_c * dim * 4, kind, c.stream);
+        return e;
+    };
+
     // ---- similarity batches: row ranges ("pieces") of the scene groups are
     //      laid end to end in S while they fit kSimCapBytes; each batch takes
     //      one similarity launch per piece, then the rank selection: on the
@@ -833,106 +851,163 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         }
     }
 
-    // ---- stage 0: inputs and normalisation
-    const int m0 = mark_begin(ctx, 0);
-    CK(cudaMemcpyAsync(d_rowmap, h_rowmap, (size_t)(n_q + n_c) * 4, cudaMemcpyHostToDevice, c.stream));
-    CK(cudaMemcpyAsync(d_perm, h_perm, (size_t)n_q * 4, cudaMemcpyHostToDevice, c.stream));
-    CK(cudaMemcpyAsync(d_meta, h_meta, (size_t)n_q * 8 * 4, cudaMemcpyHostToDevice, c.stream));
-    CK(cudaMemcpyAsync(d_blob, ctx->h_blob, blob_bytes, cudaMemcpyHostToDevice, c.stream));
-    CK(cudaEventRecord(ctx->stage_done, c.stream));
-    const float *src_t = tgt_emb, *src_c = c_emb;
-    if (!dev) {
-        CK(ws_get(ctx, farm::B_RAW, (size_t)(n_q + n_c) * dim, &d_raw));
-        CK(cudaMemcpyAsync(d_raw, tgt_emb, (size_t)n_q * dim * 4, cudaMemcpyHostToDevice, c.stream));
+    // The batch's device work, in stream order: run directly, or captured
+    // into a CUDA graph (FARM_GRAPH), in which case everything it reads was
+    // staged into library buffers first.
+    const float *src_t = dev ? tgt_emb : d_raw;
+    const float *src_c = dev ? c_emb : d_raw + (size_t)n_q * dim;
+    auto enqueue = [&]() -> farm_status {
+        // ---- stage 0: inputs and normalisation
+        const int m0 = mark_begin(ctx, 0);
+        CK(cudaMemcpyAsync(d_rowmap, h_rowmap, (size_t)(n_q + n_c) * 4, cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(d_perm, h_perm, (size_t)n_q * 4, cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(d_meta, h_meta, (size_t)n_q * 8 * 4, cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(d_blob, ctx->h_blob, blob_bytes, cudaMemcpyHostToDevice, c.stream));
+        if (!graph) CK(cudaEventRecord(ctx->stage_done, c.stream));
+        if (!graph && !dev) CK(copy_inputs(cudaMemcpyHostToDevice));
+        LAUNCH(farm::launch_normalize_rows(src_t, d_rowmap, n_q, dim, dim_pad, ops.q32, ops.qhi, ops.qlo, ops.qbf,
+                                           c.d_err, farm::kErrBadRow, c.stream));
         if (n_c > 0)
-            CK(cudaMemcpyAsync(d_raw + (size_t)n_q * dim, c_emb, (size_t)n_c * dim * 4, cudaMemcpyHostToDevice,
-                               c.stream));
-        src_t = d_raw;
-        src_c = d_raw + (size_t)n_q * dim;
-    }
-    LAUNCH(farm::launch_normalize_rows(src_t, d_rowmap, n_q, dim, dim_pad, ops.q32, ops.qhi, ops.qlo, ops.qbf,
-                                       c.d_err, farm::kErrBadRow, c.stream));
-    if (n_c > 0)
-        LAUNCH(farm::launch_normalize_rows(src_c, d_rowmap + n_q, n_c, dim, dim_pad, ops.q32, ops.qhi, ops.qlo,
-                                           ops.qbf, c.d_err, farm::kErrBadRow, c.stream));
-    if (precision == FARM_PREC_FP8)
-        LAUNCH(farm::launch_quantize_fp8_rows(ops.q32, rows_total, dim_pad, ops.qf8, ops.qscale, c.stream));
-    if (precision == FARM_PREC_LEARNED) CK(farm::learned_embed_rows(ctx, ops.qbf, rows_total, ops.qcomp));
-    mark_end(ctx, m0);
+            LAUNCH(farm::launch_normalize_rows(src_c, d_rowmap + n_q, n_c, dim, dim_pad, ops.q32, ops.qhi, ops.qlo,
+                                               ops.qbf, c.d_err, farm::kErrBadRow, c.stream));
+        if (precision == FARM_PREC_FP8)
+            LAUNCH(farm::launch_quantize_fp8_rows(ops.q32, rows_total, dim_pad, ops.qf8, ops.qscale, c.stream));
+        if (precision == FARM_PREC_LEARNED) CK(farm::learned_embed_rows(ctx, ops.qbf, rows_total, ops.qcomp));
+        mark_end(ctx, m0);
 
-    // ---- stages 1-2: similarity per piece, then the batch's rank selection
-    int32_t *sel_ti = reduced ? bsel_t : tsel_idx, *sel_li = reduced ? bsel_l : lsel_idx;
-    float *sel_tc = reduced ? bsel_tv : tsel_cos, *sel_lc = reduced ? bsel_lv : nullptr;
-    const int32_t sel_st = reduced ? cstride_t : stride_t, sel_sl = reduced ? cstride_l : stride_l;
-    for (size_t b = 0; b < batches.size(); ++b) {
-        const Batch &bt = batches[b];
-        const int m1 = mark_begin(ctx, 1);
-        if (sim_mode >= 0) {
-            const void *q0, *q1 = nullptr;
-            int32_t kdim = dim_pad;
-            int64_t q_rows = rows_total;
-            if (precision == FARM_PREC_FP32) { q0 = ops.qhi; q1 = ops.qlo; }
-            else if (precision == FARM_PREC_BF16) q0 = ops.qbf;
-            else if (precision == FARM_PREC_LEARNED) { q0 = ops.qcomp; kdim = c.mlp.P; }
-            else q0 = ops.qf8;
-            LAUNCH(farm::launch_sim_tc_grouped(sim_mode, q0, q1, q_rows, kdim, d_gpieces + bt.p0, (int32_t)bt.np,
-                                               batch_tiles[b], d_sim, tile_tops ? d_tops : nullptr,
-                                               precision == FARM_PREC_FP8 ? ops.qscale : nullptr, c.num_sms, c.d_err,
-                                               c.stream));
-        } else {
+        // ---- stages 1-2: similarity per piece, then the batch's rank selection
+        int32_t *sel_ti = reduced ? bsel_t : tsel_idx, *sel_li = reduced ? bsel_l : lsel_idx;
+        float *sel_tc = reduced ? bsel_tv : tsel_cos, *sel_lc = reduced ? bsel_lv : nullptr;
+        const int32_t sel_st = reduced ? cstride_t : stride_t, sel_sl = reduced ? cstride_l : stride_l;
+        for (size_t b = 0; b < batches.size(); ++b) {
+            const Batch &bt = batches[b];
+            const int m1 = mark_begin(ctx, 1);
+            if (sim_mode >= 0) {
+                const void *q0, *q1 = nullptr;
+                int32_t kdim = dim_pad;
+                int64_t q_rows = rows_total;
+                if (precision == FARM_PREC_FP32) { q0 = ops.qhi; q1 = ops.qlo; }
+                else if (precision == FARM_PREC_BF16) q0 = ops.qbf;
+                else if (precision == FARM_PREC_LEARNED) { q0 = ops.qcomp; kdim = c.mlp.P; }
+                else q0 = ops.qf8;
+                LAUNCH(farm::launch_sim_tc_grouped(sim_mode, q0, q1, q_rows, kdim, d_gpieces + bt.p0, (int32_t)bt.np,
+                                                   batch_tiles[b], d_sim, tile_tops ? d_tops : nullptr,
+                                                   precision == FARM_PREC_FP8 ? ops.qscale : nullptr, c.num_sms, c.d_err,
+                                                   c.stream));
+            } else {
+                for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
+                    const farm::Piece &pc = pieces[k];
+                    farm_status st = run_similarity(ctx, precision, ops, pc.q_row0, pc.rows, c.scenes[piece_sid[k]],
+                                                    d_sim + pc.s_off, pc.ld, nullptr);
+                    if (st != FARM_OK) return st;
+                }
+            }
+            mark_end(ctx, m1);
+            const int m2 = mark_begin(ctx, 2);
+            const farm::Piece *dp = d_pieces + bt.p0;
+            if (bt.blocks > 0)
+                LAUNCH(farm::launch_select_grouped(d_sim, dp, (int32_t)bt.np, bt.blocks, bt.smem_sel, sel_ti, sel_tc,
+                                                   sel_st, sel_li, sel_lc, sel_sl, tmp_idx, tmp_val, tmp_stride,
+                                                   c.stream));
+            if (bt.chunked)
+                LAUNCH(farm::launch_merge_chunks(dp, (int32_t)bt.np, bt.rows, bt.smem_merge, tmp_idx, tmp_val, tmp_stride,
+                                                 sel_ti, sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.stream));
+            if (bt.tblocks > 0)
+                LAUNCH(farm::launch_select_thresh(d_sim, d_tops, dp, (int32_t)bt.np, bt.tblocks, bt.max_union, sel_ti,
+                                                  sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.d_fallback, c.stream));
             for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
                 const farm::Piece &pc = pieces[k];
-                farm_status st = run_similarity(ctx, precision, ops, pc.q_row0, pc.rows, c.scenes[piece_sid[k]],
-                                                d_sim + pc.s_off, pc.ld, nullptr);
-                if (st != FARM_OK) return st;
+                if (pc.chunks != 0 || pc.th0 == 0) continue;
+                LAUNCH(farm::launch_select_rows_ex(d_sim + pc.s_off, pc.ld, pc.n, pc.th0, pc.ntr, pc.keep_t, pc.keep_l,
+                                                   sel_ti, sel_tc, pc.t_row0, sel_st, sel_li, sel_lc, pc.l_row0, sel_sl,
+                                                   c.stream));
             }
+            if (reduced) {
+                const float band = precision == FARM_PREC_FP8 ? 16.f * p.rescore_band : p.rescore_band;
+                LAUNCH(farm::launch_rescore_grouped(dp, (int32_t)bt.np, bt.rows, ops.q32, dim_pad, bsel_t, bsel_tv,
+                                                    cstride_t, bsel_l, bsel_lv, cstride_l, band, tsel_idx, tsel_cos,
+                                                    stride_t, lsel_idx, stride_l, c.stream));
+            }
+            mark_end(ctx, m2);
         }
-        mark_end(ctx, m1);
-        const int m2 = mark_begin(ctx, 2);
-        const farm::Piece *dp = d_pieces + bt.p0;
-        if (bt.blocks > 0)
-            LAUNCH(farm::launch_select_grouped(d_sim, dp, (int32_t)bt.np, bt.blocks, bt.smem_sel, sel_ti, sel_tc,
-                                               sel_st, sel_li, sel_lc, sel_sl, tmp_idx, tmp_val, tmp_stride,
-                                               c.stream));
-        if (bt.chunked)
-            LAUNCH(farm::launch_merge_chunks(dp, (int32_t)bt.np, bt.rows, bt.smem_merge, tmp_idx, tmp_val, tmp_stride,
-                                             sel_ti, sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.stream));
-        if (bt.tblocks > 0)
-            LAUNCH(farm::launch_select_thresh(d_sim, d_tops, dp, (int32_t)bt.np, bt.tblocks, bt.max_union, sel_ti,
-                                              sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.d_fallback, c.stream));
-        for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
-            const farm::Piece &pc = pieces[k];
-            if (pc.chunks != 0 || pc.th0 == 0) continue;
-            LAUNCH(farm::launch_select_rows_ex(d_sim + pc.s_off, pc.ld, pc.n, pc.th0, pc.ntr, pc.keep_t, pc.keep_l,
-                                               sel_ti, sel_tc, pc.t_row0, sel_st, sel_li, sel_lc, pc.l_row0, sel_sl,
-                                               c.stream));
-        }
-        if (reduced) {
-            const float band = precision == FARM_PREC_FP8 ? 16.f * p.rescore_band : p.rescore_band;
-            LAUNCH(farm::launch_rescore_grouped(dp, (int32_t)bt.np, bt.rows, ops.q32, dim_pad, bsel_t, bsel_tv,
-                                                cstride_t, bsel_l, bsel_lv, cstride_l, band, tsel_idx, tsel_cos,
-                                                stride_t, lsel_idx, stride_l, c.stream));
-        }
-        mark_end(ctx, m2);
-    }
 
-    // ---- stage 3: relations, composite, sort
-    const int m3 = mark_begin(ctx, 3);
-    farm::ComposeArgs ca;
-    ca.n_q = n_q;
-    ca.qmeta = d_meta;
-    ca.tsel_idx = tsel_idx;
-    ca.lsel_idx = lsel_idx;
-    ca.stride_t = stride_t;
-    ca.stride_l = stride_l;
-    ca.scenes = ctx->d_scenes;
-    ca.p = p;
-    ca.out_idx = o_idx;
-    ca.out_score = o_score;
-    ca.out_t = o_t;
-    ca.out_anchor = o_anc;
-    LAUNCH(farm::launch_compose(ca, c.stream));
-    mark_end(ctx, m3);
+        // ---- stage 3: relations, composite, sort
+        const int m3 = mark_begin(ctx, 3);
+        farm::ComposeArgs ca;
+        ca.n_q = n_q;
+        ca.qmeta = d_meta;
+        ca.tsel_idx = tsel_idx;
+        ca.lsel_idx = lsel_idx;
+        ca.stride_t = stride_t;
+        ca.stride_l = stride_l;
+        ca.scenes = ctx->d_scenes;
+        ca.p = p;
+        ca.out_idx = o_idx;
+        ca.out_score = o_score;
+        ca.out_t = o_t;
+        ca.out_anchor = o_anc;
+        LAUNCH(farm::launch_compose(ca, c.stream));
+        mark_end(ctx, m3);
+        return FARM_OK;
+    };
+
+    if (!graph) {
+        const farm_status st = enqueue();
+        if (st != FARM_OK) return st;
+    } else {
+        if (!dev) CK(copy_inputs(cudaMemcpyHostToDevice));
+        // the batch's shape: everything that fixes the launch sequence and its
+        // arguments (the captured copies read the pinned staging buffers at
+        // these addresses; device inputs are read where the caller keeps them)
+        std::vector<int64_t> key = {precision, n_q, n_c, dim, (int64_t)c.ws_gen, (int64_t)c.scene_gen,
+                                    (int64_t)c.mlp.version, (int64_t)(intptr_t)ctx->h_stage,
+                                    (int64_t)(intptr_t)ctx->h_blob, (int64_t)(intptr_t)src_t,
+                                    (int64_t)(intptr_t)src_c, (int64_t)groups.size()};
+        for (const auto &g : groups) {
+            key.push_back(g.sid);
+            key.push_back(g.nq);
+            key.push_back(g.nc);
+        }
+        farm_ctx::GraphEntry *hit = nullptr;
+        for (auto &ge : ctx->graphs)
+            if (ge.key == key) hit = &ge;
+        if (!hit) {
+            const int64_t launches0 = c.launches;
+            CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeRelaxed));
+            ctx->capturing = true;
+            const farm_status st = enqueue();
+            ctx->capturing = false;
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(c.stream, &g);
+            if (st != FARM_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (ec != cudaSuccess) return fail(ctx, FARM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+            cudaGraphExec_t exec = nullptr;
+            const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) return fail(ctx, FARM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+            if (ctx->graphs.size() >= 8) {
+                auto lru = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                            [](const farm_ctx::GraphEntry &x, const farm_ctx::GraphEntry &y) {
+                                                return x.used < y.used;
+                                            });
+                cudaGraphExecDestroy(lru->exec);
+                ctx->graphs.erase(lru);
+            }
+            farm_ctx::GraphEntry ge;
+            ge.key = std::move(key);
+            ge.exec = exec;
+            ge.launches = c.launches - launches0;
+            ctx->graphs.push_back(std::move(ge));
+            hit = &ctx->graphs.back();
+            c.launches = launches0;
+        }
+        hit->used = ++ctx->graph_clock;
+        CK(cudaGraphLaunch(hit->exec, c.stream));
+        c.launches += hit->launches;
+    }
 
     c.batch_gen += 1;
     c.batch_valid = true;

@@ -126,6 +126,8 @@ struct Ctx {
     std::vector<Scene> scenes;
     Workspace ws;
     int32_t *d_err = nullptr;     // device error word
+    uint64_t ws_gen = 0;          // bumped whenever a workspace buffer moves
+    uint64_t scene_gen = 0;       // bumped on every scene upload
     int32_t *d_fallback = nullptr;  // rows the thresholded select handed to its exact fallback
     int32_t *h_err = nullptr;     // pinned host mirror
     // batch state
@@ -166,6 +168,9 @@ cudaError_t ws_alloc(farm_ctx *ctx, Buf b, size_t bytes, void **out);
 
 // Learned embeddings f(x) of BF16 unit rows xb [rows, D_pad] into BF16
 // out [rows, P], on the tensor cores, in chunks (the prefilter's host code).
+// Grow the prefilter's work buffers for embedding `rows` rows, so that
+// learned_embed_rows then allocates nothing (required before graph capture).
+cudaError_t learned_reserve(farm_ctx *ctx, int64_t rows);
 cudaError_t learned_embed_rows(farm_ctx *ctx, const uint16_t *xb, int64_t rows, uint16_t *out);
 // Recompute a scene's cached learned embeddings if the weights changed.
 cudaError_t learned_refresh_scene(farm_ctx *ctx, int32_t scene_id);

@@ -136,6 +136,28 @@ cudaError_t refresh_bf16_weights(Ctx &c)
 
 }  // namespace
 
+namespace {
+
+cudaError_t embed_buffers(farm_ctx *ctx, int64_t rows, void **h, void **a, void **ab, void **z, void **e)
+{
+    const Mlp &M = farm::ctx_of(ctx)->mlp;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows, kEmbedChunk));
+    cudaError_t r;
+    if ((r = farm::ws_alloc(ctx, farm::B_MLP_H, (size_t)chunk * M.H * 4, h))) return r;
+    if ((r = farm::ws_alloc(ctx, farm::B_MLP_A, (size_t)chunk * M.H * 4, a))) return r;
+    if ((r = farm::ws_alloc(ctx, farm::B_MLP_AB, (size_t)chunk * M.H * 2, ab))) return r;
+    if ((r = farm::ws_alloc(ctx, farm::B_MLP_Z, (size_t)chunk * M.P * 4, z))) return r;
+    return farm::ws_alloc(ctx, farm::B_MLP_E, (size_t)chunk * M.P * 4, e);
+}
+
+}  // namespace
+
+cudaError_t farm::learned_reserve(farm_ctx *ctx, int64_t rows)
+{
+    void *h, *a, *ab, *z, *e;
+    return embed_buffers(ctx, rows, &h, &a, &ab, &z, &e);
+}
+
 cudaError_t farm::learned_embed_rows(farm_ctx *ctx, const uint16_t *xb, int64_t rows, uint16_t *out)
 {
     Ctx &c = *ctx_of(ctx);
@@ -143,11 +165,7 @@ cudaError_t farm::learned_embed_rows(farm_ctx *ctx, const uint16_t *xb, int64_t 
     const int64_t chunk = std::min<int64_t>(rows, kEmbedChunk);
     void *h, *a, *ab, *z, *e;
     cudaError_t r;
-    if ((r = ws_alloc(ctx, B_MLP_H, (size_t)chunk * M.H * 4, &h))) return r;
-    if ((r = ws_alloc(ctx, B_MLP_A, (size_t)chunk * M.H * 4, &a))) return r;
-    if ((r = ws_alloc(ctx, B_MLP_AB, (size_t)chunk * M.H * 2, &ab))) return r;
-    if ((r = ws_alloc(ctx, B_MLP_Z, (size_t)chunk * M.P * 4, &z))) return r;
-    if ((r = ws_alloc(ctx, B_MLP_E, (size_t)chunk * M.P * 4, &e))) return r;
+    if ((r = embed_buffers(ctx, rows, &h, &a, &ab, &z, &e))) return r;
     for (int64_t r0 = 0; r0 < rows; r0 += chunk) {
         const int64_t b = std::min(chunk, rows - r0);
         c.launches += 6;

@@ -20,6 +20,7 @@ PREC_FP8 = 2
 PREC_FP32_SIMT = 3
 PREC_LEARNED = 4
 PTR_DEVICE = 1
+GRAPH = 2          # FARM_GRAPH
 N_STAGES = 4
 STATUS = {0: "FARM_OK", 1: "FARM_EINVAL", 2: "FARM_ENOMEM", 3: "FARM_ECUDA", 4: "FARM_ESTATE",
           5: "FARM_ETIMEOUT"}
@@ -170,7 +171,8 @@ def farm_memory_upload(ctx, scene_id: int, desc, cls, box, views=None) -> None:
 
 
 def farm_query_batch(ctx, scene_of_q, tgt_emb, tgt_cls, c_off, c_pred, c_emb,
-                     precision: int = PREC_FP32) -> int:
+                     precision: int = PREC_FP32, graph: bool = False) -> int:
+    """Enqueue a batch (see farm.h); graph=True passes FARM_GRAPH."""
     n_q = int(len(tgt_cls))
     s = _Arr(scene_of_q, np.int32, "scene_of_q", allow_device=False)
     tc = _Arr(tgt_cls, np.int32, "tgt_cls", allow_device=False)
@@ -178,7 +180,7 @@ def farm_query_batch(ctx, scene_of_q, tgt_emb, tgt_cls, c_off, c_pred, c_emb,
     cp = _Arr(c_pred, np.int32, "c_pred", allow_device=False)
     te = _Arr(tgt_emb, np.float32, "tgt_emb")
     ce = _Arr(c_emb, np.float32, "c_emb")
-    flags = _flags(te, ce)
+    flags = _flags(te, ce) | (GRAPH if graph else 0)
     h = C.c_uint64()
     _ck(ctx, _lib.farm_query_batch(ctx, n_q, s.ptr, te.ptr, tc.ptr, co.ptr, cp.ptr, ce.ptr,
                                    int(precision), flags, C.byref(h)))
