@@ -397,6 +397,9 @@ def main():
         "e2e": {"value": job_rate(n_q, world, e2e_ms), "unit": "queries/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
+        "autotuned_tiles": [{"mode": d[0], "log2_rows": d[1], "log2_objects": d[2],
+                             "variant": d[3], "tile_n": 256 if d[3] < 2 else 128,
+                             "cluster": 1 if d[3] & 1 else 2} for d in F.farm_sim_tuning(ctx)],
         "stage_ms_per_step": {"prepare": stage_ms[0] / args.steps, "similarity": gemm_ms,
                               "select": stage_ms[2] / args.steps, "compose": stage_ms[3] / args.steps,
                               "direct_ms_per_step": ms_prof / args.steps},

@@ -220,6 +220,31 @@ farm_status farm_sync(farm_ctx *ctx);
 farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t reset);
 
 /*
+ * The tensor-core similarity kernel comes in four tile configurations
+ * ("variants": 0 = 256 objects per tile, CTAs in clusters of two sharing the
+ * descriptor tile; 1 = 256, alone; 2 = 128, clusters of two; 3 = 128, alone).
+ * All compute each cosine with the same sequence of products, so they give
+ * bitwise identical results.  The first farm_query_batch of each class of
+ * batch (similarity mode, and the powers of two of its total rows and of its
+ * mean objects per row) times every variant on its first similarity block and
+ * keeps the fastest for the context.
+ *
+ * farm_sim_tuning: the decisions so far, up to cap records of four int32:
+ * mode (0 = FP32-accurate, 1 = BF16 and the learned prefilter, 2 = FP8),
+ * log2 of the rows, log2 of the mean objects per row, chosen variant.
+ * *count receives the number of decisions.
+ */
+farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_t *count);
+
+/*
+ * Cosines as farm_similarity (FARM_PREC_FP32, FARM_PREC_BF16 or FARM_PREC_FP8),
+ * computed by the given tile variant (0 .. 3), for checking the variants
+ * against one another.
+ */
+farm_status farm_similarity_variant(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb,
+                                    int32_t precision, int32_t variant, float *out, uint32_t flags);
+
+/*
  * Object count n and descriptor length dim of an uploaded scene, for sizing
  * the output of farm_similarity (n_rows x n floats).  Either pointer may be
  * NULL.  FARM_EINVAL for a scene id that holds no scene.

@@ -503,7 +503,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     if (n_q > 0 && (!scene_of_q || !tgt_emb || !tgt_cls || !c_off))
         return fail(ctx, FARM_EINVAL, "scene_of_q, tgt_emb, tgt_cls and c_off must be non-null");
     const bool dev = (flags & FARM_PTR_DEVICE) != 0;
-    const bool graph = (flags & FARM_GRAPH) != 0;
+    bool graph = (flags & FARM_GRAPH) != 0;
     int64_t n_c = 0;
     int32_t dim = -1;
     int64_t min_n = INT64_MAX, max_n = 0;
@@ -799,10 +799,31 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                 map_scenes.push_back(g.sid);
             }
     }
-    // device blob: select pieces | GEMM pieces | tensor maps (128-byte aligned sections)
+    // tile variant of the grouped similarity: the autotuner's choice for this
+    // class of batch (mode, total rows, mean objects per row, each to a power
+    // of two), or, the first time, every variant timed on the first
+    // similarity batch (a graph is captured only once the class is tuned)
+    std::vector<int> vlist = {0};
+    int64_t tune_key = -1;
+    if (sim_mode >= 0) {
+        double wn = 0.0;
+        for (const auto &g : groups) wn += (double)(g.nq + g.nc) * (double)c.scenes[g.sid].n;
+        auto log2i = [](int64_t x) { int b = 0; while (b < 62 && (int64_t(1) << (b + 1)) <= x) ++b; return b; };
+        tune_key = (int64_t)sim_mode * 10000 + log2i(rows_total) * 100 + log2i((int64_t)(wn / (double)rows_total));
+        auto it = c.tuned.find(tune_key);
+        if (it != c.tuned.end()) {
+            vlist = {it->second};
+        } else {
+            vlist = {0, 1, 2, 3};
+            graph = false;
+        }
+    }
+    const int nv = (int)vlist.size();
+    // device blob: select pieces | GEMM pieces, one table per variant | tensor maps (128-byte aligned sections)
     const size_t off_gp = round_up((int64_t)(pieces.size() * sizeof(farm::Piece)), 128);
-    const size_t off_maps = off_gp + round_up((int64_t)(pieces.size() * sizeof(farm::GemmPiece)), 128);
-    const size_t blob_bytes = off_maps + map_scenes.size() * 2 * farm::kTensorMapBytes;
+    const size_t gp_table = round_up((int64_t)(pieces.size() * sizeof(farm::GemmPiece)), 128);
+    const size_t off_maps = off_gp + nv * gp_table;
+    const size_t blob_bytes = off_maps + map_scenes.size() * nv * 2 * farm::kTensorMapBytes;
     uint8_t *d_blob;
     CK(ws_get(ctx, farm::B_PIECES, blob_bytes, &d_blob));
     if (ctx->h_blob_n < blob_bytes) {
@@ -813,41 +834,50 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         ctx->h_blob_n = blob_bytes * 5 / 4 + 256;
     }
     farm::Piece *d_pieces = reinterpret_cast<farm::Piece *>(d_blob);
-    farm::GemmPiece *d_gpieces = reinterpret_cast<farm::GemmPiece *>(d_blob + off_gp);
     std::memcpy(ctx->h_blob, pieces.data(), pieces.size() * sizeof(farm::Piece));
-    std::vector<int64_t> batch_tiles(batches.size(), 0);
+    std::vector<int64_t> batch_tiles(batches.size() * nv, 0);
     if (sim_mode >= 0) {
-        farm::GemmPiece *hg = reinterpret_cast<farm::GemmPiece *>(ctx->h_blob + off_gp);
-        for (size_t b = 0; b < batches.size(); ++b) {
-            int64_t tiles = 0;
-            for (size_t k = batches[b].p0; k < batches[b].p0 + batches[b].np; ++k) {
-                const farm::Piece &pc = pieces[k];
-                const Scene &sc = c.scenes[piece_sid[k]];
-                farm::GemmPiece gp{};
-                gp.q_row0 = pc.q_row0;
-                gp.s_off = pc.s_off;
-                gp.tops_off = tile_tops ? pc.tops_off : -1;
-                gp.scale_d = sim_mode == farm::kSimFp8 ? sc.desc_scale : nullptr;
-                gp.bmap = d_blob + off_maps + (size_t)map_of_scene[piece_sid[k]] * 2 * farm::kTensorMapBytes;
-                gp.rows = pc.rows;
-                gp.n = pc.n;
-                gp.ld = pc.ld;
-                gp.tile_begin = (int32_t)tiles;
-                tiles += farm::sim_cluster_tiles(pc.rows, pc.n);
-                hg[k] = gp;
+        for (int vi = 0; vi < nv; ++vi) {
+            farm::GemmPiece *hg = reinterpret_cast<farm::GemmPiece *>(ctx->h_blob + off_gp + vi * gp_table);
+            for (size_t b = 0; b < batches.size(); ++b) {
+                int64_t tiles = 0;
+                for (size_t k = batches[b].p0; k < batches[b].p0 + batches[b].np; ++k) {
+                    const farm::Piece &pc = pieces[k];
+                    const Scene &sc = c.scenes[piece_sid[k]];
+                    farm::GemmPiece gp{};
+                    gp.q_row0 = pc.q_row0;
+                    gp.s_off = pc.s_off;
+                    gp.tops_off = tile_tops ? pc.tops_off : -1;
+                    gp.scale_d = sim_mode == farm::kSimFp8 ? sc.desc_scale : nullptr;
+                    gp.bmap = d_blob + off_maps +
+                              ((size_t)map_of_scene[piece_sid[k]] * nv + vi) * 2 * farm::kTensorMapBytes;
+                    gp.rows = pc.rows;
+                    gp.n = pc.n;
+                    gp.ld = pc.ld;
+                    gp.tile_begin = (int32_t)tiles;
+                    tiles += farm::sim_cluster_tiles(pc.rows, pc.n, vlist[vi]);
+                    hg[k] = gp;
+                }
+                if (tiles > 0x7fffffffLL) return fail(ctx, FARM_EINVAL, "similarity batch exceeds 2^31 tiles");
+                batch_tiles[b * nv + vi] = tiles;
             }
-            if (tiles > 0x7fffffffLL) return fail(ctx, FARM_EINVAL, "similarity batch exceeds 2^31 tiles");
-            batch_tiles[b] = tiles;
         }
         for (size_t m = 0; m < map_scenes.size(); ++m) {
             const Scene &sc = c.scenes[map_scenes[m]];
-            void *out = ctx->h_blob + off_maps + m * 2 * farm::kTensorMapBytes;
-            bool ok;
-            if (precision == FARM_PREC_FP32) ok = farm::sim_tc_encode_b(sim_mode, out, sc.desc_hi, sc.desc_lo, sc.n, sc.dim_pad);
-            else if (precision == FARM_PREC_BF16) ok = farm::sim_tc_encode_b(sim_mode, out, sc.desc_bf16, nullptr, sc.n, sc.dim_pad);
-            else if (precision == FARM_PREC_LEARNED) ok = farm::sim_tc_encode_b(sim_mode, out, sc.comp, nullptr, sc.n, c.mlp.P);
-            else ok = farm::sim_tc_encode_b(sim_mode, out, sc.desc_fp8, nullptr, sc.n, sc.dim_pad);
-            if (!ok) return fail(ctx, FARM_ECUDA, "tensor map encoding failed for scene " + std::to_string(map_scenes[m]));
+            for (int vi = 0; vi < nv; ++vi) {
+                void *out = ctx->h_blob + off_maps + (m * nv + vi) * 2 * farm::kTensorMapBytes;
+                bool ok;
+                if (precision == FARM_PREC_FP32)
+                    ok = farm::sim_tc_encode_b(sim_mode, vlist[vi], out, sc.desc_hi, sc.desc_lo, sc.n, sc.dim_pad);
+                else if (precision == FARM_PREC_BF16)
+                    ok = farm::sim_tc_encode_b(sim_mode, vlist[vi], out, sc.desc_bf16, nullptr, sc.n, sc.dim_pad);
+                else if (precision == FARM_PREC_LEARNED)
+                    ok = farm::sim_tc_encode_b(sim_mode, vlist[vi], out, sc.comp, nullptr, sc.n, c.mlp.P);
+                else
+                    ok = farm::sim_tc_encode_b(sim_mode, vlist[vi], out, sc.desc_fp8, nullptr, sc.n, sc.dim_pad);
+                if (!ok)
+                    return fail(ctx, FARM_ECUDA, "tensor map encoding failed for scene " + std::to_string(map_scenes[m]));
+            }
         }
     }
 
@@ -879,21 +909,52 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         int32_t *sel_ti = reduced ? bsel_t : tsel_idx, *sel_li = reduced ? bsel_l : lsel_idx;
         float *sel_tc = reduced ? bsel_tv : tsel_cos, *sel_lc = reduced ? bsel_lv : nullptr;
         const int32_t sel_st = reduced ? cstride_t : stride_t, sel_sl = reduced ? cstride_l : stride_l;
+        int vsel = nv == 1 ? 0 : -1;     // index into vlist of the variant in use
         for (size_t b = 0; b < batches.size(); ++b) {
             const Batch &bt = batches[b];
             const int m1 = mark_begin(ctx, 1);
             if (sim_mode >= 0) {
                 const void *q0, *q1 = nullptr;
                 int32_t kdim = dim_pad;
-                int64_t q_rows = rows_total;
                 if (precision == FARM_PREC_FP32) { q0 = ops.qhi; q1 = ops.qlo; }
                 else if (precision == FARM_PREC_BF16) q0 = ops.qbf;
                 else if (precision == FARM_PREC_LEARNED) { q0 = ops.qcomp; kdim = c.mlp.P; }
                 else q0 = ops.qf8;
-                LAUNCH(farm::launch_sim_tc_grouped(sim_mode, q0, q1, q_rows, kdim, d_gpieces + bt.p0, (int32_t)bt.np,
-                                                   batch_tiles[b], d_sim, tile_tops ? d_tops : nullptr,
-                                                   precision == FARM_PREC_FP8 ? ops.qscale : nullptr, c.num_sms, c.d_err,
-                                                   c.stream));
+                auto launch_variant = [&](int vi) {
+                    return farm::launch_sim_tc_grouped(
+                        sim_mode, vlist[vi], q0, q1, rows_total, kdim,
+                        reinterpret_cast<farm::GemmPiece *>(d_blob + off_gp + vi * gp_table) + bt.p0, (int32_t)bt.np,
+                        batch_tiles[b * nv + vi], d_sim, tile_tops ? d_tops : nullptr,
+                        precision == FARM_PREC_FP8 ? ops.qscale : nullptr, c.num_sms, c.d_err, c.stream);
+                };
+                if (vsel < 0) {
+                    // autotune: every variant twice, the second run timed; all
+                    // write the same results, so the last run's output stands
+                    cudaEvent_t e0, e1;
+                    CK(cudaEventCreate(&e0));
+                    CK(cudaEventCreate(&e1));
+                    float best_ms = 0.f;
+                    for (int vi = 0; vi < nv; ++vi) {
+                        LAUNCH(launch_variant(vi));
+                        CK(cudaEventRecord(e0, c.stream));
+                        LAUNCH(launch_variant(vi));
+                        CK(cudaEventRecord(e1, c.stream));
+                        CK(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                        if (vsel < 0 || ms < best_ms) {
+                            best_ms = ms;
+                            vsel = vi;
+                        }
+                    }
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    c.tuned[tune_key] = vlist[vsel];
+                    // the batch's results come from the chosen variant, as every later batch's will
+                    if (vsel != nv - 1) LAUNCH(launch_variant(vsel));
+                } else {
+                    LAUNCH(launch_variant(vsel));
+                }
             } else {
                 for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
                     const farm::Piece &pc = pieces[k];
@@ -1115,6 +1176,98 @@ farm_status farm_similarity(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, con
         return check_device_errors(ctx);
     }
     return FARM_OK;
+}
+
+farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_t *count)
+{
+    if (!ctx) return FARM_EINVAL;
+    if (cap < 0 || (cap > 0 && !entries)) return fail(ctx, FARM_EINVAL, "entries must hold cap records");
+    int32_t i = 0;
+    for (const auto &kv : ctx->c.tuned) {
+        if (i < cap) {
+            entries[4 * i + 0] = (int32_t)(kv.first / 10000);
+            entries[4 * i + 1] = (int32_t)(kv.first / 100 % 100);
+            entries[4 * i + 2] = (int32_t)(kv.first % 100);
+            entries[4 * i + 3] = kv.second;
+        }
+        ++i;
+    }
+    if (count) *count = i;
+    return FARM_OK;
+}
+
+farm_status farm_similarity_variant(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb,
+                                    int32_t precision, int32_t variant, float *out, uint32_t flags)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    if (scene_id < 0 || scene_id >= kMaxScenes || !c.scenes[scene_id].present)
+        return fail(ctx, FARM_EINVAL, "unknown scene");
+    if (n_rows < 0) return fail(ctx, FARM_EINVAL, "n_rows must be >= 0");
+    if (variant < 0 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [0, 4)");
+    int mode;
+    if (precision == FARM_PREC_FP32) mode = farm::kSimF16x3;
+    else if (precision == FARM_PREC_BF16) mode = farm::kSimBf16;
+    else if (precision == FARM_PREC_FP8) mode = farm::kSimFp8;
+    else return fail(ctx, FARM_EINVAL, "precision must be FARM_PREC_FP32, FARM_PREC_BF16 or FARM_PREC_FP8");
+    if (n_rows == 0) return FARM_OK;
+    if (!emb || !out) return fail(ctx, FARM_EINVAL, "emb and out must be non-null");
+    if (!farm::sim_tc_available()) return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
+    CK(cudaSetDevice(c.device));
+    const Scene &s = c.scenes[scene_id];
+    const bool dev = (flags & FARM_PTR_DEVICE) != 0;
+    const float *src = emb;
+    if (!dev) {
+        float *raw;
+        CK(ws_get(ctx, farm::B_RAW, (size_t)n_rows * s.dim, &raw));
+        CK(cudaMemcpyAsync(raw, emb, (size_t)n_rows * s.dim * 4, cudaMemcpyHostToDevice, c.stream));
+        src = raw;
+    }
+    RowOps ops;
+    CK(alloc_rows(ctx, precision, n_rows, s.dim_pad, ops));
+    LAUNCH(farm::launch_normalize_rows(src, nullptr, n_rows, s.dim, s.dim_pad, ops.q32, ops.qhi, ops.qlo, ops.qbf,
+                                       c.d_err, farm::kErrBadRow, c.stream));
+    if (precision == FARM_PREC_FP8)
+        LAUNCH(farm::launch_quantize_fp8_rows(ops.q32, n_rows, s.dim_pad, ops.qf8, ops.qscale, c.stream));
+    const int64_t ld = round_up(s.n, 32);
+    float *S;
+    CK(ws_get(ctx, farm::B_SIM, (size_t)n_rows * ld, &S));
+    // one piece and its scene's tensor maps, copied from pageable host memory
+    // (the copy completes before the call returns, so the host buffer is free)
+    std::vector<uint8_t> blob(128 + 2 * farm::kTensorMapBytes + 64);
+    uint8_t *hb = blob.data() + ((64 - (reinterpret_cast<uintptr_t>(blob.data()) & 63)) & 63);
+    uint8_t *d_blob;
+    CK(ws_get(ctx, farm::B_VARIANT, 128 + 2 * farm::kTensorMapBytes, &d_blob));
+    bool ok;
+    if (mode == farm::kSimF16x3) ok = farm::sim_tc_encode_b(mode, variant, hb + 128, s.desc_hi, s.desc_lo, s.n, s.dim_pad);
+    else if (mode == farm::kSimBf16) ok = farm::sim_tc_encode_b(mode, variant, hb + 128, s.desc_bf16, nullptr, s.n, s.dim_pad);
+    else ok = farm::sim_tc_encode_b(mode, variant, hb + 128, s.desc_fp8, nullptr, s.n, s.dim_pad);
+    if (!ok) return fail(ctx, FARM_ECUDA, "tensor map encoding failed");
+    farm::GemmPiece gp{};
+    gp.q_row0 = 0;
+    gp.s_off = 0;
+    gp.tops_off = -1;
+    gp.scale_d = mode == farm::kSimFp8 ? s.desc_scale : nullptr;
+    gp.bmap = d_blob + 128;
+    gp.rows = (int32_t)n_rows;
+    gp.n = (int32_t)s.n;
+    gp.ld = (int32_t)ld;
+    gp.tile_begin = 0;
+    std::memcpy(hb, &gp, sizeof(gp));
+    CK(cudaMemcpyAsync(d_blob, hb, 128 + 2 * farm::kTensorMapBytes, cudaMemcpyHostToDevice, c.stream));
+    const void *q0 = mode == farm::kSimF16x3 ? (const void *)ops.qhi : (mode == farm::kSimBf16 ? (const void *)ops.qbf : (const void *)ops.qf8);
+    LAUNCH(farm::launch_sim_tc_grouped(mode, variant, q0, ops.qlo, n_rows, s.dim_pad,
+                                       reinterpret_cast<const farm::GemmPiece *>(d_blob), 1,
+                                       farm::sim_cluster_tiles(n_rows, s.n, variant), S, nullptr,
+                                       mode == farm::kSimFp8 ? ops.qscale : nullptr, c.num_sms, c.d_err, c.stream));
+    if (dev) {
+        CK(cudaMemcpy2DAsync(out, (size_t)s.n * 4, S, (size_t)ld * 4, (size_t)s.n * 4, (size_t)n_rows,
+                             cudaMemcpyDeviceToDevice, c.stream));
+        return FARM_OK;
+    }
+    CK(cudaMemcpy2DAsync(out, (size_t)s.n * 4, S, (size_t)ld * 4, (size_t)s.n * 4, (size_t)n_rows,
+                         cudaMemcpyDeviceToHost, c.stream));
+    return check_device_errors(ctx);
 }
 
 farm_status farm_candidates(farm_ctx *ctx, uint64_t batch_handle, int32_t *tgt_idx, int32_t *lm_idx,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -87,7 +88,8 @@ enum Buf {
     B_PIECES,       // Piece tables of the batch's grouped launches
     B_CHUNK_IDX,    // int32 chunk lists of long rows (select, then merge)
     B_CHUNK_VAL,    // float their values
-    B_TOPS,         // float per-row tile maxima of the tensor-core similarity (thresholded select)
+    B_TOPS,         // float per-row group maxima of the tensor-core similarity (thresholded select)
+    B_VARIANT,      // one piece and its tensor maps (farm_similarity_variant)
     B_COUNT
 };
 
@@ -128,6 +130,7 @@ struct Ctx {
     int32_t *d_err = nullptr;     // device error word
     uint64_t ws_gen = 0;          // bumped whenever a workspace buffer moves
     uint64_t scene_gen = 0;       // bumped on every scene upload
+    std::map<int64_t, int> tuned; // similarity class -> fastest tile variant (autotuner)
     int32_t *d_fallback = nullptr;  // rows the thresholded select handed to its exact fallback
     int32_t *h_err = nullptr;     // pinned host mirror
     // batch state
@@ -202,12 +205,16 @@ cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_vi
 cudaError_t launch_sim_simt(const float *q, const float *d, float *S, int64_t rows, int64_t n,
                             int32_t dim_pad, int64_t ld_s, cudaStream_t s);
 
-// Tiles of the tensor-core similarity kernels: kSimTileM query rows x
-// kSimTileN objects per CTA, kSimCluster vertically adjacent CTAs per cluster
-// sharing one descriptor tile.
+// Tiles of the tensor-core similarity kernels: kSimTileM query rows per CTA;
+// a tile configuration ("variant") fixes the tile width and the cluster size
+// (CTAs on vertically adjacent tiles sharing one descriptor tile):
+//   0: 256 objects, clusters of 2;  1: 256, 1;  2: 128, 2;  3: 128, 1.
+// Every variant computes each output with the same K order, so they give
+// bitwise identical results; the planner's autotuner picks the fastest.
 constexpr int kSimTileM = 128;
-constexpr int kSimTileN = 256;
-constexpr int kSimCluster = 2;
+constexpr int kSimVariants = 4;
+inline int sim_variant_bn(int v) { return v < 2 ? 256 : 128; }
+inline int sim_variant_cluster(int v) { return (v & 1) ? 1 : 2; }
 enum SimMode { kSimF16x3 = 0, kSimBf16 = 1, kSimFp8 = 2 };
 
 // Group maxima: with a non-null `tops` the similarity epilogue also writes,
@@ -230,29 +237,32 @@ struct GemmPiece {
 };
 constexpr size_t kTensorMapBytes = 128;
 
-// Cluster tiles of one block of `rows` rows against `n` objects.
-inline int64_t sim_cluster_tiles(int64_t rows, int64_t n)
+// Cluster tiles of one block of `rows` rows against `n` objects in a variant.
+inline int64_t sim_cluster_tiles(int64_t rows, int64_t n, int variant)
 {
+    const int64_t bn = sim_variant_bn(variant), cm = sim_variant_cluster(variant);
     const int64_t mt = (rows + kSimTileM - 1) / kSimTileM;
-    return (mt + kSimCluster - 1) / kSimCluster * ((n + kSimTileN - 1) / kSimTileN);
+    return (mt + cm - 1) / cm * ((n + bn - 1) / bn);
 }
 
 // The two B tensor maps (hi / lo, or the one operand twice) of a scene's
-// descriptor operand in `mode`, written to host memory `out`
+// descriptor operand in `mode` for `variant`, written to host memory `out`
 // (2 * kTensorMapBytes, 64-byte aligned).  False when the encoder fails.
-bool sim_tc_encode_b(int mode, void *out, const void *d0, const void *d1, int64_t n, int32_t dim_pad);
+bool sim_tc_encode_b(int mode, int variant, void *out, const void *d0, const void *d1, int64_t n, int32_t dim_pad);
 
-// Grouped launch: every piece of the device table `pieces` (n_pieces,
-// ordered by tile_begin; total_tiles cluster tiles) against its scene, the
-// query operands q0 / q1 ([rows_total, dim_pad] in the mode's element type)
-// and FP8 row scales scale_q.  S and tops are the bases the pieces' offsets
-// refer to (tops nullable).
-cudaError_t launch_sim_tc_grouped(int mode, const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
-                                  const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S,
-                                  float *tops, const float *scale_q, int num_sms, int32_t *err, cudaStream_t s);
+// Grouped launch of `variant`: every piece of the device table `pieces`
+// (n_pieces, ordered by tile_begin, numbered with the variant's tiles;
+// total_tiles cluster tiles) against its scene, the query operands q0 / q1
+// ([rows_total, dim_pad] in the mode's element type) and FP8 row scales
+// scale_q.  S and tops are the bases the pieces' offsets refer to (tops
+// nullable).
+cudaError_t launch_sim_tc_grouped(int mode, int variant, const void *q0, const void *q1, int64_t rows_total,
+                                  int32_t dim_pad, const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles,
+                                  float *S, float *tops, const float *scale_q, int num_sms, int32_t *err,
+                                  cudaStream_t s);
 
 // One problem (rows x n, S leading dimension ld_s, group maxima at tops with
-// group_stride(n) floats per row, nullable) on the tensor cores.
+// group_stride(n) floats per row, nullable) on the tensor cores, variant 0.
 // Three FP16 terms, hi*hi + 2^-11 (hi*lo + lo*hi), from the split the
 // normalisation writes.
 cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, const uint16_t *d_hi,

@@ -55,58 +55,62 @@ namespace farm {
 namespace {
 
 constexpr int BM = kSimTileM;
-constexpr int BN = kSimTileN;
-static_assert(BN % 128 == 0, "group maxima are stored four at a time");
-constexpr int STAGES = 4;
-constexpr int STAGE_BYTES = 48 * 1024;       // BM + BN rows of 128 bytes of operand data
 constexpr int THREADS = 192;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int STAGE_BUDGET = 192 * 1024;     // shared memory for the operand pipeline
 constexpr uint32_t WAIT_LIMIT = 1u << 24;    // try_wait polls before giving up (about a second)
-constexpr int GROUP_M = 8;                   // tile raster: 8 cluster rows (16 row tiles) share each column tile
-constexpr int CM = kSimCluster;              // CTAs per cluster: vertically adjacent tiles sharing one B tile
-constexpr int ACC_CORR = 256;                // TMEM column of the correction accumulator (FP16x3 mode)
+constexpr int GROUP_M = 8;                   // tile raster: 8 cluster rows share each column tile
 constexpr float RESID_SCALE_INV = 1.f / 2048.f;   // the residual operands carry a factor 2^11
 
-
-// Per-mode layout of a pipeline stage.
+// Per-mode element layout of the operand rows of a K slice.
 template <int MODE>
-struct Mode;
+struct Elem;
 template <>
-struct Mode<kSimF16x3> {                        // three-term FP16 with scaled residuals
+struct Elem<kSimF16x3> {                     // three-term FP16 with scaled residuals
     static constexpr int BK = 32;            // FP16 elements per K slice (64-byte rows)
     static constexpr int ROW_BYTES = 64;
-    static constexpr int A_BYTES = BM * ROW_BYTES;   // 8 KB, twice (hi, lo)
-    static constexpr int B_BYTES = BN * ROW_BYTES;   // 16 KB, twice
     static constexpr int KSTEPS = 2;         // 16 FP16 values (32 bytes) per MMA
-    static constexpr int TMEM_COLS = 512;
+    static constexpr bool SPLIT = true;      // hi and lo tiles of each operand
     static constexpr uint64_t LAYOUT = 4;    // 64-byte swizzle
     static constexpr uint32_t SBO = 512;     // 8 rows x 64 bytes
 };
 template <>
-struct Mode<kSimBf16> {                         // BF16
+struct Elem<kSimBf16> {                      // BF16
     static constexpr int BK = 64;            // BF16 elements per K slice (128-byte rows)
     static constexpr int ROW_BYTES = 128;
-    static constexpr int A_BYTES = BM * ROW_BYTES;   // 16 KB
-    static constexpr int B_BYTES = BN * ROW_BYTES;   // 32 KB
     static constexpr int KSTEPS = 4;         // 16 BF16 values (32 bytes) per MMA
-    static constexpr int TMEM_COLS = 256;
+    static constexpr bool SPLIT = false;
     static constexpr uint64_t LAYOUT = 2;    // 128-byte swizzle
     static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
 };
 template <>
-struct Mode<kSimFp8> {                          // FP8 E4M3
+struct Elem<kSimFp8> {                       // FP8 E4M3
     static constexpr int BK = 128;           // FP8 elements per K slice (128-byte rows)
     static constexpr int ROW_BYTES = 128;
-    static constexpr int A_BYTES = BM * ROW_BYTES;   // 16 KB
-    static constexpr int B_BYTES = BN * ROW_BYTES;   // 32 KB
     static constexpr int KSTEPS = 4;         // 32 FP8 values (32 bytes) per MMA
-    static constexpr int TMEM_COLS = 256;
+    static constexpr bool SPLIT = false;
     static constexpr uint64_t LAYOUT = 2;    // 128-byte swizzle
     static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
 };
-static_assert(2 * Mode<kSimF16x3>::A_BYTES + 2 * Mode<kSimF16x3>::B_BYTES == STAGE_BYTES, "stage size");
-static_assert(Mode<kSimBf16>::A_BYTES + Mode<kSimBf16>::B_BYTES == STAGE_BYTES, "stage size");
-static_assert(Mode<kSimFp8>::A_BYTES + Mode<kSimFp8>::B_BYTES == STAGE_BYTES, "stage size");
+
+// A tile configuration: BN objects per tile, CM CTAs per cluster.
+template <int MODE, int BN_, int CM_>
+struct Cfg {
+    using E = Elem<MODE>;
+    static constexpr int BN = BN_;
+    static constexpr int CM = CM_;
+    static constexpr int OPS = E::SPLIT ? 2 : 1;                // operand copies (hi, lo)
+    static constexpr int A_BYTES = BM * E::ROW_BYTES;
+    static constexpr int B_BYTES = BN_ * E::ROW_BYTES;
+    static constexpr int B_PART = B_BYTES / CM_;                // this CTA's share of a B tile
+    static constexpr int STAGE_BYTES = OPS * (A_BYTES + B_BYTES);
+    static constexpr int STAGES = STAGE_BUDGET / STAGE_BYTES < 8 ? STAGE_BUDGET / STAGE_BYTES : 8;
+    static constexpr int ACC_COLS = OPS * BN_;                  // TMEM columns of one tile's accumulators
+    static constexpr int NACC = 512 / ACC_COLS >= 2 ? 2 : 1;    // tiles in flight in TMEM
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static_assert(BN_ % 128 == 0 && BN_ <= 256, "tile width");
+    static_assert(STAGES >= 3, "pipeline depth");
+    static_assert(BN_ / CM_ >= 8 && (B_PART % 1024) == 0, "B share must keep the swizzle atoms whole");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -184,48 +188,42 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);              // start address
-    d |= (uint64_t)(Mode<MODE>::SBO >> 4) << 32;            // stride byte offset
+    d |= (uint64_t)(Elem<MODE>::SBO >> 4) << 32;            // stride byte offset
     d |= (uint64_t)1 << 46;                                 // descriptor version
-    d |= Mode<MODE>::LAYOUT << 61;                          // swizzle mode
+    d |= Elem<MODE>::LAYOUT << 61;                          // swizzle mode
     return d;
 }
 
-// Instruction descriptors: D = F32, A and B K-major, M = 128, N = 256;
+// Instruction descriptors: D = F32, A and B K-major, M = 128, N = n;
 // operand format FP16 (0, kind::f16), BF16 (1, kind::f16) or E4M3 (0, kind::f8f6f4).
-__host__ __device__ constexpr uint32_t idesc(uint32_t ab_format)
+__host__ __device__ constexpr uint32_t idesc(uint32_t ab_format, int n)
 {
     return (1u << 4)                      // D format F32
            | (ab_format << 7)             // A format
            | (ab_format << 10)            // B format
-           | ((uint32_t)(BN >> 3) << 17)  // N / 8
+           | ((uint32_t)(n >> 3) << 17)   // N / 8
            | ((uint32_t)(BM >> 4) << 24); // M / 16
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
+// One MMA of the mode's kind (FP16 and BF16 operands: kind::f16; E4M3:
+// kind::f8f6f4), D (+)= A B^T into TMEM.
+template <int MODE, int BN_>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(0u)), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(1u)), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(0u)), "r"(accumulate));
+    if (MODE == kSimFp8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(0u, BN_)), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(MODE == kSimBf16 ? 1u : 0u, BN_)),
+              "r"(accumulate));
+    }
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
@@ -270,6 +268,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // CM vertically adjacent row tiles (CTA rank r takes the r-th) of one column
 // tile; under the grouped raster GROUP_M cluster rows share each column tile
 // so a descriptor tile is read from HBM about once per group.
+template <int BN_, int CM_>
 __device__ __forceinline__ void tile_origin(int tile, int m_super, int n_tiles, uint32_t rank, int &m0, int &n0)
 {
     const int per_group = GROUP_M * n_tiles;
@@ -277,8 +276,8 @@ __device__ __forceinline__ void tile_origin(int tile, int m_super, int n_tiles, 
     const int first_m = g * GROUP_M;
     const int gm = min(GROUP_M, m_super - first_m);
     const int in_g = tile - g * per_group;
-    m0 = ((first_m + in_g % gm) * CM + (int)rank) * BM;
-    n0 = (in_g / gm) * BN;
+    m0 = ((first_m + in_g % gm) * CM_ + (int)rank) * BM;
+    n0 = (in_g / gm) * BN_;
 }
 
 // Persistent, in clusters of CM CTAs: cluster c walks cluster tiles c,
@@ -288,12 +287,12 @@ __device__ __forceinline__ void tile_origin(int tile, int m_super, int n_tiles, 
 // when the CTA's own A and all CM parts of B have landed; a stage is free
 // again when the MMAs of every CTA have consumed it (the "empty" mbarrier
 // counts CM multicast commits).  The shared-memory pipeline runs on across
-// tiles.  Two-operand modes (BF16,
-// FP8) keep two accumulators in the 512 TMEM columns, so the epilogue of one
-// tile overlaps the MMAs of the next (acc_full / acc_empty mbarriers); the
-// FP16x3 mode needs both halves of TMEM for its main and correction
-// accumulators and drains before the next tile's MMAs start, while the
-// producer already prefetches that tile's first stages.
+// tiles.  When two tiles' accumulators fit the 512 TMEM columns (BF16 and
+// FP8; FP16x3 at 128-object tiles, whose main and correction accumulators
+// take 256 columns) the epilogue of one tile overlaps the MMAs of the next
+// (acc_full / acc_empty mbarriers); FP16x3 at 256-object tiles drains before
+// the next tile's MMAs start, while the producer already prefetches that
+// tile's first stages.
 // A launch covers either one problem (`single`, its B maps map_d0 / map_d1)
 // or, GROUPED, the pieces of a device table: blocks of query rows against
 // different scenes, with their B maps in device memory, numbered by cluster
@@ -317,14 +316,15 @@ __device__ __forceinline__ GemmPiece piece_of(int tile, const GemmPiece *pieces,
 
 // This CTA's tile of cluster tile `tile` within piece pc: first row (local
 // to the piece) and first column.
+template <int BN_, int CM_>
 __device__ __forceinline__ void piece_tile(const GemmPiece &pc, int tile, uint32_t rank, int &m0, int &n0)
 {
     const int m_tiles = (pc.rows + BM - 1) / BM;
-    const int n_tiles = (pc.n + BN - 1) / BN;
-    tile_origin(tile - pc.tile_begin, (m_tiles + CM - 1) / CM, n_tiles, rank, m0, n0);
+    const int n_tiles = (pc.n + BN_ - 1) / BN_;
+    tile_origin<BN_, CM_>(tile - pc.tile_begin, (m_tiles + CM_ - 1) / CM_, n_tiles, rank, m0, n0);
 }
 
-template <int MODE, bool GROUPED>
+template <int MODE, int BN_, int CM_, bool GROUPED>
 __global__ void __launch_bounds__(THREADS, 1)
 sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant__ CUtensorMap map_q1,
               const __grid_constant__ CUtensorMap map_d0, const __grid_constant__ CUtensorMap map_d1,
@@ -332,9 +332,14 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
               float *__restrict__ S, float *__restrict__ tops, int32_t k_slices, int32_t total,
               const float *__restrict__ scale_q, int32_t *err)
 {
-    using M = Mode<MODE>;
-    constexpr bool TWO_OPERAND_TILES = MODE != kSimF16x3;
-    constexpr int NACC = TWO_OPERAND_TILES ? 2 : 1;
+    using C = Cfg<MODE, BN_, CM_>;
+    using M = Elem<MODE>;
+    constexpr bool TWO_OPERAND_TILES = !M::SPLIT;
+    constexpr int NACC = C::NACC;
+    constexpr int STAGES = C::STAGES;
+    constexpr int STAGE_BYTES = C::STAGE_BYTES;
+    constexpr int BN = BN_, CM = CM_;
+    constexpr int ACC_CORR = BN_;            // correction accumulator: the columns after the main one
     constexpr uint32_t TMEM_ALLOC = 512;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -349,7 +354,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     const uint32_t rank = cluster_rank();
     const int cluster_id = blockIdx.x / CM, n_clusters = gridDim.x / CM;
     constexpr uint16_t ALL_CTAS = (uint16_t)((1u << CM) - 1u);
-    constexpr int B_PART = M::B_BYTES / CM;   // bytes of this CTA's share of a B tile
+    constexpr int B_PART = C::B_PART;         // bytes of this CTA's share of a B tile
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -379,7 +384,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             for (int tile = cluster_id; tile < total && !*abort_flag; tile += n_clusters) {
                 const GemmPiece pc = piece_of<GROUPED>(tile, pieces, n_pieces, single);
                 int m0, n0;
-                piece_tile(pc, tile, rank, m0, n0);
+                piece_tile<BN_, CM_>(pc, tile, rank, m0, n0);
                 const int qa = (int)(pc.q_row0 + m0);     // A rows: the piece's rows in the operand arrays
                 const CUtensorMap *bmap0 = GROUPED ? static_cast<const CUtensorMap *>(pc.bmap) : &map_d0;
                 const CUtensorMap *bmap1 = GROUPED ? static_cast<const CUtensorMap *>(pc.bmap) + 1 : &map_d1;
@@ -396,12 +401,12 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     const int nb = n0 + (int)rank * (BN / CM);   // first B row of this CTA's share
                     if (TWO_OPERAND_TILES) {
                         tma_load_2d(st, &map_q0, &full[s], kx, qa);
-                        tma_load_2d_mc(st + M::A_BYTES + rank * B_PART, bmap0, &full[s], kx, nb, ALL_CTAS);
+                        tma_load_2d_mc(st + C::A_BYTES + rank * B_PART, bmap0, &full[s], kx, nb, ALL_CTAS);
                     } else {
                         tma_load_2d(st, &map_q0, &full[s], kx, qa);
-                        tma_load_2d(st + M::A_BYTES, &map_q1, &full[s], kx, qa);
-                        tma_load_2d_mc(st + 2 * M::A_BYTES + rank * B_PART, bmap0, &full[s], kx, nb, ALL_CTAS);
-                        tma_load_2d_mc(st + 2 * M::A_BYTES + M::B_BYTES + rank * B_PART, bmap1, &full[s], kx, nb,
+                        tma_load_2d(st + C::A_BYTES, &map_q1, &full[s], kx, qa);
+                        tma_load_2d_mc(st + 2 * C::A_BYTES + rank * B_PART, bmap0, &full[s], kx, nb, ALL_CTAS);
+                        tma_load_2d_mc(st + 2 * C::A_BYTES + C::B_BYTES + rank * B_PART, bmap1, &full[s], kx, nb,
                                        ALL_CTAS);
                     }
                 }
@@ -423,7 +428,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t acc = tmem + (TWO_OPERAND_TILES ? buf * 256u : 0u);
+                const uint32_t acc = tmem + buf * (uint32_t)C::ACC_COLS;
                 for (int kb = 0; kb < k_slices; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1u;
@@ -434,25 +439,23 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
                     if (TWO_OPERAND_TILES) {
-                        const uint32_t a = st, b = st + M::A_BYTES;
+                        const uint32_t a = st, b = st + C::A_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < M::KSTEPS; ++kk) {
                             const uint32_t off = kk * 32;     // 32 bytes along K: 16 BF16 or 32 FP8 values
-                            if (MODE == kSimBf16)
-                                mma_bf16(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
-                            else
-                                mma_e4m3(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
+                            mma<MODE, BN_>(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
                         }
                     } else {
-                        const uint32_t a_hi = st, a_lo = st + M::A_BYTES;
-                        const uint32_t b_hi = st + 2 * M::A_BYTES, b_lo = st + 2 * M::A_BYTES + M::B_BYTES;
+                        const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
+                        const uint32_t b_hi = st + 2 * C::A_BYTES, b_lo = st + 2 * C::A_BYTES + C::B_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < M::KSTEPS; ++kk) {
                             const uint32_t off = kk * 32;     // 16 FP16 values = 32 bytes along K
                             const uint32_t first = (kb | kk) != 0;
-                            mma_f16(acc, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), first);
-                            mma_f16(acc + ACC_CORR, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_lo + off), first);
-                            mma_f16(acc + ACC_CORR, smem_desc<MODE>(a_lo + off), smem_desc<MODE>(b_hi + off), 1u);
+                            mma<MODE, BN_>(acc, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), first);
+                            mma<MODE, BN_>(acc + ACC_CORR, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_lo + off),
+                                           first);
+                            mma<MODE, BN_>(acc + ACC_CORR, smem_desc<MODE>(a_lo + off), smem_desc<MODE>(b_hi + off), 1u);
                         }
                     }
                     mma_commit_mc(&empty[s], ALL_CTAS);
@@ -475,7 +478,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             asm volatile("tcgen05.fence::after_thread_sync;");
             const GemmPiece pc = piece_of<GROUPED>(tile, pieces, n_pieces, single);
             int m0, n0;
-            piece_tile(pc, tile, rank, m0, n0);
+            piece_tile<BN_, CM_>(pc, tile, rank, m0, n0);
             const int64_t r = (int64_t)m0 + quad * 32 + lane;    // row within the piece
             const int64_t rows = pc.rows, n = pc.n;
             const bool live = r < rows;
@@ -488,8 +491,8 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
 #pragma unroll
             for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
-                const uint32_t lane_addr = tmem + (TWO_OPERAND_TILES ? buf * 256u : 0u) +
-                                           ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32);
+                const uint32_t lane_addr = tmem + buf * (uint32_t)C::ACC_COLS + ((uint32_t)(quad * 32) << 16) +
+                                           (uint32_t)(c * 32);
                 tmem_ld32(lane_addr, v);
                 if (MODE == kSimF16x3) {
                     float w[32];
@@ -565,7 +568,7 @@ bool get_encoder()
 template <int MODE>
 bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, int box_outer)
 {
-    using M = Mode<MODE>;
+    using M = Elem<MODE>;
     const int esize = MODE == kSimFp8 ? 1 : 2;
     const CUtensorMapDataType dt = MODE == kSimF16x3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : (MODE == kSimBf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
@@ -582,47 +585,48 @@ bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, in
 
 // Launch with the cluster attribute and a persistent grid of as many clusters
 // as can be resident at once (a GPC with an odd number of free SMs cannot
-// hold a whole cluster on its last SM); the count is cached per device,
-// mode and kind (concurrent first calls compute the same value).
-template <int MODE, bool GROUPED>
+// hold a whole cluster on its last SM); the count is cached per device and
+// kernel (concurrent first calls compute the same value).
+template <int MODE, int BN_, int CM_, bool GROUPED>
 cudaError_t launch_impl(const CUtensorMap &mq0, const CUtensorMap &mq1, const CUtensorMap &md0,
                         const CUtensorMap &md1, const GemmPiece *pieces, int32_t n_pieces, const GemmPiece &single,
                         float *S, float *tops, int32_t k_slices, int64_t total_tiles, const float *scale_q,
                         int num_sms, int32_t *err, cudaStream_t s)
 {
+    using C = Cfg<MODE, BN_, CM_>;
     if (total_tiles <= 0) return cudaSuccess;
     if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(sim_tc_kernel<MODE, GROUPED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
+    auto kernel = sim_tc_kernel<MODE, BN_, CM_, GROUPED>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.dynamicSmemBytes = C::SMEM_BYTES;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CM;
+    attr[0].val.clusterDim.x = CM_;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    static int resident[64][3][2] = {};
+    static int resident[64] = {};
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    int *slot = dev >= 0 && dev < 64 ? &resident[dev][MODE][GROUPED ? 1 : 0] : nullptr;
+    int *slot = dev >= 0 && dev < 64 ? &resident[dev] : nullptr;
     int nc = slot ? *slot : 0;
     if (nc == 0) {
-        cfg.gridDim = dim3((unsigned)(std::max(num_sms / CM, 1) * CM));
-        if (cudaOccupancyMaxActiveClusters(&nc, sim_tc_kernel<MODE, GROUPED>, &cfg) != cudaSuccess || nc < 1) {
+        cfg.gridDim = dim3((unsigned)(std::max(num_sms / CM_, 1) * CM_));
+        if (cudaOccupancyMaxActiveClusters(&nc, kernel, &cfg) != cudaSuccess || nc < 1) {
             (void)cudaGetLastError();    // the query's error is not the launch's
-            nc = std::max(num_sms / CM, 1);
+            nc = std::max(num_sms / CM_, 1);
         }
         if (slot) *slot = nc;
     }
     const int clusters = (int)std::min<int64_t>(total_tiles, nc);
-    cfg.gridDim = dim3((unsigned)(clusters * CM));
-    e = cudaLaunchKernelEx(&cfg, sim_tc_kernel<MODE, GROUPED>, mq0, mq1, md0, md1, pieces, n_pieces, single, S, tops,
-                           k_slices, (int32_t)total_tiles, scale_q, err);
+    cfg.gridDim = dim3((unsigned)(clusters * CM_));
+    e = cudaLaunchKernelEx(&cfg, kernel, mq0, mq1, md0, md1, pieces, n_pieces, single, S, tops, k_slices,
+                           (int32_t)total_tiles, scale_q, err);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -632,17 +636,20 @@ cudaError_t launch_impl(const CUtensorMap &mq0, const CUtensorMap &mq1, const CU
 template <int MODE>
 int32_t k_slices_of(int32_t dim_pad)
 {
-    return (dim_pad + Mode<MODE>::BK - 1) / Mode<MODE>::BK;
+    return (dim_pad + Elem<MODE>::BK - 1) / Elem<MODE>::BK;
 }
 
+// One problem, tile configuration 0 (256-object tiles, clusters of two).
 template <int MODE>
 cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void *d1, float *S, int64_t rows,
                       int64_t n, int32_t dim_pad, int64_t ld_s, const float *scale_q, const float *scale_d,
                       float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
-    constexpr bool TWO = MODE != kSimF16x3;
+    constexpr int BN_ = 256, CM_ = 2;
+    constexpr bool TWO = !Elem<MODE>::SPLIT;
     if (rows <= 0 || n <= 0) return cudaSuccess;
-    if (dim_pad % kDimAlign != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL || ld_s < n) return cudaErrorInvalidValue;
+    if (dim_pad % kDimAlign != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL || ld_s < n || ld_s > 0x7fffffffLL)
+        return cudaErrorInvalidValue;
     if (!get_encoder()) return cudaErrorNotSupported;
     // TMA: 16-byte aligned bases; row strides are multiples of 16 bytes (dim_pad % 64 == 0)
     const uintptr_t al = (uintptr_t)q0 | (uintptr_t)d0 | (TWO ? 0 : ((uintptr_t)q1 | (uintptr_t)d1));
@@ -650,12 +657,12 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     if (tops && ((uintptr_t)tops & 15u)) return cudaErrorMisalignedAddress;
     if (MODE == kSimFp8 && (!scale_q || !scale_d)) return cudaErrorInvalidValue;
     CUtensorMap mq0, mq1, md0, md1;
-    if (!make_map<MODE>(&mq0, q0, dim_pad, rows, BM) || !make_map<MODE>(&md0, d0, dim_pad, n, BN / CM))
+    if (!make_map<MODE>(&mq0, q0, dim_pad, rows, BM) || !make_map<MODE>(&md0, d0, dim_pad, n, BN_ / CM_))
         return cudaErrorInvalidValue;
     if (TWO) {
         mq1 = mq0;
         md1 = md0;
-    } else if (!make_map<MODE>(&mq1, q1, dim_pad, rows, BM) || !make_map<MODE>(&md1, d1, dim_pad, n, BN / CM)) {
+    } else if (!make_map<MODE>(&mq1, q1, dim_pad, rows, BM) || !make_map<MODE>(&md1, d1, dim_pad, n, BN_ / CM_)) {
         return cudaErrorInvalidValue;
     }
     GemmPiece single{};
@@ -668,17 +675,17 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     single.n = (int32_t)n;
     single.ld = (int32_t)ld_s;
     single.tile_begin = 0;
-    if (ld_s > 0x7fffffffLL) return cudaErrorInvalidValue;
-    return launch_impl<MODE, false>(mq0, mq1, md0, md1, nullptr, 1, single, S, tops, k_slices_of<MODE>(dim_pad),
-                                    sim_cluster_tiles(rows, n), scale_q, num_sms, err, s);
+    return launch_impl<MODE, BN_, CM_, false>(mq0, mq1, md0, md1, nullptr, 1, single, S, tops,
+                                              k_slices_of<MODE>(dim_pad), sim_cluster_tiles(rows, n, 0), scale_q,
+                                              num_sms, err, s);
 }
 
-template <int MODE>
+template <int MODE, int BN_, int CM_>
 cudaError_t launch_grouped(const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
                            const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S, float *tops,
                            const float *scale_q, int num_sms, int32_t *err, cudaStream_t s)
 {
-    constexpr bool TWO = MODE != kSimF16x3;
+    constexpr bool TWO = !Elem<MODE>::SPLIT;
     if (total_tiles <= 0) return cudaSuccess;
     if (n_pieces < 1 || rows_total < 1 || rows_total > 0x7fffffffLL || dim_pad % kDimAlign != 0 || !pieces)
         return cudaErrorInvalidValue;
@@ -692,45 +699,73 @@ cudaError_t launch_grouped(const void *q0, const void *q1, int64_t rows_total, i
     else if (!make_map<MODE>(&mq1, q1, dim_pad, rows_total, BM)) return cudaErrorInvalidValue;
     GemmPiece unused{};
     // the B maps of the pieces live in device memory; map_d0 / map_d1 are unused
-    return launch_impl<MODE, true>(mq0, mq1, mq0, mq1, pieces, n_pieces, unused, S, tops, k_slices_of<MODE>(dim_pad),
-                                   total_tiles, scale_q, num_sms, err, s);
+    return launch_impl<MODE, BN_, CM_, true>(mq0, mq1, mq0, mq1, pieces, n_pieces, unused, S, tops,
+                                             k_slices_of<MODE>(dim_pad), total_tiles, scale_q, num_sms, err, s);
+}
+
+template <int MODE>
+cudaError_t launch_grouped_variant(int variant, const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
+                                   const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S,
+                                   float *tops, const float *scale_q, int num_sms, int32_t *err, cudaStream_t s)
+{
+    switch (variant) {
+    case 0:
+        return launch_grouped<MODE, 256, 2>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
+                                            scale_q, num_sms, err, s);
+    case 1:
+        return launch_grouped<MODE, 256, 1>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
+                                            scale_q, num_sms, err, s);
+    case 2:
+        return launch_grouped<MODE, 128, 2>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
+                                            scale_q, num_sms, err, s);
+    case 3:
+        return launch_grouped<MODE, 128, 1>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
+                                            scale_q, num_sms, err, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <int MODE>
+bool encode_b_variant(void *out, const void *d0, const void *d1, int64_t n, int32_t dim_pad, int variant)
+{
+    CUtensorMap *m = static_cast<CUtensorMap *>(out);
+    const int box = sim_variant_bn(variant) / sim_variant_cluster(variant);
+    return make_map<MODE>(&m[0], d0, dim_pad, n, box) && make_map<MODE>(&m[1], d1 ? d1 : d0, dim_pad, n, box);
 }
 
 }  // namespace
 
 bool sim_tc_available() { return get_encoder(); }
 
-bool sim_tc_encode_b(int mode, void *out, const void *d0, const void *d1, int64_t n, int32_t dim_pad)
+bool sim_tc_encode_b(int mode, int variant, void *out, const void *d0, const void *d1, int64_t n, int32_t dim_pad)
 {
-    if (!get_encoder() || n < 1 || (reinterpret_cast<uintptr_t>(out) & 63u)) return false;
-    CUtensorMap *m = static_cast<CUtensorMap *>(out);
     static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
-    switch (mode) {
-    case kSimF16x3:
-        return make_map<kSimF16x3>(&m[0], d0, dim_pad, n, BN / CM) && make_map<kSimF16x3>(&m[1], d1, dim_pad, n, BN / CM);
-    case kSimBf16:
-        return make_map<kSimBf16>(&m[0], d0, dim_pad, n, BN / CM) && make_map<kSimBf16>(&m[1], d0, dim_pad, n, BN / CM);
-    case kSimFp8:
-        return make_map<kSimFp8>(&m[0], d0, dim_pad, n, BN / CM) && make_map<kSimFp8>(&m[1], d0, dim_pad, n, BN / CM);
-    default:
+    if (!get_encoder() || n < 1 || variant < 0 || variant >= kSimVariants || (reinterpret_cast<uintptr_t>(out) & 63u))
         return false;
+    switch (mode) {
+    case kSimF16x3: return encode_b_variant<kSimF16x3>(out, d0, d1, n, dim_pad, variant);
+    case kSimBf16: return encode_b_variant<kSimBf16>(out, d0, nullptr, n, dim_pad, variant);
+    case kSimFp8: return encode_b_variant<kSimFp8>(out, d0, nullptr, n, dim_pad, variant);
+    default: return false;
     }
 }
 
-cudaError_t launch_sim_tc_grouped(int mode, const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
-                                  const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S,
-                                  float *tops, const float *scale_q, int num_sms, int32_t *err, cudaStream_t s)
+cudaError_t launch_sim_tc_grouped(int mode, int variant, const void *q0, const void *q1, int64_t rows_total,
+                                  int32_t dim_pad, const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles,
+                                  float *S, float *tops, const float *scale_q, int num_sms, int32_t *err,
+                                  cudaStream_t s)
 {
     switch (mode) {
     case kSimF16x3:
-        return launch_grouped<kSimF16x3>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops, scale_q,
-                                      num_sms, err, s);
+        return launch_grouped_variant<kSimF16x3>(variant, q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles,
+                                                 S, tops, scale_q, num_sms, err, s);
     case kSimBf16:
-        return launch_grouped<kSimBf16>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops, scale_q,
-                                     num_sms, err, s);
+        return launch_grouped_variant<kSimBf16>(variant, q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles,
+                                                S, tops, scale_q, num_sms, err, s);
     case kSimFp8:
-        return launch_grouped<kSimFp8>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops, scale_q,
-                                    num_sms, err, s);
+        return launch_grouped_variant<kSimFp8>(variant, q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles,
+                                               S, tops, scale_q, num_sms, err, s);
     default:
         return cudaErrorInvalidValue;
     }
@@ -740,21 +775,23 @@ cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, cons
                                 const uint16_t *d_lo, float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s,
                                 float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kSimF16x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms, err,
-                             s);
+    return launch_tc<kSimF16x3>(q_hi, q_lo, d_hi, d_lo, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms,
+                                err, s);
 }
 
 cudaError_t launch_sim_tc_bf16(const uint16_t *q, const uint16_t *d, float *S, int64_t rows, int64_t n,
                                int32_t dim_pad, int64_t ld_s, float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kSimBf16>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms, err, s);
+    return launch_tc<kSimBf16>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, nullptr, nullptr, tops, num_sms,
+                               err, s);
 }
 
 cudaError_t launch_sim_tc_fp8(const uint8_t *q, const float *scale_q, const uint8_t *d, const float *scale_d,
                               float *S, int64_t rows, int64_t n, int32_t dim_pad, int64_t ld_s, float *tops,
                               int num_sms, int32_t *err, cudaStream_t s)
 {
-    return launch_tc<kSimFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, tops, num_sms, err, s);
+    return launch_tc<kSimFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, tops, num_sms,
+                              err, s);
 }
 
 }  // namespace farm

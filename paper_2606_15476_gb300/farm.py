@@ -56,6 +56,8 @@ def _load():
         "farm_similarity": (C.c_int, [P, I32, I64, P, I32, P, U32]),
         "farm_scene_info": (C.c_int, [P, I32, P, P]),
         "farm_select_fallbacks": (C.c_int, [P, P, I32]),
+        "farm_sim_tuning": (C.c_int, [P, P, I32, P]),
+        "farm_similarity_variant": (C.c_int, [P, I32, I64, P, I32, I32, P, U32]),
         "farm_candidates": (C.c_int, [P, U64, P, P, P, P]),
         "farm_rank_rows_noalloc": (C.c_int, [P, I32, I64, P, I32, I32, P, P]),
         "farm_mlp_set": (C.c_int, [P, I32, I32, I32, P, P, P, P]),
@@ -81,7 +83,7 @@ _lib = _load()
 def exported_symbols():
     return ["farm_default_params", "farm_create", "farm_destroy", "farm_memory_upload",
             "farm_query_batch", "farm_topk", "farm_sync", "farm_similarity", "farm_scene_info",
-            "farm_select_fallbacks",
+            "farm_select_fallbacks", "farm_sim_tuning", "farm_similarity_variant",
             "farm_candidates",
             "farm_rank_rows_noalloc", "farm_mlp_set", "farm_mlp_get", "farm_mlp_loss_grad",
             "farm_mlp_train", "farm_mlp_embed", "farm_set_profiling", "farm_stage_times",
@@ -220,6 +222,25 @@ def farm_select_fallbacks(ctx, reset: bool = False) -> int:
     v = C.c_int64()
     _ck(ctx, _lib.farm_select_fallbacks(ctx, C.byref(v), 1 if reset else 0))
     return int(v.value)
+
+
+def farm_sim_tuning(ctx):
+    """The autotuner's decisions: a list of (mode, log2 rows, log2 mean objects per row, variant)."""
+    n = C.c_int32()
+    _ck(ctx, _lib.farm_sim_tuning(ctx, None, 0, C.byref(n)))
+    buf = np.zeros((max(n.value, 1), 4), np.int32)
+    _ck(ctx, _lib.farm_sim_tuning(ctx, buf.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
+    return [tuple(int(x) for x in r) for r in buf[:n.value]]
+
+
+def farm_similarity_variant(ctx, scene_id: int, emb, precision: int, variant: int):
+    """Cosines [rows, n] of `emb` against a scene by one tile variant (host arrays)."""
+    e = np.ascontiguousarray(emb, dtype=np.float32)
+    n_scene, _ = farm_scene_info(ctx, scene_id)
+    out = np.zeros((e.shape[0], n_scene), np.float32)
+    _ck(ctx, _lib.farm_similarity_variant(ctx, int(scene_id), int(e.shape[0]), e.ctypes.data_as(C.c_void_p),
+                                          int(precision), int(variant), out.ctypes.data_as(C.c_void_p), 0))
+    return out
 
 
 def farm_scene_info(ctx, scene_id: int):

@@ -245,3 +245,35 @@ def test_no_fallback_on_the_site_scene(F):
             assert F.farm_select_fallbacks(ctx) == 0, code
     finally:
         F.farm_destroy(ctx)
+
+
+# ---- tile variants of the similarity kernel (autotuner) -------------------------
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_tile_variants_are_bitwise_identical(F, world, prec):
+    """Every tile variant computes each cosine with the same products in the
+    same order, so the autotuner may pick any of them without changing a
+    result: odd row counts, a ragged last column tile and rows that leave the
+    second CTA of a cluster idle."""
+    ctx, scenes, qb = world
+    code = {"fp32": F.PREC_FP32, "bf16": F.PREC_BF16, "fp8": F.PREC_FP8}[prec]
+    for sid, rows in ((30, 131), (32, 77), (34, 5)):
+        emb = qb.tgt_emb[:rows] if rows <= qb.n_q else qb.tgt_emb
+        ref = F.farm_similarity_variant(ctx, sid, emb, code, 0)
+        assert np.isfinite(ref).all()
+        for v in (1, 2, 3):
+            np.testing.assert_array_equal(F.farm_similarity_variant(ctx, sid, emb, code, v), ref,
+                                          err_msg=f"variant {v}, scene {sid}")
+        if prec != "fp8":
+            got = F.farm_similarity(ctx, sid, emb, scenes[sid].n, code)
+            np.testing.assert_array_equal(got, ref)
+
+
+def test_autotuner_records_a_decision(F, world):
+    ctx, scenes, qb = world
+    h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred, qb.c_emb,
+                           F.PREC_FP32)
+    F.farm_topk(ctx, h, 10, qb.n_q)
+    dec = F.farm_sim_tuning(ctx)
+    assert dec and all(0 <= d[3] < 4 for d in dec)
+    assert any(d[0] == 0 for d in dec)
