@@ -695,7 +695,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
         const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
         const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows_g, (int64_t)(kSimCapBytes / (ld * 4))));
-        const int32_t uni = (int32_t)std::min<int64_t>(farm::group_count(s.n), 8192);
+        const int gshift = farm::group_shift_for(s.n);
+        const int32_t uni = (int32_t)std::min<int64_t>(farm::group_count(s.n, gshift), 8192);
         // long rows of the shared-memory select: column chunks, merged after
         int32_t chunks = 1, chunk_len = (int32_t)s.n;
         bool global_select = false;
@@ -735,10 +736,14 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             pc.tops_off = -1;
             // rows [0, th0): shared-memory select; rows [th0, rows): thresholded select
             pc.th0 = pc.rows;
+            pc.gshift = gshift;
             if (tile_tops) {
-                pc.th0 = uni >= pc.keep_t ? 0 : (uni >= pc.keep_l ? pc.ntr : pc.rows);
+                // a row goes to the thresholded select when its group maxima
+                // number at least its list length, or it is short enough to sort whole
+                const bool small = s.n <= farm::kSelectSortAll;
+                pc.th0 = (small || uni >= pc.keep_t) ? 0 : (uni >= pc.keep_l ? pc.ntr : pc.rows);
                 pc.tops_off = bt.tops;
-                bt.tops += nr * farm::group_stride(s.n);
+                bt.tops += nr * farm::group_stride(s.n, gshift);
                 if (pc.th0 < pc.rows) {
                     bt.tblocks += pc.rows - pc.th0;
                     bt.max_union = std::max(bt.max_union, uni);
@@ -855,6 +860,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                     gp.n = pc.n;
                     gp.ld = pc.ld;
                     gp.tile_begin = (int32_t)tiles;
+                    gp.gshift = pc.gshift;
                     tiles += farm::sim_cluster_tiles(pc.rows, pc.n, vlist[vi]);
                     hg[k] = gp;
                 }
@@ -1253,6 +1259,7 @@ farm_status farm_similarity_variant(farm_ctx *ctx, int32_t scene_id, int64_t n_r
     gp.n = (int32_t)s.n;
     gp.ld = (int32_t)ld;
     gp.tile_begin = 0;
+    gp.gshift = farm::group_shift_for(s.n);
     std::memcpy(hb, &gp, sizeof(gp));
     CK(cudaMemcpyAsync(d_blob, hb, 128 + 2 * farm::kTensorMapBytes, cudaMemcpyHostToDevice, c.stream));
     const void *q0 = mode == farm::kSimF16x3 ? (const void *)ops.qhi : (mode == farm::kSimBf16 ? (const void *)ops.qbf : (const void *)ops.qf8);

@@ -218,12 +218,22 @@ inline int sim_variant_cluster(int v) { return (v & 1) ? 1 : 2; }
 enum SimMode { kSimF16x3 = 0, kSimBf16 = 1, kSimFp8 = 2 };
 
 // Group maxima: with a non-null `tops` the similarity epilogue also writes,
-// per row, the maximum of every group of 32 consecutive objects (-inf for
-// positions past the row end), group_stride(n) floats per row, 16-byte
-// aligned.  They are entries of the row, so their R-th largest value bounds
-// the row's R-th largest from below (the thresholded select uses it).
-__host__ __device__ constexpr int64_t group_count(int64_t n) { return (n + 31) / 32; }
-__host__ __device__ constexpr int64_t group_stride(int64_t n) { return (group_count(n) + 7) / 8 * 8; }
+// per row, the maximum of every group of 2^gshift consecutive objects
+// (gshift 5: groups of 32; 3: groups of 8, for small scenes; -inf for
+// positions past the row end), group_stride(n, gshift) floats per row,
+// 16-byte aligned.  They are entries of the row, so their R-th largest value
+// bounds the row's R-th largest from below (the thresholded select uses it).
+__host__ __device__ constexpr int64_t group_count(int64_t n, int gshift)
+{
+    return (n + (int64_t(1) << gshift) - 1) >> gshift;
+}
+__host__ __device__ constexpr int64_t group_stride(int64_t n, int gshift) { return (group_count(n, gshift) + 7) / 8 * 8; }
+constexpr int kGroupShiftSmall = 3;     // scenes of fewer than kSmallScene objects
+constexpr int kGroupShift = 5;
+constexpr int64_t kSmallScene = 8192;
+inline int group_shift_for(int64_t n) { return n < kSmallScene ? kGroupShiftSmall : kGroupShift; }
+// Rows of at most this many objects may be selected by sorting every entry.
+constexpr int kSelectSortAll = 2048;
 
 // One block of query rows against one scene in a grouped similarity launch.
 struct GemmPiece {
@@ -234,6 +244,8 @@ struct GemmPiece {
     const void *bmap;        // the scene's two B tensor maps (device memory, 64-byte aligned)
     int32_t rows, n, ld;     // rows of the block, objects, leading dimension of S
     int32_t tile_begin;      // first cluster tile of the block in the launch
+    int32_t gshift;          // group maxima over 2^gshift objects
+    int32_t pad;
 };
 constexpr size_t kTensorMapBytes = 128;
 
@@ -302,7 +314,7 @@ cudaError_t launch_select_rows_ex(const float *S, int64_t ld_s, int64_t n, int64
 // target rows.  Rows [0, th0) are selected by the shared-memory select
 // (launch_select_grouped, blocks from block_begin), rows [th0, rows) by the
 // thresholded select (launch_select_thresh, blocks from tblock_begin, group
-// maxima at tops + tops_off, group_stride(n) floats per row).
+// maxima at tops + tops_off, group_stride(n, gshift) floats per row).
 // A row of the shared-memory select longer than its limit is selected in
 // `chunks` column chunks of chunk_len entries, whose lists (tmp_stride
 // entries each, rows at tmp + tmp_off + i * chunks * tmp_stride) are merged
@@ -322,7 +334,8 @@ struct Piece {
     int32_t keep_t, keep_l; // list lengths the select keeps (R / K_a, or the rescore's C)
     int32_t R, klm;         // list lengths after a rescore
     int32_t chunks, chunk_len;
-    int32_t th0, pad0;
+    int32_t th0;
+    int32_t gshift;         // group maxima over 2^gshift objects (thresholded select)
 };
 
 // Grouped select over `pieces` (device; n_pieces entries) in one launch of
@@ -344,7 +357,8 @@ cudaError_t launch_merge_chunks(const Piece *pieces, int32_t n_pieces, int64_t t
                                 float *lsel_cos, int32_t stride_l, cudaStream_t s);
 // Thresholded select of rows [th0, rows) of every piece (one block per row,
 // total_blocks of them), from the group maxima `tops` the tensor-core
-// similarity kernel wrote; each row needs group_count(n) >= its list length.
+// similarity kernel wrote; each row needs group_count(n, gshift) >= its list
+// length, or n <= kSelectSortAll (then every entry is a candidate).
 // max_union: the largest group count of the launch (at most 8,192 are used).  Rows
 // whose candidates overflow fall back to an exact global-memory select and
 // are counted in *n_fallback (device).  Outputs as launch_select_grouped.

@@ -3,7 +3,7 @@
 // candidates): the R largest entries of a row, in rank order.
 //
 // The similarity kernel's epilogue leaves, per row, the maximum of every
-// group of 32 consecutive objects.  Those values are entries of the row, so
+// group of 32 (8 in small scenes) consecutive objects.  Those values are entries of the row, so
 // the R-th largest of their union, tau, is at most the row's R-th largest
 // value: every entry of rank <= R has a value >= tau.  One pass over the row
 // collects the entries >= tau (the top R, their ties, and the few entries
@@ -63,19 +63,21 @@ select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops
     }
     const int n = pc.n;
     const float *row = S + pc.s_off + (int64_t)i * pc.ld;
-    const int U = (int)min(group_count(n), (int64_t)UNION_MAX);
+    const int U = (int)min(group_count(n, pc.gshift), (int64_t)UNION_MAX);
 
-    // tau: the R-th largest key of the group maxima (the planner routes rows with U < R elsewhere)
-    const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(n);
-    for (int j = tid; j < U; j += TT) ukeys[j] = order_key(__ldg(tp + j));
-    __syncthreads();
-    const uint32_t T = kth_key<TT>(ukeys, U, R, hist, wsum, s3);
-
-    // one pass over the row: every entry with key >= T.  tau = key_value(T)
-    // is the union value itself (never -0), and for non-NaN x, x >= tau holds
-    // exactly when order_key(x) >= T, so the pass compares floats and builds
-    // keys only for the entries it keeps.
-    const float tau = key_value(T);
+    // tau: the R-th largest of the group maxima; a row with fewer groups than
+    // R (the planner sends only rows of at most kSelectSortAll objects) takes
+    // every entry as a candidate.  tau = key_value(T) is the group value
+    // itself (never -0), and for non-NaN x, x >= tau holds exactly when
+    // order_key(x) >= T, so the pass below compares floats and builds keys
+    // only for the entries it keeps.
+    float tau = -__int_as_float(0x7f800000);
+    if (U >= R) {
+        const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(n, pc.gshift);
+        for (int j = tid; j < U; j += TT) ukeys[j] = order_key(__ldg(tp + j));
+        __syncthreads();
+        tau = key_value(kth_key<TT>(ukeys, U, R, hist, wsum, s3));
+    }
     if (tid == 0) s_cnt = 0;
     __syncthreads();
     const int n4 = n >> 2;
@@ -135,6 +137,7 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
         ((uintptr_t)tops & 15u) != 0 || !n_fallback)
         return cudaErrorInvalidValue;
     const size_t smem = (size_t)(max_union < UNION_MAX ? max_union : UNION_MAX) * sizeof(uint32_t);
+    static_assert(CAP >= kSelectSortAll, "rows that take every entry fit the candidate buffer");
     cudaError_t e = cudaFuncSetAttribute(select_thresh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     select_thresh_kernel<<<(unsigned)total_blocks, TT, smem, s>>>(S, tops, pieces, n_pieces, tsel_idx, tsel_cos,

@@ -487,7 +487,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             const float sr = (MODE == kSimFp8 && live) ? scale_q[pc.q_row0 + r] : 1.f;
             const float *__restrict__ scale_d = pc.scale_d;
             const bool keep_tops = tops != nullptr && pc.tops_off >= 0 && live;
-            float gmax[BN / 32];     // maximum of each 32-column group of row r in this tile
+            float gmax[BN / 8];      // maximum of each 8-column group of row r in this tile
 #pragma unroll
             for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
@@ -506,16 +506,20 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     for (int i = 0; i < 32; ++i) v[i] *= sr * (col0 + i < n ? __ldg(scale_d + col0 + i) : 0.f);
                 }
                 if (keep_tops) {
-                    float m = -__int_as_float(0x7f800000);
-                    if (col0 + 32 <= n) {
+                    const float ninf = -__int_as_float(0x7f800000);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) m = fmaxf(m, v[i]);
-                    } else {
+                    for (int g = 0; g < 4; ++g) {
+                        float m = ninf;
+                        if (col0 + 32 <= n) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            if (col0 + i < n) m = fmaxf(m, v[i]);
+                            for (int i = 0; i < 8; ++i) m = fmaxf(m, v[8 * g + i]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                if (col0 + 8 * g + i < n) m = fmaxf(m, v[8 * g + i]);
+                        }
+                        gmax[4 * c + g] = m;
                     }
-                    gmax[c] = m;
                 }
                 if (live) {
                     if (vec && col0 + 32 <= n) {
@@ -530,10 +534,24 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 }
             }
             if (keep_tops) {
-                float4 *tp = reinterpret_cast<float4 *>(tops + pc.tops_off + r * group_stride(n) + n0 / 32);
+                float *trow = tops + pc.tops_off + r * group_stride(n, pc.gshift);
+                if (pc.gshift == kGroupShiftSmall) {
+                    float4 *tp = reinterpret_cast<float4 *>(trow + n0 / 8);
 #pragma unroll
-                for (int j = 0; j < BN / 32; j += 4)
-                    tp[j / 4] = make_float4(gmax[j], gmax[j + 1], gmax[j + 2], gmax[j + 3]);
+                    for (int j = 0; j < BN / 8; j += 4)
+                        tp[j / 4] = make_float4(gmax[j], gmax[j + 1], gmax[j + 2], gmax[j + 3]);
+                } else {
+                    float4 *tp = reinterpret_cast<float4 *>(trow + n0 / 32);
+#pragma unroll
+                    for (int j = 0; j < BN / 32; j += 4) {
+                        float g4[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            g4[u] = fmaxf(fmaxf(gmax[4 * (j + u)], gmax[4 * (j + u) + 1]),
+                                          fmaxf(gmax[4 * (j + u) + 2], gmax[4 * (j + u) + 3]));
+                        tp[j / 4] = make_float4(g4[0], g4[1], g4[2], g4[3]);
+                    }
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
@@ -675,6 +693,7 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     single.n = (int32_t)n;
     single.ld = (int32_t)ld_s;
     single.tile_begin = 0;
+    single.gshift = group_shift_for(n);
     return launch_impl<MODE, BN_, CM_, false>(mq0, mq1, md0, md1, nullptr, 1, single, S, tops,
                                               k_slices_of<MODE>(dim_pad), sim_cluster_tiles(rows, n, 0), scale_q,
                                               num_sms, err, s);
