@@ -221,13 +221,18 @@ enum SimMode { kSimF16x3 = 0, kSimBf16 = 1, kSimFp8 = 2 };
 // per row, the maximum of every group of 2^gshift consecutive objects
 // (gshift 5: groups of 32; 3: groups of 8, for small scenes; -inf for
 // positions past the row end), group_stride(n, gshift) floats per row,
-// 16-byte aligned.  They are entries of the row, so their R-th largest value
+// 16-byte aligned.  The epilogue writes the groups of whole column tiles, so
+// a row holds every group of ceil(n / 256) tiles of 256 objects (the widest
+// tile variant).  They are entries of the row, so their R-th largest value
 // bounds the row's R-th largest from below (the thresholded select uses it).
 __host__ __device__ constexpr int64_t group_count(int64_t n, int gshift)
 {
     return (n + (int64_t(1) << gshift) - 1) >> gshift;
 }
-__host__ __device__ constexpr int64_t group_stride(int64_t n, int gshift) { return (group_count(n, gshift) + 7) / 8 * 8; }
+__host__ __device__ constexpr int64_t group_stride(int64_t n, int gshift)
+{
+    return (n + 255) / 256 * (256 >> gshift);
+}
 constexpr int kGroupShiftSmall = 3;     // scenes of fewer than kSmallScene objects
 constexpr int kGroupShift = 5;
 constexpr int64_t kSmallScene = 8192;

@@ -1,8 +1,9 @@
 // k_compose.cu -- relation evaluation, best-witness binding and composite
 // scoring of every kept target candidate (App. D.2 steps 4-5; App. B).
 //
-// One CTA per query.  The query's landmark candidates (K_a per constraint,
-// in rank order) and their centres are staged in shared memory.  For every
+// One CTA per query; shared memory is sized by the batch's longest lists.
+// The query's landmark candidates (K_a per constraint, in rank order) and
+// their centres are staged in shared memory.  For every
 // kept target candidate of rank r the CTA computes
 //   s_sem = cf / (mu + r)                       (cf = class_mis on a class mismatch)
 // and the k_max-th largest s_sem, S_K.  k_max candidates score at least
@@ -10,8 +11,10 @@
 // size <= k_max (its composite is at most s_sem); only the others are scored:
 //   t_i   = max_{a in L_i, a != e} r_rho_i(e, a)   (bound anchor = argmax, lower index on ties)
 //   gbar  = (prod_i t_i)^(1/m),  s = s_sem * ((1 - w) + w * gbar)
-// with (candidate, constraint, landmark) triples spread over the threads and
-// the best witness kept by a 64-bit atomic max over (r, ~index).  Because the
+// with one warp per scored candidate: the warp stages the candidate's stored
+// views and its own projection in each (depth, image coordinate), its lanes
+// take the (constraint, landmark) pairs, and the best witness is kept by a
+// 64-bit shared-memory max over (r, ~index).  Because the
 // composite is non-decreasing in every t_i and the anchors only meet at the
 // target, the best binding takes each anchor's best witness on its own (the
 // star decomposition of App. B).  The CTA then sorts the scored candidates by
@@ -36,34 +39,35 @@ __device__ __forceinline__ uint32_t order_key(float f)
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// Left/right in the stored views of the candidate e (sign +1: LeftOf, -1: RightOf).
-__device__ float viewpoint_lr(const float *__restrict__ ve, int n_views, float ex, float ey,
-                              float ez, float ax, float ay, float az, float sign,
+// Per view of a candidate e, staged once per candidate: origin, unit forward,
+// unit right (x, y), e's depth Ze and image coordinate ue.
+constexpr int VREC = 12;                  // floats per staged view (three float4)
+
+// Left/right of landmark position (ax, ay, az) in the staged views of the
+// candidate (sign +1: LeftOf, -1: RightOf): mean over the views in which both
+// lie deeper than z_min, 0.5 when none does.
+__device__ float viewpoint_lr(const float *__restrict__ vs, int n_views, float ax, float ay, float az, float sign,
                               const farm_params &p)
 {
     float acc = 0.f;
     int counted = 0;
     for (int v = 0; v < n_views; ++v) {
-        const float4 o = *reinterpret_cast<const float4 *>(ve + v * kViewStride);
-        const float4 f = *reinterpret_cast<const float4 *>(ve + v * kViewStride + 4);
-        // o = (ox, oy, oz, fx), f = (fy, fz, rx, ry)
-        const float fx = o.w, fy = f.x, fz = f.y, rx = f.z, ry = f.w;
-        const float dex = ex - o.x, dey = ey - o.y, dez = ez - o.z;
+        const float4 o = *reinterpret_cast<const float4 *>(vs + v * VREC);      // ox, oy, oz, fx
+        const float4 f = *reinterpret_cast<const float4 *>(vs + v * VREC + 4);  // fy, fz, rx, ry
+        const float2 e = *reinterpret_cast<const float2 *>(vs + v * VREC + 8);  // Ze, ue
+        if (!(e.x > p.z_min)) continue;
         const float dax = ax - o.x, day = ay - o.y, daz = az - o.z;
-        const float Ze = dex * fx + dey * fy + dez * fz;
-        const float Za = dax * fx + day * fy + daz * fz;
-        if (!(Ze > p.z_min && Za > p.z_min)) continue;
-        const float ue = (dex * rx + dey * ry) / Ze;
-        const float ua = (dax * rx + day * ry) / Za;
-        acc += sigm(sign * (ua - ue) / p.tau_h);
+        const float Za = dax * o.w + day * f.x + daz * f.y;
+        if (!(Za > p.z_min)) continue;
+        const float ua = (dax * f.z + day * f.w) / Za;
+        acc += sigm(sign * (ua - e.y) / p.tau_h);
         ++counted;
     }
     return counted ? acc / (float)counted : 0.5f;
 }
 
-__device__ __forceinline__ float relation(int pred, float ex, float ey, float ez, float ax,
-                                          float ay, float az, const float *__restrict__ ve,
-                                          int n_views, const farm_params &p)
+__device__ __forceinline__ float relation(int pred, float ex, float ey, float ez, float ax, float ay, float az,
+                                          const float *__restrict__ vs, int n_views, const farm_params &p)
 {
     switch (pred) {
     case FARM_ABOVE: return sigm((ez - az) / p.tau_v);
@@ -73,28 +77,56 @@ __device__ __forceinline__ float relation(int pred, float ex, float ey, float ez
         const float d2 = dx * dx + dy * dy + dz * dz;
         return expf(-d2 / (2.f * p.sigma_near * p.sigma_near));
     }
-    case FARM_LEFT_OF: return viewpoint_lr(ve, n_views, ex, ey, ez, ax, ay, az, 1.f, p);
-    case FARM_RIGHT_OF: return viewpoint_lr(ve, n_views, ex, ey, ez, ax, ay, az, -1.f, p);
+    case FARM_LEFT_OF: return viewpoint_lr(vs, n_views, ax, ay, az, 1.f, p);
+    case FARM_RIGHT_OF: return viewpoint_lr(vs, n_views, ax, ay, az, -1.f, p);
     default: return 0.f;
     }
 }
 
+constexpr int WARPS = TH / 32;
+
+// Shared-memory layout of one query, sized by the batch's longest target list
+// RM (sorted as PM, the next power of two) and landmark list KM; every section
+// starts on a 16-byte boundary (the view slots are read as float4).
+struct ComposeSmem {
+    size_t best, key, vslot, lm_pos, lm_idx, cand_e, ssem, surv, slot, bytes;
+    __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
+    __host__ __device__ ComposeSmem(int RM, int PM, int KM)
+    {
+        size_t o = 0;
+        best = o;   o = up16(o + (size_t)RM * FARM_MAX_CONSTRAINTS * 8);
+        key = o;    o = up16(o + (size_t)PM * 8);
+        vslot = o;  o = up16(o + (size_t)WARPS * FARM_MAX_VIEWS * VREC * 4);
+        lm_pos = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
+        lm_idx = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 4);
+        cand_e = o; o = up16(o + (size_t)RM * 4);
+        ssem = o;   o = up16(o + (size_t)RM * 4);
+        surv = o;   o = up16(o + (size_t)RM * 2);
+        slot = o;   o = up16(o + (size_t)PM * 2);
+        bytes = o;
+    }
+};
+
 __global__ void __launch_bounds__(TH)
-compose_kernel(ComposeArgs a)
+compose_kernel(ComposeArgs a, int32_t PM)
 {
-    __shared__ int32_t lm_idx[FARM_MAX_CONSTRAINTS][kMaxAnchorCands];
-    __shared__ float lm_pos[FARM_MAX_CONSTRAINTS][kMaxAnchorCands][3];
-    __shared__ int32_t cand_e[kMaxTargetCands];
-    __shared__ float ssem[kMaxTargetCands];
-    __shared__ uint16_t surv[kMaxTargetCands];
-    __shared__ unsigned long long best[kMaxTargetCands][FARM_MAX_CONSTRAINTS];
-    __shared__ uint64_t key[kMaxTargetCands];
-    __shared__ uint16_t slot[kMaxTargetCands];
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int RM = a.stride_t, KM = a.stride_l;
+    const ComposeSmem L(RM, PM, KM);
+    unsigned long long *best = reinterpret_cast<unsigned long long *>(sm + L.best);   // [RM][4]
+    uint64_t *key = reinterpret_cast<uint64_t *>(sm + L.key);
+    float *vslot = reinterpret_cast<float *>(sm + L.vslot);                           // [WARPS][16][VREC]
+    float *lm_pos = reinterpret_cast<float *>(sm + L.lm_pos);                         // [4][KM][3]
+    int32_t *lm_idx = reinterpret_cast<int32_t *>(sm + L.lm_idx);                     // [4][KM]
+    int32_t *cand_e = reinterpret_cast<int32_t *>(sm + L.cand_e);
+    float *ssem = reinterpret_cast<float *>(sm + L.ssem);
+    uint16_t *surv = reinterpret_cast<uint16_t *>(sm + L.surv);
+    uint16_t *slot = reinterpret_cast<uint16_t *>(sm + L.slot);
     __shared__ float s_thr;
     __shared__ int s_ns;
 
     const int64_t q = blockIdx.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t *meta = a.qmeta + q * 8;
     const int scene = meta[QM_SCENE];
     const int c_t = meta[QM_CLS];
@@ -106,21 +138,27 @@ compose_kernel(ComposeArgs a)
     const int klm = meta[QM_KLM];
     const SceneDev sd = a.scenes[scene];
     const farm_params p = a.p;
+    bool any_lr = false;
+    for (int i = 0; i < m; ++i) any_lr |= preds[i] == FARM_LEFT_OF || preds[i] == FARM_RIGHT_OF;
 
+    // (an index outside the scene never reaches a memory access: such a
+    // landmark is skipped and such a candidate never survives)
     for (int t = tid; t < m * klm; t += TH) {
         const int i = t / klm, l = t - i * klm;
-        const int32_t ai = a.lsel_idx[(c0 + i) * a.stride_l + l];
-        lm_idx[i][l] = ai;
-        lm_pos[i][l][0] = sd.pos[ai];
-        lm_pos[i][l][1] = sd.pos[sd.n + ai];
-        lm_pos[i][l][2] = sd.pos[2 * sd.n + ai];
+        int32_t ai = a.lsel_idx[(c0 + i) * a.stride_l + l];
+        if (ai < 0 || ai >= sd.n) ai = -1;
+        lm_idx[i * KM + l] = ai;
+        lm_pos[(i * KM + l) * 3 + 0] = ai >= 0 ? sd.pos[ai] : 0.f;
+        lm_pos[(i * KM + l) * 3 + 1] = ai >= 0 ? sd.pos[sd.n + ai] : 0.f;
+        lm_pos[(i * KM + l) * 3 + 2] = ai >= 0 ? sd.pos[2 * sd.n + ai] : 0.f;
     }
     const int32_t *cand = a.tsel_idx + q * a.stride_t;
     for (int c = tid; c < R; c += TH) {
         const int32_t e = cand[c];
-        cand_e[c] = e;
-        const float cf = (c_t >= 0 && sd.cls[e] != c_t) ? p.class_mis : 1.f;
-        ssem[c] = cf / (p.mu + (float)(c + 1));
+        const bool ok = e >= 0 && e < sd.n;
+        cand_e[c] = ok ? e : -1;
+        const float cf = (c_t >= 0 && ok && sd.cls[e] != c_t) ? p.class_mis : 1.f;
+        ssem[c] = ok ? cf / (p.mu + (float)(c + 1)) : -1.f;
     }
     if (tid == 0) { s_thr = 0.f; s_ns = 0; }
     __syncthreads();
@@ -147,24 +185,39 @@ compose_kernel(ComposeArgs a)
     }
     __syncthreads();
     const int ns = s_ns;
-    for (int t = tid; t < ns * FARM_MAX_CONSTRAINTS; t += TH) best[t / FARM_MAX_CONSTRAINTS][t % FARM_MAX_CONSTRAINTS] = 0ull;
-    __syncthreads();
-    // best witness per (survivor, constraint): max r, lower landmark index on ties
+    // best witness per (survivor, constraint): one warp per survivor stages the
+    // candidate's views, each lane evaluates (constraint, landmark) pairs, and
+    // a max over (r, lower landmark index on ties) keeps the witness
+    float *vs = vslot + warp * FARM_MAX_VIEWS * VREC;
     const int per = m * klm;
-    for (int t = tid; t < ns * per; t += TH) {
-        const int pos = t / per;
-        const int rem = t - pos * per;
-        const int i = rem / klm, l = rem - i * klm;
+    for (int pos = warp; pos < ns; pos += WARPS) {
         const int32_t e = cand_e[surv[pos]];
-        const int32_t ai = lm_idx[i][l];
-        if (ai == e) continue;
         const float ex = sd.pos[e], ey = sd.pos[sd.n + e], ez = sd.pos[2 * sd.n + e];
-        const float *ve = sd.views + (int64_t)e * sd.n_views * kViewStride;
-        const float r = relation(preds[i], ex, ey, ez, lm_pos[i][l][0], lm_pos[i][l][1], lm_pos[i][l][2], ve,
-                                 sd.n_views, p);
-        const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) |
-                                     (unsigned long long)(0xffffffffu - (uint32_t)ai);
-        atomicMax(&best[pos][i], k);
+        if (lane < FARM_MAX_CONSTRAINTS) best[pos * FARM_MAX_CONSTRAINTS + lane] = 0ull;
+        if (any_lr && lane < sd.n_views) {
+            const float *ve = sd.views + ((int64_t)e * sd.n_views + lane) * kViewStride;
+            const float4 o = *reinterpret_cast<const float4 *>(ve);        // ox, oy, oz, fx
+            const float4 f = *reinterpret_cast<const float4 *>(ve + 4);    // fy, fz, rx, ry
+            const float dex = ex - o.x, dey = ey - o.y, dez = ez - o.z;
+            const float Ze = dex * o.w + dey * f.x + dez * f.y;
+            const float ue = (dex * f.z + dey * f.w) / Ze;
+            float *slotv = vs + lane * VREC;
+            *reinterpret_cast<float4 *>(slotv) = o;
+            *reinterpret_cast<float4 *>(slotv + 4) = f;
+            *reinterpret_cast<float2 *>(slotv + 8) = make_float2(Ze, ue);
+        }
+        __syncwarp();
+        for (int t = lane; t < per; t += 32) {
+            const int i = t / klm, l = t - i * klm;
+            const int32_t ai = lm_idx[i * KM + l];
+            if (ai == e || ai < 0) continue;
+            const float *ap = lm_pos + (i * KM + l) * 3;
+            const float r = relation(preds[i], ex, ey, ez, ap[0], ap[1], ap[2], vs, sd.n_views, p);
+            const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) |
+                                         (unsigned long long)(0xffffffffu - (uint32_t)ai);
+            atomicMax(&best[pos * FARM_MAX_CONSTRAINTS + i], k);
+        }
+        __syncwarp();      // the warp's view slot is rewritten for its next survivor
     }
     __syncthreads();
     for (int pos = tid; pos < ns; pos += TH) {
@@ -172,7 +225,7 @@ compose_kernel(ComposeArgs a)
         float t[FARM_MAX_CONSTRAINTS];
         bool zero = false;
         for (int i = 0; i < m; ++i) {
-            const unsigned long long b = best[pos][i];
+            const unsigned long long b = best[pos * FARM_MAX_CONSTRAINTS + i];
             t[i] = b ? __uint_as_float((uint32_t)(b >> 32)) : 0.f;
             zero |= !(t[i] > 0.f);
         }
@@ -216,7 +269,7 @@ compose_kernel(ComposeArgs a)
             a.out_idx[ob + c] = cand_e[surv[pos]];
             a.out_score[ob + c] = __uint_as_float(u);
             for (int i = 0; i < FARM_MAX_CONSTRAINTS; ++i) {
-                const unsigned long long b = i < m ? best[pos][i] : 0ull;
+                const unsigned long long b = i < m ? best[pos * FARM_MAX_CONSTRAINTS + i] : 0ull;
                 a.out_t[(ob + c) * 4 + i] = i < m ? (b ? __uint_as_float((uint32_t)(b >> 32)) : 0.f) : -1.f;
                 a.out_anchor[(ob + c) * 4 + i] = (i < m && b) ? (int32_t)(0xffffffffu - (uint32_t)(b & 0xffffffffu)) : -1;
             }
@@ -255,7 +308,17 @@ __global__ void gather_topk_kernel(int64_t n_q, int32_t k, int32_t ld, const int
 cudaError_t launch_compose(const ComposeArgs &a, cudaStream_t s)
 {
     if (a.n_q <= 0) return cudaSuccess;
-    compose_kernel<<<(unsigned)a.n_q, TH, 0, s>>>(a);
+    if (a.stride_t < 1 || a.stride_t > kMaxTargetCands || a.stride_l < 1 || a.stride_l > kMaxAnchorCands)
+        return cudaErrorInvalidValue;
+    int PM = 1;
+    while (PM < a.stride_t) PM <<= 1;
+    const ComposeSmem L(a.stride_t, PM, a.stride_l);
+    if (L.bytes + 64 > 48 * 1024) {     // (plus the kernel's few bytes of static shared memory)
+        const cudaError_t e = cudaFuncSetAttribute(compose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)L.bytes);
+        if (e != cudaSuccess) return e;
+    }
+    compose_kernel<<<(unsigned)a.n_q, TH, L.bytes, s>>>(a, PM);
     return cudaGetLastError();
 }
 

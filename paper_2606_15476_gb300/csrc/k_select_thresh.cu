@@ -112,7 +112,9 @@ select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops
     }
     __syncthreads();
     const int cnt = s_cnt;
-    if (cnt <= CAP) {
+    // (fewer than R candidates cannot happen with group maxima of this row;
+    // the exact select then stands in rather than list unfilled entries)
+    if (cnt >= R && cnt <= CAP) {
         int P = 1;
         while (P < cnt) P <<= 1;
         for (int j = cnt + tid; j < P; j += TT) cand[j] = 0ull;
