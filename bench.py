@@ -140,6 +140,29 @@ def cpu_baseline(scenes, qb, k, n_sample, seed=0):
                       f"queries, {dt:.1f} s wall"}, qs, ref
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the similarity kernel, from one ncu capture per (workload, precision, tile
+# variant) -- profiles/sim_tc_f16x3_site_n20k.md and profiles/sim_tc_bf16_site_n20k.md --
+# valid only while the kernel source is the one captured (sha256 prefix).
+SIM_TRAFFIC = {
+    ("site_n20k_d1152", "fp32", 0): 715.797504e6 + 1122.223e6,
+    ("site_n20k_d1152", "fp32", 1): 1352.835e6 + 1133.660e6,
+    ("site_n20k_d1152", "bf16", 0): 359.154432e6 + 1117.139e6,
+}
+SIM_TRAFFIC_SOURCE = "65ea3e3203eb11ae"
+
+
+def sim_traffic(workload, precision, variants):
+    """Captured bytes per launch, or None when the run differs from the capture."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2606_15476_gb300", "csrc", "k_sim_tc.cu"), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != SIM_TRAFFIC_SOURCE:
+            return None
+    if len(variants) != 1:
+        return None
+    return SIM_TRAFFIC.get((workload, precision, variants[0]))
+
+
 def similarity_flops(scenes, qb):
     """2 D N per (row, object) over every scene's rows: the algorithmic work of the similarity stage."""
     rows = np.bincount(qb.scene_of_q, minlength=len(scenes)).astype(np.float64)
@@ -236,6 +259,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=384)
     ap.add_argument("--ref-queries", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-variant", type=int, default=-1,
+                    help="pin the similarity kernel's tile variant (0-3) instead of autotuning it")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the timed steps directly instead of as CUDA graphs (FARM_GRAPH)")
     args = ap.parse_args()
@@ -270,6 +295,8 @@ def main():
     stream = torch.cuda.Stream()          # the library and the timing events share it
     torch.cuda.set_stream(stream)
     ctx = F.farm_create(local, stream)
+    if args.tile_variant >= 0:
+        F.farm_sim_variant_pin(ctx, args.tile_variant)
     for sid, scn in enumerate(scenes):
         F.farm_memory_upload(ctx, sid, scn.desc, scn.cls, scn.box, scn.views)
     training = train_prefilter(F, ctx, scenes) if args.precision == "learned" else None
@@ -400,11 +427,15 @@ def main():
         "autotuned_tiles": [{"mode": d[0], "log2_rows": d[1], "log2_objects": d[2],
                              "variant": d[3], "tile_n": 256 if d[3] < 2 else 128,
                              "cluster": 1 if d[3] & 1 else 2} for d in F.farm_sim_tuning(ctx)],
+        "pinned_tile_variant": args.tile_variant if args.tile_variant >= 0 else None,
         "stage_ms_per_step": {"prepare": stage_ms[0] / args.steps, "similarity": gemm_ms,
                               "select": stage_ms[2] / args.steps, "compose": stage_ms[3] / args.steps,
                               "direct_ms_per_step": ms_prof / args.steps},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None,
+                     "traffic": sim_traffic(args.workload, args.precision,
+                                            [args.tile_variant] if args.tile_variant >= 0
+                                            else sorted({d[3] for d in F.farm_sim_tuning(ctx)})),
                      "kernel": "similarity", "peak_source": peak_note},
         "clocks": clk.summary(),
     }

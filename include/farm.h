@@ -237,6 +237,13 @@ farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t rese
 farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_t *count);
 
 /*
+ * Pins every later batch of the context to one tile variant (0 .. 3), or,
+ * with -1, returns to the autotuner: for reproducible configurations, and for
+ * runs under a profiler, whose serialisation distorts the autotuner's timings.
+ */
+farm_status farm_sim_variant_pin(farm_ctx *ctx, int32_t variant);
+
+/*
  * Cosines as farm_similarity (FARM_PREC_FP32, FARM_PREC_BF16 or FARM_PREC_FP8),
  * computed by the given tile variant (0 .. 3), for checking the variants
  * against one another.

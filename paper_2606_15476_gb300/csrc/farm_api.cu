@@ -816,7 +816,9 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         auto log2i = [](int64_t x) { int b = 0; while (b < 62 && (int64_t(1) << (b + 1)) <= x) ++b; return b; };
         tune_key = (int64_t)sim_mode * 10000 + log2i(rows_total) * 100 + log2i((int64_t)(wn / (double)rows_total));
         auto it = c.tuned.find(tune_key);
-        if (it != c.tuned.end()) {
+        if (c.pinned_variant >= 0) {
+            vlist = {c.pinned_variant};
+        } else if (it != c.tuned.end()) {
             vlist = {it->second};
         } else {
             vlist = {0, 1, 2, 3};
@@ -1199,6 +1201,14 @@ farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_
         ++i;
     }
     if (count) *count = i;
+    return FARM_OK;
+}
+
+farm_status farm_sim_variant_pin(farm_ctx *ctx, int32_t variant)
+{
+    if (!ctx) return FARM_EINVAL;
+    if (variant < -1 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [-1, 4)");
+    ctx->c.pinned_variant = variant;
     return FARM_OK;
 }
 

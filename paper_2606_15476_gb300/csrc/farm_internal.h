@@ -131,6 +131,7 @@ struct Ctx {
     uint64_t ws_gen = 0;          // bumped whenever a workspace buffer moves
     uint64_t scene_gen = 0;       // bumped on every scene upload
     std::map<int64_t, int> tuned; // similarity class -> fastest tile variant (autotuner)
+    int pinned_variant = -1;      // >= 0: every grouped similarity launch uses this variant
     int32_t *d_fallback = nullptr;  // rows the thresholded select handed to its exact fallback
     int32_t *h_err = nullptr;     // pinned host mirror
     // batch state

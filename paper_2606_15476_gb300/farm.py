@@ -57,6 +57,7 @@ def _load():
         "farm_scene_info": (C.c_int, [P, I32, P, P]),
         "farm_select_fallbacks": (C.c_int, [P, P, I32]),
         "farm_sim_tuning": (C.c_int, [P, P, I32, P]),
+        "farm_sim_variant_pin": (C.c_int, [P, I32]),
         "farm_similarity_variant": (C.c_int, [P, I32, I64, P, I32, I32, P, U32]),
         "farm_candidates": (C.c_int, [P, U64, P, P, P, P]),
         "farm_rank_rows_noalloc": (C.c_int, [P, I32, I64, P, I32, I32, P, P]),
@@ -83,7 +84,7 @@ _lib = _load()
 def exported_symbols():
     return ["farm_default_params", "farm_create", "farm_destroy", "farm_memory_upload",
             "farm_query_batch", "farm_topk", "farm_sync", "farm_similarity", "farm_scene_info",
-            "farm_select_fallbacks", "farm_sim_tuning", "farm_similarity_variant",
+            "farm_select_fallbacks", "farm_sim_tuning", "farm_sim_variant_pin", "farm_similarity_variant",
             "farm_candidates",
             "farm_rank_rows_noalloc", "farm_mlp_set", "farm_mlp_get", "farm_mlp_loss_grad",
             "farm_mlp_train", "farm_mlp_embed", "farm_set_profiling", "farm_stage_times",
@@ -231,6 +232,11 @@ def farm_sim_tuning(ctx):
     buf = np.zeros((max(n.value, 1), 4), np.int32)
     _ck(ctx, _lib.farm_sim_tuning(ctx, buf.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
     return [tuple(int(x) for x in r) for r in buf[:n.value]]
+
+
+def farm_sim_variant_pin(ctx, variant: int) -> None:
+    """Pin the grouped similarity to one tile variant (0..3), or -1 for the autotuner."""
+    _ck(ctx, _lib.farm_sim_variant_pin(ctx, int(variant)))
 
 
 def farm_similarity_variant(ctx, scene_id: int, emb, precision: int, variant: int):

@@ -277,3 +277,23 @@ def test_autotuner_records_a_decision(F, world):
     dec = F.farm_sim_tuning(ctx)
     assert dec and all(0 <= d[3] < 4 for d in dec)
     assert any(d[0] == 0 for d in dec)
+
+
+def test_pinned_variant_gives_the_same_results(F, world):
+    ctx, scenes, qb = world
+    outs = []
+    try:
+        for v in (0, 2, 3):
+            F.farm_sim_variant_pin(ctx, v)
+            h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred,
+                                   qb.c_emb, F.PREC_FP32)
+            outs.append((F.farm_topk(ctx, h, 10, qb.n_q), F.farm_candidates(ctx, h, qb.n_q, qb.n_c)))
+    finally:
+        F.farm_sim_variant_pin(ctx, -1)
+    for o, (t, l) in outs[1:]:
+        for key in ("idx", "score", "pred", "anchor"):
+            np.testing.assert_array_equal(o[key], outs[0][0][key])
+        np.testing.assert_array_equal(t, outs[0][1][0])
+        np.testing.assert_array_equal(l, outs[0][1][1])
+    with pytest.raises(F.FarmError):
+        F.farm_sim_variant_pin(ctx, 4)
