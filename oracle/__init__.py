@@ -4,10 +4,10 @@ TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's
 CPU-baseline leg import this package.  The product path (the CUDA library and
 its binding) never does.
 """
-from .oracle import (ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, OracleParams, build, load,
-                     cosines, ranks, relation, sigmoid, query_all, query_bounds, batch,
-                     topk, num_threads)
+from .oracle import (ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND,
+                     CLOSEST, FARTHEST, OracleParams, build, load, cosines, ranks, relation,
+                     relation_in, sigmoid, query_all, query_bounds, batch, topk, num_threads)
 
-__all__ = ["ABOVE", "BELOW", "LEFT_OF", "RIGHT_OF", "NEAR", "OracleParams", "build", "load",
-           "cosines", "ranks", "relation", "sigmoid", "query_all", "query_bounds", "batch",
-           "topk", "num_threads"]
+__all__ = ["ABOVE", "BELOW", "LEFT_OF", "RIGHT_OF", "NEAR", "NEXT_TO", "ON", "IN_FRONT_OF", "BEHIND",
+           "CLOSEST", "FARTHEST", "OracleParams", "build", "load", "cosines", "ranks", "relation",
+           "relation_in", "sigmoid", "query_all", "query_bounds", "batch", "topk", "num_threads"]

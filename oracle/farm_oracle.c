@@ -43,6 +43,20 @@
  *       exceed z_min; left_of = mean over counted views of
  *       sig((u_a - u_e)/tau_h), right_of = mean of sig((u_e - u_a)/tau_h);
  *       0.5 when no view counts.
+ *       next_to(e,a) = exp(-|p_e - p_a|^2 / (2 sigma_next^2)), sigma_next = 1.0 m
+ *       on(e,a) = gate * band: gate = sig((rho_a - d_xy)/on_gate) with rho_a
+ *       half the landmark's larger horizontal size and d_xy the horizontal
+ *       centre distance; band = exp(-g^2 / (2 on_band^2)) with g the gap
+ *       between e's bottom and a's top.
+ *       in_front_of / behind: in the same counted views of e,
+ *       sig((Z_a - Z_e)/tau_d) (e nearer the camera) and sig((Z_e - Z_a)/tau_d);
+ *       mean over counted views, 0.5 when none counts.
+ *       closest / farthest: a rank within the candidate set C = the k_closest
+ *       objects of smallest target rank (step 2): rank_d(e) = 1 + #{j in
+ *       C \ {a} : |p_j - p_a| < |p_e - p_a|, or equal and j < e};
+ *       closest = 1 / rank_d, farthest = 1 / (|C \ {a}| - rank_d + 1)
+ *       (score = 1/(|rank - r*| + 1) with r* = 1 or |C \ {a}|); 0 when e is
+ *       not in C.
  *  6. t_i(e) = max_{a in L_i, a != e} r_rho_i(e, a), 0 without a witness; the
  *     bound anchor is the argmax (lower object index on ties).
  *  7. gbar = (prod_i t_i)^(1/m) (0 if some t_i = 0, 1 if m = 0);
@@ -69,6 +83,12 @@
 #define ORC_LEFT_OF 2
 #define ORC_RIGHT_OF 3
 #define ORC_NEAR 4
+#define ORC_NEXT_TO 5
+#define ORC_ON 6
+#define ORC_IN_FRONT_OF 7
+#define ORC_BEHIND 8
+#define ORC_CLOSEST 9
+#define ORC_FARTHEST 10
 
 #define ORC_OK 0
 #define ORC_EINVAL -1
@@ -83,6 +103,11 @@ typedef struct {
     double tau_h;       /* LeftOf/RightOf sigmoid scale, image units */
     double z_min;       /* minimum camera depth for a view to count, metres */
     int64_t k_anchor;   /* landmark candidates per constraint (K_a) */
+    double sigma_next;  /* NextTo Gaussian width, metres (1.0) */
+    double on_gate;     /* On: horizontal gate sigmoid scale, metres */
+    double on_band;     /* On: vertical band width, metres */
+    double tau_d;       /* InFrontOf/Behind depth sigmoid scale, metres */
+    int64_t k_closest;  /* Closest/Farthest: target candidates ranked (the set C) */
 } orc_params;
 
 typedef struct {
@@ -118,10 +143,10 @@ static double view_comp(const orc_scene *s, int comp, int64_t v, int64_t j)
     return (double)s->views[((int64_t)comp * s->n_views + v) * s->n + j];
 }
 
-/* Left/right in the stored views of e (step 5).  sign = +1 for left_of,
- * -1 for right_of. */
-static double viewpoint_lr(const orc_scene *s, const orc_params *p, int64_t e,
-                           int64_t a, double sign)
+/* Left/right (depth = 0) or front/behind (depth = 1) in the stored views of
+ * e (step 5).  sign = +1 for left_of / in_front_of, -1 for right_of / behind. */
+static double viewpoint_rel(const orc_scene *s, const orc_params *p, int64_t e,
+                            int64_t a, double sign, int depth)
 {
     double acc = 0.0;
     int64_t counted = 0;
@@ -141,23 +166,80 @@ static double viewpoint_lr(const orc_scene *s, const orc_params *p, int64_t e,
         double Ze = dex * fx + dey * fy + dez * fz;
         double Za = dax * fx + day * fy + daz * fz;
         if (!(Ze > p->z_min && Za > p->z_min)) continue;
-        double Xe = dex * rx + dey * ry;
-        double Xa = dax * rx + day * ry;
-        double ue = Xe / Ze, ua = Xa / Za;
-        acc += orc_sigmoid(sign * (ua - ue) / p->tau_h);
+        if (depth) {
+            acc += orc_sigmoid(sign * (Za - Ze) / p->tau_d);
+        } else {
+            double Xe = dex * rx + dey * ry;
+            double Xa = dax * rx + day * ry;
+            double ue = Xe / Ze, ua = Xa / Za;
+            acc += orc_sigmoid(sign * (ua - ue) / p->tau_h);
+        }
         counted += 1;
     }
     if (counted == 0) return 0.5;
     return acc / (double)counted;
 }
 
+static double box_size(const orc_scene *s, int axis, int64_t j)
+{
+    return (double)s->box[(int64_t)(3 + axis) * s->n + j];
+}
+
+static double dist2(const orc_scene *s, int64_t i, int64_t j)
+{
+    double dx = center(s, 0, i) - center(s, 0, j);
+    double dy = center(s, 1, i) - center(s, 1, j);
+    double dz = center(s, 2, i) - center(s, 2, j);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+/* Closest / farthest (step 5): rank of e by distance to a within the set
+ * `set` (n_set objects; e and a may or may not be members). */
+static double rank_relation(const orc_scene *s, int32_t pred, int64_t e, int64_t a,
+                            const int64_t *set, int64_t n_set)
+{
+    int in = 0;
+    for (int64_t k = 0; k < n_set; ++k) in |= set[k] == e;
+    if (!in || e == a) return 0.0;
+    double de = dist2(s, e, a);
+    int64_t members = 0, closer = 0;
+    for (int64_t k = 0; k < n_set; ++k) {
+        int64_t j = set[k];
+        if (j == a) continue;
+        members += 1;
+        double dj = dist2(s, j, a);
+        if (dj < de || (dj == de && j < e)) closer += 1;
+    }
+    int64_t rank_d = 1 + closer;
+    return pred == ORC_CLOSEST ? 1.0 / (double)rank_d : 1.0 / (double)(members - rank_d + 1);
+}
+
 /* r_rho(e, a): the soft relation score of predicate `pred` with e as the
- * target-side argument and a as the anchor (App. D.2 step 4). */
-double orc_relation(const orc_scene *s, const orc_params *p, int32_t pred,
-                    int64_t e, int64_t a)
+ * target-side argument and a as the anchor (App. D.2 step 4).  Closest and
+ * farthest need the query's candidate set: orc_relation_in. */
+double orc_relation_in(const orc_scene *s, const orc_params *p, int32_t pred, int64_t e, int64_t a,
+                       const int64_t *set, int64_t n_set)
 {
     double dz = center(s, 2, e) - center(s, 2, a);
     switch (pred) {
+    case ORC_NEXT_TO:
+        return exp(-dist2(s, e, a) / (2.0 * p->sigma_next * p->sigma_next));
+    case ORC_ON: {
+        double dx = center(s, 0, e) - center(s, 0, a);
+        double dy = center(s, 1, e) - center(s, 1, a);
+        double sxa = box_size(s, 0, a), sya = box_size(s, 1, a);
+        double rho = 0.5 * (sxa > sya ? sxa : sya);
+        double gate = orc_sigmoid((rho - sqrt(dx * dx + dy * dy)) / p->on_gate);
+        double gap = (center(s, 2, e) - 0.5 * box_size(s, 2, e)) - (center(s, 2, a) + 0.5 * box_size(s, 2, a));
+        return gate * exp(-gap * gap / (2.0 * p->on_band * p->on_band));
+    }
+    case ORC_IN_FRONT_OF:
+        return viewpoint_rel(s, p, e, a, +1.0, 1);
+    case ORC_BEHIND:
+        return viewpoint_rel(s, p, e, a, -1.0, 1);
+    case ORC_CLOSEST:
+    case ORC_FARTHEST:
+        return rank_relation(s, pred, e, a, set, n_set);
     case ORC_ABOVE:
         return orc_sigmoid(dz / p->tau_v);
     case ORC_BELOW:
@@ -169,12 +251,17 @@ double orc_relation(const orc_scene *s, const orc_params *p, int32_t pred,
         return exp(-d2 / (2.0 * p->sigma_near * p->sigma_near));
     }
     case ORC_LEFT_OF:
-        return viewpoint_lr(s, p, e, a, +1.0);
+        return viewpoint_rel(s, p, e, a, +1.0, 0);
     case ORC_RIGHT_OF:
-        return viewpoint_lr(s, p, e, a, -1.0);
+        return viewpoint_rel(s, p, e, a, -1.0, 0);
     default:
         return NAN;
     }
+}
+
+double orc_relation(const orc_scene *s, const orc_params *p, int32_t pred, int64_t e, int64_t a)
+{
+    return orc_relation_in(s, p, pred, e, a, NULL, 0);
 }
 
 /* Step 1: cosine of embedding u against every descriptor, all in FP64.
@@ -277,7 +364,7 @@ int orc_query_all(const orc_scene *s, const orc_params *p, const float *u0, int3
                   double *t_out, int64_t *anchor_out, double *s_out)
 {
     int64_t n = s->n;
-    if (n <= 0 || m < 0 || m > 64 || p->k_anchor < 1) return ORC_EINVAL;
+    if (n <= 0 || m < 0 || m > 64 || p->k_anchor < 1 || p->k_closest < 1) return ORC_EINVAL;
     int rc = ORC_OK;
     double *cos = (double *)malloc((size_t)n * sizeof(double));
     int64_t *rank = (int64_t *)malloc((size_t)n * sizeof(int64_t));
@@ -285,7 +372,10 @@ int orc_query_all(const orc_scene *s, const orc_params *p, const float *u0, int3
     int64_t *anc = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(int64_t));
     int64_t *lm = (int64_t *)malloc((size_t)p->k_anchor * sizeof(int64_t));
     double *ssem = (double *)malloc((size_t)n * sizeof(double));
-    if (!cos || !rank || !t || !anc || !lm || !ssem) { rc = ORC_ENOMEM; goto done; }
+    int64_t kc = p->k_closest < n ? p->k_closest : n;
+    int64_t *cset = (int64_t *)malloc((size_t)(kc > 0 ? kc : 1) * sizeof(int64_t));
+    int64_t n_cset = 0;
+    if (!cos || !rank || !t || !anc || !lm || !ssem || !cset) { rc = ORC_ENOMEM; goto done; }
 
     /* Steps 1-3 for the target row. */
     if ((rc = orc_cosines(s, u0, cos)) != ORC_OK) goto done;
@@ -296,6 +386,10 @@ int orc_query_all(const orc_scene *s, const orc_params *p, const float *u0, int3
         if (rank0_out) rank0_out[j] = rank[j];
         if (s_sem_out) s_sem_out[j] = ssem[j];
     }
+    /* the candidate set of closest / farthest: target ranks 1..k_closest */
+    for (int64_t r = 1; r <= kc; ++r)
+        for (int64_t j = 0; j < n; ++j)
+            if (rank[j] == r) { cset[n_cset++] = j; break; }
 
     /* Steps 1, 2, 4, 5, 6 for every constraint. */
     for (int32_t i = 0; i < m; ++i) {
@@ -313,7 +407,7 @@ int orc_query_all(const orc_scene *s, const orc_params *p, const float *u0, int3
             for (int64_t l = 0; l < n_lm; ++l) {
                 int64_t a = lm[l];
                 if (a == e) continue;
-                double r = orc_relation(s, p, preds[i], e, a);
+                double r = orc_relation_in(s, p, preds[i], e, a, cset, n_cset);
                 if (arg < 0 || r > best || (r == best && a < arg)) { best = r; arg = a; }
             }
             t[(int64_t)i * n + e] = arg < 0 ? 0.0 : best;
@@ -331,7 +425,7 @@ int orc_query_all(const orc_scene *s, const orc_params *p, const float *u0, int3
     if (t_out) memcpy(t_out, t, (size_t)m * (size_t)n * sizeof(double));
     if (anchor_out) memcpy(anchor_out, anc, (size_t)m * (size_t)n * sizeof(int64_t));
 done:
-    free(cos); free(rank); free(t); free(anc); free(lm); free(ssem);
+    free(cos); free(rank); free(t); free(anc); free(lm); free(ssem); free(cset);
     return rc;
 }
 
@@ -441,6 +535,33 @@ static int64_t count_geq(const double *a, int64_t n, double x)
     return n - lo;
 }
 
+/* Bounds of closest / farthest for a candidate e that is certainly in the
+ * candidate set `set` (n_set objects): distances within a relative dtol of
+ * one another may be ordered either way. */
+static void rank_relation_bounds(const orc_scene *s, int32_t pred, int64_t e, int64_t a,
+                                 const int64_t *set, int64_t n_set, double dtol, double *lo, double *hi)
+{
+    double de = dist2(s, e, a);
+    int64_t members = 0, c_lo = 0, c_hi = 0;
+    for (int64_t k = 0; k < n_set; ++k) {
+        int64_t j = set[k];
+        if (j == a) continue;
+        members += 1;
+        if (j == e) continue;
+        double dj = dist2(s, j, a);
+        if (dj < de * (1.0 - dtol)) c_lo += 1;
+        if (dj <= de * (1.0 + dtol)) c_hi += 1;
+    }
+    int64_t r_lo = 1 + c_lo, r_hi = 1 + c_hi;
+    if (pred == ORC_CLOSEST) {
+        *lo = 1.0 / (double)r_hi;
+        *hi = 1.0 / (double)r_lo;
+    } else {
+        *lo = 1.0 / (double)(members - r_lo + 1);
+        *hi = 1.0 / (double)(members - r_hi + 1);
+    }
+}
+
 /*
  * When two cosines differ by at most tau, an implementation whose cosines are
  * within tau/2 of the exact ones may order them either way.  For every object
@@ -451,6 +572,11 @@ static int64_t count_geq(const double *a, int64_t n, double x)
  *   s_sem in [cf/(mu + rank_hi), cf/(mu + rank_lo)];
  *   L_i contains D_i = {a : rank_hi_i(a) <= K_a} and lies in P_i = {a : rank_lo_i(a) <= K_a};
  *   t_i(e) in [max over D_i \ {e}, max over P_i \ {e}];  s in [s_lo, s_hi].
+ * Closest / farthest depend on the candidate set C (target ranks up to
+ * k_closest): when C is ambiguous (some object's rank range straddles
+ * k_closest) their scores are only known to lie in [0, 1] for possible
+ * members; otherwise squared distances within a relative 1e-5 may be
+ * ordered either way.
  * With tau = 0 on tie-free data every interval is a single point equal to
  * orc_query_all's result.
  * Outputs (length n; per-constraint arrays m*n; any may be NULL):
@@ -474,7 +600,14 @@ int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, i
     int8_t *in_d = (int8_t *)malloc((size_t)n);
     int8_t *in_p = (int8_t *)malloc((size_t)n);
     int64_t *plist = (int64_t *)malloc((size_t)n * sizeof(int64_t));
-    if (!cos || !sorted || !slo || !shi || !tlo || !thi || !in_d || !in_p || !plist) { rc = ORC_ENOMEM; goto done; }
+    int8_t *c_d = (int8_t *)malloc((size_t)n);     /* certainly in the candidate set C */
+    int8_t *c_p = (int8_t *)malloc((size_t)n);     /* possibly in C */
+    int64_t *cset = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t n_cset = 0, n_cp = 0;
+    if (!cos || !sorted || !slo || !shi || !tlo || !thi || !in_d || !in_p || !plist || !c_d || !c_p || !cset) {
+        rc = ORC_ENOMEM;
+        goto done;
+    }
 
     if ((rc = orc_cosines(s, u0, cos)) != ORC_OK) goto done;
     memcpy(sorted, cos, (size_t)n * sizeof(double));
@@ -487,7 +620,12 @@ int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, i
         shi[j] = cf / (p->mu + (double)rlo);
         if (rank_lo0) rank_lo0[j] = rlo;
         if (rank_hi0) rank_hi0[j] = rhi;
+        c_d[j] = rhi <= p->k_closest;
+        c_p[j] = rlo <= p->k_closest;
+        if (c_d[j]) cset[n_cset++] = j;
+        n_cp += c_p[j];
     }
+    const int cset_certain = n_cset == n_cp;
     for (int32_t i = 0; i < m; ++i) {
         if ((rc = orc_cosines(s, u_c + (int64_t)i * s->dim, cos)) != ORC_OK) goto done;
         memcpy(sorted, cos, (size_t)n * sizeof(double));
@@ -504,12 +642,23 @@ int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, i
             if (in_p[a]) plist[n_p++] = a;
         for (int64_t e = 0; e < n; ++e) {
             double lo = 0.0, hi = 0.0;
+            const int ranked = preds[i] == ORC_CLOSEST || preds[i] == ORC_FARTHEST;
             for (int64_t l = 0; l < n_p; ++l) {
                 int64_t a = plist[l];
                 if (a == e) continue;
-                double r = orc_relation(s, p, preds[i], e, a);
-                if (r > hi) hi = r;
-                if (in_d[a] && r > lo) lo = r;
+                double r_lo, r_hi;
+                if (!ranked) {
+                    r_lo = r_hi = orc_relation(s, p, preds[i], e, a);
+                } else if (!c_p[e]) {
+                    r_lo = r_hi = 0.0;
+                } else if (!cset_certain || !c_d[e]) {
+                    r_lo = 0.0;
+                    r_hi = 1.0;
+                } else {
+                    rank_relation_bounds(s, preds[i], e, a, cset, n_cset, 1e-5, &r_lo, &r_hi);
+                }
+                if (r_hi > hi) hi = r_hi;
+                if (in_d[a] && r_lo > lo) lo = r_lo;
             }
             tlo[(int64_t)i * n + e] = lo;
             thi[(int64_t)i * n + e] = hi;
@@ -528,6 +677,7 @@ int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, i
     if (t_hi_out) memcpy(t_hi_out, thi, (size_t)m * (size_t)n * sizeof(double));
 done:
     free(cos); free(sorted); free(slo); free(shi); free(tlo); free(thi); free(in_d); free(in_p); free(plist);
+    free(c_d); free(c_p); free(cset);
     return rc;
 }
 

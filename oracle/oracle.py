@@ -17,14 +17,15 @@ _SRC = os.path.join(_HERE, "farm_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
-ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR = range(5)
+ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND, CLOSEST, FARTHEST = range(11)
 
 
 @dataclasses.dataclass
 class OracleParams:
     """The method's constants (App. D.2): RRF offset mu = 5, blend weight
-    w = 0.5, class-mismatch factor 0.3, Near width 0.5 m; tau_v, tau_h and
-    z_min are not given by the paper (readings)."""
+    w = 0.5, class-mismatch factor 0.3, Near width 0.5 m, NextTo width 1.0 m;
+    tau_v, tau_h, z_min, the On gate and band widths, tau_d and the size of
+    the Closest/Farthest candidate set are not given by the paper (readings)."""
     mu: float = 5.0
     w: float = 0.5
     class_mis: float = 0.3
@@ -33,12 +34,19 @@ class OracleParams:
     tau_h: float = 0.10
     z_min: float = 0.05
     k_anchor: int = 16
+    sigma_next: float = 1.0
+    on_gate: float = 0.10
+    on_band: float = 0.10
+    tau_d: float = 0.25
+    k_closest: int = 16
 
 
 class _Params(C.Structure):
     _fields_ = [("mu", C.c_double), ("w", C.c_double), ("class_mis", C.c_double),
                 ("sigma_near", C.c_double), ("tau_v", C.c_double), ("tau_h", C.c_double),
-                ("z_min", C.c_double), ("k_anchor", C.c_int64)]
+                ("z_min", C.c_double), ("k_anchor", C.c_int64), ("sigma_next", C.c_double),
+                ("on_gate", C.c_double), ("on_band", C.c_double), ("tau_d", C.c_double),
+                ("k_closest", C.c_int64)]
 
 
 class _Scene(C.Structure):
@@ -79,6 +87,8 @@ def load():
         lib.orc_sigmoid.argtypes = [C.c_double]
         lib.orc_relation.restype = C.c_double
         lib.orc_relation.argtypes = [P, P, C.c_int32, C.c_int64, C.c_int64]
+        lib.orc_relation_in.restype = C.c_double
+        lib.orc_relation_in.argtypes = [P, P, C.c_int32, C.c_int64, C.c_int64, P, C.c_int64]
         lib.orc_cosines.restype = C.c_int
         lib.orc_cosines.argtypes = [P, P, P]
         lib.orc_ranks.restype = C.c_int
@@ -119,7 +129,8 @@ class _SceneRef:
 
 def _params(p: OracleParams | None):
     p = p or OracleParams()
-    return _Params(p.mu, p.w, p.class_mis, p.sigma_near, p.tau_v, p.tau_h, p.z_min, p.k_anchor)
+    return _Params(p.mu, p.w, p.class_mis, p.sigma_near, p.tau_v, p.tau_h, p.z_min, p.k_anchor,
+                   p.sigma_next, p.on_gate, p.on_band, p.tau_d, p.k_closest)
 
 
 def _check(rc, what):
@@ -138,6 +149,14 @@ def sigmoid(x: float) -> float:
 def relation(scene, pred: int, e: int, a: int, params: OracleParams | None = None) -> float:
     sr, pp = _SceneRef(scene), _params(params)
     return float(load().orc_relation(C.byref(sr.c), C.byref(pp), int(pred), int(e), int(a)))
+
+
+def relation_in(scene, pred: int, e: int, a: int, cand_set, params: OracleParams | None = None) -> float:
+    """r_rho(e, a) with the Closest/Farthest candidate set given explicitly."""
+    sr, pp = _SceneRef(scene), _params(params)
+    cs = np.ascontiguousarray(cand_set, dtype=np.int64)
+    return float(load().orc_relation_in(C.byref(sr.c), C.byref(pp), int(pred), int(e), int(a),
+                                        _ptr(cs if cs.size else np.zeros(1, np.int64)), int(cs.size)))
 
 
 def cosines(scene, u) -> np.ndarray:

@@ -28,7 +28,8 @@ import numpy as np
 
 # Predicate codes of the C-ABI (include/farm.h): above, below, left_of,
 # right_of, near.
-N_PRED = 5
+N_PRED = 5          # the predicates of the benchmark workloads (codes 0-4)
+N_PRED_ALL = 11     # with NextTo, On, InFrontOf, Behind, Closest, Farthest (codes 5-10)
 
 
 @dataclasses.dataclass
@@ -171,8 +172,10 @@ def _plant_landmark(rng, centers, e, pred, tree, radius=5.0):
     """Pick a landmark object for constraint `pred` on planted target `e`.
 
     Prefers objects within `radius` metres; among them, for above (0) a lower
-    centre, for below (1) a higher centre, for near (4) one within 1 m; for
-    left/right (2, 3) any neighbour.  Falls back to any other object.
+    centre, for below (1) a higher centre, for near (4) one within 1 m, for
+    next_to (5) one within 2 m, for on (6) a lower centre within 1 m
+    horizontally; for the others any neighbour.  Falls back to any other
+    object.
     `tree` is a KD-tree over the centres (neighbour lookup only).
     """
     n = centers.shape[0]
@@ -188,6 +191,12 @@ def _plant_landmark(rng, centers, e, pred, tree, radius=5.0):
     elif pred == 4:
         d = centers[cand] - centers[e]
         pref = cand[np.einsum("ij,ij->i", d, d) <= 1.0]
+    elif pred == 5:
+        d = centers[cand] - centers[e]
+        pref = cand[np.einsum("ij,ij->i", d, d) <= 4.0]
+    elif pred == 6:
+        d = centers[cand, :2] - centers[e, :2]
+        pref = cand[(np.einsum("ij,ij->i", d, d) <= 1.0) & (centers[cand, 2] < centers[e, 2])]
     else:
         pref = cand
     pool = pref if pref.size else cand
@@ -196,14 +205,15 @@ def _plant_landmark(rng, centers, e, pred, tree, radius=5.0):
 
 def make_queries(seed: int, scene: Scene, n_q: int, m_choices=(2,),
                  distractor_classes: int = 0, distractor_target_frac: float = 0.0,
-                 scene_id: int = 0, with_class: bool = True) -> QueryBatch:
+                 scene_id: int = 0, with_class: bool = True, preds=None) -> QueryBatch:
     """Relational queries with a planted target and planted landmarks.
 
     Each query plants a target object e*; its target embedding is the
     centroid of e*'s class plus the scene's descriptor noise (not
     renormalised), and its target class is e*'s class (or -1 when
     `with_class` is False).  The number of constraints is drawn uniformly from
-    `m_choices`; each constraint draws a predicate uniformly from the five and
+    `m_choices`; each constraint draws a predicate uniformly from the five of
+    the benchmark workloads (or from `preds`, a list of predicate codes) and
     plants a landmark near e* (see `_plant_landmark`); the landmark embedding
     is its class centroid plus noise.
     """
@@ -229,7 +239,8 @@ def make_queries(seed: int, scene: Scene, n_q: int, m_choices=(2,),
     c_off = np.zeros(n_q + 1, np.int32)
     c_off[1:] = np.cumsum(ms)
     n_c = int(c_off[-1])
-    preds = rng.integers(0, N_PRED, size=n_c)
+    pred_set = preds
+    preds = rng.integers(0, N_PRED, size=n_c) if pred_set is None else rng.choice(np.asarray(pred_set), size=n_c)
     lms = np.zeros(n_c, np.int64)
     from scipy.spatial import cKDTree
     tree = cKDTree(centers)

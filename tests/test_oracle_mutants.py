@@ -1,8 +1,8 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case plants one mistake in a copy of oracle/farm_oracle.c (on the CPU),
-compiles it, and runs the pin suite against it in a subprocess: the suite must
-fail.  A pin set that passes a planted mistake is not pinning that part.
+compiles it, and runs the pin suites (test_oracle_pins.py,
+test_oracle_pins_more.py) against it in a subprocess: they must fail.  A pin set that passes a planted mistake is not pinning that part.
 """
 import os
 import subprocess
@@ -25,8 +25,18 @@ MUTANTS = {
                         "ssem[j] = class_factor(s, p, c_t, j) / (p->mu + (double)rank[j] - 1.0);"),
     "class_factor_inverted": ("return (c_t >= 0 && s->cls[j] != c_t) ? p->class_mis : 1.0;",
                               "return (c_t >= 0 && s->cls[j] == c_t) ? p->class_mis : 1.0;"),
-    "landmark_may_be_target": ("                if (a == e) continue;\n                double r = orc_relation(s, p, preds[i], e, a);\n                if (arg < 0",
-                               "                double r = orc_relation(s, p, preds[i], e, a);\n                if (arg < 0"),
+    "next_to_width": ("exp(-dist2(s, e, a) / (2.0 * p->sigma_next * p->sigma_next))",
+                      "exp(-dist2(s, e, a) / (2.0 * p->sigma_near * p->sigma_near))"),
+    "on_gap_from_centres": ("double gap = (center(s, 2, e) - 0.5 * box_size(s, 2, e)) - (center(s, 2, a) + 0.5 * box_size(s, 2, a));",
+                            "double gap = center(s, 2, e) - center(s, 2, a);"),
+    "front_depth_sign": ("acc += orc_sigmoid(sign * (Za - Ze) / p->tau_d);",
+                         "acc += orc_sigmoid(sign * (Ze - Za) / p->tau_d);"),
+    "closest_tie_reversed": ("if (dj < de || (dj == de && j < e)) closer += 1;",
+                             "if (dj < de || (dj == de && j > e)) closer += 1;"),
+    "farthest_counts_anchor": ("        if (j == a) continue;\n        members += 1;\n        double dj",
+                               "        members += 1;\n        double dj"),
+    "landmark_may_be_target": ("                if (a == e) continue;\n                double r = orc_relation_in(s, p, preds[i], e, a, cset, n_cset);\n                if (arg < 0",
+                               "                double r = orc_relation_in(s, p, preds[i], e, a, cset, n_cset);\n                if (arg < 0"),
     "product_not_geometric_mean": ("gbar = zero ? 0.0 : exp(lsum / (double)m);", "gbar = zero ? 0.0 : exp(lsum);"),
     "full_product_not_blend": ("return s_sem * ((1.0 - p->w) + p->w * gbar);", "return s_sem * gbar;"),
 }
@@ -44,6 +54,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                    check=True)
     env = dict(os.environ, FARM_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_pins_more.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins pass with mutant {name}:\n{r.stdout[-2000:]}"
