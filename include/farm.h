@@ -58,7 +58,16 @@ typedef enum {
     FARM_BELOW = 1,     /* sig((z_a - z_e) / tau_v) */
     FARM_LEFT_OF = 2,   /* mean over the candidate's stored views of sig((u_a - u_e) / tau_h) */
     FARM_RIGHT_OF = 3,  /* mean over the candidate's stored views of sig((u_e - u_a) / tau_h) */
-    FARM_NEAR = 4       /* exp(-|p_e - p_a|^2 / (2 sigma_near^2)) */
+    FARM_NEAR = 4,      /* exp(-|p_e - p_a|^2 / (2 sigma_near^2)) */
+    FARM_NEXT_TO = 5,   /* exp(-|p_e - p_a|^2 / (2 sigma_next^2)) */
+    FARM_ON = 6,        /* sig((rho_a - d_xy) / on_gate) * exp(-g^2 / (2 on_band^2)): rho_a half the
+                           landmark's larger horizontal size, d_xy the horizontal centre distance,
+                           g = e's bottom - a's top */
+    FARM_IN_FRONT_OF = 7, /* mean over the candidate's stored views of sig((Z_a - Z_e) / tau_d) */
+    FARM_BEHIND = 8,    /* mean over the candidate's stored views of sig((Z_e - Z_a) / tau_d) */
+    FARM_CLOSEST = 9,   /* 1 / rank_d: e's rank by distance to a among the query's k_closest
+                           best target candidates other than a (0 for e outside them) */
+    FARM_FARTHEST = 10  /* 1 / (|C| - rank_d + 1) over the same set C */
 } farm_pred;
 
 /* Arithmetic of the descriptor-similarity stage (App. D.2 step 3). */
@@ -94,6 +103,10 @@ typedef enum {
  * (four fewer significant bits); farm_default_params sets 2e-3, about thirty
  * standard deviations of the BF16 stage's cosine error on unit descriptors
  * of length 1152.
+ * sigma_next = 1.0 m (NextTo) is given in App. D.2 step 4; on_gate, on_band
+ * (m), tau_d (m) and k_closest (the candidate set of Closest / Farthest: the
+ * query's k_closest objects of smallest target rank; 1 .. the rank bound R)
+ * are not; farm_default_params sets 0.10, 0.10, 0.25 and 16.
  */
 typedef struct {
     float mu;
@@ -107,6 +120,11 @@ typedef struct {
     int32_t k_max;
     int32_t rescore;
     float rescore_band;
+    float sigma_next;
+    float on_gate;
+    float on_band;
+    float tau_d;
+    int32_t k_closest;
 } farm_params;
 
 /* Fills *p with the defaults above (k_max = 10, rescore = 256, rescore_band = 2e-3). */
@@ -161,9 +179,10 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
  *   precision  a farm_precision value
  *   flags      FARM_PTR_DEVICE: tgt_emb and c_emb are device pointers (the
  *              other arrays are always host memory).
- *              FARM_GRAPH: the batch's device work (staging copies, row
- *              normalisation, similarity, rank selection, rescore, relations
- *              and composite) runs as a CUDA graph.  Graphs are cached by the
+ *              FARM_GRAPH: the batch's kernels (row normalisation,
+ *              similarity, rank selection, rescore, relations and composite)
+ *              run as a CUDA graph; the copies of the batch's metadata and
+ *              piece tables are issued on the stream before each replay.  Graphs are cached by the
  *              batch's shape: precision, n_q, n_c, and the scenes in order of
  *              first use with each one's query and constraint counts, and, for
  *              device embeddings, their addresses.  A batch of a cached shape

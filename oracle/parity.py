@@ -17,7 +17,9 @@ may take under any admissible order (oracle.query_bounds), and the check is:
     object left out whose lower bound beats the k-th returned score;
   * breakdown: each returned per-constraint score t_i lies in [t_lo, t_hi];
     the returned anchor is an admissible landmark candidate, not the target,
-    and its relation score (evaluated by the oracle) equals t_i.
+    and its relation score (evaluated by the oracle) equals t_i -- for
+    Closest / Farthest, evaluated within the query's candidate set (skipped
+    when that set is itself tie-ambiguous), up to near-equal distances.
 """
 from __future__ import annotations
 
@@ -49,6 +51,24 @@ class ParityReport:
         return s
 
 
+def _rank_score_range(scene, pred, e, a, cset, dtol=1e-5):
+    """Closest / farthest of e to anchor a within the candidate set `cset`:
+    the range of scores when squared distances within a relative dtol may be
+    ordered either way (e outside the set scores 0)."""
+    if e not in cset or e == a:
+        return 0.0, 0.0
+    c = np.asarray(scene.box[:3], np.float64).T
+    d = lambda j: float(np.sum((c[j] - c[a]) ** 2))   # noqa: E731
+    de = d(e)
+    members = [j for j in cset if j != a]
+    c_lo = sum(1 for j in members if j != e and d(j) < de * (1 - dtol))
+    c_hi = sum(1 for j in members if j != e and d(j) <= de * (1 + dtol))
+    r_lo, r_hi = 1 + c_lo, 1 + c_hi
+    if pred == O.CLOSEST:
+        return 1.0 / r_hi, 1.0 / r_lo
+    return 1.0 / (len(members) - r_lo + 1), 1.0 / (len(members) - r_hi + 1)
+
+
 def _check_one(scene, qb, q, k, idx, score, t, anchor, params, tau, rtol, atol_t):
     fails = []
     m0, m1 = int(qb.c_off[q]), int(qb.c_off[q + 1])
@@ -58,6 +78,11 @@ def _check_one(scene, qb, q, k, idx, score, t, anchor, params, tau, rtol, atol_t
     ex = O.query_all(*args, params=params)
     s_lo, s_hi = b["s_lo"], b["s_hi"]
     n = scene.n
+    # the Closest / Farthest candidate set: target ranks 1..k_closest, when
+    # the tie tolerance leaves it unambiguous
+    kc = min(params.k_closest, n)
+    cset_certain = not np.any((b["rank_lo"] <= kc) & (b["rank_hi"] > kc))
+    cset = set(np.flatnonzero(b["rank_hi"] <= kc).tolist()) if cset_certain else None
     idx = np.asarray(idx, np.int64)
     score = np.asarray(score, np.float64)
     if np.any(idx < 0) or np.any(idx >= n) or len(set(idx.tolist())) != k:
@@ -110,7 +135,15 @@ def _check_one(scene, qb, q, k, idx, score, t, anchor, params, tau, rtol, atol_t
                 if av == e or not b["in_p"][i][av]:
                     fails.append(f"q{q} e{e} c{i}: anchor {av} not an admissible landmark")
                     continue
-                rv = O.relation(scene, int(qb.c_pred[m0 + i]), e, av, params)
+                pred = int(qb.c_pred[m0 + i])
+                if pred in (O.CLOSEST, O.FARTHEST):
+                    if cset is None:
+                        continue            # the set itself is ambiguous: the t bounds above decide
+                    rl, rh = _rank_score_range(scene, pred, e, av, cset)
+                    if tv < rl * (1 - rtol) - atol_t or tv > rh * (1 + rtol) + atol_t:
+                        fails.append(f"q{q} e{e} c{i}: anchor {av} scores [{rl:.9g}, {rh:.9g}], reported t {tv:.9g}")
+                    continue
+                rv = O.relation(scene, pred, e, av, params)
                 if abs(rv - tv) > rtol * abs(rv) + atol_t:
                     fails.append(f"q{q} e{e} c{i}: anchor {av} scores {rv:.9g}, reported t {tv:.9g}")
     return fails, exact, rel

@@ -98,6 +98,15 @@ bool params_ok(const farm_params &p, std::string &why)
     }
     if (p.rescore < 1 || p.rescore > farm::kMaxTargetCands) { why = "rescore must lie in [1, 512]"; return false; }
     if (!(p.rescore_band >= 0.f) || !std::isfinite(p.rescore_band)) { why = "rescore_band must be >= 0"; return false; }
+    if (!(p.sigma_next > 0.f && p.on_gate > 0.f && p.on_band > 0.f && p.tau_d > 0.f) ||
+        !std::isfinite(p.sigma_next) || !std::isfinite(p.on_gate) || !std::isfinite(p.on_band) || !std::isfinite(p.tau_d)) {
+        why = "sigma_next, on_gate, on_band, tau_d must be > 0";
+        return false;
+    }
+    if (p.k_closest < 1 || p.k_closest > target_bound(p)) {
+        why = "k_closest must lie in [1, R]: the candidate set of Closest / Farthest lies within the kept ranks";
+        return false;
+    }
     return true;
 }
 
@@ -185,6 +194,7 @@ farm_status check_device_errors(farm_ctx *ctx)
     CK(cudaStreamSynchronize(c.stream));
     c.batch_valid = false;
     if (e & farm::kErrTimeout) return fail(ctx, FARM_ETIMEOUT, "a bounded device-side wait gave up");
+    if (e & farm::kErrPieceTable) return fail(ctx, FARM_ECUDA, "a similarity piece table entry was malformed");
     if (e & farm::kErrBadDesc)
         return fail(ctx, FARM_EINVAL, "a descriptor row has zero or non-finite norm");
     return fail(ctx, FARM_EINVAL, "an embedding row has zero or non-finite norm");
@@ -311,6 +321,11 @@ void farm_default_params(farm_params *p)
     p->k_max = 10;
     p->rescore = 256;
     p->rescore_band = 2e-3f;
+    p->sigma_next = 1.0f;
+    p->on_gate = 0.10f;
+    p->on_band = 0.10f;
+    p->tau_d = 0.25f;
+    p->k_closest = 16;
 }
 
 const char *farm_last_error(farm_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
@@ -473,7 +488,7 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
     }
     if (tmp_desc) cudaFreeAsync(tmp_desc, c.stream);
     if (tmp_views) cudaFreeAsync(tmp_views, c.stream);
-    SceneDev sd{ns.pos, ns.views, ns.cls, n, n_views, 0};
+    SceneDev sd{ns.pos, ns.views, ns.cls, ns.size, n, n_views, 0};
     if ((e = cudaMemcpyAsync(ctx->d_scenes + scene_id, &sd, sizeof(sd), cudaMemcpyHostToDevice, c.stream)) !=
         cudaSuccess)
         return bailmem(e);
@@ -528,7 +543,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         n_c = c_off[n_q];
         if (n_c > 0 && (!c_pred || !c_emb)) return fail(ctx, FARM_EINVAL, "c_pred and c_emb must be non-null");
         for (int64_t i = 0; i < n_c; ++i)
-            if (c_pred[i] < 0 || c_pred[i] > FARM_NEAR)
+            if (c_pred[i] < 0 || c_pred[i] > FARM_FARTHEST)
                 return fail(ctx, FARM_EINVAL, "unknown predicate code " + std::to_string(c_pred[i]));
     }
     c.batch_valid = false;
@@ -894,15 +909,19 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     // staged into library buffers first.
     const float *src_t = dev ? tgt_emb : d_raw;
     const float *src_c = dev ? c_emb : d_raw + (size_t)n_q * dim;
+    // Staging copies, always issued directly on the stream (never inside a
+    // graph): the host refills the pinned buffers for its next batch once the
+    // stage_done event after them has completed.  (Stage marks are taken for
+    // batches run directly only.)
+    const int m0 = graph ? -1 : mark_begin(ctx, 0);
+    CK(cudaMemcpyAsync(d_rowmap, h_rowmap, (size_t)(n_q + n_c) * 4, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(d_perm, h_perm, (size_t)n_q * 4, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(d_meta, h_meta, (size_t)n_q * 8 * 4, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(d_blob, ctx->h_blob, blob_bytes, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaEventRecord(ctx->stage_done, c.stream));
+    if (!dev) CK(copy_inputs(cudaMemcpyHostToDevice));
     auto enqueue = [&]() -> farm_status {
-        // ---- stage 0: inputs and normalisation
-        const int m0 = mark_begin(ctx, 0);
-        CK(cudaMemcpyAsync(d_rowmap, h_rowmap, (size_t)(n_q + n_c) * 4, cudaMemcpyHostToDevice, c.stream));
-        CK(cudaMemcpyAsync(d_perm, h_perm, (size_t)n_q * 4, cudaMemcpyHostToDevice, c.stream));
-        CK(cudaMemcpyAsync(d_meta, h_meta, (size_t)n_q * 8 * 4, cudaMemcpyHostToDevice, c.stream));
-        CK(cudaMemcpyAsync(d_blob, ctx->h_blob, blob_bytes, cudaMemcpyHostToDevice, c.stream));
-        if (!graph) CK(cudaEventRecord(ctx->stage_done, c.stream));
-        if (!graph && !dev) CK(copy_inputs(cudaMemcpyHostToDevice));
+        // ---- stage 0: normalisation (the staging copies above are not part of it)
         LAUNCH(farm::launch_normalize_rows(src_t, d_rowmap, n_q, dim, dim_pad, ops.q32, ops.qhi, ops.qlo, ops.qbf,
                                            c.d_err, farm::kErrBadRow, c.stream));
         if (n_c > 0)
@@ -1024,14 +1043,11 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         const farm_status st = enqueue();
         if (st != FARM_OK) return st;
     } else {
-        if (!dev) CK(copy_inputs(cudaMemcpyHostToDevice));
         // the batch's shape: everything that fixes the launch sequence and its
-        // arguments (the captured copies read the pinned staging buffers at
-        // these addresses; device inputs are read where the caller keeps them)
+        // arguments (device inputs are read where the caller keeps them)
         std::vector<int64_t> key = {precision, n_q, n_c, dim, (int64_t)c.ws_gen, (int64_t)c.scene_gen,
-                                    (int64_t)c.mlp.version, (int64_t)(intptr_t)ctx->h_stage,
-                                    (int64_t)(intptr_t)ctx->h_blob, (int64_t)(intptr_t)src_t,
-                                    (int64_t)(intptr_t)src_c, (int64_t)groups.size()};
+                                    (int64_t)c.mlp.version, (int64_t)(intptr_t)src_t, (int64_t)(intptr_t)src_c,
+                                    (int64_t)groups.size()};
         for (const auto &g : groups) {
             key.push_back(g.sid);
             key.push_back(g.nq);

@@ -34,6 +34,7 @@ constexpr int kViewStride = 8;
 constexpr int kErrBadRow = 1;        // zero or non-finite embedding row
 constexpr int kErrBadDesc = 2;       // zero or non-finite descriptor row
 constexpr int kErrTimeout = 4;       // a bounded wait gave up
+constexpr int kErrPieceTable = 8;    // a similarity piece carried a misaligned tensor-map pointer
 
 struct Scene {
     bool present = false;
@@ -413,6 +414,7 @@ struct SceneDev {
     const float *pos;       // [3, n]
     const float *views;     // [n, n_views, kViewStride]
     const int32_t *cls;     // [n]
+    const float *size;      // [3, n]
     int64_t n;
     int32_t n_views;
     int32_t pad;

@@ -66,19 +66,83 @@ __device__ float viewpoint_lr(const float *__restrict__ vs, int n_views, float a
     return counted ? acc / (float)counted : 0.5f;
 }
 
-__device__ __forceinline__ float relation(int pred, float ex, float ey, float ez, float ax, float ay, float az,
-                                          const float *__restrict__ vs, int n_views, const farm_params &p)
+// Front/behind of landmark position (ax, ay, az) in the staged views of the
+// candidate (sign +1: InFrontOf, -1: Behind): mean over the views in which
+// both lie deeper than z_min, 0.5 when none does.
+__device__ float viewpoint_depth(const float *__restrict__ vs, int n_views, float ax, float ay, float az, float sign,
+                                 const farm_params &p)
+{
+    float acc = 0.f;
+    int counted = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const float4 o = *reinterpret_cast<const float4 *>(vs + v * VREC);      // ox, oy, oz, fx
+        const float4 f = *reinterpret_cast<const float4 *>(vs + v * VREC + 4);  // fy, fz, rx, ry
+        const float Ze = vs[v * VREC + 8];
+        if (!(Ze > p.z_min)) continue;
+        const float dax = ax - o.x, day = ay - o.y, daz = az - o.z;
+        const float Za = dax * o.w + day * f.x + daz * f.y;
+        if (!(Za > p.z_min)) continue;
+        acc += sigm(sign * (Za - Ze) / p.tau_d);
+        ++counted;
+    }
+    return counted ? acc / (float)counted : 0.5f;
+}
+
+// What a relation needs beyond the two objects: the candidate's staged views
+// and the query's Closest / Farthest candidate set (its kc best target
+// candidates, indices and centres).
+struct RelCtx {
+    const float *vs;
+    int n_views;
+    const int32_t *cset_idx;
+    const float *cset_pos;     // [kc][3]
+    int kc;
+};
+
+// r_rho(e, a) (App. D.2 step 4).  ce: e's position in the query's target
+// list (rank - 1), which decides membership of the Closest / Farthest set.
+__device__ __forceinline__ float relation(int pred, int32_t e, int ce, float ex, float ey, float ez, float esz,
+                                          int32_t ai, float ax, float ay, float az, float asx, float asy,
+                                          float asz, const RelCtx &rc, const farm_params &p)
 {
     switch (pred) {
     case FARM_ABOVE: return sigm((ez - az) / p.tau_v);
     case FARM_BELOW: return sigm((az - ez) / p.tau_v);
-    case FARM_NEAR: {
+    case FARM_NEAR:
+    case FARM_NEXT_TO: {
         const float dx = ex - ax, dy = ey - ay, dz = ez - az;
         const float d2 = dx * dx + dy * dy + dz * dz;
-        return expf(-d2 / (2.f * p.sigma_near * p.sigma_near));
+        const float sg = pred == FARM_NEAR ? p.sigma_near : p.sigma_next;
+        return expf(-d2 / (2.f * sg * sg));
     }
-    case FARM_LEFT_OF: return viewpoint_lr(vs, n_views, ax, ay, az, 1.f, p);
-    case FARM_RIGHT_OF: return viewpoint_lr(vs, n_views, ax, ay, az, -1.f, p);
+    case FARM_ON: {
+        const float dx = ex - ax, dy = ey - ay;
+        const float rho = 0.5f * fmaxf(asx, asy);
+        const float gate = sigm((rho - sqrtf(dx * dx + dy * dy)) / p.on_gate);
+        const float gap = (ez - 0.5f * esz) - (az + 0.5f * asz);
+        return gate * expf(-gap * gap / (2.f * p.on_band * p.on_band));
+    }
+    case FARM_LEFT_OF: return viewpoint_lr(rc.vs, rc.n_views, ax, ay, az, 1.f, p);
+    case FARM_RIGHT_OF: return viewpoint_lr(rc.vs, rc.n_views, ax, ay, az, -1.f, p);
+    case FARM_IN_FRONT_OF: return viewpoint_depth(rc.vs, rc.n_views, ax, ay, az, 1.f, p);
+    case FARM_BEHIND: return viewpoint_depth(rc.vs, rc.n_views, ax, ay, az, -1.f, p);
+    case FARM_CLOSEST:
+    case FARM_FARTHEST: {
+        if (ce >= rc.kc) return 0.f;                // e is not in the candidate set
+        const float dx = ex - ax, dy = ey - ay, dz = ez - az;
+        const float de = dx * dx + dy * dy + dz * dz;
+        int members = 0, closer = 0;
+        for (int k = 0; k < rc.kc; ++k) {
+            const int32_t j = rc.cset_idx[k];
+            if (j == ai) continue;
+            ++members;
+            const float jx = rc.cset_pos[3 * k] - ax, jy = rc.cset_pos[3 * k + 1] - ay, jz = rc.cset_pos[3 * k + 2] - az;
+            const float dj = jx * jx + jy * jy + jz * jz;
+            closer += (dj < de || (dj == de && j < e)) ? 1 : 0;
+        }
+        const int rank = 1 + closer;
+        return pred == FARM_CLOSEST ? 1.f / (float)rank : 1.f / (float)(members - rank + 1);
+    }
     default: return 0.f;
     }
 }
@@ -86,18 +150,21 @@ __device__ __forceinline__ float relation(int pred, float ex, float ey, float ez
 constexpr int WARPS = TH / 32;
 
 // Shared-memory layout of one query, sized by the batch's longest target list
-// RM (sorted as PM, the next power of two) and landmark list KM; every section
-// starts on a 16-byte boundary (the view slots are read as float4).
+// RM (sorted as PM, the next power of two), landmark list KM and Closest /
+// Farthest set KC; every section starts on a 16-byte boundary (the view slots
+// are read as float4).
 struct ComposeSmem {
-    size_t best, key, vslot, lm_pos, lm_idx, cand_e, ssem, surv, slot, bytes;
+    size_t best, key, vslot, lm_pos, lm_size, cset_pos, lm_idx, cand_e, ssem, surv, slot, bytes;
     __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
-    __host__ __device__ ComposeSmem(int RM, int PM, int KM)
+    __host__ __device__ ComposeSmem(int RM, int PM, int KM, int KC)
     {
         size_t o = 0;
         best = o;   o = up16(o + (size_t)RM * FARM_MAX_CONSTRAINTS * 8);
         key = o;    o = up16(o + (size_t)PM * 8);
         vslot = o;  o = up16(o + (size_t)WARPS * FARM_MAX_VIEWS * VREC * 4);
         lm_pos = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
+        lm_size = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
+        cset_pos = o; o = up16(o + (size_t)KC * 3 * 4);
         lm_idx = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 4);
         cand_e = o; o = up16(o + (size_t)RM * 4);
         ssem = o;   o = up16(o + (size_t)RM * 4);
@@ -108,15 +175,17 @@ struct ComposeSmem {
 };
 
 __global__ void __launch_bounds__(TH)
-compose_kernel(ComposeArgs a, int32_t PM)
+compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     const int RM = a.stride_t, KM = a.stride_l;
-    const ComposeSmem L(RM, PM, KM);
+    const ComposeSmem L(RM, PM, KM, KC);
     unsigned long long *best = reinterpret_cast<unsigned long long *>(sm + L.best);   // [RM][4]
     uint64_t *key = reinterpret_cast<uint64_t *>(sm + L.key);
     float *vslot = reinterpret_cast<float *>(sm + L.vslot);                           // [WARPS][16][VREC]
     float *lm_pos = reinterpret_cast<float *>(sm + L.lm_pos);                         // [4][KM][3]
+    float *lm_size = reinterpret_cast<float *>(sm + L.lm_size);                       // [4][KM][3]
+    float *cset_pos = reinterpret_cast<float *>(sm + L.cset_pos);                     // [KC][3]
     int32_t *lm_idx = reinterpret_cast<int32_t *>(sm + L.lm_idx);                     // [4][KM]
     int32_t *cand_e = reinterpret_cast<int32_t *>(sm + L.cand_e);
     float *ssem = reinterpret_cast<float *>(sm + L.ssem);
@@ -138,8 +207,11 @@ compose_kernel(ComposeArgs a, int32_t PM)
     const int klm = meta[QM_KLM];
     const SceneDev sd = a.scenes[scene];
     const farm_params p = a.p;
-    bool any_lr = false;
-    for (int i = 0; i < m; ++i) any_lr |= preds[i] == FARM_LEFT_OF || preds[i] == FARM_RIGHT_OF;
+    bool any_view = false;
+    for (int i = 0; i < m; ++i)
+        any_view |= preds[i] == FARM_LEFT_OF || preds[i] == FARM_RIGHT_OF || preds[i] == FARM_IN_FRONT_OF ||
+                    preds[i] == FARM_BEHIND;
+    const int kc = min(min(p.k_closest, R), KC);     // the Closest / Farthest set: target ranks 1..kc
 
     // (an index outside the scene never reaches a memory access: such a
     // landmark is skipped and such a candidate never survives)
@@ -151,6 +223,9 @@ compose_kernel(ComposeArgs a, int32_t PM)
         lm_pos[(i * KM + l) * 3 + 0] = ai >= 0 ? sd.pos[ai] : 0.f;
         lm_pos[(i * KM + l) * 3 + 1] = ai >= 0 ? sd.pos[sd.n + ai] : 0.f;
         lm_pos[(i * KM + l) * 3 + 2] = ai >= 0 ? sd.pos[2 * sd.n + ai] : 0.f;
+        lm_size[(i * KM + l) * 3 + 0] = ai >= 0 ? sd.size[ai] : 0.f;
+        lm_size[(i * KM + l) * 3 + 1] = ai >= 0 ? sd.size[sd.n + ai] : 0.f;
+        lm_size[(i * KM + l) * 3 + 2] = ai >= 0 ? sd.size[2 * sd.n + ai] : 0.f;
     }
     const int32_t *cand = a.tsel_idx + q * a.stride_t;
     for (int c = tid; c < R; c += TH) {
@@ -159,6 +234,11 @@ compose_kernel(ComposeArgs a, int32_t PM)
         cand_e[c] = ok ? e : -1;
         const float cf = (c_t >= 0 && ok && sd.cls[e] != c_t) ? p.class_mis : 1.f;
         ssem[c] = ok ? cf / (p.mu + (float)(c + 1)) : -1.f;
+        if (c < kc) {
+            cset_pos[3 * c + 0] = ok ? sd.pos[e] : 0.f;
+            cset_pos[3 * c + 1] = ok ? sd.pos[sd.n + e] : 0.f;
+            cset_pos[3 * c + 2] = ok ? sd.pos[2 * sd.n + e] : 0.f;
+        }
     }
     if (tid == 0) { s_thr = 0.f; s_ns = 0; }
     __syncthreads();
@@ -189,12 +269,15 @@ compose_kernel(ComposeArgs a, int32_t PM)
     // candidate's views, each lane evaluates (constraint, landmark) pairs, and
     // a max over (r, lower landmark index on ties) keeps the witness
     float *vs = vslot + warp * FARM_MAX_VIEWS * VREC;
+    const RelCtx rc{vs, sd.n_views, cand_e, cset_pos, kc};
     const int per = m * klm;
     for (int pos = warp; pos < ns; pos += WARPS) {
-        const int32_t e = cand_e[surv[pos]];
+        const int ce = surv[pos];
+        const int32_t e = cand_e[ce];
         const float ex = sd.pos[e], ey = sd.pos[sd.n + e], ez = sd.pos[2 * sd.n + e];
+        const float esz = sd.size[2 * sd.n + e];
         if (lane < FARM_MAX_CONSTRAINTS) best[pos * FARM_MAX_CONSTRAINTS + lane] = 0ull;
-        if (any_lr && lane < sd.n_views) {
+        if (any_view && lane < sd.n_views) {
             const float *ve = sd.views + ((int64_t)e * sd.n_views + lane) * kViewStride;
             const float4 o = *reinterpret_cast<const float4 *>(ve);        // ox, oy, oz, fx
             const float4 f = *reinterpret_cast<const float4 *>(ve + 4);    // fy, fz, rx, ry
@@ -212,7 +295,9 @@ compose_kernel(ComposeArgs a, int32_t PM)
             const int32_t ai = lm_idx[i * KM + l];
             if (ai == e || ai < 0) continue;
             const float *ap = lm_pos + (i * KM + l) * 3;
-            const float r = relation(preds[i], ex, ey, ez, ap[0], ap[1], ap[2], vs, sd.n_views, p);
+            const float *as = lm_size + (i * KM + l) * 3;
+            const float r = relation(preds[i], e, ce, ex, ey, ez, esz, ai, ap[0], ap[1], ap[2], as[0], as[1], as[2],
+                                     rc, p);
             const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) |
                                          (unsigned long long)(0xffffffffu - (uint32_t)ai);
             atomicMax(&best[pos * FARM_MAX_CONSTRAINTS + i], k);
@@ -312,13 +397,14 @@ cudaError_t launch_compose(const ComposeArgs &a, cudaStream_t s)
         return cudaErrorInvalidValue;
     int PM = 1;
     while (PM < a.stride_t) PM <<= 1;
-    const ComposeSmem L(a.stride_t, PM, a.stride_l);
+    const int KC = a.p.k_closest < a.stride_t ? a.p.k_closest : a.stride_t;
+    const ComposeSmem L(a.stride_t, PM, a.stride_l, KC);
     if (L.bytes + 64 > 48 * 1024) {     // (plus the kernel's few bytes of static shared memory)
         const cudaError_t e = cudaFuncSetAttribute(compose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)L.bytes);
         if (e != cudaSuccess) return e;
     }
-    compose_kernel<<<(unsigned)a.n_q, TH, L.bytes, s>>>(a, PM);
+    compose_kernel<<<(unsigned)a.n_q, TH, L.bytes, s>>>(a, PM, KC);
     return cudaGetLastError();
 }
 

@@ -388,6 +388,12 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 const int qa = (int)(pc.q_row0 + m0);     // A rows: the piece's rows in the operand arrays
                 const CUtensorMap *bmap0 = GROUPED ? static_cast<const CUtensorMap *>(pc.bmap) : &map_d0;
                 const CUtensorMap *bmap1 = GROUPED ? static_cast<const CUtensorMap *>(pc.bmap) + 1 : &map_d1;
+                if (GROUPED && (reinterpret_cast<uintptr_t>(pc.bmap) & 63u)) {
+                    // a tensor map must be 64-byte aligned: never hand the copy engine anything else
+                    atomicOr(err, kErrPieceTable);
+                    *abort_flag = 1;
+                    break;
+                }
                 for (int kb = 0; kb < k_slices; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1u;

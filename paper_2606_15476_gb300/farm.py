@@ -36,7 +36,9 @@ class FarmParams(C.Structure):
     _fields_ = [("mu", C.c_float), ("w", C.c_float), ("class_mis", C.c_float),
                 ("sigma_near", C.c_float), ("tau_v", C.c_float), ("tau_h", C.c_float),
                 ("z_min", C.c_float), ("k_anchor", C.c_int32), ("k_max", C.c_int32),
-                ("rescore", C.c_int32), ("rescore_band", C.c_float)]
+                ("rescore", C.c_int32), ("rescore_band", C.c_float), ("sigma_next", C.c_float),
+                ("on_gate", C.c_float), ("on_band", C.c_float), ("tau_d", C.c_float),
+                ("k_closest", C.c_int32)]
 
 
 def _load():

@@ -267,11 +267,12 @@ def test_invalid_calls(F, ctx, room):
     bad.scene_of_q[:] = 77                        # unknown scene
     with pytest.raises(F.FarmError):
         run(F, ctx, bad, prec_code(F, DEFAULT))
-    bad = sub.subset(range(4))
-    bad.c_pred[:] = 9                             # unknown predicate
-    if bad.n_c:
-        with pytest.raises(F.FarmError):
-            run(F, ctx, bad, prec_code(F, DEFAULT))
+    for code in (11, -1):                         # unknown predicate codes (0..10 are defined)
+        bad = sub.subset(range(4))
+        bad.c_pred[:] = code
+        if bad.n_c:
+            with pytest.raises(F.FarmError):
+                run(F, ctx, bad, prec_code(F, DEFAULT))
     five = QueryBatch(tgt_emb=sub.tgt_emb[:1], tgt_cls=sub.tgt_cls[:1],
                       c_off=np.array([0, 5], np.int32), c_pred=np.zeros(5, np.int32),
                       c_emb=np.repeat(sub.tgt_emb[:1], 5, axis=0), scene_of_q=np.zeros(1, np.int32))
