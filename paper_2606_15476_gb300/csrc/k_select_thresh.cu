@@ -3,18 +3,24 @@
 // candidates): the R largest entries of a row, in rank order.
 //
 // The similarity kernel's epilogue leaves, per row, the maximum of every
-// group of 32 (8 in small scenes) consecutive objects.  Those values are entries of the row, so
-// the R-th largest of their union, tau, is at most the row's R-th largest
-// value: every entry of rank <= R has a value >= tau.  One pass over the row
-// collects the entries >= tau (the top R, their ties, and the few entries
-// between tau and the R-th value when two of the top R share a group), and a
-// sort of those candidates by (value desc, index asc) gives the exact rank
-// list.  A row whose candidates overflow the buffer is
-// selected exactly by the global-memory radix select instead.
+// group of 32 (8 in small scenes) consecutive objects.  Those values are
+// entries of the row, so the R-th largest of their union, tau, is at most the
+// row's R-th largest value: every entry of rank <= R has a value >= tau, and
+// it lies in a group whose maximum is >= tau.  Only those groups (about R of
+// them) are read: their entries >= tau are the candidates (the top R, their
+// ties, and the few entries between tau and the R-th value when two of the
+// top R share a group), and a sort of the candidates by (value desc, index
+// asc) gives the exact rank list.  A row whose qualifying groups exceed the
+// group list is streamed whole instead; a row whose candidates overflow the
+// buffer is selected exactly by the global-memory radix select.
 //
-// One CTA of 256 threads per row: the union (at most 8,192 values) is staged
-// in shared memory and its R-th largest key found by three radix passes;
-// the row is streamed once from global memory with evict-first loads.
+// Short rows (at most 2,048 objects) with fewer groups than R are staged whole
+// in shared memory; their R-th largest key is found there and the candidates
+// are taken from the staged keys.
+//
+// One CTA of 256 threads per row: the group maxima (at most 8,192 values) are
+// staged in shared memory and their R-th largest key found by three radix
+// passes.
 #include "select_common.cuh"
 
 namespace farm {
@@ -25,7 +31,45 @@ using namespace sel;
 constexpr int TT = 256;
 constexpr int CAP = 2048;          // candidate words per row before the exact fallback
 constexpr int UNION_MAX = 8192;    // union values staged (a prefix of a longer union is still a subset)
+constexpr int GLIST = 2048;        // qualifying groups gathered before the row is streamed whole
 constexpr int UNROLL = 4;          // float4 loads in flight per thread
+
+__device__ __forceinline__ void push_cand(uint64_t *cand, int *s_cnt, float x, int32_t j)
+{
+    const int pos = atomicAdd(s_cnt, 1);
+    if (pos < CAP) cand[pos] = cand_word(order_key(x), j);
+}
+
+// Entries [j0, n) of the row compared against tau (float4 loads from a
+// 16-byte aligned j0, scalar loads for the last n % 4).
+__device__ __forceinline__ void stream_tail(const float *__restrict__ row, int j0, int n, float tau, uint64_t *cand,
+                                            int *s_cnt)
+{
+    const int tid = threadIdx.x;
+    const int n4 = n >> 2, g4 = j0 >> 2;
+    const float4 *row4 = reinterpret_cast<const float4 *>(row);
+    for (int g0 = g4; g0 < n4; g0 += TT * UNROLL) {
+        float4 v[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int g = g0 + u * TT + tid;
+            v[u] = g < n4 ? __ldcs(row4 + g) : make_float4(-1e30f, -1e30f, -1e30f, -1e30f);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int g = g0 + u * TT + tid;
+            if (g >= n4) continue;
+            const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (x[c] >= tau) push_cand(cand, s_cnt, x[c], 4 * g + c);
+        }
+    }
+    for (int j = max(4 * n4, j0) + tid; j < n; j += TT) {
+        const float x = __ldcs(row + j);
+        if (x >= tau) push_cand(cand, s_cnt, x, j);
+    }
+}
 
 __global__ void __launch_bounds__(TT)
 select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops, const Piece *__restrict__ pieces,
@@ -35,11 +79,12 @@ select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops
 {
     extern __shared__ uint32_t ukeys[];
     __shared__ uint64_t cand[CAP];
-    __shared__ uint32_t hist[2048];
+    __shared__ uint32_t hist[2048];     // radix histogram, then the list of qualifying groups
     __shared__ uint32_t wsum[TT / 32];
     __shared__ uint32_t s3[3];
-    __shared__ int s_cnt;
+    __shared__ int s_cnt, s_ng;
     __shared__ int s_misc[TT / 32 + 3];
+    static_assert(GLIST <= 2048, "the group list reuses the histogram");
 
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
@@ -63,52 +108,78 @@ select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops
     }
     const int n = pc.n;
     const float *row = S + pc.s_off + (int64_t)i * pc.ld;
-    const int U = (int)min(group_count(n, pc.gshift), (int64_t)UNION_MAX);
+    const int gshift = pc.gshift;
+    const int64_t n_groups = group_count(n, gshift);
+    const int U = (int)min(n_groups, (int64_t)UNION_MAX);
+    if (tid == 0) { s_cnt = 0; s_ng = 0; }
 
-    // tau: the R-th largest of the group maxima; a row with fewer groups than
-    // R (the planner sends only rows of at most kSelectSortAll objects) takes
-    // every entry as a candidate.  tau = key_value(T) is the group value
-    // itself (never -0), and for non-NaN x, x >= tau holds exactly when
-    // order_key(x) >= T, so the pass below compares floats and builds keys
-    // only for the entries it keeps.
-    float tau = -__int_as_float(0x7f800000);
+    // tau = key_value(T) is an entry of the row (never -0), and for non-NaN x,
+    // x >= tau holds exactly when order_key(x) >= T, so the passes below
+    // compare floats and build keys only for the entries they keep.
     if (U >= R) {
-        const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(n, pc.gshift);
+        // tau: the R-th largest of the group maxima; then the groups whose
+        // maximum reaches it, in any order
+        const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(n, gshift);
         for (int j = tid; j < U; j += TT) ukeys[j] = order_key(__ldg(tp + j));
         __syncthreads();
-        tau = key_value(kth_key<TT>(ukeys, U, R, hist, wsum, s3));
-    }
-    if (tid == 0) s_cnt = 0;
-    __syncthreads();
-    const int n4 = n >> 2;
-    const float4 *row4 = reinterpret_cast<const float4 *>(row);
-    for (int g0 = 0; g0 < n4; g0 += TT * UNROLL) {
-        float4 v[UNROLL];
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            const int g = g0 + u * TT + tid;
-            v[u] = g < n4 ? __ldcs(row4 + g) : make_float4(-1e30f, -1e30f, -1e30f, -1e30f);
-        }
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            const int g = g0 + u * TT + tid;
-            if (g >= n4) continue;
-            const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (x[c] >= tau) {
-                    const int pos = atomicAdd(&s_cnt, 1);
-                    if (pos < CAP) cand[pos] = cand_word(order_key(x[c]), 4 * g + c);
-                }
+        const uint32_t T = kth_key<TT>(ukeys, U, R, hist, wsum, s3);
+        const float tau = key_value(T);
+        for (int j = tid; j < U; j += TT) {
+            if (ukeys[j] >= T) {
+                const int pos = atomicAdd(&s_ng, 1);
+                if (pos < GLIST) hist[pos] = (uint32_t)j;
             }
         }
-    }
-    for (int j = 4 * n4 + tid; j < n; j += TT) {
-        const float x = __ldcs(row + j);
-        if (x >= tau) {
-            const int pos = atomicAdd(&s_cnt, 1);
-            if (pos < CAP) cand[pos] = cand_word(order_key(x), j);
+        __syncthreads();
+        const int ng = s_ng;
+        if (ng <= GLIST) {
+            // the qualifying groups, read as float4 slots (a group of 32 is
+            // eight slots, of 8 two); group starts are 32-byte aligned and a
+            // row holds round_up(n, 32) floats, so a slot never leaves it
+            const int sshift = gshift - 2;
+            const int smask = (1 << sshift) - 1;
+            const int slots = ng << sshift;
+            for (int s0 = 0; s0 < slots; s0 += TT * UNROLL) {
+                float4 v[UNROLL];
+                int j4[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int sl = s0 + u * TT + tid;
+                    j4[u] = sl < slots ? (int)((hist[sl >> sshift] << gshift) + ((sl & smask) << 2)) : n;
+                    v[u] = j4[u] < n ? __ldcs(reinterpret_cast<const float4 *>(row + j4[u]))
+                                     : make_float4(-1e30f, -1e30f, -1e30f, -1e30f);
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    if (j4[u] >= n) continue;
+                    const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (j4[u] + c < n && x[c] >= tau) push_cand(cand, &s_cnt, x[c], j4[u] + c);
+                }
+            }
+            // groups past the staged union (rows of more than 8,192 groups)
+            if (n_groups > U) stream_tail(row, U << gshift, n, tau, cand, &s_cnt);
+        } else {
+            stream_tail(row, 0, n, tau, cand, &s_cnt);
         }
+    } else if (n <= kSelectSortAll) {
+        // a short row: every entry staged, its R-th largest key found in shared memory
+        for (int j = tid; j < n; j += TT) ukeys[j] = order_key(__ldcs(row + j));
+        __syncthreads();
+        const uint32_t T = kth_key<TT>(ukeys, n, R, hist, wsum, s3);
+        for (int j = tid; j < n; j += TT) {
+            const uint32_t k = ukeys[j];
+            if (k >= T) {
+                const int pos = atomicAdd(&s_cnt, 1);
+                if (pos < CAP) cand[pos] = cand_word(k, j);
+            }
+        }
+    } else {
+        // (the planner sends no such row; every entry is a candidate, and the
+        // exact select below stands in when they overflow the buffer)
+        __syncthreads();
+        stream_tail(row, 0, n, -__int_as_float(0x7f800000), cand, &s_cnt);
     }
     __syncthreads();
     const int cnt = s_cnt;
@@ -138,7 +209,9 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
     if (n_pieces < 1 || total_blocks > 0x7fffffff || max_union < 1 || ((uintptr_t)S & 15u) != 0 ||
         ((uintptr_t)tops & 15u) != 0 || !n_fallback)
         return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(max_union < UNION_MAX ? max_union : UNION_MAX) * sizeof(uint32_t);
+    // the staged group maxima, or a whole short row
+    const int32_t staged = max_union < UNION_MAX ? (max_union > kSelectSortAll ? max_union : kSelectSortAll) : UNION_MAX;
+    const size_t smem = (size_t)staged * sizeof(uint32_t);
     static_assert(CAP >= kSelectSortAll, "rows that take every entry fit the candidate buffer");
     cudaError_t e = cudaFuncSetAttribute(select_thresh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
