@@ -5,9 +5,9 @@ CPU-baseline leg import this package.  The product path (the CUDA library and
 its binding) never does.
 """
 from .oracle import (ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND,
-                     CLOSEST, FARTHEST, OracleParams, build, load, cosines, ranks, relation,
+                     CLOSEST, FARTHEST, NEAR_H, INSIDE, OracleParams, build, load, cosines, ranks, relation,
                      relation_in, sigmoid, query_all, query_bounds, batch, topk, num_threads)
 
 __all__ = ["ABOVE", "BELOW", "LEFT_OF", "RIGHT_OF", "NEAR", "NEXT_TO", "ON", "IN_FRONT_OF", "BEHIND",
-           "CLOSEST", "FARTHEST", "OracleParams", "build", "load", "cosines", "ranks", "relation",
+           "CLOSEST", "FARTHEST", "NEAR_H", "INSIDE", "OracleParams", "build", "load", "cosines", "ranks", "relation",
            "relation_in", "sigmoid", "query_all", "query_bounds", "batch", "topk", "num_threads"]

@@ -57,6 +57,21 @@
  *       closest = 1 / rank_d, farthest = 1 / (|C \ {a}| - rank_d + 1)
  *       (score = 1/(|rank - r*| + 1) with r* = 1 or |C \ {a}|); 0 when e is
  *       not in C.
+ *       near_h: the Hellinger form of Near (Sec. 2.3): each object is the
+ *       Gaussian whose mean is its box centre and whose covariance is the
+ *       covariance of the uniform distribution over its box,
+ *       diag(s_x^2, s_y^2, s_z^2) / 12; with the Bhattacharyya coefficient
+ *       BC = integral of sqrt(N_e N_a), the Hellinger distance is
+ *       H = sqrt(1 - BC) and near_h(e,a) = 1 - H.  For diagonal Gaussians
+ *       BC = prod_k sqrt(2 sd_ek sd_ak / (sd_ek^2 + sd_ak^2))
+ *            * exp(-sum_k dp_k^2 / (4 (sd_ek^2 + sd_ak^2)))
+ *       with sd the per-axis standard deviations and dp the centre offset
+ *       (an axis on which both objects have zero extent contributes 1 when
+ *       their centres agree on it, else 0).
+ *       inside(e,a): the containment test of App. D.2 step 4 as the fraction
+ *       of e's box volume that lies in a's box, the product over the three
+ *       axes of |[e] cap [a]|_k / s_ek (an axis of zero extent contributes 1
+ *       when e's coordinate lies in a's interval, else 0).
  *  6. t_i(e) = max_{a in L_i, a != e} r_rho_i(e, a), 0 without a witness; the
  *     bound anchor is the argmax (lower object index on ties).
  *  7. gbar = (prod_i t_i)^(1/m) (0 if some t_i = 0, 1 if m = 0);
@@ -64,8 +79,8 @@
  *  8. TopK by s descending, lower object index first on ties.
  *
  * Readings where the paper is silent (the same list is kept with the design
- * notes): one retrieval channel; Gaussian Near (App. D.2) rather than the
- * Hellinger wording of Sec. 2.3; box centres stand in for Gaussian means and
+ * notes): one retrieval channel; Near is the Gaussian of App. D.2, and the
+ * Hellinger wording of Sec. 2.3 is the separate predicate near_h; box centres stand in for Gaussian means and
  * mask centroids; mean over views; the constants tau_v, tau_h, z_min are
  * parameters; a landmark may not be the target itself; ties go to the lower
  * object index.
@@ -89,6 +104,8 @@
 #define ORC_BEHIND 8
 #define ORC_CLOSEST 9
 #define ORC_FARTHEST 10
+#define ORC_NEAR_H 11
+#define ORC_INSIDE 12
 
 #define ORC_OK 0
 #define ORC_EINVAL -1
@@ -193,6 +210,48 @@ static double dist2(const orc_scene *s, int64_t i, int64_t j)
     return dx * dx + dy * dy + dz * dz;
 }
 
+/* Hellinger form of Near (step 5): 1 - H(N_e, N_a) with box-moment Gaussians.
+ * With per-axis variances s^2 / 12 the factor 2 sd_e sd_a / (sd_e^2 + sd_a^2)
+ * is 2 |s_e| |s_a| / (s_e^2 + s_a^2) and the exponent d^2 / (4 (sd_e^2 + sd_a^2))
+ * is 3 d^2 / (s_e^2 + s_a^2). */
+static double near_hellinger(const orc_scene *s, int64_t e, int64_t a)
+{
+    double bc = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        double se = fabs(box_size(s, k, e)), sa = fabs(box_size(s, k, a));
+        double d = center(s, k, e) - center(s, k, a);
+        double q = se * se + sa * sa;
+        if (q == 0.0) {
+            if (d != 0.0) bc = 0.0;
+            continue;
+        }
+        bc *= sqrt(2.0 * se * sa / q) * exp(-3.0 * d * d / q);
+    }
+    double h2 = 1.0 - bc;
+    if (h2 < 0.0) h2 = 0.0;
+    return 1.0 - sqrt(h2);
+}
+
+/* Inside (step 5): the fraction of e's box volume inside a's box. */
+static double inside_fraction(const orc_scene *s, int64_t e, int64_t a)
+{
+    double frac = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        double he = 0.5 * fabs(box_size(s, k, e)), ha = 0.5 * fabs(box_size(s, k, a));
+        double ce = center(s, k, e), ca = center(s, k, a);
+        if (he == 0.0) {
+            if (!(fabs(ce - ca) <= ha)) return 0.0;
+            continue;
+        }
+        double lo = ce - he > ca - ha ? ce - he : ca - ha;
+        double hi = ce + he < ca + ha ? ce + he : ca + ha;
+        double ov = hi - lo;
+        if (!(ov > 0.0)) return 0.0;
+        frac *= ov / (2.0 * he);
+    }
+    return frac;
+}
+
 /* Closest / farthest (step 5): rank of e by distance to a within the set
  * `set` (n_set objects; e and a may or may not be members). */
 static double rank_relation(const orc_scene *s, int32_t pred, int64_t e, int64_t a,
@@ -240,6 +299,10 @@ double orc_relation_in(const orc_scene *s, const orc_params *p, int32_t pred, in
     case ORC_CLOSEST:
     case ORC_FARTHEST:
         return rank_relation(s, pred, e, a, set, n_set);
+    case ORC_NEAR_H:
+        return near_hellinger(s, e, a);
+    case ORC_INSIDE:
+        return inside_fraction(s, e, a);
     case ORC_ABOVE:
         return orc_sigmoid(dz / p->tau_v);
     case ORC_BELOW:

@@ -17,7 +17,8 @@ _SRC = os.path.join(_HERE, "farm_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
-ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND, CLOSEST, FARTHEST = range(11)
+(ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND, CLOSEST, FARTHEST, NEAR_H,
+ INSIDE) = range(13)
 
 
 @dataclasses.dataclass

@@ -38,6 +38,11 @@ MUTANTS = {
     "landmark_may_be_target": ("                if (a == e) continue;\n                double r = orc_relation_in(s, p, preds[i], e, a, cset, n_cset);\n                if (arg < 0",
                                "                double r = orc_relation_in(s, p, preds[i], e, a, cset, n_cset);\n                if (arg < 0"),
     "product_not_geometric_mean": ("gbar = zero ? 0.0 : exp(lsum / (double)m);", "gbar = zero ? 0.0 : exp(lsum);"),
+    "hellinger_variance_not_box_moment": ("bc *= sqrt(2.0 * se * sa / q) * exp(-3.0 * d * d / q);",
+                                          "bc *= sqrt(2.0 * se * sa / q) * exp(-d * d / q);"),
+    "hellinger_det_factor_dropped": ("bc *= sqrt(2.0 * se * sa / q) * exp(-3.0 * d * d / q);",
+                                     "bc *= exp(-3.0 * d * d / q);"),
+    "inside_divides_by_anchor": ("frac *= ov / (2.0 * he);", "frac *= ov / (2.0 * ha);"),
     "full_product_not_blend": ("return s_sem * ((1.0 - p->w) + p->w * gbar);", "return s_sem * gbar;"),
 }
 

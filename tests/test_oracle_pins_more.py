@@ -213,3 +213,117 @@ def test_bounds_collapse_at_zero_tolerance_and_contain_the_value(pred):
         b = oracle.query_bounds(s, qb.tgt_emb[q], int(qb.tgt_cls[q]), preds, u_c, tau=2e-5)
         assert np.all(b["s_lo"] <= ex["s"] * (1 + 1e-12)) and np.all(ex["s"] <= b["s_hi"] * (1 + 1e-12))
     del rng
+
+
+# --- Near, Hellinger form (Sec. 2.3) -------------------------------------------
+
+def _bc_by_quadrature(c0, s0, c1, s1):
+    """Bhattacharyya coefficient of the two box-moment Gaussians, integrated
+    numerically axis by axis (the densities factorise over the axes)."""
+    from scipy import integrate
+    bc = 1.0
+    for k in range(3):
+        v0, v1 = s0[k] ** 2 / 12.0, s1[k] ** 2 / 12.0
+        g0 = lambda x, m=c0[k], v=v0: math.exp(-(x - m) ** 2 / (2 * v)) / math.sqrt(2 * math.pi * v)  # noqa: E731
+        g1 = lambda x, m=c1[k], v=v1: math.exp(-(x - m) ** 2 / (2 * v)) / math.sqrt(2 * math.pi * v)  # noqa: E731
+        lo = min(c0[k], c1[k]) - 12 * max(s0[k], s1[k])
+        hi = max(c0[k], c1[k]) + 12 * max(s0[k], s1[k])
+        val, _ = integrate.quad(lambda x: math.sqrt(g0(x) * g1(x)), lo, hi, points=[c0[k], c1[k]],
+                                limit=200, epsabs=1e-13, epsrel=1e-11)
+        bc *= val
+    return bc
+
+
+def test_near_h_matches_the_integral_of_the_densities():
+    from oracle import NEAR_H
+    pytest.importorskip("scipy")
+    rng = np.random.default_rng(7)
+    for _ in range(12):
+        c0, c1 = rng.uniform(0, 2, 3), rng.uniform(0, 2, 3)
+        s0, s1 = rng.lognormal(-1, 0.5, 3), rng.lognormal(-1, 0.5, 3)
+        sc = boxes([c0, c1], [s0, s1])
+        # the scene stores float32 geometry: integrate the stored values
+        bc = _bc_by_quadrature(sc.box[:3, 0].astype(np.float64), sc.box[3:, 0].astype(np.float64),
+                               sc.box[:3, 1].astype(np.float64), sc.box[3:, 1].astype(np.float64))
+        want = 1.0 - math.sqrt(max(0.0, 1.0 - bc))
+        assert oracle.relation(sc, NEAR_H, 0, 1) == pytest.approx(want, abs=1e-7)
+
+
+def test_near_h_identities():
+    from oracle import NEAR_H
+    # identical Gaussians: H = 0
+    same = boxes([[1.0, 2.0, 0.5], [1.0, 2.0, 0.5]], [[0.4, 0.3, 0.8]] * 2)
+    assert oracle.relation(same, NEAR_H, 0, 1) == 1.0
+    # equal boxes offset by d along x: BC = exp(-d^2 / (8 var)), var = s^2 / 12
+    s, d = 0.6, 0.25
+    sc = boxes([[0.0, 0.0, 0.0], [d, 0.0, 0.0]], [[s, s, s]] * 2)
+    bc = math.exp(-d * d / (8.0 * s * s / 12.0))
+    assert oracle.relation(sc, NEAR_H, 0, 1) == pytest.approx(1.0 - math.sqrt(1.0 - bc), abs=1e-7)
+    # concentric boxes differing in one size only: BC = sqrt(2 s0 s1 / (s0^2 + s1^2))
+    sc = boxes([[0.0, 0.0, 0.0], [0.0, 0.0, 0.0]], [[0.5, 0.5, 0.5], [0.5, 0.5, 2.0]])
+    bc = math.sqrt(2 * 0.5 * 2.0 / (0.25 + 4.0))
+    assert oracle.relation(sc, NEAR_H, 0, 1) == pytest.approx(1.0 - math.sqrt(1.0 - bc), abs=1e-7)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        c = rng.uniform(0, 3, (2, 3))
+        sz = rng.lognormal(-1, 0.5, (2, 3))
+        sc = boxes(c, sz)
+        r01, r10 = oracle.relation(sc, NEAR_H, 0, 1), oracle.relation(sc, NEAR_H, 1, 0)
+        assert r01 == r10                       # symmetric, bit for bit
+        assert 0.0 <= r01 <= 1.0
+    # moving one box away never raises the score
+    vals = [oracle.relation(boxes([[0, 0, 0], [x, 0.2, 0]], [[0.4, 0.4, 0.4], [0.5, 0.3, 0.6]]), NEAR_H, 0, 1)
+            for x in np.linspace(0.0, 3.0, 31)]
+    assert all(a >= b for a, b in zip(vals, vals[1:]))
+
+
+def test_near_h_degenerate_axes():
+    from oracle import NEAR_H
+    # two flat boxes (zero height) at the same height: that axis contributes 1
+    flat = boxes([[0.0, 0.0, 1.0], [0.3, 0.0, 1.0]], [[0.5, 0.5, 0.0], [0.5, 0.5, 0.0]])
+    bc = math.exp(-0.09 / (8.0 * 0.25 / 12.0))
+    assert oracle.relation(flat, NEAR_H, 0, 1) == pytest.approx(1.0 - math.sqrt(1.0 - bc), abs=1e-7)
+    # ... at different heights: BC = 0
+    apart = boxes([[0.0, 0.0, 1.0], [0.0, 0.0, 1.5]], [[0.5, 0.5, 0.0], [0.5, 0.5, 0.0]])
+    assert oracle.relation(apart, NEAR_H, 0, 1) == 0.0
+    # zero extent against positive extent on one axis: BC = 0
+    mixed = boxes([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0]], [[0.5, 0.5, 0.0], [0.5, 0.5, 0.4]])
+    assert oracle.relation(mixed, NEAR_H, 0, 1) == 0.0
+
+
+# --- Inside (App. D.2 step 4, containment) ---------------------------------------
+
+def test_inside_closed_forms():
+    from oracle import INSIDE
+    big = [2.0, 2.0, 2.0]
+    # fully inside, touching the walls, fully outside
+    assert oracle.relation(boxes([[0.1, -0.2, 0.3], [0, 0, 0]], [[0.5, 0.5, 0.5], big]), INSIDE, 0, 1) == 1.0
+    assert oracle.relation(boxes([[0.75, 0, 0], [0, 0, 0]], [[0.5, 0.5, 0.5], big]), INSIDE, 0, 1) == 1.0
+    assert oracle.relation(boxes([[3.0, 0, 0], [0, 0, 0]], [[0.5, 0.5, 0.5], big]), INSIDE, 0, 1) == 0.0
+    # half out along x, a quarter out along y: 0.5 * 0.75
+    sc = boxes([[1.0, 0.875, 0.0], [0, 0, 0]], [[0.5, 0.5, 0.5], big])
+    assert oracle.relation(sc, INSIDE, 0, 1) == pytest.approx(0.5 * 0.75, abs=1e-7)
+    # not symmetric: the big box is mostly outside the small one
+    sc = boxes([[0, 0, 0], [0, 0, 0]], [big, [0.5, 0.5, 0.5]])
+    assert oracle.relation(sc, INSIDE, 0, 1) == pytest.approx(0.25 ** 3, abs=1e-9)
+    # a point (zero size) inside / outside
+    assert oracle.relation(boxes([[0.2, 0.2, 0.2], [0, 0, 0]], [[0, 0, 0], big]), INSIDE, 0, 1) == 1.0
+    assert oracle.relation(boxes([[1.2, 0.2, 0.2], [0, 0, 0]], [[0, 0, 0], big]), INSIDE, 0, 1) == 0.0
+
+
+def test_inside_is_the_volume_fraction_on_a_grid():
+    from oracle import INSIDE
+    rng = np.random.default_rng(11)
+    g = (np.arange(40) + 0.5) / 40.0 - 0.5          # cell centres of a 40^3 grid over a unit box
+    for _ in range(10):
+        c = rng.uniform(0, 1, (2, 3))
+        sz = rng.uniform(0.2, 1.0, (2, 3))
+        sc = boxes(c, sz)
+        ce, se = sc.box[:3, 0].astype(np.float64), sc.box[3:, 0].astype(np.float64)
+        ca, sa = sc.box[:3, 1].astype(np.float64), sc.box[3:, 1].astype(np.float64)
+        frac = 1.0
+        for k in range(3):
+            x = ce[k] + g * se[k]
+            frac *= np.mean(np.abs(x - ca[k]) <= sa[k] / 2)
+        # the midpoint rule over 40 cells per axis is within 1/40 per axis
+        assert oracle.relation(sc, INSIDE, 0, 1) == pytest.approx(frac, abs=3 * 1.0 / 40 + 1e-9)
