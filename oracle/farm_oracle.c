@@ -744,6 +744,288 @@ done:
     return rc;
 }
 
+/* ------------------------------------------------------------------ */
+/* Several retrieval channels: reciprocal-rank fusion (App. D.2 step 3) */
+/* ------------------------------------------------------------------ */
+
+/*
+ * App. D.2 step 3 ranks the whole pool once per query channel -- four
+ * channels over three embedding spaces, each channel contributing
+ * w / (mu + rank) -- and takes the sum as the fused rank score; landmark
+ * variables are retrieved the same way.  Here:
+ *
+ *   F(j)   = sum_c w_c / (mu + rank_c(j)),  rank_c over the cosines of
+ *            channel c's embedding against every object's descriptor in
+ *            channel c's space (steps 1-2 per channel);
+ *   s_sem  = cf(j) * F(j);
+ *   L_i    = the K_a objects of largest F_i (the landmark's channels),
+ *            lower index first on equal F_i;
+ *   the Closest / Farthest set C = the k_closest objects of largest F.
+ * Steps 5-8 are unchanged.  With one channel of weight 1 this is
+ * orc_query_all.
+ *
+ * spaces[s] = (dim_s, descriptors [n, dim_s]) for s < n_spaces; channel c
+ * reads space ch_space[c] with weight ch_w[c].  u0 holds the target's
+ * channel embeddings end to end (dim of channel 0's space, then channel 1's,
+ * ...); u_c holds, channel after channel, the m landmark embeddings of that
+ * channel ([m, dim] per channel).  Outputs as orc_query_all, with F of the
+ * target in fused_out.
+ */
+typedef struct {
+    int64_t dim;
+    const float *desc;
+} orc_space;
+
+/* Fused score of every object for one variable (target or landmark):
+ * emb holds its n_ch channel embeddings end to end. */
+static int fused_scores(const orc_scene *s, const orc_space *spaces, int32_t n_spaces, const orc_params *p,
+                        int32_t n_ch, const int32_t *ch_space, const double *ch_w, const float *const *emb,
+                        double *F, double *cos, int64_t *rank)
+{
+    for (int64_t j = 0; j < s->n; ++j) F[j] = 0.0;
+    for (int32_t c = 0; c < n_ch; ++c) {
+        if (ch_space[c] < 0 || ch_space[c] >= n_spaces) return ORC_EINVAL;
+        orc_scene sc = *s;
+        sc.dim = spaces[ch_space[c]].dim;
+        sc.desc = spaces[ch_space[c]].desc;
+        int rc = orc_cosines(&sc, emb[c], cos);
+        if (rc != ORC_OK) return rc;
+        if ((rc = orc_ranks(s->n, cos, rank)) != ORC_OK) return rc;
+        for (int64_t j = 0; j < s->n; ++j) F[j] += ch_w[c] / (p->mu + (double)rank[j]);
+    }
+    return ORC_OK;
+}
+
+int orc_query_mc(const orc_scene *s, const orc_space *spaces, int32_t n_spaces, const orc_params *p,
+                 int32_t n_ch, const int32_t *ch_space, const double *ch_w, const float *u0, int32_t c_t,
+                 int32_t m, const int32_t *preds, const float *u_c,
+                 double *fused_out, double *s_sem_out, double *t_out, int64_t *anchor_out, double *s_out)
+{
+    int64_t n = s->n;
+    if (n <= 0 || m < 0 || m > 64 || n_ch < 1 || n_ch > 16 || p->k_anchor < 1 || p->k_closest < 1)
+        return ORC_EINVAL;
+    int rc = ORC_OK;
+    double *F = (double *)malloc((size_t)n * sizeof(double));
+    double *Fl = (double *)malloc((size_t)n * sizeof(double));
+    double *cos = (double *)malloc((size_t)n * sizeof(double));
+    int64_t *rank = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *tmp = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    double *ssem = (double *)malloc((size_t)n * sizeof(double));
+    double *tt = (double *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(double));
+    int64_t *aa = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(int64_t));
+    const float *emb[16];
+    if (!F || !Fl || !cos || !rank || !order || !tmp || !ssem || !tt || !aa) { rc = ORC_ENOMEM; goto out; }
+
+    /* the target: fused score and s_sem */
+    {
+        int64_t off = 0;
+        for (int32_t c = 0; c < n_ch; ++c) {
+            emb[c] = u0 + off;
+            off += spaces[ch_space[c] >= 0 && ch_space[c] < n_spaces ? ch_space[c] : 0].dim;
+        }
+    }
+    if ((rc = fused_scores(s, spaces, n_spaces, p, n_ch, ch_space, ch_w, emb, F, cos, rank)) != ORC_OK) goto out;
+    for (int64_t j = 0; j < n; ++j) ssem[j] = class_factor(s, p, c_t, j) * F[j];
+    /* C: the k_closest objects of largest F */
+    sort_by_value(n, F, order, tmp);
+    int64_t kc = p->k_closest < n ? p->k_closest : n;
+    int64_t cset[4096];
+    if (kc > 4096) { rc = ORC_EINVAL; goto out; }
+    for (int64_t r = 0; r < kc; ++r) cset[r] = order[r];
+
+    for (int32_t i = 0; i < m; ++i) {
+        /* the landmark's channel embeddings: row i of each channel's block */
+        int64_t off = 0;
+        for (int32_t c = 0; c < n_ch; ++c) {
+            int64_t d = spaces[ch_space[c]].dim;
+            emb[c] = u_c + off + (int64_t)i * d;
+            off += (int64_t)m * d;
+        }
+        if ((rc = fused_scores(s, spaces, n_spaces, p, n_ch, ch_space, ch_w, emb, Fl, cos, rank)) != ORC_OK)
+            goto out;
+        sort_by_value(n, Fl, order, tmp);       /* order[0 .. K_a) is L_i */
+        int64_t ka = p->k_anchor < n ? p->k_anchor : n;
+        for (int64_t e = 0; e < n; ++e) {
+            double tbest = 0.0;
+            int64_t abest = -1;
+            for (int64_t l = 0; l < ka; ++l) {
+                int64_t cand = order[l];
+                if (cand == e) continue;
+                double rv = orc_relation_in(s, p, preds[i], e, cand, cset, kc);
+                if (abest < 0 || rv > tbest || (rv == tbest && cand < abest)) {
+                    tbest = rv;
+                    abest = cand;
+                }
+            }
+            tt[(int64_t)i * n + e] = abest < 0 ? 0.0 : tbest;
+            aa[(int64_t)i * n + e] = abest;
+        }
+    }
+    for (int64_t e = 0; e < n; ++e) {
+        double te[64];
+        for (int32_t i = 0; i < m; ++i) te[i] = tt[(int64_t)i * n + e];
+        if (s_out) s_out[e] = compose(p, ssem[e], m, te);
+        if (fused_out) fused_out[e] = F[e];
+        if (s_sem_out) s_sem_out[e] = ssem[e];
+    }
+    if (t_out) memcpy(t_out, tt, (size_t)m * (size_t)n * sizeof(double));
+    if (anchor_out) memcpy(anchor_out, aa, (size_t)m * (size_t)n * sizeof(int64_t));
+out:
+    free(F); free(Fl); free(cos); free(rank); free(order); free(tmp); free(ssem); free(tt); free(aa);
+    return rc;
+}
+
+/*
+ * Tie-tolerant bounds for several channels (as orc_query_bounds for one):
+ * each channel's rank range [rank_lo, rank_hi] at tie tolerance tau gives
+ * F in [F_lo, F_hi] = [sum_c w_c / (mu + rank_hi_c), sum_c w_c / (mu + rank_lo_c)].
+ * An object is certainly among the K largest F when fewer than K others can
+ * reach its F_lo (#{j != a : F_hi(j) >= F_lo(a)} < K), possibly so when
+ * fewer than K others certainly beat it (#{j != a : F_lo(j) > F_hi(a)} < K).
+ * That decides L_i's certain (D_i) and possible (P_i) members and the
+ * Closest / Farthest set; the rest follows orc_query_bounds.  Outputs:
+ * s_lo, s_hi, t_lo, t_hi, F_lo, F_hi (target), in_p (m*n).
+ */
+static void fused_range(const orc_scene *s, const orc_space *spaces, const orc_params *p, int32_t n_ch,
+                        const int32_t *ch_space, const double *ch_w, const float *const *emb, double tau,
+                        double *Flo, double *Fhi, double *cos, double *sorted)
+{
+    int64_t n = s->n;
+    for (int64_t j = 0; j < n; ++j) Flo[j] = Fhi[j] = 0.0;
+    for (int32_t c = 0; c < n_ch; ++c) {
+        orc_scene sc = *s;
+        sc.dim = spaces[ch_space[c]].dim;
+        sc.desc = spaces[ch_space[c]].desc;
+        orc_cosines(&sc, emb[c], cos);
+        memcpy(sorted, cos, (size_t)n * sizeof(double));
+        qsort(sorted, (size_t)n, sizeof(double), cmp_double);
+        for (int64_t j = 0; j < n; ++j) {
+            int64_t rlo = 1 + count_greater(sorted, n, cos[j] + tau);
+            int64_t rhi = count_geq(sorted, n, cos[j] - tau);
+            Flo[j] += ch_w[c] / (p->mu + (double)rhi);
+            Fhi[j] += ch_w[c] / (p->mu + (double)rlo);
+        }
+    }
+}
+
+/* certain[j] / possible[j]: j is certainly / possibly among the K largest. */
+static void topk_membership(int64_t n, const double *lo, const double *hi, int64_t K, int8_t *certain,
+                            int8_t *possible, double *sorted)
+{
+    memcpy(sorted, hi, (size_t)n * sizeof(double));
+    qsort(sorted, (size_t)n, sizeof(double), cmp_double);
+    for (int64_t j = 0; j < n; ++j) {
+        /* others whose upper bound reaches lo[j] (j itself counts when hi[j] >= lo[j]) */
+        int64_t reach = count_geq(sorted, n, lo[j]) - (hi[j] >= lo[j] ? 1 : 0);
+        certain[j] = reach < K;
+    }
+    memcpy(sorted, lo, (size_t)n * sizeof(double));
+    qsort(sorted, (size_t)n, sizeof(double), cmp_double);
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t beat = count_greater(sorted, n, hi[j]) - (lo[j] > hi[j] ? 1 : 0);
+        possible[j] = beat < K;
+    }
+}
+
+int orc_query_bounds_mc(const orc_scene *s, const orc_space *spaces, int32_t n_spaces, const orc_params *p,
+                        int32_t n_ch, const int32_t *ch_space, const double *ch_w, const float *u0,
+                        int32_t c_t, int32_t m, const int32_t *preds, const float *u_c, double tau,
+                        double *s_lo, double *s_hi, double *t_lo_out, double *t_hi_out,
+                        double *F_lo_out, double *F_hi_out, int8_t *in_p_out)
+{
+    int64_t n = s->n;
+    if (n <= 0 || m < 0 || m > 64 || n_ch < 1 || n_ch > 16 || !(tau >= 0.0)) return ORC_EINVAL;
+    for (int32_t c = 0; c < n_ch; ++c)
+        if (ch_space[c] < 0 || ch_space[c] >= n_spaces) return ORC_EINVAL;
+    int rc = ORC_OK;
+    double *Flo = (double *)malloc((size_t)n * sizeof(double));
+    double *Fhi = (double *)malloc((size_t)n * sizeof(double));
+    double *Llo = (double *)malloc((size_t)n * sizeof(double));
+    double *Lhi = (double *)malloc((size_t)n * sizeof(double));
+    double *cos = (double *)malloc((size_t)n * sizeof(double));
+    double *sorted = (double *)malloc((size_t)n * sizeof(double));
+    double *tlo = (double *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(double));
+    double *thi = (double *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(double));
+    int8_t *c_d = (int8_t *)malloc((size_t)n), *c_p = (int8_t *)malloc((size_t)n);
+    int8_t *l_d = (int8_t *)malloc((size_t)n), *l_p = (int8_t *)malloc((size_t)n);
+    int64_t *cset = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *plist = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    const float *emb[16];
+    int64_t n_cset = 0, n_cp = 0;
+    if (!Flo || !Fhi || !Llo || !Lhi || !cos || !sorted || !tlo || !thi || !c_d || !c_p || !l_d || !l_p ||
+        !cset || !plist) {
+        rc = ORC_ENOMEM;
+        goto out;
+    }
+    {
+        int64_t off = 0;
+        for (int32_t c = 0; c < n_ch; ++c) { emb[c] = u0 + off; off += spaces[ch_space[c]].dim; }
+    }
+    fused_range(s, spaces, p, n_ch, ch_space, ch_w, emb, tau, Flo, Fhi, cos, sorted);
+    topk_membership(n, Flo, Fhi, p->k_closest, c_d, c_p, sorted);
+    for (int64_t j = 0; j < n; ++j) {
+        if (c_d[j]) cset[n_cset++] = j;
+        n_cp += c_p[j];
+    }
+    const int cset_certain = n_cset == n_cp;
+    for (int32_t i = 0; i < m; ++i) {
+        int64_t off = 0;
+        for (int32_t c = 0; c < n_ch; ++c) {
+            int64_t d = spaces[ch_space[c]].dim;
+            emb[c] = u_c + off + (int64_t)i * d;
+            off += (int64_t)m * d;
+        }
+        fused_range(s, spaces, p, n_ch, ch_space, ch_w, emb, tau, Llo, Lhi, cos, sorted);
+        topk_membership(n, Llo, Lhi, p->k_anchor, l_d, l_p, sorted);
+        int64_t n_p = 0;
+        for (int64_t a = 0; a < n; ++a) {
+            if (in_p_out) in_p_out[(int64_t)i * n + a] = l_p[a];
+            if (l_p[a]) plist[n_p++] = a;
+        }
+        const int ranked = preds[i] == ORC_CLOSEST || preds[i] == ORC_FARTHEST;
+        for (int64_t e = 0; e < n; ++e) {
+            double lo = 0.0, hi = 0.0;
+            for (int64_t l = 0; l < n_p; ++l) {
+                int64_t a = plist[l];
+                if (a == e) continue;
+                double r_lo, r_hi;
+                if (!ranked) {
+                    r_lo = r_hi = orc_relation(s, p, preds[i], e, a);
+                } else if (!c_p[e]) {
+                    r_lo = r_hi = 0.0;
+                } else if (!cset_certain || !c_d[e]) {
+                    r_lo = 0.0;
+                    r_hi = 1.0;
+                } else {
+                    rank_relation_bounds(s, preds[i], e, a, cset, n_cset, 1e-5, &r_lo, &r_hi);
+                }
+                if (r_hi > hi) hi = r_hi;
+                if (l_d[a] && r_lo > lo) lo = r_lo;
+            }
+            tlo[(int64_t)i * n + e] = lo;
+            thi[(int64_t)i * n + e] = hi;
+        }
+    }
+    for (int64_t e = 0; e < n; ++e) {
+        double cf = class_factor(s, p, c_t, e), te[64];
+        for (int32_t i = 0; i < m; ++i) te[i] = tlo[(int64_t)i * n + e];
+        double a = compose(p, cf * Flo[e], m, te);
+        for (int32_t i = 0; i < m; ++i) te[i] = thi[(int64_t)i * n + e];
+        double b = compose(p, cf * Fhi[e], m, te);
+        if (s_lo) s_lo[e] = a;
+        if (s_hi) s_hi[e] = b;
+        if (F_lo_out) F_lo_out[e] = Flo[e];
+        if (F_hi_out) F_hi_out[e] = Fhi[e];
+    }
+    if (t_lo_out) memcpy(t_lo_out, tlo, (size_t)m * (size_t)n * sizeof(double));
+    if (t_hi_out) memcpy(t_hi_out, thi, (size_t)m * (size_t)n * sizeof(double));
+out:
+    free(Flo); free(Fhi); free(Llo); free(Lhi); free(cos); free(sorted); free(tlo); free(thi);
+    free(c_d); free(c_p); free(l_d); free(l_p); free(cset); free(plist);
+    return rc;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

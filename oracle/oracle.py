@@ -103,6 +103,12 @@ def load():
         lib.orc_query_bounds.restype = C.c_int
         lib.orc_query_bounds.argtypes = [P, P, P, C.c_int32, C.c_int32, P, P, C.c_double,
                                          P, P, P, P, P, P, P]
+        lib.orc_query_mc.restype = C.c_int
+        lib.orc_query_mc.argtypes = [P, P, C.c_int32, P, C.c_int32, P, P, P, C.c_int32, C.c_int32, P, P,
+                                     P, P, P, P, P]
+        lib.orc_query_bounds_mc.restype = C.c_int
+        lib.orc_query_bounds_mc.argtypes = [P, P, C.c_int32, P, C.c_int32, P, P, P, C.c_int32, C.c_int32, P,
+                                            P, C.c_double, P, P, P, P, P, P, P]
         lib.orc_num_threads.restype = C.c_int
         lib.orc_num_threads.argtypes = []
         _lib = lib
@@ -235,4 +241,66 @@ def batch(scene, qb, k: int, params: OracleParams | None = None, n_threads: int 
                           int(k), _ptr(out["idx"]), _ptr(out["score"]), _ptr(out["t"]),
                           _ptr(out["anchor"]), int(n_threads))
     _check(rc, "batch")
+    return out
+
+
+class _Space(C.Structure):
+    _fields_ = [("dim", C.c_int64), ("desc", C.c_void_p)]
+
+
+class _SpacesRef:
+    """Contiguous float32 copies of a scene's descriptor spaces (a list of
+    [n, dim_s] arrays) and the C table pointing at them."""
+
+    def __init__(self, spaces):
+        self.arrs = [np.ascontiguousarray(d, dtype=np.float32) for d in spaces]
+        self.table = (_Space * len(self.arrs))(*[_Space(a.shape[1], _ptr(a)) for a in self.arrs])
+        self.n = len(self.arrs)
+
+
+def _mc_args(spaces, channels, u0, u_c, m):
+    """channels: list of (space, weight); u0: list of per-channel target
+    embeddings; u_c: list of per-channel [m, dim] landmark embeddings."""
+    sp = _SpacesRef(spaces)
+    ch_space = np.ascontiguousarray([c[0] for c in channels], dtype=np.int32)
+    ch_w = np.ascontiguousarray([c[1] for c in channels], dtype=np.float64)
+    u0f = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).ravel() for x in u0]))
+    ucf = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).reshape(m, -1).ravel() for x in u_c])
+                               if m > 0 else np.zeros(1, np.float32))
+    return sp, ch_space, ch_w, u0f, ucf
+
+
+def query_mc(scene, spaces, channels, u0, c_t, preds, u_c, params: OracleParams | None = None) -> dict:
+    """One query over several retrieval channels (reciprocal-rank fusion,
+    App. D.2 step 3): every intermediate over all objects."""
+    sr, pp = _SceneRef(scene), _params(params)
+    preds = np.ascontiguousarray(preds, dtype=np.int32)
+    m = int(preds.shape[0])
+    sp, chs, chw, u0f, ucf = _mc_args(spaces, channels, u0, u_c, m)
+    n = sr.n
+    out = dict(fused=np.zeros(n), s_sem=np.zeros(n), t=np.zeros((m, n)), anchor=np.zeros((m, n), np.int64),
+               s=np.zeros(n))
+    rc = load().orc_query_mc(C.byref(sr.c), sp.table, sp.n, C.byref(pp), len(channels), _ptr(chs), _ptr(chw),
+                             _ptr(u0f), int(c_t), m, _ptr(preds if m else np.zeros(1, np.int32)), _ptr(ucf),
+                             _ptr(out["fused"]), _ptr(out["s_sem"]), _ptr(out["t"]), _ptr(out["anchor"]),
+                             _ptr(out["s"]))
+    _check(rc, "query_mc")
+    return out
+
+
+def query_bounds_mc(scene, spaces, channels, u0, c_t, preds, u_c, tau: float,
+                    params: OracleParams | None = None) -> dict:
+    """Tie-tolerant bounds of query_mc (cosine error <= tau/2 in every channel)."""
+    sr, pp = _SceneRef(scene), _params(params)
+    preds = np.ascontiguousarray(preds, dtype=np.int32)
+    m = int(preds.shape[0])
+    sp, chs, chw, u0f, ucf = _mc_args(spaces, channels, u0, u_c, m)
+    n = sr.n
+    out = dict(s_lo=np.zeros(n), s_hi=np.zeros(n), t_lo=np.zeros((m, n)), t_hi=np.zeros((m, n)),
+               F_lo=np.zeros(n), F_hi=np.zeros(n), in_p=np.zeros((m, n), np.int8))
+    rc = load().orc_query_bounds_mc(C.byref(sr.c), sp.table, sp.n, C.byref(pp), len(channels), _ptr(chs),
+                                    _ptr(chw), _ptr(u0f), int(c_t), m, _ptr(preds if m else np.zeros(1, np.int32)),
+                                    _ptr(ucf), float(tau), _ptr(out["s_lo"]), _ptr(out["s_hi"]), _ptr(out["t_lo"]),
+                                    _ptr(out["t_hi"]), _ptr(out["F_lo"]), _ptr(out["F_hi"]), _ptr(out["in_p"]))
+    _check(rc, "query_bounds_mc")
     return out

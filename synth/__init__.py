@@ -4,7 +4,7 @@ This package draws random numbers and lays them out; it holds none of the
 retrieval method's arithmetic (no cosines, ranks, predicates or scores).
 """
 from .scenes import (Scene, QueryBatch, make_scene, make_queries, workload,
-                     WORKLOADS)
+                     WORKLOADS, Spaces, add_spaces, ChannelQueries, channel_queries, PAPER_CHANNELS)
 
 __all__ = ["Scene", "QueryBatch", "make_scene", "make_queries", "workload",
-           "WORKLOADS"]
+           "WORKLOADS", "Spaces", "add_spaces", "ChannelQueries", "channel_queries", "PAPER_CHANNELS"]

@@ -29,7 +29,7 @@ import numpy as np
 # Predicate codes of the C-ABI (include/farm.h): above, below, left_of,
 # right_of, near.
 N_PRED = 5          # the predicates of the benchmark workloads (codes 0-4)
-N_PRED_ALL = 11     # with NextTo, On, InFrontOf, Behind, Closest, Farthest (codes 5-10)
+N_PRED_ALL = 13     # with NextTo, On, InFrontOf, Behind, Closest, Farthest, NearH, Inside (codes 5-12)
 
 
 @dataclasses.dataclass
@@ -168,13 +168,14 @@ def make_scene(seed: int, n: int, dim: int, extent=(10.0, 10.0, 3.0),
                  noise_sigma=sigma)
 
 
-def _plant_landmark(rng, centers, e, pred, tree, radius=5.0):
+def _plant_landmark(rng, centers, e, pred, tree, radius=5.0, sizes=None):
     """Pick a landmark object for constraint `pred` on planted target `e`.
 
     Prefers objects within `radius` metres; among them, for above (0) a lower
     centre, for below (1) a higher centre, for near (4) one within 1 m, for
     next_to (5) one within 2 m, for on (6) a lower centre within 1 m
-    horizontally; for the others any neighbour.  Falls back to any other
+    horizontally, for near_h (11) one within 1 m, for inside (12) the
+    largest box within 1 m; for the others any neighbour.  Falls back to any other
     object.
     `tree` is a KD-tree over the centres (neighbour lookup only).
     """
@@ -197,6 +198,13 @@ def _plant_landmark(rng, centers, e, pred, tree, radius=5.0):
     elif pred == 6:
         d = centers[cand, :2] - centers[e, :2]
         pref = cand[(np.einsum("ij,ij->i", d, d) <= 1.0) & (centers[cand, 2] < centers[e, 2])]
+    elif pred == 11:
+        d = centers[cand] - centers[e]
+        pref = cand[np.einsum("ij,ij->i", d, d) <= 1.0]
+    elif pred == 12 and sizes is not None:
+        d = centers[cand] - centers[e]
+        near = cand[np.einsum("ij,ij->i", d, d) <= 1.0]
+        pref = near[np.argsort(-np.prod(sizes[near], axis=1), kind="stable")[:1]] if near.size else near
     else:
         pref = cand
     pool = pref if pref.size else cand
@@ -220,6 +228,7 @@ def make_queries(seed: int, scene: Scene, n_q: int, m_choices=(2,),
     rng = np.random.Generator(np.random.PCG64(seed))
     n, dim = scene.n, scene.dim
     centers = scene.centers.astype(np.float64)
+    sizes = np.abs(scene.box[3:].T.astype(np.float64))
     cent = scene.centroids
     sigma = scene.noise_sigma
     if distractor_classes > 0:
@@ -246,7 +255,7 @@ def make_queries(seed: int, scene: Scene, n_q: int, m_choices=(2,),
     tree = cKDTree(centers)
     for q in range(n_q):
         for c in range(c_off[q], c_off[q + 1]):
-            lms[c] = _plant_landmark(rng, centers, int(targets[q]), int(preds[c]), tree)
+            lms[c] = _plant_landmark(rng, centers, int(targets[q]), int(preds[c]), tree, sizes=sizes)
     c_emb = cent[scene.cls[lms]] + sigma * rng.standard_normal((n_c, dim))
     tgt_cls = scene.cls[targets].astype(np.int32) if with_class else np.full(n_q, -1, np.int32)
     return QueryBatch(tgt_emb=np.ascontiguousarray(tgt_emb.astype(np.float32)),
@@ -300,6 +309,73 @@ def _site_n100k(n_q=16384):
     qb = make_queries(104, sc, n_q, m_choices=(1, 2, 3, 4),
                       distractor_classes=100, distractor_target_frac=0.5)
     return [sc], qb
+
+
+# ---------------------------------------------------------------------------
+# Several embedding spaces and query channels (App. D.2 step 3: four query
+# channels over three embedding spaces; caption text, SigLIP2 image and
+# Qwen3-VL image embeddings).  Space 0 is the scene's own descriptor array.
+# ---------------------------------------------------------------------------
+
+# (space, weight, noise multiplier) per channel, in the paper's order: the
+# caption-text space queried with the target description (w = 1.0) and with
+# the raw utterance (w = 0.5, a less specific phrase: twice the noise), the
+# image space of the scene's descriptors (w = 0.75) and a second image space
+# (w = 1.0).  Spaces: 0 = the scene's descriptors, 1 = text, 2 = second image.
+PAPER_CHANNELS = ((1, 1.0, 1.0), (1, 0.5, 2.0), (0, 0.75, 1.0), (2, 1.0, 1.0))
+
+
+@dataclasses.dataclass
+class Spaces:
+    desc: list                # per space [n, dim_s] float32, unit rows
+    centroids: list           # per space [n_classes, dim_s] float64
+    noise_sigma: list         # per space: per-dimension descriptor noise
+
+    @property
+    def dims(self):
+        return [int(d.shape[1]) for d in self.desc]
+
+
+def add_spaces(scene: Scene, seed: int, dims=(1024, 2048), noise_scale: float = 0.15) -> Spaces:
+    """The scene's descriptors as space 0 plus one space per entry of `dims`:
+    per space, unit Gaussian class centroids of its own and each object's
+    descriptor = its class centroid + N(0, (noise_scale / sqrt(dim))^2),
+    renormalised (the recipe of make_scene)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_classes = scene.centroids.shape[0]
+    descs, cents, sigmas = [scene.desc], [scene.centroids], [scene.noise_sigma]
+    for dim in dims:
+        cen = _unit_rows(rng.standard_normal((n_classes, dim)))
+        sg = noise_scale / math.sqrt(dim)
+        d = _unit_rows(cen[scene.cls] + sg * rng.standard_normal((scene.n, dim))).astype(np.float32)
+        descs.append(np.ascontiguousarray(d))
+        cents.append(cen)
+        sigmas.append(sg)
+    return Spaces(desc=descs, centroids=cents, noise_sigma=sigmas)
+
+
+@dataclasses.dataclass
+class ChannelQueries:
+    channels: list            # [(space, weight)]
+    tgt: list                 # per channel [n_q, dim_space] float32
+    lm: list                  # per channel [n_c, dim_space] float32
+
+
+def channel_queries(seed: int, scene: Scene, spaces: Spaces, qb: QueryBatch, channels=PAPER_CHANNELS) -> ChannelQueries:
+    """Per-channel target and landmark embeddings for the planted targets and
+    landmarks of `qb`: channel c of space s draws its class centroid in s plus
+    noise of (noise multiplier x the space's descriptor noise)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tcls = scene.cls[qb.planted]
+    lcls = scene.cls[qb.planted_lm] if qb.n_c else np.zeros(0, np.int64)
+    tgt, lm = [], []
+    for sp, _, mult in channels:
+        cen, sg = spaces.centroids[sp], spaces.noise_sigma[sp] * mult
+        dim = cen.shape[1]
+        tgt.append(np.ascontiguousarray((cen[tcls] + sg * rng.standard_normal((qb.n_q, dim))).astype(np.float32)))
+        lm.append(np.ascontiguousarray((cen[lcls] + sg * rng.standard_normal((qb.n_c, dim))).astype(np.float32)
+                                       .reshape(qb.n_c, dim)))
+    return ChannelQueries(channels=[(int(c[0]), float(c[1])) for c in channels], tgt=tgt, lm=lm)
 
 
 def concat_batches(parts):

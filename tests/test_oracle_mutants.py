@@ -2,7 +2,7 @@
 
 Each case plants one mistake in a copy of oracle/farm_oracle.c (on the CPU),
 compiles it, and runs the pin suites (test_oracle_pins.py,
-test_oracle_pins_more.py) against it in a subprocess: they must fail.  A pin set that passes a planted mistake is not pinning that part.
+test_oracle_pins_more.py, test_oracle_pins_mc.py) against it in a subprocess: they must fail.  A pin set that passes a planted mistake is not pinning that part.
 """
 import os
 import subprocess
@@ -43,6 +43,12 @@ MUTANTS = {
     "hellinger_det_factor_dropped": ("bc *= sqrt(2.0 * se * sa / q) * exp(-3.0 * d * d / q);",
                                      "bc *= exp(-3.0 * d * d / q);"),
     "inside_divides_by_anchor": ("frac *= ov / (2.0 * he);", "frac *= ov / (2.0 * ha);"),
+    "fusion_weight_dropped": ("for (int64_t j = 0; j < s->n; ++j) F[j] += ch_w[c] / (p->mu + (double)rank[j]);",
+                              "for (int64_t j = 0; j < s->n; ++j) F[j] += 1.0 / (p->mu + (double)rank[j]);"),
+    "fusion_class_factor_dropped": ("for (int64_t j = 0; j < n; ++j) ssem[j] = class_factor(s, p, c_t, j) * F[j];",
+                                    "for (int64_t j = 0; j < n; ++j) ssem[j] = F[j];"),
+    "fusion_landmarks_from_target": ("        if ((rc = fused_scores(s, spaces, n_spaces, p, n_ch, ch_space, ch_w, emb, Fl, cos, rank)) != ORC_OK)\n            goto out;\n        sort_by_value(n, Fl, order, tmp);",
+                                     "        if ((rc = fused_scores(s, spaces, n_spaces, p, n_ch, ch_space, ch_w, emb, Fl, cos, rank)) != ORC_OK)\n            goto out;\n        sort_by_value(n, F, order, tmp);"),
     "full_product_not_blend": ("return s_sem * ((1.0 - p->w) + p->w * gbar);", "return s_sem * gbar;"),
 }
 
@@ -60,6 +66,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     env = dict(os.environ, FARM_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_pins_more.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins_more.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_pins_mc.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins pass with mutant {name}:\n{r.stdout[-2000:]}"
