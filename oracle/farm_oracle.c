@@ -62,7 +62,7 @@
  *       covariance of the uniform distribution over its box,
  *       diag(s_x^2, s_y^2, s_z^2) / 12; with the Bhattacharyya coefficient
  *       BC = integral of sqrt(N_e N_a), the Hellinger distance is
- *       H = sqrt(1 - BC) and near_h(e,a) = 1 - H.  For diagonal Gaussians
+ *       H = sqrt(1 - BC) and near_h(e,a) = 1 - H (= BC / (1 + H)).  For diagonal Gaussians
  *       BC = prod_k sqrt(2 sd_ek sd_ak / (sd_ek^2 + sd_ak^2))
  *            * exp(-sum_k dp_k^2 / (4 (sd_ek^2 + sd_ak^2)))
  *       with sd the per-axis standard deviations and dp the centre offset
@@ -229,7 +229,10 @@ static double near_hellinger(const orc_scene *s, int64_t e, int64_t a)
     }
     double h2 = 1.0 - bc;
     if (h2 < 0.0) h2 = 0.0;
-    return 1.0 - sqrt(h2);
+    /* 1 - H written as BC / (1 + H) (the same number): 1 - sqrt(1 - BC)
+     * would round to 0 once BC is below the FP64 epsilon, where the score is
+     * still positive */
+    return bc / (1.0 + sqrt(h2));
 }
 
 /* Inside (step 5): the fraction of e's box volume inside a's box. */
