@@ -153,6 +153,36 @@ def cpu_baseline(scenes, qb, k, n_sample, seed=0, budget_s=15.0):
         np.concatenate(refs)
 
 
+def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
+    """The oracle of the several-channel batch on a seeded query sample (a
+    thread per host core, each scoring one query at a time)."""
+    import concurrent.futures as cf
+    import oracle
+    order = np.random.default_rng(seed).permutation(qb.n_q)[:min(n_sample, qb.n_q)]
+    threads = os.cpu_count() or 1
+
+    def one(q):
+        m0, m1 = int(qb.c_off[q]), int(qb.c_off[q + 1])
+        out = oracle.query_mc(scene, spaces.desc, cq.channels, [x[q] for x in cq.tgt], int(qb.tgt_cls[q]),
+                              qb.c_pred[m0:m1], [x[m0:m1] for x in cq.lm])
+        return oracle.topk(out["s"], k)
+
+    done, refs = [], []
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for c0 in range(0, len(order), threads):
+            chunk = order[c0:c0 + threads]
+            refs.extend(ex.map(one, chunk.tolist()))
+            done.extend(chunk.tolist())
+            if time.perf_counter() - t0 >= budget_s:
+                break
+    dt = time.perf_counter() - t0
+    return {"value": len(done) / dt, "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(done)} of the {qb.n_q} queries (seeded, {threads} at a time until about "
+                      f"{budget_s:.0f} s), FP64 oracle over {len(cq.channels)} channels, {dt:.1f} s wall"}, \
+        np.asarray(done), np.asarray(refs)
+
+
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the similarity kernel, from one ncu capture per (workload, precision, tile
 # variant) -- profiles/sim_tc_f16x3_site_n20k.md and profiles/sim_tc_bf16_site_n20k.md --
@@ -277,6 +307,9 @@ def main():
                     help="pin the similarity kernel's tile variant (0-3) instead of autotuning it")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the timed steps directly instead of as CUDA graphs (FARM_GRAPH)")
+    ap.add_argument("--channels", default="one", choices=["one", "paper"],
+                    help="'paper': reciprocal-rank fusion over four query channels in three descriptor "
+                         "spaces (the scene's, a 1,024-d and a 2,048-d one; weights 1.0 / 0.5 / 0.75 / 1.0)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -315,6 +348,18 @@ def main():
         F.farm_memory_upload(ctx, sid, scn.desc, scn.cls, scn.box, scn.views)
     training = train_prefilter(F, ctx, scenes) if args.precision == "learned" else None
     n_q, n_c = qb.n_q, qb.n_c
+    fused = args.channels == "paper"
+    if fused:
+        if len(scenes) != 1 or args.precision != "fp32":
+            raise SystemExit("--channels paper runs one scene in FP32")
+        spaces = synth.add_spaces(sc, 9001, dims=(1024, 2048))
+        for s_i in range(1, len(spaces.desc)):
+            F.farm_memory_add_space(ctx, 0, s_i, spaces.desc[s_i])
+        cq = synth.channel_queries(9002, sc, spaces, qb)
+        # the channels' embeddings laid end to end, as the call takes them
+        flat_t = np.concatenate([x.ravel() for x in cq.tgt])
+        flat_l = np.concatenate([x.ravel() for x in cq.lm])
+        d_tgts, d_lms = torch.from_numpy(flat_t).cuda(), torch.from_numpy(flat_l).cuda()
     d_tgt = torch.from_numpy(qb.tgt_emb).cuda()
     d_cemb = torch.from_numpy(qb.c_emb).cuda()
     o_idx = torch.empty((n_q, K_TOP), dtype=torch.int32, device="cuda")
@@ -322,11 +367,14 @@ def main():
     o_pred = torch.empty((n_q, K_TOP, 4), dtype=torch.float32, device="cuda")
     o_anc = torch.empty((n_q, K_TOP, 4), dtype=torch.int32, device="cuda")
 
-    graph = not args.no_graph
+    graph = not args.no_graph and not fused
 
     def step_device(use_graph=graph):
-        h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec,
-                               graph=use_graph)
+        if fused:
+            h = F.farm_query_batch_rrf(ctx, 0, cq.channels, d_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, d_lms)
+        else:
+            h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec,
+                                   graph=use_graph)
         F.farm_topk(ctx, h, K_TOP, n_q, o_idx, o_score, o_pred, o_anc)
 
     def timed(fn, sample_clocks):
@@ -372,9 +420,16 @@ def main():
                  pred=torch.empty((n_q, K_TOP, 4), dtype=torch.float32).pin_memory().numpy(),
                  anchor=torch.empty((n_q, K_TOP, 4), dtype=torch.int32).pin_memory().numpy())
 
+    if fused:
+        h_tgts = torch.from_numpy(flat_t).pin_memory().numpy()
+        h_lms = torch.from_numpy(flat_l).pin_memory().numpy()
+
     def step_host():
-        h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec,
-                               graph=graph)
+        if fused:
+            h = F.farm_query_batch_rrf(ctx, 0, cq.channels, h_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, h_lms)
+        else:
+            h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec,
+                                   graph=graph)
         F.farm_topk(ctx, h, K_TOP, n_q, h_out["idx"], h_out["score"], h_out["pred"], h_out["anchor"])
 
     for _ in range(args.warmup):
@@ -388,12 +443,18 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     e2e_ms = max_over_ranks([e2e_ms], dist, "cuda" if dist else None)[0]
-    h2d = (n_q + n_c) * sc.dim * 4 + 4 * (3 * n_q + 1 + n_c)
+    if fused:
+        h2d = flat_t.nbytes + flat_l.nbytes + 4 * (2 * n_q + 1 + n_c)
+    else:
+        h2d = (n_q + n_c) * sc.dim * 4 + 4 * (3 * n_q + 1 + n_c)
     d2h = n_q * K_TOP * (4 + 4 + 16 + 16)
 
     # ---- roofline of the similarity contraction (stage 1), measured over the timed region
     peaks, peak_kind = _peaks()
     flops_step = similarity_flops(scenes, qb)
+    if fused:
+        dims = spaces.dims
+        flops_step = sum(2.0 * (n_q + n_c) * sc.n * dims[sp] for sp, _ in cq.channels)
     if args.precision == "learned":
         # the similarity stage works in the 128-d embedding space
         flops_step *= 128.0 / sc.dim
@@ -433,6 +494,8 @@ def main():
                    "n_objects": int(sum(x.n for x in scenes)), "dim": sc.dim, "n_views": sc.n_views,
                    "queries": n_q, "constraint_rows": n_c, "top_k": K_TOP,
                    "precision": args.precision, "parallelism": f"replicas{world}",
+                   "channels": ([{"space": sp, "dim": spaces.dims[sp], "weight": w} for sp, w in cq.channels]
+                                if fused else 1),
                    "cuda_graph": graph,
                    "l2": "inputs larger than L2 (descriptor copies and the similarity block exceed 129 MB)"},
         "e2e": {"value": job_rate(n_q, world, e2e_ms), "unit": "queries/s",
@@ -456,7 +519,10 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        base, qs, ref_idx = cpu_baseline(scenes, qb, K_TOP, args.cpu_sample)
+        if fused:
+            base, qs, ref_idx = cpu_baseline_mc(sc, spaces, qb, cq, K_TOP, args.cpu_sample)
+        else:
+            base, qs, ref_idx = cpu_baseline(scenes, qb, K_TOP, args.cpu_sample)
         line["cpu_baseline"] = base
         got = h_out["idx"][qs]
         hits = sum(len(set(got[i].tolist()) & set(ref_idx[i].tolist())) for i in range(len(qs)))

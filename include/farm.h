@@ -11,7 +11,9 @@
  *
  * with the unary score s_sem given by reciprocal-rank fusion of descriptor
  * similarity (App. D.2 step 3), the closed-form relation evaluators of App. D.2
- * step 4 (Above, Below, LeftOf, RightOf, Near), anchors bound greedily to
+ * step 4 (Above, Below, LeftOf, RightOf, Near, NextTo, On, InFrontOf, Behind,
+ * Closest, Farthest, Inside) and the Hellinger form of Near (Sec. 2.3),
+ * anchors bound greedily to
  * their best witness among the top-K_a landmark candidates (App. B,
  * "Query-time complexity"; App. D.2 step 4) and the composite
  * s = s_sem * [(1 - w) + w * gbar] of App. D.2 step 5.
@@ -67,7 +69,10 @@ typedef enum {
     FARM_BEHIND = 8,    /* mean over the candidate's stored views of sig((Z_e - Z_a) / tau_d) */
     FARM_CLOSEST = 9,   /* 1 / rank_d: e's rank by distance to a among the query's k_closest
                            best target candidates other than a (0 for e outside them) */
-    FARM_FARTHEST = 10  /* 1 / (|C| - rank_d + 1) over the same set C */
+    FARM_FARTHEST = 10, /* 1 / (|C| - rank_d + 1) over the same set C */
+    FARM_NEAR_H = 11,   /* 1 - H(N_e, N_a): the Hellinger form of Near (Sec. 2.3), with each object the
+                           Gaussian of its box centre and covariance diag(s^2) / 12 */
+    FARM_INSIDE = 12    /* containment (App. D.2 step 4): the fraction of e's box volume inside a's box */
 } farm_pred;
 
 /* Arithmetic of the descriptor-similarity stage (App. D.2 step 3). */
@@ -206,6 +211,68 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                              const float *tgt_emb, const int32_t *tgt_cls, const int32_t *c_off,
                              const int32_t *c_pred, const float *c_emb, int32_t precision,
                              uint32_t flags, uint64_t *batch_handle);
+
+/*
+ * Several retrieval channels (App. D.2 step 3).  The paper ranks the whole
+ * candidate pool once per query channel -- four channels over three
+ * embedding spaces of every object (caption text, two image embeddings) --
+ * and takes the reciprocal-rank fusion
+ *   F(j) = sum_c w_c / (mu + rank_c(j))
+ * as the target similarity, s_sem = cf * F; landmark variables are retrieved
+ * the same way (L_i = the K_a objects of largest fused landmark score) and
+ * the Closest / Farthest candidate set is the k_closest objects of largest F.
+ * Everything after that (relations, binding, composite, TopK) is as for
+ * farm_query_batch.
+ *
+ * farm_memory_add_space: stores descriptor space `space` (1 ..
+ * FARM_MAX_SPACES - 1) of an uploaded scene: desc [n, dim] FP32 rows of the
+ * scene's n objects in the same order (host, or device with
+ * FARM_PTR_DEVICE), unit-normalised on upload; space 0 is the descriptor
+ * array of farm_memory_upload.  Replaces an earlier upload of that space;
+ * re-uploading the scene drops its extra spaces.  Rows with zero or
+ * non-finite norm: FARM_EINVAL (host input) or reported by the next
+ * synchronising call (device input).
+ */
+#define FARM_MAX_SPACES 4
+#define FARM_MAX_CHANNELS 4
+farm_status farm_memory_add_space(farm_ctx *ctx, int32_t scene_id, int32_t space, int32_t dim, const float *desc,
+                                  uint32_t flags);
+
+typedef struct {
+    int32_t space;   /* descriptor space the channel is scored in */
+    float weight;    /* its reciprocal-rank-fusion weight w_c (> 0) */
+} farm_channel;
+
+/*
+ * A batch of n_q queries against one scene over n_ch channels (1 ..
+ * FARM_MAX_CHANNELS), FP32-accurate similarity (as FARM_PREC_FP32):
+ *   ch        [n_ch]  the channels
+ *   tgt_emb   the target's channel embeddings, channel after channel: block
+ *             c is [n_q, dim of ch[c].space] FP32
+ *   tgt_cls, c_off, c_pred  as farm_query_batch (host)
+ *   c_emb     the landmarks' channel embeddings, channel after channel:
+ *             block c is [n_c, dim of ch[c].space] FP32
+ *   flags     FARM_PTR_DEVICE: tgt_emb and c_emb are device pointers
+ *             (FARM_GRAPH is not supported here: FARM_EINVAL)
+ * Each channel keeps its R_t best objects per target row and R_l per landmark
+ * row, with R_t and R_l chosen so that no object outside every channel's list
+ * can reach the result: an unlisted object fuses to at most
+ * W / (mu + R + 1) (W the sum of the weights), below the k_max-th composite
+ * and the k_closest-th / K_a-th fused score.  Listed objects that could reach
+ * the result get their exact rank in the channels that did not list them
+ * (by counting over that channel's similarity row), so the result equals
+ * scoring every object.  Weights so uneven that R_t would exceed 512 (or R_l
+ * 256) are rejected (FARM_EINVAL).  A query whose objects that can still
+ * reach its TopK exceed 512 is reported by the next synchronising call
+ * (FARM_EINVAL).  The similarity block of every channel is kept until the
+ * fusion: n_ch x (n_q + n_c) x n x 4 bytes of device memory (at most 32 GiB
+ * per call, else FARM_EINVAL; split the batch).  farm_topk reads the result
+ * as for farm_query_batch; a new batch of either kind invalidates the handle.
+ */
+farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, int32_t n_ch,
+                                 const farm_channel *ch, const float *tgt_emb, const int32_t *tgt_cls,
+                                 const int32_t *c_off, const int32_t *c_pred, const float *c_emb, uint32_t flags,
+                                 uint64_t *batch_handle);
 
 /*
  * Writes the TopK of every query of a batch, the ScoredCandidate records of

@@ -70,19 +70,46 @@ def _rank_score_range(scene, pred, e, a, cset, dtol=1e-5):
 
 
 def _check_one(scene, qb, q, k, idx, score, t, anchor, params, tau, rtol, atol_t):
-    fails = []
     m0, m1 = int(qb.c_off[q]), int(qb.c_off[q + 1])
-    m = m1 - m0
     args = (scene, qb.tgt_emb[q], int(qb.tgt_cls[q]), qb.c_pred[m0:m1], qb.c_emb[m0:m1])
     b = O.query_bounds(*args, tau=tau, params=params)
     ex = O.query_all(*args, params=params)
-    s_lo, s_hi = b["s_lo"], b["s_hi"]
-    n = scene.n
     # the Closest / Farthest candidate set: target ranks 1..k_closest, when
     # the tie tolerance leaves it unambiguous
-    kc = min(params.k_closest, n)
+    kc = min(params.k_closest, scene.n)
     cset_certain = not np.any((b["rank_lo"] <= kc) & (b["rank_hi"] > kc))
     cset = set(np.flatnonzero(b["rank_hi"] <= kc).tolist()) if cset_certain else None
+    return _judge(scene, qb, q, k, idx, score, t, anchor, params, rtol, atol_t, b, ex, cset)
+
+
+def _topk_sets(lo, hi, K):
+    """Objects certainly / possibly among the K largest when each value is
+    only known to lie in [lo, hi]."""
+    n = lo.shape[0]
+    hs, ls = np.sort(hi), np.sort(lo)
+    reach = n - np.searchsorted(hs, lo, side="left") - 1          # others with hi >= my lo
+    beat = n - np.searchsorted(ls, hi, side="right")              # others with lo > my hi
+    return reach < K, beat < K
+
+
+def _check_one_mc(scene, spaces, qb, cq, q, k, idx, score, t, anchor, params, tau, rtol, atol_t):
+    m0, m1 = int(qb.c_off[q]), int(qb.c_off[q + 1])
+    args = (scene, spaces, cq.channels, [x[q] for x in cq.tgt], int(qb.tgt_cls[q]), qb.c_pred[m0:m1],
+            [x[m0:m1] for x in cq.lm])
+    b = O.query_bounds_mc(*args, tau=tau, params=params)
+    ex = O.query_mc(*args, params=params)
+    kc = min(params.k_closest, scene.n)
+    certain, possible = _topk_sets(b["F_lo"], b["F_hi"], kc)
+    cset = set(np.flatnonzero(certain).tolist()) if np.array_equal(certain, possible) else None
+    return _judge(scene, qb, q, k, idx, score, t, anchor, params, rtol, atol_t, b, ex, cset)
+
+
+def _judge(scene, qb, q, k, idx, score, t, anchor, params, rtol, atol_t, b, ex, cset):
+    fails = []
+    m0, m1 = int(qb.c_off[q]), int(qb.c_off[q + 1])
+    m = m1 - m0
+    s_lo, s_hi = b["s_lo"], b["s_hi"]
+    n = scene.n
     idx = np.asarray(idx, np.int64)
     score = np.asarray(score, np.float64)
     if np.any(idx < 0) or np.any(idx >= n) or len(set(idx.tolist())) != k:
@@ -160,6 +187,30 @@ def check_topk(scene, qb, k, idx, score, t=None, anchor=None, params=None, tau=2
     def one(q):
         return _check_one(scene, qb, q, k, idx[q], score[q], None if t is None else t[q],
                           None if anchor is None else anchor[q], params, tau, rtol, atol_t)
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for fails, exact, rel in ex.map(one, qs):
+            rep.failures.extend(fails)
+            if exact:
+                rep.n_exact += 1
+                rep.max_rel_err_exact = max(rep.max_rel_err_exact, rel)
+            else:
+                rep.n_ambiguous += 1
+    return rep
+
+
+def check_topk_mc(scene, spaces, qb, cq, k, idx, score, t=None, anchor=None, params=None, tau=2e-5, rtol=1e-5,
+                  atol_t=2e-6, queries=None, threads=None) -> ParityReport:
+    """check_topk for a batch over several channels: `spaces` the scene's
+    descriptor spaces, `cq` the per-channel embeddings (synth.ChannelQueries)."""
+    params = params or O.OracleParams()
+    qs = list(range(qb.n_q)) if queries is None else [int(x) for x in queries]
+    rep = ParityReport(n_queries=len(qs))
+    threads = threads or max(1, min(32, os.cpu_count() or 1))
+
+    def one(q):
+        return _check_one_mc(scene, spaces, qb, cq, q, k, idx[q], score[q], None if t is None else t[q],
+                             None if anchor is None else anchor[q], params, tau, rtol, atol_t)
 
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
         for fails, exact, rel in ex.map(one, qs):

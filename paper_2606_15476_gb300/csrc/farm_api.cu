@@ -152,6 +152,7 @@ void free_scene(Scene &s)
     cudaFree(s.desc32); cudaFree(s.desc_hi); cudaFree(s.desc_lo); cudaFree(s.desc_bf16);
     cudaFree(s.desc_fp8); cudaFree(s.desc_scale); cudaFree(s.comp);
     cudaFree(s.cls); cudaFree(s.pos); cudaFree(s.size); cudaFree(s.views);
+    for (auto &sp : s.spaces) { cudaFree(sp.hi); cudaFree(sp.lo); }
     s = Scene{};
 }
 
@@ -543,7 +544,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         n_c = c_off[n_q];
         if (n_c > 0 && (!c_pred || !c_emb)) return fail(ctx, FARM_EINVAL, "c_pred and c_emb must be non-null");
         for (int64_t i = 0; i < n_c; ++i)
-            if (c_pred[i] < 0 || c_pred[i] > FARM_FARTHEST)
+            if (c_pred[i] < 0 || c_pred[i] > FARM_INSIDE)
                 return fail(ctx, FARM_EINVAL, "unknown predicate code " + std::to_string(c_pred[i]));
     }
     c.batch_valid = false;
@@ -1101,6 +1102,322 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     c.batch_rtgt = stride_t;
     c.batch_klm = stride_l;
     c.batch_min_n = (int32_t)std::min<int64_t>(min_n, 0x7fffffff);
+    *batch_handle = c.batch_gen;
+    return FARM_OK;
+}
+
+farm_status farm_memory_add_space(farm_ctx *ctx, int32_t scene_id, int32_t space, int32_t dim, const float *desc,
+                                  uint32_t flags)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    if (scene_id < 0 || scene_id >= kMaxScenes || !c.scenes[scene_id].present)
+        return fail(ctx, FARM_EINVAL, "unknown scene");
+    if (space < 1 || space >= FARM_MAX_SPACES) return fail(ctx, FARM_EINVAL, "space must lie in [1, FARM_MAX_SPACES)");
+    if (dim < 1 || dim > 8192) return fail(ctx, FARM_EINVAL, "dim must lie in [1, 8192]");
+    if (!desc) return fail(ctx, FARM_EINVAL, "desc must be non-null");
+    Scene &s = c.scenes[scene_id];
+    const int64_t n = s.n;
+    const bool dev = (flags & FARM_PTR_DEVICE) != 0;
+    if (!dev) {
+        for (int64_t j = 0; j < n; ++j) {
+            double ss = 0.0;
+            const float *d = desc + j * dim;
+            for (int32_t k = 0; k < dim; ++k) ss += (double)d[k] * (double)d[k];
+            if (!(ss > 0.0) || !std::isfinite(ss))
+                return fail(ctx, FARM_EINVAL, "descriptor row " + std::to_string(j) + " has zero or non-finite norm");
+        }
+    }
+    CK(cudaSetDevice(c.device));
+    CK(cudaStreamSynchronize(c.stream));
+    farm::SpaceDesc &sp = s.spaces[space];
+    cudaFree(sp.hi);
+    cudaFree(sp.lo);
+    sp = farm::SpaceDesc{};
+    farm::SpaceDesc ns;
+    ns.dim = dim;
+    ns.dim_pad = (int32_t)round_up(dim, farm::kDimAlign);
+    const size_t nd = (size_t)n * ns.dim_pad;
+    auto bail = [&](cudaError_t e) {
+        cudaFree(ns.hi);
+        cudaFree(ns.lo);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? FARM_ENOMEM : FARM_ECUDA,
+                    std::string("space upload: ") + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&ns.hi, nd * 2)) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&ns.lo, nd * 2)) != cudaSuccess) return bail(e);
+    const float *d_desc = desc;
+    float *tmp = nullptr;
+    if (!dev) {
+        if ((e = cudaMallocAsync(&tmp, (size_t)n * dim * 4, c.stream)) != cudaSuccess) return bail(e);
+        if ((e = cudaMemcpyAsync(tmp, desc, (size_t)n * dim * 4, cudaMemcpyHostToDevice, c.stream)) != cudaSuccess)
+            return bail(e);
+        d_desc = tmp;
+    }
+    c.launches += 1;
+    if ((e = farm::launch_normalize_rows(d_desc, nullptr, n, dim, ns.dim_pad, nullptr, ns.hi, ns.lo, nullptr, c.d_err,
+                                         farm::kErrBadDesc, c.stream)) != cudaSuccess)
+        return bail(e);
+    if (tmp) cudaFreeAsync(tmp, c.stream);
+    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return bail(e);
+    sp = ns;
+    c.batch_valid = false;
+    c.scene_gen += 1;
+    return FARM_OK;
+}
+
+farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, int32_t n_ch,
+                                 const farm_channel *ch, const float *tgt_emb, const int32_t *tgt_cls,
+                                 const int32_t *c_off, const int32_t *c_pred, const float *c_emb, uint32_t flags,
+                                 uint64_t *batch_handle)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    if (!batch_handle) return fail(ctx, FARM_EINVAL, "batch_handle must be non-null");
+    if (flags & FARM_GRAPH) return fail(ctx, FARM_EINVAL, "FARM_GRAPH is not supported for fused batches");
+    if (scene_id < 0 || scene_id >= kMaxScenes || !c.scenes[scene_id].present)
+        return fail(ctx, FARM_EINVAL, "unknown scene");
+    if (n_q < 1 || n_q > 0x7fffffff) return fail(ctx, FARM_EINVAL, "n_q must lie in [1, 2^31)");
+    if (n_ch < 1 || n_ch > FARM_MAX_CHANNELS || !ch) return fail(ctx, FARM_EINVAL, "n_ch must lie in [1, 4]");
+    if (!tgt_emb || !tgt_cls || !c_off) return fail(ctx, FARM_EINVAL, "tgt_emb, tgt_cls and c_off must be non-null");
+    if (!farm::sim_tc_available()) return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
+    const Scene &s = c.scenes[scene_id];
+    const farm_params &p = c.params;
+    const int64_t n = s.n;
+    int32_t dims[FARM_MAX_CHANNELS], dpad[FARM_MAX_CHANNELS];
+    const uint16_t *dhi[FARM_MAX_CHANNELS], *dlo[FARM_MAX_CHANNELS];
+    double W = 0.0, wmax = 0.0;
+    for (int32_t k = 0; k < n_ch; ++k) {
+        const int32_t sp = ch[k].space;
+        if (sp < 0 || sp >= FARM_MAX_SPACES) return fail(ctx, FARM_EINVAL, "channel space out of range");
+        if (!(ch[k].weight > 0.f) || !std::isfinite(ch[k].weight))
+            return fail(ctx, FARM_EINVAL, "channel weights must be positive and finite");
+        if (sp == 0) {
+            dims[k] = s.dim; dpad[k] = s.dim_pad; dhi[k] = s.desc_hi; dlo[k] = s.desc_lo;
+        } else {
+            if (!s.spaces[sp].hi) return fail(ctx, FARM_EINVAL, "channel names a space the scene does not hold");
+            dims[k] = s.spaces[sp].dim; dpad[k] = s.spaces[sp].dim_pad; dhi[k] = s.spaces[sp].hi; dlo[k] = s.spaces[sp].lo;
+        }
+        W += ch[k].weight;
+        wmax = std::max(wmax, (double)ch[k].weight);
+    }
+    if (c_off[0] != 0) return fail(ctx, FARM_EINVAL, "c_off[0] must be 0");
+    for (int64_t q = 0; q < n_q; ++q) {
+        const int32_t m = c_off[q + 1] - c_off[q];
+        if (m < 0 || m > FARM_MAX_CONSTRAINTS)
+            return fail(ctx, FARM_EINVAL, "query " + std::to_string(q) + " has more than 4 constraints");
+    }
+    const int64_t n_c = c_off[n_q];
+    if (n_c > 0 && (!c_pred || !c_emb)) return fail(ctx, FARM_EINVAL, "c_pred and c_emb must be non-null");
+    for (int64_t i = 0; i < n_c; ++i)
+        if (c_pred[i] < 0 || c_pred[i] > FARM_INSIDE)
+            return fail(ctx, FARM_EINVAL, "unknown predicate code " + std::to_string(c_pred[i]));
+    if (p.k_max > n) return fail(ctx, FARM_EINVAL, "k_max exceeds the scene's object count");
+    // list depths: an object no channel lists fuses to at most W / (mu + R + 1);
+    // keep that below the k_max-th composite's floor (1 - w) class_mis wmax / (mu + k_max),
+    // the k_closest-th fused score's floor wmax / (mu + k_closest) and, for
+    // landmark rows, the K_a-th fused score's floor wmax / (mu + K_a)
+    const double mu = p.mu;
+    const double bt = std::min((1.0 - p.w) * p.class_mis * wmax / (mu + p.k_max), wmax / (mu + p.k_closest));
+    const double bl = wmax / (mu + p.k_anchor);
+    const int64_t Rt_need = (int64_t)std::floor(W / bt - mu - 1.0) + 2;
+    const int64_t Rl_need = (int64_t)std::floor(W / bl - mu - 1.0) + 2;
+    if (Rt_need > farm::kMaxTargetCands || Rl_need > farm::kMaxAnchorCands)
+        return fail(ctx, FARM_EINVAL, "channel weights too uneven: the per-channel lists would exceed 512 / 256");
+    const int32_t Rt = (int32_t)std::min<int64_t>(std::max<int64_t>(Rt_need, p.k_max), n);
+    const int32_t Rl = (int32_t)std::min<int64_t>(std::max<int64_t>(Rl_need, p.k_anchor), n);
+    const int32_t Ka = (int32_t)std::min<int64_t>(p.k_anchor, n);
+    const int32_t RF = (int32_t)std::min<int64_t>(farm::kMaxTargetCands, n);
+    const int64_t rows = n_q + n_c;
+    const int64_t ld = round_up(n, 32);
+    const int gshift = farm::group_shift_for(n);
+    const int64_t gstride = farm::group_stride(n, gshift);
+    const double s_bytes = (double)n_ch * rows * ld * 4.0;
+    if (s_bytes > 32.0 * (1ull << 30)) return fail(ctx, FARM_EINVAL, "fused batch too large (similarity blocks > 32 GiB)");
+    const bool dev = (flags & FARM_PTR_DEVICE) != 0;    // (zero or non-finite rows are caught on the GPU)
+    c.batch_valid = false;
+    *batch_handle = 0;
+    CK(cudaSetDevice(c.device));
+
+    // ---- buffers
+    int32_t dmax = 0;
+    int64_t emb_t = 0, emb_c = 0;
+    for (int32_t k = 0; k < n_ch; ++k) {
+        dmax = std::max(dmax, dpad[k]);
+        emb_t += n_q * dims[k];
+        emb_c += n_c * dims[k];
+    }
+    uint16_t *qhi, *qlo;
+    float *d_sim, *d_tops, *d_fused, *d_raw = nullptr;
+    int32_t *d_tl, *d_ll, *d_meta, *d_perm, *tsel_idx, *lsel_idx, *o_idx, *o_anc;
+    float *o_score, *o_t;
+    CK(ws_get(ctx, farm::B_QHI, (size_t)rows * dmax, &qhi));
+    CK(ws_get(ctx, farm::B_QLO, (size_t)rows * dmax, &qlo));
+    CK(ws_get(ctx, farm::B_MC_SIM, (size_t)(n_ch * rows * ld), &d_sim));
+    CK(ws_get(ctx, farm::B_MC_TOPS, (size_t)(n_ch * rows * gstride), &d_tops));
+    CK(ws_get(ctx, farm::B_MC_TLIST, (size_t)(n_ch * n_q * Rt), &d_tl));
+    CK(ws_get(ctx, farm::B_MC_LLIST, (size_t)std::max<int64_t>(n_ch * n_c * Rl, 1), &d_ll));
+    CK(ws_get(ctx, farm::B_MC_FUSED, (size_t)(n_q * RF), &d_fused));
+    CK(ws_get(ctx, farm::B_QMETA, (size_t)n_q * 8, &d_meta));
+    CK(ws_get(ctx, farm::B_PERM, (size_t)n_q, &d_perm));
+    CK(ws_get(ctx, farm::B_TSEL_IDX, (size_t)n_q * RF, &tsel_idx));
+    CK(ws_get(ctx, farm::B_LSEL_IDX, (size_t)std::max<int64_t>(n_c, 1) * Ka, &lsel_idx));
+    CK(ws_get(ctx, farm::B_OUT_IDX, (size_t)n_q * RF, &o_idx));
+    CK(ws_get(ctx, farm::B_OUT_SCORE, (size_t)n_q * RF, &o_score));
+    CK(ws_get(ctx, farm::B_OUT_T, (size_t)n_q * RF * 4, &o_t));
+    CK(ws_get(ctx, farm::B_OUT_ANCHOR, (size_t)n_q * RF * 4, &o_anc));
+    if (!dev) CK(ws_get(ctx, farm::B_RAW, (size_t)(emb_t + emb_c), &d_raw));
+    uint8_t *d_pieces;
+    CK(ws_get(ctx, farm::B_PIECES, (size_t)n_ch * sizeof(farm::Piece), &d_pieces));
+
+    // ---- metadata (caller order is the planned order), select pieces
+    std::vector<int32_t> meta((size_t)n_q * 8), perm((size_t)n_q);
+    ctx->h_perm.assign((size_t)n_q, 0);
+    ctx->h_cplan.assign((size_t)n_c, 0);
+    for (int64_t q = 0; q < n_q; ++q) {
+        const int32_t m = c_off[q + 1] - c_off[q];
+        int32_t pr[4] = {0, 0, 0, 0};
+        for (int32_t i = 0; i < m; ++i) pr[i] = c_pred[c_off[q] + i];
+        int32_t *mt = meta.data() + q * 8;
+        mt[farm::QM_SCENE] = scene_id;
+        mt[farm::QM_CLS] = tgt_cls[q];
+        mt[farm::QM_M] = m;
+        mt[farm::QM_C0] = c_off[q];
+        mt[farm::QM_PRED01] = pr[0] | (pr[1] << 16);
+        mt[farm::QM_PRED23] = pr[2] | (pr[3] << 16);
+        mt[farm::QM_R] = RF;            // (the fusion writes the kept count)
+        mt[farm::QM_KLM] = Ka;
+        perm[q] = (int32_t)q;
+        ctx->h_perm[q] = (int32_t)q;
+    }
+    for (int64_t i = 0; i < n_c; ++i) ctx->h_cplan[i] = (int32_t)i;
+    // rows [0, th0) of a channel take the shared-memory select, [th0, rows) the thresholded one
+    const int32_t uni = (int32_t)std::min<int64_t>(farm::group_count(n, gshift), 8192);
+    const bool small = n <= farm::kSelectSortAll;
+    const bool t_thresh = small || uni >= Rt || n > farm::kSelectRowMax;
+    const bool l_thresh = small || uni >= Rl || n > farm::kSelectRowMax;
+    const int64_t th0 = t_thresh ? (l_thresh ? 0 : -1) : (l_thresh ? n_q : rows);
+    if (th0 < 0) return fail(ctx, FARM_EINVAL, "unsupported scene size for a fused batch");
+    std::vector<farm::Piece> pcs((size_t)n_ch);
+    for (int32_t k = 0; k < n_ch; ++k) {
+        farm::Piece pc{};
+        pc.d32 = nullptr;
+        pc.s_off = (int64_t)k * rows * ld;
+        pc.tops_off = (int64_t)k * rows * gstride;
+        pc.row_begin = 0;
+        pc.block_begin = 0;
+        pc.tblock_begin = 0;
+        pc.q_row0 = 0;
+        pc.t_row0 = 0;
+        pc.l_row0 = 0;
+        pc.tmp_off = -1;
+        pc.rows = (int32_t)rows;
+        pc.ntr = (int32_t)n_q;
+        pc.n = (int32_t)n;
+        pc.ld = (int32_t)ld;
+        pc.keep_t = Rt;
+        pc.keep_l = Rl;
+        pc.R = Rt;
+        pc.klm = Rl;
+        pc.chunks = 1;
+        pc.chunk_len = (int32_t)n;
+        pc.th0 = (int32_t)th0;
+        pc.gshift = gshift;
+        pcs[k] = pc;
+    }
+    // (pageable sources: each copy has been staged when the call returns)
+    CK(cudaMemcpyAsync(d_meta, meta.data(), meta.size() * 4, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(d_perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(d_pieces, pcs.data(), pcs.size() * sizeof(farm::Piece), cudaMemcpyHostToDevice, c.stream));
+    if (!dev) {
+        CK(cudaMemcpyAsync(d_raw, tgt_emb, (size_t)emb_t * 4, cudaMemcpyHostToDevice, c.stream));
+        if (n_c > 0) CK(cudaMemcpyAsync(d_raw + emb_t, c_emb, (size_t)emb_c * 4, cudaMemcpyHostToDevice, c.stream));
+    }
+    const float *src_t = dev ? tgt_emb : d_raw;
+    const float *src_c = dev ? c_emb : d_raw + emb_t;
+
+    // ---- per channel: normalise its rows, FP32-accurate similarity, rank select
+    int64_t off_t = 0, off_c = 0;
+    for (int32_t k = 0; k < n_ch; ++k) {
+        const int m0 = mark_begin(ctx, 0);
+        LAUNCH(farm::launch_normalize_rows(src_t + off_t, nullptr, n_q, dims[k], dpad[k], nullptr, qhi, qlo, nullptr,
+                                           c.d_err, farm::kErrBadRow, c.stream));
+        if (n_c > 0)
+            LAUNCH(farm::launch_normalize_rows(src_c + off_c, nullptr, n_c, dims[k], dpad[k], nullptr,
+                                               qhi + (size_t)n_q * dpad[k], qlo + (size_t)n_q * dpad[k], nullptr,
+                                               c.d_err, farm::kErrBadRow, c.stream));
+        mark_end(ctx, m0);
+        off_t += n_q * dims[k];
+        off_c += n_c * dims[k];
+        const int m1 = mark_begin(ctx, 1);
+        LAUNCH(farm::launch_sim_tc_f16x3(qhi, qlo, dhi[k], dlo[k], d_sim + pcs[k].s_off, rows, n, dpad[k], ld,
+                                         d_tops + pcs[k].tops_off, c.num_sms, c.d_err, c.stream));
+        mark_end(ctx, m1);
+        const int m2 = mark_begin(ctx, 2);
+        int32_t *tl = d_tl + (size_t)k * n_q * Rt, *ll = d_ll + (size_t)k * n_c * Rl;
+        if (th0 > 0)
+            LAUNCH(farm::launch_select_rows_ex(d_sim + pcs[k].s_off, ld, n, th0, n_q, Rt, Rl, tl, nullptr, 0, Rt, ll,
+                                               nullptr, 0, Rl, c.stream));
+        if (th0 < rows)
+            LAUNCH(farm::launch_select_thresh(d_sim, d_tops, reinterpret_cast<farm::Piece *>(d_pieces) + k, 1,
+                                              rows - th0, uni, tl, nullptr, Rt, ll, nullptr, Rl, c.d_fallback,
+                                              c.stream));
+        mark_end(ctx, m2);
+    }
+
+    // ---- fusion, then relations / composite / sort
+    const int m2 = mark_begin(ctx, 2);
+    farm::FuseArgs fa{};
+    fa.n_q = n_q;
+    fa.n_c = n_c;
+    fa.n_ch = n_ch;
+    for (int32_t k = 0; k < n_ch; ++k) fa.w[k] = ch[k].weight;
+    fa.Rt = Rt;
+    fa.Rl = Rl;
+    fa.tlist = d_tl;
+    fa.llist = d_ll;
+    fa.S = d_sim;
+    fa.rows = rows;
+    fa.ld = ld;
+    fa.n = (int32_t)n;
+    fa.cls = s.cls;
+    fa.qmeta = d_meta;
+    fa.p = p;
+    fa.RF = RF;
+    fa.out_tidx = tsel_idx;
+    fa.out_tF = d_fused;
+    fa.Ka = Ka;
+    fa.out_lidx = lsel_idx;
+    fa.err = c.d_err;
+    LAUNCH(farm::launch_fuse(fa, 0, c.stream));
+    if (n_c > 0) LAUNCH(farm::launch_fuse(fa, 1, c.stream));
+    mark_end(ctx, m2);
+    const int m3 = mark_begin(ctx, 3);
+    farm::ComposeArgs ca;
+    ca.n_q = n_q;
+    ca.qmeta = d_meta;
+    ca.tsel_idx = tsel_idx;
+    ca.lsel_idx = lsel_idx;
+    ca.stride_t = RF;
+    ca.stride_l = Ka;
+    ca.scenes = ctx->d_scenes;
+    ca.p = p;
+    ca.out_idx = o_idx;
+    ca.out_score = o_score;
+    ca.out_t = o_t;
+    ca.out_anchor = o_anc;
+    ca.tsel_F = d_fused;
+    LAUNCH(farm::launch_compose(ca, c.stream));
+    mark_end(ctx, m3);
+
+    c.batch_gen += 1;
+    c.batch_valid = true;
+    c.batch_nq = n_q;
+    c.batch_nc = n_c;
+    c.batch_rtgt = RF;
+    c.batch_klm = Ka;
+    c.batch_min_n = (int32_t)std::min<int64_t>(n, 0x7fffffff);
     *batch_handle = c.batch_gen;
     return FARM_OK;
 }

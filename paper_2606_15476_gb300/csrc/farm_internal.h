@@ -35,6 +35,15 @@ constexpr int kErrBadRow = 1;        // zero or non-finite embedding row
 constexpr int kErrBadDesc = 2;       // zero or non-finite descriptor row
 constexpr int kErrTimeout = 4;       // a bounded wait gave up
 constexpr int kErrPieceTable = 8;    // a similarity piece carried a misaligned tensor-map pointer
+constexpr int kErrFusedOverflow = 16; // a query of a fused batch kept more candidates than its list holds
+
+// A further descriptor space of a scene (farm_memory_add_space): the FP16
+// split of its unit rows, as desc_hi / desc_lo below.
+struct SpaceDesc {
+    int32_t dim = 0, dim_pad = 0;
+    uint16_t *hi = nullptr;      // [n, dim_pad]
+    uint16_t *lo = nullptr;      // [n, dim_pad]
+};
 
 struct Scene {
     bool present = false;
@@ -54,6 +63,7 @@ struct Scene {
     float *pos = nullptr;       // [3, n] centres (SoA)
     float *size = nullptr;      // [3, n]
     float *views = nullptr;     // [n, n_views, kViewStride]
+    SpaceDesc spaces[FARM_MAX_SPACES];   // [1 ..]: further descriptor spaces (space 0 is desc_hi / desc_lo)
 };
 
 enum Buf {
@@ -91,6 +101,11 @@ enum Buf {
     B_CHUNK_VAL,    // float their values
     B_TOPS,         // float per-row group maxima of the tensor-core similarity (thresholded select)
     B_VARIANT,      // one piece and its tensor maps (farm_similarity_variant)
+    B_MC_SIM,       // float [n_ch, rows, ld] every channel's similarity block (fused batches)
+    B_MC_TOPS,      // float [n_ch, rows, group_stride] their group maxima
+    B_MC_TLIST,     // int32 [n_ch, n_q, R_t] per-channel target lists
+    B_MC_LLIST,     // int32 [n_ch, n_c, R_l] per-channel landmark lists
+    B_MC_FUSED,     // float [n_q, RF] fused scores of the kept target candidates
     B_COUNT
 };
 
@@ -432,8 +447,36 @@ struct ComposeArgs {
     float *out_score;
     float *out_t;               // [n_q, stride_t, 4]
     int32_t *out_anchor;
+    // fused batches: the target similarity F of each listed candidate
+    // ([n_q, stride_t]; s_sem = cf * F); null: s_sem = cf / (mu + rank)
+    const float *tsel_F = nullptr;
 };
 cudaError_t launch_compose(const ComposeArgs &a, cudaStream_t s);
+
+// Reciprocal-rank fusion of a batch's channels (k_fuse.cu).  Rows of every
+// channel's similarity block: the n_q target rows, then the n_c landmark rows.
+struct FuseArgs {
+    int64_t n_q, n_c;
+    int32_t n_ch;
+    float w[FARM_MAX_CHANNELS];  // channel weights
+    int32_t Rt, Rl;             // per-channel list lengths (target, landmark rows)
+    const int32_t *tlist;       // [n_ch, n_q, Rt]
+    const int32_t *llist;       // [n_ch, n_c, Rl]
+    const float *S;             // [n_ch, rows, ld]
+    int64_t rows, ld;
+    int32_t n;                  // objects of the scene
+    const int32_t *cls;         // [n]
+    int32_t *qmeta;             // [n_q, 8]: reads QM_CLS, writes QM_R (the kept count)
+    farm_params p;
+    int32_t RF;                 // kept target candidates per query (list stride)
+    int32_t *out_tidx;          // [n_q, RF] in (F desc, index asc) order
+    float *out_tF;              // [n_q, RF]
+    int32_t Ka;                 // landmark list length
+    int32_t *out_lidx;          // [n_c, Ka]
+    int32_t *err;               // device error word (kErrFusedOverflow)
+};
+// part 0: target rows, part 1: landmark rows.
+cudaError_t launch_fuse(const FuseArgs &a, int part, cudaStream_t s);
 
 // out[q * k + j] = src[perm[q] * ld + j] (and the 4-wide breakdown): the TopK
 // prefix of each query's sorted candidates, back in the caller's query order.

@@ -1,11 +1,12 @@
 // k_compose.cu -- relation evaluation, best-witness binding and composite
 // scoring of every kept target candidate (App. D.2 steps 4-5; App. B).
 //
-// One CTA per query; shared memory is sized by the batch's longest lists.
+// One CTA of 128 threads per query; shared memory is sized by the batch's longest lists.
 // The query's landmark candidates (K_a per constraint, in rank order) and
 // their centres are staged in shared memory.  For every
 // kept target candidate of rank r the CTA computes
 //   s_sem = cf / (mu + r)                       (cf = class_mis on a class mismatch)
+// (cf * F, F the fused score of several channels, for fused batches)
 // and the k_max-th largest s_sem, S_K.  k_max candidates score at least
 // (1 - w) S_K, so a candidate with s_sem < (1 - w) S_K cannot enter any TopK of
 // size <= k_max (its composite is at most s_sem); only the others are scored:
@@ -24,7 +25,7 @@
 namespace farm {
 namespace {
 
-constexpr int TH = 256;
+constexpr int TH = 128;      // small CTAs: more queries resident per SM to hide the dependent loads
 
 __device__ __forceinline__ float sigm(float x)
 {
@@ -88,6 +89,15 @@ __device__ float viewpoint_depth(const float *__restrict__ vs, int n_views, floa
     return counted ? acc / (float)counted : 0.5f;
 }
 
+// s + e = a + b exactly (Knuth's TwoSum; round-to-nearest FP32, no
+// reassociation: nvcc keeps IEEE semantics without fast-math).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bp = s - a, ap = s - bp;
+    e = (a - ap) + (b - bp);
+}
+
 // What a relation needs beyond the two objects: the candidate's staged views
 // and the query's Closest / Farthest candidate set (its kc best target
 // candidates, indices and centres).
@@ -101,11 +111,71 @@ struct RelCtx {
 
 // r_rho(e, a) (App. D.2 step 4).  ce: e's position in the query's target
 // list (rank - 1), which decides membership of the Closest / Farthest set.
-__device__ __forceinline__ float relation(int pred, int32_t e, int ce, float ex, float ey, float ez, float esz,
-                                          int32_t ai, float ax, float ay, float az, float asx, float asy,
-                                          float asz, const RelCtx &rc, const farm_params &p)
+__device__ __forceinline__ float relation(int pred, int32_t e, int ce, float ex, float ey, float ez, float esx,
+                                          float esy, float esz, int32_t ai, float ax, float ay, float az, float asx,
+                                          float asy, float asz, const RelCtx &rc, const farm_params &p)
 {
     switch (pred) {
+    case FARM_NEAR_H: {
+        // 1 - H with box-moment Gaussians (variance s^2 / 12 per axis):
+        // ln BC = sum_k 0.5 log(1 - (|s_e| - |s_a|)^2 / q) - 3 d^2 / q,
+        // q = s_e^2 + s_a^2, and H^2 = 1 - BC = -expm1(ln BC), which keeps
+        // its relative accuracy when the two Gaussians nearly coincide
+        const float se[3] = {fabsf(esx), fabsf(esy), fabsf(esz)}, sa[3] = {fabsf(asx), fabsf(asy), fabsf(asz)};
+        const float d[3] = {ex - ax, ey - ay, ez - az};
+        float lbc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float q = se[k] * se[k] + sa[k] * sa[k];
+            if (q == 0.f) {
+                if (d[k] != 0.f) return 0.f;      // two flat boxes at different levels
+                continue;
+            }
+            const float dd = se[k] - sa[k];
+            lbc += 0.5f * log1pf(-(dd * dd) / q) - 3.f * d[k] * d[k] / q;
+        }
+        // 1 - H = BC / (1 + H): no cancellation when BC is small either, where
+        // the geometric mean of App. D.2 step 5 would magnify a relative error
+        return expf(lbc) / (1.f + sqrtf(fmaxf(-expm1f(lbc), 0.f)));
+    }
+    case FARM_INSIDE: {
+        // the fraction of e's box inside a's box.  Per axis the overlap is
+        // 2 h_e, 2 h_a, or h_e + h_a -/+ (a - e) (h the half sizes); the last
+        // two are summed without rounding error until the final add (TwoSum),
+        // so that a thin overlap keeps its relative accuracy -- the geometric
+        // mean of App. D.2 step 5 magnifies the relative error of a small score
+        const float pe[3] = {ex, ey, ez}, pa[3] = {ax, ay, az};
+        const float he[3] = {0.5f * fabsf(esx), 0.5f * fabsf(esy), 0.5f * fabsf(esz)};
+        const float ha[3] = {0.5f * fabsf(asx), 0.5f * fabsf(asy), 0.5f * fabsf(asz)};
+        float frac = 1.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float d1, d2;                    // a - e = d1 + d2 exactly
+            two_sum(pa[k], -pe[k], d1, d2);
+            if (he[k] == 0.f) {
+                if (!(fabsf(d1) <= ha[k])) return 0.f;
+                continue;
+            }
+            const bool top_e = he[k] - ha[k] <= d1;       // e's upper face is the upper bound
+            const bool bot_e = d1 <= ha[k] - he[k];       // e's lower face is the lower bound
+            float ov;
+            if (top_e && bot_e) {
+                ov = 2.f * he[k];
+            } else if (!top_e && !bot_e) {
+                ov = 2.f * ha[k];
+            } else {
+                float t1, t2, u1, u2;
+                two_sum(he[k], ha[k], t1, t2);            // h_e + h_a = t1 + t2
+                const float sg = top_e ? -1.f : 1.f;      // top_e: h_e + h_a - (a - e); else + (a - e)
+                two_sum(t1, sg * d1, u1, u2);
+                ov = u1 + (u2 + (t2 + sg * d2));
+                ov = fminf(ov, 2.f * fminf(he[k], ha[k]));
+            }
+            if (!(ov > 0.f)) return 0.f;
+            frac *= ov / (2.f * he[k]);
+        }
+        return frac;
+    }
     case FARM_ABOVE: return sigm((ez - az) / p.tau_v);
     case FARM_BELOW: return sigm((az - ez) / p.tau_v);
     case FARM_NEAR:
@@ -174,7 +244,7 @@ struct ComposeSmem {
     }
 };
 
-__global__ void __launch_bounds__(TH)
+__global__ void __launch_bounds__(TH, 8)
 compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
 {
     extern __shared__ __align__(16) uint8_t sm[];
@@ -201,16 +271,19 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
     const int c_t = meta[QM_CLS];
     const int m = meta[QM_M];
     const int64_t c0 = meta[QM_C0];
-    const int preds[4] = {meta[QM_PRED01] & 0xffff, (meta[QM_PRED01] >> 16) & 0xffff,
-                          meta[QM_PRED23] & 0xffff, (meta[QM_PRED23] >> 16) & 0xffff};
+    // the four predicate codes (each < 256) packed a byte apiece, so that a
+    // lane indexes them without a local-memory array
+    const uint32_t predw = (uint32_t)(meta[QM_PRED01] & 0xff) | (uint32_t)((meta[QM_PRED01] >> 16) & 0xff) << 8 |
+                           (uint32_t)(meta[QM_PRED23] & 0xff) << 16 | (uint32_t)((meta[QM_PRED23] >> 16) & 0xff) << 24;
+    auto pred_of = [predw](int i) { return (int)((predw >> (8 * i)) & 0xffu); };
     const int R = meta[QM_R];
     const int klm = meta[QM_KLM];
     const SceneDev sd = a.scenes[scene];
     const farm_params p = a.p;
     bool any_view = false;
     for (int i = 0; i < m; ++i)
-        any_view |= preds[i] == FARM_LEFT_OF || preds[i] == FARM_RIGHT_OF || preds[i] == FARM_IN_FRONT_OF ||
-                    preds[i] == FARM_BEHIND;
+        any_view |= pred_of(i) == FARM_LEFT_OF || pred_of(i) == FARM_RIGHT_OF || pred_of(i) == FARM_IN_FRONT_OF ||
+                    pred_of(i) == FARM_BEHIND;
     const int kc = min(min(p.k_closest, R), KC);     // the Closest / Farthest set: target ranks 1..kc
 
     // (an index outside the scene never reaches a memory access: such a
@@ -233,7 +306,7 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
         const bool ok = e >= 0 && e < sd.n;
         cand_e[c] = ok ? e : -1;
         const float cf = (c_t >= 0 && ok && sd.cls[e] != c_t) ? p.class_mis : 1.f;
-        ssem[c] = ok ? cf / (p.mu + (float)(c + 1)) : -1.f;
+        ssem[c] = ok ? (a.tsel_F ? cf * a.tsel_F[q * a.stride_t + c] : cf / (p.mu + (float)(c + 1))) : -1.f;
         if (c < kc) {
             cset_pos[3 * c + 0] = ok ? sd.pos[e] : 0.f;
             cset_pos[3 * c + 1] = ok ? sd.pos[sd.n + e] : 0.f;
@@ -258,7 +331,7 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
     __syncthreads();
     const float thr = s_thr;
     for (int c = tid; c < R; c += TH) {
-        if (ssem[c] >= thr) {
+        if (ssem[c] >= thr && cand_e[c] >= 0) {
             const int pos = atomicAdd(&s_ns, 1);
             surv[pos] = (uint16_t)c;
         }
@@ -275,8 +348,7 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
         const int ce = surv[pos];
         const int32_t e = cand_e[ce];
         const float ex = sd.pos[e], ey = sd.pos[sd.n + e], ez = sd.pos[2 * sd.n + e];
-        const float esz = sd.size[2 * sd.n + e];
-        if (lane < FARM_MAX_CONSTRAINTS) best[pos * FARM_MAX_CONSTRAINTS + lane] = 0ull;
+        const float esx = sd.size[e], esy = sd.size[sd.n + e], esz = sd.size[2 * sd.n + e];
         if (any_view && lane < sd.n_views) {
             const float *ve = sd.views + ((int64_t)e * sd.n_views + lane) * kViewStride;
             const float4 o = *reinterpret_cast<const float4 *>(ve);        // ox, oy, oz, fx
@@ -290,17 +362,31 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
             *reinterpret_cast<float2 *>(slotv + 8) = make_float2(Ze, ue);
         }
         __syncwarp();
+        // each lane keeps its best (r, ~index) per constraint; r >= 0, so its
+        // bits order like the float, and a zero word means no witness
+        uint32_t bh[FARM_MAX_CONSTRAINTS] = {0u, 0u, 0u, 0u}, bl[FARM_MAX_CONSTRAINTS] = {0u, 0u, 0u, 0u};
         for (int t = lane; t < per; t += 32) {
             const int i = t / klm, l = t - i * klm;
             const int32_t ai = lm_idx[i * KM + l];
             if (ai == e || ai < 0) continue;
             const float *ap = lm_pos + (i * KM + l) * 3;
             const float *as = lm_size + (i * KM + l) * 3;
-            const float r = relation(preds[i], e, ce, ex, ey, ez, esz, ai, ap[0], ap[1], ap[2], as[0], as[1], as[2],
+            const float r = relation(pred_of(i), e, ce, ex, ey, ez, esx, esy, esz, ai, ap[0], ap[1], ap[2], as[0], as[1], as[2],
                                      rc, p);
-            const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) |
-                                         (unsigned long long)(0xffffffffu - (uint32_t)ai);
-            atomicMax(&best[pos * FARM_MAX_CONSTRAINTS + i], k);
+            const uint32_t h = __float_as_uint(r), lo = 0xffffffffu - (uint32_t)ai;
+#pragma unroll
+            for (int c = 0; c < FARM_MAX_CONSTRAINTS; ++c) {
+                if (c == i && (h > bh[c] || (h == bh[c] && lo > bl[c]))) { bh[c] = h; bl[c] = lo; }
+            }
+        }
+        // the warp's best per constraint: the largest r, then among the lanes
+        // holding it the largest ~index (the lower landmark index)
+#pragma unroll
+        for (int c = 0; c < FARM_MAX_CONSTRAINTS; ++c) {
+            if (c >= m) break;
+            const uint32_t h = __reduce_max_sync(0xffffffffu, bh[c]);
+            const uint32_t lo = __reduce_max_sync(0xffffffffu, bh[c] == h ? bl[c] : 0u);
+            if (lane == 0) best[pos * FARM_MAX_CONSTRAINTS + c] = ((unsigned long long)h << 32) | lo;
         }
         __syncwarp();      // the warp's view slot is rewritten for its next survivor
     }
@@ -345,8 +431,10 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
             __syncthreads();
         }
     }
+    // only a TopK prefix of at most k_max entries is ever read
     const int64_t ob = q * a.stride_t;
-    for (int c = tid; c < a.stride_t; c += TH) {
+    const int n_out = min(a.stride_t, max(p.k_max, 1));
+    for (int c = tid; c < n_out; c += TH) {
         if (c < ns) {
             const int pos = slot[c];
             const uint32_t kk = (uint32_t)(key[c] >> 32);

@@ -21,6 +21,9 @@ PREC_FP32_SIMT = 3
 PREC_LEARNED = 4
 PTR_DEVICE = 1
 GRAPH = 2          # FARM_GRAPH
+# predicate codes (farm_pred)
+(ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND, CLOSEST, FARTHEST, NEAR_H,
+ INSIDE) = range(13)
 N_STAGES = 4
 STATUS = {0: "FARM_OK", 1: "FARM_EINVAL", 2: "FARM_ENOMEM", 3: "FARM_ECUDA", 4: "FARM_ESTATE",
           5: "FARM_ETIMEOUT"}
@@ -53,6 +56,8 @@ def _load():
         "farm_destroy": (C.c_int, [P]),
         "farm_memory_upload": (C.c_int, [P, I32, I64, I32, P, P, P, I32, P, U32]),
         "farm_query_batch": (C.c_int, [P, I64, P, P, P, P, P, P, I32, U32, P]),
+        "farm_memory_add_space": (C.c_int, [P, I32, I32, I32, P, U32]),
+        "farm_query_batch_rrf": (C.c_int, [P, I32, I64, I32, P, P, P, P, P, P, U32, P]),
         "farm_topk": (C.c_int, [P, U64, I32, P, P, P, P, U32]),
         "farm_sync": (C.c_int, [P]),
         "farm_similarity": (C.c_int, [P, I32, I64, P, I32, P, U32]),
@@ -85,7 +90,7 @@ _lib = _load()
 
 def exported_symbols():
     return ["farm_default_params", "farm_create", "farm_destroy", "farm_memory_upload",
-            "farm_query_batch", "farm_topk", "farm_sync", "farm_similarity", "farm_scene_info",
+            "farm_query_batch", "farm_memory_add_space", "farm_query_batch_rrf", "farm_topk", "farm_sync", "farm_similarity", "farm_scene_info",
             "farm_select_fallbacks", "farm_sim_tuning", "farm_sim_variant_pin", "farm_similarity_variant",
             "farm_candidates",
             "farm_rank_rows_noalloc", "farm_mlp_set", "farm_mlp_get", "farm_mlp_loss_grad",
@@ -189,6 +194,43 @@ def farm_query_batch(ctx, scene_of_q, tgt_emb, tgt_cls, c_off, c_pred, c_emb,
     h = C.c_uint64()
     _ck(ctx, _lib.farm_query_batch(ctx, n_q, s.ptr, te.ptr, tc.ptr, co.ptr, cp.ptr, ce.ptr,
                                    int(precision), flags, C.byref(h)))
+    return int(h.value)
+
+
+class FarmChannel(C.Structure):
+    _fields_ = [("space", C.c_int32), ("weight", C.c_float)]
+
+
+def farm_memory_add_space(ctx, scene_id: int, space: int, desc) -> None:
+    """Store descriptor space `space` (>= 1) of an uploaded scene (see farm.h)."""
+    d = _Arr(desc, np.float32, "desc")
+    _ck(ctx, _lib.farm_memory_add_space(ctx, int(scene_id), int(space), int(desc.shape[1]), d.ptr, _flags(d)))
+
+
+def farm_query_batch_rrf(ctx, scene_id: int, channels, tgt_embs, tgt_cls, c_off, c_pred, c_embs) -> int:
+    """Enqueue a fused batch over several channels (see farm.h).  channels:
+    [(space, weight)]; tgt_embs / c_embs: either one [n_q, dim] / [n_c, dim]
+    array per channel (all numpy, or all CUDA tensors; laid end to end for the
+    call) or one flat FP32 array already laid out channel after channel."""
+    n_q = int(len(tgt_cls))
+    chs = (FarmChannel * len(channels))(*[FarmChannel(int(sp), float(w)) for sp, w in channels])
+
+    def flat(xs):
+        if not isinstance(xs, (list, tuple)):
+            return xs
+        if all(_is_cuda_tensor(x) for x in xs):
+            import torch
+            return torch.cat([x.reshape(-1).float() for x in xs])
+        return np.concatenate([np.asarray(x, np.float32).ravel() for x in xs])
+    tflat, cflat = flat(tgt_embs), flat(c_embs)
+    te = _Arr(tflat, np.float32, "tgt_emb")
+    ce = _Arr(cflat if len(cflat) else None, np.float32, "c_emb")
+    tc = _Arr(tgt_cls, np.int32, "tgt_cls", allow_device=False)
+    co = _Arr(c_off, np.int32, "c_off", allow_device=False)
+    cp = _Arr(c_pred, np.int32, "c_pred", allow_device=False)
+    h = C.c_uint64()
+    _ck(ctx, _lib.farm_query_batch_rrf(ctx, int(scene_id), n_q, len(channels), chs, te.ptr, tc.ptr, co.ptr, cp.ptr,
+                                       ce.ptr, _flags(te, ce), C.byref(h)))
     return int(h.value)
 
 

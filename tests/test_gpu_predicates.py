@@ -1,8 +1,9 @@
 """GPU parity for the further predicates of App. D.2 step 4 (NextTo, On,
-InFrontOf, Behind, Closest, Farthest) next to the first five, through the C
-ABI, against the FP64 oracle with the tie-tolerant checker.
+InFrontOf, Behind, Closest, Farthest, Inside) and the Hellinger form of Near
+(Sec. 2.3) next to the first five, through the C ABI, against the FP64 oracle
+with the tie-tolerant checker.
 
-Queries draw every constraint's predicate uniformly from all eleven codes;
+Queries draw every constraint's predicate uniformly from all thirteen codes;
 the scenes are the room (200 objects, 4 views) and a slice of the
 20,000-object site (8 views), plus a hand-built scene whose answer is fixed.
 """
@@ -15,7 +16,7 @@ from synth import QueryBatch
 
 pytestmark = pytest.mark.gpu
 
-ALL = list(range(11))
+ALL = list(range(13))
 
 
 @pytest.fixture(scope="module")
@@ -115,5 +116,23 @@ def test_hand_built_scene(F, ctx, pred, expect):
                     c_emb=np.eye(1, 8, lm, dtype=np.float32), scene_of_q=np.array([62], np.int32))
     h, out = _run(F, ctx, qb, F.PREC_FP32, k=2)
     assert int(out["idx"][0, 0]) == expect
+    rep = parity.check_topk(sc, qb, 2, out["idx"], out["score"], out["pred"], out["anchor"])
+    assert rep.ok(), rep.summary()
+
+
+def test_hand_built_inside(F, ctx):
+    """'mug inside the table's box': with mug 1 lowered into the table's
+    volume it is chosen over the semantically preferred mug 0 (which scores
+    s_sem / 2 = 1/12 against mug 1's 1/7)."""
+    sc = _hand_scene()
+    sc.box[2, 1] = 0.35            # mug 1 now lies wholly inside the table's box
+    F.farm_memory_upload(ctx, 63, sc.desc, sc.cls, sc.box, sc.views)
+    qb = QueryBatch(tgt_emb=np.eye(1, 8, dtype=np.float32), tgt_cls=np.array([0], np.int32),
+                    c_off=np.array([0, 1], np.int32), c_pred=np.array([12], np.int32),
+                    c_emb=np.eye(1, 8, 1, dtype=np.float32), scene_of_q=np.array([63], np.int32))
+    h, out = _run(F, ctx, qb, F.PREC_FP32, k=2)
+    assert int(out["idx"][0, 0]) == 1 and int(out["anchor"][0, 0, 0]) == 2
+    assert float(out["pred"][0, 0, 0]) == 1.0
+    assert float(out["score"][0, 0]) == pytest.approx(1.0 / 7.0, rel=1e-6)
     rep = parity.check_topk(sc, qb, 2, out["idx"], out["score"], out["pred"], out["anchor"])
     assert rep.ok(), rep.summary()
