@@ -795,7 +795,13 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     CK(ws_get(ctx, farm::B_SIM, (size_t)s_need, &d_sim));
     if (tile_tops) CK(ws_get(ctx, farm::B_TOPS, (size_t)tops_need, &d_tops));
     bool any_chunked = false;
-    for (const auto &bt : batches) any_chunked |= bt.chunked;
+    int64_t tblocks_max = 1;
+    for (const auto &bt : batches) {
+        any_chunked |= bt.chunked;
+        tblocks_max = std::max(tblocks_max, bt.tblocks);
+    }
+    int32_t *d_rowlist;
+    CK(ws_get(ctx, farm::B_SELLIST, (size_t)tblocks_max + 1, &d_rowlist));
     if (any_chunked) {
         CK(ws_get(ctx, farm::B_CHUNK_IDX, (size_t)tmp_need, &tmp_idx));
         CK(ws_get(ctx, farm::B_CHUNK_VAL, (size_t)tmp_need, &tmp_val));
@@ -1003,7 +1009,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                                                  sel_ti, sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.stream));
             if (bt.tblocks > 0)
                 LAUNCH(farm::launch_select_thresh(d_sim, d_tops, dp, (int32_t)bt.np, bt.tblocks, bt.max_union, sel_ti,
-                                                  sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.d_fallback, c.stream));
+                                                  sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.d_fallback, d_rowlist,
+                                                  c.stream));
             for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
                 const farm::Piece &pc = pieces[k];
                 if (pc.chunks != 0 || pc.th0 == 0) continue;
@@ -1270,6 +1277,8 @@ farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, i
     if (!dev) CK(ws_get(ctx, farm::B_RAW, (size_t)(emb_t + emb_c), &d_raw));
     uint8_t *d_pieces;
     CK(ws_get(ctx, farm::B_PIECES, (size_t)n_ch * sizeof(farm::Piece), &d_pieces));
+    int32_t *d_rowlist;
+    CK(ws_get(ctx, farm::B_SELLIST, (size_t)rows + 1, &d_rowlist));
 
     // ---- metadata (caller order is the planned order), select pieces
     std::vector<int32_t> meta((size_t)n_q * 8), perm((size_t)n_q);
@@ -1362,7 +1371,7 @@ farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, i
         if (th0 < rows)
             LAUNCH(farm::launch_select_thresh(d_sim, d_tops, reinterpret_cast<farm::Piece *>(d_pieces) + k, 1,
                                               rows - th0, uni, tl, nullptr, Rt, ll, nullptr, Rl, c.d_fallback,
-                                              c.stream));
+                                              d_rowlist, c.stream));
         mark_end(ctx, m2);
     }
 

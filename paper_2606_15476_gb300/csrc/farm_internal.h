@@ -106,6 +106,7 @@ enum Buf {
     B_MC_TLIST,     // int32 [n_ch, n_q, R_t] per-channel target lists
     B_MC_LLIST,     // int32 [n_ch, n_c, R_l] per-channel landmark lists
     B_MC_FUSED,     // float [n_q, RF] fused scores of the kept target candidates
+    B_SELLIST,      // int32 [1 + rows] rows the warp-level select hands to the block-level one
     B_COUNT
 };
 
@@ -384,10 +385,14 @@ cudaError_t launch_merge_chunks(const Piece *pieces, int32_t n_pieces, int64_t t
 // max_union: the largest group count of the launch (at most 8,192 are used).  Rows
 // whose candidates overflow fall back to an exact global-memory select and
 // are counted in *n_fallback (device).  Outputs as launch_select_grouped.
+// With row_list (device, total_blocks + 1 int32 of scratch) a warp-level
+// select takes every row of a list of at most 128 entries and at most 1,024
+// group maxima first (one warp per row, no block barriers) and hands the
+// rest to the block-level select; both give the same lists.
 cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,
                                  int64_t total_blocks, int32_t max_union, int32_t *tsel_idx, float *tsel_cos,
                                  int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
-                                 int32_t *n_fallback, cudaStream_t s);
+                                 int32_t *n_fallback, int32_t *row_list, cudaStream_t s);
 // Grouped FP32 rescore (one block per launch row): the keep_t / keep_l
 // candidates of bsel_* (strides cstride_t / cstride_l; descending by their
 // reduced-precision values bsel_tv / bsel_lv, nullable) are re-scored with

@@ -71,23 +71,31 @@ __device__ __forceinline__ void stream_tail(const float *__restrict__ row, int j
     }
 }
 
-__global__ void __launch_bounds__(TT)
-select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops, const Piece *__restrict__ pieces,
-                     int32_t n_pieces, int32_t *__restrict__ tsel_idx, float *__restrict__ tsel_cos, int32_t stride_t,
-                     int32_t *__restrict__ lsel_idx, float *__restrict__ lsel_cos, int32_t stride_l,
-                     int32_t *__restrict__ n_fallback)
+// Shared memory of one CTA of the block-level select.
+struct ThreshSmem {
+    uint32_t *ukeys;        // staged group maxima or a short row (dynamic)
+    uint64_t *cand;         // CAP candidate words
+    uint32_t *hist;         // radix histogram, then the list of qualifying groups (2048 words)
+    uint32_t *wsum, *s3;
+    int *s_cnt, *s_ng, *s_misc;
+};
+
+// The block-level select of thresholded row b (ends with the row written;
+// the caller separates rows by a barrier).
+__device__ __forceinline__ void thresh_row(const float *__restrict__ S, const float *__restrict__ tops,
+                                           const Piece *__restrict__ pieces, int32_t n_pieces, int64_t b,
+                                           int32_t *__restrict__ tsel_idx, float *__restrict__ tsel_cos,
+                                           int32_t stride_t, int32_t *__restrict__ lsel_idx,
+                                           float *__restrict__ lsel_cos, int32_t stride_l,
+                                           int32_t *__restrict__ n_fallback, const ThreshSmem &sm)
 {
-    extern __shared__ uint32_t ukeys[];
-    __shared__ uint64_t cand[CAP];
-    __shared__ uint32_t hist[2048];     // radix histogram, then the list of qualifying groups
-    __shared__ uint32_t wsum[TT / 32];
-    __shared__ uint32_t s3[3];
-    __shared__ int s_cnt, s_ng;
-    __shared__ int s_misc[TT / 32 + 3];
+    uint32_t *ukeys = sm.ukeys, *hist = sm.hist, *wsum = sm.wsum, *s3 = sm.s3;
+    uint64_t *cand = sm.cand;
+    int &s_cnt = *sm.s_cnt, &s_ng = *sm.s_ng;
+    int *s_misc = sm.s_misc;
     static_assert(GLIST <= 2048, "the group list reuses the histogram");
 
     const int tid = threadIdx.x;
-    const int64_t b = blockIdx.x;
     const Piece pc = pieces[find_piece(pieces, n_pieces, b, [](const Piece &x) { return x.tblock_begin; })];
     const int i = pc.th0 + (int)(b - pc.tblock_begin);
     const bool is_tgt = i < pc.ntr;
@@ -198,12 +206,195 @@ select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops
     }
 }
 
+#define THRESH_SMEM                                   \
+    extern __shared__ uint32_t ukeys[];               \
+    __shared__ uint64_t cand[CAP];                    \
+    __shared__ uint32_t hist[2048];                   \
+    __shared__ uint32_t wsum[TT / 32];                \
+    __shared__ uint32_t s3[3];                        \
+    __shared__ int s_cnt, s_ng;                       \
+    __shared__ int s_misc[TT / 32 + 3];               \
+    const ThreshSmem sm{ukeys, cand, hist, wsum, s3, &s_cnt, &s_ng, s_misc};
+
+// One CTA per thresholded row.
+__global__ void __launch_bounds__(TT)
+select_thresh_kernel(const float *__restrict__ S, const float *__restrict__ tops, const Piece *__restrict__ pieces,
+                     int32_t n_pieces, int32_t *__restrict__ tsel_idx, float *__restrict__ tsel_cos, int32_t stride_t,
+                     int32_t *__restrict__ lsel_idx, float *__restrict__ lsel_cos, int32_t stride_l,
+                     int32_t *__restrict__ n_fallback)
+{
+    THRESH_SMEM
+    thresh_row(S, tops, pieces, n_pieces, blockIdx.x, tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos, stride_l,
+               n_fallback, sm);
+}
+
+// The rows the warp-level select handed on (row_list[0] of them, listed
+// from row_list[1]), a grid-stride loop of CTAs.
+__global__ void __launch_bounds__(TT)
+select_thresh_list_kernel(const float *__restrict__ S, const float *__restrict__ tops,
+                          const Piece *__restrict__ pieces, int32_t n_pieces, int32_t *__restrict__ tsel_idx,
+                          float *__restrict__ tsel_cos, int32_t stride_t, int32_t *__restrict__ lsel_idx,
+                          float *__restrict__ lsel_cos, int32_t stride_l, int32_t *__restrict__ n_fallback,
+                          const int32_t *__restrict__ row_list)
+{
+    THRESH_SMEM
+    const int count = row_list[0];
+    for (int k = blockIdx.x; k < count; k += gridDim.x) {
+        thresh_row(S, tops, pieces, n_pieces, row_list[1 + k], tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos,
+                   stride_l, n_fallback, sm);
+        __syncthreads();            // the next row reuses the shared arrays
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level select: one warp per row for the common case -- a list of at
+// most WS_R entries, at most 1,024 group maxima -- with no block barriers.
+// The R-th largest group-maximum key T is found by a bitwise search (the
+// largest T with #{keys >= T} >= R), the groups whose maximum reaches it are
+// gathered, and the candidates are ranked by counting (their words are all
+// distinct).  A row outside these limits, or whose groups or candidates
+// overflow the warp's buffers, is appended to row_list for the block-level
+// select.
+constexpr int WS_R = 128;       // longest list a warp selects
+constexpr int WS_KPL = 32;      // group maxima per lane (1,024 per row)
+constexpr int WS_GL = 256;      // qualifying groups per warp
+constexpr int WS_CAP = 256;     // candidate words per warp
+constexpr int WW = 8;           // warps (rows) per CTA
+
+__global__ void __launch_bounds__(WW * 32)
+select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, const Piece *__restrict__ pieces,
+                   int32_t n_pieces, int64_t total_rows, int32_t *__restrict__ tsel_idx,
+                   float *__restrict__ tsel_cos, int32_t stride_t, int32_t *__restrict__ lsel_idx,
+                   float *__restrict__ lsel_cos, int32_t stride_l, int32_t *__restrict__ row_list)
+{
+    __shared__ uint32_t glist_all[WW][WS_GL];
+    __shared__ uint64_t cand_all[WW][WS_CAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t t = (int64_t)blockIdx.x * WW + warp;
+    if (t >= total_rows) return;            // (warp-uniform)
+    uint32_t *glist = glist_all[warp];
+    uint64_t *cand = cand_all[warp];
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+    auto hand_on = [&]() {
+        if (lane == 0) row_list[1 + atomicAdd(&row_list[0], 1)] = (int32_t)t;
+    };
+    // the piece of thresholded row t (the last whose tblock_begin <= t)
+    int lo = 0, hi = n_pieces - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pieces[mid].tblock_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const Piece &pc = pieces[lo];
+    const int i = pc.th0 + (int)(t - pc.tblock_begin);
+    const bool is_tgt = i < pc.ntr;
+    const int R = is_tgt ? pc.keep_t : pc.keep_l;
+    const int n = pc.n;
+    const int gshift = pc.gshift;
+    const int64_t n_groups = group_count(n, gshift);
+    if (R > WS_R || n_groups > 32 * WS_KPL || n_groups < R) { hand_on(); return; }
+    const int U = (int)n_groups;
+    const int kpl = (U + 31) >> 5;
+    const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(n, gshift);
+    uint32_t key[WS_KPL];
+#pragma unroll
+    for (int k = 0; k < WS_KPL; ++k) {
+        const int g = lane + 32 * k;
+        key[k] = (k < kpl && g < U) ? order_key(__ldg(tp + g)) : 0u;    // 0: below every key of a value
+    }
+    // T: the R-th largest key
+    uint32_t T = 0;
+    for (int bit = 31; bit >= 0; --bit) {
+        const uint32_t c = T | (1u << bit);
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < WS_KPL; ++k) cnt += (k < kpl && key[k] >= c) ? 1 : 0;
+        if (__reduce_add_sync(FULL, (unsigned)cnt) >= (unsigned)R) T = c;
+    }
+    // the groups whose maximum reaches T
+    int ng = 0;
+#pragma unroll
+    for (int k = 0; k < WS_KPL; ++k) {
+        if (k >= kpl) break;
+        const bool q = key[k] >= T;
+        const unsigned bal = __ballot_sync(FULL, q);
+        if (q) {
+            const int pos = ng + __popc(bal & lt);
+            if (pos < WS_GL) glist[pos] = (uint32_t)(lane + 32 * k);
+        }
+        ng += __popc(bal);
+    }
+    if (ng > WS_GL) { hand_on(); return; }
+    __syncwarp();
+    // their entries >= tau
+    const float tau = key_value(T);
+    const float *row = S + pc.s_off + (int64_t)i * pc.ld;
+    const int gmask = (1 << gshift) - 1;
+    const int slots = ng << gshift;
+    int cnt = 0;
+    for (int s0 = 0; s0 < slots; s0 += 32 * 4) {
+        float x[4];
+        int j[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int sl = s0 + 32 * u + lane;
+            j[u] = -1;
+            if (sl < slots) {
+                const int jj = (int)((glist[sl >> gshift] << gshift) + (sl & gmask));
+                if (jj < n) j[u] = jj;
+            }
+            x[u] = j[u] >= 0 ? __ldcs(row + j[u]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool q = j[u] >= 0 && x[u] >= tau;
+            const unsigned bal = __ballot_sync(FULL, q);
+            if (q) {
+                const int pos = cnt + __popc(bal & lt);
+                if (pos < WS_CAP) cand[pos] = cand_word(order_key(x[u]), j[u]);
+            }
+            cnt += __popc(bal);
+        }
+    }
+    if (cnt > WS_CAP || cnt < R) { hand_on(); return; }
+    __syncwarp();
+    // rank by counting: the words are distinct (distinct positions)
+    int32_t *oi;
+    float *oc;
+    int stride;
+    if (is_tgt) {
+        const int64_t o = (pc.t_row0 + i) * (int64_t)stride_t;
+        oi = tsel_idx + o;
+        oc = tsel_cos ? tsel_cos + o : nullptr;
+        stride = stride_t;
+    } else {
+        const int64_t o = (pc.l_row0 + (i - pc.ntr)) * (int64_t)stride_l;
+        oi = lsel_idx + o;
+        oc = lsel_cos ? lsel_cos + o : nullptr;
+        stride = stride_l;
+    }
+    for (int ci = lane; ci < cnt; ci += 32) {
+        const uint64_t w = cand[ci];
+        int r = 0;
+        for (int k = 0; k < cnt; ++k) r += cand[k] > w ? 1 : 0;
+        if (r < R) {
+            oi[r] = (int32_t)(0xffffffffu - (uint32_t)(w & 0xffffffffu));
+            if (oc) oc[r] = key_value((uint32_t)(w >> 32));
+        }
+    }
+    for (int k = R + lane; k < stride; k += 32) {
+        oi[k] = -1;
+        if (oc) oc[k] = 0.f;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,
                                  int64_t total_blocks, int32_t max_union, int32_t *tsel_idx, float *tsel_cos,
                                  int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
-                                 int32_t *n_fallback, cudaStream_t s)
+                                 int32_t *n_fallback, int32_t *row_list, cudaStream_t s)
 {
     if (total_blocks <= 0) return cudaSuccess;
     if (n_pieces < 1 || total_blocks > 0x7fffffff || max_union < 1 || ((uintptr_t)S & 15u) != 0 ||
@@ -213,10 +404,26 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
     const int32_t staged = max_union < UNION_MAX ? (max_union > kSelectSortAll ? max_union : kSelectSortAll) : UNION_MAX;
     const size_t smem = (size_t)staged * sizeof(uint32_t);
     static_assert(CAP >= kSelectSortAll, "rows that take every entry fit the candidate buffer");
-    cudaError_t e = cudaFuncSetAttribute(select_thresh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e;
+    if (!row_list) {
+        e = cudaFuncSetAttribute(select_thresh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        select_thresh_kernel<<<(unsigned)total_blocks, TT, smem, s>>>(S, tops, pieces, n_pieces, tsel_idx, tsel_cos,
+                                                                      stride_t, lsel_idx, lsel_cos, stride_l,
+                                                                      n_fallback);
+        return cudaGetLastError();
+    }
+    // the warp-level select first; the rows it hands on go to the block-level one
+    if ((e = cudaMemsetAsync(row_list, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    select_warp_kernel<<<(unsigned)((total_blocks + WW - 1) / WW), WW * 32, 0, s>>>(
+        S, tops, pieces, n_pieces, total_blocks, tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos, stride_l, row_list);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(select_thresh_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    select_thresh_kernel<<<(unsigned)total_blocks, TT, smem, s>>>(S, tops, pieces, n_pieces, tsel_idx, tsel_cos,
-                                                                  stride_t, lsel_idx, lsel_cos, stride_l, n_fallback);
+    const int64_t grid = total_blocks < 2048 ? total_blocks : 2048;
+    select_thresh_list_kernel<<<(unsigned)grid, TT, smem, s>>>(S, tops, pieces, n_pieces, tsel_idx, tsel_cos,
+                                                               stride_t, lsel_idx, lsel_cos, stride_l, n_fallback,
+                                                               row_list);
     return cudaGetLastError();
 }
 
