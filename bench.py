@@ -185,14 +185,15 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the similarity kernel, from one ncu capture per (workload, precision, tile
-# variant) -- profiles/sim_tc_f16x3_site_n20k.md and profiles/sim_tc_bf16_site_n20k.md --
-# valid only while the kernel source is the one captured (sha256 prefix).
+# variant), valid only while the kernel source is the one captured (sha256
+# prefix).
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 0): 715.797504e6 + 1122.223e6,
-    ("site_n20k_d1152", "fp32", 1): 1352.835e6 + 1133.660e6,
-    ("site_n20k_d1152", "bf16", 0): 359.154432e6 + 1117.139e6,
+    ("site_n20k_d1152", "fp32", 0): 717.308160e6 + 1121.947648e6,
+    ("site_n20k_d1152", "fp32", 1): 1354.266624e6 + 1133.388032e6,
+    ("site_n20k_d1152", "bf16", 0): 359.175680e6 + 1116.801536e6,
+    ("site_n20k_d1152", "bf16", 1): 664.022528e6 + 1117.387776e6,
 }
-SIM_TRAFFIC_SOURCE = "65ea3e3203eb11ae"
+SIM_TRAFFIC_SOURCE = "92b2f337ec7b8c77"
 
 
 def sim_traffic(workload, precision, variants):
@@ -307,6 +308,8 @@ def main():
                     help="pin the similarity kernel's tile variant (0-3) instead of autotuning it")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the timed steps directly instead of as CUDA graphs (FARM_GRAPH)")
+    ap.add_argument("--queries", type=int, default=0,
+                    help="time only the workload's first N queries (profiling captures of a smaller case)")
     ap.add_argument("--channels", default="one", choices=["one", "paper"],
                     help="'paper': reciprocal-rank fusion over four query channels in three descriptor "
                          "spaces (the scene's, a 1,024-d and a 2,048-d one; weights 1.0 / 0.5 / 0.75 / 1.0)")
@@ -336,6 +339,8 @@ def main():
     import synth
 
     scenes, qb = synth.workload(args.workload)
+    if args.queries > 0:
+        qb = qb.subset(np.arange(min(args.queries, qb.n_q)))
     sc = scenes[0]
     prec = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16,
             "fp8": F.PREC_FP8, "learned": F.PREC_LEARNED}[args.precision]
