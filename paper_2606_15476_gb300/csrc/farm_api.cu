@@ -1389,6 +1389,9 @@ farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, i
     fa.S = d_sim;
     fa.rows = rows;
     fa.ld = ld;
+    fa.tops = d_tops;
+    fa.gstride = gstride;
+    fa.gshift = gshift;
     fa.n = (int32_t)n;
     fa.cls = s.cls;
     fa.qmeta = d_meta;

@@ -469,6 +469,9 @@ struct FuseArgs {
     const int32_t *llist;       // [n_ch, n_c, Rl]
     const float *S;             // [n_ch, rows, ld]
     int64_t rows, ld;
+    const float *tops;          // [n_ch, rows, gstride] group maxima of S (over 2^gshift objects)
+    int64_t gstride;
+    int32_t gshift;
     int32_t n;                  // objects of the scene
     const int32_t *cls;         // [n]
     int32_t *qmeta;             // [n_q, 8]: reads QM_CLS, writes QM_R (the kept count)

@@ -22,7 +22,8 @@
 //  4. their exact rank in each channel that did not list them, by counting
 //     the row's entries above them: rank = 1 + #{j : c_j > c_e, or equal and
 //     j < e} (the probes sorted once, each entry of the row placed among them
-//     by binary search);
+//     by binary search; groups whose maximum -- from the similarity epilogue
+//     -- is below the smallest probe are skipped);
 //  5. exact F in FP32, and the kept members sorted by (F desc, index asc):
 //     a target row writes them (and their count to the query's metadata) for
 //     the compose kernel, a landmark row writes its first K_a.
@@ -244,8 +245,13 @@ fuse_kernel(FuseArgs a, int64_t b0, int32_t E, int32_t H, int32_t P2)
                     __syncthreads();
                 }
             }
-            // every entry j beats the probes whose key is below its own
+            // every entry j beats the probes whose key is below its own; an
+            // entry below the smallest probe's value beats none, so groups
+            // whose maximum is below it are not read
+            const float vmin = key_value((uint32_t)(probe[0] >> 32));
+            const float *trow = a.tops + ((int64_t)c * a.rows + row) * a.gstride;
             for (int j = tid; j < n; j += TF) {
+                if (trow[j >> a.gshift] < vmin) continue;
                 const uint64_t kj = entry_key(__ldcs(srow + j), j);
                 int lo = 0, hi = np;          // first probe with key >= kj
                 while (lo < hi) {

@@ -261,7 +261,7 @@ constexpr int WS_GL = 256;      // qualifying groups per warp
 constexpr int WS_CAP = 256;     // candidate words per warp
 constexpr int WW = 8;           // warps (rows) per CTA
 
-__global__ void __launch_bounds__(WW * 32)
+__global__ void __launch_bounds__(WW * 32, 4)
 select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, const Piece *__restrict__ pieces,
                    int32_t n_pieces, int64_t total_rows, int32_t *__restrict__ tsel_idx,
                    float *__restrict__ tsel_cos, int32_t stride_t, int32_t *__restrict__ lsel_idx,
@@ -303,14 +303,43 @@ select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, 
         const int g = lane + 32 * k;
         key[k] = (k < kpl && g < U) ? order_key(__ldg(tp + g)) : 0u;    // 0: below every key of a value
     }
-    // T: the R-th largest key
-    uint32_t T = 0;
-    for (int bit = 31; bit >= 0; --bit) {
-        const uint32_t c = T | (1u << bit);
-        int cnt = 0;
+    // T: the R-th largest key.  It lies between the smallest and the largest
+    // key, so it shares their common leading bits; the search sets the bits
+    // below them one at a time (keeping a bit while at least R keys reach
+    // it), and stops early once exactly R keys reach the candidate: T is
+    // then the smallest of those R.
+    uint32_t kmax = 0u, kmin = 0xffffffffu;
 #pragma unroll
-        for (int k = 0; k < WS_KPL; ++k) cnt += (k < kpl && key[k] >= c) ? 1 : 0;
-        if (__reduce_add_sync(FULL, (unsigned)cnt) >= (unsigned)R) T = c;
+    for (int k = 0; k < WS_KPL; ++k) {
+        if (k < kpl && lane + 32 * k < U) {
+            kmax = max(kmax, key[k]);
+            kmin = min(kmin, key[k]);
+        }
+    }
+    kmax = __reduce_max_sync(FULL, kmax);
+    kmin = __reduce_min_sync(FULL, kmin);
+    uint32_t T;
+    if (kmax == kmin) {
+        T = kmax;
+    } else {
+        const int hb = 31 - __clz(kmax ^ kmin);
+        T = hb == 31 ? 0u : (kmax >> (hb + 1)) << (hb + 1);
+        for (int bit = hb; bit >= 0; --bit) {
+            const uint32_t c = T | (1u << bit);
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < WS_KPL; ++k) cnt += (k < kpl && key[k] >= c) ? 1 : 0;
+            const unsigned tot = __reduce_add_sync(FULL, (unsigned)cnt);
+            if (tot == (unsigned)R) {
+                uint32_t mn = 0xffffffffu;
+#pragma unroll
+                for (int k = 0; k < WS_KPL; ++k)
+                    if (k < kpl && key[k] >= c) mn = min(mn, key[k]);
+                T = __reduce_min_sync(FULL, mn);
+                break;
+            }
+            if (tot > (unsigned)R) T = c;
+        }
     }
     // the groups whose maximum reaches T
     int ng = 0;
