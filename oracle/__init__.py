@@ -5,11 +5,11 @@ CPU-baseline leg import this package.  The product path (the CUDA library and
 its binding) never does.
 """
 from .oracle import (ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND,
-                     CLOSEST, FARTHEST, NEAR_H, INSIDE, OracleParams, build, load, cosines, ranks, relation,
+                     CLOSEST, FARTHEST, NEAR_H, INSIDE, BETWEEN, BETWEEN_AND, OracleParams, build, load, cosines, ranks, relation,
                      relation_in, sigmoid, query_all, query_bounds, batch, topk, num_threads,
-                     query_mc, query_bounds_mc)
+                     query_mc, query_bounds_mc, between)
 
 __all__ = ["ABOVE", "BELOW", "LEFT_OF", "RIGHT_OF", "NEAR", "NEXT_TO", "ON", "IN_FRONT_OF", "BEHIND",
-           "CLOSEST", "FARTHEST", "NEAR_H", "INSIDE", "OracleParams", "build", "load", "cosines", "ranks", "relation",
+           "CLOSEST", "FARTHEST", "NEAR_H", "INSIDE", "BETWEEN", "BETWEEN_AND", "OracleParams", "build", "load", "cosines", "ranks", "relation",
            "relation_in", "sigmoid", "query_all", "query_bounds", "batch", "topk", "num_threads",
-           "query_mc", "query_bounds_mc"]
+           "query_mc", "query_bounds_mc", "between"]

@@ -72,6 +72,19 @@
  *       of e's box volume that lies in a's box, the product over the three
  *       axes of |[e] cap [a]|_k / s_ek (an axis of zero extent contributes 1
  *       when e's coordinate lies in a's interval, else 0).
+ *       between(e, a_p, a_q): the ternary relation of App. B ("Between
+ *       couples only the variables it mentions"); the paper gives no
+ *       evaluator, the reading taken is: with the segment from a_p's centre to
+ *       a_q's, t = position of e's centre projected on it (0 at a_p, 1 at a_q)
+ *       and d its distance from the line,
+ *         between = sig(t / tau_b) sig((1 - t) / tau_b) exp(-d^2 / (2 sigma_near^2)),
+ *       tau_b = 0.1; 0 when the two centres coincide.  A Between occupies two
+ *       consecutive constraints (codes ORC_BETWEEN, ORC_BETWEEN_AND), each with
+ *       its own landmark embedding and candidate list, and is one factor of
+ *       the geometric mean of step 7; its witness is the best pair
+ *       (a_p, a_q) in L_p x L_q with a_p != a_q, neither the target (exact
+ *       bucket elimination of the pair, App. B), lower a_p then lower a_q on
+ *       ties; both constraints report that score.
  *  6. t_i(e) = max_{a in L_i, a != e} r_rho_i(e, a), 0 without a witness; the
  *     bound anchor is the argmax (lower object index on ties).
  *  7. gbar = (prod_i t_i)^(1/m) (0 if some t_i = 0, 1 if m = 0);
@@ -106,6 +119,8 @@
 #define ORC_FARTHEST 10
 #define ORC_NEAR_H 11
 #define ORC_INSIDE 12
+#define ORC_BETWEEN 13      /* first landmark of a Between pair: the next constraint is its second */
+#define ORC_BETWEEN_AND 14  /* second landmark of a Between pair */
 
 #define ORC_OK 0
 #define ORC_EINVAL -1
@@ -325,6 +340,95 @@ double orc_relation_in(const orc_scene *s, const orc_params *p, int32_t pred, in
     }
 }
 
+/* Between (step 5): e on the segment from a_p to a_q. */
+double orc_between(const orc_scene *s, const orc_params *p, int64_t e, int64_t ap, int64_t aq)
+{
+    double seg[3], rel[3], ss = 0.0, dot = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        seg[k] = center(s, k, aq) - center(s, k, ap);
+        rel[k] = center(s, k, e) - center(s, k, ap);
+        ss += seg[k] * seg[k];
+        dot += rel[k] * seg[k];
+    }
+    if (!(ss > 0.0)) return 0.0;
+    double t = dot / ss, d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double off = rel[k] - t * seg[k];
+        d2 += off * off;
+    }
+    const double tau_b = 0.1;
+    const double sg = p->sigma_near;
+    return orc_sigmoid(t / tau_b) * orc_sigmoid((1.0 - t) / tau_b) * exp(-0.5 * d2 / (sg * sg));
+}
+
+/* Bounds of a Between pair's score for candidate e: the best pair among the
+ * certain members (lists Dp, Dq: in_dp / in_dq flags over the possible
+ * lists) and among the possible members (Pp, Pq). */
+static void between_bounds(const orc_scene *s, const orc_params *p, int64_t e, const int64_t *Pp, int64_t np,
+                           const int8_t *dp, const int64_t *Pq, int64_t nq, const int8_t *dq, double *lo,
+                           double *hi)
+{
+    double l = 0.0, h = 0.0;
+    for (int64_t x = 0; x < np; ++x) {
+        int64_t ap = Pp[x];
+        if (ap == e) continue;
+        for (int64_t y = 0; y < nq; ++y) {
+            int64_t aq = Pq[y];
+            if (aq == e || aq == ap) continue;
+            double r = orc_between(s, p, e, ap, aq);
+            if (r > h) h = r;
+            if (dp[ap] && dq[aq] && r > l) l = r;
+        }
+    }
+    *lo = l;
+    *hi = h;
+}
+
+/* A query's constraint predicates form valid Between pairs. */
+static int pairs_ok(int32_t m, const int32_t *preds)
+{
+    for (int32_t i = 0; i < m; ++i) {
+        if (preds[i] == ORC_BETWEEN && !(i + 1 < m && preds[i + 1] == ORC_BETWEEN_AND)) return 0;
+        if (preds[i] == ORC_BETWEEN_AND && !(i > 0 && preds[i - 1] == ORC_BETWEEN)) return 0;
+    }
+    return 1;
+}
+
+/* The factors of step 7 from the per-constraint scores: a Between pair's two
+ * constraints carry one score and count once.  Returns their number. */
+static int32_t factors_of(int32_t m, const int32_t *preds, const double *t, double *f)
+{
+    int32_t k = 0;
+    for (int32_t i = 0; i < m; ++i)
+        if (preds[i] != ORC_BETWEEN_AND) f[k++] = t[i];
+    return k;
+}
+
+/* Step 6 for the Between pair (i, i+1): the best (a_p, a_q) over Lp x Lq. */
+static void between_witness(const orc_scene *s, const orc_params *p, int64_t e, const int64_t *Lp, int64_t np,
+                            const int64_t *Lq, int64_t nq, double *t_out, int64_t *ap_out, int64_t *aq_out)
+{
+    double best = 0.0;
+    int64_t bp = -1, bq = -1;
+    for (int64_t x = 0; x < np; ++x) {
+        int64_t ap = Lp[x];
+        if (ap == e) continue;
+        for (int64_t y = 0; y < nq; ++y) {
+            int64_t aq = Lq[y];
+            if (aq == e || aq == ap) continue;
+            double r = orc_between(s, p, e, ap, aq);
+            if (bp < 0 || r > best || (r == best && (ap < bp || (ap == bp && aq < bq)))) {
+                best = r;
+                bp = ap;
+                bq = aq;
+            }
+        }
+    }
+    *t_out = bp < 0 ? 0.0 : best;
+    *ap_out = bp;
+    *aq_out = bq;
+}
+
 double orc_relation(const orc_scene *s, const orc_params *p, int32_t pred, int64_t e, int64_t a)
 {
     return orc_relation_in(s, p, pred, e, a, NULL, 0);
@@ -431,17 +535,20 @@ int orc_query_all(const orc_scene *s, const orc_params *p, const float *u0, int3
 {
     int64_t n = s->n;
     if (n <= 0 || m < 0 || m > 64 || p->k_anchor < 1 || p->k_closest < 1) return ORC_EINVAL;
+    if (!pairs_ok(m, preds)) return ORC_EINVAL;
     int rc = ORC_OK;
     double *cos = (double *)malloc((size_t)n * sizeof(double));
     int64_t *rank = (int64_t *)malloc((size_t)n * sizeof(int64_t));
     double *t = (double *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(double));
     int64_t *anc = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(int64_t));
-    int64_t *lm = (int64_t *)malloc((size_t)p->k_anchor * sizeof(int64_t));
+    /* every constraint's L_i (a Between pair's second constraint needs the first's) */
+    int64_t *lm_all = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * (size_t)p->k_anchor * sizeof(int64_t));
+    int64_t n_lm_of[64];
     double *ssem = (double *)malloc((size_t)n * sizeof(double));
     int64_t kc = p->k_closest < n ? p->k_closest : n;
     int64_t *cset = (int64_t *)malloc((size_t)(kc > 0 ? kc : 1) * sizeof(int64_t));
     int64_t n_cset = 0;
-    if (!cos || !rank || !t || !anc || !lm || !ssem || !cset) { rc = ORC_ENOMEM; goto done; }
+    if (!cos || !rank || !t || !anc || !lm_all || !ssem || !cset) { rc = ORC_ENOMEM; goto done; }
 
     /* Steps 1-3 for the target row. */
     if ((rc = orc_cosines(s, u0, cos)) != ORC_OK) goto done;
@@ -462,11 +569,26 @@ int orc_query_all(const orc_scene *s, const orc_params *p, const float *u0, int3
         if ((rc = orc_cosines(s, u_c + (int64_t)i * s->dim, cos)) != ORC_OK) goto done;
         if ((rc = orc_ranks(n, cos, rank)) != ORC_OK) goto done;
         int64_t n_lm = 0;
+        int64_t *lm = lm_all + (int64_t)i * p->k_anchor;
         /* L_i in rank order: walk ranks 1..K_a. */
         int64_t ka = p->k_anchor < n ? p->k_anchor : n;
         for (int64_t r = 1; r <= ka; ++r)
             for (int64_t j = 0; j < n; ++j)
                 if (rank[j] == r) { lm[n_lm++] = j; break; }
+        n_lm_of[i] = n_lm;
+        if (preds[i] == ORC_BETWEEN) continue;     /* scored with its second constraint */
+        if (preds[i] == ORC_BETWEEN_AND) {
+            const int64_t *lp = lm_all + (int64_t)(i - 1) * p->k_anchor;
+            for (int64_t e = 0; e < n; ++e) {
+                double tb;
+                int64_t ap, aq;
+                between_witness(s, p, e, lp, n_lm_of[i - 1], lm, n_lm, &tb, &ap, &aq);
+                t[(int64_t)(i - 1) * n + e] = t[(int64_t)i * n + e] = tb;
+                anc[(int64_t)(i - 1) * n + e] = ap;
+                anc[(int64_t)i * n + e] = aq;
+            }
+            continue;
+        }
         for (int64_t e = 0; e < n; ++e) {
             double best = 0.0;
             int64_t arg = -1;
@@ -483,15 +605,16 @@ int orc_query_all(const orc_scene *s, const orc_params *p, const float *u0, int3
 
     /* Step 7. */
     for (int64_t e = 0; e < n; ++e) {
-        double te[64];
-        for (int32_t i = 0; i < m; ++i) te[i] = t[(int64_t)i * n + e];
-        double sc = compose(p, ssem[e], m, te);
+        double ts[64], te[64];
+        for (int32_t i = 0; i < m; ++i) ts[i] = t[(int64_t)i * n + e];
+        int32_t mf = factors_of(m, preds, ts, te);
+        double sc = compose(p, ssem[e], mf, te);
         if (s_out) s_out[e] = sc;
     }
     if (t_out) memcpy(t_out, t, (size_t)m * (size_t)n * sizeof(double));
     if (anchor_out) memcpy(anchor_out, anc, (size_t)m * (size_t)n * sizeof(int64_t));
 done:
-    free(cos); free(rank); free(t); free(anc); free(lm); free(ssem); free(cset);
+    free(cos); free(rank); free(t); free(anc); free(lm_all); free(ssem); free(cset);
     return rc;
 }
 
@@ -656,6 +779,7 @@ int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, i
 {
     int64_t n = s->n;
     if (n <= 0 || m < 0 || m > 64 || !(tau >= 0.0)) return ORC_EINVAL;
+    if (!pairs_ok(m, preds)) return ORC_EINVAL;
     int rc = ORC_OK;
     double *cos = (double *)malloc((size_t)n * sizeof(double));
     double *sorted = (double *)malloc((size_t)n * sizeof(double));
@@ -669,8 +793,11 @@ int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, i
     int8_t *c_d = (int8_t *)malloc((size_t)n);     /* certainly in the candidate set C */
     int8_t *c_p = (int8_t *)malloc((size_t)n);     /* possibly in C */
     int64_t *cset = (int64_t *)malloc((size_t)n * sizeof(int64_t));
-    int64_t n_cset = 0, n_cp = 0;
-    if (!cos || !sorted || !slo || !shi || !tlo || !thi || !in_d || !in_p || !plist || !c_d || !c_p || !cset) {
+    int64_t *prev_plist = (int64_t *)malloc((size_t)n * sizeof(int64_t));   /* a Between pair's first list */
+    int8_t *prev_in_d = (int8_t *)malloc((size_t)n);
+    int64_t n_prev = 0, n_cset = 0, n_cp = 0;
+    if (!cos || !sorted || !slo || !shi || !tlo || !thi || !in_d || !in_p || !plist || !c_d || !c_p || !cset ||
+        !prev_plist || !prev_in_d) {
         rc = ORC_ENOMEM;
         goto done;
     }
@@ -706,6 +833,21 @@ int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, i
         int64_t n_p = 0;
         for (int64_t a = 0; a < n; ++a)
             if (in_p[a]) plist[n_p++] = a;
+        if (preds[i] == ORC_BETWEEN) {
+            memcpy(prev_plist, plist, (size_t)n_p * sizeof(int64_t));
+            memcpy(prev_in_d, in_d, (size_t)n);
+            n_prev = n_p;
+            continue;
+        }
+        if (preds[i] == ORC_BETWEEN_AND) {
+            for (int64_t e = 0; e < n; ++e) {
+                double lo, hi;
+                between_bounds(s, p, e, prev_plist, n_prev, prev_in_d, plist, n_p, in_d, &lo, &hi);
+                tlo[(int64_t)(i - 1) * n + e] = tlo[(int64_t)i * n + e] = lo;
+                thi[(int64_t)(i - 1) * n + e] = thi[(int64_t)i * n + e] = hi;
+            }
+            continue;
+        }
         for (int64_t e = 0; e < n; ++e) {
             double lo = 0.0, hi = 0.0;
             const int ranked = preds[i] == ORC_CLOSEST || preds[i] == ORC_FARTHEST;
@@ -731,11 +873,13 @@ int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, i
         }
     }
     for (int64_t e = 0; e < n; ++e) {
-        double te[64];
-        for (int32_t i = 0; i < m; ++i) te[i] = tlo[(int64_t)i * n + e];
-        double a = compose(p, slo[e], m, te);
-        for (int32_t i = 0; i < m; ++i) te[i] = thi[(int64_t)i * n + e];
-        double b = compose(p, shi[e], m, te);
+        double ts[64], te[64];
+        for (int32_t i = 0; i < m; ++i) ts[i] = tlo[(int64_t)i * n + e];
+        int32_t mf = factors_of(m, preds, ts, te);
+        double a = compose(p, slo[e], mf, te);
+        for (int32_t i = 0; i < m; ++i) ts[i] = thi[(int64_t)i * n + e];
+        mf = factors_of(m, preds, ts, te);
+        double b = compose(p, shi[e], mf, te);
         if (s_lo) s_lo[e] = a;
         if (s_hi) s_hi[e] = b;
     }
@@ -743,7 +887,7 @@ int orc_query_bounds(const orc_scene *s, const orc_params *p, const float *u0, i
     if (t_hi_out) memcpy(t_hi_out, thi, (size_t)m * (size_t)n * sizeof(double));
 done:
     free(cos); free(sorted); free(slo); free(shi); free(tlo); free(thi); free(in_d); free(in_p); free(plist);
-    free(c_d); free(c_p); free(cset);
+    free(c_d); free(c_p); free(cset); free(prev_plist); free(prev_in_d);
     return rc;
 }
 
@@ -807,6 +951,7 @@ int orc_query_mc(const orc_scene *s, const orc_space *spaces, int32_t n_spaces, 
     int64_t n = s->n;
     if (n <= 0 || m < 0 || m > 64 || n_ch < 1 || n_ch > 16 || p->k_anchor < 1 || p->k_closest < 1)
         return ORC_EINVAL;
+    if (!pairs_ok(m, preds)) return ORC_EINVAL;
     int rc = ORC_OK;
     double *F = (double *)malloc((size_t)n * sizeof(double));
     double *Fl = (double *)malloc((size_t)n * sizeof(double));
@@ -817,8 +962,9 @@ int orc_query_mc(const orc_scene *s, const orc_space *spaces, int32_t n_spaces, 
     double *ssem = (double *)malloc((size_t)n * sizeof(double));
     double *tt = (double *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(double));
     int64_t *aa = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * (size_t)n * sizeof(int64_t));
+    int64_t *prev_L = (int64_t *)malloc((size_t)n * sizeof(int64_t));     /* a Between pair's first list */
     const float *emb[16];
-    if (!F || !Fl || !cos || !rank || !order || !tmp || !ssem || !tt || !aa) { rc = ORC_ENOMEM; goto out; }
+    if (!F || !Fl || !cos || !rank || !order || !tmp || !ssem || !tt || !aa || !prev_L) { rc = ORC_ENOMEM; goto out; }
 
     /* the target: fused score and s_sem */
     {
@@ -849,6 +995,21 @@ int orc_query_mc(const orc_scene *s, const orc_space *spaces, int32_t n_spaces, 
             goto out;
         sort_by_value(n, Fl, order, tmp);       /* order[0 .. K_a) is L_i */
         int64_t ka = p->k_anchor < n ? p->k_anchor : n;
+        if (preds[i] == ORC_BETWEEN) {          /* scored with its second constraint */
+            memcpy(prev_L, order, (size_t)ka * sizeof(int64_t));
+            continue;
+        }
+        if (preds[i] == ORC_BETWEEN_AND) {
+            for (int64_t e = 0; e < n; ++e) {
+                double tb;
+                int64_t ap, aq;
+                between_witness(s, p, e, prev_L, ka, order, ka, &tb, &ap, &aq);
+                tt[(int64_t)(i - 1) * n + e] = tt[(int64_t)i * n + e] = tb;
+                aa[(int64_t)(i - 1) * n + e] = ap;
+                aa[(int64_t)i * n + e] = aq;
+            }
+            continue;
+        }
         for (int64_t e = 0; e < n; ++e) {
             double tbest = 0.0;
             int64_t abest = -1;
@@ -866,16 +1027,17 @@ int orc_query_mc(const orc_scene *s, const orc_space *spaces, int32_t n_spaces, 
         }
     }
     for (int64_t e = 0; e < n; ++e) {
-        double te[64];
-        for (int32_t i = 0; i < m; ++i) te[i] = tt[(int64_t)i * n + e];
-        if (s_out) s_out[e] = compose(p, ssem[e], m, te);
+        double ts[64], te[64];
+        for (int32_t i = 0; i < m; ++i) ts[i] = tt[(int64_t)i * n + e];
+        int32_t mf = factors_of(m, preds, ts, te);
+        if (s_out) s_out[e] = compose(p, ssem[e], mf, te);
         if (fused_out) fused_out[e] = F[e];
         if (s_sem_out) s_sem_out[e] = ssem[e];
     }
     if (t_out) memcpy(t_out, tt, (size_t)m * (size_t)n * sizeof(double));
     if (anchor_out) memcpy(anchor_out, aa, (size_t)m * (size_t)n * sizeof(int64_t));
 out:
-    free(F); free(Fl); free(cos); free(rank); free(order); free(tmp); free(ssem); free(tt); free(aa);
+    free(F); free(Fl); free(cos); free(rank); free(order); free(tmp); free(ssem); free(tt); free(aa); free(prev_L);
     return rc;
 }
 
@@ -941,6 +1103,7 @@ int orc_query_bounds_mc(const orc_scene *s, const orc_space *spaces, int32_t n_s
     if (n <= 0 || m < 0 || m > 64 || n_ch < 1 || n_ch > 16 || !(tau >= 0.0)) return ORC_EINVAL;
     for (int32_t c = 0; c < n_ch; ++c)
         if (ch_space[c] < 0 || ch_space[c] >= n_spaces) return ORC_EINVAL;
+    if (!pairs_ok(m, preds)) return ORC_EINVAL;
     int rc = ORC_OK;
     double *Flo = (double *)malloc((size_t)n * sizeof(double));
     double *Fhi = (double *)malloc((size_t)n * sizeof(double));
@@ -954,10 +1117,13 @@ int orc_query_bounds_mc(const orc_scene *s, const orc_space *spaces, int32_t n_s
     int8_t *l_d = (int8_t *)malloc((size_t)n), *l_p = (int8_t *)malloc((size_t)n);
     int64_t *cset = (int64_t *)malloc((size_t)n * sizeof(int64_t));
     int64_t *plist = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *prev_plist = (int64_t *)malloc((size_t)n * sizeof(int64_t));   /* a Between pair's first list */
+    int8_t *prev_d = (int8_t *)malloc((size_t)n);
+    int64_t n_prev = 0;
     const float *emb[16];
     int64_t n_cset = 0, n_cp = 0;
     if (!Flo || !Fhi || !Llo || !Lhi || !cos || !sorted || !tlo || !thi || !c_d || !c_p || !l_d || !l_p ||
-        !cset || !plist) {
+        !cset || !plist || !prev_plist || !prev_d) {
         rc = ORC_ENOMEM;
         goto out;
     }
@@ -986,6 +1152,21 @@ int orc_query_bounds_mc(const orc_scene *s, const orc_space *spaces, int32_t n_s
             if (in_p_out) in_p_out[(int64_t)i * n + a] = l_p[a];
             if (l_p[a]) plist[n_p++] = a;
         }
+        if (preds[i] == ORC_BETWEEN) {
+            memcpy(prev_plist, plist, (size_t)n_p * sizeof(int64_t));
+            memcpy(prev_d, l_d, (size_t)n);
+            n_prev = n_p;
+            continue;
+        }
+        if (preds[i] == ORC_BETWEEN_AND) {
+            for (int64_t e = 0; e < n; ++e) {
+                double lo, hi;
+                between_bounds(s, p, e, prev_plist, n_prev, prev_d, plist, n_p, l_d, &lo, &hi);
+                tlo[(int64_t)(i - 1) * n + e] = tlo[(int64_t)i * n + e] = lo;
+                thi[(int64_t)(i - 1) * n + e] = thi[(int64_t)i * n + e] = hi;
+            }
+            continue;
+        }
         const int ranked = preds[i] == ORC_CLOSEST || preds[i] == ORC_FARTHEST;
         for (int64_t e = 0; e < n; ++e) {
             double lo = 0.0, hi = 0.0;
@@ -1011,11 +1192,13 @@ int orc_query_bounds_mc(const orc_scene *s, const orc_space *spaces, int32_t n_s
         }
     }
     for (int64_t e = 0; e < n; ++e) {
-        double cf = class_factor(s, p, c_t, e), te[64];
-        for (int32_t i = 0; i < m; ++i) te[i] = tlo[(int64_t)i * n + e];
-        double a = compose(p, cf * Flo[e], m, te);
-        for (int32_t i = 0; i < m; ++i) te[i] = thi[(int64_t)i * n + e];
-        double b = compose(p, cf * Fhi[e], m, te);
+        double cf = class_factor(s, p, c_t, e), ts[64], te[64];
+        for (int32_t i = 0; i < m; ++i) ts[i] = tlo[(int64_t)i * n + e];
+        int32_t mf = factors_of(m, preds, ts, te);
+        double a = compose(p, cf * Flo[e], mf, te);
+        for (int32_t i = 0; i < m; ++i) ts[i] = thi[(int64_t)i * n + e];
+        mf = factors_of(m, preds, ts, te);
+        double b = compose(p, cf * Fhi[e], mf, te);
         if (s_lo) s_lo[e] = a;
         if (s_hi) s_hi[e] = b;
         if (F_lo_out) F_lo_out[e] = Flo[e];
@@ -1025,7 +1208,7 @@ int orc_query_bounds_mc(const orc_scene *s, const orc_space *spaces, int32_t n_s
     if (t_hi_out) memcpy(t_hi_out, thi, (size_t)m * (size_t)n * sizeof(double));
 out:
     free(Flo); free(Fhi); free(Llo); free(Lhi); free(cos); free(sorted); free(tlo); free(thi);
-    free(c_d); free(c_p); free(l_d); free(l_p); free(cset); free(plist);
+    free(c_d); free(c_p); free(l_d); free(l_p); free(cset); free(plist); free(prev_plist); free(prev_d);
     return rc;
 }
 

@@ -18,7 +18,7 @@ _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
 (ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND, CLOSEST, FARTHEST, NEAR_H,
- INSIDE) = range(13)
+ INSIDE, BETWEEN, BETWEEN_AND) = range(15)
 
 
 @dataclasses.dataclass
@@ -109,6 +109,8 @@ def load():
         lib.orc_query_bounds_mc.restype = C.c_int
         lib.orc_query_bounds_mc.argtypes = [P, P, C.c_int32, P, C.c_int32, P, P, P, C.c_int32, C.c_int32, P,
                                             P, C.c_double, P, P, P, P, P, P, P]
+        lib.orc_between.restype = C.c_double
+        lib.orc_between.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64]
         lib.orc_num_threads.restype = C.c_int
         lib.orc_num_threads.argtypes = []
         _lib = lib
@@ -156,6 +158,12 @@ def sigmoid(x: float) -> float:
 def relation(scene, pred: int, e: int, a: int, params: OracleParams | None = None) -> float:
     sr, pp = _SceneRef(scene), _params(params)
     return float(load().orc_relation(C.byref(sr.c), C.byref(pp), int(pred), int(e), int(a)))
+
+
+def between(scene, e: int, ap: int, aq: int, params: OracleParams | None = None) -> float:
+    """The Between relation of e to the landmark pair (a_p, a_q)."""
+    sr, pp = _SceneRef(scene), _params(params)
+    return float(load().orc_between(C.byref(sr.c), C.byref(pp), int(e), int(ap), int(aq)))
 
 
 def relation_in(scene, pred: int, e: int, a: int, cand_set, params: OracleParams | None = None) -> float:

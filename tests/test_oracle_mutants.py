@@ -2,7 +2,7 @@
 
 Each case plants one mistake in a copy of oracle/farm_oracle.c (on the CPU),
 compiles it, and runs the pin suites (test_oracle_pins.py,
-test_oracle_pins_more.py, test_oracle_pins_mc.py) against it in a subprocess: they must fail.  A pin set that passes a planted mistake is not pinning that part.
+test_oracle_pins_more.py, test_oracle_pins_mc.py, test_oracle_pins_between.py) against it in a subprocess: they must fail.  A pin set that passes a planted mistake is not pinning that part.
 """
 import os
 import subprocess
@@ -49,6 +49,11 @@ MUTANTS = {
                                     "for (int64_t j = 0; j < n; ++j) ssem[j] = F[j];"),
     "fusion_landmarks_from_target": ("        if ((rc = fused_scores(s, spaces, n_spaces, p, n_ch, ch_space, ch_w, emb, Fl, cos, rank)) != ORC_OK)\n            goto out;\n        sort_by_value(n, Fl, order, tmp);",
                                      "        if ((rc = fused_scores(s, spaces, n_spaces, p, n_ch, ch_space, ch_w, emb, Fl, cos, rank)) != ORC_OK)\n            goto out;\n        sort_by_value(n, F, order, tmp);"),
+    "between_off_line_term_dropped": ("return orc_sigmoid(t / tau_b) * orc_sigmoid((1.0 - t) / tau_b) * exp(-0.5 * d2 / (sg * sg));",
+                                      "return orc_sigmoid(t / tau_b) * orc_sigmoid((1.0 - t) / tau_b) + 0.0 * sg;"),
+    "between_pair_counted_twice": ("if (preds[i] != ORC_BETWEEN_AND) f[k++] = t[i];", "f[k++] = t[i];"),
+    "between_same_landmark_twice": ("            if (aq == e || aq == ap) continue;\n            double r = orc_between(s, p, e, ap, aq);\n            if (bp < 0",
+                                    "            if (aq == e) continue;\n            double r = orc_between(s, p, e, ap, aq);\n            if (bp < 0"),
     "full_product_not_blend": ("return s_sem * ((1.0 - p->w) + p->w * gbar);", "return s_sem * gbar;"),
 }
 
@@ -67,6 +72,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_pins_more.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_pins_mc.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins_mc.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_pins_between.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins pass with mutant {name}:\n{r.stdout[-2000:]}"
