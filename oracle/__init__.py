@@ -7,9 +7,9 @@ its binding) never does.
 from .oracle import (ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND,
                      CLOSEST, FARTHEST, NEAR_H, INSIDE, BETWEEN, BETWEEN_AND, OracleParams, build, load, cosines, ranks, relation,
                      relation_in, sigmoid, query_all, query_bounds, batch, topk, num_threads,
-                     query_mc, query_bounds_mc, between)
+                     query_mc, query_bounds_mc, between, hellinger, associate)
 
 __all__ = ["ABOVE", "BELOW", "LEFT_OF", "RIGHT_OF", "NEAR", "NEXT_TO", "ON", "IN_FRONT_OF", "BEHIND",
            "CLOSEST", "FARTHEST", "NEAR_H", "INSIDE", "BETWEEN", "BETWEEN_AND", "OracleParams", "build", "load", "cosines", "ranks", "relation",
            "relation_in", "sigmoid", "query_all", "query_bounds", "batch", "topk", "num_threads",
-           "query_mc", "query_bounds_mc", "between"]
+           "query_mc", "query_bounds_mc", "between", "hellinger", "associate"]

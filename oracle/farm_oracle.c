@@ -1212,6 +1212,198 @@ out:
     return rc;
 }
 
+/* ------------------------------------------------------------------ */
+/* Mapping-side association (App. D.1 steps 3-5)                      */
+/* ------------------------------------------------------------------ */
+
+/*
+ * A batch of detections against the memory's entities, each a 3D Gaussian
+ * (mean; covariance packed as xx, xy, xz, yy, yz, zz) with an appearance
+ * feature and, for entities, a weight w (the detections fused so far) and an
+ * active flag:
+ *  3. neighbour search: for detection d, the active entities e with
+ *     cos(f_d, f_e) >= tau_f, then the Hellinger distance
+ *       H = sqrt(1 - BC),  BC = det(S_d)^(1/4) det(S_e)^(1/4) / det(S)^(1/2)
+ *                               * exp(-(1/8) dmu' S^-1 dmu),  S = (S_d + S_e) / 2,
+ *     keeping those with H <= h_max sorted by H (lower index on ties); the
+ *     first max_m of them are the detection's matches;
+ *  4. correspondence: the connected components of the graph whose edges join
+ *     each detection to its matches (union-find); in a component holding
+ *     entities the winner is the entity of largest w (lower index on ties),
+ *     every other entity of it merges into the winner; a detection without a
+ *     match starts a new entity (slot n_ent + d);
+ *  5. fusion: the winner absorbs every member (entities with their w,
+ *     detections with w = 1) by the sufficient-statistics merge
+ *       w = sum w_i,  M1 = sum w_i mu_i,  M2 = sum w_i (S_i + mu_i mu_i'),
+ *       mu = M1 / w,  S = M2 / w - mu mu',
+ *     here evaluated in the equal form S = sum w_i (S_i + (mu_i - mu)(mu_i - mu)') / w,
+ *     and the appearance feature by the w-weighted average sum w_i f_i / w.
+ * Outputs over n_ent + n_det slots (entities, then one slot per detection):
+ * parent (the slot a slot merges into; itself for a winner, an untouched
+ * entity or a new entity), w (0 for a merged-away slot), mu [3, slots],
+ * cov [6, slots], feat [slots, F]; per detection: match_cnt (matches within
+ * the budget, before the max_m cap), match_idx / match_h [n_det, max_m]
+ * (-1 / -1 past the count).
+ */
+static double det3(const double c[6])
+{
+    /* c = xx, xy, xz, yy, yz, zz */
+    return c[0] * (c[3] * c[5] - c[4] * c[4]) - c[1] * (c[1] * c[5] - c[4] * c[2]) +
+           c[2] * (c[1] * c[4] - c[3] * c[2]);
+}
+
+/* Hellinger distance between two Gaussians (packed covariances). */
+double orc_hellinger(const double *mu1, const double *c1, const double *mu2, const double *c2)
+{
+    double S[6], d[3];
+    for (int k = 0; k < 6; ++k) S[k] = 0.5 * (c1[k] + c2[k]);
+    for (int k = 0; k < 3; ++k) d[k] = mu1[k] - mu2[k];
+    double dS = det3(S), d1 = det3(c1), d2 = det3(c2);
+    if (!(dS > 0.0) || !(d1 > 0.0) || !(d2 > 0.0)) return 1.0;
+    /* S^-1 d by the adjugate */
+    double a[6] = {S[3] * S[5] - S[4] * S[4], S[2] * S[4] - S[1] * S[5], S[1] * S[4] - S[2] * S[3],
+                   S[0] * S[5] - S[2] * S[2], S[1] * S[2] - S[0] * S[4], S[0] * S[3] - S[1] * S[1]};
+    double x0 = a[0] * d[0] + a[1] * d[1] + a[2] * d[2];
+    double x1 = a[1] * d[0] + a[3] * d[1] + a[4] * d[2];
+    double x2 = a[2] * d[0] + a[4] * d[1] + a[5] * d[2];
+    double q = (d[0] * x0 + d[1] * x1 + d[2] * x2) / dS;
+    double bc = pow(d1, 0.25) * pow(d2, 0.25) / sqrt(dS) * exp(-q / 8.0);
+    double h2 = 1.0 - bc;
+    return h2 > 0.0 ? sqrt(h2) : 0.0;
+}
+
+static int64_t uf_find(int64_t *par, int64_t x)
+{
+    while (par[x] != x) {
+        par[x] = par[par[x]];     /* path halving */
+        x = par[x];
+    }
+    return x;
+}
+
+int orc_associate(int64_t n_ent, const float *ent_mu, const float *ent_cov, const float *ent_feat,
+                  const int32_t *ent_active, const float *ent_w, int64_t n_det, const float *det_mu,
+                  const float *det_cov, const float *det_feat, int64_t F, double tau_f, double h_max,
+                  int64_t max_m, int64_t *match_cnt, int64_t *match_idx, double *match_h, int64_t *parent,
+                  double *out_w, double *out_mu, double *out_cov, double *out_feat)
+{
+    if (n_ent < 0 || n_det < 0 || F < 1 || max_m < 1) return ORC_EINVAL;
+    const int64_t N = n_ent, B = n_det, T = N + B;
+    int rc = ORC_OK;
+    double *en = (double *)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
+    int64_t *uf = (int64_t *)malloc((size_t)(T > 0 ? T : 1) * sizeof(int64_t));
+    int64_t *win = (int64_t *)malloc((size_t)(T > 0 ? T : 1) * sizeof(int64_t));
+    double *cand_h = (double *)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
+    int64_t *cand_i = (int64_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t));
+    int64_t *tmp = (int64_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t));
+    double *key = (double *)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
+    if (!en || !uf || !win || !cand_h || !cand_i || !tmp || !key) { rc = ORC_ENOMEM; goto out; }
+    for (int64_t e = 0; e < N; ++e) {
+        double ss = 0.0;
+        for (int64_t k = 0; k < F; ++k) ss += (double)ent_feat[e * F + k] * ent_feat[e * F + k];
+        en[e] = sqrt(ss);
+    }
+    /* slot accessors: entities 0..N-1, detections N..N+B-1 */
+#define MU(x, k) ((x) < N ? (double)ent_mu[(int64_t)(k) * N + (x)] : (double)det_mu[(int64_t)(k) * B + (x) - N])
+#define CV(x, k) ((x) < N ? (double)ent_cov[(int64_t)(k) * N + (x)] : (double)det_cov[(int64_t)(k) * B + (x) - N])
+#define FT(x, k) ((x) < N ? (double)ent_feat[(x) * F + (k)] : (double)det_feat[((x) - N) * F + (k)])
+#define WT(x) ((x) < N ? (double)ent_w[x] : 1.0)
+
+    /* 3. neighbour search */
+    for (int64_t t = 0; t < T; ++t) uf[t] = t;
+    for (int64_t d = 0; d < B; ++d) {
+        double dn = 0.0, mud[3], cd[6];
+        for (int64_t k = 0; k < F; ++k) dn += (double)det_feat[d * F + k] * det_feat[d * F + k];
+        dn = sqrt(dn);
+        for (int k = 0; k < 3; ++k) mud[k] = det_mu[(int64_t)k * B + d];
+        for (int k = 0; k < 6; ++k) cd[k] = det_cov[(int64_t)k * B + d];
+        int64_t nc = 0;
+        for (int64_t e = 0; e < N; ++e) {
+            if (!ent_active[e]) continue;
+            double dot = 0.0;
+            for (int64_t k = 0; k < F; ++k) dot += (double)det_feat[d * F + k] * ent_feat[e * F + k];
+            if (!(dn > 0.0 && en[e] > 0.0) || dot / (dn * en[e]) < tau_f) continue;
+            double mue[3], ce[6];
+            for (int k = 0; k < 3; ++k) mue[k] = ent_mu[(int64_t)k * N + e];
+            for (int k = 0; k < 6; ++k) ce[k] = ent_cov[(int64_t)k * N + e];
+            double h = orc_hellinger(mud, cd, mue, ce);
+            if (h <= h_max) {
+                cand_h[nc] = h;
+                cand_i[nc] = e;
+                ++nc;
+            }
+        }
+        /* sort by H ascending, lower index on ties: sort_by_value orders by
+         * larger value first and lower index first, so sort -H over positions */
+        for (int64_t i = 0; i < nc; ++i) key[i] = -cand_h[i];
+        sort_by_value(nc, key, tmp, win);
+        match_cnt[d] = nc;
+        for (int64_t j = 0; j < max_m; ++j) {
+            if (j < nc) {
+                int64_t e = cand_i[tmp[j]];
+                match_idx[d * max_m + j] = e;
+                match_h[d * max_m + j] = cand_h[tmp[j]];
+                /* 4. union of the detection with its match */
+                int64_t a = uf_find(uf, N + d), b = uf_find(uf, e);
+                if (a != b) uf[a] = b;
+            } else {
+                match_idx[d * max_m + j] = -1;
+                match_h[d * max_m + j] = -1.0;
+            }
+        }
+    }
+    /* 4. winners: per component root, the entity of largest w, lower index on ties */
+    for (int64_t t = 0; t < T; ++t) win[t] = -1;
+    for (int64_t e = 0; e < N; ++e) {
+        int64_t r = uf_find(uf, e);
+        if (win[r] < 0 || ent_w[e] > ent_w[win[r]] || (ent_w[e] == ent_w[win[r]] && e < win[r])) win[r] = e;
+    }
+    for (int64_t t = 0; t < T; ++t) {
+        int64_t r = uf_find(uf, t);
+        parent[t] = win[r] >= 0 ? win[r] : t;       /* a component without an entity: a lone detection */
+    }
+    /* 5. fusion: winners gather their members */
+    for (int64_t t = 0; t < T; ++t) {
+        out_w[t] = 0.0;
+        for (int k = 0; k < 3; ++k) out_mu[(int64_t)k * T + t] = 0.0;
+        for (int k = 0; k < 6; ++k) out_cov[(int64_t)k * T + t] = 0.0;
+        for (int64_t k = 0; k < F; ++k) out_feat[t * F + k] = 0.0;
+    }
+    for (int64_t t = 0; t < T; ++t) {              /* w and w mu */
+        int64_t g = parent[t];
+        double w = WT(t);
+        out_w[g] += w;
+        for (int k = 0; k < 3; ++k) out_mu[(int64_t)k * T + g] += w * MU(t, k);
+        for (int64_t k = 0; k < F; ++k) out_feat[g * F + k] += w * FT(t, k);
+    }
+    for (int64_t g = 0; g < T; ++g) {
+        if (parent[g] != g) continue;
+        if (!(out_w[g] > 0.0)) continue;
+        for (int k = 0; k < 3; ++k) out_mu[(int64_t)k * T + g] /= out_w[g];
+        for (int64_t k = 0; k < F; ++k) out_feat[g * F + k] /= out_w[g];
+    }
+    for (int64_t t = 0; t < T; ++t) {              /* w (S_i + (mu_i - mu)(mu_i - mu)') */
+        int64_t g = parent[t];
+        double w = WT(t), dm[3];
+        for (int k = 0; k < 3; ++k) dm[k] = MU(t, k) - out_mu[(int64_t)k * T + g];
+        const int ix[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+        for (int k = 0; k < 6; ++k)
+            out_cov[(int64_t)k * T + g] += w * (CV(t, k) + dm[ix[k][0]] * dm[ix[k][1]]);
+    }
+    for (int64_t g = 0; g < T; ++g) {
+        if (parent[g] != g || !(out_w[g] > 0.0)) continue;
+        for (int k = 0; k < 6; ++k) out_cov[(int64_t)k * T + g] /= out_w[g];
+    }
+    /* merged-away slots keep w = 0 and zero statistics */
+#undef MU
+#undef CV
+#undef FT
+#undef WT
+out:
+    free(en); free(uf); free(win); free(cand_h); free(cand_i); free(tmp); free(key);
+    return rc;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -111,6 +111,11 @@ def load():
                                             P, C.c_double, P, P, P, P, P, P, P]
         lib.orc_between.restype = C.c_double
         lib.orc_between.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64]
+        lib.orc_hellinger.restype = C.c_double
+        lib.orc_hellinger.argtypes = [P, P, P, P]
+        lib.orc_associate.restype = C.c_int
+        lib.orc_associate.argtypes = [C.c_int64, P, P, P, P, P, C.c_int64, P, P, P, C.c_int64, C.c_double,
+                                      C.c_double, C.c_int64, P, P, P, P, P, P, P, P]
         lib.orc_num_threads.restype = C.c_int
         lib.orc_num_threads.argtypes = []
         _lib = lib
@@ -311,4 +316,33 @@ def query_bounds_mc(scene, spaces, channels, u0, c_t, preds, u_c, tau: float,
                                     _ptr(ucf), float(tau), _ptr(out["s_lo"]), _ptr(out["s_hi"]), _ptr(out["t_lo"]),
                                     _ptr(out["t_hi"]), _ptr(out["F_lo"]), _ptr(out["F_hi"]), _ptr(out["in_p"]))
     _check(rc, "query_bounds_mc")
+    return out
+
+
+def hellinger(mu1, cov1, mu2, cov2) -> float:
+    """Hellinger distance of two 3D Gaussians (covariances packed xx, xy, xz, yy, yz, zz)."""
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (mu1, cov1, mu2, cov2)]
+    return float(load().orc_hellinger(*[_ptr(x) for x in a]))
+
+
+def associate(ent, det, tau_f: float, h_max: float, max_m: int) -> dict:
+    """Mapping-side association of a detection batch with the entities
+    (neighbour search, union-find correspondence, sufficient-statistics
+    fusion).  ent: dict(mu [3, N], cov [6, N], feat [N, F], active [N], w [N]);
+    det: dict(mu [3, B], cov [6, B], feat [B, F])."""
+    f32 = lambda x: np.ascontiguousarray(x, dtype=np.float32)   # noqa: E731
+    emu, ecov, efeat, ew = f32(ent["mu"]), f32(ent["cov"]), f32(ent["feat"]), f32(ent["w"])
+    eact = np.ascontiguousarray(ent["active"], dtype=np.int32)
+    dmu, dcov, dfeat = f32(det["mu"]), f32(det["cov"]), f32(det["feat"])
+    N, B, F = emu.shape[1], dmu.shape[1], efeat.shape[1] if efeat.size else dfeat.shape[1]
+    T = N + B
+    out = dict(match_cnt=np.zeros(B, np.int64), match_idx=np.zeros((B, max_m), np.int64),
+               match_h=np.zeros((B, max_m)), parent=np.zeros(T, np.int64), w=np.zeros(T),
+               mu=np.zeros((3, T)), cov=np.zeros((6, T)), feat=np.zeros((T, F)))
+    one = lambda a: _ptr(a if a.size else np.zeros(1, a.dtype))   # noqa: E731
+    rc = load().orc_associate(N, one(emu), one(ecov), one(efeat), one(eact), one(ew), B, one(dmu), one(dcov),
+                              one(dfeat), F, float(tau_f), float(h_max), int(max_m), one(out["match_cnt"]),
+                              one(out["match_idx"]), one(out["match_h"]), one(out["parent"]), one(out["w"]),
+                              one(out["mu"]), one(out["cov"]), one(out["feat"]))
+    _check(rc, "associate")
     return out

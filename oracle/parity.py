@@ -163,6 +163,17 @@ def _judge(scene, qb, q, k, idx, score, t, anchor, params, rtol, atol_t, b, ex, 
                     fails.append(f"q{q} e{e} c{i}: anchor {av} not an admissible landmark")
                     continue
                 pred = int(qb.c_pred[m0 + i])
+                if pred == O.BETWEEN_AND:
+                    continue                # checked with its first landmark
+                if pred == O.BETWEEN:
+                    aq = int(anchor[r][i + 1])
+                    if aq < 0 or aq == e or aq == av or not b["in_p"][i + 1][aq]:
+                        fails.append(f"q{q} e{e} c{i}: Between pair ({av}, {aq}) not admissible")
+                        continue
+                    rv = O.between(scene, e, av, aq, params)
+                    if abs(rv - tv) > rtol * abs(rv) + atol_t:
+                        fails.append(f"q{q} e{e} c{i}: pair ({av}, {aq}) scores {rv:.9g}, reported t {tv:.9g}")
+                    continue
                 if pred in (O.CLOSEST, O.FARTHEST):
                     if cset is None:
                         continue            # the set itself is ambiguous: the t bounds above decide

@@ -29,7 +29,7 @@ import numpy as np
 # Predicate codes of the C-ABI (include/farm.h): above, below, left_of,
 # right_of, near.
 N_PRED = 5          # the predicates of the benchmark workloads (codes 0-4)
-N_PRED_ALL = 13     # with NextTo, On, InFrontOf, Behind, Closest, Farthest, NearH, Inside (codes 5-12)
+N_PRED_ALL = 15     # with NextTo, On, InFrontOf, Behind, Closest, Farthest, NearH, Inside, Between (5-14)
 
 
 @dataclasses.dataclass
@@ -250,11 +250,32 @@ def make_queries(seed: int, scene: Scene, n_q: int, m_choices=(2,),
     n_c = int(c_off[-1])
     pred_set = preds
     preds = rng.integers(0, N_PRED, size=n_c) if pred_set is None else rng.choice(np.asarray(pred_set), size=n_c)
+    if pred_set is not None and (13 in pred_set or 14 in pred_set):
+        # Between takes two consecutive constraints (13 then 14); a 13 with no
+        # room after it, or a 14 without its 13, becomes near (4)
+        for q in range(n_q):
+            c, c1 = int(c_off[q]), int(c_off[q + 1])
+            while c < c1:
+                if preds[c] == 13 and c + 1 < c1:
+                    preds[c + 1] = 14
+                    c += 2
+                    continue
+                if preds[c] in (13, 14):
+                    preds[c] = 4
+                c += 1
     lms = np.zeros(n_c, np.int64)
     from scipy.spatial import cKDTree
     tree = cKDTree(centers)
     for q in range(n_q):
         for c in range(c_off[q], c_off[q + 1]):
+            if preds[c] == 14:
+                # the second landmark of a Between: the object nearest the far
+                # side of the target from the first one
+                far = 2.0 * centers[targets[q]] - centers[lms[c - 1]]
+                _, near_idx = tree.query(far, k=min(4, n))
+                near_idx = [int(j) for j in np.atleast_1d(near_idx) if j != targets[q] and j != lms[c - 1]]
+                lms[c] = near_idx[0] if near_idx else int(lms[c - 1])
+                continue
             lms[c] = _plant_landmark(rng, centers, int(targets[q]), int(preds[c]), tree, sizes=sizes)
     c_emb = cent[scene.cls[lms]] + sigma * rng.standard_normal((n_c, dim))
     tgt_cls = scene.cls[targets].astype(np.int32) if with_class else np.full(n_q, -1, np.int32)
@@ -376,6 +397,76 @@ def channel_queries(seed: int, scene: Scene, spaces: Spaces, qb: QueryBatch, cha
         lm.append(np.ascontiguousarray((cen[lcls] + sg * rng.standard_normal((qb.n_c, dim))).astype(np.float32)
                                        .reshape(qb.n_c, dim)))
     return ChannelQueries(channels=[(int(c[0]), float(c[1])) for c in channels], tgt=tgt, lm=lm)
+
+
+# ---------------------------------------------------------------------------
+# Mapping-side association (App. D.1 steps 3-5): the memory's entities as 3D
+# Gaussians with appearance features and weights, and a batch of detections.
+# ---------------------------------------------------------------------------
+
+def _yaw_cov(sizes, yaw):
+    """Packed covariances (xx, xy, xz, yy, yz, zz) of boxes of the given sizes
+    (the moments of the uniform distribution over the box) turned by yaw."""
+    v = (sizes ** 2) / 12.0
+    c, s_ = np.cos(yaw), np.sin(yaw)
+    xx = c * c * v[:, 0] + s_ * s_ * v[:, 1]
+    yy = s_ * s_ * v[:, 0] + c * c * v[:, 1]
+    xy = c * s_ * (v[:, 0] - v[:, 1])
+    z = np.zeros_like(xx)
+    return np.stack([xx, xy, z, yy, z, v[:, 2]]).astype(np.float32)
+
+
+def make_association(seed: int, scene: Scene, n_det: int, feat_dim: int = 256, new_frac: float = 0.1,
+                     bridge_frac: float = 0.05, inactive_frac: float = 0.05):
+    """Entities: the scene's objects as Gaussians (box centre; box-moment
+    covariance turned by a random yaw), a feat_dim appearance feature per
+    object (its class's unit Gaussian centroid plus noise of norm about 0.15),
+    a weight (1-20 fused detections) and an active flag.  Detections: mostly
+    re-observations of random entities (centre moved by N(0, 0.05^2) m,
+    sizes by 5%, yaw by 0.1 rad, feature re-drawn around the class centroid),
+    a fraction placed midway between two same-class neighbours (a detection
+    that bridges two entities) and a fraction of new objects."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = scene.n
+    n_cls = int(scene.cls.max()) + 1
+    cent = _unit_rows(rng.standard_normal((n_cls, feat_dim)))
+    sg = 0.15 / math.sqrt(feat_dim)
+    sizes = scene.box[3:].T.astype(np.float64)
+    yaw = rng.uniform(0, np.pi, n)
+    ent = dict(mu=scene.box[:3].astype(np.float32), cov=_yaw_cov(sizes, yaw),
+               feat=_unit_rows(cent[scene.cls] + sg * rng.standard_normal((n, feat_dim))).astype(np.float32),
+               w=rng.integers(1, 21, n).astype(np.float32),
+               active=(rng.uniform(size=n) >= inactive_frac).astype(np.int32))
+    kind = rng.uniform(size=n_det)
+    src = rng.integers(0, n, n_det)
+    mu = np.zeros((3, n_det)); sz = np.zeros((n_det, 3)); yw = np.zeros(n_det); cls = np.zeros(n_det, np.int64)
+    from scipy.spatial import cKDTree
+    centers = scene.box[:3].T.astype(np.float64)
+    tree = cKDTree(centers)
+    for d in range(n_det):
+        e = int(src[d])
+        if kind[d] < new_frac:
+            ext = np.asarray(scene.extent if scene.extent[0] > 0 else centers.max(axis=0))
+            mu[:, d] = rng.uniform(0, 1, 3) * ext
+            sz[d] = rng.lognormal(-1.0, 0.5, 3)
+            yw[d] = rng.uniform(0, np.pi)
+            cls[d] = rng.integers(0, n_cls)
+            continue
+        cls[d] = scene.cls[e]
+        if kind[d] < new_frac + bridge_frac:
+            _, nb = tree.query(centers[e], k=min(8, n))
+            same = [int(j) for j in np.atleast_1d(nb) if j != e and scene.cls[j] == scene.cls[e]]
+            if same:
+                mu[:, d] = 0.5 * (centers[e] + centers[same[0]])
+                sz[d] = np.abs(centers[e] - centers[same[0]]) + 0.5 * (sizes[e] + sizes[same[0]])
+                yw[d] = yaw[e]
+                continue
+        mu[:, d] = centers[e] + 0.05 * rng.standard_normal(3)
+        sz[d] = sizes[e] * (1.0 + 0.05 * rng.standard_normal(3))
+        yw[d] = yaw[e] + 0.1 * rng.standard_normal()
+    det = dict(mu=mu.astype(np.float32), cov=_yaw_cov(np.abs(sz), yw),
+               feat=_unit_rows(cent[cls] + sg * rng.standard_normal((n_det, feat_dim))).astype(np.float32))
+    return ent, det
 
 
 def concat_batches(parts):

@@ -2,7 +2,8 @@
 
 Each case plants one mistake in a copy of oracle/farm_oracle.c (on the CPU),
 compiles it, and runs the pin suites (test_oracle_pins.py,
-test_oracle_pins_more.py, test_oracle_pins_mc.py, test_oracle_pins_between.py) against it in a subprocess: they must fail.  A pin set that passes a planted mistake is not pinning that part.
+test_oracle_pins_more.py, test_oracle_pins_mc.py, test_oracle_pins_between.py,
+test_oracle_pins_assoc.py) against it in a subprocess: they must fail.  A pin set that passes a planted mistake is not pinning that part.
 """
 import os
 import subprocess
@@ -54,6 +55,9 @@ MUTANTS = {
     "between_pair_counted_twice": ("if (preds[i] != ORC_BETWEEN_AND) f[k++] = t[i];", "f[k++] = t[i];"),
     "between_same_landmark_twice": ("            if (aq == e || aq == ap) continue;\n            double r = orc_between(s, p, e, ap, aq);\n            if (bp < 0",
                                     "            if (aq == e) continue;\n            double r = orc_between(s, p, e, ap, aq);\n            if (bp < 0"),
+    "assoc_winner_lightest": ("if (win[r] < 0 || ent_w[e] > ent_w[win[r]]", "if (win[r] < 0 || ent_w[e] < ent_w[win[r]]"),
+    "assoc_spread_dropped": ("w * (CV(t, k) + dm[ix[k][0]] * dm[ix[k][1]]);", "w * (CV(t, k) + 0.0 * dm[ix[k][0]]);"),
+    "assoc_hellinger_exponent": ("* exp(-q / 8.0);", "* exp(-q / 4.0);"),
     "full_product_not_blend": ("return s_sem * ((1.0 - p->w) + p->w * gbar);", "return s_sem * gbar;"),
 }
 
@@ -73,6 +77,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_pins_more.py"),
                         os.path.join(ROOT, "tests", "test_oracle_pins_mc.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_pins_between.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins_between.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_pins_assoc.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins pass with mutant {name}:\n{r.stdout[-2000:]}"
