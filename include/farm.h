@@ -12,7 +12,8 @@
  * with the unary score s_sem given by reciprocal-rank fusion of descriptor
  * similarity (App. D.2 step 3), the closed-form relation evaluators of App. D.2
  * step 4 (Above, Below, LeftOf, RightOf, Near, NextTo, On, InFrontOf, Behind,
- * Closest, Farthest, Inside) and the Hellinger form of Near (Sec. 2.3),
+ * Closest, Farthest, Inside), the Hellinger form of Near (Sec. 2.3) and the
+ * ternary Between of App. B,
  * anchors bound greedily to
  * their best witness among the top-K_a landmark candidates (App. B,
  * "Query-time complexity"; App. D.2 step 4) and the composite
@@ -72,7 +73,15 @@ typedef enum {
     FARM_FARTHEST = 10, /* 1 / (|C| - rank_d + 1) over the same set C */
     FARM_NEAR_H = 11,   /* 1 - H(N_e, N_a): the Hellinger form of Near (Sec. 2.3), with each object the
                            Gaussian of its box centre and covariance diag(s^2) / 12 */
-    FARM_INSIDE = 12    /* containment (App. D.2 step 4): the fraction of e's box volume inside a's box */
+    FARM_INSIDE = 12,   /* containment (App. D.2 step 4): the fraction of e's box volume inside a's box */
+    FARM_BETWEEN = 13,  /* Between(e, a_p, a_q) (App. B), first landmark a_p: the constraint right after it
+                           must be FARM_BETWEEN_AND with the second landmark a_q.  The pair is bound jointly
+                           (the best (a_p, a_q) over L_p x L_q, a_p != a_q, neither = e; lower a_p, then
+                           lower a_q on ties) and is one factor of the geometric mean; both constraints
+                           report its score.  sig(t / 0.1) sig((1 - t) / 0.1) exp(-d^2 / (2 sigma_near^2)):
+                           t = e's centre projected on the segment a_p -> a_q (0 at a_p, 1 at a_q), d its
+                           distance from the line; 0 when the two centres coincide */
+    FARM_BETWEEN_AND = 14 /* the second landmark of a Between */
 } farm_pred;
 
 /* Arithmetic of the descriptor-similarity stage (App. D.2 step 3). */
@@ -273,6 +282,42 @@ farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, i
                                  const farm_channel *ch, const float *tgt_emb, const int32_t *tgt_cls,
                                  const int32_t *c_off, const int32_t *c_pred, const float *c_emb, uint32_t flags,
                                  uint64_t *batch_handle);
+
+/*
+ * Mapping-side association (App. D.1 steps 3-5): a batch of n_det detections
+ * against the memory's n_ent entities, each a 3D Gaussian -- mean [3, n] SoA
+ * and covariance packed [6, n] SoA (xx, xy, xz, yy, yz, zz) -- with an
+ * appearance feature ([n, F] row-major FP32); entities also carry a weight
+ * ent_w (the detections fused so far, finite and >= 0) and an active flag.
+ *  - neighbour search: for each detection, the active entities whose feature
+ *    cosine is >= tau_f (computed as the FP32-accurate similarity), then the
+ *    Hellinger distance of the two Gaussians, keeping those with H <= h_max
+ *    sorted by (H, index): match_cnt [n_det] (all within the budget),
+ *    match_idx / match_h [n_det, max_m] (the first max_m; -1 after);
+ *  - correspondence: the connected components of the graph joining every
+ *    detection to its (at most max_m) matches (union-find); in a component
+ *    with entities the entity of largest weight (lower index on ties) wins
+ *    and the others merge into it; a detection without a match starts a new
+ *    entity;
+ *  - fusion: the winner absorbs its component by the sufficient-statistics
+ *    merge (w = sum w_i, M1 = sum w_i mu_i, M2 = sum w_i (S_i + mu_i mu_i'),
+ *    mu = M1 / w, S = M2 / w - mu mu'; detections weigh 1), and its feature
+ *    becomes the w-weighted average.
+ * Outputs over T = n_ent + n_det slots (the entities, then one per
+ * detection): parent [T] (the slot each merges into; itself for a winner, an
+ * untouched entity or a new entity), out_w [T] (0 for slots merged away),
+ * out_mu [3, T], out_cov [6, T], out_feat [T, F] (zero for merged slots).
+ * 1 <= max_m <= 64, F <= 8192, tau_f in [-1, 1], h_max in [0, 1].  All
+ * arrays host memory, or all device memory with FARM_PTR_DEVICE.  The call
+ * synchronises.  A detection with more than 1,024 entities within the
+ * budget is reported as FARM_EINVAL.
+ */
+farm_status farm_associate(farm_ctx *ctx, int64_t n_ent, const float *ent_mu, const float *ent_cov,
+                           const float *ent_feat, const int32_t *ent_active, const float *ent_w, int64_t n_det,
+                           const float *det_mu, const float *det_cov, const float *det_feat, int32_t F, float tau_f,
+                           float h_max, int32_t max_m, int32_t *match_cnt, int32_t *match_idx, float *match_h,
+                           int32_t *parent, float *out_w, float *out_mu, float *out_cov, float *out_feat,
+                           uint32_t flags);
 
 /*
  * Writes the TopK of every query of a batch, the ScoredCandidate records of

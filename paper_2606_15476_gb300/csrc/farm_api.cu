@@ -74,6 +74,27 @@ farm_status fail(farm_ctx *ctx, farm_status st, const std::string &msg)
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// A query's predicate codes: each known, and every FARM_BETWEEN directly
+// followed by its FARM_BETWEEN_AND (and only there).
+bool preds_ok(const int32_t *pr, int32_t m, std::string &why)
+{
+    for (int32_t i = 0; i < m; ++i) {
+        if (pr[i] < 0 || pr[i] > FARM_BETWEEN_AND) {
+            why = "unknown predicate code " + std::to_string(pr[i]);
+            return false;
+        }
+        if (pr[i] == FARM_BETWEEN && !(i + 1 < m && pr[i + 1] == FARM_BETWEEN_AND)) {
+            why = "FARM_BETWEEN must be followed by FARM_BETWEEN_AND";
+            return false;
+        }
+        if (pr[i] == FARM_BETWEEN_AND && !(i > 0 && pr[i - 1] == FARM_BETWEEN)) {
+            why = "FARM_BETWEEN_AND must follow FARM_BETWEEN";
+            return false;
+        }
+    }
+    return true;
+}
+
 int64_t target_bound(const farm_params &p)
 {
     // A candidate of rank r scores at most 1/(mu + r); k_max objects score at
@@ -196,6 +217,10 @@ farm_status check_device_errors(farm_ctx *ctx)
     c.batch_valid = false;
     if (e & farm::kErrTimeout) return fail(ctx, FARM_ETIMEOUT, "a bounded device-side wait gave up");
     if (e & farm::kErrPieceTable) return fail(ctx, FARM_ECUDA, "a similarity piece table entry was malformed");
+    if (e & farm::kErrFusedOverflow)
+        return fail(ctx, FARM_EINVAL, "a fused query kept more than 512 candidates that can reach its TopK");
+    if (e & farm::kErrAssocOverflow)
+        return fail(ctx, FARM_EINVAL, "a detection has more than 1,024 entities within the Hellinger budget");
     if (e & farm::kErrBadDesc)
         return fail(ctx, FARM_EINVAL, "a descriptor row has zero or non-finite norm");
     return fail(ctx, FARM_EINVAL, "an embedding row has zero or non-finite norm");
@@ -543,9 +568,10 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         }
         n_c = c_off[n_q];
         if (n_c > 0 && (!c_pred || !c_emb)) return fail(ctx, FARM_EINVAL, "c_pred and c_emb must be non-null");
-        for (int64_t i = 0; i < n_c; ++i)
-            if (c_pred[i] < 0 || c_pred[i] > FARM_INSIDE)
-                return fail(ctx, FARM_EINVAL, "unknown predicate code " + std::to_string(c_pred[i]));
+        std::string why;
+        for (int64_t q = 0; q < n_q; ++q)
+            if (!preds_ok(c_pred + c_off[q], c_off[q + 1] - c_off[q], why))
+                return fail(ctx, FARM_EINVAL, "query " + std::to_string(q) + ": " + why);
     }
     c.batch_valid = false;
     *batch_handle = 0;
@@ -1217,9 +1243,12 @@ farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, i
     }
     const int64_t n_c = c_off[n_q];
     if (n_c > 0 && (!c_pred || !c_emb)) return fail(ctx, FARM_EINVAL, "c_pred and c_emb must be non-null");
-    for (int64_t i = 0; i < n_c; ++i)
-        if (c_pred[i] < 0 || c_pred[i] > FARM_INSIDE)
-            return fail(ctx, FARM_EINVAL, "unknown predicate code " + std::to_string(c_pred[i]));
+    {
+        std::string why;
+        for (int64_t q = 0; q < n_q; ++q)
+            if (!preds_ok(c_pred + c_off[q], c_off[q + 1] - c_off[q], why))
+                return fail(ctx, FARM_EINVAL, "query " + std::to_string(q) + ": " + why);
+    }
     if (p.k_max > n) return fail(ctx, FARM_EINVAL, "k_max exceeds the scene's object count");
     // list depths: an object no channel lists fuses to at most W / (mu + R + 1);
     // keep that below the k_max-th composite's floor (1 - w) class_mis wmax / (mu + k_max),

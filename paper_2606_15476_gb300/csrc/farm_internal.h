@@ -36,6 +36,7 @@ constexpr int kErrBadDesc = 2;       // zero or non-finite descriptor row
 constexpr int kErrTimeout = 4;       // a bounded wait gave up
 constexpr int kErrPieceTable = 8;    // a similarity piece carried a misaligned tensor-map pointer
 constexpr int kErrFusedOverflow = 16; // a query of a fused batch kept more candidates than its list holds
+constexpr int kErrAssocOverflow = 32; // a detection had more matches within the budget than the search holds
 
 // A further descriptor space of a scene (farm_memory_add_space): the FP16
 // split of its unit rows, as desc_hi / desc_lo below.
@@ -485,6 +486,27 @@ struct FuseArgs {
 };
 // part 0: target rows, part 1: landmark rows.
 cudaError_t launch_fuse(const FuseArgs &a, int part, cudaStream_t s);
+
+// Mapping-side association (k_assoc.cu): device arrays only.
+struct AssocArgs {
+    int32_t N, B, F;                    // entities, detections, feature length
+    const float *S;                     // [B, ld] detection-by-entity feature cosines
+    int64_t ld;
+    const float *ent_mu, *ent_cov, *ent_feat, *ent_w;   // [3, N], [6, N], [N, F], [N]
+    const int32_t *ent_active;          // [N]
+    const float *det_mu, *det_cov, *det_feat;           // [3, B], [6, B], [B, F]
+    float tau_f, h_max;
+    int32_t max_m;
+    int32_t *match_cnt, *match_idx;     // [B], [B, max_m]
+    float *match_h;                     // [B, max_m]
+    int32_t *label;                     // [N + B] scratch
+    unsigned long long *win;            // [N + B] scratch
+    float *acc;                         // [(N + B) * (10 + F)] scratch
+    int32_t *parent;                    // [N + B]
+    float *out_w, *out_mu, *out_cov, *out_feat;         // [T], [3, T], [6, T], [T, F]
+    int32_t *err;
+};
+cudaError_t launch_assoc(const AssocArgs &a, cudaStream_t s);
 
 // out[q * k + j] = src[perm[q] * ld + j] (and the 4-wide breakdown): the TopK
 // prefix of each query's sorted candidates, back in the caller's query order.

@@ -98,6 +98,51 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = (a - ap) + (b - bp);
 }
 
+// a b - c d with an error of a few units in the last place of the result
+// (Kahan's algorithm: the rounding error of c d recovered by an FMA).
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d)
+{
+    const float w = c * d;
+    const float e = fmaf(-c, d, w);
+    const float f = fmaf(a, b, -w);
+    return f + e;
+}
+
+// Between(e, a_p, a_q): e's centre on the segment from a_p to a_q, t its
+// projected position (0 at a_p, 1 at a_q) and d2 its squared distance from
+// the line: sig(t / 0.1) sig((1 - t) / 0.1) exp(-d2 / (2 sigma_near^2)); 0 for
+// coincident landmarks.
+__device__ __forceinline__ float between_rel(float ex, float ey, float ez, const float *pp, const float *pq,
+                                             const farm_params &p)
+{
+    // rel = e - a_p and seg = a_q - a_p exactly, each as a rounded part plus
+    // its error (TwoSum): the landmarks of a Between may lie a hundred metres
+    // apart while e stays close to their line, and the rounding of those
+    // differences would otherwise dominate d^2
+    const float pe[3] = {ex, ey, ez};
+    float rh[3], rl[3], sh[3], sl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        two_sum(pe[k], -pp[k], rh[k], rl[k]);
+        two_sum(pq[k], -pp[k], sh[k], sl[k]);
+    }
+    const float ss = sh[0] * sh[0] + sh[1] * sh[1] + sh[2] * sh[2];
+    if (!(ss > 0.f)) return 0.f;
+    const float t = (rh[0] * sh[0] + rh[1] * sh[1] + rh[2] * sh[2]) / ss;
+    // d^2 = |rel x seg|^2 / |seg|^2 (free of t's rounding); each component
+    // a b - c d by Kahan's FMA difference of products, plus the first-order
+    // terms of the low parts
+    float c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+        c[k] = diff_of_products(rh[i], sh[j], rh[j], sh[i]) +
+               ((rh[i] * sl[j] + rl[i] * sh[j]) - (rh[j] * sl[i] + rl[j] * sh[i]));
+    }
+    const float d2 = (c[0] * c[0] + c[1] * c[1] + c[2] * c[2]) / ss;
+    return sigm(t / 0.1f) * sigm((1.f - t) / 0.1f) * expf(-0.5f * d2 / (p.sigma_near * p.sigma_near));
+}
+
 // What a relation needs beyond the two objects: the candidate's staged views
 // and the query's Closest / Farthest candidate set (its kc best target
 // candidates, indices and centres).
@@ -367,6 +412,7 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
         uint32_t bh[FARM_MAX_CONSTRAINTS] = {0u, 0u, 0u, 0u}, bl[FARM_MAX_CONSTRAINTS] = {0u, 0u, 0u, 0u};
         for (int t = lane; t < per; t += 32) {
             const int i = t / klm, l = t - i * klm;
+            if (pred_of(i) >= FARM_BETWEEN) continue;        // Between pairs: below
             const int32_t ai = lm_idx[i * KM + l];
             if (ai == e || ai < 0) continue;
             const float *ap = lm_pos + (i * KM + l) * 3;
@@ -384,28 +430,56 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
 #pragma unroll
         for (int c = 0; c < FARM_MAX_CONSTRAINTS; ++c) {
             if (c >= m) break;
+            if (pred_of(c) >= FARM_BETWEEN) continue;
             const uint32_t h = __reduce_max_sync(0xffffffffu, bh[c]);
             const uint32_t lo = __reduce_max_sync(0xffffffffu, bh[c] == h ? bl[c] : 0u);
             if (lane == 0) best[pos * FARM_MAX_CONSTRAINTS + c] = ((unsigned long long)h << 32) | lo;
+        }
+        // Between pairs (constraints c, c + 1): the best (a_p, a_q) over
+        // L_c x L_{c+1} -- exact elimination of the pair -- with the larger r,
+        // then the lower a_p, then the lower a_q
+        for (int c = 0; c + 1 < m; ++c) {
+            if (pred_of(c) != FARM_BETWEEN) continue;
+            uint32_t h = 0u, wp = 0u, wq = 0u;
+            for (int t = lane; t < klm * klm; t += 32) {
+                const int x = t / klm, y = t - x * klm;
+                const int32_t ap = lm_idx[c * KM + x], aq = lm_idx[(c + 1) * KM + y];
+                if (ap < 0 || aq < 0 || ap == e || aq == e || ap == aq) continue;
+                const float r = between_rel(ex, ey, ez, lm_pos + (c * KM + x) * 3, lm_pos + ((c + 1) * KM + y) * 3, p);
+                const uint32_t rh = __float_as_uint(r), lp = 0xffffffffu - (uint32_t)ap,
+                               lq = 0xffffffffu - (uint32_t)aq;
+                if (rh > h || (rh == h && (lp > wp || (lp == wp && lq > wq)))) { h = rh; wp = lp; wq = lq; }
+            }
+            const uint32_t hm = __reduce_max_sync(0xffffffffu, h);
+            const uint32_t pm = __reduce_max_sync(0xffffffffu, h == hm ? wp : 0u);
+            const uint32_t qm = __reduce_max_sync(0xffffffffu, (h == hm && wp == pm) ? wq : 0u);
+            if (lane == 0) {
+                best[pos * FARM_MAX_CONSTRAINTS + c] = ((unsigned long long)hm << 32) | pm;
+                best[pos * FARM_MAX_CONSTRAINTS + c + 1] = ((unsigned long long)hm << 32) | qm;
+            }
         }
         __syncwarp();      // the warp's view slot is rewritten for its next survivor
     }
     __syncthreads();
     for (int pos = tid; pos < ns; pos += TH) {
         const int c = surv[pos];
+        // the factors of the geometric mean: a Between pair counts once
         float t[FARM_MAX_CONSTRAINTS];
+        int mf = 0;
         bool zero = false;
         for (int i = 0; i < m; ++i) {
+            if (pred_of(i) == FARM_BETWEEN_AND) continue;
             const unsigned long long b = best[pos * FARM_MAX_CONSTRAINTS + i];
-            t[i] = b ? __uint_as_float((uint32_t)(b >> 32)) : 0.f;
-            zero |= !(t[i] > 0.f);
+            t[mf] = b ? __uint_as_float((uint32_t)(b >> 32)) : 0.f;
+            zero |= !(t[mf] > 0.f);
+            ++mf;
         }
         float g;
-        if (m == 0) g = 1.f;
+        if (mf == 0) g = 1.f;
         else if (zero) g = 0.f;
-        else if (m == 1) g = t[0];
-        else if (m == 2) g = sqrtf(t[0] * t[1]);
-        else if (m == 3) g = cbrtf(t[0] * t[1] * t[2]);
+        else if (mf == 1) g = t[0];
+        else if (mf == 2) g = sqrtf(t[0] * t[1]);
+        else if (mf == 3) g = cbrtf(t[0] * t[1] * t[2]);
         else g = sqrtf(sqrtf(t[0] * t[1]) * sqrtf(t[2] * t[3]));
         const float s = ssem[c] * ((1.f - p.w) + p.w * g);
         key[pos] = ((uint64_t)order_key(s) << 32) | (uint64_t)(0xffffffffu - (uint32_t)cand_e[c]);

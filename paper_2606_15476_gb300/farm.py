@@ -58,6 +58,8 @@ def _load():
         "farm_query_batch": (C.c_int, [P, I64, P, P, P, P, P, P, I32, U32, P]),
         "farm_memory_add_space": (C.c_int, [P, I32, I32, I32, P, U32]),
         "farm_query_batch_rrf": (C.c_int, [P, I32, I64, I32, P, P, P, P, P, P, U32, P]),
+        "farm_associate": (C.c_int, [P, I64, P, P, P, P, P, I64, P, P, P, I32, C.c_float, C.c_float, I32,
+                                     P, P, P, P, P, P, P, P, U32]),
         "farm_topk": (C.c_int, [P, U64, I32, P, P, P, P, U32]),
         "farm_sync": (C.c_int, [P]),
         "farm_similarity": (C.c_int, [P, I32, I64, P, I32, P, U32]),
@@ -90,7 +92,7 @@ _lib = _load()
 
 def exported_symbols():
     return ["farm_default_params", "farm_create", "farm_destroy", "farm_memory_upload",
-            "farm_query_batch", "farm_memory_add_space", "farm_query_batch_rrf", "farm_topk", "farm_sync", "farm_similarity", "farm_scene_info",
+            "farm_query_batch", "farm_memory_add_space", "farm_query_batch_rrf", "farm_associate", "farm_topk", "farm_sync", "farm_similarity", "farm_scene_info",
             "farm_select_fallbacks", "farm_sim_tuning", "farm_sim_variant_pin", "farm_similarity_variant",
             "farm_candidates",
             "farm_rank_rows_noalloc", "farm_mlp_set", "farm_mlp_get", "farm_mlp_loss_grad",
@@ -232,6 +234,38 @@ def farm_query_batch_rrf(ctx, scene_id: int, channels, tgt_embs, tgt_cls, c_off,
     _ck(ctx, _lib.farm_query_batch_rrf(ctx, int(scene_id), n_q, len(channels), chs, te.ptr, tc.ptr, co.ptr, cp.ptr,
                                        ce.ptr, _flags(te, ce), C.byref(h)))
     return int(h.value)
+
+
+def farm_associate(ctx, ent, det, tau_f: float, h_max: float, max_m: int, out=None) -> dict:
+    """Mapping-side association (see farm.h).  ent: dict(mu [3, N], cov [6, N],
+    feat [N, F], active [N], w [N]); det: dict(mu [3, B], cov [6, B],
+    feat [B, F]); all numpy, or all CUDA tensors (then `out` may hold CUDA
+    tensors for the results)."""
+    arrs = [_Arr(ent["mu"], np.float32, "ent_mu"), _Arr(ent["cov"], np.float32, "ent_cov"),
+            _Arr(ent["feat"], np.float32, "ent_feat"), _Arr(ent["active"], np.int32, "ent_active"),
+            _Arr(ent["w"], np.float32, "ent_w"), _Arr(det["mu"], np.float32, "det_mu"),
+            _Arr(det["cov"], np.float32, "det_cov"), _Arr(det["feat"], np.float32, "det_feat")]
+    N, B = int(ent["mu"].shape[1]), int(det["mu"].shape[1])
+    F = int(ent["feat"].shape[1])
+    T = N + B
+    dev = _flags(*arrs) == PTR_DEVICE
+    if out is None:
+        if dev:
+            import torch
+            mk = lambda shape, dt: torch.empty(shape, dtype=dt, device="cuda")   # noqa: E731
+            i32, f32 = torch.int32, torch.float32
+        else:
+            mk = lambda shape, dt: np.empty(shape, dtype=dt)   # noqa: E731
+            i32, f32 = np.int32, np.float32
+        out = dict(match_cnt=mk((B,), i32), match_idx=mk((B, max_m), i32), match_h=mk((B, max_m), f32),
+                   parent=mk((T,), i32), w=mk((T,), f32), mu=mk((3, T), f32), cov=mk((6, T), f32),
+                   feat=mk((T, F), f32))
+    keys = ["match_cnt", "match_idx", "match_h", "parent", "w", "mu", "cov", "feat"]
+    ptr = lambda x: C.c_void_p(x.data_ptr()) if _is_cuda_tensor(x) else x.ctypes.data_as(C.c_void_p)  # noqa: E731
+    _ck(ctx, _lib.farm_associate(ctx, N, *[a.ptr for a in arrs[:5]], B, *[a.ptr for a in arrs[5:]], F,
+                                 float(tau_f), float(h_max), int(max_m), *[ptr(out[k]) for k in keys],
+                                 PTR_DEVICE if dev else 0))
+    return out
 
 
 def farm_topk(ctx, handle: int, k: int, n_q: int, out_idx=None, out_score=None, out_pred=None,

@@ -267,7 +267,7 @@ def test_invalid_calls(F, ctx, room):
     bad.scene_of_q[:] = 77                        # unknown scene
     with pytest.raises(F.FarmError):
         run(F, ctx, bad, prec_code(F, DEFAULT))
-    for code in (13, -1):   # unknown predicate codes (0..12 are defined)
+    for code in (15, -1):   # unknown predicate codes (0..14 are defined)
         bad = sub.subset(range(4))
         bad.c_pred[:] = code
         if bad.n_c:

@@ -1,9 +1,11 @@
 """GPU parity for the further predicates of App. D.2 step 4 (NextTo, On,
 InFrontOf, Behind, Closest, Farthest, Inside) and the Hellinger form of Near
-(Sec. 2.3) next to the first five, through the C ABI, against the FP64 oracle
+(Sec. 2.3) and the ternary Between (App. B) next to the first five, through
+the C ABI, against the FP64 oracle
 with the tie-tolerant checker.
 
-Queries draw every constraint's predicate uniformly from all thirteen codes;
+Queries draw every constraint's predicate uniformly from all fifteen codes
+(a Between takes two consecutive constraints);
 the scenes are the room (200 objects, 4 views) and a slice of the
 20,000-object site (8 views), plus a hand-built scene whose answer is fixed.
 """
@@ -16,7 +18,7 @@ from synth import QueryBatch
 
 pytestmark = pytest.mark.gpu
 
-ALL = list(range(13))
+ALL = list(range(15))
 
 
 @pytest.fixture(scope="module")
@@ -136,3 +138,22 @@ def test_hand_built_inside(F, ctx):
     assert float(out["score"][0, 0]) == pytest.approx(1.0 / 7.0, rel=1e-6)
     rep = parity.check_topk(sc, qb, 2, out["idx"], out["score"], out["pred"], out["anchor"])
     assert rep.ok(), rep.summary()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_simt"])
+def test_between_pairs(F, ctx, prec):
+    """Queries made mostly of Between pairs (with Above / Near beside them)."""
+    scenes, _ = synth.workload("room_n200_d512")
+    sc = scenes[0]
+    F.farm_memory_upload(ctx, 64, sc.desc, sc.cls, sc.box, sc.views)
+    qb = synth.make_queries(605, sc, 96, m_choices=(2, 3, 4), scene_id=64, preds=[13, 13, 0, 4])
+    assert int(np.sum(qb.c_pred == 13)) >= 40
+    code = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT}[prec]
+    h, out = _run(F, ctx, qb, code)
+    rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"])
+    assert rep.ok(), rep.summary()
+    # a malformed pair is rejected before anything runs
+    bad = qb.subset(range(4))
+    bad.c_pred[:] = 14
+    with pytest.raises(F.FarmError):
+        _run(F, ctx, bad, code)

@@ -6,7 +6,7 @@ Scenes: the room (200 objects) with two further spaces, a 9,000-object scene
 (its target rows take the shared-memory select: fewer 32-object groups than
 the channel list length), a 30-object scene (every list holds every object)
 and a slice of the 20,000-object site with spaces of 1,024 and 2,048
-dimensions.  Queries draw predicates from all thirteen codes.
+dimensions.  Queries draw predicates from all fifteen codes (Between pairs included).
 """
 import numpy as np
 import pytest
@@ -50,7 +50,7 @@ def _case(scene_seed, n, dim, dims, n_q, extent, n_classes=16, distractors=0, m_
     sc = synth.make_scene(scene_seed, n, dim, extent=extent, n_classes=n_classes, n_views=4,
                           distractor_classes=distractors, distractor_frac=0.3 if distractors else 0.0)
     sp = synth.add_spaces(sc, scene_seed + 50, dims=dims)
-    qb = synth.make_queries(scene_seed + 60, sc, n_q, m_choices=m_choices, preds=list(range(13)),
+    qb = synth.make_queries(scene_seed + 60, sc, n_q, m_choices=m_choices, preds=list(range(15)),
                             distractor_classes=distractors, distractor_target_frac=0.5 if distractors else 0.0)
     cq = synth.channel_queries(scene_seed + 70, sc, sp, qb)
     return sc, sp, qb, cq
@@ -77,7 +77,7 @@ def test_fused_site_slice(F, ctx):
     sc = scenes[0]
     sp = synth.add_spaces(sc, 801, dims=(1024, 2048))
     qb = synth.make_queries(802, sc, 96, m_choices=(1, 2, 3, 4), distractor_classes=20,
-                            distractor_target_frac=0.5, preds=list(range(13)))
+                            distractor_target_frac=0.5, preds=list(range(15)))
     cq = synth.channel_queries(803, sc, sp, qb)
     _upload(F, ctx, 71, sc, sp)
     h, out = _run(F, ctx, 71, qb, cq)

@@ -31,7 +31,7 @@ P = OracleParams()
 def _small(seed=0, n=40, dims=(24, 16, 32)):
     sc = synth.make_scene(seed, n, dims[0], extent=(6.0, 6.0, 3.0), n_classes=5, n_views=3)
     sp = synth.add_spaces(sc, seed + 100, dims=dims[1:])
-    qb = synth.make_queries(seed + 200, sc, 6, m_choices=(0, 1, 2, 3), preds=list(range(13)))
+    qb = synth.make_queries(seed + 200, sc, 6, m_choices=(0, 1, 2, 3), preds=list(range(15)))
     cq = synth.channel_queries(seed + 300, sc, sp, qb)
     return sc, sp, qb, cq
 
