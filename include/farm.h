@@ -308,9 +308,11 @@ farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, i
  * untouched entity or a new entity), out_w [T] (0 for slots merged away),
  * out_mu [3, T], out_cov [6, T], out_feat [T, F] (zero for merged slots).
  * 1 <= max_m <= 64, F <= 8192, tau_f in [-1, 1], h_max in [0, 1].  All
- * arrays host memory, or all device memory with FARM_PTR_DEVICE.  The call
- * synchronises.  A detection with more than 1,024 entities within the
- * budget is reported as FARM_EINVAL.
+ * arrays host memory, or all device memory with FARM_PTR_DEVICE.  With host
+ * arrays the call synchronises and reports device-side errors; with device
+ * arrays its work is enqueued on the context's stream (errors come with the
+ * next synchronising call).  A detection with more than 1,024 entities
+ * within the budget is reported as FARM_EINVAL.
  */
 farm_status farm_associate(farm_ctx *ctx, int64_t n_ent, const float *ent_mu, const float *ent_cov,
                            const float *ent_feat, const int32_t *ent_active, const float *ent_w, int64_t n_det,

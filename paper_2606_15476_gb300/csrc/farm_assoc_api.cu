@@ -18,23 +18,18 @@ farm_status afail(Ctx &c, farm_status st, const std::string &msg)
     return st;
 }
 
-// One call's device memory, freed when the call returns.
-struct DevBufs {
-    cudaStream_t stream = nullptr;
-    std::vector<void *> ptrs;
-    ~DevBufs()
-    {
-        if (stream) cudaStreamSynchronize(stream);    // no work of the call still uses them
-        for (void *p : ptrs) cudaFree(p);
-    }
+// Sub-arrays carved from the context's grow-only association buffer (each
+// on a 256-byte boundary): a first pass sums the sizes, the second hands out
+// pointers.
+struct Carve {
+    uint8_t *base = nullptr;
+    size_t off = 0;
     template <class T>
-    cudaError_t get(T **out, size_t count)
+    T *take(size_t count)
     {
-        void *p = nullptr;
-        const cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
-        if (e == cudaSuccess) ptrs.push_back(p);
-        *out = static_cast<T *>(p);
-        return e;
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += (std::max<size_t>(count, 1) * sizeof(T) + 255) & ~size_t(255);
+        return p;
     }
 };
 
@@ -78,49 +73,63 @@ extern "C" farm_status farm_associate(farm_ctx *ctx, int64_t n_ent, const float 
         if (st_ != FARM_OK) return st_;                \
     } while (0)
     ACK(cudaSetDevice(c.device), "set device");
-    DevBufs db;
-    db.stream = c.stream;
-    // inputs on the device
+    farm::AssocArgs a{};
     const float *d_emu = ent_mu, *d_ecov = ent_cov, *d_efeat = ent_feat, *d_ew = ent_w;
     const int32_t *d_eact = ent_active;
     const float *d_dmu = det_mu, *d_dcov = det_cov, *d_dfeat = det_feat;
+    uint16_t *dhi = nullptr, *dlo = nullptr, *ehi = nullptr, *elo = nullptr;
+    float *S = nullptr;
+    float *h_emu = nullptr, *h_ecov = nullptr, *h_efeat = nullptr, *h_ew = nullptr, *h_dmu = nullptr,
+          *h_dcov = nullptr, *h_dfeat = nullptr;
+    int32_t *h_eact = nullptr;
+    // the layout of the call's device memory: sized with a null base, then
+    // carved from the context's grow-only buffer
+    auto layout = [&](Carve &cv) {
+        if (!dev) {
+            h_emu = cv.take<float>((size_t)3 * N); h_ecov = cv.take<float>((size_t)6 * N);
+            h_efeat = cv.take<float>((size_t)N * F); h_ew = cv.take<float>((size_t)N);
+            h_eact = cv.take<int32_t>((size_t)N); h_dmu = cv.take<float>((size_t)3 * B);
+            h_dcov = cv.take<float>((size_t)6 * B); h_dfeat = cv.take<float>((size_t)B * F);
+        }
+        dhi = cv.take<uint16_t>((size_t)B * F_pad); dlo = cv.take<uint16_t>((size_t)B * F_pad);
+        ehi = cv.take<uint16_t>((size_t)N * F_pad); elo = cv.take<uint16_t>((size_t)N * F_pad);
+        S = cv.take<float>((size_t)B * ld);
+        a.label = cv.take<int32_t>((size_t)T);
+        a.win = cv.take<unsigned long long>((size_t)T);
+        a.acc = cv.take<float>((size_t)T * (10 + F));
+        if (dev) {
+            a.match_cnt = match_cnt; a.match_idx = match_idx; a.match_h = match_h; a.parent = parent;
+            a.out_w = out_w; a.out_mu = out_mu; a.out_cov = out_cov; a.out_feat = out_feat;
+        } else {
+            a.match_cnt = cv.take<int32_t>((size_t)B); a.match_idx = cv.take<int32_t>((size_t)B * max_m);
+            a.match_h = cv.take<float>((size_t)B * max_m); a.parent = cv.take<int32_t>((size_t)T);
+            a.out_w = cv.take<float>((size_t)T); a.out_mu = cv.take<float>((size_t)3 * T);
+            a.out_cov = cv.take<float>((size_t)6 * T); a.out_feat = cv.take<float>((size_t)T * F);
+        }
+    };
+    {
+        Carve sizing;
+        layout(sizing);
+        void *buf = nullptr;
+        ACK(farm::ws_alloc(ctx, farm::B_ASSOC, sizing.off, &buf), "workspace");
+        Carve cv;
+        cv.base = static_cast<uint8_t *>(buf);
+        layout(cv);
+    }
     if (!dev) {
-        float *p;
-        int32_t *pi;
         const cudaMemcpyKind k = cudaMemcpyHostToDevice;
-        ACK(db.get(&p, (size_t)3 * N), "alloc");
-        ACK(cudaMemcpyAsync(p, ent_mu, (size_t)3 * N * 4, k, c.stream), "copy");
-        d_emu = p;
-        ACK(db.get(&p, (size_t)6 * N), "alloc");
-        ACK(cudaMemcpyAsync(p, ent_cov, (size_t)6 * N * 4, k, c.stream), "copy");
-        d_ecov = p;
-        ACK(db.get(&p, (size_t)N * F), "alloc");
-        ACK(cudaMemcpyAsync(p, ent_feat, (size_t)N * F * 4, k, c.stream), "copy");
-        d_efeat = p;
-        ACK(db.get(&p, (size_t)N), "alloc");
-        ACK(cudaMemcpyAsync(p, ent_w, (size_t)N * 4, k, c.stream), "copy");
-        d_ew = p;
-        ACK(db.get(&pi, (size_t)N), "alloc");
-        ACK(cudaMemcpyAsync(pi, ent_active, (size_t)N * 4, k, c.stream), "copy");
-        d_eact = pi;
-        ACK(db.get(&p, (size_t)3 * B), "alloc");
-        ACK(cudaMemcpyAsync(p, det_mu, (size_t)3 * B * 4, k, c.stream), "copy");
-        d_dmu = p;
-        ACK(db.get(&p, (size_t)6 * B), "alloc");
-        ACK(cudaMemcpyAsync(p, det_cov, (size_t)6 * B * 4, k, c.stream), "copy");
-        d_dcov = p;
-        ACK(db.get(&p, (size_t)B * F), "alloc");
-        ACK(cudaMemcpyAsync(p, det_feat, (size_t)B * F * 4, k, c.stream), "copy");
-        d_dfeat = p;
+        ACK(cudaMemcpyAsync(h_emu, ent_mu, (size_t)3 * N * 4, k, c.stream), "copy");
+        ACK(cudaMemcpyAsync(h_ecov, ent_cov, (size_t)6 * N * 4, k, c.stream), "copy");
+        ACK(cudaMemcpyAsync(h_efeat, ent_feat, (size_t)N * F * 4, k, c.stream), "copy");
+        ACK(cudaMemcpyAsync(h_ew, ent_w, (size_t)N * 4, k, c.stream), "copy");
+        ACK(cudaMemcpyAsync(h_eact, ent_active, (size_t)N * 4, k, c.stream), "copy");
+        ACK(cudaMemcpyAsync(h_dmu, det_mu, (size_t)3 * B * 4, k, c.stream), "copy");
+        ACK(cudaMemcpyAsync(h_dcov, det_cov, (size_t)6 * B * 4, k, c.stream), "copy");
+        ACK(cudaMemcpyAsync(h_dfeat, det_feat, (size_t)B * F * 4, k, c.stream), "copy");
+        d_emu = h_emu; d_ecov = h_ecov; d_efeat = h_efeat; d_ew = h_ew; d_eact = h_eact;
+        d_dmu = h_dmu; d_dcov = h_dcov; d_dfeat = h_dfeat;
     }
     // feature cosines: unit rows in the FP16 split, the FP32-accurate similarity kernel
-    uint16_t *dhi, *dlo, *ehi, *elo;
-    float *S;
-    ACK(db.get(&dhi, (size_t)B * F_pad), "alloc");
-    ACK(db.get(&dlo, (size_t)B * F_pad), "alloc");
-    ACK(db.get(&ehi, (size_t)N * F_pad), "alloc");
-    ACK(db.get(&elo, (size_t)N * F_pad), "alloc");
-    ACK(db.get(&S, (size_t)B * ld), "alloc");
     c.launches += 3;
     ACK(farm::launch_normalize_rows(d_dfeat, nullptr, B, F, F_pad, nullptr, dhi, dlo, nullptr, c.d_err,
                                     farm::kErrBadRow, c.stream), "normalise detections");
@@ -130,7 +139,6 @@ extern "C" farm_status farm_associate(farm_ctx *ctx, int64_t n_ent, const float 
     ACK(farm::launch_sim_tc_f16x3(dhi, dlo, ehi, elo, S, B, N, F_pad, ld, nullptr, c.num_sms, c.d_err, c.stream),
         "feature cosines");
     // search, components, fusion
-    farm::AssocArgs a{};
     a.N = N;
     a.B = B;
     a.F = F;
@@ -148,28 +156,6 @@ extern "C" farm_status farm_associate(farm_ctx *ctx, int64_t n_ent, const float 
     a.h_max = h_max;
     a.max_m = max_m;
     a.err = c.d_err;
-    ACK(db.get(&a.label, (size_t)T), "alloc");
-    ACK(db.get(&a.win, (size_t)T), "alloc");
-    ACK(db.get(&a.acc, (size_t)T * (10 + F)), "alloc");
-    if (dev) {
-        a.match_cnt = match_cnt;
-        a.match_idx = match_idx;
-        a.match_h = match_h;
-        a.parent = parent;
-        a.out_w = out_w;
-        a.out_mu = out_mu;
-        a.out_cov = out_cov;
-        a.out_feat = out_feat;
-    } else {
-        ACK(db.get(&a.match_cnt, (size_t)B), "alloc");
-        ACK(db.get(&a.match_idx, (size_t)B * max_m), "alloc");
-        ACK(db.get(&a.match_h, (size_t)B * max_m), "alloc");
-        ACK(db.get(&a.parent, (size_t)T), "alloc");
-        ACK(db.get(&a.out_w, (size_t)T), "alloc");
-        ACK(db.get(&a.out_mu, (size_t)3 * T), "alloc");
-        ACK(db.get(&a.out_cov, (size_t)6 * T), "alloc");
-        ACK(db.get(&a.out_feat, (size_t)T * F), "alloc");
-    }
     c.launches += 9;
     ACK(farm::launch_assoc(a, c.stream), "association kernels");
     if (!dev) {
@@ -183,7 +169,7 @@ extern "C" farm_status farm_associate(farm_ctx *ctx, int64_t n_ent, const float 
         ACK(cudaMemcpyAsync(out_cov, a.out_cov, (size_t)6 * T * 4, k, c.stream), "copy out");
         ACK(cudaMemcpyAsync(out_feat, a.out_feat, (size_t)T * F * 4, k, c.stream), "copy out");
     }
-    // the call's buffers are freed on return: wait for the work that uses them
+    if (dev) return FARM_OK;            // stream-ordered; errors at the next synchronising call
     ACK(cudaStreamSynchronize(c.stream), "synchronise");
     return farm_sync(ctx);
 #undef ACK

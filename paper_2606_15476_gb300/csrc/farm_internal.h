@@ -108,6 +108,7 @@ enum Buf {
     B_MC_LLIST,     // int32 [n_ch, n_c, R_l] per-channel landmark lists
     B_MC_FUSED,     // float [n_q, RF] fused scores of the kept target candidates
     B_SELLIST,      // int32 [1 + rows] rows the warp-level select hands to the block-level one
+    B_ASSOC,        // farm_associate: its inputs' copies, operand rows, similarity block and scratch
     B_COUNT
 };
 

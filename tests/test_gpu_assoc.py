@@ -94,6 +94,7 @@ def test_site_association_and_device_pointers(F, ctx):
     dent = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in ent.items()}
     ddet = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in det.items()}
     gd = F.farm_associate(ctx, dent, ddet, TAU, HMAX, MM)
+    F.farm_sync(ctx)          # device outputs are written on the context's stream
     for k in ("match_cnt", "match_idx", "parent"):
         assert np.array_equal(gd[k].cpu().numpy(), got[k])
     assert np.allclose(gd["mu"].cpu().numpy(), got["mu"], atol=2e-5)
