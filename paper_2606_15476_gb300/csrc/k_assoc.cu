@@ -72,9 +72,15 @@ assoc_search_kernel(const float *__restrict__ S, int64_t ld, int32_t N, int32_t 
     for (int k = 0; k < 3; ++k) md[k] = det_mu[(int64_t)k * B + d];
 #pragma unroll
     for (int k = 0; k < 6; ++k) cd[k] = det_cov[(int64_t)k * B + d];
+    // the row is streamed in float4 loads, four in flight per thread (its
+    // leading dimension is a multiple of 32 floats, so the row is 16-byte
+    // aligned and a load never leaves it); only entities past the cosine
+    // prefilter -- few -- are looked up further
     const float *row = S + (int64_t)d * ld;
-    for (int e = tid; e < N; e += TA) {
-        if (!ent_active[e] || !(row[e] >= tau_f)) continue;
+    const float4 *row4 = reinterpret_cast<const float4 *>(row);
+    const int n4 = (N + 3) >> 2;
+    auto consider = [&](int e) {
+        if (!ent_active[e]) return;
         float me[3], ce[6];
 #pragma unroll
         for (int k = 0; k < 3; ++k) me[k] = ent_mu[(int64_t)k * N + e];
@@ -84,6 +90,22 @@ assoc_search_kernel(const float *__restrict__ S, int64_t ld, int32_t N, int32_t 
         if (h <= h_max) {
             const int pos = atomicAdd(&s_cnt, 1);
             if (pos < CAPA) cand[pos] = ((uint64_t)__float_as_uint(h) << 32) | (uint32_t)e;   // H >= 0: bits order like H
+        }
+    };
+    for (int g0 = 0; g0 < n4; g0 += TA * 4) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int g = g0 + u * TA + tid;
+            v[u] = g < n4 ? __ldcs(row4 + g) : make_float4(-2.f, -2.f, -2.f, -2.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e0 = 4 * (g0 + u * TA + tid);
+            const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (x[c] >= tau_f && e0 + c < N) consider(e0 + c);
         }
     }
     __syncthreads();

@@ -248,7 +248,9 @@ select_thresh_list_kernel(const float *__restrict__ S, const float *__restrict__
 
 // ---------------------------------------------------------------------------
 // Warp-level select: one warp per row for the common case -- a list of at
-// most WS_R entries, at most 1,024 group maxima -- with no block barriers.
+// most WS_R entries, at most 1,024 group maxima (or, for a row with fewer
+// group maxima than its list length, at most 1,024 entries, ranked
+// directly) -- with no block barriers.
 // The R-th largest group-maximum key T is found by a bitwise search (the
 // largest T with #{keys >= T} >= R), the groups whose maximum reaches it are
 // gathered, and the candidates are ranked by counting (their words are all
@@ -293,15 +295,19 @@ select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, 
     const int n = pc.n;
     const int gshift = pc.gshift;
     const int64_t n_groups = group_count(n, gshift);
-    if (R > WS_R || n_groups > 32 * WS_KPL || n_groups < R) { hand_on(); return; }
-    const int U = (int)n_groups;
+    // a row with fewer group maxima than R (a short row) ranks its entries
+    // themselves: their R-th largest key, then every entry reaching it
+    const bool entries = n_groups < R;
+    if (R > WS_R || (entries ? (int64_t)n : n_groups) > 32 * WS_KPL) { hand_on(); return; }
+    const int U = entries ? n : (int)n_groups;
     const int kpl = (U + 31) >> 5;
+    const float *row = S + pc.s_off + (int64_t)i * pc.ld;
     const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(n, gshift);
     uint32_t key[WS_KPL];
 #pragma unroll
     for (int k = 0; k < WS_KPL; ++k) {
         const int g = lane + 32 * k;
-        key[k] = (k < kpl && g < U) ? order_key(__ldg(tp + g)) : 0u;    // 0: below every key of a value
+        key[k] = (k < kpl && g < U) ? order_key(entries ? __ldcs(row + g) : __ldg(tp + g)) : 0u;  // 0: no value
     }
     // T: the R-th largest key.  It lies between the smallest and the largest
     // key, so it shares their common leading bits; the search sets the bits
@@ -341,49 +347,63 @@ select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, 
             if (tot > (unsigned)R) T = c;
         }
     }
-    // the groups whose maximum reaches T
-    int ng = 0;
-#pragma unroll
-    for (int k = 0; k < WS_KPL; ++k) {
-        if (k >= kpl) break;
-        const bool q = key[k] >= T;
-        const unsigned bal = __ballot_sync(FULL, q);
-        if (q) {
-            const int pos = ng + __popc(bal & lt);
-            if (pos < WS_GL) glist[pos] = (uint32_t)(lane + 32 * k);
-        }
-        ng += __popc(bal);
-    }
-    if (ng > WS_GL) { hand_on(); return; }
-    __syncwarp();
-    // their entries >= tau
-    const float tau = key_value(T);
-    const float *row = S + pc.s_off + (int64_t)i * pc.ld;
-    const int gmask = (1 << gshift) - 1;
-    const int slots = ng << gshift;
     int cnt = 0;
-    for (int s0 = 0; s0 < slots; s0 += 32 * 4) {
-        float x[4];
-        int j[4];
+    if (entries) {
+        // the entries reaching T (the top R and their ties) are the candidates
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int sl = s0 + 32 * u + lane;
-            j[u] = -1;
-            if (sl < slots) {
-                const int jj = (int)((glist[sl >> gshift] << gshift) + (sl & gmask));
-                if (jj < n) j[u] = jj;
-            }
-            x[u] = j[u] >= 0 ? __ldcs(row + j[u]) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool q = j[u] >= 0 && x[u] >= tau;
+        for (int k = 0; k < WS_KPL; ++k) {
+            if (k >= kpl) break;
+            const bool q = key[k] >= T;
             const unsigned bal = __ballot_sync(FULL, q);
             if (q) {
                 const int pos = cnt + __popc(bal & lt);
-                if (pos < WS_CAP) cand[pos] = cand_word(order_key(x[u]), j[u]);
+                if (pos < WS_CAP) cand[pos] = cand_word(key[k], lane + 32 * k);
             }
             cnt += __popc(bal);
+        }
+    } else {
+        // the groups whose maximum reaches T
+        int ng = 0;
+#pragma unroll
+        for (int k = 0; k < WS_KPL; ++k) {
+            if (k >= kpl) break;
+            const bool q = key[k] >= T;
+            const unsigned bal = __ballot_sync(FULL, q);
+            if (q) {
+                const int pos = ng + __popc(bal & lt);
+                if (pos < WS_GL) glist[pos] = (uint32_t)(lane + 32 * k);
+            }
+            ng += __popc(bal);
+        }
+        if (ng > WS_GL) { hand_on(); return; }
+        __syncwarp();
+        // their entries >= tau
+        const float tau = key_value(T);
+        const int gmask = (1 << gshift) - 1;
+        const int slots = ng << gshift;
+        for (int s0 = 0; s0 < slots; s0 += 32 * 4) {
+            float x[4];
+            int j[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int sl = s0 + 32 * u + lane;
+                j[u] = -1;
+                if (sl < slots) {
+                    const int jj = (int)((glist[sl >> gshift] << gshift) + (sl & gmask));
+                    if (jj < n) j[u] = jj;
+                }
+                x[u] = j[u] >= 0 ? __ldcs(row + j[u]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool q = j[u] >= 0 && x[u] >= tau;
+                const unsigned bal = __ballot_sync(FULL, q);
+                if (q) {
+                    const int pos = cnt + __popc(bal & lt);
+                    if (pos < WS_CAP) cand[pos] = cand_word(order_key(x[u]), j[u]);
+                }
+                cnt += __popc(bal);
+            }
         }
     }
     if (cnt > WS_CAP || cnt < R) { hand_on(); return; }
