@@ -388,7 +388,7 @@ cudaError_t launch_merge_chunks(const Piece *pieces, int32_t n_pieces, int64_t t
 // whose candidates overflow fall back to an exact global-memory select and
 // are counted in *n_fallback (device).  Outputs as launch_select_grouped.
 // With row_list (device, total_blocks + 1 int32 of scratch) a warp-level
-// select takes every row of a list of at most 128 entries and at most 1,024
+// select takes every row of a list of at most 256 entries and at most 1,024
 // group maxima first (one warp per row, no block barriers) and hands the
 // rest to the block-level select; both give the same lists.
 cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,

@@ -55,6 +55,24 @@ __device__ float hellinger_f(const float m1[3], const float c1[6], const float m
     return sqrtf(fmaxf(-expm1f(lbc), 0.f));
 }
 
+// The Hellinger distance of detection (md, cd) to entity e, -1 for an
+// inactive entity.  Kept out of line: the streaming loop that calls it for
+// the few entities past the cosine prefilter is unrolled sixteen-fold, and
+// inlining it there overflowed the instruction cache.
+__device__ __noinline__ float entity_distance(int e, int32_t N, const float *__restrict__ ent_mu,
+                                              const float *__restrict__ ent_cov,
+                                              const int32_t *__restrict__ ent_active, const float md[3],
+                                              const float cd[6])
+{
+    if (!ent_active[e]) return -1.f;
+    float me[3], ce[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) me[k] = ent_mu[(int64_t)k * N + e];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ce[k] = ent_cov[(int64_t)k * N + e];
+    return hellinger_f(md, cd, me, ce);
+}
+
 __global__ void __launch_bounds__(TA)
 assoc_search_kernel(const float *__restrict__ S, int64_t ld, int32_t N, int32_t B, const float *__restrict__ ent_mu,
                     const float *__restrict__ ent_cov, const int32_t *__restrict__ ent_active,
@@ -80,14 +98,8 @@ assoc_search_kernel(const float *__restrict__ S, int64_t ld, int32_t N, int32_t 
     const float4 *row4 = reinterpret_cast<const float4 *>(row);
     const int n4 = (N + 3) >> 2;
     auto consider = [&](int e) {
-        if (!ent_active[e]) return;
-        float me[3], ce[6];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) me[k] = ent_mu[(int64_t)k * N + e];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) ce[k] = ent_cov[(int64_t)k * N + e];
-        const float h = hellinger_f(md, cd, me, ce);
-        if (h <= h_max) {
+        const float h = entity_distance(e, N, ent_mu, ent_cov, ent_active, md, cd);
+        if (h >= 0.f && h <= h_max) {
             const int pos = atomicAdd(&s_cnt, 1);
             if (pos < CAPA) cand[pos] = ((uint64_t)__float_as_uint(h) << 32) | (uint32_t)e;   // H >= 0: bits order like H
         }

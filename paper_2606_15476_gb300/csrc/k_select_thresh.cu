@@ -257,10 +257,10 @@ select_thresh_list_kernel(const float *__restrict__ S, const float *__restrict__
 // distinct).  A row outside these limits, or whose groups or candidates
 // overflow the warp's buffers, is appended to row_list for the block-level
 // select.
-constexpr int WS_R = 128;       // longest list a warp selects
+constexpr int WS_R = 256;       // longest list a warp selects (the BF16 path's 256 candidates)
 constexpr int WS_KPL = 32;      // group maxima per lane (1,024 per row)
-constexpr int WS_GL = 256;      // qualifying groups per warp
-constexpr int WS_CAP = 256;     // candidate words per warp
+constexpr int WS_GL = 320;      // qualifying groups per warp
+constexpr int WS_CAP = 512;     // candidate words per warp
 constexpr int WW = 8;           // warps (rows) per CTA
 
 __global__ void __launch_bounds__(WW * 32, 4)
