@@ -106,7 +106,8 @@ struct Cfg {
     static constexpr int STAGES = STAGE_BUDGET / STAGE_BYTES < 8 ? STAGE_BUDGET / STAGE_BYTES : 8;
     static constexpr int ACC_COLS = OPS * BN_;                  // TMEM columns of one tile's accumulators
     static constexpr int NACC = 512 / ACC_COLS >= 2 ? 2 : 1;    // tiles in flight in TMEM
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int STAGING_BYTES = 4 * 32 * 32 * 4;      // epilogue: one 32 x 32 FP32 block per warp
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES;
     static_assert(BN_ % 128 == 0 && BN_ <= 256, "tile width");
     static_assert(STAGES >= 3, "pipeline depth");
     static_assert(BN_ / CM_ >= 8 && (B_PART % 1024) == 0, "B share must keep the swizzle atoms whole");
@@ -349,6 +350,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     uint64_t *acc_empty = acc_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *staging = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
@@ -472,8 +474,14 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             if (*abort_flag) atomicOr(err, kErrTimeout);
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31.  Each 32-row x
+        // 32-column block passes through the warp's shared-memory block (16-byte
+        // slots XOR-swizzled by row, conflict-free both ways) so that every
+        // store instruction writes four whole 128-byte row segments of S
+        // instead of 16 bytes in each of 32 rows.
         const int quad = warp & 3;
+        float4 *blk = reinterpret_cast<float4 *>(staging + (warp - 2) * 32 * 32);
+        const int sub = lane >> 3, slot = lane & 7;    // read-back: row sub + 4i, 16-byte slot
         uint32_t tc = 0;
         for (int tile = cluster_id; tile < total; tile += n_clusters, ++tc) {
             const uint32_t buf = tc % NACC, use = tc / NACC;
@@ -488,7 +496,8 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             const int64_t r = (int64_t)m0 + quad * 32 + lane;    // row within the piece
             const int64_t rows = pc.rows, n = pc.n;
             const bool live = r < rows;
-            float *srow = S + pc.s_off + r * pc.ld;
+            const int64_t r_blk = (int64_t)m0 + quad * 32;       // first row of the warp's blocks
+            float *sblk = S + pc.s_off + r_blk * pc.ld;
             const bool vec = (pc.ld % 4) == 0;
             const float sr = (MODE == kSimFp8 && live) ? scale_q[pc.q_row0 + r] : 1.f;
             const float *__restrict__ scale_d = pc.scale_d;
@@ -527,17 +536,28 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                         gmax[4 * c + g] = m;
                     }
                 }
-                if (live) {
-                    if (vec && col0 + 32 <= n) {
 #pragma unroll
-                        for (int i = 0; i < 32; i += 4)
-                            *reinterpret_cast<float4 *>(srow + col0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                    } else {
+                for (int j = 0; j < 8; ++j)
+                    blk[lane * 8 + (j ^ (lane & 7))] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                __syncwarp();
+                const int64_t cs = col0 + slot * 4;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            if (col0 + i < n) srow[col0 + i] = v[i];
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = 4 * i + sub;
+                    const float4 x = blk[rr * 8 + (slot ^ (rr & 7))];
+                    if (r_blk + rr < rows) {
+                        float *dst = sblk + (int64_t)rr * pc.ld + cs;
+                        if (vec && cs + 4 <= n) {
+                            *reinterpret_cast<float4 *>(dst) = x;
+                        } else {
+                            if (cs < n) dst[0] = x.x;
+                            if (cs + 1 < n) dst[1] = x.y;
+                            if (cs + 2 < n) dst[2] = x.z;
+                            if (cs + 3 < n) dst[3] = x.w;
+                        }
                     }
                 }
+                __syncwarp();
             }
             if (keep_tops) {
                 float *trow = tops + pc.tops_off + r * group_stride(n, pc.gshift);
