@@ -188,12 +188,12 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
 # variant), valid only while the kernel source is the one captured (sha256
 # prefix).
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 0): 717.308160e6 + 1121.947648e6,
-    ("site_n20k_d1152", "fp32", 1): 1354.266624e6 + 1133.388032e6,
-    ("site_n20k_d1152", "bf16", 0): 359.175680e6 + 1116.801536e6,
-    ("site_n20k_d1152", "bf16", 1): 664.022528e6 + 1117.387776e6,
+    ("site_n20k_d1152", "fp32", 0): 715.113984e6 + 1128.573440e6,
+    ("site_n20k_d1152", "fp32", 1): 1356.524544e6 + 1137.107968e6,
+    ("site_n20k_d1152", "bf16", 0): 355.669760e6 + 1114.267648e6,
+    ("site_n20k_d1152", "bf16", 1): 672.350208e6 + 1118.404608e6,
 }
-SIM_TRAFFIC_SOURCE = "92b2f337ec7b8c77"
+SIM_TRAFFIC_SOURCE = "a16db95eaa148cca"
 
 
 def sim_traffic(workload, precision, variants):

@@ -325,6 +325,26 @@ __device__ __forceinline__ void piece_tile(const GemmPiece &pc, int tile, uint32
     tile_origin<BN_, CM_>(tile - pc.tile_begin, (m_tiles + CM_ - 1) / CM_, n_tiles, rank, m0, n0);
 }
 
+// Store SL float4 values per row of the warp's 32 rows (lane = row) to
+// dst + row * stride through the warp's shared-memory block (slots
+// XOR-swizzled by row), so that a store instruction writes whole row segments
+// of SL * 16 bytes; rows >= rows_left are skipped.
+template <int SL>
+__device__ __forceinline__ void store_rows_staged(float4 *blk, const float4 (&val)[SL], int lane, float *dst,
+                                                  int64_t stride, int64_t rows_left)
+{
+#pragma unroll
+    for (int j = 0; j < SL; ++j) blk[lane * SL + (j ^ (lane & (SL - 1)))] = val[j];
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < SL; ++it) {
+        const int q = it * 32 + lane, rr = q / SL, sl = q % SL;
+        const float4 x = blk[rr * SL + (sl ^ (rr & (SL - 1)))];
+        if (rr < rows_left) *reinterpret_cast<float4 *>(dst + rr * stride + sl * 4) = x;
+    }
+    __syncwarp();
+}
+
 template <int MODE, int BN_, int CM_, bool GROUPED>
 __global__ void __launch_bounds__(THREADS, 1)
 sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant__ CUtensorMap map_q1,
@@ -501,7 +521,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             const bool vec = (pc.ld % 4) == 0;
             const float sr = (MODE == kSimFp8 && live) ? scale_q[pc.q_row0 + r] : 1.f;
             const float *__restrict__ scale_d = pc.scale_d;
-            const bool keep_tops = tops != nullptr && pc.tops_off >= 0 && live;
+            const bool keep_tops = tops != nullptr && pc.tops_off >= 0;    // uniform across the warp
             float gmax[BN / 8];      // maximum of each 8-column group of row r in this tile
 #pragma unroll
             for (int c = 0; c < BN / 32; ++c) {
@@ -560,23 +580,26 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 __syncwarp();
             }
             if (keep_tops) {
-                float *trow = tops + pc.tops_off + r * group_stride(n, pc.gshift);
+                const int64_t gs = group_stride(n, pc.gshift);
+                float *tblk = tops + pc.tops_off + r_blk * gs;
                 if (pc.gshift == kGroupShiftSmall) {
-                    float4 *tp = reinterpret_cast<float4 *>(trow + n0 / 8);
+                    float4 t4[BN / 32];
 #pragma unroll
-                    for (int j = 0; j < BN / 8; j += 4)
-                        tp[j / 4] = make_float4(gmax[j], gmax[j + 1], gmax[j + 2], gmax[j + 3]);
+                    for (int j = 0; j < BN / 32; ++j)
+                        t4[j] = make_float4(gmax[4 * j], gmax[4 * j + 1], gmax[4 * j + 2], gmax[4 * j + 3]);
+                    store_rows_staged<BN / 32>(blk, t4, lane, tblk + n0 / 8, gs, rows - r_blk);
                 } else {
-                    float4 *tp = reinterpret_cast<float4 *>(trow + n0 / 32);
+                    float4 t4[BN / 128];
 #pragma unroll
-                    for (int j = 0; j < BN / 32; j += 4) {
+                    for (int j = 0; j < BN / 128; ++j) {
                         float g4[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            g4[u] = fmaxf(fmaxf(gmax[4 * (j + u)], gmax[4 * (j + u) + 1]),
-                                          fmaxf(gmax[4 * (j + u) + 2], gmax[4 * (j + u) + 3]));
-                        tp[j / 4] = make_float4(g4[0], g4[1], g4[2], g4[3]);
+                            g4[u] = fmaxf(fmaxf(gmax[16 * j + 4 * u], gmax[16 * j + 4 * u + 1]),
+                                          fmaxf(gmax[16 * j + 4 * u + 2], gmax[16 * j + 4 * u + 3]));
+                        t4[j] = make_float4(g4[0], g4[1], g4[2], g4[3]);
                     }
+                    store_rows_staged<BN / 128>(blk, t4, lane, tblk + n0 / 32, gs, rows - r_blk);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
