@@ -188,12 +188,14 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
 # variant), valid only while the kernel source is the one captured (sha256
 # prefix).
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 0): 715.113984e6 + 1128.573440e6,
-    ("site_n20k_d1152", "fp32", 1): 1356.524544e6 + 1137.107968e6,
-    ("site_n20k_d1152", "bf16", 0): 355.669760e6 + 1114.267648e6,
-    ("site_n20k_d1152", "bf16", 1): 672.350208e6 + 1118.404608e6,
+    ("site_n20k_d1152", "fp32", 0): 715.093248e6 + 1129.676288e6,
+    ("site_n20k_d1152", "fp32", 1): 1359.185408e6 + 1138.319872e6,
+    ("site_n20k_d1152", "fp32", 4): 725.757184e6 + 1132.319744e6,
+    ("site_n20k_d1152", "bf16", 0): 355.813888e6 + 1114.249728e6,
+    ("site_n20k_d1152", "bf16", 1): 672.520448e6 + 1118.487040e6,
+    ("site_n20k_d1152", "bf16", 4): 355.888896e6 + 1114.270208e6,
 }
-SIM_TRAFFIC_SOURCE = "a16db95eaa148cca"
+SIM_TRAFFIC_SOURCE = "927f8d17305fbde0"
 
 
 def sim_traffic(workload, precision, variants):
@@ -596,8 +598,9 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "autotuned_tiles": [{"mode": d[0], "log2_rows": d[1], "log2_objects": d[2],
-                             "variant": d[3], "tile_n": 256 if d[3] < 2 else 128,
-                             "cluster": 1 if d[3] & 1 else 2} for d in F.farm_sim_tuning(ctx)],
+                             "variant": d[3], "tile_n": 256 if d[3] in (0, 1, 4) else 128,
+                             "cluster": 1 if d[3] & 1 else 2, "cta_pair": d[3] == 4}
+                            for d in F.farm_sim_tuning(ctx)],
         "pinned_tile_variant": args.tile_variant if args.tile_variant >= 0 else None,
         "stage_ms_per_step": {"prepare": stage_ms[0] / args.steps, "similarity": gemm_ms,
                               "select": stage_ms[2] / args.steps, "compose": stage_ms[3] / args.steps,

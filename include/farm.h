@@ -353,9 +353,10 @@ farm_status farm_sync(farm_ctx *ctx);
 farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t reset);
 
 /*
- * The tensor-core similarity kernel comes in four tile configurations
+ * The tensor-core similarity kernel comes in five tile configurations
  * ("variants": 0 = 256 objects per tile, CTAs in clusters of two sharing the
- * descriptor tile; 1 = 256, alone; 2 = 128, clusters of two; 3 = 128, alone).
+ * descriptor tile; 1 = 256, alone; 2 = 128, clusters of two; 3 = 128, alone;
+ * 4 = 256 x 256 tiles computed by a pair of CTAs with two-SM MMAs).
  * All compute each cosine with the same sequence of products, so they give
  * bitwise identical results.  The first farm_query_batch of each class of
  * batch (similarity mode, and the powers of two of its total rows and of its
@@ -370,7 +371,7 @@ farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t rese
 farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_t *count);
 
 /*
- * Pins every later batch of the context to one tile variant (0 .. 3), or,
+ * Pins every later batch of the context to one tile variant (0 .. 4), or,
  * with -1, returns to the autotuner: for reproducible configurations, and for
  * runs under a profiler, whose serialisation distorts the autotuner's timings.
  */
@@ -378,7 +379,7 @@ farm_status farm_sim_variant_pin(farm_ctx *ctx, int32_t variant);
 
 /*
  * Cosines as farm_similarity (FARM_PREC_FP32, FARM_PREC_BF16 or FARM_PREC_FP8),
- * computed by the given tile variant (0 .. 3), for checking the variants
+ * computed by the given tile variant (0 .. 4), for checking the variants
  * against one another.
  */
 farm_status farm_similarity_variant(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb,

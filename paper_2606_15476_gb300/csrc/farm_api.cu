@@ -869,7 +869,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         } else if (it != c.tuned.end()) {
             vlist = {it->second};
         } else {
-            vlist = {0, 1, 2, 3};
+            vlist = {0, 1, 2, 3, 4};
             graph = false;
         }
     }
@@ -1581,7 +1581,7 @@ farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_
 farm_status farm_sim_variant_pin(farm_ctx *ctx, int32_t variant)
 {
     if (!ctx) return FARM_EINVAL;
-    if (variant < -1 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [-1, 4)");
+    if (variant < -1 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [-1, 5)");
     ctx->c.pinned_variant = variant;
     return FARM_OK;
 }
@@ -1594,7 +1594,7 @@ farm_status farm_similarity_variant(farm_ctx *ctx, int32_t scene_id, int64_t n_r
     if (scene_id < 0 || scene_id >= kMaxScenes || !c.scenes[scene_id].present)
         return fail(ctx, FARM_EINVAL, "unknown scene");
     if (n_rows < 0) return fail(ctx, FARM_EINVAL, "n_rows must be >= 0");
-    if (variant < 0 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [0, 4)");
+    if (variant < 0 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [0, 5)");
     int mode;
     if (precision == FARM_PREC_FP32) mode = farm::kSimF16x3;
     else if (precision == FARM_PREC_BF16) mode = farm::kSimBf16;

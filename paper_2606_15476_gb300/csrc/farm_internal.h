@@ -228,12 +228,13 @@ cudaError_t launch_sim_simt(const float *q, const float *d, float *S, int64_t ro
 // Tiles of the tensor-core similarity kernels: kSimTileM query rows per CTA;
 // a tile configuration ("variant") fixes the tile width and the cluster size
 // (CTAs on vertically adjacent tiles sharing one descriptor tile):
-//   0: 256 objects, clusters of 2;  1: 256, 1;  2: 128, 2;  3: 128, 1.
+//   0: 256 objects, clusters of 2;  1: 256, 1;  2: 128, 2;  3: 128, 1;
+//   4: 256 objects, a CTA pair computing 256 x 256 tiles with two-SM MMAs.
 // Every variant computes each output with the same K order, so they give
 // bitwise identical results; the planner's autotuner picks the fastest.
 constexpr int kSimTileM = 128;
-constexpr int kSimVariants = 4;
-inline int sim_variant_bn(int v) { return v < 2 ? 256 : 128; }
+constexpr int kSimVariants = 5;
+inline int sim_variant_bn(int v) { return (v < 2 || v == 4) ? 256 : 128; }
 inline int sim_variant_cluster(int v) { return (v & 1) ? 1 : 2; }
 enum SimMode { kSimF16x3 = 0, kSimBf16 = 1, kSimFp8 = 2 };
 
@@ -299,7 +300,7 @@ cudaError_t launch_sim_tc_grouped(int mode, int variant, const void *q0, const v
                                   cudaStream_t s);
 
 // One problem (rows x n, S leading dimension ld_s, group maxima at tops with
-// group_stride(n) floats per row, nullable) on the tensor cores, variant 0.
+// group_stride(n) floats per row, nullable) on the tensor cores, variant 4 (CTA pairs).
 // Three FP16 terms, hi*hi + 2^-11 (hi*lo + lo*hi), from the split the
 // normalisation writes.
 cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, const uint16_t *d_hi,

@@ -92,8 +92,10 @@ struct Elem<kSimFp8> {                       // FP8 E4M3
     static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
 };
 
-// A tile configuration: BN objects per tile, CM CTAs per cluster.
-template <int MODE, int BN_, int CM_>
+// A tile configuration: BN objects per tile, CM CTAs per cluster; PAIR: the
+// two CTAs of a cluster compute one 256 x BN tile with two-SM MMAs
+// (cta_group::2), each holding its 128 rows of A and half of B.
+template <int MODE, int BN_, int CM_, bool PAIR_ = false>
 struct Cfg {
     using E = Elem<MODE>;
     static constexpr int BN = BN_;
@@ -102,7 +104,8 @@ struct Cfg {
     static constexpr int A_BYTES = BM * E::ROW_BYTES;
     static constexpr int B_BYTES = BN_ * E::ROW_BYTES;
     static constexpr int B_PART = B_BYTES / CM_;                // this CTA's share of a B tile
-    static constexpr int STAGE_BYTES = OPS * (A_BYTES + B_BYTES);
+    static constexpr int B_SMEM = PAIR_ ? B_PART : B_BYTES;     // B bytes a stage holds in this CTA
+    static constexpr int STAGE_BYTES = OPS * (A_BYTES + B_SMEM);
     static constexpr int STAGES = STAGE_BUDGET / STAGE_BYTES < 8 ? STAGE_BUDGET / STAGE_BYTES : 8;
     static constexpr int ACC_COLS = OPS * BN_;                  // TMEM columns of one tile's accumulators
     static constexpr int NACC = 512 / ACC_COLS >= 2 ? 2 : 1;    // tiles in flight in TMEM
@@ -111,6 +114,7 @@ struct Cfg {
     static_assert(BN_ % 128 == 0 && BN_ <= 256, "tile width");
     static_assert(STAGES >= 3, "pipeline depth");
     static_assert(BN_ / CM_ >= 8 && (B_PART % 1024) == 0, "B share must keep the swizzle atoms whole");
+    static_assert(!PAIR_ || (CM_ == 2 && BN_ == 256), "CTA pairs: clusters of two, 256-object tiles");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -195,35 +199,49 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptors: D = F32, A and B K-major, M = 128, N = n;
-// operand format FP16 (0, kind::f16), BF16 (1, kind::f16) or E4M3 (0, kind::f8f6f4).
-__host__ __device__ constexpr uint32_t idesc(uint32_t ab_format, int n)
+// Instruction descriptors: D = F32, A and B K-major, M = m (128, or 256 for
+// a CTA pair), N = n; operand format FP16 (0, kind::f16), BF16 (1,
+// kind::f16) or E4M3 (0, kind::f8f6f4).
+__host__ __device__ constexpr uint32_t idesc(uint32_t ab_format, int n, int m)
 {
     return (1u << 4)                      // D format F32
            | (ab_format << 7)             // A format
            | (ab_format << 10)            // B format
            | ((uint32_t)(n >> 3) << 17)   // N / 8
-           | ((uint32_t)(BM >> 4) << 24); // M / 16
+           | ((uint32_t)(m >> 4) << 24);  // M / 16
 }
 
 // One MMA of the mode's kind (FP16 and BF16 operands: kind::f16; E4M3:
-// kind::f8f6f4), D (+)= A B^T into TMEM.
-template <int MODE, int BN_>
+// kind::f8f6f4), D (+)= A B^T into TMEM; PAIR: a two-SM MMA (M = 256) over
+// both CTAs' shared-memory halves and TMEM, issued by the even CTA.
+template <int MODE, int BN_, bool PAIR>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
 {
-    if (MODE == kSimFp8) {
+    constexpr uint32_t id = idesc(MODE == kSimBf16 ? 1u : 0u, BN_, PAIR ? 2 * BM : BM);
+    if (MODE == kSimFp8 && !PAIR) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(0u, BN_)), "r"(accumulate));
-    } else {
+            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(id), "r"(accumulate));
+    } else if (MODE == kSimFp8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(id), "r"(accumulate));
+    } else if (!PAIR) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc(MODE == kSimBf16 ? 1u : 0u, BN_)),
-              "r"(accumulate));
+            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(id), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(id), "r"(accumulate));
     }
 }
 
@@ -258,6 +276,41 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The pair's commit: arrives on the mbarrier at the offset of `bar` in both
+// CTAs once the two-SM MMAs issued so far have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(smem_u32(bar)), "h"((uint16_t)3)
+                 : "memory");
+}
+
+// Cluster address of the object at this CTA's shared-memory address `saddr`
+// in the CTA of the given cluster rank.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t saddr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+// A TMA load into this CTA's shared memory whose completion is counted on an
+// mbarrier of either CTA of the pair (bar: cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Arrive on an mbarrier of another CTA of the cluster (cluster address).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -345,7 +398,7 @@ __device__ __forceinline__ void store_rows_staged(float4 *blk, const float4 (&va
     __syncwarp();
 }
 
-template <int MODE, int BN_, int CM_, bool GROUPED>
+template <int MODE, int BN_, int CM_, bool GROUPED, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1)
 sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant__ CUtensorMap map_q1,
               const __grid_constant__ CUtensorMap map_d0, const __grid_constant__ CUtensorMap map_d1,
@@ -353,9 +406,10 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
               float *__restrict__ S, float *__restrict__ tops, int32_t k_slices, int32_t total,
               const float *__restrict__ scale_q, int32_t *err)
 {
-    using C = Cfg<MODE, BN_, CM_>;
+    using C = Cfg<MODE, BN_, CM_, PAIR>;
     using M = Elem<MODE>;
     constexpr bool TWO_OPERAND_TILES = !M::SPLIT;
+    constexpr int B_SMEM = C::B_SMEM;
     constexpr int NACC = C::NACC;
     constexpr int STAGES = C::STAGES;
     constexpr int STAGE_BYTES = C::STAGE_BYTES;
@@ -381,19 +435,27 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CM);    // one multicast commit from each CTA's MMA issuer
+            // one multicast commit from each CTA's MMA issuer (a pair: from the even CTA's)
+            mbar_init(&empty[s], PAIR ? 1 : CM);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);     // one arrival per epilogue warp
+            mbar_init(&acc_empty[b], PAIR ? 8 : 4);     // one arrival per epilogue warp (of both CTAs of a pair)
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_ALLOC));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        // a pair: one warp of each CTA allocates collectively (the same columns in both)
+        if (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(smem_u32(tmem_slot)), "r"(TMEM_ALLOC));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(smem_u32(tmem_slot)), "r"(TMEM_ALLOC));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     cluster_sync();    // every CTA's mbarriers are initialised before any multicast reaches them
@@ -424,9 +486,26 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                         break;
                     }
                     uint8_t *st = smem + s * STAGE_BYTES;
-                    mbar_expect_tx(&full[s], STAGE_BYTES);
                     const int kx = kb * M::BK;
                     const int nb = n0 + (int)rank * (BN / CM);   // first B row of this CTA's share
+                    if (PAIR) {
+                        // both CTAs' copies count on the even CTA's "full" barrier, which
+                        // expects the pair's bytes; each CTA holds its rows of A and its
+                        // half of B at the same offsets
+                        if (rank == 0) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
+                        const uint32_t fb = cluster_addr(smem_u32(&full[s]), 0u);
+                        if (TWO_OPERAND_TILES) {
+                            tma_load_2d_pair(st, &map_q0, fb, kx, qa);
+                            tma_load_2d_pair(st + C::A_BYTES, bmap0, fb, kx, nb);
+                        } else {
+                            tma_load_2d_pair(st, &map_q0, fb, kx, qa);
+                            tma_load_2d_pair(st + C::A_BYTES, &map_q1, fb, kx, qa);
+                            tma_load_2d_pair(st + 2 * C::A_BYTES, bmap0, fb, kx, nb);
+                            tma_load_2d_pair(st + 2 * C::A_BYTES + B_SMEM, bmap1, fb, kx, nb);
+                        }
+                        continue;
+                    }
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
                     if (TWO_OPERAND_TILES) {
                         tma_load_2d(st, &map_q0, &full[s], kx, qa);
                         tma_load_2d_mc(st + C::A_BYTES + rank * B_PART, bmap0, &full[s], kx, nb, ALL_CTAS);
@@ -441,13 +520,15 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             }
             if (*abort_flag) {
                 // let the copies already issued land before shared memory is released
-                for (uint32_t j = (it > (uint32_t)STAGES ? it - STAGES : 0u); j < it; ++j)
-                    mbar_wait(&full[j % STAGES], (j / STAGES) & 1u);
+                // (a pair's copies are counted on the even CTA's barriers)
+                if (!PAIR || rank == 0)
+                    for (uint32_t j = (it > (uint32_t)STAGES ? it - STAGES : 0u); j < it; ++j)
+                        mbar_wait(&full[j % STAGES], (j / STAGES) & 1u);
                 atomicOr(err, kErrTimeout);
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && (!PAIR || rank == 0)) {     // a pair's MMAs are issued by its even CTA
             uint32_t it = 0, tc = 0;
             for (int tile = cluster_id; tile < total && !*abort_flag; tile += n_clusters, ++tc) {
                 const uint32_t buf = tc % NACC, use = tc / NACC;
@@ -471,25 +552,29 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
 #pragma unroll
                         for (int kk = 0; kk < M::KSTEPS; ++kk) {
                             const uint32_t off = kk * 32;     // 32 bytes along K: 16 BF16 or 32 FP8 values
-                            mma<MODE, BN_>(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off), (kb | kk) != 0);
+                            mma<MODE, BN_, PAIR>(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off),
+                                                 (kb | kk) != 0);
                         }
                     } else {
                         const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
-                        const uint32_t b_hi = st + 2 * C::A_BYTES, b_lo = st + 2 * C::A_BYTES + C::B_BYTES;
+                        const uint32_t b_hi = st + 2 * C::A_BYTES, b_lo = st + 2 * C::A_BYTES + B_SMEM;
 #pragma unroll
                         for (int kk = 0; kk < M::KSTEPS; ++kk) {
                             const uint32_t off = kk * 32;     // 16 FP16 values = 32 bytes along K
                             const uint32_t first = (kb | kk) != 0;
-                            mma<MODE, BN_>(acc, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), first);
-                            mma<MODE, BN_>(acc + ACC_CORR, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_lo + off),
-                                           first);
-                            mma<MODE, BN_>(acc + ACC_CORR, smem_desc<MODE>(a_lo + off), smem_desc<MODE>(b_hi + off), 1u);
+                            mma<MODE, BN_, PAIR>(acc, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), first);
+                            mma<MODE, BN_, PAIR>(acc + ACC_CORR, smem_desc<MODE>(a_hi + off),
+                                                 smem_desc<MODE>(b_lo + off), first);
+                            mma<MODE, BN_, PAIR>(acc + ACC_CORR, smem_desc<MODE>(a_lo + off),
+                                                 smem_desc<MODE>(b_hi + off), 1u);
                         }
                     }
-                    mma_commit_mc(&empty[s], ALL_CTAS);
+                    if (PAIR) mma_commit_pair(&empty[s]);
+                    else mma_commit_mc(&empty[s], ALL_CTAS);
                 }
                 if (*abort_flag) break;
-                mma_commit(&acc_full[buf]);
+                if (PAIR) mma_commit_pair(&acc_full[buf]);
+                else mma_commit(&acc_full[buf]);
             }
             if (*abort_flag) atomicOr(err, kErrTimeout);
         }
@@ -604,7 +689,10 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            if (lane == 0) {
+                if (PAIR && rank != 0) mbar_arrive_remote(cluster_addr(smem_u32(&acc_empty[buf]), 0u));
+                else mbar_arrive(&acc_empty[buf]);
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -612,7 +700,8 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     cluster_sync();    // no CTA leaves while a peer's copies or commits may still target its shared memory
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_ALLOC));
+        if (PAIR) asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_ALLOC));
+        else asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_ALLOC));
     }
 }
 
@@ -654,16 +743,16 @@ bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, in
 // as can be resident at once (a GPC with an odd number of free SMs cannot
 // hold a whole cluster on its last SM); the count is cached per device and
 // kernel (concurrent first calls compute the same value).
-template <int MODE, int BN_, int CM_, bool GROUPED>
+template <int MODE, int BN_, int CM_, bool GROUPED, bool PAIR = false>
 cudaError_t launch_impl(const CUtensorMap &mq0, const CUtensorMap &mq1, const CUtensorMap &md0,
                         const CUtensorMap &md1, const GemmPiece *pieces, int32_t n_pieces, const GemmPiece &single,
                         float *S, float *tops, int32_t k_slices, int64_t total_tiles, const float *scale_q,
                         int num_sms, int32_t *err, cudaStream_t s)
 {
-    using C = Cfg<MODE, BN_, CM_>;
+    using C = Cfg<MODE, BN_, CM_, PAIR>;
     if (total_tiles <= 0) return cudaSuccess;
     if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto kernel = sim_tc_kernel<MODE, BN_, CM_, GROUPED>;
+    auto kernel = sim_tc_kernel<MODE, BN_, CM_, GROUPED, PAIR>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -706,7 +795,7 @@ int32_t k_slices_of(int32_t dim_pad)
     return (dim_pad + Elem<MODE>::BK - 1) / Elem<MODE>::BK;
 }
 
-// One problem, tile configuration 0 (256-object tiles, clusters of two).
+// One problem, tile configuration 4 (256 x 256 tiles on CTA pairs).
 template <int MODE>
 cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void *d1, float *S, int64_t rows,
                       int64_t n, int32_t dim_pad, int64_t ld_s, const float *scale_q, const float *scale_d,
@@ -743,12 +832,12 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     single.ld = (int32_t)ld_s;
     single.tile_begin = 0;
     single.gshift = group_shift_for(n);
-    return launch_impl<MODE, BN_, CM_, false>(mq0, mq1, md0, md1, nullptr, 1, single, S, tops,
-                                              k_slices_of<MODE>(dim_pad), sim_cluster_tiles(rows, n, 0), scale_q,
+    return launch_impl<MODE, BN_, CM_, false, true>(mq0, mq1, md0, md1, nullptr, 1, single, S, tops,
+                                              k_slices_of<MODE>(dim_pad), sim_cluster_tiles(rows, n, 4), scale_q,
                                               num_sms, err, s);
 }
 
-template <int MODE, int BN_, int CM_>
+template <int MODE, int BN_, int CM_, bool PAIR = false>
 cudaError_t launch_grouped(const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
                            const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S, float *tops,
                            const float *scale_q, int num_sms, int32_t *err, cudaStream_t s)
@@ -767,7 +856,7 @@ cudaError_t launch_grouped(const void *q0, const void *q1, int64_t rows_total, i
     else if (!make_map<MODE>(&mq1, q1, dim_pad, rows_total, BM)) return cudaErrorInvalidValue;
     GemmPiece unused{};
     // the B maps of the pieces live in device memory; map_d0 / map_d1 are unused
-    return launch_impl<MODE, BN_, CM_, true>(mq0, mq1, mq0, mq1, pieces, n_pieces, unused, S, tops,
+    return launch_impl<MODE, BN_, CM_, true, PAIR>(mq0, mq1, mq0, mq1, pieces, n_pieces, unused, S, tops,
                                              k_slices_of<MODE>(dim_pad), total_tiles, scale_q, num_sms, err, s);
 }
 
@@ -789,6 +878,9 @@ cudaError_t launch_grouped_variant(int variant, const void *q0, const void *q1, 
     case 3:
         return launch_grouped<MODE, 128, 1>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
                                             scale_q, num_sms, err, s);
+    case 4:
+        return launch_grouped<MODE, 256, 2, true>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S,
+                                                  tops, scale_q, num_sms, err, s);
     default:
         return cudaErrorInvalidValue;
     }

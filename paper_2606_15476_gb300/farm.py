@@ -313,7 +313,7 @@ def farm_sim_tuning(ctx):
 
 
 def farm_sim_variant_pin(ctx, variant: int) -> None:
-    """Pin the grouped similarity to one tile variant (0..3), or -1 for the autotuner."""
+    """Pin the grouped similarity to one tile variant (0..4), or -1 for the autotuner."""
     _ck(ctx, _lib.farm_sim_variant_pin(ctx, int(variant)))
 
 
