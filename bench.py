@@ -389,7 +389,7 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-variant", type=int, default=-1,
-                    help="pin the similarity kernel's tile variant (0-3) instead of autotuning it")
+                    help="pin the similarity kernel's tile variant (0-4) instead of autotuning it")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the timed steps directly instead of as CUDA graphs (FARM_GRAPH)")
     ap.add_argument("--task", default="retrieve", choices=["retrieve", "associate"],
@@ -598,8 +598,8 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "autotuned_tiles": [{"mode": d[0], "log2_rows": d[1], "log2_objects": d[2],
-                             "variant": d[3], "tile_n": 256 if d[3] in (0, 1, 4) else 128,
-                             "cluster": 1 if d[3] & 1 else 2, "cta_pair": d[3] == 4}
+                             "variant": d[3], "tile_n": 128 if d[3] in (2, 3) else 256,
+                             "cluster": 1 if d[3] in (1, 3) else 2, "cta_pair": d[3] == 4}
                             for d in F.farm_sim_tuning(ctx)],
         "pinned_tile_variant": args.tile_variant if args.tile_variant >= 0 else None,
         "stage_ms_per_step": {"prepare": stage_ms[0] / args.steps, "similarity": gemm_ms,
