@@ -151,6 +151,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
+// One non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1)
 {
     asm volatile(
@@ -313,6 +327,27 @@ __device__ __forceinline__ void mbar_arrive_remote(uint32_t bar)
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Store 32 consecutive columns of the warp's 32 TMEM lanes (one per thread).
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+          "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+          "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+          "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+          "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+          "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+          "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+          "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+          "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+          "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+          "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -415,6 +450,11 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     constexpr int STAGE_BYTES = C::STAGE_BYTES;
     constexpr int BN = BN_, CM = CM_;
     constexpr int ACC_CORR = BN_;            // correction accumulator: the columns after the main one
+    // FP32-accurate mode with one tile in TMEM: the epilogue first folds the
+    // correction into the main accumulator in TMEM and frees the correction
+    // columns, so the next tile's correction products (two thirds of its
+    // MMAs) run while the main accumulator is drained to S
+    constexpr bool FOLD = M::SPLIT && NACC == 1;
     constexpr uint32_t TMEM_ALLOC = 512;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -425,6 +465,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     float *staging = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256);
+    uint64_t *corr_free = acc_empty + 1;      // FOLD: the correction columns are free (tile accumulators: one)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
@@ -529,50 +570,108 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
         }
     } else if (warp == 1) {
         if (lane == 0 && (!PAIR || rank == 0)) {     // a pair's MMAs are issued by its even CTA
-            uint32_t it = 0, tc = 0;
-            for (int tile = cluster_id; tile < total && !*abort_flag; tile += n_clusters, ++tc) {
-                const uint32_t buf = tc % NACC, use = tc / NACC;
-                if (!mbar_wait(&acc_empty[buf], (use & 1u) ^ 1u) || *abort_flag) {
-                    *abort_flag = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t acc = tmem + buf * (uint32_t)C::ACC_COLS;
-                for (int kb = 0; kb < k_slices; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (it / STAGES) & 1u;
-                    if (!mbar_wait(&full[s], ph) || *abort_flag) {
-                        *abort_flag = 1;
-                        break;
+            // the products of K slice kb from stage s: the main one (hi.hi, or the
+            // only one) and / or the two correction products
+            auto issue = [&](uint32_t acc, int kb, int s, bool main, bool corr) {
+                const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+                if (TWO_OPERAND_TILES) {
+                    const uint32_t a = st, b = st + C::A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < M::KSTEPS; ++kk) {
+                        const uint32_t off = kk * 32;     // 32 bytes along K: 16 BF16 or 32 FP8 values
+                        mma<MODE, BN_, PAIR>(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off),
+                                             (kb | kk) != 0);
                     }
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-                    if (TWO_OPERAND_TILES) {
-                        const uint32_t a = st, b = st + C::A_BYTES;
+                } else {
+                    const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
+                    const uint32_t b_hi = st + 2 * C::A_BYTES, b_lo = st + 2 * C::A_BYTES + B_SMEM;
 #pragma unroll
-                        for (int kk = 0; kk < M::KSTEPS; ++kk) {
-                            const uint32_t off = kk * 32;     // 32 bytes along K: 16 BF16 or 32 FP8 values
-                            mma<MODE, BN_, PAIR>(acc, smem_desc<MODE>(a + off), smem_desc<MODE>(b + off),
-                                                 (kb | kk) != 0);
-                        }
-                    } else {
-                        const uint32_t a_hi = st, a_lo = st + C::A_BYTES;
-                        const uint32_t b_hi = st + 2 * C::A_BYTES, b_lo = st + 2 * C::A_BYTES + B_SMEM;
-#pragma unroll
-                        for (int kk = 0; kk < M::KSTEPS; ++kk) {
-                            const uint32_t off = kk * 32;     // 16 FP16 values = 32 bytes along K
-                            const uint32_t first = (kb | kk) != 0;
-                            mma<MODE, BN_, PAIR>(acc, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off), first);
+                    for (int kk = 0; kk < M::KSTEPS; ++kk) {
+                        const uint32_t off = kk * 32;     // 16 FP16 values = 32 bytes along K
+                        const uint32_t first = (kb | kk) != 0;
+                        if (main)
+                            mma<MODE, BN_, PAIR>(acc, smem_desc<MODE>(a_hi + off), smem_desc<MODE>(b_hi + off),
+                                                 first);
+                        if (corr) {
                             mma<MODE, BN_, PAIR>(acc + ACC_CORR, smem_desc<MODE>(a_hi + off),
                                                  smem_desc<MODE>(b_lo + off), first);
                             mma<MODE, BN_, PAIR>(acc + ACC_CORR, smem_desc<MODE>(a_lo + off),
                                                  smem_desc<MODE>(b_hi + off), 1u);
                         }
                     }
-                    if (PAIR) mma_commit_pair(&empty[s]);
-                    else mma_commit_mc(&empty[s], ALL_CTAS);
+                }
+            };
+            auto release = [&](int s) {
+                if (PAIR) mma_commit_pair(&empty[s]);
+                else mma_commit_mc(&empty[s], ALL_CTAS);
+            };
+            uint32_t it = 0, tc = 0;
+            for (int tile = cluster_id; tile < total && !*abort_flag; tile += n_clusters, ++tc) {
+                const uint32_t buf = tc % NACC, use = tc / NACC;
+                // FOLD: the correction columns are free after the previous tile's fold,
+                // the main columns after its stores; otherwise both with the accumulator
+                if (!mbar_wait(FOLD ? corr_free : &acc_empty[buf], (use & 1u) ^ 1u) || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t acc = tmem + buf * (uint32_t)C::ACC_COLS;
+                // FOLD: until the main columns are free, slices get their correction
+                // products only and keep their stage ("held"); at most STAGES of them,
+                // since the producer refills a stage only once it is released
+                bool main_ready = !FOLD;
+                int held = 0, held_kb = 0;
+                uint32_t held_it = 0;
+                auto flush = [&]() {
+                    for (int j = 0; j < held; ++j) {
+                        const int sj = (int)((held_it + (uint32_t)j) % STAGES);
+                        issue(acc, held_kb + j, sj, true, false);
+                        release(sj);
+                    }
+                    held = 0;
+                };
+                for (int kb = 0; kb < k_slices; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1u;
+                    if (FOLD && !main_ready && held >= STAGES) {
+                        if (!mbar_wait(&acc_empty[buf], (use & 1u) ^ 1u) || *abort_flag) {
+                            *abort_flag = 1;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        main_ready = true;
+                        flush();
+                    }
+                    if (!mbar_wait(&full[s], ph) || *abort_flag) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    if (FOLD && !main_ready && mbar_test(&acc_empty[buf], (use & 1u) ^ 1u)) {
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        main_ready = true;
+                        flush();
+                    }
+                    issue(acc, kb, s, main_ready, true);
+                    if (main_ready) {
+                        release(s);
+                    } else {
+                        if (held == 0) {
+                            held_kb = kb;
+                            held_it = it;
+                        }
+                        ++held;
+                    }
                 }
                 if (*abort_flag) break;
+                if (FOLD && !main_ready) {
+                    if (!mbar_wait(&acc_empty[buf], (use & 1u) ^ 1u) || *abort_flag) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    flush();
+                }
                 if (PAIR) mma_commit_pair(&acc_full[buf]);
                 else mma_commit(&acc_full[buf]);
             }
@@ -595,6 +694,26 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
+            if (FOLD) {
+                // main += 2^-11 correction, in place; then the correction columns are free
+                const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16);
+#pragma unroll
+                for (int c = 0; c < BN / 32; ++c) {
+                    float v[32], w[32];
+                    tmem_ld32(tb + (uint32_t)(c * 32), v);
+                    tmem_ld32(tb + ACC_CORR + (uint32_t)(c * 32), w);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = fmaf(w[i], RESID_SCALE_INV, v[i]);
+                    tmem_st32(tb + (uint32_t)(c * 32), v);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) {
+                    if (PAIR && rank != 0) mbar_arrive_remote(cluster_addr(smem_u32(corr_free), 0u));
+                    else mbar_arrive(corr_free);
+                }
+            }
             const GemmPiece pc = piece_of<GROUPED>(tile, pieces, n_pieces, single);
             int m0, n0;
             piece_tile<BN_, CM_>(pc, tile, rank, m0, n0);
@@ -614,7 +733,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 const uint32_t lane_addr = tmem + buf * (uint32_t)C::ACC_COLS + ((uint32_t)(quad * 32) << 16) +
                                            (uint32_t)(c * 32);
                 tmem_ld32(lane_addr, v);
-                if (MODE == kSimF16x3) {
+                if (MODE == kSimF16x3 && !FOLD) {
                     float w[32];
                     tmem_ld32(lane_addr + ACC_CORR, w);
 #pragma unroll
