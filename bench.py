@@ -188,14 +188,14 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
 # variant), valid only while the kernel source is the one captured (sha256
 # prefix).
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 0): 715.093248e6 + 1129.676288e6,
-    ("site_n20k_d1152", "fp32", 1): 1359.185408e6 + 1138.319872e6,
-    ("site_n20k_d1152", "fp32", 4): 725.757184e6 + 1132.319744e6,
-    ("site_n20k_d1152", "bf16", 0): 355.813888e6 + 1114.249728e6,
-    ("site_n20k_d1152", "bf16", 1): 672.520448e6 + 1118.487040e6,
-    ("site_n20k_d1152", "bf16", 4): 355.888896e6 + 1114.270208e6,
+    ("site_n20k_d1152", "fp32", 0): 720.129792e6 + 1128.559872e6,
+    ("site_n20k_d1152", "fp32", 1): 1356.648192e6 + 1136.768000e6,
+    ("site_n20k_d1152", "fp32", 4): 727.125760e6 + 1128.285440e6,
+    ("site_n20k_d1152", "bf16", 0): 356.045824e6 + 1114.383104e6,
+    ("site_n20k_d1152", "bf16", 1): 672.559104e6 + 1118.444544e6,
+    ("site_n20k_d1152", "bf16", 4): 356.896512e6 + 1114.394624e6,
 }
-SIM_TRAFFIC_SOURCE = "927f8d17305fbde0"
+SIM_TRAFFIC_SOURCE = "dc2d99e773f81975"
 
 
 def sim_traffic(workload, precision, variants):
