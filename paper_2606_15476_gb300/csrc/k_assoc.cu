@@ -28,6 +28,8 @@ namespace {
 
 constexpr int TA = 128;
 constexpr int CAPA = 1024;       // candidates within the budget a detection may have
+constexpr int CAPP = 4096;       // prefilter list: entities past the cosine threshold awaiting evaluation
+constexpr int PER_PASS = TA * 16;   // entries one streaming pass can add (four float4 per thread)
 
 __device__ __forceinline__ float det3f(const float c[6])
 {
@@ -81,9 +83,13 @@ assoc_search_kernel(const float *__restrict__ S, int64_t ld, int32_t N, int32_t 
                     float *__restrict__ match_h, int32_t *err)
 {
     __shared__ uint64_t cand[CAPA];
-    __shared__ int s_cnt;
+    __shared__ int32_t pre[CAPP];
+    __shared__ int s_cnt, s_np;
     const int d = blockIdx.x, tid = threadIdx.x;
-    if (tid == 0) s_cnt = 0;
+    if (tid == 0) {
+        s_cnt = 0;
+        s_np = 0;
+    }
     __syncthreads();
     float md[3], cd[6];
 #pragma unroll
@@ -92,16 +98,22 @@ assoc_search_kernel(const float *__restrict__ S, int64_t ld, int32_t N, int32_t 
     for (int k = 0; k < 6; ++k) cd[k] = det_cov[(int64_t)k * B + d];
     // the row is streamed in float4 loads, four in flight per thread (its
     // leading dimension is a multiple of 32 floats, so the row is 16-byte
-    // aligned and a load never leaves it); only entities past the cosine
-    // prefilter -- few -- are looked up further
+    // aligned and a load never leaves it); the entities past the cosine
+    // prefilter are listed in shared memory and evaluated by all threads
+    // together (one entity per thread), whenever the list could overflow in
+    // the next pass and at the end: evaluated where they are found, they
+    // would each run on one lane of a warp
     const float *row = S + (int64_t)d * ld;
     const float4 *row4 = reinterpret_cast<const float4 *>(row);
     const int n4 = (N + 3) >> 2;
-    auto consider = [&](int e) {
-        const float h = entity_distance(e, N, ent_mu, ent_cov, ent_active, md, cd);
-        if (h >= 0.f && h <= h_max) {
-            const int pos = atomicAdd(&s_cnt, 1);
-            if (pos < CAPA) cand[pos] = ((uint64_t)__float_as_uint(h) << 32) | (uint32_t)e;   // H >= 0: bits order like H
+    auto evaluate = [&](int np) {
+        for (int i = tid; i < np; i += TA) {
+            const int e = pre[i];
+            const float h = entity_distance(e, N, ent_mu, ent_cov, ent_active, md, cd);
+            if (h >= 0.f && h <= h_max) {
+                const int pos = atomicAdd(&s_cnt, 1);
+                if (pos < CAPA) cand[pos] = ((uint64_t)__float_as_uint(h) << 32) | (uint32_t)e;   // H >= 0: bits order like H
+            }
         }
     };
     for (int g0 = 0; g0 < n4; g0 += TA * 4) {
@@ -117,9 +129,18 @@ assoc_search_kernel(const float *__restrict__ S, int64_t ld, int32_t N, int32_t 
             const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                if (x[c] >= tau_f && e0 + c < N) consider(e0 + c);
+                if (x[c] >= tau_f && e0 + c < N) pre[atomicAdd(&s_np, 1)] = e0 + c;
+        }
+        __syncthreads();
+        const int np = s_np;
+        if (np > CAPP - PER_PASS) {      // (uniform) at most PER_PASS more could come in the next pass
+            evaluate(np);
+            __syncthreads();
+            if (tid == 0) s_np = 0;
+            __syncthreads();
         }
     }
+    evaluate(s_np);
     __syncthreads();
     const int cnt = s_cnt;
     if (cnt > CAPA) {
