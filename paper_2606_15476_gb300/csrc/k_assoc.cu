@@ -174,13 +174,17 @@ assoc_search_kernel(const float *__restrict__ S, int64_t ld, int32_t N, int32_t 
 
 // Connected components of the match graph: label[t] ends as the smallest
 // node of t's component.  One CTA; hooking rounds until nothing changes (at
-// most max_rounds, else the error bit).
+// most max_rounds, else the error bit).  With in_smem the labels live in
+// shared memory (T * 4 bytes of dynamic shared memory) and are written to
+// `label` at the end; otherwise they are worked on in `label` directly.
 __global__ void __launch_bounds__(1024)
 assoc_components_kernel(int32_t N, int32_t B, int32_t max_m, const int32_t *__restrict__ match_idx,
-                        int32_t *label, int32_t max_rounds, int32_t *err)
+                        int32_t *label_out, int32_t max_rounds, int32_t *err, int32_t in_smem)
 {
+    extern __shared__ int32_t s_label[];
     __shared__ int s_changed;
     const int T = N + B, tid = threadIdx.x;
+    int32_t *label = in_smem ? s_label : label_out;
     for (int t = tid; t < T; t += blockDim.x) label[t] = t;
     __syncthreads();
     const int E = B * max_m;
@@ -215,6 +219,8 @@ assoc_components_kernel(int32_t N, int32_t B, int32_t max_m, const int32_t *__re
         __syncthreads();
     }
     if (tid == 0 && round >= max_rounds) atomicOr(err, kErrTimeout);
+    if (in_smem)
+        for (int t = tid; t < T; t += blockDim.x) label_out[t] = s_label[t];
 }
 
 // win[r]: the heaviest entity of component r as (w bits, ~index).
@@ -316,7 +322,15 @@ cudaError_t launch_assoc(const AssocArgs &a, cudaStream_t s)
     assoc_search_kernel<<<B, TA, 0, s>>>(a.S, a.ld, N, B, a.ent_mu, a.ent_cov, a.ent_active, a.det_mu, a.det_cov,
                                          a.tau_f, a.h_max, a.max_m, a.match_cnt, a.match_idx, a.match_h, a.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    assoc_components_kernel<<<1, 1024, 0, s>>>(N, B, a.max_m, a.match_idx, a.label, 256, a.err);
+    // the labels in shared memory when they fit (up to 200 KB: 51,200 nodes)
+    const size_t lab_bytes = (size_t)T * sizeof(int32_t);
+    const int32_t in_smem = lab_bytes <= 200 * 1024 ? 1 : 0;
+    if (in_smem && lab_bytes > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(assoc_components_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024)) != cudaSuccess)
+        return e;
+    assoc_components_kernel<<<1, 1024, in_smem ? lab_bytes : 0, s>>>(N, B, a.max_m, a.match_idx, a.label, 256,
+                                                                     a.err, in_smem);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.win, 0, (size_t)T * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if (N > 0) {
