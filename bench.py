@@ -48,7 +48,13 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    nvidia-smi takes a while to start, so entering waits (at most 5 s) for its
+    first line; it then samples every 20 ms, and leaving waits (at most 1 s)
+    until at least one sample was taken after the region began, so that a
+    region of a few tens of milliseconds still has one.  The summary uses the
+    samples from the region's start on."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -57,6 +63,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.n0 = 0
 
     def __enter__(self):
         if self.index < 0:          # not sampled
@@ -64,12 +71,17 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
+            return self
+        t0 = time.time()
+        while not self.lines and self.proc.poll() is None and time.time() - t0 < 5.0:
+            time.sleep(0.005)
+        self.n0 = len(self.lines)
         return self
 
     def _read(self):
@@ -78,6 +90,9 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc:
+            t0 = time.time()
+            while len(self.lines) <= self.n0 and self.proc.poll() is None and time.time() - t0 < 1.0:
+                time.sleep(0.002)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -87,7 +102,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.n0:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
