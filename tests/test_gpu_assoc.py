@@ -45,7 +45,7 @@ def _full(c):
     return m
 
 
-def _ambiguous(ent, det, ref):
+def _ambiguous(ent, det, ref, hmax=HMAX):
     """Detections whose match list depends on a decision within 1e-5."""
     ef = ent["feat"].astype(np.float64)
     df = det["feat"].astype(np.float64)
@@ -53,15 +53,15 @@ def _ambiguous(ent, det, ref):
     amb = set(np.flatnonzero(np.any(np.abs(cos - TAU) < 1e-5, axis=1)).tolist())
     for d in range(df.shape[0]):
         hs = ref["match_h"][d][ref["match_h"][d] >= 0]
-        if np.any(np.abs(hs - HMAX) < 1e-5) or np.any(np.diff(hs) < 1e-5):
+        if np.any(np.abs(hs - hmax) < 1e-5) or np.any(np.diff(hs) < 1e-5):
             amb.add(d)
         if ref["match_cnt"][d] > MM:     # the (max_m + 1)-th could tie with the last kept
             amb.add(d)
     return amb
 
 
-def _check(ent, det, got, ref):
-    assert not _ambiguous(ent, det, ref)
+def _check(ent, det, got, ref, hmax=HMAX):
+    assert not _ambiguous(ent, det, ref, hmax)
     assert np.array_equal(got["match_cnt"], ref["match_cnt"])
     assert np.array_equal(got["match_idx"], ref["match_idx"])
     kept = ref["match_idx"] >= 0
@@ -98,6 +98,21 @@ def test_site_association_and_device_pointers(F, ctx):
     for k in ("match_cnt", "match_idx", "parent"):
         assert np.array_equal(gd[k].cpu().numpy(), got[k])
     assert np.allclose(gd["mu"].cpu().numpy(), got["mu"], atol=2e-5)
+
+
+def test_association_beyond_shared_memory_labels(F, ctx):
+    """Over 51,200 nodes (100,000 entities): the components kernel keeps its
+    labels in global memory instead of shared memory.  A looser budget lets
+    bridging detections merge entities at this scene's sparser classes."""
+    scenes, _ = synth.workload("site_n100k_d1152")
+    hmax = 0.97
+    ent, det = synth.make_association(15, scenes[0], 256, feat_dim=64, bridge_frac=0.3)
+    n = ent["mu"].shape[1]
+    assert n + det["mu"].shape[1] > 51200
+    ref = oracle.associate(ent, det, TAU, hmax, MM)
+    assert np.sum(ref["parent"][:n] != np.arange(n)) > 0      # a component holds two entities
+    got = F.farm_associate(ctx, ent, det, TAU, hmax, MM)
+    _check(ent, det, got, ref, hmax)
 
 
 def test_association_invalid_arguments(F, ctx):
