@@ -25,25 +25,32 @@
 // the bytes of a TF32 split.
 //
 // Kernel organisation (persistent: one CTA of 192 threads per SM walks the
-// 128 x 256 tiles of S):
+// 128 x BN tiles of S; in a CTA pair the two CTAs of a cluster compute one
+// 256 x 256 tile together):
 //   warp 0      TMA producer: for each K slice (32 FP16 values, 64-byte swizzle,
 //               four tiles q_hi, q_lo, d_hi, d_lo; or 64 BF16 / 128 FP8 values,
 //               128-byte swizzle, two tiles q, d) fills one pipeline stage,
-//               signalling a "full" mbarrier with the byte count;
+//               signalling a "full" mbarrier with the byte count (a pair: both
+//               CTAs' copies count on the even CTA's barrier);
 //   warp 1      allocates TMEM (main and correction 128 x 256 FP32
 //               accumulators in the FP32-accurate mode, two alternating tile
 //               accumulators otherwise); one thread issues, per K slice,
-//               2 K-steps x 3 products of tcgen05.mma.cta_group::1.kind::f16
-//               with FP16 operands (M=128, N=256, K=16), or 4 K-steps of
-//               kind::f16 (BF16) / kind::f8f6f4 (E4M3), and tcgen05.commit to
-//               the stage's "empty" mbarrier, finally to the "accumulator
+//               2 K-steps x 3 products of tcgen05.mma.kind::f16 with FP16
+//               operands (M=128, or 256 for a pair; N=256, K=16), or 4 K-steps
+//               of kind::f16 (BF16) / kind::f8f6f4 (E4M3), and tcgen05.commit
+//               to the stage's "empty" mbarrier, finally to the "accumulator
 //               ready" mbarrier;
-//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns at a time (FP32-
-//               accurate mode: of both accumulators, combined), store the rows
-//               of S (bounds-checked), then release the accumulator.
-// Four pipeline stages of 48 KB each.  Every mbarrier wait is bounded: on
-// expiry the kernel raises the error flag, stops issuing work, waits (bounded)
-// for the copies it issued, frees its TMEM and returns.
+//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns at a time, each
+//               32 x 32 block staged through shared memory so that stores
+//               write whole row segments of S (bounds-checked), the group
+//               maxima likewise, then release the accumulator.  FP32-accurate
+//               mode at 256-object tiles first folds the correction into the
+//               main accumulator in TMEM and releases the correction columns,
+//               so the next tile's correction products overlap the stores.
+// Stages of 48 KB (32 KB in a pair) within 192 KB, plus 16 KB of epilogue
+// staging.  Every mbarrier wait is bounded: on expiry the kernel raises the
+// error flag, stops issuing work, waits (bounded) for the copies it issued,
+// frees its TMEM and returns.
 #include <algorithm>
 
 #include <cuda.h>
