@@ -203,14 +203,14 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
 # variant), valid only while the kernel source is the one captured (sha256
 # prefix).
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 0): 720.129792e6 + 1128.559872e6,
-    ("site_n20k_d1152", "fp32", 1): 1356.648192e6 + 1136.768000e6,
-    ("site_n20k_d1152", "fp32", 4): 727.125760e6 + 1128.285440e6,
-    ("site_n20k_d1152", "bf16", 0): 356.045824e6 + 1114.383104e6,
-    ("site_n20k_d1152", "bf16", 1): 672.559104e6 + 1118.444544e6,
-    ("site_n20k_d1152", "bf16", 4): 356.896512e6 + 1114.394624e6,
+    ("site_n20k_d1152", "fp32", 0): 718.267904e6 + 1127.048192e6,
+    ("site_n20k_d1152", "fp32", 1): 1358.385152e6 + 1137.302016e6,
+    ("site_n20k_d1152", "fp32", 4): 723.392256e6 + 1128.313600e6,
+    ("site_n20k_d1152", "bf16", 0): 356.149760e6 + 1114.003712e6,
+    ("site_n20k_d1152", "bf16", 1): 672.556800e6 + 1118.364416e6,
+    ("site_n20k_d1152", "bf16", 4): 357.285376e6 + 1114.222080e6,
 }
-SIM_TRAFFIC_SOURCE = "dc2d99e773f81975"
+SIM_TRAFFIC_SOURCE = "45ffcc9296a3b75d"
 
 
 def sim_traffic(workload, precision, variants):
