@@ -106,3 +106,22 @@ def test_reduced_matches_fp32_path_on_full_batch(F, ctx, prec):
     b = _run(F, ctx, qb, code(F, prec))
     same = np.mean([len(set(a["idx"][q].tolist()) & set(b["idx"][q].tolist())) / 10.0 for q in range(qb.n_q)])
     assert same >= 0.99, same
+
+
+@pytest.mark.parametrize("prec", REDUCED)
+def test_reduced_recall_at_10_16k_queries(F, ctx, prec):
+    """The precision workload as configured: 16,384 queries on the 20,000-object
+    site in one graph-captured batch; Recall@10 against the FP64 oracle on a
+    seeded sample of 192 queries."""
+    scenes, qb = synth.workload("site_n20k_d1152_q16k")
+    sc = scenes[0]
+    F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+    args = (qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred, qb.c_emb, code(F, prec))
+    F.farm_query_batch(ctx, *args)                   # the batch class's first run: the autotuner
+    h = F.farm_query_batch(ctx, *args, graph=True)
+    out = F.farm_topk(ctx, h, 10, qb.n_q)
+    qs = np.sort(np.random.default_rng(23).choice(qb.n_q, size=192, replace=False))
+    ref = oracle.batch(sc, qb.subset(qs), 10)
+    hits = sum(len(set(out["idx"][q].tolist()) & set(ref["idx"][i].tolist())) for i, q in enumerate(qs))
+    recall = hits / (10.0 * qs.size)
+    assert recall >= 0.99, recall

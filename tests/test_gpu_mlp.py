@@ -174,3 +174,35 @@ def test_learned_path_recall_and_gain_over_untrained(F):
     ref = oracle.batch(sc, sub, 10)
     hits = sum(len(set(trained["idx"][q].tolist()) & set(ref["idx"][q].tolist())) for q in range(sub.n_q))
     assert hits / (10.0 * sub.n_q) >= 0.99
+
+
+@pytest.fixture(scope="module")
+def site100k():
+    return synth.workload("site_n100k_d1152")
+
+
+@pytest.mark.parametrize("prec", ["learned", "bf16"])
+def test_reduced_paths_recall_100k_objects(F, site100k, prec):
+    """The learned prefilter's configured workload (and BF16 on it): the
+    100,000-object site, all 16,384 queries in one batch -- after the
+    self-supervised training the benchmark runs, for the learned path --
+    with Recall@10 >= 0.99 against the FP64 oracle on a seeded sample of 64
+    queries."""
+    import bench
+    scenes, qb = site100k
+    sc = scenes[0]
+    ctx = F.farm_create(0)
+    try:
+        F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+        code = F.PREC_BF16
+        if prec == "learned":
+            bench.train_prefilter(F, ctx, scenes)
+            code = F.PREC_LEARNED
+        h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred, qb.c_emb, code)
+        out = F.farm_topk(ctx, h, 10, qb.n_q)
+    finally:
+        F.farm_destroy(ctx)
+    qs = np.sort(np.random.default_rng(29).choice(qb.n_q, size=64, replace=False))
+    ref = oracle.batch(sc, qb.subset(qs), 10)
+    hits = sum(len(set(out["idx"][q].tolist()) & set(ref["idx"][i].tolist())) for i, q in enumerate(qs))
+    assert hits / (10.0 * qs.size) >= 0.99, hits / (10.0 * qs.size)
