@@ -203,14 +203,14 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
 # variant), valid only while the kernel source is the one captured (sha256
 # prefix).
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 0): 718.267904e6 + 1127.048192e6,
-    ("site_n20k_d1152", "fp32", 1): 1358.385152e6 + 1137.302016e6,
-    ("site_n20k_d1152", "fp32", 4): 723.392256e6 + 1128.313600e6,
-    ("site_n20k_d1152", "bf16", 0): 356.149760e6 + 1114.003712e6,
-    ("site_n20k_d1152", "bf16", 1): 672.556800e6 + 1118.364416e6,
-    ("site_n20k_d1152", "bf16", 4): 357.285376e6 + 1114.222080e6,
+    ("site_n20k_d1152", "fp32", 0): 716.080384e6 + 1127.595264e6,
+    ("site_n20k_d1152", "fp32", 1): 1356.870912e6 + 1136.986880e6,
+    ("site_n20k_d1152", "fp32", 4): 718.807040e6 + 1127.427328e6,
+    ("site_n20k_d1152", "bf16", 0): 355.865088e6 + 1114.267392e6,
+    ("site_n20k_d1152", "bf16", 1): 672.504832e6 + 1118.159872e6,
+    ("site_n20k_d1152", "bf16", 4): 356.113664e6 + 1114.226432e6,
 }
-SIM_TRAFFIC_SOURCE = "45ffcc9296a3b75d"
+SIM_TRAFFIC_SOURCE = "18ae7d215d7f3cd7"
 
 
 def sim_traffic(workload, precision, variants):

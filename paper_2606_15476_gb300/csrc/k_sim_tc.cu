@@ -117,7 +117,9 @@ struct Cfg {
     static constexpr int ACC_COLS = OPS * BN_;                  // TMEM columns of one tile's accumulators
     static constexpr int NACC = 512 / ACC_COLS >= 2 ? 2 : 1;    // tiles in flight in TMEM
     static constexpr int STAGING_BYTES = 4 * 32 * 32 * 4;      // epilogue: one 32 x 32 FP32 block per warp
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES;
+    static constexpr int SCALE_BYTES = MODE == kSimFp8 ? 4 * BN_ * 4 : 0;   // FP8: a tile's column scales per warp
+    static constexpr int SMEM_BYTES =
+        STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES + SCALE_BYTES;
     static_assert(BN_ % 128 == 0 && BN_ <= 256, "tile width");
     static_assert(STAGES >= 3, "pipeline depth");
     static_assert(BN_ / CM_ >= 8 && (B_PART % 1024) == 0, "B share must keep the swizzle atoms whole");
@@ -472,6 +474,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     float *staging = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256);
+    float *tile_scales = staging + 4 * 32 * 32;    // FP8 mode: [4 warps][BN]
     uint64_t *corr_free = acc_empty + 1;      // FOLD: the correction columns are free (tile accumulators: one)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -731,7 +734,14 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             float *sblk = S + pc.s_off + r_blk * pc.ld;
             const bool vec = (pc.ld % 4) == 0;
             const float sr = (MODE == kSimFp8 && live) ? scale_q[pc.q_row0 + r] : 1.f;
-            const float *__restrict__ scale_d = pc.scale_d;
+            // FP8 mode: the tile's column scales (zero past the row end), staged once
+            // per tile in the warp's slot instead of one bounds-checked load per entry
+            float *scl = tile_scales + (warp - 2) * BN;
+            if (MODE == kSimFp8) {
+                const float *__restrict__ scale_d = pc.scale_d;
+                for (int j = lane; j < BN; j += 32) scl[j] = (int64_t)n0 + j < n ? __ldg(scale_d + n0 + j) : 0.f;
+                __syncwarp();
+            }
             const bool keep_tops = tops != nullptr && pc.tops_off >= 0;    // uniform across the warp
             float gmax[BN / 8];      // maximum of each 8-column group of row r in this tile
 #pragma unroll
@@ -748,8 +758,15 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 }
                 const int64_t col0 = (int64_t)n0 + c * 32;
                 if (MODE == kSimFp8 && live) {
+                    const float4 *s4 = reinterpret_cast<const float4 *>(scl + c * 32);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] *= sr * (col0 + i < n ? __ldg(scale_d + col0 + i) : 0.f);
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 t = s4[q];
+                        v[4 * q] *= sr * t.x;
+                        v[4 * q + 1] *= sr * t.y;
+                        v[4 * q + 2] *= sr * t.z;
+                        v[4 * q + 3] *= sr * t.w;
+                    }
                 }
                 if (keep_tops) {
                     const float ninf = -__int_as_float(0x7f800000);
