@@ -353,10 +353,9 @@ farm_status farm_sync(farm_ctx *ctx);
 farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t reset);
 
 /*
- * The tensor-core similarity kernel comes in five tile configurations
- * ("variants": 0 = 256 objects per tile, CTAs in clusters of two sharing the
- * descriptor tile; 1 = 256, alone; 2 = 128, clusters of two; 3 = 128, alone;
- * 4 = 256 x 256 tiles computed by a pair of CTAs with two-SM MMAs).
+ * The tensor-core similarity kernel comes in three tile configurations
+ * ("variants": 0 = 128 query rows x 256 objects per CTA; 1 = 128 x 128 per
+ * CTA; 2 = 256 x 256 tiles computed by a pair of CTAs with two-SM MMAs).
  * All compute each cosine with the same sequence of products, so they give
  * bitwise identical results.  The first farm_query_batch of each class of
  * batch (similarity mode, and the powers of two of its total rows and of its
@@ -371,7 +370,7 @@ farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t rese
 farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_t *count);
 
 /*
- * Pins every later batch of the context to one tile variant (0 .. 4), or,
+ * Pins every later batch of the context to one tile variant (0 .. 2), or,
  * with -1, returns to the autotuner: for reproducible configurations, and for
  * runs under a profiler, whose serialisation distorts the autotuner's timings.
  */
@@ -379,11 +378,18 @@ farm_status farm_sim_variant_pin(farm_ctx *ctx, int32_t variant);
 
 /*
  * Cosines as farm_similarity (FARM_PREC_FP32, FARM_PREC_BF16 or FARM_PREC_FP8),
- * computed by the given tile variant (0 .. 4), for checking the variants
+ * computed by the given tile variant (0 .. 2), for checking the variants
  * against one another.
  */
 farm_status farm_similarity_variant(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *emb,
                                     int32_t precision, int32_t variant, float *out, uint32_t flags);
+
+/*
+ * Frees an uploaded scene's device memory (after the context's queued work);
+ * the scene id may then be uploaded again.  FARM_EINVAL for an id that holds
+ * no scene.  Synchronises.
+ */
+farm_status farm_memory_release(farm_ctx *ctx, int32_t scene_id);
 
 /*
  * Object count n and descriptor length dim of an uploaded scene, for sizing
@@ -426,21 +432,21 @@ farm_status farm_candidates(farm_ctx *ctx, uint64_t batch_handle, int32_t *tgt_i
  * of the scene) it writes the r objects of scene `scene_id` with the largest
  * cosine, in rank order (larger cosine first, lower index on ties), to
  * out_idx ([n_rows, r] int32, device) and their cosines to out_cos
- * ([n_rows, r] FP32, device, may be NULL) -- the candidate ranking of App. D.2
- * step 3 -- using the similarity arithmetic of `precision` (FARM_PREC_FP32 or
- * FARM_PREC_FP32_SIMT).  1 <= r <= min(512, n).
+ * ([n_rows, r] FP32, device, may be NULL), using the similarity arithmetic of
+ * `precision` (FARM_PREC_FP32 or FARM_PREC_FP32_SIMT).  1 <= r <= min(512, n).
  *
  * Memory: every intermediate array (normalised rows and the
  * n_rows x round_up(n, 32) similarity block) lives in one statically
- * allocated device array of FARM_NOALLOC_SCRATCH_BYTES that each GPU loading
- * the library holds until the process exits.  The call allocates and frees
- * nothing.  Sizes that do not fit return FARM_EINVAL (split the rows into
- * smaller calls).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  All calls share the array and it keeps
- * the last call's contents (nothing in it needs to start at zero): calls whose
- * work overlaps on the GPU -- on different streams or contexts of the same
- * device -- race on it and must be serialised by the caller.
+ * allocated device array of FARM_NOALLOC_SCRATCH_BYTES per GPU.  farm_create
+ * looks up its device address (cudaGetSymbolAddress, with the context's
+ * device current), which loads it: the array's memory is taken when the
+ * first context on a device is created and held until the process exits.
+ * The call itself allocates, frees and loads nothing.  Sizes that do not fit
+ * return FARM_EINVAL (split the rows into smaller calls).  All calls share
+ * the array and it keeps the last call's contents (nothing in it needs to
+ * start at zero): calls whose work overlaps on the GPU -- on different
+ * streams or contexts of the same device -- race on it and must be
+ * serialised by the caller.
  * Work is enqueued on the context's stream; nothing is synchronised.  A zero
  * or non-finite row is reported by the next farm_sync as FARM_EINVAL.
  */
@@ -469,13 +475,19 @@ farm_status farm_rank_rows_noalloc(farm_ctx *ctx, int32_t scene_id, int64_t n_ro
  *   y[i], weight w[i] (NULL: 1)) rows used as given, writes the loss
  *   L = sum_i w_i (f(xq_i).f(xd_i) - y_i)^2 / sum_i w_i and its gradient with
  *   respect to [W1 | b1 | W2 | b2] (grad, hidden*dim + hidden + out_dim*hidden
- *   + out_dim floats; NULL to skip).  Host pointers; synchronises.
+ *   + out_dim floats; NULL to skip), in the arithmetic of `precision`:
+ *   FARM_PREC_FP32_SIMT (FP32 on the CUDA cores, the reference) or
+ *   FARM_PREC_BF16 (the training step's: inputs, weights and activations
+ *   rounded to BF16 for the tensor-core contractions, FP32 accumulation and
+ *   elementwise steps).  Host pointers; synchronises.
  * farm_mlp_train: minimises that loss with Adam (lr, betas 0.9/0.999) over
  *   `epochs` passes of mini-batches of `batch` pairs, shuffled each epoch by
- *   SplitMix64 from `seed`; pair i joins row pair_row[i] of `rows` ([n_rows,
- *   dim], host, normalised on the GPU) with object pair_obj[i] of scene
- *   scene_id.  loss_out[epoch] (nullable) receives the mean batch loss.
- *   Starts from the installed weights.  Synchronises.
+ *   SplitMix64 from `seed`, every contraction on the BF16 tensor cores (FP32
+ *   master weights).  Pair i joins row pair_row[i] of `rows` ([n_rows, dim],
+ *   host, normalised on the GPU) with object pair_obj[i] of scene
+ *   scene_ids[pair_scene[i]] (pair_scene may be NULL when n_scenes == 1).
+ *   loss_out[epoch] (nullable) receives the mean batch loss.  Starts from the
+ *   installed weights.  Synchronises.
  * farm_mlp_embed: f of n_rows host rows x (normalised first) into host
  *   out [n_rows, out_dim], with FP32 CUDA-core kernels (FARM_PREC_FP32_SIMT)
  *   or the BF16 tensor-core inference path (FARM_PREC_BF16).
@@ -484,10 +496,11 @@ farm_status farm_mlp_set(farm_ctx *ctx, int32_t dim, int32_t hidden, int32_t out
                          const float *b1, const float *W2, const float *b2);
 farm_status farm_mlp_get(farm_ctx *ctx, float *W1, float *b1, float *W2, float *b2);
 farm_status farm_mlp_loss_grad(farm_ctx *ctx, int64_t n_pairs, const float *xq, const float *xd, const float *y,
-                               const float *w, float *loss, float *grad);
-farm_status farm_mlp_train(farm_ctx *ctx, int32_t scene_id, int64_t n_rows, const float *rows, int64_t n_pairs,
-                           const int32_t *pair_row, const int32_t *pair_obj, const float *y, const float *w,
-                           int32_t epochs, int32_t batch, float lr, uint64_t seed, float *loss_out);
+                               const float *w, int32_t precision, float *loss, float *grad);
+farm_status farm_mlp_train(farm_ctx *ctx, int32_t n_scenes, const int32_t *scene_ids, int64_t n_rows,
+                           const float *rows, int64_t n_pairs, const int32_t *pair_row, const int32_t *pair_scene,
+                           const int32_t *pair_obj, const float *y, const float *w, int32_t epochs, int32_t batch,
+                           float lr, uint64_t seed, float *loss_out);
 farm_status farm_mlp_embed(farm_ctx *ctx, int64_t n_rows, const float *x, int32_t precision, float *out);
 
 /*

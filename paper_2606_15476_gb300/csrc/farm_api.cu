@@ -371,6 +371,7 @@ farm_status farm_destroy(farm_ctx *ctx)
     cudaFree(c.mlp.params);
     cudaFree(c.mlp.w1b);
     cudaFree(c.mlp.w2b);
+    cudaFree(c.mlp.w2t);
     if (c.h_err) cudaFreeHost(c.h_err);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->h_blob) cudaFreeHost(ctx->h_blob);
@@ -420,6 +421,9 @@ farm_status farm_create(farm_ctx **out, int device, void *cuda_stream, const far
     if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) return bail(FARM_ECUDA);
     if (cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return bail(FARM_ECUDA);
+    // the static scratch array of farm_rank_rows_noalloc: resolved here, so
+    // that calls of that entry point take no memory and load no module
+    if (farm::noalloc_setup(device) != cudaSuccess) return bail(FARM_ECUDA);
     *out = ctx;
     return FARM_OK;
 }
@@ -869,7 +873,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         } else if (it != c.tuned.end()) {
             vlist = {it->second};
         } else {
-            vlist = {0, 1, 2, 3, 4};
+            vlist = {0, 1, 2};
             graph = false;
         }
     }
@@ -1509,6 +1513,23 @@ farm_status farm_sync(farm_ctx *ctx)
     return check_device_errors(ctx);
 }
 
+farm_status farm_memory_release(farm_ctx *ctx, int32_t scene_id)
+{
+    if (!ctx) return FARM_EINVAL;
+    Ctx &c = ctx->c;
+    if (scene_id < 0 || scene_id >= kMaxScenes || !c.scenes[scene_id].present)
+        return fail(ctx, FARM_EINVAL, "unknown scene");
+    CK(cudaSetDevice(c.device));
+    // queued work may still read the scene
+    CK(cudaStreamSynchronize(c.stream));
+    free_scene(c.scenes[scene_id]);
+    CK(cudaMemsetAsync(ctx->d_scenes + scene_id, 0, sizeof(SceneDev), c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    c.batch_valid = false;
+    c.scene_gen += 1;
+    return FARM_OK;
+}
+
 farm_status farm_scene_info(farm_ctx *ctx, int32_t scene_id, int64_t *n, int32_t *dim)
 {
     if (!ctx) return FARM_EINVAL;
@@ -1581,7 +1602,7 @@ farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_
 farm_status farm_sim_variant_pin(farm_ctx *ctx, int32_t variant)
 {
     if (!ctx) return FARM_EINVAL;
-    if (variant < -1 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [-1, 5)");
+    if (variant < -1 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [-1, 3)");
     ctx->c.pinned_variant = variant;
     return FARM_OK;
 }
@@ -1594,7 +1615,7 @@ farm_status farm_similarity_variant(farm_ctx *ctx, int32_t scene_id, int64_t n_r
     if (scene_id < 0 || scene_id >= kMaxScenes || !c.scenes[scene_id].present)
         return fail(ctx, FARM_EINVAL, "unknown scene");
     if (n_rows < 0) return fail(ctx, FARM_EINVAL, "n_rows must be >= 0");
-    if (variant < 0 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [0, 5)");
+    if (variant < 0 || variant >= farm::kSimVariants) return fail(ctx, FARM_EINVAL, "variant must lie in [0, 3)");
     int mode;
     if (precision == FARM_PREC_FP32) mode = farm::kSimF16x3;
     else if (precision == FARM_PREC_BF16) mode = farm::kSimBf16;

@@ -130,6 +130,7 @@ struct Mlp {
     float *params = nullptr;      // FP32 [W1 (H x D) | b1 (H) | W2 (P x H) | b2 (P)]
     uint16_t *w1b = nullptr;      // BF16 [H, D_pad], zero padded
     uint16_t *w2b = nullptr;      // BF16 [P, H]
+    uint16_t *w2t = nullptr;      // BF16 [H, P] (W2 transposed, for the backward pass)
     uint64_t version = 0;         // bumped whenever the weights change
     int64_t count() const { return (int64_t)H * D + H + (int64_t)P * H + P; }
     float *W1() const { return params; }
@@ -172,7 +173,17 @@ struct Ctx {
 // ---- learned prefilter (k_mlp.cu) ----
 cudaError_t mlp_gemm(bool ta, bool tb, int M, int N, int K, float alpha, const float *A, int lda, const float *B,
                      int ldb, float beta, float *C, int ldc, cudaStream_t s);
-cudaError_t mlp_bias_gelu(float *h, const float *b, float *a, int64_t rows, int cols, cudaStream_t s);
+cudaError_t mlp_bias_gelu(float *h, const float *b, float *a, int64_t rows, int cols, cudaStream_t s,
+                          uint16_t *ab = nullptr);
+// BF16 rows gathered from several tables: dst[r] = base[sel[r]] + idx[r] * lds
+// (sel null: base[0]); cols, lds, ldd multiples of 8, dst 16-byte aligned.
+cudaError_t mlp_gather_rows_bf16(const uint16_t *const *base, const int32_t *sel, const int32_t *idx, int64_t lds,
+                                 int64_t rows, int cols, uint16_t *dst, int64_t ldd, cudaStream_t s);
+// dst[c * ldd + col0 + r] = bf16(src[r * lds + c]) (src FP32 src32, or BF16 src16).
+cudaError_t mlp_transpose_bf16(const float *src32, const uint16_t *src16, int64_t lds, int64_t rows, int cols,
+                               uint16_t *dst, int64_t ldd, int64_t col0, cudaStream_t s);
+// BF16 copy of a row-major FP32 [rows, cols] matrix with rows zero-padded to ldd.
+cudaError_t mlp_to_bf16_padded(const float *src, int64_t rows, int cols, uint16_t *dst, int ldd, cudaStream_t s);
 cudaError_t mlp_bias_normalize(float *z, const float *b, float *e, float *norm, int64_t rows, int cols,
                                cudaStream_t s);
 cudaError_t mlp_pair_loss(const float *eq, const float *ed, const float *y, const float *w, float wsum, int64_t pairs,
@@ -202,6 +213,16 @@ cudaError_t learned_refresh_scene(farm_ctx *ctx, int32_t scene_id);
 // The internal state behind a public farm_ctx handle.
 Ctx *ctx_of(farm_ctx *ctx);
 
+// Device address of farm_rank_rows_noalloc's static scratch array for the
+// current device `device`, resolved once (loads its module); farm_create calls it.
+cudaError_t noalloc_setup(int device);
+// Force-load the kernels farm_rank_rows_noalloc launches, so that its calls
+// load no code (modules and functions load lazily on first use).
+cudaError_t preload_prep();
+cudaError_t preload_sim_simt();
+cudaError_t preload_select_rows();
+cudaError_t preload_sim_tc_f16x3();
+
 // ---- kernel launchers (each returns cudaGetLastError() after launching) ----
 
 // Unit-normalise `rows` rows of length dim into dst rows of length dim_pad
@@ -226,16 +247,17 @@ cudaError_t launch_sim_simt(const float *q, const float *d, float *S, int64_t ro
                             int32_t dim_pad, int64_t ld_s, cudaStream_t s);
 
 // Tiles of the tensor-core similarity kernels: kSimTileM query rows per CTA;
-// a tile configuration ("variant") fixes the tile width and the cluster size
-// (CTAs on vertically adjacent tiles sharing one descriptor tile):
-//   0: 256 objects, clusters of 2;  1: 256, 1;  2: 128, 2;  3: 128, 1;
-//   4: 256 objects, a CTA pair computing 256 x 256 tiles with two-SM MMAs.
+// a tile configuration ("variant") fixes the tile width and whether two CTAs
+// compute one tile together:
+//   0: 128 x 256 tiles, one CTA each;  1: 128 x 128, one CTA each;
+//   2: 256 x 256 tiles, a CTA pair with two-SM MMAs.
 // Every variant computes each output with the same K order, so they give
 // bitwise identical results; the planner's autotuner picks the fastest.
 constexpr int kSimTileM = 128;
-constexpr int kSimVariants = 5;
-inline int sim_variant_bn(int v) { return (v < 2 || v == 4) ? 256 : 128; }
-inline int sim_variant_cluster(int v) { return (v & 1) ? 1 : 2; }
+constexpr int kSimVariants = 3;
+constexpr int kSimPairVariant = 2;      // the single-problem launches use the CTA pairs
+inline int sim_variant_bn(int v) { return v == 1 ? 128 : 256; }
+inline int sim_variant_cluster(int v) { return v == 2 ? 2 : 1; }
 enum SimMode { kSimF16x3 = 0, kSimBf16 = 1, kSimFp8 = 2 };
 
 // Group maxima: with a non-null `tops` the similarity epilogue also writes,
@@ -300,7 +322,7 @@ cudaError_t launch_sim_tc_grouped(int mode, int variant, const void *q0, const v
                                   cudaStream_t s);
 
 // One problem (rows x n, S leading dimension ld_s, group maxima at tops with
-// group_stride(n) floats per row, nullable) on the tensor cores, variant 4 (CTA pairs).
+// group_stride(n) floats per row, nullable) on the tensor cores, variant 2 (CTA pairs).
 // Three FP16 terms, hi*hi + 2^-11 (hi*lo + lo*hi), from the split the
 // normalisation writes.
 cudaError_t launch_sim_tc_f16x3(const uint16_t *q_hi, const uint16_t *q_lo, const uint16_t *d_hi,

@@ -3,9 +3,13 @@
 // its forward and backward passes for training on (query row, descriptor,
 // oracle cosine) pairs with the loss
 //   L = sum_i w_i (f(q_i) . f(d_i) - y_i)^2 / sum_i w_i,
-// and an Adam update.  All arithmetic is FP32 on the CUDA cores; inference
-// reuses the forward kernels (the compressed rows are then used by the
-// tensor-core similarity kernel).  GELU is the exact erf form.
+// and an Adam update.  The contractions of training and inference run on the
+// tensor cores (BF16 operands, FP32 accumulation) through the similarity
+// kernel of k_sim_tc.cu, fed by the gathers, transposes and BF16 conversions
+// below; the tiled FP32 GEMM on the CUDA cores here is the FP32 reference
+// arithmetic of farm_mlp_loss_grad and farm_mlp_embed.  Elementwise steps
+// (bias, GELU in its exact erf form, normalisation, the loss and their
+// gradients, Adam) are FP32 on the CUDA cores.
 #include <cuda_bf16.h>
 
 #include "farm_internal.h"
@@ -85,15 +89,23 @@ __device__ __forceinline__ float gelu_grad(float x)
     return cdf + x * pdf;
 }
 
-// h[r, j] += b[j] (pre-activation kept), a[r, j] = gelu(h[r, j]).
+__device__ __forceinline__ uint16_t bf16_bits(float x)
+{
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<uint16_t *>(&b);
+}
+
+// h[r, j] += b[j] (pre-activation kept), a[r, j] = gelu(h[r, j]) (and its BF16 copy ab, nullable).
 __global__ void bias_gelu_kernel(float *__restrict__ h, const float *__restrict__ b, float *__restrict__ a,
-                                 int64_t rows, int cols)
+                                 uint16_t *__restrict__ ab, int64_t rows, int cols)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows * cols) return;
     const float v = h[i] + b[i % cols];
     h[i] = v;
-    a[i] = gelu(v);
+    const float g = gelu(v);
+    a[i] = g;
+    if (ab) ab[i] = bf16_bits(g);
 }
 
 // z[r, :] += b, then e = z / |z| (norm kept); one warp per row.
@@ -204,6 +216,60 @@ __global__ void gather_rows_kernel(const float *__restrict__ src, int lds, const
     dst[i] = src[(int64_t)idx[r] * lds + c];
 }
 
+// dst[r, 0:cols] = src_r[0:cols] with src_r = base[sel[r]] + idx[r] * lds (BF16 rows;
+// sel null: table entry 0), 16 bytes per thread (cols and the strides multiples of 8).
+__global__ void gather_rows_bf16_kernel(const uint16_t *const *__restrict__ base, const int32_t *__restrict__ sel,
+                                        const int32_t *__restrict__ idx, int64_t lds, int64_t rows, int cols,
+                                        uint16_t *__restrict__ dst, int64_t ldd)
+{
+    const int per_row = cols >> 3;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * per_row) return;
+    const int64_t r = i / per_row;
+    const int c = (int)(i - r * per_row);
+    const uint16_t *src = base[sel ? sel[r] : 0] + (int64_t)idx[r] * lds;
+    reinterpret_cast<uint4 *>(dst + r * ldd)[c] = reinterpret_cast<const uint4 *>(src)[c];
+}
+
+// dst[c, col0 + r] = bf16(src[r, c]) for r < rows, c < cols (32 x 32 tiles
+// through shared memory: reads along rows of src, writes along rows of dst).
+template <class T>
+__global__ void transpose_bf16_kernel(const T *__restrict__ src, int64_t lds, int64_t rows, int cols,
+                                      uint16_t *__restrict__ dst, int64_t ldd, int64_t col0)
+{
+    __shared__ uint16_t tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8 threads
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t r = r0 + k;
+        const int c = c0 + tx;
+        uint16_t v = 0;
+        if (r < rows && c < cols) {
+            if constexpr (sizeof(T) == 4) v = bf16_bits(src[r * lds + c]);
+            else v = src[r * lds + c];
+        }
+        tile[k][tx] = v;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int c = c0 + k;
+        const int64_t r = r0 + tx;
+        if (c < cols && r < rows) dst[(int64_t)c * ldd + col0 + r] = tile[tx][k];
+    }
+}
+
+// dst[r, c] = bf16(src[r, c]) for c < cols, 0 for cols <= c < ldd.
+__global__ void to_bf16_padded_kernel(const float *__restrict__ src, int64_t rows, int cols, uint16_t *__restrict__ dst,
+                                      int ldd)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * ldd) return;
+    const int64_t r = i / ldd;
+    const int c = (int)(i - r * ldd);
+    dst[i] = c < cols ? bf16_bits(src[r * cols + c]) : (uint16_t)0;
+}
+
 // Adam with bias correction (step t >= 1).
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                             float *__restrict__ v, int64_t count, float lr, float b1, float b2, float eps, int t)
@@ -236,10 +302,39 @@ cudaError_t mlp_gemm(bool ta, bool tb, int M, int N, int K, float alpha, const f
     return cudaGetLastError();
 }
 
-cudaError_t mlp_bias_gelu(float *h, const float *b, float *a, int64_t rows, int cols, cudaStream_t s)
+cudaError_t mlp_bias_gelu(float *h, const float *b, float *a, int64_t rows, int cols, cudaStream_t s,
+                          uint16_t *ab)
 {
     if (rows * cols <= 0) return cudaSuccess;
-    bias_gelu_kernel<<<blocks_for(rows * cols, 256), 256, 0, s>>>(h, b, a, rows, cols);
+    bias_gelu_kernel<<<blocks_for(rows * cols, 256), 256, 0, s>>>(h, b, a, ab, rows, cols);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_gather_rows_bf16(const uint16_t *const *base, const int32_t *sel, const int32_t *idx, int64_t lds,
+                                 int64_t rows, int cols, uint16_t *dst, int64_t ldd, cudaStream_t s)
+{
+    if (rows * cols <= 0) return cudaSuccess;
+    if ((cols & 7) || (lds & 7) || (ldd & 7) || (reinterpret_cast<uintptr_t>(dst) & 15)) return cudaErrorInvalidValue;
+    gather_rows_bf16_kernel<<<blocks_for(rows * (cols >> 3), 256), 256, 0, s>>>(base, sel, idx, lds, rows, cols, dst,
+                                                                                ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_transpose_bf16(const float *src32, const uint16_t *src16, int64_t lds, int64_t rows, int cols,
+                               uint16_t *dst, int64_t ldd, int64_t col0, cudaStream_t s)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    if (src32) transpose_bf16_kernel<float><<<grid, 256, 0, s>>>(src32, lds, rows, cols, dst, ldd, col0);
+    else transpose_bf16_kernel<uint16_t><<<grid, 256, 0, s>>>(src16, lds, rows, cols, dst, ldd, col0);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_to_bf16_padded(const float *src, int64_t rows, int cols, uint16_t *dst, int ldd, cudaStream_t s)
+{
+    if (rows <= 0 || ldd <= 0) return cudaSuccess;
+    if (ldd < cols) return cudaErrorInvalidValue;
+    to_bf16_padded_kernel<<<blocks_for(rows * ldd, 256), 256, 0, s>>>(src, rows, cols, dst, ldd);
     return cudaGetLastError();
 }
 

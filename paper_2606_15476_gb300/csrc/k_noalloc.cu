@@ -10,12 +10,15 @@
 // similarity product against a scene's descriptors, the per-row rank select --
 // with every intermediate array in one statically allocated device array.
 //
-// The array is a file-scope __device__ variable, so every GPU that loads the
-// library holds it until the process exits.  Host code cannot use the
-// variable's name as a device address (on the host it is only a stand-in), so
-// the first call on each device resolves the address with
-// cudaGetSymbolAddress, with that device current, and every kernel receives
-// that pointer.
+// The array is a file-scope __device__ variable.  Host code cannot use the
+// variable's name as a device address (on the host it is only a stand-in),
+// so farm_create resolves the address with cudaGetSymbolAddress once per
+// device, with that device current, and every kernel receives that pointer.
+// Resolving the symbol also loads this file's device module (modules load
+// lazily), so the array's memory is taken when the first context on the
+// device is created, not inside a call of the entry point; the device keeps
+// it until the process exits.  The kernels the entry point launches are
+// loaded at the same time.
 #include <mutex>
 
 #include "farm_internal.h"
@@ -34,6 +37,28 @@ void *g_scratch_ptr[kMaxDevices] = {};
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
+
+// Resolves the scratch array's device address for `device` (which must be the
+// current device) unless that is done already.  Called by farm_create.
+cudaError_t noalloc_setup(int device)
+{
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (g_scratch_ptr[device]) return cudaSuccess;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
+    // the kernels of the entry point, loaded now for the same reason
+    cudaError_t el = preload_prep();
+    if (el == cudaSuccess) el = preload_sim_simt();
+    if (el == cudaSuccess) el = preload_select_rows();
+    if (el == cudaSuccess && sim_tc_available()) el = preload_sim_tc_f16x3();
+    if (el != cudaSuccess) return el;
+    g_scratch_ptr[device] = p;
+    return cudaSuccess;
+}
+
 }  // namespace farm
 
 using farm::Ctx;
@@ -74,14 +99,9 @@ extern "C" farm_status farm_rank_rows_noalloc(farm_ctx *ctx, int32_t scene_id, i
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lock(farm::g_setup_mutex);
-        if (!farm::g_scratch_ptr[c.device]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, farm::g_noalloc_scratch);
-            if (e != cudaSuccess || !p) return fail(FARM_ECUDA, "farm_rank_rows_noalloc: cudaGetSymbolAddress failed");
-            farm::g_scratch_ptr[c.device] = p;
-        }
         base = farm::g_scratch_ptr[c.device];
     }
+    if (!base) return fail(FARM_ESTATE, "farm_rank_rows_noalloc: the scratch array was not set up by farm_create");
     unsigned char *b = static_cast<unsigned char *>(base);
     float *q0 = reinterpret_cast<float *>(b);
     float *q1 = n_row_copies == 2 ? reinterpret_cast<float *>(b + row_bytes) : nullptr;

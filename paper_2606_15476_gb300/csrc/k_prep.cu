@@ -145,4 +145,11 @@ cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_vi
     return cudaGetLastError();
 }
 
+// Loads the normalisation kernel (modules and functions load lazily on first use).
+cudaError_t preload_prep()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, normalize_rows_kernel);
+}
+
 }  // namespace farm

@@ -366,4 +366,13 @@ cudaError_t launch_merge_chunks(const Piece *pieces, int32_t n_pieces, int64_t t
     return cudaGetLastError();
 }
 
+// Loads the per-row select kernels (modules and functions load lazily on first use).
+cudaError_t preload_select_rows()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, select_rows_smem_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, select_rows_global_kernel);
+    return e;
+}
+
 }  // namespace farm

@@ -109,4 +109,11 @@ cudaError_t launch_sim_simt(const float *q, const float *d, float *S, int64_t ro
     return cudaGetLastError();
 }
 
+// Loads the CUDA-core similarity kernel (modules and functions load lazily on first use).
+cudaError_t preload_sim_simt()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, sim_simt_kernel);
+}
+
 }  // namespace farm

@@ -99,9 +99,10 @@ struct Elem<kSimFp8> {                       // FP8 E4M3
     static constexpr uint32_t SBO = 1024;    // 8 rows x 128 bytes
 };
 
-// A tile configuration: BN objects per tile, CM CTAs per cluster; PAIR: the
-// two CTAs of a cluster compute one 256 x BN tile with two-SM MMAs
-// (cta_group::2), each holding its 128 rows of A and half of B.
+// A tile configuration: BN objects per tile, CM CTAs per cluster (1, or 2
+// for a pair); PAIR: the two CTAs of a cluster compute one 256 x BN tile with
+// two-SM MMAs (cta_group::2), each holding its 128 rows of A and half of B.
+// Every CTA loads its own operand tiles: no copy is delivered to several CTAs.
 template <int MODE, int BN_, int CM_, bool PAIR_ = false>
 struct Cfg {
     using E = Elem<MODE>;
@@ -124,6 +125,7 @@ struct Cfg {
     static_assert(STAGES >= 3, "pipeline depth");
     static_assert(BN_ / CM_ >= 8 && (B_PART % 1024) == 0, "B share must keep the swizzle atoms whole");
     static_assert(!PAIR_ || (CM_ == 2 && BN_ == 256), "CTA pairs: clusters of two, 256-object tiles");
+    static_assert(PAIR_ || CM_ == 1, "clusters of two only as CTA pairs");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -179,19 +181,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
         ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-        : "memory");
-}
-
-// The same copy delivered to the same shared-memory offset of every CTA in
-// cta_mask, signalling each destination CTA's mbarrier at the offset of `bar`.
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                               uint16_t cta_mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1),
-          "h"(cta_mask)
         : "memory");
 }
 
@@ -271,15 +260,6 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// Commit whose arrival lands on the mbarrier at the offset of `bar` in every
-// CTA of cta_mask.
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t cta_mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(smem_u32(bar)), "h"(cta_mask)
                  : "memory");
 }
 
@@ -372,25 +352,25 @@ __device__ __forceinline__ void tile_origin(int tile, int m_super, int n_tiles, 
     const int per_group = GROUP_M * n_tiles;
     const int g = tile / per_group;
     const int first_m = g * GROUP_M;
-    const int gm = min(GROUP_M, m_super - first_m);
+    // (a tile past the piece, which a correct tile count never gives, lands
+    // beyond its last row: loads read the zero fill, the epilogue writes nothing)
+    const int gm = max(1, min(GROUP_M, m_super - first_m));
     const int in_g = tile - g * per_group;
     m0 = ((first_m + in_g % gm) * CM_ + (int)rank) * BM;
     n0 = (in_g / gm) * BN_;
 }
 
-// Persistent, in clusters of CM CTAs: cluster c walks cluster tiles c,
-// c + (number of clusters), ...; its CTAs compute vertically adjacent tiles of
-// one column tile in lockstep.  Each CTA loads its own A tile and 1/CM of the
-// shared B tile, multicast to every CTA of the cluster, so a stage is full
-// when the CTA's own A and all CM parts of B have landed; a stage is free
-// again when the MMAs of every CTA have consumed it (the "empty" mbarrier
-// counts CM multicast commits).  The shared-memory pipeline runs on across
-// tiles.  When two tiles' accumulators fit the 512 TMEM columns (BF16 and
-// FP8; FP16x3 at 128-object tiles, whose main and correction accumulators
-// take 256 columns) the epilogue of one tile overlaps the MMAs of the next
-// (acc_full / acc_empty mbarriers); FP16x3 at 256-object tiles drains before
-// the next tile's MMAs start, while the producer already prefetches that
-// tile's first stages.
+// Persistent: cluster c (one CTA, or a CTA pair) walks cluster tiles c,
+// c + (number of clusters), ....  A stage is full when the CTA's A tile and
+// its B tile (a pair: both CTAs' A tiles and B halves, counted on the even
+// CTA's barrier) have landed, and free again when the MMAs that read it have
+// completed.  The shared-memory pipeline runs on across tiles.  When two
+// tiles' accumulators fit the 512 TMEM columns (BF16 and FP8; FP16x3 at
+// 128-object tiles, whose main and correction accumulators take 256 columns)
+// the epilogue of one tile overlaps the MMAs of the next (acc_full /
+// acc_empty mbarriers); FP16x3 at 256-object tiles folds the correction
+// accumulator first so that the next tile's correction products overlap the
+// stores, while the producer already prefetches that tile's first stages.
 // A launch covers either one problem (`single`, its B maps map_d0 / map_d1)
 // or, GROUPED, the pieces of a device table: blocks of query rows against
 // different scenes, with their B maps in device memory, numbered by cluster
@@ -480,14 +460,12 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
     const int cluster_id = blockIdx.x / CM, n_clusters = gridDim.x / CM;
-    constexpr uint16_t ALL_CTAS = (uint16_t)((1u << CM) - 1u);
-    constexpr int B_PART = C::B_PART;         // bytes of this CTA's share of a B tile
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            // one multicast commit from each CTA's MMA issuer (a pair: from the even CTA's)
-            mbar_init(&empty[s], PAIR ? 1 : CM);
+            // one commit from the MMA issuer (a pair: the even CTA's, arriving in both CTAs)
+            mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -509,7 +487,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    cluster_sync();    // every CTA's mbarriers are initialised before any multicast reaches them
+    cluster_sync();    // a pair: both CTAs' mbarriers are initialised before the peer's copies or commits reach them
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
@@ -559,13 +537,12 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     mbar_expect_tx(&full[s], STAGE_BYTES);
                     if (TWO_OPERAND_TILES) {
                         tma_load_2d(st, &map_q0, &full[s], kx, qa);
-                        tma_load_2d_mc(st + C::A_BYTES + rank * B_PART, bmap0, &full[s], kx, nb, ALL_CTAS);
+                        tma_load_2d(st + C::A_BYTES, bmap0, &full[s], kx, nb);
                     } else {
                         tma_load_2d(st, &map_q0, &full[s], kx, qa);
                         tma_load_2d(st + C::A_BYTES, &map_q1, &full[s], kx, qa);
-                        tma_load_2d_mc(st + 2 * C::A_BYTES + rank * B_PART, bmap0, &full[s], kx, nb, ALL_CTAS);
-                        tma_load_2d_mc(st + 2 * C::A_BYTES + C::B_BYTES + rank * B_PART, bmap1, &full[s], kx, nb,
-                                       ALL_CTAS);
+                        tma_load_2d(st + 2 * C::A_BYTES, bmap0, &full[s], kx, nb);
+                        tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, bmap1, &full[s], kx, nb);
                     }
                 }
             }
@@ -613,7 +590,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             };
             auto release = [&](int s) {
                 if (PAIR) mma_commit_pair(&empty[s]);
-                else mma_commit_mc(&empty[s], ALL_CTAS);
+                else mma_commit(&empty[s]);
             };
             uint32_t it = 0, tc = 0;
             for (int tile = cluster_id; tile < total && !*abort_flag; tile += n_clusters, ++tc) {
@@ -938,15 +915,18 @@ int32_t k_slices_of(int32_t dim_pad)
     return (dim_pad + Elem<MODE>::BK - 1) / Elem<MODE>::BK;
 }
 
-// One problem, tile configuration 4 (256 x 256 tiles on CTA pairs).
+// One problem, tile configuration 2 (256 x 256 tiles on CTA pairs).
 template <int MODE>
 cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void *d1, float *S, int64_t rows,
                       int64_t n, int32_t dim_pad, int64_t ld_s, const float *scale_q, const float *scale_d,
                       float *tops, int num_sms, int32_t *err, cudaStream_t s)
 {
     constexpr int BN_ = 256, CM_ = 2;
+    static_assert(BN_ == 256 && CM_ == 2, "the tile count below is that of the pair variant");
     constexpr bool TWO = !Elem<MODE>::SPLIT;
     if (rows <= 0 || n <= 0) return cudaSuccess;
+    if (sim_variant_bn(kSimPairVariant) != BN_ || sim_variant_cluster(kSimPairVariant) != CM_)
+        return cudaErrorInvalidConfiguration;
     if (dim_pad % kDimAlign != 0 || rows > 0x7fffffffLL || n > 0x7fffffffLL || ld_s < n || ld_s > 0x7fffffffLL)
         return cudaErrorInvalidValue;
     if (!get_encoder()) return cudaErrorNotSupported;
@@ -976,7 +956,7 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     single.tile_begin = 0;
     single.gshift = group_shift_for(n);
     return launch_impl<MODE, BN_, CM_, false, true>(mq0, mq1, md0, md1, nullptr, 1, single, S, tops,
-                                              k_slices_of<MODE>(dim_pad), sim_cluster_tiles(rows, n, 4), scale_q,
+                                              k_slices_of<MODE>(dim_pad), sim_cluster_tiles(rows, n, kSimPairVariant), scale_q,
                                               num_sms, err, s);
 }
 
@@ -1010,18 +990,12 @@ cudaError_t launch_grouped_variant(int variant, const void *q0, const void *q1, 
 {
     switch (variant) {
     case 0:
-        return launch_grouped<MODE, 256, 2>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
-                                            scale_q, num_sms, err, s);
-    case 1:
         return launch_grouped<MODE, 256, 1>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
                                             scale_q, num_sms, err, s);
-    case 2:
-        return launch_grouped<MODE, 128, 2>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
-                                            scale_q, num_sms, err, s);
-    case 3:
+    case 1:
         return launch_grouped<MODE, 128, 1>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
                                             scale_q, num_sms, err, s);
-    case 4:
+    case 2:
         return launch_grouped<MODE, 256, 2, true>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S,
                                                   tops, scale_q, num_sms, err, s);
     default:
@@ -1095,6 +1069,14 @@ cudaError_t launch_sim_tc_fp8(const uint8_t *q, const float *scale_q, const uint
 {
     return launch_tc<kSimFp8>(q, nullptr, d, nullptr, S, rows, n, dim_pad, ld_s, scale_q, scale_d, tops, num_sms,
                               err, s);
+}
+
+// Loads the single-problem FP32-accurate kernel (CTA pairs; modules and
+// functions load lazily on first use).
+cudaError_t preload_sim_tc_f16x3()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, sim_tc_kernel<kSimF16x3, 256, 2, false, true>);
 }
 
 }  // namespace farm

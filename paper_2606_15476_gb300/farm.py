@@ -72,8 +72,9 @@ def _load():
         "farm_rank_rows_noalloc": (C.c_int, [P, I32, I64, P, I32, I32, P, P]),
         "farm_mlp_set": (C.c_int, [P, I32, I32, I32, P, P, P, P]),
         "farm_mlp_get": (C.c_int, [P, P, P, P, P]),
-        "farm_mlp_loss_grad": (C.c_int, [P, I64, P, P, P, P, P, P]),
-        "farm_mlp_train": (C.c_int, [P, I32, I64, P, I64, P, P, P, P, I32, I32, C.c_float, U64, P]),
+        "farm_memory_release": (C.c_int, [P, I32]),
+        "farm_mlp_loss_grad": (C.c_int, [P, I64, P, P, P, P, I32, P, P]),
+        "farm_mlp_train": (C.c_int, [P, I32, P, I64, P, I64, P, P, P, P, P, I32, I32, C.c_float, U64, P]),
         "farm_mlp_embed": (C.c_int, [P, I64, P, I32, P]),
         "farm_set_profiling": (C.c_int, [P, I32]),
         "farm_stage_times": (C.c_int, [P, P, P, I32]),
@@ -95,7 +96,7 @@ def exported_symbols():
             "farm_query_batch", "farm_memory_add_space", "farm_query_batch_rrf", "farm_associate", "farm_topk", "farm_sync", "farm_similarity", "farm_scene_info",
             "farm_select_fallbacks", "farm_sim_tuning", "farm_sim_variant_pin", "farm_similarity_variant",
             "farm_candidates",
-            "farm_rank_rows_noalloc", "farm_mlp_set", "farm_mlp_get", "farm_mlp_loss_grad",
+            "farm_rank_rows_noalloc", "farm_memory_release", "farm_mlp_set", "farm_mlp_get", "farm_mlp_loss_grad",
             "farm_mlp_train", "farm_mlp_embed", "farm_set_profiling", "farm_stage_times",
             "farm_last_error", "farm_version"]
 
@@ -313,7 +314,7 @@ def farm_sim_tuning(ctx):
 
 
 def farm_sim_variant_pin(ctx, variant: int) -> None:
-    """Pin the grouped similarity to one tile variant (0..4), or -1 for the autotuner."""
+    """Pin the grouped similarity to one tile variant (0..2), or -1 for the autotuner."""
     _ck(ctx, _lib.farm_sim_variant_pin(ctx, int(variant)))
 
 
@@ -411,7 +412,14 @@ def farm_mlp_get(ctx, dim: int, hidden: int, out_dim: int):
     return W1, b1, W2, b2
 
 
-def farm_mlp_loss_grad(ctx, xq, xd, y, w, n_params: int):
+def farm_memory_release(ctx, scene_id: int) -> None:
+    """Free an uploaded scene's device memory."""
+    _ck(ctx, _lib.farm_memory_release(ctx, int(scene_id)))
+
+
+def farm_mlp_loss_grad(ctx, xq, xd, y, w, n_params: int, precision: int = PREC_FP32_SIMT):
+    """Loss and gradient of the prefilter network on host pairs, in FP32 on the
+    CUDA cores (PREC_FP32_SIMT) or in the BF16 tensor-core training arithmetic (PREC_BF16)."""
     xq, pq = _host(xq, np.float32)
     xd, pd = _host(xd, np.float32)
     y, py = _host(y, np.float32)
@@ -420,13 +428,17 @@ def farm_mlp_loss_grad(ctx, xq, xd, y, w, n_params: int):
         w, wp = _host(w, np.float32)
     loss = np.zeros(1, np.float32)
     grad = np.zeros(n_params, np.float32)
-    _ck(ctx, _lib.farm_mlp_loss_grad(ctx, int(xq.shape[0]), pq, pd, py, wp, loss.ctypes.data_as(C.c_void_p),
-                                     grad.ctypes.data_as(C.c_void_p)))
+    _ck(ctx, _lib.farm_mlp_loss_grad(ctx, int(xq.shape[0]), pq, pd, py, wp, int(precision),
+                                     loss.ctypes.data_as(C.c_void_p), grad.ctypes.data_as(C.c_void_p)))
     return float(loss[0]), grad
 
 
-def farm_mlp_train(ctx, scene_id: int, rows, pair_row, pair_obj, y, w=None, epochs: int = 1,
-                   batch: int = 4096, lr: float = 1e-3, seed: int = 0):
+def farm_mlp_train(ctx, scene_id, rows, pair_row, pair_obj, y, w=None, epochs: int = 1,
+                   batch: int = 4096, lr: float = 1e-3, seed: int = 0, pair_scene=None):
+    """Train the prefilter; scene_id is one scene id, or a list of them with
+    pair_scene[i] the position of pair i's scene in that list."""
+    ids = [int(scene_id)] if np.isscalar(scene_id) else [int(x) for x in scene_id]
+    sids, ps_ = _host(np.asarray(ids, np.int32), np.int32)
     rows, pr = _host(rows, np.float32)
     a, pa = _host(pair_row, np.int32)
     o, po = _host(pair_obj, np.int32)
@@ -434,8 +446,11 @@ def farm_mlp_train(ctx, scene_id: int, rows, pair_row, pair_obj, y, w=None, epoc
     wp = None
     if w is not None:
         ww, wp = _host(w, np.float32)
+    psp = None
+    if pair_scene is not None:
+        psa, psp = _host(pair_scene, np.int32)
     losses = np.zeros(epochs, np.float32)
-    _ck(ctx, _lib.farm_mlp_train(ctx, int(scene_id), int(rows.shape[0]), pr, int(a.shape[0]), pa, po, py, wp,
+    _ck(ctx, _lib.farm_mlp_train(ctx, len(ids), ps_, int(rows.shape[0]), pr, int(a.shape[0]), pa, psp, po, py, wp,
                                  int(epochs), int(batch), C.c_float(lr), C.c_uint64(seed),
                                  losses.ctypes.data_as(C.c_void_p)))
     return losses

@@ -196,7 +196,7 @@ def test_reduced_paths_recall_100k_objects(F, site100k, prec):
         F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
         code = F.PREC_BF16
         if prec == "learned":
-            bench.train_prefilter(F, ctx, scenes)
+            bench.train_prefilter(F, ctx, sc.dim)
             code = F.PREC_LEARNED
         h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred, qb.c_emb, code)
         out = F.farm_topk(ctx, h, 10, qb.n_q)
