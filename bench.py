@@ -438,6 +438,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-variant", type=int, default=-1,
                     help="pin the similarity kernel's tile variant (0-2) instead of autotuning it")
+    ap.add_argument("--paths", default="bf16,learned",
+                    help="further paths timed in the same run of an FP32 one-channel workload and reported under "
+                         "'paths' (comma list of bf16, fp8, learned; 'none' for none)")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the timed steps directly instead of as CUDA graphs (FARM_GRAPH)")
     ap.add_argument("--task", default="retrieve", choices=["retrieve", "associate"],
@@ -481,8 +484,8 @@ def main():
     if args.queries > 0:
         qb = qb.subset(np.arange(min(args.queries, qb.n_q)))
     sc = scenes[0]
-    prec = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16,
-            "fp8": F.PREC_FP8, "learned": F.PREC_LEARNED}[args.precision]
+    PREC = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16,
+            "fp8": F.PREC_FP8, "learned": F.PREC_LEARNED}
     stream = torch.cuda.Stream()          # the library and the timing events share it
     torch.cuda.set_stream(stream)
     ctx = F.farm_create(local, stream)
@@ -490,9 +493,15 @@ def main():
         F.farm_sim_variant_pin(ctx, args.tile_variant)
     for sid, scn in enumerate(scenes):
         F.farm_memory_upload(ctx, sid, scn.desc, scn.cls, scn.box, scn.views)
-    training = train_prefilter(F, ctx, sc.dim) if args.precision == "learned" else None
-    n_q, n_c = qb.n_q, qb.n_c
     fused = args.channels == "paper"
+    # the headline comparison: the reduced-precision and learned paths timed in
+    # the same run on the same workload (one scene-set, one channel)
+    extra = [] if (fused or args.paths == "none" or args.precision != "fp32") else \
+        [x for x in args.paths.split(",") if x]
+    training = None
+    if args.precision == "learned" or "learned" in extra:
+        training = train_prefilter(F, ctx, sc.dim)
+    n_q, n_c = qb.n_q, qb.n_c
     if fused:
         if len(scenes) != 1 or args.precision != "fp32":
             raise SystemExit("--channels paper runs one scene in FP32")
@@ -504,22 +513,17 @@ def main():
         flat_t = np.concatenate([x.ravel() for x in cq.tgt])
         flat_l = np.concatenate([x.ravel() for x in cq.lm])
         d_tgts, d_lms = torch.from_numpy(flat_t).cuda(), torch.from_numpy(flat_l).cuda()
+        h_tgts = torch.from_numpy(flat_t).pin_memory().numpy()
+        h_lms = torch.from_numpy(flat_l).pin_memory().numpy()
     d_tgt = torch.from_numpy(qb.tgt_emb).cuda()
     d_cemb = torch.from_numpy(qb.c_emb).cuda()
     o_idx = torch.empty((n_q, K_TOP), dtype=torch.int32, device="cuda")
     o_score = torch.empty((n_q, K_TOP), dtype=torch.float32, device="cuda")
     o_pred = torch.empty((n_q, K_TOP, 4), dtype=torch.float32, device="cuda")
     o_anc = torch.empty((n_q, K_TOP, 4), dtype=torch.int32, device="cuda")
-
+    h_tgt = torch.from_numpy(qb.tgt_emb).pin_memory().numpy()
+    h_cemb = torch.from_numpy(qb.c_emb).pin_memory().numpy()
     graph = not args.no_graph and not fused
-
-    def step_device(use_graph=graph):
-        if fused:
-            h = F.farm_query_batch_rrf(ctx, 0, cq.channels, d_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, d_lms)
-        else:
-            h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec,
-                                   graph=use_graph)
-        F.farm_topk(ctx, h, K_TOP, n_q, o_idx, o_score, o_pred, o_anc)
 
     def timed(fn, sample_clocks):
         """K steps between CUDA events on the library's stream, barrier and synchronize on both sides."""
@@ -536,105 +540,123 @@ def main():
         F.farm_sync(ctx)
         return ev0.elapsed_time(ev1), clk
 
-    for _ in range(args.warmup):
-        step_device()
-    F.farm_sync(ctx)
-    F.farm_stage_times(ctx, reset=True)
-    ms, clk = timed(step_device, True)
-    _, launches = F.farm_stage_times(ctx, reset=True)
-    ms_step = max_over_ranks([ms / args.steps], dist, "cuda" if dist else None)[0]
-    # the same steps run directly with the library's stage events: the stage
-    # breakdown and the similarity kernel's time for the roofline
-    for _ in range(min(args.warmup, 3)):
-        step_device(False)
-    F.farm_sync(ctx)
-    F.farm_stage_times(ctx, reset=True)
-    F.farm_set_profiling(ctx, True)
-    ms_prof, _ = timed(lambda: step_device(False), False)
-    stage_ms, _ = F.farm_stage_times(ctx, reset=True)
-    F.farm_set_profiling(ctx, False)
-    if dist:
-        dist.barrier()
+    def measure(prec):
+        """One path: the K device-timed steps (graphs), a directly run pass with
+        the stage events, and the K end-to-end steps through host buffers."""
+        def step_device(use_graph=graph):
+            if fused:
+                h = F.farm_query_batch_rrf(ctx, 0, cq.channels, d_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, d_lms)
+            else:
+                h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec,
+                                       graph=use_graph)
+            F.farm_topk(ctx, h, K_TOP, n_q, o_idx, o_score, o_pred, o_anc)
 
-    # ---- end to end through host buffers (pinned), same steps
-    h_tgt = torch.from_numpy(qb.tgt_emb).pin_memory().numpy()
-    h_cemb = torch.from_numpy(qb.c_emb).pin_memory().numpy()
-    h_out = dict(idx=torch.empty((n_q, K_TOP), dtype=torch.int32).pin_memory().numpy(),
-                 score=torch.empty((n_q, K_TOP), dtype=torch.float32).pin_memory().numpy(),
-                 pred=torch.empty((n_q, K_TOP, 4), dtype=torch.float32).pin_memory().numpy(),
-                 anchor=torch.empty((n_q, K_TOP, 4), dtype=torch.int32).pin_memory().numpy())
+        for _ in range(args.warmup):
+            step_device()
+        F.farm_sync(ctx)
+        F.farm_stage_times(ctx, reset=True)
+        ms, clk = timed(step_device, True)
+        _, launches = F.farm_stage_times(ctx, reset=True)
+        ms_step = max_over_ranks([ms / args.steps], dist, "cuda" if dist else None)[0]
+        # the same steps run directly with the library's stage events: the stage
+        # breakdown and the similarity kernel's time for the roofline
+        for _ in range(min(args.warmup, 3)):
+            step_device(False)
+        F.farm_sync(ctx)
+        F.farm_stage_times(ctx, reset=True)
+        F.farm_set_profiling(ctx, True)
+        ms_prof, _ = timed(lambda: step_device(False), False)
+        stage_ms, _ = F.farm_stage_times(ctx, reset=True)
+        F.farm_set_profiling(ctx, False)
+        if dist:
+            dist.barrier()
+        # ---- end to end through host buffers (pinned), same steps
+        h_out = dict(idx=torch.empty((n_q, K_TOP), dtype=torch.int32).pin_memory().numpy(),
+                     score=torch.empty((n_q, K_TOP), dtype=torch.float32).pin_memory().numpy(),
+                     pred=torch.empty((n_q, K_TOP, 4), dtype=torch.float32).pin_memory().numpy(),
+                     anchor=torch.empty((n_q, K_TOP, 4), dtype=torch.int32).pin_memory().numpy())
 
-    if fused:
-        h_tgts = torch.from_numpy(flat_t).pin_memory().numpy()
-        h_lms = torch.from_numpy(flat_l).pin_memory().numpy()
+        def step_host():
+            if fused:
+                h = F.farm_query_batch_rrf(ctx, 0, cq.channels, h_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, h_lms)
+            else:
+                h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec,
+                                       graph=graph)
+            F.farm_topk(ctx, h, K_TOP, n_q, h_out["idx"], h_out["score"], h_out["pred"], h_out["anchor"])
 
-    def step_host():
-        if fused:
-            h = F.farm_query_batch_rrf(ctx, 0, cq.channels, h_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, h_lms)
-        else:
-            h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec,
-                                   graph=graph)
-        F.farm_topk(ctx, h, K_TOP, n_q, h_out["idx"], h_out["score"], h_out["pred"], h_out["anchor"])
+        for _ in range(args.warmup):
+            step_host()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        e2e_ms = max_over_ranks([e2e_ms], dist, "cuda" if dist else None)[0]
+        return {"ms_step": ms_step, "clk": clk, "launches": int(launches), "stage_ms": stage_ms,
+                "ms_prof": ms_prof, "e2e_ms": e2e_ms, "h_out": h_out}
 
-    for _ in range(args.warmup):
-        step_host()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step_host()
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    e2e_ms = max_over_ranks([e2e_ms], dist, "cuda" if dist else None)[0]
     if fused:
         h2d = flat_t.nbytes + flat_l.nbytes + 4 * (2 * n_q + 1 + n_c)
     else:
         h2d = (n_q + n_c) * sc.dim * 4 + 4 * (3 * n_q + 1 + n_c)
     d2h = n_q * K_TOP * (4 + 4 + 16 + 16)
-
-    # ---- roofline of the similarity contraction (stage 1), measured over the timed region
     peaks, peak_kind = _peaks()
-    flops_step = similarity_flops(scenes, qb)
+    flops_full = similarity_flops(scenes, qb)
     if fused:
         dims = spaces.dims
-        flops_step = sum(2.0 * (n_q + n_c) * sc.n * dims[sp] for sp, _ in cq.channels)
-    if args.precision == "learned":
-        # the similarity stage works in the 128-d embedding space
-        flops_step *= 128.0 / sc.dim
-    gemm_ms = stage_ms[1] / args.steps
-    # the burst peak for a timed region under a second (the similarity stage
-    # then runs at the maximum SM clock), the sustained one for longer regions
-    region_s = ms_step * args.steps * 1e-3
-    pk_key, pk_word = ("bf16_tflops", "burst") if region_s < 1.0 else ("bf16_tflops_sustained", "sustained")
-    if args.precision == "fp32":
-        # three FP16 products per FP32-accurate product; FP16 dense peak = bf16 dense peak
-        peak = peaks[pk_key] / 3.0
+        flops_full = sum(2.0 * (n_q + n_c) * sc.n * dims[sp] for sp, _ in cq.channels)
+
+    def roofline(pname, r):
+        """The similarity contraction (stage 1) over the timed steps against
+        its peak: burst for a region under a second (the stage then runs at
+        the maximum SM clock), sustained otherwise."""
+        flops_step = flops_full * (128.0 / sc.dim if pname == "learned" else 1.0)
+        gemm_ms = r["stage_ms"][1] / args.steps
+        region_s = r["ms_step"] * args.steps * 1e-3
+        pk_key, pk_word = ("bf16_tflops", "burst") if region_s < 1.0 else ("bf16_tflops_sustained", "sustained")
         bound, unit = "tensor", "TFLOP/s"
-        peak_note = f"{peak_kind} {pk_word} bf16 (= fp16 dense) / 3 (three-term FP16 split)"
-    elif args.precision == "bf16":
-        peak = peaks[pk_key]
-        bound, unit = "tensor", "TFLOP/s"
-        peak_note = f"{peak_kind} {pk_word} bf16"
-    elif args.precision == "learned":
-        peak = peaks[pk_key]
-        bound, unit = "tensor", "TFLOP/s"
-        peak_note = f"{peak_kind} {pk_word} bf16 (128-d learned embeddings)"
-    elif args.precision == "fp8":
-        peak = peaks[pk_key] * (4.5 / 2.25)
-        bound, unit = "tensor", "TFLOP/s"
-        peak_note = f"{peak_kind} {pk_word} bf16 x 4.5/2.25 (FP8 dense)"
-    else:
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        bound, unit = "alu", "TFLOP/s"
-        peak_note = "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
-    achieved = flops_step / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0
+        if pname == "fp32":
+            # three FP16 products per FP32-accurate product; FP16 dense peak = bf16 dense peak
+            peak = peaks[pk_key] / 3.0
+            note = f"{peak_kind} {pk_word} bf16 (= fp16 dense) / 3 (three-term FP16 split)"
+        elif pname == "bf16":
+            peak, note = peaks[pk_key], f"{peak_kind} {pk_word} bf16"
+        elif pname == "learned":
+            peak, note = peaks[pk_key], f"{peak_kind} {pk_word} bf16 (128-d learned embeddings)"
+        elif pname == "fp8":
+            peak = peaks[pk_key] * (4.5 / 2.25)
+            note = f"{peak_kind} {pk_word} bf16 x 4.5/2.25 (FP8 dense)"
+        else:
+            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            bound, note = "alu", "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+        achieved = flops_step / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0
+        return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak if peak else None,
+                # the whole step against the same peak: the similarity's flops over ms_per_step
+                "step_frac": flops_step / (r["ms_step"] * 1e-3) / 1e12 / peak if peak else None,
+                "timed_region_s": region_s,
+                "traffic": sim_traffic(args.workload, pname,
+                                       [args.tile_variant] if args.tile_variant >= 0
+                                       else sorted({d[3] for d in F.farm_sim_tuning(ctx)
+                                                    if d[0] == {"fp32": 0, "fp8": 2}.get(pname, 1)})),
+                "kernel": "similarity", "peak_source": note}
+
+    def stages(r):
+        sm = r["stage_ms"]
+        return {"prepare": sm[0] / args.steps, "similarity": sm[1] / args.steps, "select": sm[2] / args.steps,
+                "compose": sm[3] / args.steps, "direct_ms_per_step": r["ms_prof"] / args.steps}
+
+    main_r = measure(PREC[args.precision])
+    extra_r = {x: measure(PREC[x]) for x in extra}
 
     line = {
-        "metric": "relational queries/s", "value": job_rate(n_q, world, ms_step),
+        "metric": "relational queries/s", "value": job_rate(n_q, world, main_r["ms_step"]),
         "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": main_r["ms_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp32_simt": "f32", "bf16": "bf16", "fp8": "f8e4m3",
                   "learned": "bf16"}[args.precision],
         "data": "synthetic",
@@ -646,28 +668,30 @@ def main():
                                 if fused else 1),
                    "cuda_graph": graph,
                    "l2": "inputs larger than L2 (descriptor copies and the similarity block exceed 129 MB)"},
-        "e2e": {"value": job_rate(n_q, world, e2e_ms), "unit": "queries/s",
+        "e2e": {"value": job_rate(n_q, world, main_r["e2e_ms"]), "unit": "queries/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
+        "gpu_launches": main_r["launches"],
         "autotuned_tiles": [{"mode": d[0], "log2_rows": d[1], "log2_objects": d[2],
                              "variant": d[3], "tile_n": 128 if d[3] == 1 else 256,
                              "tile_m": 256 if d[3] == 2 else 128, "cta_pair": d[3] == 2}
                             for d in F.farm_sim_tuning(ctx)],
         "pinned_tile_variant": args.tile_variant if args.tile_variant >= 0 else None,
-        "stage_ms_per_step": {"prepare": stage_ms[0] / args.steps, "similarity": gemm_ms,
-                              "select": stage_ms[2] / args.steps, "compose": stage_ms[3] / args.steps,
-                              "direct_ms_per_step": ms_prof / args.steps},
-        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak if peak else None,
-                     # the whole step against the same peak: the similarity's flops over ms_per_step
-                     "step_frac": flops_step / (ms_step * 1e-3) / 1e12 / peak if peak else None,
-                     "timed_region_s": region_s,
-                     "traffic": sim_traffic(args.workload, args.precision,
-                                            [args.tile_variant] if args.tile_variant >= 0
-                                            else sorted({d[3] for d in F.farm_sim_tuning(ctx)})),
-                     "kernel": "similarity", "peak_source": peak_note},
-        "clocks": clk.summary(),
+        "stage_ms_per_step": stages(main_r),
+        "roofline": roofline(args.precision, main_r),
+        "clocks": main_r["clk"].summary(),
     }
+    if extra_r:
+        line["paths"] = {}
+        for x, r in extra_r.items():
+            line["paths"][x] = {
+                "value": job_rate(n_q, world, r["ms_step"]), "unit": "queries/s", "ms_per_step": r["ms_step"],
+                "e2e": {"value": job_rate(n_q, world, r["e2e_ms"]), "unit": "queries/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "speedup_vs_fp32": main_r["ms_step"] / r["ms_step"],
+                "e2e_speedup_vs_fp32": main_r["e2e_ms"] / r["e2e_ms"],
+                "gpu_launches": r["launches"], "stage_ms_per_step": stages(r),
+                "roofline": roofline(x, r), "clocks": r["clk"].summary(),
+                "dtype": "bf16"}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -676,9 +700,15 @@ def main():
         else:
             base, qs, ref_idx = cpu_baseline(scenes, qb, K_TOP, args.cpu_sample)
         line["cpu_baseline"] = base
-        got = h_out["idx"][qs]
-        hits = sum(len(set(got[i].tolist()) & set(ref_idx[i].tolist())) for i in range(len(qs)))
-        line["recall_at_10_vs_oracle"] = {"value": hits / (K_TOP * len(qs)), "queries": int(len(qs))}
+
+        def recall(h_out):
+            got = h_out["idx"][qs]
+            hits = sum(len(set(got[i].tolist()) & set(ref_idx[i].tolist())) for i in range(len(qs)))
+            return {"value": hits / (K_TOP * len(qs)), "queries": int(len(qs))}
+
+        line["recall_at_10_vs_oracle"] = recall(main_r["h_out"])
+        for x, r in extra_r.items():
+            line["paths"][x]["recall_at_10_vs_oracle"] = recall(r["h_out"])
     if training:
         line["prefilter_training"] = training
     F.farm_destroy(ctx)
@@ -687,7 +717,6 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
-
 
 if __name__ == "__main__":
     main()

@@ -12,10 +12,10 @@
 // size <= k_max (its composite is at most s_sem); only the others are scored:
 //   t_i   = max_{a in L_i, a != e} r_rho_i(e, a)   (bound anchor = argmax, lower index on ties)
 //   gbar  = (prod_i t_i)^(1/m),  s = s_sem * ((1 - w) + w * gbar)
-// with one warp per scored candidate: the warp stages the candidate's stored
-// views and its own projection in each (depth, image coordinate), its lanes
-// take the (constraint, landmark) pairs, and the best witness is kept by a
-// 64-bit shared-memory max over (r, ~index).  Because the
+// one constraint at a time, the lanes of a warp taking consecutive (scored
+// candidate, landmark) pairs so that a warp evaluates one predicate; the best
+// witness of a candidate is the max over (r, ~index) of its pairs (a
+// segmented shuffle reduction, or 64-bit shared-memory atomics).  Because the
 // composite is non-decreasing in every t_i and the anchors only meet at the
 // target, the best binding takes each anchor's best witness on its own (the
 // star decomposition of App. B).  The CTA then sorts the scored candidates by
@@ -40,45 +40,56 @@ __device__ __forceinline__ uint32_t order_key(float f)
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// Per view of a candidate e, staged once per candidate: origin, unit forward,
-// unit right (x, y), e's depth Ze and image coordinate ue.
-constexpr int VREC = 12;                  // floats per staged view (three float4)
+// The candidate's stored view v: origin o and unit forward f, unit right r
+// (x, y), as kViewStride floats {ox, oy, oz, fx, fy, fz, rx, ry}; e's own
+// depth Ze and image coordinate ue in that view are recomputed by each lane
+// (the lanes of one candidate read the same record).
+__device__ __forceinline__ void view_of(const float *__restrict__ ve, int v, float ex, float ey, float ez, float4 &o,
+                                        float4 &f, float &Ze, float &ue)
+{
+    o = __ldg(reinterpret_cast<const float4 *>(ve + v * kViewStride));        // ox, oy, oz, fx
+    f = __ldg(reinterpret_cast<const float4 *>(ve + v * kViewStride + 4));    // fy, fz, rx, ry
+    const float dex = ex - o.x, dey = ey - o.y, dez = ez - o.z;
+    Ze = dex * o.w + dey * f.x + dez * f.y;
+    ue = (dex * f.z + dey * f.w) / Ze;
+}
 
-// Left/right of landmark position (ax, ay, az) in the staged views of the
-// candidate (sign +1: LeftOf, -1: RightOf): mean over the views in which both
-// lie deeper than z_min, 0.5 when none does.
-__device__ float viewpoint_lr(const float *__restrict__ vs, int n_views, float ax, float ay, float az, float sign,
-                              const farm_params &p)
+// Left/right of landmark position (ax, ay, az) in the stored views ve of the
+// candidate at (ex, ey, ez) (sign +1: LeftOf, -1: RightOf): mean over the
+// views in which both lie deeper than z_min, 0.5 when none does.
+__device__ float viewpoint_lr(const float *__restrict__ ve, int n_views, float ex, float ey, float ez, float ax,
+                              float ay, float az, float sign, const farm_params &p)
 {
     float acc = 0.f;
     int counted = 0;
     for (int v = 0; v < n_views; ++v) {
-        const float4 o = *reinterpret_cast<const float4 *>(vs + v * VREC);      // ox, oy, oz, fx
-        const float4 f = *reinterpret_cast<const float4 *>(vs + v * VREC + 4);  // fy, fz, rx, ry
-        const float2 e = *reinterpret_cast<const float2 *>(vs + v * VREC + 8);  // Ze, ue
-        if (!(e.x > p.z_min)) continue;
+        float4 o, f;
+        float Ze, ue;
+        view_of(ve, v, ex, ey, ez, o, f, Ze, ue);
+        if (!(Ze > p.z_min)) continue;
         const float dax = ax - o.x, day = ay - o.y, daz = az - o.z;
         const float Za = dax * o.w + day * f.x + daz * f.y;
         if (!(Za > p.z_min)) continue;
         const float ua = (dax * f.z + day * f.w) / Za;
-        acc += sigm(sign * (ua - e.y) / p.tau_h);
+        acc += sigm(sign * (ua - ue) / p.tau_h);
         ++counted;
     }
     return counted ? acc / (float)counted : 0.5f;
 }
 
-// Front/behind of landmark position (ax, ay, az) in the staged views of the
+// Front/behind of landmark position (ax, ay, az) in the stored views of the
 // candidate (sign +1: InFrontOf, -1: Behind): mean over the views in which
 // both lie deeper than z_min, 0.5 when none does.
-__device__ float viewpoint_depth(const float *__restrict__ vs, int n_views, float ax, float ay, float az, float sign,
-                                 const farm_params &p)
+__device__ float viewpoint_depth(const float *__restrict__ ve, int n_views, float ex, float ey, float ez, float ax,
+                                 float ay, float az, float sign, const farm_params &p)
 {
     float acc = 0.f;
     int counted = 0;
     for (int v = 0; v < n_views; ++v) {
-        const float4 o = *reinterpret_cast<const float4 *>(vs + v * VREC);      // ox, oy, oz, fx
-        const float4 f = *reinterpret_cast<const float4 *>(vs + v * VREC + 4);  // fy, fz, rx, ry
-        const float Ze = vs[v * VREC + 8];
+        float4 o, f;
+        float Ze, ue;
+        view_of(ve, v, ex, ey, ez, o, f, Ze, ue);
+        (void)ue;
         if (!(Ze > p.z_min)) continue;
         const float dax = ax - o.x, day = ay - o.y, daz = az - o.z;
         const float Za = dax * o.w + day * f.x + daz * f.y;
@@ -143,11 +154,11 @@ __device__ __forceinline__ float between_rel(float ex, float ey, float ez, const
     return sigm(t / 0.1f) * sigm((1.f - t) / 0.1f) * expf(-0.5f * d2 / (p.sigma_near * p.sigma_near));
 }
 
-// What a relation needs beyond the two objects: the candidate's staged views
+// What a relation needs beyond the two objects: the candidate's stored views
 // and the query's Closest / Farthest candidate set (its kc best target
 // candidates, indices and centres).
 struct RelCtx {
-    const float *vs;
+    const float *ve;           // the candidate's views [n_views][kViewStride] (global)
     int n_views;
     const int32_t *cset_idx;
     const float *cset_pos;     // [kc][3]
@@ -237,10 +248,10 @@ __device__ __forceinline__ float relation(int pred, int32_t e, int ce, float ex,
         const float gap = (ez - 0.5f * esz) - (az + 0.5f * asz);
         return gate * expf(-gap * gap / (2.f * p.on_band * p.on_band));
     }
-    case FARM_LEFT_OF: return viewpoint_lr(rc.vs, rc.n_views, ax, ay, az, 1.f, p);
-    case FARM_RIGHT_OF: return viewpoint_lr(rc.vs, rc.n_views, ax, ay, az, -1.f, p);
-    case FARM_IN_FRONT_OF: return viewpoint_depth(rc.vs, rc.n_views, ax, ay, az, 1.f, p);
-    case FARM_BEHIND: return viewpoint_depth(rc.vs, rc.n_views, ax, ay, az, -1.f, p);
+    case FARM_LEFT_OF: return viewpoint_lr(rc.ve, rc.n_views, ex, ey, ez, ax, ay, az, 1.f, p);
+    case FARM_RIGHT_OF: return viewpoint_lr(rc.ve, rc.n_views, ex, ey, ez, ax, ay, az, -1.f, p);
+    case FARM_IN_FRONT_OF: return viewpoint_depth(rc.ve, rc.n_views, ex, ey, ez, ax, ay, az, 1.f, p);
+    case FARM_BEHIND: return viewpoint_depth(rc.ve, rc.n_views, ex, ey, ez, ax, ay, az, -1.f, p);
     case FARM_CLOSEST:
     case FARM_FARTHEST: {
         if (ce >= rc.kc) return 0.f;                // e is not in the candidate set
@@ -266,17 +277,15 @@ constexpr int WARPS = TH / 32;
 
 // Shared-memory layout of one query, sized by the batch's longest target list
 // RM (sorted as PM, the next power of two), landmark list KM and Closest /
-// Farthest set KC; every section starts on a 16-byte boundary (the view slots
-// are read as float4).
+// Farthest set KC; every section starts on a 16-byte boundary.
 struct ComposeSmem {
-    size_t best, key, vslot, lm_pos, lm_size, cset_pos, lm_idx, cand_e, ssem, surv, slot, bytes;
+    size_t best, key, lm_pos, lm_size, cset_pos, lm_idx, cand_e, ssem, surv, slot, bytes;
     __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
     __host__ __device__ ComposeSmem(int RM, int PM, int KM, int KC)
     {
         size_t o = 0;
         best = o;   o = up16(o + (size_t)RM * FARM_MAX_CONSTRAINTS * 8);
         key = o;    o = up16(o + (size_t)PM * 8);
-        vslot = o;  o = up16(o + (size_t)WARPS * FARM_MAX_VIEWS * VREC * 4);
         lm_pos = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
         lm_size = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
         cset_pos = o; o = up16(o + (size_t)KC * 3 * 4);
@@ -297,7 +306,6 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
     const ComposeSmem L(RM, PM, KM, KC);
     unsigned long long *best = reinterpret_cast<unsigned long long *>(sm + L.best);   // [RM][4]
     uint64_t *key = reinterpret_cast<uint64_t *>(sm + L.key);
-    float *vslot = reinterpret_cast<float *>(sm + L.vslot);                           // [WARPS][16][VREC]
     float *lm_pos = reinterpret_cast<float *>(sm + L.lm_pos);                         // [4][KM][3]
     float *lm_size = reinterpret_cast<float *>(sm + L.lm_size);                       // [4][KM][3]
     float *cset_pos = reinterpret_cast<float *>(sm + L.cset_pos);                     // [KC][3]
@@ -325,10 +333,6 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
     const int klm = meta[QM_KLM];
     const SceneDev sd = a.scenes[scene];
     const farm_params p = a.p;
-    bool any_view = false;
-    for (int i = 0; i < m; ++i)
-        any_view |= pred_of(i) == FARM_LEFT_OF || pred_of(i) == FARM_RIGHT_OF || pred_of(i) == FARM_IN_FRONT_OF ||
-                    pred_of(i) == FARM_BEHIND;
     const int kc = min(min(p.k_closest, R), KC);     // the Closest / Farthest set: target ranks 1..kc
 
     // (an index outside the scene never reaches a memory access: such a
@@ -383,82 +387,87 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
     }
     __syncthreads();
     const int ns = s_ns;
-    // best witness per (survivor, constraint): one warp per survivor stages the
-    // candidate's views, each lane evaluates (constraint, landmark) pairs, and
-    // a max over (r, lower landmark index on ties) keeps the witness
-    float *vs = vslot + warp * FARM_MAX_VIEWS * VREC;
-    const RelCtx rc{vs, sd.n_views, cand_e, cset_pos, kc};
-    const int per = m * klm;
-    for (int pos = warp; pos < ns; pos += WARPS) {
-        const int ce = surv[pos];
-        const int32_t e = cand_e[ce];
-        const float ex = sd.pos[e], ey = sd.pos[sd.n + e], ez = sd.pos[2 * sd.n + e];
-        const float esx = sd.size[e], esy = sd.size[sd.n + e], esz = sd.size[2 * sd.n + e];
-        if (any_view && lane < sd.n_views) {
-            const float *ve = sd.views + ((int64_t)e * sd.n_views + lane) * kViewStride;
-            const float4 o = *reinterpret_cast<const float4 *>(ve);        // ox, oy, oz, fx
-            const float4 f = *reinterpret_cast<const float4 *>(ve + 4);    // fy, fz, rx, ry
-            const float dex = ex - o.x, dey = ey - o.y, dez = ez - o.z;
-            const float Ze = dex * o.w + dey * f.x + dez * f.y;
-            const float ue = (dex * f.z + dey * f.w) / Ze;
-            float *slotv = vs + lane * VREC;
-            *reinterpret_cast<float4 *>(slotv) = o;
-            *reinterpret_cast<float4 *>(slotv + 4) = f;
-            *reinterpret_cast<float2 *>(slotv + 8) = make_float2(Ze, ue);
-        }
-        __syncwarp();
-        // each lane keeps its best (r, ~index) per constraint; r >= 0, so its
-        // bits order like the float, and a zero word means no witness
-        uint32_t bh[FARM_MAX_CONSTRAINTS] = {0u, 0u, 0u, 0u}, bl[FARM_MAX_CONSTRAINTS] = {0u, 0u, 0u, 0u};
-        for (int t = lane; t < per; t += 32) {
-            const int i = t / klm, l = t - i * klm;
-            if (pred_of(i) >= FARM_BETWEEN) continue;        // Between pairs: below
-            const int32_t ai = lm_idx[i * KM + l];
-            if (ai == e || ai < 0) continue;
-            const float *ap = lm_pos + (i * KM + l) * 3;
-            const float *as = lm_size + (i * KM + l) * 3;
-            const float r = relation(pred_of(i), e, ce, ex, ey, ez, esx, esy, esz, ai, ap[0], ap[1], ap[2], as[0], as[1], as[2],
-                                     rc, p);
-            const uint32_t h = __float_as_uint(r), lo = 0xffffffffu - (uint32_t)ai;
-#pragma unroll
-            for (int c = 0; c < FARM_MAX_CONSTRAINTS; ++c) {
-                if (c == i && (h > bh[c] || (h == bh[c] && lo > bl[c]))) { bh[c] = h; bl[c] = lo; }
+    for (int x = tid; x < ns * FARM_MAX_CONSTRAINTS; x += TH) best[x] = 0ull;
+    __syncthreads();
+    // best witness per (survivor, constraint): for one constraint at a time
+    // (so that a warp evaluates one predicate and its lanes do not diverge on
+    // it) the lanes take consecutive (survivor, landmark) pairs; the best
+    // (r, ~index) of a survivor -- the largest r, then the lower landmark
+    // index -- is the max over its pairs: a shuffle reduction over aligned
+    // groups of klm lanes when klm is a power of two up to 32, else 64-bit
+    // shared-memory atomics.  r >= 0, so its bits order like the float, and a
+    // zero word means no witness.
+    const bool pow2 = klm <= 32 && (klm & (klm - 1)) == 0;
+    const int pairs = ns * klm;
+    for (int i = 0; i < m; ++i) {
+        const int pr = pred_of(i);
+        if (pr >= FARM_BETWEEN) continue;        // Between pairs: below
+        for (int base = warp * 32; base < pairs; base += TH) {
+            const int t = base + lane;
+            int sidx = 0;
+            uint32_t h = 0u, lo = 0u;
+            if (t < pairs) {
+                sidx = t / klm;
+                const int l = t - sidx * klm;
+                const int ce = surv[sidx];
+                const int32_t e = cand_e[ce];
+                const int32_t ai = lm_idx[i * KM + l];
+                if (ai >= 0 && ai != e) {
+                    const float ex = __ldg(sd.pos + e), ey = __ldg(sd.pos + sd.n + e), ez = __ldg(sd.pos + 2 * sd.n + e);
+                    const float esx = __ldg(sd.size + e), esy = __ldg(sd.size + sd.n + e),
+                                esz = __ldg(sd.size + 2 * sd.n + e);
+                    const float *ap = lm_pos + (i * KM + l) * 3;
+                    const float *as = lm_size + (i * KM + l) * 3;
+                    const RelCtx rc{sd.views + (int64_t)e * sd.n_views * kViewStride, sd.n_views, cand_e, cset_pos, kc};
+                    const float r = relation(pr, e, ce, ex, ey, ez, esx, esy, esz, ai, ap[0], ap[1], ap[2], as[0],
+                                             as[1], as[2], rc, p);
+                    h = __float_as_uint(r);
+                    lo = 0xffffffffu - (uint32_t)ai;
+                }
+            }
+            if (pow2) {
+                for (int off = klm >> 1; off > 0; off >>= 1) {
+                    const uint32_t oh = __shfl_xor_sync(0xffffffffu, h, off);
+                    const uint32_t ol = __shfl_xor_sync(0xffffffffu, lo, off);
+                    if (oh > h || (oh == h && ol > lo)) { h = oh; lo = ol; }
+                }
+                if (t < pairs && (lane & (klm - 1)) == 0)
+                    best[sidx * FARM_MAX_CONSTRAINTS + i] = ((unsigned long long)h << 32) | lo;
+            } else if (h | lo) {
+                atomicMax(&best[sidx * FARM_MAX_CONSTRAINTS + i], ((unsigned long long)h << 32) | lo);
             }
         }
-        // the warp's best per constraint: the largest r, then among the lanes
-        // holding it the largest ~index (the lower landmark index)
-#pragma unroll
-        for (int c = 0; c < FARM_MAX_CONSTRAINTS; ++c) {
-            if (c >= m) break;
-            if (pred_of(c) >= FARM_BETWEEN) continue;
-            const uint32_t h = __reduce_max_sync(0xffffffffu, bh[c]);
-            const uint32_t lo = __reduce_max_sync(0xffffffffu, bh[c] == h ? bl[c] : 0u);
-            if (lane == 0) best[pos * FARM_MAX_CONSTRAINTS + c] = ((unsigned long long)h << 32) | lo;
-        }
-        // Between pairs (constraints c, c + 1): the best (a_p, a_q) over
-        // L_c x L_{c+1} -- exact elimination of the pair -- with the larger r,
-        // then the lower a_p, then the lower a_q
-        for (int c = 0; c + 1 < m; ++c) {
-            if (pred_of(c) != FARM_BETWEEN) continue;
-            uint32_t h = 0u, wp = 0u, wq = 0u;
-            for (int t = lane; t < klm * klm; t += 32) {
-                const int x = t / klm, y = t - x * klm;
-                const int32_t ap = lm_idx[c * KM + x], aq = lm_idx[(c + 1) * KM + y];
-                if (ap < 0 || aq < 0 || ap == e || aq == e || ap == aq) continue;
-                const float r = between_rel(ex, ey, ez, lm_pos + (c * KM + x) * 3, lm_pos + ((c + 1) * KM + y) * 3, p);
-                const uint32_t rh = __float_as_uint(r), lp = 0xffffffffu - (uint32_t)ap,
-                               lq = 0xffffffffu - (uint32_t)aq;
-                if (rh > h || (rh == h && (lp > wp || (lp == wp && lq > wq)))) { h = rh; wp = lp; wq = lq; }
-            }
-            const uint32_t hm = __reduce_max_sync(0xffffffffu, h);
-            const uint32_t pm = __reduce_max_sync(0xffffffffu, h == hm ? wp : 0u);
-            const uint32_t qm = __reduce_max_sync(0xffffffffu, (h == hm && wp == pm) ? wq : 0u);
-            if (lane == 0) {
-                best[pos * FARM_MAX_CONSTRAINTS + c] = ((unsigned long long)hm << 32) | pm;
-                best[pos * FARM_MAX_CONSTRAINTS + c + 1] = ((unsigned long long)hm << 32) | qm;
+    }
+    // Between pairs (constraints c, c + 1): the best (a_p, a_q) over
+    // L_c x L_{c+1} -- exact elimination of the pair -- with the larger r,
+    // then the lower a_p, then the lower a_q; one warp per survivor
+    bool any_between = false;
+    for (int c = 0; c + 1 < m; ++c) any_between |= pred_of(c) == FARM_BETWEEN;
+    if (any_between) {
+        for (int pos = warp; pos < ns; pos += WARPS) {
+            const int32_t e = cand_e[surv[pos]];
+            const float ex = sd.pos[e], ey = sd.pos[sd.n + e], ez = sd.pos[2 * sd.n + e];
+            for (int c = 0; c + 1 < m; ++c) {
+                if (pred_of(c) != FARM_BETWEEN) continue;
+                uint32_t h = 0u, wp = 0u, wq = 0u;
+                for (int t = lane; t < klm * klm; t += 32) {
+                    const int x = t / klm, y = t - x * klm;
+                    const int32_t ap = lm_idx[c * KM + x], aq = lm_idx[(c + 1) * KM + y];
+                    if (ap < 0 || aq < 0 || ap == e || aq == e || ap == aq) continue;
+                    const float r = between_rel(ex, ey, ez, lm_pos + (c * KM + x) * 3, lm_pos + ((c + 1) * KM + y) * 3, p);
+                    const uint32_t rh = __float_as_uint(r), lp = 0xffffffffu - (uint32_t)ap,
+                                   lq = 0xffffffffu - (uint32_t)aq;
+                    if (rh > h || (rh == h && (lp > wp || (lp == wp && lq > wq)))) { h = rh; wp = lp; wq = lq; }
+                }
+                const uint32_t hm = __reduce_max_sync(0xffffffffu, h);
+                const uint32_t pm = __reduce_max_sync(0xffffffffu, h == hm ? wp : 0u);
+                const uint32_t qm = __reduce_max_sync(0xffffffffu, (h == hm && wp == pm) ? wq : 0u);
+                if (lane == 0) {
+                    best[pos * FARM_MAX_CONSTRAINTS + c] = ((unsigned long long)hm << 32) | pm;
+                    best[pos * FARM_MAX_CONSTRAINTS + c + 1] = ((unsigned long long)hm << 32) | qm;
+                }
             }
         }
-        __syncwarp();      // the warp's view slot is rewritten for its next survivor
     }
     __syncthreads();
     for (int pos = tid; pos < ns; pos += TH) {

@@ -1,11 +1,16 @@
 """GPU: the learned prefilter's kernels against its FP64 CPU oracle.
 
 * the loss and its gradient from the GPU backward kernels against FP64 finite
-  differences of the oracle's forward (relative 1e-3 of the largest entry);
+  differences of the oracle's forward: FP32 on the CUDA cores within 1e-3 of
+  the largest entry, the BF16 tensor-core training arithmetic within its
+  rounding;
 * inference: the FP32 CUDA-core forward within 1e-5 of the oracle, the BF16
   tensor-core forward within BF16 rounding;
 * training lowers the loss, and the trained network beats the untrained one
   on held-out pairs;
+* on the configured 100,000-object workload, with the network trained on
+  separate seeded scenes, training raises the candidate recall at a fixed
+  candidate count over the untrained network and matches linear projections;
 * the learned path reaches Recall@10 >= 0.99 against the FP64 oracle.
 """
 import math
@@ -65,6 +70,34 @@ def test_gradient_matches_oracle_finite_differences(F):
     fd = omlp.fd_grad(p64, xq, xd, y, w, idx=idx)
     scale = np.abs(fd).max()
     np.testing.assert_allclose(grad[idx], fd, rtol=0, atol=1e-3 * scale)
+
+
+def test_bf16_training_gradient_matches_oracle_finite_differences(F):
+    """The training step's arithmetic (BF16 operands on the tensor cores, FP32
+    accumulation): its gradient against FP64 central differences of the
+    oracle's loss, within the rounding of BF16 operands (2^-8 relative each)."""
+    rng = np.random.default_rng(10)
+    D, H, P = 40, 64, 64
+    params = init_params(rng, D, H, P)
+    xq = unit(rng.standard_normal((24, D))).astype(np.float32)
+    xd = unit(rng.standard_normal((24, D))).astype(np.float32)
+    y = rng.uniform(-0.5, 1.0, 24).astype(np.float32)
+    w = rng.uniform(0.5, 2.0, 24).astype(np.float32)
+    ctx = F.farm_create(0)
+    try:
+        F.farm_mlp_set(ctx, *params)
+        n = H * D + H + P * H + P
+        loss, grad = F.farm_mlp_loss_grad(ctx, xq, xd, y, w, n, precision=F.PREC_BF16)
+    finally:
+        F.farm_destroy(ctx)
+    p64 = [p.astype(np.float64) for p in params]
+    assert loss == pytest.approx(omlp.loss(p64, xq, xd, y, w), rel=3e-2)
+    idx = np.concatenate([rng.choice(H * D, 120, replace=False), H * D + np.arange(H),
+                          H * D + H + rng.choice(P * H, 120, replace=False), H * D + H + P * H + np.arange(P)])
+    fd = omlp.fd_grad(p64, xq, xd, y, w, idx=idx)
+    scale = np.abs(fd).max()
+    np.testing.assert_allclose(grad[idx], fd, rtol=0, atol=5e-2 * scale)
+    assert np.linalg.norm(grad[idx] - fd) <= 3e-2 * np.linalg.norm(fd)
 
 
 def test_inference_matches_oracle_forward(F):
@@ -130,55 +163,59 @@ def test_training_lowers_loss_and_generalises(F):
     assert after < 0.5 * before, (before, after)
 
 
-def test_learned_path_recall_and_gain_over_untrained(F):
-    """Training lowers the held-out distillation loss by orders of magnitude and
-    raises the recall of each row's exact top-16 within its compressed top-64
-    (what decides how few candidates the FP32 rescore needs); the learned path
-    then meets Recall@10 >= 0.99 against the FP64 oracle."""
-    scenes, qb = synth.workload("site_n20k_d1152")
-    sc = scenes[0]
-    sub = qb.subset(range(96))
-    rng = np.random.default_rng(6)
-    D, H, P = 1152, 512, 128
-    params = init_params(rng, D, H, P)
-    ctx = F.farm_create(0)
-    try:
-        F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
-        F.farm_mlp_set(ctx, *params)
-        rows_eval = np.concatenate([qb.tgt_emb[:200], qb.c_emb[:200]])
-        S = F.farm_similarity(ctx, 0, rows_eval, sc.n, F.PREC_FP32)
-        true_top = np.argsort(-S, axis=1)[:, :16]
-
-        def cand_recall():
-            ed = F.farm_mlp_embed(ctx, sc.desc, P, F.PREC_BF16)
-            eq = F.farm_mlp_embed(ctx, rows_eval, P, F.PREC_BF16)
-            ctop = np.argsort(-(eq @ ed.T), axis=1)[:, :64]
-            return np.mean([len(set(true_top[i]) & set(ctop[i])) / 16.0 for i in range(len(rows_eval))])
-
-        hold = _self_supervised_pairs(F, ctx, sc, 0, 200, 256, 768, seed=4)
-        xq, xd = unit(hold[0][hold[1]]), sc.desc[hold[2]]
-        n = H * D + H + P * H + P
-        loss_u = F.farm_mlp_loss_grad(ctx, xq, xd, hold[3], hold[4], n)[0]
-        rec_u = cand_recall()
-        rows, pr, po, y, w = _self_supervised_pairs(F, ctx, sc, 0, 1000, 256, 768, seed=7)
-        F.farm_mlp_train(ctx, 0, rows, pr, po, y, w, epochs=2, batch=4096, lr=1e-3, seed=8)
-        loss_t = F.farm_mlp_loss_grad(ctx, xq, xd, hold[3], hold[4], n)[0]
-        rec_t = cand_recall()
-        h = F.farm_query_batch(ctx, sub.scene_of_q, sub.tgt_emb, sub.tgt_cls, sub.c_off, sub.c_pred,
-                               sub.c_emb, F.PREC_LEARNED)
-        trained = F.farm_topk(ctx, h, 10, sub.n_q)
-    finally:
-        F.farm_destroy(ctx)
-    assert loss_t < 0.05 * loss_u, (loss_u, loss_t)
-    assert rec_t >= rec_u + 0.01, (rec_u, rec_t)
-    ref = oracle.batch(sc, sub, 10)
-    hits = sum(len(set(trained["idx"][q].tolist()) & set(ref["idx"][q].tolist())) for q in range(sub.n_q))
-    assert hits / (10.0 * sub.n_q) >= 0.99
-
-
 @pytest.fixture(scope="module")
 def site100k():
     return synth.workload("site_n100k_d1152")
+
+
+def test_trained_network_gain_at_fixed_candidate_count(F, site100k):
+    """What training buys, on the configured workload (the 100,000-object
+    site; the network trained as the benchmark trains it, on 2,000,000 tuples
+    from two separate seeded scenes, never on this memory): the fraction of
+    the plain FP32 path's top 10 that lies within each query's compressed
+    top C.  Training raises it over the untrained network at C = 128 and 256
+    (measured 0.77 -> 0.86 and 0.96 -> 0.98), and matches the two linear
+    baselines -- a Gaussian random projection and PCA-128 -- within 0.02: on
+    these isotropic descriptors (class centroid plus isotropic noise) no
+    128-d map has structure to exploit beyond a well-conditioned projection."""
+    import bench
+    scenes, qb = site100k
+    sc = scenes[0]
+    qs = np.sort(np.random.default_rng(5).choice(qb.n_q, 384, replace=False))
+    sub = qb.subset(qs)
+    ctx = F.farm_create(0)
+    try:
+        F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+        h = F.farm_query_batch(ctx, sub.scene_of_q, sub.tgt_emb, sub.tgt_cls, sub.c_off, sub.c_pred, sub.c_emb,
+                               F.PREC_FP32)
+        ref = F.farm_topk(ctx, h, 10, sub.n_q)["idx"]
+
+        def recall(eq, ed, Cs=(128, 256)):
+            order = np.argsort(-(eq @ ed.T), axis=1)[:, :max(Cs)]
+            return {C: float(np.mean([len(set(ref[i].tolist()) & set(order[i, :C].tolist())) / 10.0
+                                      for i in range(len(ref))])) for C in Cs}
+
+        def mlp_recall():
+            return recall(F.farm_mlp_embed(ctx, sub.tgt_emb, 128, F.PREC_BF16),
+                          F.farm_mlp_embed(ctx, sc.desc, 128, F.PREC_BF16))
+
+        rng = np.random.default_rng(0)
+        F.farm_mlp_set(ctx, *init_params(rng, sc.dim, 512, 128))
+        untrained = mlp_recall()
+        bench.train_prefilter(F, ctx, sc.dim)        # the benchmark's training (its own seeded initial weights)
+        trained = mlp_recall()
+    finally:
+        F.farm_destroy(ctx)
+    Xd, Xq = sc.desc.astype(np.float64), unit(sub.tgt_emb)
+    rp = rng.standard_normal((sc.dim, 128))
+    random_proj = recall(unit(Xq @ rp), unit(Xd @ rp))
+    _, _, vt = np.linalg.svd(Xd[rng.choice(sc.n, 20000, replace=False)], full_matrices=False)
+    pca = recall(unit(Xq @ vt[:128].T), unit(Xd @ vt[:128].T))
+    print(f"\ncandidate recall of the FP32 top 10 within the compressed top C: untrained {untrained}, "
+          f"trained {trained}, random projection {random_proj}, PCA-128 {pca}")
+    for C in (128, 256):
+        assert trained[C] >= untrained[C] + 0.015, (C, untrained, trained)
+        assert trained[C] >= max(random_proj[C], pca[C]) - 0.02, (C, trained, random_proj, pca)
 
 
 @pytest.mark.parametrize("prec", ["learned", "bf16"])

@@ -121,6 +121,30 @@ def test_site_scene_query_slice(F, ctx, site, prec):
 
 
 @pytest.mark.parametrize("prec", [DEFAULT])
+def test_site_tie_free_recipe_exact(F, ctx, prec):
+    """The site at full size (20,000 objects, 4,096 queries in one batch) with
+    a recipe that leaves few ties at the parity tolerance: descriptor noise of
+    norm 1.0 instead of 0.15 and no look-alike classes.  (In the benchmark's
+    recipe the 300-object look-alike classes put most queries' top ranks
+    within the 2e-5 cosine tie tolerance, so most are only bound-checked.)
+    Of 192 sampled queries at least 80% have a unique oracle result (measured
+    169), and for each of those the index list must equal the oracle's
+    exactly and every score lie within 1e-5 relative; the rest pass the bound
+    checks."""
+    sc = synth.make_scene(1, 20000, 1152, extent=(120.0, 120.0, 10.0), n_classes=400, n_views=8,
+                          noise_scale=1.0)
+    qb = synth.make_queries(101, sc, 4096, m_choices=(1, 2, 3, 4))
+    F.farm_memory_upload(ctx, 1, sc.desc, sc.cls, sc.box, sc.views)
+    qb.scene_of_q[:] = 1
+    h, out = run(F, ctx, qb, prec_code(F, prec))
+    sample = np.random.default_rng(3).choice(qb.n_q, size=192, replace=False)
+    rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"], queries=sample)
+    print(f"\nsite, tie-free recipe, 192 sampled queries: {rep.summary()}")
+    assert rep.ok(), rep.summary()
+    assert rep.n_exact >= 0.8 * len(sample), rep.summary()
+
+
+@pytest.mark.parametrize("prec", [DEFAULT])
 def test_site_full_batch_sampled(F, ctx, site, prec):
     """All 4,096 queries in one batch (the benchmark's launch shape); 48 sampled checks."""
     sc, qb = site
@@ -131,6 +155,7 @@ def test_site_full_batch_sampled(F, ctx, site, prec):
     sample = np.random.default_rng(0).choice(qb.n_q, size=48, replace=False)
     rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"],
                             queries=sample)
+    print(f"\nsite, full batch, 48 sampled queries: {rep.summary()}")
     assert rep.ok(), rep.summary()
     # properties that hold for every query at any size
     assert np.all(np.diff(out["score"], axis=1) <= 0)
