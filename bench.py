@@ -133,6 +133,27 @@ def max_over_ranks(values, dist=None, device=None):
     return [float(x) for x in t.tolist()]
 
 
+def l2_statement(args, scenes, dim, rows, multi_ch):
+    """Why no L2 flush is needed between steps: the bytes each step streams
+    (tensor-core operand copies of descriptors and query rows, and the stored
+    similarity columns) against the 129 MB L2."""
+    n_obj = sum(x.n for x in scenes)
+    per = {"fp32": 4, "bf16": 2, "fp8": 1, "learned": 2, "fp32_simt": 4}[args.precision]
+    # the learned path's operands are its 128-d BF16 embeddings
+    operands = (n_obj + rows) * (128 if args.precision == "learned" else dim) * per
+    fused = args.precision in ("fp32", "bf16") and (
+        args.fused == "on" or (args.fused == "default" and args.precision == "fp32"))
+    stored = 0 if fused else 4 * rows * n_obj
+    if multi_ch:
+        return "inputs larger than L2 (four descriptor spaces and their similarity blocks)"
+    what = f"operand copies {operands / 1e6:.0f} MB"
+    if stored:
+        what += f", similarity block {stored / 1e6:.0f} MB written and re-read"
+    elif fused:
+        what += " (plus a stored sample of the similarity block)"
+    return f"inputs larger than L2 ({what}; L2 129 MB)"
+
+
 def job_rate(n_units_per_rank, world, ms_per_step):
     """Whole-job throughput: units all ranks processed / the slowest rank's step time."""
     return world * n_units_per_rank / (ms_per_step * 1e-3)
@@ -441,6 +462,12 @@ def main():
     ap.add_argument("--paths", default="bf16,learned",
                     help="further paths timed in the same run of an FP32 one-channel workload and reported under "
                          "'paths' (comma list of bf16, fp8, learned; 'none' for none)")
+    ap.add_argument("--e2e-sync", action="store_true",
+                    help="end-to-end steps wait for each step's TopK records (no overlap of a step's input copy "
+                         "with the previous step's kernels)")
+    ap.add_argument("--fused", default="default", choices=["default", "on", "off"],
+                    help="the fused rank selection: the library's default (FP32 fused, BF16 not), on (FARM_FUSED) "
+                         "or off (FARM_UNFUSED)")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the timed steps directly instead of as CUDA graphs (FARM_GRAPH)")
     ap.add_argument("--task", default="retrieve", choices=["retrieve", "associate"],
@@ -493,16 +520,16 @@ def main():
         F.farm_sim_variant_pin(ctx, args.tile_variant)
     for sid, scn in enumerate(scenes):
         F.farm_memory_upload(ctx, sid, scn.desc, scn.cls, scn.box, scn.views)
-    fused = args.channels == "paper"
+    multi_ch = args.channels == "paper"
     # the headline comparison: the reduced-precision and learned paths timed in
     # the same run on the same workload (one scene-set, one channel)
-    extra = [] if (fused or args.paths == "none" or args.precision != "fp32") else \
+    extra = [] if (multi_ch or args.paths == "none" or args.precision != "fp32") else \
         [x for x in args.paths.split(",") if x]
     training = None
     if args.precision == "learned" or "learned" in extra:
         training = train_prefilter(F, ctx, sc.dim)
     n_q, n_c = qb.n_q, qb.n_c
-    if fused:
+    if multi_ch:
         if len(scenes) != 1 or args.precision != "fp32":
             raise SystemExit("--channels paper runs one scene in FP32")
         spaces = synth.add_spaces(sc, 9001, dims=(1024, 2048))
@@ -523,7 +550,8 @@ def main():
     o_anc = torch.empty((n_q, K_TOP, 4), dtype=torch.int32, device="cuda")
     h_tgt = torch.from_numpy(qb.tgt_emb).pin_memory().numpy()
     h_cemb = torch.from_numpy(qb.c_emb).pin_memory().numpy()
-    graph = not args.no_graph and not fused
+    graph = not args.no_graph and not multi_ch
+    FUSE = {"default": None, "on": True, "off": False}[args.fused]
 
     def timed(fn, sample_clocks):
         """K steps between CUDA events on the library's stream, barrier and synchronize on both sides."""
@@ -543,21 +571,38 @@ def main():
     def measure(prec):
         """One path: the K device-timed steps (graphs), a directly run pass with
         the stage events, and the K end-to-end steps through host buffers."""
+        host_s = [0.0]
+
         def step_device(use_graph=graph):
-            if fused:
+            t0 = time.perf_counter()
+            if multi_ch:
                 h = F.farm_query_batch_rrf(ctx, 0, cq.channels, d_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, d_lms)
             else:
                 h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec,
-                                       graph=use_graph)
+                                       graph=use_graph, fused=FUSE)
+            host_s[0] += time.perf_counter() - t0
             F.farm_topk(ctx, h, K_TOP, n_q, o_idx, o_score, o_pred, o_anc)
 
         for _ in range(args.warmup):
             step_device()
         F.farm_sync(ctx)
         F.farm_stage_times(ctx, reset=True)
+        F.farm_select_fallbacks(ctx, reset=True)
+        host_s[0] = 0.0
         ms, clk = timed(step_device, True)
+        host_ms = host_s[0] * 1e3 / args.steps
+        fallbacks = F.farm_select_fallbacks(ctx, reset=True)
         _, launches = F.farm_stage_times(ctx, reset=True)
         ms_step = max_over_ranks([ms / args.steps], dist, "cuda" if dist else None)[0]
+        # the host's own time per call (planning, staging, graph launch), the GPU idle before each call
+        plan_s = []
+        for _ in range(min(args.steps, 20)):
+            F.farm_sync(ctx)
+            t0 = time.perf_counter()
+            step_device()
+            plan_s.append(time.perf_counter() - t0)
+        F.farm_sync(ctx)
+        host_plan_ms = statistics.median(plan_s) * 1e3
         # the same steps run directly with the library's stage events: the stage
         # breakdown and the similarity kernel's time for the roofline
         for _ in range(min(args.warmup, 3)):
@@ -576,36 +621,44 @@ def main():
                      pred=torch.empty((n_q, K_TOP, 4), dtype=torch.float32).pin_memory().numpy(),
                      anchor=torch.empty((n_q, K_TOP, 4), dtype=torch.int32).pin_memory().numpy())
 
-        def step_host():
-            if fused:
+        def step_host(asynchronous):
+            if multi_ch:
                 h = F.farm_query_batch_rrf(ctx, 0, cq.channels, h_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, h_lms)
             else:
                 h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec,
-                                       graph=graph)
-            F.farm_topk(ctx, h, K_TOP, n_q, h_out["idx"], h_out["score"], h_out["pred"], h_out["anchor"])
+                                       graph=graph, fused=FUSE)
+            F.farm_topk(ctx, h, K_TOP, n_q, h_out["idx"], h_out["score"], h_out["pred"], h_out["anchor"],
+                        asynchronous=asynchronous)
 
+        # a serving loop: each step copies its rows in and its TopK records out
+        # (pinned host buffers); with the asynchronous TopK (default) a step's
+        # input copy overlaps the previous step's kernels, and the last
+        # step's records are read after the closing farm_sync
+        asynchronous = not args.e2e_sync
         for _ in range(args.warmup):
-            step_host()
+            step_host(False)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            step_host()
+            step_host(asynchronous)
+        F.farm_sync(ctx)
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
         e2e_ms = max_over_ranks([e2e_ms], dist, "cuda" if dist else None)[0]
         return {"ms_step": ms_step, "clk": clk, "launches": int(launches), "stage_ms": stage_ms,
-                "ms_prof": ms_prof, "e2e_ms": e2e_ms, "h_out": h_out}
+                "ms_prof": ms_prof, "e2e_ms": e2e_ms, "h_out": h_out, "host_ms": host_ms,
+                "fallbacks": fallbacks / args.steps, "host_plan_ms": host_plan_ms}
 
-    if fused:
+    if multi_ch:
         h2d = flat_t.nbytes + flat_l.nbytes + 4 * (2 * n_q + 1 + n_c)
     else:
         h2d = (n_q + n_c) * sc.dim * 4 + 4 * (3 * n_q + 1 + n_c)
     d2h = n_q * K_TOP * (4 + 4 + 16 + 16)
     peaks, peak_kind = _peaks()
     flops_full = similarity_flops(scenes, qb)
-    if fused:
+    if multi_ch:
         dims = spaces.dims
         flops_full = sum(2.0 * (n_q + n_c) * sc.n * dims[sp] for sp, _ in cq.channels)
 
@@ -642,13 +695,16 @@ def main():
                 "traffic": sim_traffic(args.workload, pname,
                                        [args.tile_variant] if args.tile_variant >= 0
                                        else sorted({d[3] for d in F.farm_sim_tuning(ctx)
-                                                    if d[0] == {"fp32": 0, "fp8": 2}.get(pname, 1)})),
+                                                    if d[0] % 10 == {"fp32": 0, "fp8": 2}.get(pname, 1)})),
                 "kernel": "similarity", "peak_source": note}
 
     def stages(r):
         sm = r["stage_ms"]
         return {"prepare": sm[0] / args.steps, "similarity": sm[1] / args.steps, "select": sm[2] / args.steps,
-                "compose": sm[3] / args.steps, "direct_ms_per_step": r["ms_prof"] / args.steps}
+                "compose": sm[3] / args.steps, "direct_ms_per_step": r["ms_prof"] / args.steps,
+                "host_ms_per_query_batch_call": r["host_ms"],
+                "host_ms_per_step_gpu_idle": r["host_plan_ms"],
+                "exact_fallback_rows_per_step": r["fallbacks"]}
 
     main_r = measure(PREC[args.precision])
     extra_r = {x: measure(PREC[x]) for x in extra}
@@ -665,13 +721,14 @@ def main():
                    "queries": n_q, "constraint_rows": n_c, "top_k": K_TOP,
                    "precision": args.precision, "parallelism": f"replicas{world}",
                    "channels": ([{"space": sp, "dim": spaces.dims[sp], "weight": w} for sp, w in cq.channels]
-                                if fused else 1),
-                   "cuda_graph": graph,
-                   "l2": "inputs larger than L2 (descriptor copies and the similarity block exceed 129 MB)"},
+                                if multi_ch else 1),
+                   "cuda_graph": graph, "fused_selection": args.fused,
+                   "l2": l2_statement(args, scenes, sc.dim, n_q + n_c, multi_ch)},
         "e2e": {"value": job_rate(n_q, world, main_r["e2e_ms"]), "unit": "queries/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "pipelined": not args.e2e_sync},
         "gpu_launches": main_r["launches"],
-        "autotuned_tiles": [{"mode": d[0], "log2_rows": d[1], "log2_objects": d[2],
+        "autotuned_tiles": [{"mode": d[0] % 10, "fused_selection": d[0] >= 10, "log2_rows": d[1], "log2_objects": d[2],
                              "variant": d[3], "tile_n": 128 if d[3] == 1 else 256,
                              "tile_m": 256 if d[3] == 2 else 128, "cta_pair": d[3] == 2}
                             for d in F.farm_sim_tuning(ctx)],
@@ -695,7 +752,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        if fused:
+        if multi_ch:
             base, qs, ref_idx = cpu_baseline_mc(sc, spaces, qb, cq, K_TOP, args.cpu_sample)
         else:
             base, qs, ref_idx = cpu_baseline(scenes, qb, K_TOP, args.cpu_sample)

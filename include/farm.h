@@ -99,6 +99,9 @@ typedef enum {
 /* flags */
 #define FARM_PTR_DEVICE 1u    /* the call's array arguments are device pointers */
 #define FARM_GRAPH 2u         /* farm_query_batch: run the batch's device work as a CUDA graph (see there) */
+#define FARM_UNFUSED 4u       /* farm_query_batch: write the whole similarity block and select from it (see there) */
+#define FARM_ASYNC 8u         /* farm_topk with host outputs: do not synchronise (see there) */
+#define FARM_FUSED 16u        /* farm_query_batch: the fused rank selection also for FARM_PREC_BF16 (see there) */
 
 /*
  * The method's constants.  mu = 5 (reciprocal-rank offset), w = 0.5 (blend
@@ -207,6 +210,17 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
  *              Re-uploading a scene, changing the prefilter weights or growing
  *              a work buffer starts new captures.  At most 8 graphs are kept
  *              (least recently used go).
+ *              FARM_UNFUSED / FARM_FUSED: whether FARM_PREC_FP32 and
+ *              FARM_PREC_BF16 select the ranks from the whole similarity
+ *              block written to memory (as FP8 and the learned path always
+ *              do; the default for BF16) or by the fused selection (the
+ *              default for FP32), which writes only a sample of each
+ *              row (every s-th tile of 256 objects), takes the row's
+ *              threshold from the sample's ranks and has the similarity
+ *              kernel keep only the entries reaching it (rows whose kept
+ *              entries overflow their buffer are recomputed exactly).  Both
+ *              give the same ranks; the defaults are the faster ones measured
+ *              on a 20,000-object scene.
  *   batch_handle  receives the handle that farm_topk takes
  * Only target candidates whose rank r can still place them in the top k_max
  * are scored: a candidate scores at most 1/(mu + r) while k_max objects score
@@ -333,7 +347,12 @@ farm_status farm_associate(farm_ctx *ctx, int64_t n_ent, const float *ent_mu, co
  * 1 <= k <= k_max and k <= n of every scene in the batch.
  * flags: FARM_PTR_DEVICE when the outputs are device pointers (no
  * synchronisation); otherwise the call synchronises and reports device-side
- * input errors.
+ * input errors, unless FARM_ASYNC is given: then the copies into the host
+ * outputs are only enqueued (from pinned memory they overlap the host's next
+ * calls; from pageable memory CUDA copies synchronously anyway), the outputs
+ * are valid after the next farm_sync, which also reports device-side errors,
+ * and a following batch may already be enqueued meanwhile -- its host input
+ * copies then overlap this batch's kernels.
  */
 farm_status farm_topk(farm_ctx *ctx, uint64_t batch_handle, int32_t k, int32_t *out_idx,
                       float *out_score, float *out_pred, int32_t *out_anchor, uint32_t flags);
@@ -342,12 +361,16 @@ farm_status farm_topk(farm_ctx *ctx, uint64_t batch_handle, int32_t k, int32_t *
 farm_status farm_sync(farm_ctx *ctx);
 
 /*
- * Rows that the thresholded rank selection of the tensor-core paths handed
- * to its exact fallback since the context was created (or last reset).  The
- * threshold comes from per-tile maxima of the similarity block; a row whose
- * entries at or above it overflow the candidate buffer (many exact ties, or
- * top-ranked objects crowded into a few 256-object tiles) is selected by a
- * slower exact radix select.  Results are exact either way.  Synchronises the
+ * Rows that the rank selection of the tensor-core paths handed to an exact
+ * fallback since the context was created (or last reset).  The thresholded
+ * select takes its threshold from per-tile maxima of the stored similarity
+ * values; a row whose entries at or above it overflow the candidate buffer
+ * (many exact ties, or top-ranked objects crowded into a few 256-object
+ * tiles) is selected by a slower exact radix select.  The fused selection
+ * takes its threshold from the row's sample; a row whose kept entries
+ * overflow its buffer (a sample unlike the rest of the row, e.g. objects
+ * ordered by class) is recomputed over all objects on the CUDA cores and
+ * selected exactly.  Results are exact either way.  Synchronises the
  * context's stream; reset != 0 zeroes the count afterwards.
  */
 farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t reset);
@@ -363,7 +386,8 @@ farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t rese
  * keeps the fastest for the context.
  *
  * farm_sim_tuning: the decisions so far, up to cap records of four int32:
- * mode (0 = FP32-accurate, 1 = BF16 and the learned prefilter, 2 = FP8),
+ * mode (0 = FP32-accurate, 1 = BF16 and the learned prefilter, 2 = FP8; plus
+ * 10 for batches with the fused selection, whose two launches are timed together),
  * log2 of the rows, log2 of the mean objects per row, chosen variant.
  * *count receives the number of decisions.
  */

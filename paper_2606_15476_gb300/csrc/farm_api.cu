@@ -31,6 +31,14 @@ struct farm_ctx {
     uint8_t *h_blob = nullptr;        // pinned staging of the batch's piece tables and tensor maps
     size_t h_blob_n = 0;
     cudaEvent_t stage_done = nullptr;
+    // host embedding rows of farm_query_batch travel on their own stream into
+    // one of two slots, so that a batch's copy overlaps the previous batch's
+    // kernels: the copy waits until the batch before last is done with the
+    // slot, the ctx stream waits for the copy
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_slot_free[2] = {nullptr, nullptr};
+    int raw_slot = 0;
     // CUDA graphs of batch shapes (FARM_GRAPH), least recently used evicted
     struct GraphEntry { std::vector<int64_t> key; cudaGraphExec_t exec = nullptr; int64_t launches = 0; uint64_t used = 0; };
     std::vector<GraphEntry> graphs;
@@ -376,6 +384,14 @@ farm_status farm_destroy(farm_ctx *ctx)
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->h_blob) cudaFreeHost(ctx->h_blob);
     if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->ev_copied[k]) cudaEventDestroy(ctx->ev_copied[k]);
+        if (ctx->ev_slot_free[k]) cudaEventDestroy(ctx->ev_slot_free[k]);
+    }
     for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
@@ -419,6 +435,11 @@ farm_status farm_create(farm_ctx **out, int device, void *cuda_stream, const far
     if (cudaMalloc(&ctx->d_scenes, kMaxScenes * sizeof(SceneDev)) != cudaSuccess) return bail(FARM_ENOMEM);
     if (cudaMemset(ctx->d_scenes, 0, kMaxScenes * sizeof(SceneDev)) != cudaSuccess) return bail(FARM_ECUDA);
     if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) return bail(FARM_ECUDA);
+    if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(FARM_ECUDA);
+    for (int k = 0; k < 2; ++k)
+        if (cudaEventCreateWithFlags(&ctx->ev_copied[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_slot_free[k], cudaEventDisableTiming) != cudaSuccess)
+            return bail(FARM_ECUDA);
     if (cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return bail(FARM_ECUDA);
     // the static scratch array of farm_rank_rows_noalloc: resolved here, so
@@ -701,12 +722,24 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             CK(ws_get(ctx, farm::B_BSEL_LV, (size_t)std::max<int64_t>(n_c, 1) * cstride_l, &bsel_lv));
         }
     }
-    if (!dev) CK(ws_get(ctx, farm::B_RAW, (size_t)(n_q + n_c) * dim, &d_raw));
+    // host rows: the next of two slots (each half of the buffer)
+    const int raw_slot = ctx->raw_slot;
+    if (!dev) {
+        uint8_t *pipe = nullptr;
+        CK(ws_get(ctx, farm::B_RAW_PIPE, 2 * (size_t)round_up((int64_t)(n_q + n_c) * dim * 4, 256), &pipe));
+        const size_t half = c.ws.bytes[farm::B_RAW_PIPE] / 2 / 256 * 256;
+        d_raw = reinterpret_cast<float *>(pipe + raw_slot * half);
+        ctx->raw_slot ^= 1;
+    }
     if (graph && precision == FARM_PREC_LEARNED) CK(farm::learned_reserve(ctx, rows_total));
+    // on the copy stream once the slot is free again; the ctx stream waits for it
     auto copy_inputs = [&](cudaMemcpyKind kind) -> cudaError_t {
-        cudaError_t e = cudaMemcpyAsync(d_raw, tgt_emb, (size_t)n_q * dim * 4, kind, c.stream);
+        cudaError_t e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_slot_free[raw_slot], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_raw, tgt_emb, (size_t)n_q * dim * 4, kind, ctx->copy_stream);
         if (e == cudaSuccess && n_c > 0)
-            e = cudaMemcpyAsync(d_raw + (size_t)n_q * dim, c_emb, (size_t)n_c * dim * 4, kind, c.stream);
+            e = cudaMemcpyAsync(d_raw + (size_t)n_q * dim, c_emb, (size_t)n_c * dim * 4, kind, ctx->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied[raw_slot], ctx->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c.stream, ctx->ev_copied[raw_slot], 0);
         return e;
     };
 
@@ -725,6 +758,30 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     std::vector<Batch> batches;
     const bool reduced = reduced_precision(precision);
     const bool tile_tops = precision != FARM_PREC_FP32_SIMT;
+    int sim_mode = -1;
+    if (precision == FARM_PREC_FP32) sim_mode = farm::kSimF16x3;
+    else if (precision == FARM_PREC_BF16 || precision == FARM_PREC_LEARNED) sim_mode = farm::kSimBf16;
+    else if (precision == FARM_PREC_FP8) sim_mode = farm::kSimFp8;
+    // the fused selection (tensor-core paths, tiles of 256 objects): each row's
+    // sample -- every fs-th tile -- is stored; the row's threshold is the R-th
+    // largest of its group maxima, and the other tiles keep only the entries
+    // reaching it.  fs sizes the sample so that the kept entries stay well
+    // inside the merge capacity (fuse_merge_capacity: 2,048 words): somewhat
+    // over R fs of them for a list of R
+    // (FP32 and BF16 only: E4M3's few significant bits tie many FP8 entries at
+    // any threshold, and the learned path's lists of 512 would need a sample
+    // of half the row and still crowd the buffer)
+    // The default is the faster configuration measured on the 20,000-object
+    // site: fused for FP32 (the similarity stage gains what the threshold and
+    // merge cost, and S is never written), unfused for BF16 (its lists of 256
+    // make the sample's threshold and the merge cost more than the stores of S)
+    const bool fusable = (precision == FARM_PREC_FP32 || precision == FARM_PREC_BF16) && c.pinned_variant != 1;
+    const bool fused = fusable && !(flags & FARM_UNFUSED) &&
+                       ((flags & FARM_FUSED) || precision == FARM_PREC_FP32);
+    const int32_t keep_max = reduced ? std::max(cstride_t, cstride_l) : std::max(stride_t, stride_l);
+    const int32_t fs = keep_max <= 128 ? 8 : (keep_max <= 256 ? 4 : 2);
+    // the length of a scene's selected rows: its sample's in a fused batch
+    auto sel_len = [&](int64_t n) { return fused ? farm::sample_width(n, fs) : n; };
     int32_t tmp_stride = 4;
     for (const auto &g : groups) {
         const Scene &s = c.scenes[g.sid];
@@ -732,24 +789,28 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
         const int32_t kt = reduced ? reduced_keep_target(p, precision, Rs, s.n) : Rs;
         const int32_t kl = reduced ? reduced_keep_landmark(p, precision, klm, s.n) : klm;
-        if (s.n > farm::kSelectRowMax) tmp_stride = std::max<int32_t>(tmp_stride, (int32_t)round_up(std::max(kt, kl), 4));
+        if (sel_len(s.n) > farm::kSelectRowMax)
+            tmp_stride = std::max<int32_t>(tmp_stride, (int32_t)round_up(std::max(kt, kl), 4));
     }
+    int32_t max_fkeep = 1;
     for (const auto &g : groups) {
         const Scene &s = c.scenes[g.sid];
-        const int64_t ld = round_up(s.n, 32);
+        const int64_t nsel = sel_len(s.n);
+        // fused: the stored sample tiles, compacted
+        const int64_t ld = fused ? farm::col_tiles(s.n, 256, farm::kColSample, fs) * 256 : round_up(s.n, 32);
         const int64_t rows_g = g.nq + g.nc;
         const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
         const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
         const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows_g, (int64_t)(kSimCapBytes / (ld * 4))));
-        const int gshift = farm::group_shift_for(s.n);
-        const int32_t uni = (int32_t)std::min<int64_t>(farm::group_count(s.n, gshift), 8192);
+        const int gshift = farm::group_shift_for(nsel);
+        const int32_t uni = (int32_t)std::min<int64_t>(farm::group_count(nsel, gshift), 8192);
         // long rows of the shared-memory select: column chunks, merged after
-        int32_t chunks = 1, chunk_len = (int32_t)s.n;
+        int32_t chunks = 1, chunk_len = (int32_t)nsel;
         bool global_select = false;
-        if (s.n > farm::kSelectRowMax) {
-            const int64_t c0 = (s.n + farm::kSelectRowMax - 1) / farm::kSelectRowMax;
-            chunk_len = (int32_t)round_up((s.n + c0 - 1) / c0, 32);
-            chunks = (int32_t)((s.n + chunk_len - 1) / chunk_len);
+        if (nsel > farm::kSelectRowMax) {
+            const int64_t c0 = (nsel + farm::kSelectRowMax - 1) / farm::kSelectRowMax;
+            chunk_len = (int32_t)round_up((nsel + c0 - 1) / c0, 32);
+            chunks = (int32_t)((nsel + chunk_len - 1) / chunk_len);
             global_select = (int64_t)chunks * tmp_stride > farm::kSelectRowMax;
         }
         for (int64_t r0 = 0; r0 < rows_g; r0 += chunk) {
@@ -772,12 +833,17 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             pc.t_row0 = g.q0 + r0;
             pc.l_row0 = g.cp0 + r0 + pc.ntr - g.nq;
             pc.rows = (int32_t)nr;
-            pc.n = (int32_t)s.n;
+            pc.n = (int32_t)nsel;
+            pc.n_obj = (int32_t)s.n;
             pc.ld = (int32_t)ld;
             pc.R = Rs;
             pc.klm = klm;
-            pc.keep_t = reduced ? reduced_keep_target(p, precision, Rs, s.n) : Rs;
-            pc.keep_l = reduced ? reduced_keep_landmark(p, precision, klm, s.n) : klm;
+            pc.fkeep_t = reduced ? reduced_keep_target(p, precision, Rs, s.n) : Rs;
+            pc.fkeep_l = reduced ? reduced_keep_landmark(p, precision, klm, s.n) : klm;
+            // the select keeps the whole-row lengths, or, fused, as many of them as the sample holds
+            pc.keep_t = (int32_t)std::min<int64_t>(pc.fkeep_t, nsel);
+            pc.keep_l = (int32_t)std::min<int64_t>(pc.fkeep_l, nsel);
+            max_fkeep = std::max(max_fkeep, std::max(pc.fkeep_t, pc.fkeep_l));
             pc.tmp_off = -1;
             pc.tops_off = -1;
             // rows [0, th0): shared-memory select; rows [th0, rows): thresholded select
@@ -786,10 +852,10 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             if (tile_tops) {
                 // a row goes to the thresholded select when its group maxima
                 // number at least its list length, or it is short enough to sort whole
-                const bool small = s.n <= farm::kSelectSortAll;
+                const bool small = nsel <= farm::kSelectSortAll;
                 pc.th0 = (small || uni >= pc.keep_t) ? 0 : (uni >= pc.keep_l ? pc.ntr : pc.rows);
                 pc.tops_off = bt.tops;
-                bt.tops += nr * farm::group_stride(s.n, gshift);
+                bt.tops += nr * farm::group_stride(nsel, gshift);
                 if (pc.th0 < pc.rows) {
                     bt.tblocks += pc.rows - pc.th0;
                     bt.max_union = std::max(bt.max_union, uni);
@@ -836,12 +902,27 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         CK(ws_get(ctx, farm::B_CHUNK_IDX, (size_t)tmp_need, &tmp_idx));
         CK(ws_get(ctx, farm::B_CHUNK_VAL, (size_t)tmp_need, &tmp_val));
     }
-    // tensor-core similarity: one grouped launch per batch over its pieces;
-    // each scene's two B tensor maps are encoded once per call
-    int sim_mode = -1;
-    if (precision == FARM_PREC_FP32) sim_mode = farm::kSimF16x3;
-    else if (precision == FARM_PREC_BF16 || precision == FARM_PREC_LEARNED) sim_mode = farm::kSimBf16;
-    else if (precision == FARM_PREC_FP8) sim_mode = farm::kSimFp8;
+    // the fused selection's buffers (per operand row) and the landmark list values it ranks by
+    farm::FuseEmit emit{};
+    int32_t *d_ovf = nullptr;
+    float *d_slab = nullptr, *lsel_cos = nullptr;
+    if (fused) {
+        emit.cap = farm::fuse_merge_capacity(max_fkeep);
+        CK(ws_get(ctx, farm::B_FUSE_TAU, (size_t)rows_total, &emit.tau_key));
+        CK(ws_get(ctx, farm::B_FUSE_CNT, (size_t)rows_total, &emit.cnt));
+        CK(ws_get(ctx, farm::B_FUSE_CAND, (size_t)rows_total * emit.cap, &emit.cand));
+        CK(ws_get(ctx, farm::B_FUSE_OVF, (size_t)rows_total + 1, &d_ovf));
+        CK(ws_get(ctx, farm::B_FUSE_SLAB, (size_t)farm::kFuseFallbackBlocks * round_up(max_n, 4), &d_slab));
+        if (!reduced) CK(ws_get(ctx, farm::B_LSEL_COS, (size_t)std::max<int64_t>(n_c, 1) * stride_l, &lsel_cos));
+        if (precision == FARM_PREC_LEARNED) {
+            // the sample lists' values give the thresholds
+            CK(ws_get(ctx, farm::B_BSEL_TV, (size_t)n_q * cstride_t, &bsel_tv));
+            CK(ws_get(ctx, farm::B_BSEL_LV, (size_t)std::max<int64_t>(n_c, 1) * cstride_l, &bsel_lv));
+        }
+    }
+    // tensor-core similarity: one grouped launch per batch over its pieces
+    // (fused: two, the sample tiles and the others); each scene's two B
+    // tensor maps are encoded once per call
     if (sim_mode >= 0 && !farm::sim_tc_available())
         return fail(ctx, FARM_EINVAL, "the tensor-core similarity path is not built");
     std::vector<int32_t> map_of_scene;
@@ -866,14 +947,15 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         double wn = 0.0;
         for (const auto &g : groups) wn += (double)(g.nq + g.nc) * (double)c.scenes[g.sid].n;
         auto log2i = [](int64_t x) { int b = 0; while (b < 62 && (int64_t(1) << (b + 1)) <= x) ++b; return b; };
-        tune_key = (int64_t)sim_mode * 10000 + log2i(rows_total) * 100 + log2i((int64_t)(wn / (double)rows_total));
+        tune_key = (fused ? 100000 : 0) + (int64_t)sim_mode * 10000 + log2i(rows_total) * 100 +
+                   log2i((int64_t)(wn / (double)rows_total));
         auto it = c.tuned.find(tune_key);
         if (c.pinned_variant >= 0) {
             vlist = {c.pinned_variant};
         } else if (it != c.tuned.end()) {
             vlist = {it->second};
         } else {
-            vlist = {0, 1, 2};
+            vlist = fused ? std::vector<int>{0, 2} : std::vector<int>{0, 1, 2};     // fused: tiles of 256 objects
             graph = false;
         }
     }
@@ -881,7 +963,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     // device blob: select pieces | GEMM pieces, one table per variant | tensor maps (128-byte aligned sections)
     const size_t off_gp = round_up((int64_t)(pieces.size() * sizeof(farm::Piece)), 128);
     const size_t gp_table = round_up((int64_t)(pieces.size() * sizeof(farm::GemmPiece)), 128);
-    const size_t off_maps = off_gp + nv * gp_table;
+    const int n_tables = fused ? 2 : 1;        // fused: the sample tiles' table, then the others'
+    const size_t off_maps = off_gp + nv * n_tables * gp_table;
     const size_t blob_bytes = off_maps + map_scenes.size() * nv * 2 * farm::kTensorMapBytes;
     uint8_t *d_blob;
     CK(ws_get(ctx, farm::B_PIECES, blob_bytes, &d_blob));
@@ -894,32 +977,40 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     }
     farm::Piece *d_pieces = reinterpret_cast<farm::Piece *>(d_blob);
     std::memcpy(ctx->h_blob, pieces.data(), pieces.size() * sizeof(farm::Piece));
-    std::vector<int64_t> batch_tiles(batches.size() * nv, 0);
+    // tiles of batch b, variant vi, table t at batch_tiles[(b * nv + vi) * n_tables + t]
+    std::vector<int64_t> batch_tiles(batches.size() * nv * n_tables, 0);
+    auto gp_base = [&](int vi, int t) { return off_gp + (size_t)(vi * n_tables + t) * gp_table; };
     if (sim_mode >= 0) {
         for (int vi = 0; vi < nv; ++vi) {
-            farm::GemmPiece *hg = reinterpret_cast<farm::GemmPiece *>(ctx->h_blob + off_gp + vi * gp_table);
-            for (size_t b = 0; b < batches.size(); ++b) {
-                int64_t tiles = 0;
-                for (size_t k = batches[b].p0; k < batches[b].p0 + batches[b].np; ++k) {
-                    const farm::Piece &pc = pieces[k];
-                    const Scene &sc = c.scenes[piece_sid[k]];
-                    farm::GemmPiece gp{};
-                    gp.q_row0 = pc.q_row0;
-                    gp.s_off = pc.s_off;
-                    gp.tops_off = tile_tops ? pc.tops_off : -1;
-                    gp.scale_d = sim_mode == farm::kSimFp8 ? sc.desc_scale : nullptr;
-                    gp.bmap = d_blob + off_maps +
-                              ((size_t)map_of_scene[piece_sid[k]] * nv + vi) * 2 * farm::kTensorMapBytes;
-                    gp.rows = pc.rows;
-                    gp.n = pc.n;
-                    gp.ld = pc.ld;
-                    gp.tile_begin = (int32_t)tiles;
-                    gp.gshift = pc.gshift;
-                    tiles += farm::sim_cluster_tiles(pc.rows, pc.n, vlist[vi]);
-                    hg[k] = gp;
+            for (int t = 0; t < n_tables; ++t) {
+                const int mode = !fused ? farm::kColAll : (t == 0 ? farm::kColSample : farm::kColRest);
+                farm::GemmPiece *hg = reinterpret_cast<farm::GemmPiece *>(ctx->h_blob + gp_base(vi, t));
+                for (size_t b = 0; b < batches.size(); ++b) {
+                    int64_t tiles = 0;
+                    for (size_t k = batches[b].p0; k < batches[b].p0 + batches[b].np; ++k) {
+                        const farm::Piece &pc = pieces[k];
+                        const Scene &sc = c.scenes[piece_sid[k]];
+                        farm::GemmPiece gp{};
+                        gp.q_row0 = pc.q_row0;
+                        gp.s_off = mode == farm::kColRest ? 0 : pc.s_off;
+                        gp.tops_off = (tile_tops && mode != farm::kColRest) ? pc.tops_off : -1;
+                        gp.scale_d = sim_mode == farm::kSimFp8 ? sc.desc_scale : nullptr;
+                        gp.bmap = d_blob + off_maps +
+                                  ((size_t)map_of_scene[piece_sid[k]] * nv + vi) * 2 * farm::kTensorMapBytes;
+                        gp.rows = pc.rows;
+                        gp.n = pc.n_obj;
+                        gp.ld = pc.ld;
+                        gp.tile_begin = (int32_t)tiles;
+                        gp.gshift = pc.gshift;
+                        gp.col_mode = mode;
+                        gp.col_stride = fused ? fs : 0;
+                        gp.n_store = mode == farm::kColRest ? 0 : pc.n;
+                        tiles += farm::sim_cluster_tiles(pc.rows, pc.n_obj, vlist[vi], mode, fs);
+                        hg[k] = gp;
+                    }
+                    if (tiles > 0x7fffffffLL) return fail(ctx, FARM_EINVAL, "similarity batch exceeds 2^31 tiles");
+                    batch_tiles[((size_t)b * nv + vi) * n_tables + t] = tiles;
                 }
-                if (tiles > 0x7fffffffLL) return fail(ctx, FARM_EINVAL, "similarity batch exceeds 2^31 tiles");
-                batch_tiles[b * nv + vi] = tiles;
             }
         }
         for (size_t m = 0; m < map_scenes.size(); ++m) {
@@ -971,37 +1062,46 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
 
         // ---- stages 1-2: similarity per piece, then the batch's rank selection
         int32_t *sel_ti = reduced ? bsel_t : tsel_idx, *sel_li = reduced ? bsel_l : lsel_idx;
-        float *sel_tc = reduced ? bsel_tv : tsel_cos, *sel_lc = reduced ? bsel_lv : nullptr;
+        float *sel_tc = reduced ? bsel_tv : tsel_cos, *sel_lc = reduced ? bsel_lv : lsel_cos;
         const int32_t sel_st = reduced ? cstride_t : stride_t, sel_sl = reduced ? cstride_l : stride_l;
         int vsel = nv == 1 ? 0 : -1;     // index into vlist of the variant in use
         for (size_t b = 0; b < batches.size(); ++b) {
             const Batch &bt = batches[b];
             const int m1 = mark_begin(ctx, 1);
+            const void *q0 = nullptr, *q1 = nullptr;
+            int32_t kdim = dim_pad;
+            if (precision == FARM_PREC_FP32) { q0 = ops.qhi; q1 = ops.qlo; }
+            else if (precision == FARM_PREC_BF16) q0 = ops.qbf;
+            else if (precision == FARM_PREC_LEARNED) { q0 = ops.qcomp; kdim = c.mlp.P; }
+            else q0 = ops.qf8;
+            // table t of variant vi (fused: 0 the sample tiles, 1 the others, appending to the rows' buffers)
+            auto launch_variant = [&](int vi, int t) {
+                return farm::launch_sim_tc_grouped(
+                    sim_mode, vlist[vi], q0, q1, rows_total, kdim,
+                    reinterpret_cast<farm::GemmPiece *>(d_blob + gp_base(vi, t)) + bt.p0, (int32_t)bt.np,
+                    batch_tiles[((size_t)b * nv + vi) * n_tables + t], d_sim, tile_tops ? d_tops : nullptr,
+                    precision == FARM_PREC_FP8 ? ops.qscale : nullptr, c.num_sms, c.d_err, c.stream,
+                    t == 1 ? &emit : nullptr);
+            };
             if (sim_mode >= 0) {
-                const void *q0, *q1 = nullptr;
-                int32_t kdim = dim_pad;
-                if (precision == FARM_PREC_FP32) { q0 = ops.qhi; q1 = ops.qlo; }
-                else if (precision == FARM_PREC_BF16) q0 = ops.qbf;
-                else if (precision == FARM_PREC_LEARNED) { q0 = ops.qcomp; kdim = c.mlp.P; }
-                else q0 = ops.qf8;
-                auto launch_variant = [&](int vi) {
-                    return farm::launch_sim_tc_grouped(
-                        sim_mode, vlist[vi], q0, q1, rows_total, kdim,
-                        reinterpret_cast<farm::GemmPiece *>(d_blob + off_gp + vi * gp_table) + bt.p0, (int32_t)bt.np,
-                        batch_tiles[b * nv + vi], d_sim, tile_tops ? d_tops : nullptr,
-                        precision == FARM_PREC_FP8 ? ops.qscale : nullptr, c.num_sms, c.d_err, c.stream);
-                };
                 if (vsel < 0) {
-                    // autotune: every variant twice, the second run timed; all
-                    // write the same results, so the last run's output stands
+                    // autotune: every variant twice, the second run timed (fused:
+                    // both launches, the second with no threshold reached, so
+                    // that it appends nothing); the sample tiles' values are
+                    // the same whichever variant stores them last
                     cudaEvent_t e0, e1;
                     CK(cudaEventCreate(&e0));
                     CK(cudaEventCreate(&e1));
+                    if (fused) {
+                        CK(cudaMemsetAsync(emit.tau_key, 0xff, (size_t)rows_total * 4, c.stream));
+                        CK(cudaMemsetAsync(emit.cnt, 0, (size_t)rows_total * 4, c.stream));
+                    }
                     float best_ms = 0.f;
                     for (int vi = 0; vi < nv; ++vi) {
-                        LAUNCH(launch_variant(vi));
-                        CK(cudaEventRecord(e0, c.stream));
-                        LAUNCH(launch_variant(vi));
+                        for (int rep = 0; rep < 2; ++rep) {
+                            if (rep == 1) CK(cudaEventRecord(e0, c.stream));
+                            for (int t = 0; t < n_tables; ++t) LAUNCH(launch_variant(vi, t));
+                        }
                         CK(cudaEventRecord(e1, c.stream));
                         CK(cudaEventSynchronize(e1));
                         float ms = 0.f;
@@ -1015,9 +1115,9 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                     cudaEventDestroy(e1);
                     c.tuned[tune_key] = vlist[vsel];
                     // the batch's results come from the chosen variant, as every later batch's will
-                    if (vsel != nv - 1) LAUNCH(launch_variant(vsel));
+                    if (fused || vsel != nv - 1) LAUNCH(launch_variant(vsel, 0));
                 } else {
-                    LAUNCH(launch_variant(vsel));
+                    LAUNCH(launch_variant(vsel, 0));
                 }
             } else {
                 for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
@@ -1030,31 +1130,57 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             mark_end(ctx, m1);
             const int m2 = mark_begin(ctx, 2);
             const farm::Piece *dp = d_pieces + bt.p0;
-            if (bt.blocks > 0)
+            if (fused) {
+                // each row's threshold from its sample's group maxima; the sample's entries reaching it
+                LAUNCH(farm::launch_fuse_sample_tau(d_sim, d_tops, dp, (int32_t)bt.np, bt.rows, fs, emit, c.stream));
+            }
+            if (!fused && bt.blocks > 0)
                 LAUNCH(farm::launch_select_grouped(d_sim, dp, (int32_t)bt.np, bt.blocks, bt.smem_sel, sel_ti, sel_tc,
                                                    sel_st, sel_li, sel_lc, sel_sl, tmp_idx, tmp_val, tmp_stride,
                                                    c.stream));
-            if (bt.chunked)
+            if (!fused && bt.chunked)
                 LAUNCH(farm::launch_merge_chunks(dp, (int32_t)bt.np, bt.rows, bt.smem_merge, tmp_idx, tmp_val, tmp_stride,
                                                  sel_ti, sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.stream));
-            if (bt.tblocks > 0)
+            if (!fused && bt.tblocks > 0)
                 LAUNCH(farm::launch_select_thresh(d_sim, d_tops, dp, (int32_t)bt.np, bt.tblocks, bt.max_union, sel_ti,
                                                   sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.d_fallback, d_rowlist,
                                                   c.stream));
-            for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
+            for (size_t k = bt.p0; k < bt.p0 + bt.np && !fused; ++k) {
                 const farm::Piece &pc = pieces[k];
                 if (pc.chunks != 0 || pc.th0 == 0) continue;
                 LAUNCH(farm::launch_select_rows_ex(d_sim + pc.s_off, pc.ld, pc.n, pc.th0, pc.ntr, pc.keep_t, pc.keep_l,
                                                    sel_ti, sel_tc, pc.t_row0, sel_st, sel_li, sel_lc, pc.l_row0, sel_sl,
                                                    c.stream));
             }
+            if (fused) {
+                // the other tiles append what reaches the thresholds; the merge, and
+                // the exact recomputation of rows whose candidates overflowed
+                mark_end(ctx, m2);
+                const int m1b = mark_begin(ctx, 1);
+                CK(cudaMemsetAsync(d_ovf, 0, sizeof(int32_t), c.stream));
+                LAUNCH(launch_variant(vsel, 1));
+                mark_end(ctx, m1b);
+                const int m2b = mark_begin(ctx, 2);
+                LAUNCH(farm::launch_fuse_final(dp, (int32_t)bt.np, bt.rows, sel_ti, sel_tc, sel_st, sel_li, sel_lc,
+                                               sel_sl, emit, d_ovf, d_ovf + 1, max_fkeep, c.stream));
+                LAUNCH(farm::launch_fuse_fallback(dp, (int32_t)bt.np, d_ovf, d_ovf + 1,
+                                                  precision == FARM_PREC_FP32 ? nullptr : ops.q32, ops.qhi, ops.qlo,
+                                                  dim_pad, sel_ti, sel_tc, sel_st, sel_li, sel_lc, sel_sl, d_slab,
+                                                  round_up(max_n, 4), farm::kFuseFallbackBlocks, c.d_fallback,
+                                                  c.stream));
+                mark_end(ctx, m2b);
+            }
+            const int m2c = fused ? mark_begin(ctx, 2) : -1;
             if (reduced) {
                 const float band = precision == FARM_PREC_FP8 ? 16.f * p.rescore_band : p.rescore_band;
-                LAUNCH(farm::launch_rescore_grouped(dp, (int32_t)bt.np, bt.rows, ops.q32, dim_pad, bsel_t, bsel_tv,
-                                                    cstride_t, bsel_l, bsel_lv, cstride_l, band, tsel_idx, tsel_cos,
-                                                    stride_t, lsel_idx, stride_l, c.stream));
+                // (the learned path's list values are compressed-space scores: no band)
+                LAUNCH(farm::launch_rescore_grouped(dp, (int32_t)bt.np, bt.rows, ops.q32, dim_pad, bsel_t,
+                                                    precision == FARM_PREC_LEARNED ? nullptr : bsel_tv, cstride_t,
+                                                    bsel_l, precision == FARM_PREC_LEARNED ? nullptr : bsel_lv,
+                                                    cstride_l, band, tsel_idx, tsel_cos, stride_t, lsel_idx, stride_l,
+                                                    c.stream));
             }
-            mark_end(ctx, m2);
+            mark_end(ctx, fused ? m2c : m2);
         }
 
         // ---- stage 3: relations, composite, sort
@@ -1083,7 +1209,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     } else {
         // the batch's shape: everything that fixes the launch sequence and its
         // arguments (device inputs are read where the caller keeps them)
-        std::vector<int64_t> key = {precision, n_q, n_c, dim, (int64_t)c.ws_gen, (int64_t)c.scene_gen,
+        std::vector<int64_t> key = {precision, (int64_t)fused, n_q, n_c, dim, (int64_t)c.ws_gen, (int64_t)c.scene_gen,
                                     (int64_t)c.mlp.version, (int64_t)(intptr_t)src_t, (int64_t)(intptr_t)src_c,
                                     (int64_t)groups.size()};
         for (const auto &g : groups) {
@@ -1131,6 +1257,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         CK(cudaGraphLaunch(hit->exec, c.stream));
         c.launches += hit->launches;
     }
+    if (!dev) CK(cudaEventRecord(ctx->ev_slot_free[raw_slot], c.stream));   // the batch is done with its slot
 
     c.batch_gen += 1;
     c.batch_valid = true;
@@ -1360,6 +1487,9 @@ farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, i
         pc.ld = (int32_t)ld;
         pc.keep_t = Rt;
         pc.keep_l = Rl;
+        pc.fkeep_t = Rt;
+        pc.fkeep_l = Rl;
+        pc.n_obj = (int32_t)n;
         pc.R = Rt;
         pc.klm = Rl;
         pc.chunks = 1;
@@ -1503,6 +1633,7 @@ farm_status farm_topk(farm_ctx *ctx, uint64_t batch_handle, int32_t k, int32_t *
     CK(cudaMemcpyAsync(out_score, s_score, (size_t)n_q * k * 4, cudaMemcpyDeviceToHost, c.stream));
     if (out_pred) CK(cudaMemcpyAsync(out_pred, s_t, (size_t)n_q * k * 16, cudaMemcpyDeviceToHost, c.stream));
     if (out_anchor) CK(cudaMemcpyAsync(out_anchor, s_anc, (size_t)n_q * k * 16, cudaMemcpyDeviceToHost, c.stream));
+    if (flags & FARM_ASYNC) return FARM_OK;      // valid after the next farm_sync
     return check_device_errors(ctx);
 }
 
@@ -1588,7 +1719,7 @@ farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_
     int32_t i = 0;
     for (const auto &kv : ctx->c.tuned) {
         if (i < cap) {
-            entries[4 * i + 0] = (int32_t)(kv.first / 10000);
+            entries[4 * i + 0] = (int32_t)(kv.first / 10000 % 10) + (kv.first >= 100000 ? 10 : 0);
             entries[4 * i + 1] = (int32_t)(kv.first / 100 % 100);
             entries[4 * i + 2] = (int32_t)(kv.first % 100);
             entries[4 * i + 3] = kv.second;
@@ -1665,6 +1796,9 @@ farm_status farm_similarity_variant(farm_ctx *ctx, int32_t scene_id, int64_t n_r
     gp.ld = (int32_t)ld;
     gp.tile_begin = 0;
     gp.gshift = farm::group_shift_for(s.n);
+    gp.col_mode = farm::kColAll;
+    gp.col_stride = 0;
+    gp.n_store = (int32_t)s.n;
     std::memcpy(hb, &gp, sizeof(gp));
     CK(cudaMemcpyAsync(d_blob, hb, 128 + 2 * farm::kTensorMapBytes, cudaMemcpyHostToDevice, c.stream));
     const void *q0 = mode == farm::kSimF16x3 ? (const void *)ops.qhi : (mode == farm::kSimBf16 ? (const void *)ops.qbf : (const void *)ops.qf8);

@@ -109,6 +109,13 @@ enum Buf {
     B_MC_FUSED,     // float [n_q, RF] fused scores of the kept target candidates
     B_SELLIST,      // int32 [1 + rows] rows the warp-level select hands to the block-level one
     B_ASSOC,        // farm_associate: its inputs' copies, operand rows, similarity block and scratch
+    B_LSEL_COS,     // float [n_c, k_lm] landmark list values (fused selection)
+    B_FUSE_TAU,     // uint32 [rows] per operand row: the fused selection's threshold key
+    B_FUSE_CNT,     // int32 [rows] its appended candidate count
+    B_FUSE_CAND,    // uint64 [rows, cap] its candidate words
+    B_FUSE_OVF,     // int32 [1 + rows] rows whose candidates overflowed (count, then launch rows)
+    B_FUSE_SLAB,    // float [blocks, n] the exact fallback's similarity rows
+    B_RAW_PIPE,     // farm_query_batch's host rows: two slots, each [n_q + n_c, dim] (copy stream)
     B_COUNT
 };
 
@@ -283,6 +290,35 @@ inline int group_shift_for(int64_t n) { return n < kSmallScene ? kGroupShiftSmal
 // Rows of at most this many objects may be selected by sorting every entry.
 constexpr int kSelectSortAll = 2048;
 
+// Column tiles of a similarity launch.  kColAll: every tile of the row.
+// With a sampling stride s (in tiles of 256 objects):
+//   kColSample: the sample tiles 0, s, 2s, ...; the block stores its values
+//     compacted (the j-th sample tile at columns [256 j, 256 j + 256)), so a
+//     row holds sample_width(n, s) valid entries;
+//   kColRest:   every other tile; values are not stored but compared with the
+//     row's threshold, and those reaching it are appended to the row's
+//     candidate buffer (the fused rank selection).
+enum ColMode { kColAll = 0, kColSample = 1, kColRest = 2 };
+__host__ __device__ inline int64_t col_tiles(int64_t n, int bn, int mode, int s)
+{
+    const int64_t nt = (n + bn - 1) / bn;
+    if (mode == kColAll) return nt;
+    const int64_t ns = (nt + s - 1) / s;
+    return mode == kColSample ? ns : nt - ns;
+}
+// The object tile of the launch's j-th column tile of a block.
+__host__ __device__ inline int64_t col_tile_of(int64_t j, int mode, int s)
+{
+    return mode == kColAll ? j : (mode == kColSample ? j * s : j + j / (s - 1) + 1);
+}
+// Valid entries of a sample row: full sample tiles, then the last one, which may be the row's ragged tail.
+__host__ __device__ inline int64_t sample_width(int64_t n, int s)
+{
+    const int64_t ns = col_tiles(n, 256, kColSample, s);
+    const int64_t last = (ns - 1) * s * 256;
+    return (ns - 1) * 256 + (n - last < 256 ? n - last : 256);
+}
+
 // One block of query rows against one scene in a grouped similarity launch.
 struct GemmPiece {
     int64_t q_row0;          // first row of the block in the operand arrays
@@ -292,18 +328,32 @@ struct GemmPiece {
     const void *bmap;        // the scene's two B tensor maps (device memory, 64-byte aligned)
     int32_t rows, n, ld;     // rows of the block, objects, leading dimension of S
     int32_t tile_begin;      // first cluster tile of the block in the launch
-    int32_t gshift;          // group maxima over 2^gshift objects
-    int32_t pad;
+    int32_t gshift;          // group maxima over 2^gshift objects (of the stored columns)
+    int32_t col_mode;        // ColMode
+    int32_t col_stride;      // sampling stride s (kColSample / kColRest)
+    int32_t n_store;         // valid stored columns: n, or sample_width(n, s) for kColSample
 };
 constexpr size_t kTensorMapBytes = 128;
 
-// Cluster tiles of one block of `rows` rows against `n` objects in a variant.
-inline int64_t sim_cluster_tiles(int64_t rows, int64_t n, int variant)
+// Cluster tiles of one block of `rows` rows against `n` objects in a variant
+// (column mode and sampling stride as GemmPiece).
+inline int64_t sim_cluster_tiles(int64_t rows, int64_t n, int variant, int mode = kColAll, int s = 0)
 {
     const int64_t bn = sim_variant_bn(variant), cm = sim_variant_cluster(variant);
     const int64_t mt = (rows + kSimTileM - 1) / kSimTileM;
-    return (mt + cm - 1) / cm * ((n + bn - 1) / bn);
+    return (mt + cm - 1) / cm * col_tiles(n, (int)bn, mode, s);
 }
+
+// The fused rank selection's outputs of a kColRest launch, indexed by operand
+// row: each row's threshold (order-preserving key of its sample's R-th
+// value), candidate count and buffer of `cap` candidate words
+// (key << 32 | (2^32 - 1 - object index)).
+struct FuseEmit {
+    uint32_t *tau_key;
+    int32_t *cnt;
+    uint64_t *cand;
+    int32_t cap;
+};
 
 // The two B tensor maps (hi / lo, or the one operand twice) of a scene's
 // descriptor operand in `mode` for `variant`, written to host memory `out`
@@ -316,10 +366,12 @@ bool sim_tc_encode_b(int mode, int variant, void *out, const void *d0, const voi
 // ([rows_total, dim_pad] in the mode's element type) and FP8 row scales
 // scale_q.  S and tops are the bases the pieces' offsets refer to (tops
 // nullable).
+// With `emit` (its pieces in kColRest mode, variants 0 and 2 only) the
+// values are appended to the rows' candidate buffers instead of stored.
 cudaError_t launch_sim_tc_grouped(int mode, int variant, const void *q0, const void *q1, int64_t rows_total,
                                   int32_t dim_pad, const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles,
                                   float *S, float *tops, const float *scale_q, int num_sms, int32_t *err,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const FuseEmit *emit = nullptr);
 
 // One problem (rows x n, S leading dimension ld_s, group maxima at tops with
 // group_stride(n) floats per row, nullable) on the tensor cores, variant 2 (CTA pairs).
@@ -384,6 +436,8 @@ struct Piece {
     int32_t chunks, chunk_len;
     int32_t th0;
     int32_t gshift;         // group maxima over 2^gshift objects (thresholded select)
+    int32_t fkeep_t, fkeep_l; // fused selection: list lengths over the whole row (keep_t / keep_l: over its sample)
+    int32_t n_obj;          // objects of the scene (n: the selected row length, its sample's in a fused batch)
 };
 
 // Grouped select over `pieces` (device; n_pieces entries) in one launch of
@@ -418,6 +472,40 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
                                  int64_t total_blocks, int32_t max_union, int32_t *tsel_idx, float *tsel_cos,
                                  int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
                                  int32_t *n_fallback, int32_t *row_list, cudaStream_t s);
+// The fused rank selection (k_fuse_select.cu) over the launch rows of
+// `pieces`, whose sample rows (sampling stride s) the similarity kernel
+// stored at S with their group maxima at tops (each piece's n, ld, s_off,
+// tops_off and gshift describe the sample rows): sample_tau sets each row's
+// threshold in `emit` (the R-th largest group maximum of its sample, R =
+// fkeep) and appends the sample's entries reaching it; after the similarity
+// kernel appended the other tiles' entries, fuse_final writes each row's
+// final list of fkeep_t / fkeep_l entries from its buffer and records rows
+// whose candidates overflowed (count in *n_overflow, launch rows in overflow_rows).
+cudaError_t launch_fuse_sample_tau(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,
+                                   int64_t total_rows, int32_t s, const FuseEmit &emit, cudaStream_t st);
+cudaError_t launch_fuse_final(const Piece *pieces, int32_t n_pieces, int64_t total_rows, int32_t *tsel_idx,
+                              float *tsel_cos, int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
+                              const FuseEmit &emit, int32_t *n_overflow, int32_t *overflow_rows, int32_t max_keep,
+                              cudaStream_t st);
+
+// The exact fallback of the fused selection for the rows fuse_final recorded
+// (*n_overflow of them, launch rows in overflow_rows): a grid-stride loop of
+// blocks, each computing a row's FP32 cosines against all n_obj objects on
+// the CUDA cores (unit row from q32, or from the FP16 split q_hi + 2^-11 q_lo
+// when q32 is null) into its slab of `slab` (slab_ld floats per block, >= the
+// longest n_obj) and selecting the row's fkeep best exactly into its list.
+// The number of such rows is added to *n_fallback (nullable).
+cudaError_t launch_fuse_fallback(const Piece *pieces, int32_t n_pieces, const int32_t *n_overflow,
+                                 const int32_t *overflow_rows, const float *q32, const uint16_t *q_hi,
+                                 const uint16_t *q_lo, int32_t dim_pad, int32_t *tsel_idx, float *tsel_cos,
+                                 int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l, float *slab,
+                                 int64_t slab_ld, int32_t blocks, int32_t *n_fallback, cudaStream_t st);
+constexpr int kFuseFallbackBlocks = 64;
+
+// The words a row can merge when no list is longer than max_keep; a row
+// with more candidates is recomputed by the fallback.  Use it as FuseEmit::cap.
+int fuse_merge_capacity(int32_t max_keep);
+
 // Grouped FP32 rescore (one block per launch row): the keep_t / keep_l
 // candidates of bsel_* (strides cstride_t / cstride_l; descending by their
 // reduced-precision values bsel_tv / bsel_lv, nullable) are re-scored with

@@ -18,8 +18,9 @@
 // segmented shuffle reduction, or 64-bit shared-memory atomics).  Because the
 // composite is non-decreasing in every t_i and the anchors only meet at the
 // target, the best binding takes each anchor's best witness on its own (the
-// star decomposition of App. B).  The CTA then sorts the scored candidates by
-// (s descending, object index ascending) so that any TopK is a prefix.
+// star decomposition of App. B).  The CTA then orders the scored candidates by
+// (s descending, object index ascending), each one's position counted against
+// the others, and writes the first k_max, so that any TopK is a prefix.
 #include "farm_internal.h"
 
 namespace farm {
@@ -276,16 +277,16 @@ __device__ __forceinline__ float relation(int pred, int32_t e, int ce, float ex,
 constexpr int WARPS = TH / 32;
 
 // Shared-memory layout of one query, sized by the batch's longest target list
-// RM (sorted as PM, the next power of two), landmark list KM and Closest /
+// RM, landmark list KM and Closest /
 // Farthest set KC; every section starts on a 16-byte boundary.
 struct ComposeSmem {
-    size_t best, key, lm_pos, lm_size, cset_pos, lm_idx, cand_e, ssem, surv, slot, bytes;
+    size_t best, key, lm_pos, lm_size, cset_pos, lm_idx, cand_e, ssem, surv, bytes;
     __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
-    __host__ __device__ ComposeSmem(int RM, int PM, int KM, int KC)
+    __host__ __device__ ComposeSmem(int RM, int KM, int KC)
     {
         size_t o = 0;
         best = o;   o = up16(o + (size_t)RM * FARM_MAX_CONSTRAINTS * 8);
-        key = o;    o = up16(o + (size_t)PM * 8);
+        key = o;    o = up16(o + (size_t)RM * 8);
         lm_pos = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
         lm_size = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
         cset_pos = o; o = up16(o + (size_t)KC * 3 * 4);
@@ -293,17 +294,16 @@ struct ComposeSmem {
         cand_e = o; o = up16(o + (size_t)RM * 4);
         ssem = o;   o = up16(o + (size_t)RM * 4);
         surv = o;   o = up16(o + (size_t)RM * 2);
-        slot = o;   o = up16(o + (size_t)PM * 2);
         bytes = o;
     }
 };
 
 __global__ void __launch_bounds__(TH, 8)
-compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
+compose_kernel(ComposeArgs a, int32_t KC)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     const int RM = a.stride_t, KM = a.stride_l;
-    const ComposeSmem L(RM, PM, KM, KC);
+    const ComposeSmem L(RM, KM, KC);
     unsigned long long *best = reinterpret_cast<unsigned long long *>(sm + L.best);   // [RM][4]
     uint64_t *key = reinterpret_cast<uint64_t *>(sm + L.key);
     float *lm_pos = reinterpret_cast<float *>(sm + L.lm_pos);                         // [4][KM][3]
@@ -313,7 +313,6 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
     int32_t *cand_e = reinterpret_cast<int32_t *>(sm + L.cand_e);
     float *ssem = reinterpret_cast<float *>(sm + L.ssem);
     uint16_t *surv = reinterpret_cast<uint16_t *>(sm + L.surv);
-    uint16_t *slot = reinterpret_cast<uint16_t *>(sm + L.slot);
     __shared__ float s_thr;
     __shared__ int s_ns;
 
@@ -492,50 +491,34 @@ compose_kernel(ComposeArgs a, int32_t PM, int32_t KC)
         else g = sqrtf(sqrtf(t[0] * t[1]) * sqrtf(t[2] * t[3]));
         const float s = ssem[c] * ((1.f - p.w) + p.w * g);
         key[pos] = ((uint64_t)order_key(s) << 32) | (uint64_t)(0xffffffffu - (uint32_t)cand_e[c]);
-        slot[pos] = (uint16_t)pos;
     }
-    int P = 1;
-    while (P < ns) P <<= 1;
-    for (int c = ns + tid; c < P; c += TH) { key[c] = 0ull; slot[c] = 0; }
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < P; i += TH) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t x = key[i], y = key[ixj];
-                    const bool desc = (i & k) == 0;
-                    if (desc ? (x < y) : (x > y)) {
-                        key[i] = y; key[ixj] = x;
-                        const uint16_t u = slot[i]; slot[i] = slot[ixj]; slot[ixj] = u;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // only a TopK prefix of at most k_max entries is ever read
+    // the scored candidates in (s desc, object index asc) order are the key
+    // order, all keys distinct: each one's position is the number of larger
+    // keys; only a TopK prefix of at most k_max entries is ever read
     const int64_t ob = q * a.stride_t;
     const int n_out = min(a.stride_t, max(p.k_max, 1));
-    for (int c = tid; c < n_out; c += TH) {
-        if (c < ns) {
-            const int pos = slot[c];
-            const uint32_t kk = (uint32_t)(key[c] >> 32);
-            const uint32_t u = (kk & 0x80000000u) ? (kk & 0x7fffffffu) : ~kk;
-            a.out_idx[ob + c] = cand_e[surv[pos]];
-            a.out_score[ob + c] = __uint_as_float(u);
-            for (int i = 0; i < FARM_MAX_CONSTRAINTS; ++i) {
-                const unsigned long long b = i < m ? best[pos * FARM_MAX_CONSTRAINTS + i] : 0ull;
-                a.out_t[(ob + c) * 4 + i] = i < m ? (b ? __uint_as_float((uint32_t)(b >> 32)) : 0.f) : -1.f;
-                a.out_anchor[(ob + c) * 4 + i] = (i < m && b) ? (int32_t)(0xffffffffu - (uint32_t)(b & 0xffffffffu)) : -1;
-            }
-        } else {
-            a.out_idx[ob + c] = -1;
-            a.out_score[ob + c] = 0.f;
-            for (int i = 0; i < FARM_MAX_CONSTRAINTS; ++i) {
-                a.out_t[(ob + c) * 4 + i] = -1.f;
-                a.out_anchor[(ob + c) * 4 + i] = -1;
-            }
+    for (int pos = tid; pos < ns; pos += TH) {
+        const uint64_t kp = key[pos];
+        int c = 0;
+        for (int j = 0; j < ns; ++j) c += key[j] > kp ? 1 : 0;
+        if (c >= n_out) continue;
+        const uint32_t kk = (uint32_t)(kp >> 32);
+        const uint32_t u = (kk & 0x80000000u) ? (kk & 0x7fffffffu) : ~kk;
+        a.out_idx[ob + c] = cand_e[surv[pos]];
+        a.out_score[ob + c] = __uint_as_float(u);
+        for (int i = 0; i < FARM_MAX_CONSTRAINTS; ++i) {
+            const unsigned long long b = i < m ? best[pos * FARM_MAX_CONSTRAINTS + i] : 0ull;
+            a.out_t[(ob + c) * 4 + i] = i < m ? (b ? __uint_as_float((uint32_t)(b >> 32)) : 0.f) : -1.f;
+            a.out_anchor[(ob + c) * 4 + i] = (i < m && b) ? (int32_t)(0xffffffffu - (uint32_t)(b & 0xffffffffu)) : -1;
+        }
+    }
+    for (int c = ns + tid; c < n_out; c += TH) {
+        a.out_idx[ob + c] = -1;
+        a.out_score[ob + c] = 0.f;
+        for (int i = 0; i < FARM_MAX_CONSTRAINTS; ++i) {
+            a.out_t[(ob + c) * 4 + i] = -1.f;
+            a.out_anchor[(ob + c) * 4 + i] = -1;
         }
     }
 }
@@ -566,16 +549,14 @@ cudaError_t launch_compose(const ComposeArgs &a, cudaStream_t s)
     if (a.n_q <= 0) return cudaSuccess;
     if (a.stride_t < 1 || a.stride_t > kMaxTargetCands || a.stride_l < 1 || a.stride_l > kMaxAnchorCands)
         return cudaErrorInvalidValue;
-    int PM = 1;
-    while (PM < a.stride_t) PM <<= 1;
     const int KC = a.p.k_closest < a.stride_t ? a.p.k_closest : a.stride_t;
-    const ComposeSmem L(a.stride_t, PM, a.stride_l, KC);
+    const ComposeSmem L(a.stride_t, a.stride_l, KC);
     if (L.bytes + 64 > 48 * 1024) {     // (plus the kernel's few bytes of static shared memory)
         const cudaError_t e = cudaFuncSetAttribute(compose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)L.bytes);
         if (e != cudaSuccess) return e;
     }
-    compose_kernel<<<(unsigned)a.n_q, TH, L.bytes, s>>>(a, PM, KC);
+    compose_kernel<<<(unsigned)a.n_q, TH, L.bytes, s>>>(a, KC);
     return cudaGetLastError();
 }
 

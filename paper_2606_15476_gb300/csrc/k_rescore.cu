@@ -144,12 +144,12 @@ rescore_grouped_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, const
     const float *q = Q32 + (pc.q_row0 + i) * (int64_t)dim_pad;
     if (i < pc.ntr) {
         const int64_t co = (pc.t_row0 + i) * (int64_t)cstride_t, oo = (pc.t_row0 + i) * (int64_t)stride_t;
-        rescore_row(q, dim_pad, pc.d32, bsel_t + co, bsel_tv ? bsel_tv + co : nullptr, band, pc.keep_t, pc.R,
+        rescore_row(q, dim_pad, pc.d32, bsel_t + co, bsel_tv ? bsel_tv + co : nullptr, band, pc.fkeep_t, pc.R,
                     tsel_idx + oo, tsel_cos ? tsel_cos + oo : nullptr, stride_t);
     } else {
         const int64_t l = pc.l_row0 + (i - pc.ntr);
         const int64_t co = l * (int64_t)cstride_l;
-        rescore_row(q, dim_pad, pc.d32, bsel_l + co, bsel_lv ? bsel_lv + co : nullptr, band, pc.keep_l, pc.klm,
+        rescore_row(q, dim_pad, pc.d32, bsel_l + co, bsel_lv ? bsel_lv + co : nullptr, band, pc.fkeep_l, pc.klm,
                     lsel_idx + l * (int64_t)stride_l, nullptr, stride_l);
     }
 }

@@ -103,7 +103,9 @@ struct Elem<kSimFp8> {                       // FP8 E4M3
 // for a pair); PAIR: the two CTAs of a cluster compute one 256 x BN tile with
 // two-SM MMAs (cta_group::2), each holding its 128 rows of A and half of B.
 // Every CTA loads its own operand tiles: no copy is delivered to several CTAs.
-template <int MODE, int BN_, int CM_, bool PAIR_ = false>
+// EMIT_: the fused selection's epilogue, whose candidate slots (32 words per
+// epilogue thread, 32 KB) take the place of one pipeline stage.
+template <int MODE, int BN_, int CM_, bool PAIR_ = false, bool EMIT_ = false>
 struct Cfg {
     using E = Elem<MODE>;
     static constexpr int BN = BN_;
@@ -114,13 +116,17 @@ struct Cfg {
     static constexpr int B_PART = B_BYTES / CM_;                // this CTA's share of a B tile
     static constexpr int B_SMEM = PAIR_ ? B_PART : B_BYTES;     // B bytes a stage holds in this CTA
     static constexpr int STAGE_BYTES = OPS * (A_BYTES + B_SMEM);
-    static constexpr int STAGES = STAGE_BUDGET / STAGE_BYTES < 8 ? STAGE_BUDGET / STAGE_BYTES : 8;
+    static constexpr int EMIT_SLOTS = 32;
+    static constexpr int EMIT_BYTES = EMIT_ ? 4 * 32 * EMIT_SLOTS * 8 : 0;
+    static constexpr int BUDGET = STAGE_BUDGET - EMIT_BYTES;
+    static constexpr int STAGES = BUDGET / STAGE_BYTES < 8 ? BUDGET / STAGE_BYTES : 8;
     static constexpr int ACC_COLS = OPS * BN_;                  // TMEM columns of one tile's accumulators
     static constexpr int NACC = 512 / ACC_COLS >= 2 ? 2 : 1;    // tiles in flight in TMEM
     static constexpr int STAGING_BYTES = 4 * 32 * 32 * 4;      // epilogue: one 32 x 32 FP32 block per warp
     static constexpr int SCALE_BYTES = MODE == kSimFp8 ? 4 * BN_ * 4 : 0;   // FP8: a tile's column scales per warp
     static constexpr int SMEM_BYTES =
-        STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES + SCALE_BYTES;
+        STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES + SCALE_BYTES + EMIT_BYTES;
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
     static_assert(BN_ % 128 == 0 && BN_ <= 256, "tile width");
     static_assert(STAGES >= 3, "pipeline depth");
     static_assert(BN_ / CM_ >= 8 && (B_PART % 1024) == 0, "B share must keep the swizzle atoms whole");
@@ -393,13 +399,27 @@ __device__ __forceinline__ GemmPiece piece_of(int tile, const GemmPiece *pieces,
 }
 
 // This CTA's tile of cluster tile `tile` within piece pc: first row (local
-// to the piece) and first column.
+// to the piece), first object column n0 and first stored column c0 (they
+// differ for the compacted sample tiles).
 template <int BN_, int CM_>
-__device__ __forceinline__ void piece_tile(const GemmPiece &pc, int tile, uint32_t rank, int &m0, int &n0)
+__device__ __forceinline__ void piece_tile(const GemmPiece &pc, int tile, uint32_t rank, int &m0, int &n0, int &c0)
 {
     const int m_tiles = (pc.rows + BM - 1) / BM;
-    const int n_tiles = (pc.n + BN_ - 1) / BN_;
-    tile_origin<BN_, CM_>(tile - pc.tile_begin, (m_tiles + CM_ - 1) / CM_, n_tiles, rank, m0, n0);
+    const int n_tiles = (int)col_tiles(pc.n, BN_, pc.col_mode, pc.col_stride);
+    tile_origin<BN_, CM_>(tile - pc.tile_begin, (m_tiles + CM_ - 1) / CM_, n_tiles, rank, m0, c0);
+    n0 = (int)col_tile_of(c0 / BN_, pc.col_mode, pc.col_stride) * BN_;
+}
+
+__device__ __forceinline__ uint32_t order_key(float f)
+{
+    const uint32_t u = __float_as_uint(f + 0.0f);   // -0 -> +0
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_value(uint32_t k)
+{
+    const uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(u);
 }
 
 // Store SL float4 values per row of the warp's 32 rows (lane = row) to
@@ -422,15 +442,15 @@ __device__ __forceinline__ void store_rows_staged(float4 *blk, const float4 (&va
     __syncwarp();
 }
 
-template <int MODE, int BN_, int CM_, bool GROUPED, bool PAIR>
+template <int MODE, int BN_, int CM_, bool GROUPED, bool PAIR, bool EMIT = false>
 __global__ void __launch_bounds__(THREADS, 1)
 sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant__ CUtensorMap map_q1,
               const __grid_constant__ CUtensorMap map_d0, const __grid_constant__ CUtensorMap map_d1,
               const GemmPiece *__restrict__ pieces, int32_t n_pieces, const GemmPiece single,
               float *__restrict__ S, float *__restrict__ tops, int32_t k_slices, int32_t total,
-              const float *__restrict__ scale_q, int32_t *err)
+              const float *__restrict__ scale_q, int32_t *err, const FuseEmit emit)
 {
-    using C = Cfg<MODE, BN_, CM_, PAIR>;
+    using C = Cfg<MODE, BN_, CM_, PAIR, EMIT>;
     using M = Elem<MODE>;
     constexpr bool TWO_OPERAND_TILES = !M::SPLIT;
     constexpr int B_SMEM = C::B_SMEM;
@@ -442,8 +462,10 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     // FP32-accurate mode with one tile in TMEM: the epilogue first folds the
     // correction into the main accumulator in TMEM and frees the correction
     // columns, so the next tile's correction products (two thirds of its
-    // MMAs) run while the main accumulator is drained to S
+    // MMAs) run while the main accumulator is drained to S (EMIT: compared
+    // with the rows' thresholds).
     constexpr bool FOLD = M::SPLIT && NACC == 1;
+    static_assert(!EMIT || GROUPED, "the fused selection runs grouped launches");
     constexpr uint32_t TMEM_ALLOC = 512;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -455,6 +477,8 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     float *staging = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256);
     float *tile_scales = staging + 4 * 32 * 32;    // FP8 mode: [4 warps][BN]
+    // EMIT: [4 warps][32 lanes][EMIT_SLOTS] candidate words
+    uint64_t *emit_slots = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(tile_scales) + C::SCALE_BYTES);
     uint64_t *corr_free = acc_empty + 1;      // FOLD: the correction columns are free (tile accumulators: one)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -496,8 +520,8 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             uint32_t it = 0;
             for (int tile = cluster_id; tile < total && !*abort_flag; tile += n_clusters) {
                 const GemmPiece pc = piece_of<GROUPED>(tile, pieces, n_pieces, single);
-                int m0, n0;
-                piece_tile<BN_, CM_>(pc, tile, rank, m0, n0);
+                int m0, n0, c0;
+                piece_tile<BN_, CM_>(pc, tile, rank, m0, n0, c0);
                 const int qa = (int)(pc.q_row0 + m0);     // A rows: the piece's rows in the operand arrays
                 const CUtensorMap *bmap0 = GROUPED ? static_cast<const CUtensorMap *>(pc.bmap) : &map_d0;
                 const CUtensorMap *bmap1 = GROUPED ? static_cast<const CUtensorMap *>(pc.bmap) + 1 : &map_d1;
@@ -676,6 +700,15 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
         uint32_t tc = 0;
         for (int tile = cluster_id; tile < total; tile += n_clusters, ++tc) {
             const uint32_t buf = tc % NACC, use = tc / NACC;
+            // EMIT: the row's threshold is read before the accumulator is waited for
+            uint32_t tk = 0xffffffffu;
+            if constexpr (EMIT) {
+                const GemmPiece pt = piece_of<GROUPED>(tile, pieces, n_pieces, single);
+                int tm0, tn0, tc0;
+                piece_tile<BN_, CM_>(pt, tile, rank, tm0, tn0, tc0);
+                const int64_t tr = (int64_t)tm0 + quad * 32 + lane;
+                if (tr < pt.rows) tk = __ldg(emit.tau_key + pt.q_row0 + tr);
+            }
             if (!mbar_wait(&acc_full[buf], use & 1u) || *abort_flag) {
                 *abort_flag = 1;
                 break;
@@ -702,14 +735,124 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 }
             }
             const GemmPiece pc = piece_of<GROUPED>(tile, pieces, n_pieces, single);
-            int m0, n0;
-            piece_tile<BN_, CM_>(pc, tile, rank, m0, n0);
+            int m0, n0, c0;
+            piece_tile<BN_, CM_>(pc, tile, rank, m0, n0, c0);
             const int64_t r = (int64_t)m0 + quad * 32 + lane;    // row within the piece
             const int64_t rows = pc.rows, n = pc.n;
             const bool live = r < rows;
+            if constexpr (EMIT) {
+                // the fused selection: every value of a live row whose order key
+                // reaches the row's threshold (tk, read above; dead rows never
+                // reach it) is appended to the row's candidate buffer.  Per
+                // 32-column chunk a branch-free compare gives the row's hit mask;
+                // a row with hits stages the chunk's values in its part of the
+                // warp's staging block and copies each hit's word, found by its
+                // bit, into its EMIT_SLOTS slots.  The accumulator is released
+                // before the row's places are reserved (one atomic per row and
+                // tile) and the slots written out; a row with more hits than
+                // slots reserves first and writes them during a second pass over
+                // its chunks.  Entries past the capacity are dropped (the count
+                // still tells).
+                constexpr int SLOTS = C::EMIT_SLOTS;
+                const int64_t grow = pc.q_row0 + r;
+                uint64_t *dst = emit.cand + grow * (int64_t)emit.cap;
+                uint64_t *slotw = emit_slots + ((warp - 2) * 32 + lane) * SLOTS;
+                float *vst = staging + (warp - 2) * 32 * 32 + lane * 32;   // 32 floats, 16-byte slots swizzled
+                const float sr = (MODE == kSimFp8 && live) ? scale_q[pc.q_row0 + r] : 1.f;
+                // the row's values of column chunk c (32 objects from n0 + 32 c)
+                auto chunk = [&](int c, float (&v)[32]) {
+                    const uint32_t lane_addr = tmem + buf * (uint32_t)C::ACC_COLS + ((uint32_t)(quad * 32) << 16) +
+                                               (uint32_t)(c * 32);
+                    tmem_ld32(lane_addr, v);
+                    if (MODE == kSimF16x3 && !FOLD) {
+                        float w[32];
+                        tmem_ld32(lane_addr + ACC_CORR, w);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = fmaf(w[i], RESID_SCALE_INV, v[i]);
+                    }
+                    if (MODE == kSimFp8 && live) {
+                        const int64_t obj0 = (int64_t)n0 + c * 32;
+                        const float *__restrict__ scale_d = pc.scale_d;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            v[i] *= sr * (obj0 + i < n ? __ldg(scale_d + obj0 + i) : 0.f);
+                    }
+                };
+                // the threshold as a float: for non-NaN values v >= tf exactly when
+                // order_key(v) >= tk (-0 and +0 compare equal and share a key)
+                const bool dead = tk == 0xffffffffu;
+                const bool all_pass = tk == 0u;     // a sample shorter than the list: every entry
+                const float tf = (dead || all_pass) ? 0.f : key_value(tk);
+                uint32_t masks[BN / 32];
+                int nh = 0;
+#pragma unroll
+                for (int c = 0; c < BN / 32; ++c) {
+                    float v[32];
+                    chunk(c, v);
+                    const int64_t obj0 = (int64_t)n0 + c * 32;
+                    uint32_t hit = 0u;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) hit |= (v[i] >= tf || all_pass) ? (1u << i) : 0u;
+                    if (obj0 + 32 > n) hit &= obj0 >= n ? 0u : (0xffffffffu >> (32 - (int)(n - obj0)));
+                    if (dead) hit = 0u;
+                    masks[c] = hit;
+                    if (hit) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            reinterpret_cast<float4 *>(vst)[j ^ (lane & 7)] =
+                                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                        uint32_t h = hit;
+                        while (h) {
+                            const int i = __ffs(h) - 1;
+                            h &= h - 1u;
+                            if (nh < SLOTS) {
+                                const float x = vst[(((i >> 2) ^ (lane & 7)) << 2) | (i & 3)];
+                                slotw[nh] = ((uint64_t)order_key(x) << 32) |
+                                            (uint64_t)(0xffffffffu - (uint32_t)(obj0 + i));
+                            }
+                            ++nh;
+                        }
+                    }
+                }
+                const bool over = nh > SLOTS;
+                if (__any_sync(0xffffffffu, over)) {
+                    int pos = over ? atomicAdd(emit.cnt + grow, nh) : 0;
+#pragma unroll 1
+                    for (int c = 0; c < BN / 32; ++c) {
+                        if (!__any_sync(0xffffffffu, over && masks[c] != 0u)) continue;    // tcgen05.ld is warp-wide
+                        float v[32];
+                        chunk(c, v);
+                        if (!over) continue;
+                        const int64_t obj0 = (int64_t)n0 + c * 32;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if ((masks[c] >> i) & 1u) {
+                                if (pos < emit.cap)
+                                    dst[pos] = ((uint64_t)order_key(v[i]) << 32) |
+                                               (uint64_t)(0xffffffffu - (uint32_t)(obj0 + i));
+                                ++pos;
+                            }
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) {
+                    if (PAIR && rank != 0) mbar_arrive_remote(cluster_addr(smem_u32(&acc_empty[buf]), 0u));
+                    else mbar_arrive(&acc_empty[buf]);
+                }
+                if (nh > 0 && !over) {
+                    const int pos = atomicAdd(emit.cnt + grow, nh);
+                    for (int k = 0; k < nh; ++k)
+                        if (pos + k < emit.cap) dst[pos + k] = slotw[k];
+                }
+                continue;
+            }
+            const int64_t ns_ = pc.n_store;       // valid stored columns (sample tiles compacted)
             const int64_t r_blk = (int64_t)m0 + quad * 32;       // first row of the warp's blocks
             float *sblk = S + pc.s_off + r_blk * pc.ld;
             const bool vec = (pc.ld % 4) == 0;
+            // stored columns c0 + ... are valid below ns_ exactly where their objects n0 + ... are below n
             const float sr = (MODE == kSimFp8 && live) ? scale_q[pc.q_row0 + r] : 1.f;
             // FP8 mode: the tile's column scales (zero past the row end), staged once
             // per tile in the warp's slot instead of one bounds-checked load per entry
@@ -733,7 +876,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] = fmaf(w[i], RESID_SCALE_INV, v[i]);
                 }
-                const int64_t col0 = (int64_t)n0 + c * 32;
+                const int64_t col0 = (int64_t)c0 + c * 32;      // stored column
                 if (MODE == kSimFp8 && live) {
                     const float4 *s4 = reinterpret_cast<const float4 *>(scl + c * 32);
 #pragma unroll
@@ -750,13 +893,13 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         float m = ninf;
-                        if (col0 + 32 <= n) {
+                        if (col0 + 32 <= ns_) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) m = fmaxf(m, v[8 * g + i]);
                         } else {
 #pragma unroll
                             for (int i = 0; i < 8; ++i)
-                                if (col0 + 8 * g + i < n) m = fmaxf(m, v[8 * g + i]);
+                                if (col0 + 8 * g + i < ns_) m = fmaxf(m, v[8 * g + i]);
                         }
                         gmax[4 * c + g] = m;
                     }
@@ -772,27 +915,27 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                     const float4 x = blk[rr * 8 + (slot ^ (rr & 7))];
                     if (r_blk + rr < rows) {
                         float *dst = sblk + (int64_t)rr * pc.ld + cs;
-                        if (vec && cs + 4 <= n) {
+                        if (vec && cs + 4 <= ns_) {
                             *reinterpret_cast<float4 *>(dst) = x;
                         } else {
-                            if (cs < n) dst[0] = x.x;
-                            if (cs + 1 < n) dst[1] = x.y;
-                            if (cs + 2 < n) dst[2] = x.z;
-                            if (cs + 3 < n) dst[3] = x.w;
+                            if (cs < ns_) dst[0] = x.x;
+                            if (cs + 1 < ns_) dst[1] = x.y;
+                            if (cs + 2 < ns_) dst[2] = x.z;
+                            if (cs + 3 < ns_) dst[3] = x.w;
                         }
                     }
                 }
                 __syncwarp();
             }
             if (keep_tops) {
-                const int64_t gs = group_stride(n, pc.gshift);
+                const int64_t gs = group_stride(ns_, pc.gshift);
                 float *tblk = tops + pc.tops_off + r_blk * gs;
                 if (pc.gshift == kGroupShiftSmall) {
                     float4 t4[BN / 32];
 #pragma unroll
                     for (int j = 0; j < BN / 32; ++j)
                         t4[j] = make_float4(gmax[4 * j], gmax[4 * j + 1], gmax[4 * j + 2], gmax[4 * j + 3]);
-                    store_rows_staged<BN / 32>(blk, t4, lane, tblk + n0 / 8, gs, rows - r_blk);
+                    store_rows_staged<BN / 32>(blk, t4, lane, tblk + c0 / 8, gs, rows - r_blk);
                 } else {
                     float4 t4[BN / 128];
 #pragma unroll
@@ -804,7 +947,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                                           fmaxf(gmax[16 * j + 4 * u + 2], gmax[16 * j + 4 * u + 3]));
                         t4[j] = make_float4(g4[0], g4[1], g4[2], g4[3]);
                     }
-                    store_rows_staged<BN / 128>(blk, t4, lane, tblk + n0 / 32, gs, rows - r_blk);
+                    store_rows_staged<BN / 128>(blk, t4, lane, tblk + c0 / 32, gs, rows - r_blk);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -863,21 +1006,22 @@ bool make_map(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, in
 // as can be resident at once (a GPC with an odd number of free SMs cannot
 // hold a whole cluster on its last SM); the count is cached per device and
 // kernel (concurrent first calls compute the same value).
-template <int MODE, int BN_, int CM_, bool GROUPED, bool PAIR = false>
+template <int MODE, int BN_, int CM_, bool GROUPED, bool PAIR = false, bool EMIT = false>
 cudaError_t launch_impl(const CUtensorMap &mq0, const CUtensorMap &mq1, const CUtensorMap &md0,
                         const CUtensorMap &md1, const GemmPiece *pieces, int32_t n_pieces, const GemmPiece &single,
                         float *S, float *tops, int32_t k_slices, int64_t total_tiles, const float *scale_q,
-                        int num_sms, int32_t *err, cudaStream_t s)
+                        int num_sms, int32_t *err, cudaStream_t s, const FuseEmit &emit = FuseEmit{})
 {
-    using C = Cfg<MODE, BN_, CM_, PAIR>;
+    using C = Cfg<MODE, BN_, CM_, PAIR, EMIT>;
     if (total_tiles <= 0) return cudaSuccess;
     if (total_tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto kernel = sim_tc_kernel<MODE, BN_, CM_, GROUPED, PAIR>;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    auto kernel = sim_tc_kernel<MODE, BN_, CM_, GROUPED, PAIR, EMIT>;
+    const int smem_bytes = C::SMEM_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = C::SMEM_BYTES;
+    cfg.dynamicSmemBytes = smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -886,7 +1030,7 @@ cudaError_t launch_impl(const CUtensorMap &mq0, const CUtensorMap &mq1, const CU
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    static int resident[64] = {};
+    static int resident[64] = {};      // per device, per kernel instantiation
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     int *slot = dev >= 0 && dev < 64 ? &resident[dev] : nullptr;
@@ -902,7 +1046,7 @@ cudaError_t launch_impl(const CUtensorMap &mq0, const CUtensorMap &mq1, const CU
     const int clusters = (int)std::min<int64_t>(total_tiles, nc);
     cfg.gridDim = dim3((unsigned)(clusters * CM_));
     e = cudaLaunchKernelEx(&cfg, kernel, mq0, mq1, md0, md1, pieces, n_pieces, single, S, tops, k_slices,
-                           (int32_t)total_tiles, scale_q, err);
+                           (int32_t)total_tiles, scale_q, err, emit);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -955,6 +1099,9 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
     single.ld = (int32_t)ld_s;
     single.tile_begin = 0;
     single.gshift = group_shift_for(n);
+    single.col_mode = kColAll;
+    single.col_stride = 0;
+    single.n_store = (int32_t)n;
     return launch_impl<MODE, BN_, CM_, false, true>(mq0, mq1, md0, md1, nullptr, 1, single, S, tops,
                                               k_slices_of<MODE>(dim_pad), sim_cluster_tiles(rows, n, kSimPairVariant), scale_q,
                                               num_sms, err, s);
@@ -963,7 +1110,7 @@ cudaError_t launch_tc(const void *q0, const void *q1, const void *d0, const void
 template <int MODE, int BN_, int CM_, bool PAIR = false>
 cudaError_t launch_grouped(const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
                            const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S, float *tops,
-                           const float *scale_q, int num_sms, int32_t *err, cudaStream_t s)
+                           const float *scale_q, int num_sms, int32_t *err, cudaStream_t s, const FuseEmit *emit)
 {
     constexpr bool TWO = !Elem<MODE>::SPLIT;
     if (total_tiles <= 0) return cudaSuccess;
@@ -979,6 +1126,15 @@ cudaError_t launch_grouped(const void *q0, const void *q1, int64_t rows_total, i
     else if (!make_map<MODE>(&mq1, q1, dim_pad, rows_total, BM)) return cudaErrorInvalidValue;
     GemmPiece unused{};
     // the B maps of the pieces live in device memory; map_d0 / map_d1 are unused
+    if (emit) {
+        if constexpr (BN_ == 256) {
+            if (!emit->tau_key || !emit->cnt || !emit->cand || emit->cap < 1) return cudaErrorInvalidValue;
+            return launch_impl<MODE, BN_, CM_, true, PAIR, true>(mq0, mq1, mq0, mq1, pieces, n_pieces, unused, S,
+                                                           tops, k_slices_of<MODE>(dim_pad), total_tiles, scale_q,
+                                                           num_sms, err, s, *emit);
+        }
+        return cudaErrorInvalidValue;     // the fused selection samples tiles of 256 objects
+    }
     return launch_impl<MODE, BN_, CM_, true, PAIR>(mq0, mq1, mq0, mq1, pieces, n_pieces, unused, S, tops,
                                              k_slices_of<MODE>(dim_pad), total_tiles, scale_q, num_sms, err, s);
 }
@@ -986,18 +1142,19 @@ cudaError_t launch_grouped(const void *q0, const void *q1, int64_t rows_total, i
 template <int MODE>
 cudaError_t launch_grouped_variant(int variant, const void *q0, const void *q1, int64_t rows_total, int32_t dim_pad,
                                    const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles, float *S,
-                                   float *tops, const float *scale_q, int num_sms, int32_t *err, cudaStream_t s)
+                                   float *tops, const float *scale_q, int num_sms, int32_t *err, cudaStream_t s,
+                                   const FuseEmit *emit)
 {
     switch (variant) {
     case 0:
         return launch_grouped<MODE, 256, 1>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
-                                            scale_q, num_sms, err, s);
+                                            scale_q, num_sms, err, s, emit);
     case 1:
         return launch_grouped<MODE, 128, 1>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S, tops,
-                                            scale_q, num_sms, err, s);
+                                            scale_q, num_sms, err, s, emit);
     case 2:
         return launch_grouped<MODE, 256, 2, true>(q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles, S,
-                                                  tops, scale_q, num_sms, err, s);
+                                                  tops, scale_q, num_sms, err, s, emit);
     default:
         return cudaErrorInvalidValue;
     }
@@ -1031,18 +1188,18 @@ bool sim_tc_encode_b(int mode, int variant, void *out, const void *d0, const voi
 cudaError_t launch_sim_tc_grouped(int mode, int variant, const void *q0, const void *q1, int64_t rows_total,
                                   int32_t dim_pad, const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles,
                                   float *S, float *tops, const float *scale_q, int num_sms, int32_t *err,
-                                  cudaStream_t s)
+                                  cudaStream_t s, const FuseEmit *emit)
 {
     switch (mode) {
     case kSimF16x3:
         return launch_grouped_variant<kSimF16x3>(variant, q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles,
-                                                 S, tops, scale_q, num_sms, err, s);
+                                                 S, tops, scale_q, num_sms, err, s, emit);
     case kSimBf16:
         return launch_grouped_variant<kSimBf16>(variant, q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles,
-                                                S, tops, scale_q, num_sms, err, s);
+                                                S, tops, scale_q, num_sms, err, s, emit);
     case kSimFp8:
         return launch_grouped_variant<kSimFp8>(variant, q0, q1, rows_total, dim_pad, pieces, n_pieces, total_tiles,
-                                               S, tops, scale_q, num_sms, err, s);
+                                               S, tops, scale_q, num_sms, err, s, emit);
     default:
         return cudaErrorInvalidValue;
     }

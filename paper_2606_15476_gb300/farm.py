@@ -21,6 +21,9 @@ PREC_FP32_SIMT = 3
 PREC_LEARNED = 4
 PTR_DEVICE = 1
 GRAPH = 2          # FARM_GRAPH
+UNFUSED = 4        # FARM_UNFUSED
+ASYNC = 8          # FARM_ASYNC
+FUSED = 16         # FARM_FUSED
 # predicate codes (farm_pred)
 (ABOVE, BELOW, LEFT_OF, RIGHT_OF, NEAR, NEXT_TO, ON, IN_FRONT_OF, BEHIND, CLOSEST, FARTHEST, NEAR_H,
  INSIDE) = range(13)
@@ -184,8 +187,9 @@ def farm_memory_upload(ctx, scene_id: int, desc, cls, box, views=None) -> None:
 
 
 def farm_query_batch(ctx, scene_of_q, tgt_emb, tgt_cls, c_off, c_pred, c_emb,
-                     precision: int = PREC_FP32, graph: bool = False) -> int:
-    """Enqueue a batch (see farm.h); graph=True passes FARM_GRAPH."""
+                     precision: int = PREC_FP32, graph: bool = False, fused=None) -> int:
+    """Enqueue a batch (see farm.h); graph=True passes FARM_GRAPH, fused=True
+    FARM_FUSED and fused=False FARM_UNFUSED (None: the library's default)."""
     n_q = int(len(tgt_cls))
     s = _Arr(scene_of_q, np.int32, "scene_of_q", allow_device=False)
     tc = _Arr(tgt_cls, np.int32, "tgt_cls", allow_device=False)
@@ -193,7 +197,7 @@ def farm_query_batch(ctx, scene_of_q, tgt_emb, tgt_cls, c_off, c_pred, c_emb,
     cp = _Arr(c_pred, np.int32, "c_pred", allow_device=False)
     te = _Arr(tgt_emb, np.float32, "tgt_emb")
     ce = _Arr(c_emb, np.float32, "c_emb")
-    flags = _flags(te, ce) | (GRAPH if graph else 0)
+    flags = _flags(te, ce) | (GRAPH if graph else 0) | ({None: 0, True: FUSED, False: UNFUSED}[fused])
     h = C.c_uint64()
     _ck(ctx, _lib.farm_query_batch(ctx, n_q, s.ptr, te.ptr, tc.ptr, co.ptr, cp.ptr, ce.ptr,
                                    int(precision), flags, C.byref(h)))
@@ -270,8 +274,9 @@ def farm_associate(ctx, ent, det, tau_f: float, h_max: float, max_m: int, out=No
 
 
 def farm_topk(ctx, handle: int, k: int, n_q: int, out_idx=None, out_score=None, out_pred=None,
-              out_anchor=None, breakdown: bool = True):
-    """TopK of a batch.  Without output arrays, returns new numpy arrays."""
+              out_anchor=None, breakdown: bool = True, asynchronous: bool = False):
+    """TopK of a batch.  Without output arrays, returns new numpy arrays.
+    asynchronous=True (host outputs): FARM_ASYNC, valid after the next farm_sync."""
     if out_idx is None:
         out_idx = np.zeros((n_q, k), np.int32)
         out_score = np.zeros((n_q, k), np.float32)
@@ -289,7 +294,8 @@ def farm_topk(ctx, handle: int, k: int, n_q: int, out_idx=None, out_score=None, 
             raise FarmError(1, "host outputs must be C-contiguous numpy arrays")
     ptr = (lambda a: None if a is None else C.c_void_p(a.data_ptr() if dev else a.ctypes.data))
     _ck(ctx, _lib.farm_topk(ctx, C.c_uint64(handle), int(k), ptr(out_idx), ptr(out_score),
-                            ptr(out_pred), ptr(out_anchor), PTR_DEVICE if dev else 0))
+                            ptr(out_pred), ptr(out_anchor),
+                            PTR_DEVICE if dev else (ASYNC if asynchronous else 0)))
     return dict(idx=out_idx, score=out_score, pred=out_pred, anchor=out_anchor)
 
 

@@ -1,0 +1,143 @@
+"""GPU: the fused rank selection against the unfused path and the oracle.
+
+By default the tensor-core paths store only a sample of each similarity row
+(every s-th tile of 256 objects), rank it, and let the similarity kernel keep
+only the entries of the other tiles that reach the sample's R-th value; the
+row's list is then merged from the sample's list and the kept entries.
+FARM_UNFUSED writes the whole block and selects from it.  Both see the same
+tensor-core values, so their lists -- and everything after them -- must be
+bitwise equal, in every precision, graph-captured or not, over scenes of one
+tile, a ragged last sample tile, several sample tiles and rows longer than
+the shared-memory select.  A scene whose sample tiles hold a class the queries
+never ask for overflows the kept-entry buffers on purpose: those rows are
+recomputed exactly and the result must still match the oracle.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import parity
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DIM = 256
+# sampling stride of each fused path at the default parameters (tiles of 256
+# objects): lists of up to 128 (FP32) 8, up to 256 (BF16) 4
+STRIDE = {"fp32": 8, "bf16": 4}
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2606_15476_gb300 as F
+    return F
+
+
+def _code(F, prec):
+    return {"fp32": F.PREC_FP32, "bf16": F.PREC_BF16, "fp8": F.PREC_FP8, "learned": F.PREC_LEARNED}[prec]
+
+
+def _run(F, ctx, qb, code, fused, graph=False):
+    h = F.farm_query_batch(ctx, qb.scene_of_q, qb.tgt_emb, qb.tgt_cls, qb.c_off, qb.c_pred, qb.c_emb, code,
+                           graph=graph, fused=fused)
+    return F.farm_topk(ctx, h, 10, qb.n_q), F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
+
+
+def _same(a, b):
+    for key in ("idx", "score", "pred", "anchor"):
+        np.testing.assert_array_equal(a[0][key], b[0][key], err_msg=key)
+    np.testing.assert_array_equal(a[1][0], b[1][0])
+    np.testing.assert_array_equal(a[1][1], b[1][1])
+
+
+@pytest.fixture(scope="module")
+def world(F):
+    ctx = F.farm_create(0)
+    scenes, parts = {}, []
+    # one tile; a ragged last sample tile; several sample tiles; rows longer
+    # than the shared-memory select's 24,576 entries
+    for sid, n in [(60, 200), (61, 2100), (62, 9000), (63, 20000), (64, 30001)]:
+        sc = synth.make_scene(sid, n, DIM, extent=(40.0, 40.0, 5.0), n_classes=max(8, n // 50), n_views=4,
+                              distractor_classes=4, distractor_frac=0.3)
+        F.farm_memory_upload(ctx, sid, sc.desc, sc.cls, sc.box, sc.views)
+        scenes[sid] = sc
+        parts.append(synth.make_queries(sid + 500, sc, 40, m_choices=(0, 1, 2, 3, 4), scene_id=sid,
+                                        distractor_classes=4, distractor_target_frac=0.5))
+    qb = synth.scenes.concat_batches(parts)
+    qb = qb.subset(np.random.default_rng(8).permutation(qb.n_q))
+    rng = np.random.default_rng(9)
+    H, P = 128, 64
+    F.farm_mlp_set(ctx, (rng.standard_normal((H, DIM)) / math.sqrt(DIM)).astype(np.float32),
+                   (0.05 * rng.standard_normal(H)).astype(np.float32),
+                   (rng.standard_normal((P, H)) / math.sqrt(H)).astype(np.float32),
+                   (0.05 * rng.standard_normal(P)).astype(np.float32))
+    yield ctx, scenes, qb
+    F.farm_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8", "learned"])
+def test_fused_equals_unfused(F, world, prec):
+    """(FP8 and learned batches are never fused -- E4M3 ties many entries at
+    a threshold, and lists of 512 crowd the buffer -- so for them this
+    compares the default with the explicit flag.)"""
+    ctx, scenes, qb = world
+    code = _code(F, prec)
+    F.farm_select_fallbacks(ctx, reset=True)
+    fused = _run(F, ctx, qb, code, True)
+    assert F.farm_select_fallbacks(ctx) == 0
+    _same(fused, _run(F, ctx, qb, code, False))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_fused_graph_replays_bitwise(F, world, prec):
+    ctx, scenes, qb = world
+    code = _code(F, prec)
+    direct = _run(F, ctx, qb, code, True)
+    _same(_run(F, ctx, qb, code, True, graph=True), direct)
+    _same(_run(F, ctx, qb, code, True, graph=True), direct)     # a replay
+
+
+def _sample_class_scene(seed, n, fs):
+    """Objects of the sample tiles (every fs-th tile of 256) in class 0, all
+    others in class 1: a class-1 row's sample ranks only class-0 objects, so
+    its threshold lets every class-1 object through."""
+    base = synth.make_scene(seed, n, DIM, extent=(30.0, 30.0, 4.0), n_classes=2, n_views=4)
+    cls = np.where((np.arange(n) // 256) % fs == 0, 0, 1).astype(np.int32)
+    rng = np.random.default_rng(seed + 1)
+    desc = base.centroids[cls] + base.noise_sigma * rng.standard_normal((n, DIM))
+    desc = (desc / np.linalg.norm(desc, axis=1, keepdims=True)).astype(np.float32)
+    return dataclasses.replace(base, desc=desc, cls=cls)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_overflowing_rows_are_recomputed_exactly(F, prec):
+    fs = STRIDE[prec]
+    sc = _sample_class_scene(71, 4096, fs)
+    qb = synth.make_queries(72, sc, 48, m_choices=(1, 2))
+    ctx = F.farm_create(0)
+    try:
+        F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+        F.farm_select_fallbacks(ctx, reset=True)
+        out, (t, l) = _run(F, ctx, qb, _code(F, prec), True)
+        recomputed = F.farm_select_fallbacks(ctx)
+    finally:
+        F.farm_destroy(ctx)
+    # most rows ask for class 1 (all objects but every fs-th tile)
+    assert recomputed >= (qb.n_q + qb.n_c) // 2, recomputed
+    if prec == "fp32":
+        rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"])
+        assert rep.ok(), rep.summary()
+        fails = parity.check_candidates(sc, qb, t, l)
+        assert not fails, fails[:3]
+    else:
+        ref = oracle.batch(sc, qb, 10)
+        hits = sum(len(set(out["idx"][q].tolist()) & set(ref["idx"][q].tolist())) for q in range(qb.n_q))
+        assert hits / (10.0 * qb.n_q) >= 0.99

@@ -126,3 +126,31 @@ def test_graph_with_device_inputs(F, world):
     _same(dev_run(d_tgt, d_cemb, True), _run(F, ctx, v, F.PREC_FP32, graph=False))
     d_tgt2, d_cemb2 = d_tgt.clone(), d_cemb.clone()      # other buffers
     _same(dev_run(d_tgt2, d_cemb2, True), _run(F, ctx, v, F.PREC_FP32, graph=False))
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_pipelined_host_batches_with_async_topk(F, world, graph):
+    """Host embeddings travel on the copy stream into alternating slots and
+    FARM_ASYNC leaves the TopK copies enqueued: three batches of new contents
+    issued back to back, one farm_sync at the end, must give each batch's
+    synchronous result (pinned outputs, one set per batch)."""
+    import torch
+    ctx, scenes, qb = world
+    batches = [_variant(qb, seed) for seed in (21, 22, 23)]
+    ref = [_run(F, ctx, v, F.PREC_FP32, graph=False)[0] for v in batches]
+
+    def pinned(shape, dtype):
+        return torch.empty(shape, dtype=dtype).pin_memory().numpy()
+
+    outs = []
+    for v in batches:
+        o = dict(idx=pinned((v.n_q, 10), torch.int32), score=pinned((v.n_q, 10), torch.float32),
+                 pred=pinned((v.n_q, 10, 4), torch.float32), anchor=pinned((v.n_q, 10, 4), torch.int32))
+        h = F.farm_query_batch(ctx, v.scene_of_q, v.tgt_emb, v.tgt_cls, v.c_off, v.c_pred, v.c_emb, F.PREC_FP32,
+                               graph=graph)
+        F.farm_topk(ctx, h, 10, v.n_q, o["idx"], o["score"], o["pred"], o["anchor"], asynchronous=True)
+        outs.append(o)
+    F.farm_sync(ctx)
+    for o, r in zip(outs, ref):
+        for key in ("idx", "score", "pred", "anchor"):
+            np.testing.assert_array_equal(o[key], r[key], err_msg=key)

@@ -276,7 +276,7 @@ def test_autotuner_records_a_decision(F, world):
     F.farm_topk(ctx, h, 10, qb.n_q)
     dec = F.farm_sim_tuning(ctx)
     assert dec and all(0 <= d[3] < 3 for d in dec)
-    assert any(d[0] == 0 for d in dec)
+    assert any(d[0] % 10 == 0 for d in dec)
 
 
 def test_pinned_variant_gives_the_same_results(F, world):
