@@ -534,7 +534,7 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
             d_views = tmp_views;
         }
         ctx->c.launches += 1;
-        if ((e = farm::launch_prepare_views(d_views, n, n_views, ns.views, c.stream)) != cudaSuccess)
+        if ((e = farm::launch_prepare_views(d_views, ns.pos, n, n_views, ns.views, c.stream)) != cudaSuccess)
             return bailmem(e);
     }
     if (tmp_desc) cudaFreeAsync(tmp_desc, c.stream);
@@ -911,7 +911,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         CK(ws_get(ctx, farm::B_FUSE_TAU, (size_t)rows_total, &emit.tau_key));
         CK(ws_get(ctx, farm::B_FUSE_CNT, (size_t)rows_total, &emit.cnt));
         CK(ws_get(ctx, farm::B_FUSE_CAND, (size_t)rows_total * emit.cap, &emit.cand));
-        CK(ws_get(ctx, farm::B_FUSE_OVF, (size_t)rows_total + 1, &d_ovf));
+        CK(ws_get(ctx, farm::B_FUSE_OVF, 2 * (size_t)rows_total + 2, &d_ovf));
         CK(ws_get(ctx, farm::B_FUSE_SLAB, (size_t)farm::kFuseFallbackBlocks * round_up(max_n, 4), &d_slab));
         if (!reduced) CK(ws_get(ctx, farm::B_LSEL_COS, (size_t)std::max<int64_t>(n_c, 1) * stride_l, &lsel_cos));
         if (precision == FARM_PREC_LEARNED) {
@@ -1157,13 +1157,14 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                 // the exact recomputation of rows whose candidates overflowed
                 mark_end(ctx, m2);
                 const int m1b = mark_begin(ctx, 1);
-                CK(cudaMemsetAsync(d_ovf, 0, sizeof(int32_t), c.stream));
+                CK(cudaMemsetAsync(d_ovf, 0, 2 * sizeof(int32_t), c.stream));
                 LAUNCH(launch_variant(vsel, 1));
                 mark_end(ctx, m1b);
                 const int m2b = mark_begin(ctx, 2);
                 LAUNCH(farm::launch_fuse_final(dp, (int32_t)bt.np, bt.rows, sel_ti, sel_tc, sel_st, sel_li, sel_lc,
-                                               sel_sl, emit, d_ovf, d_ovf + 1, max_fkeep, c.stream));
-                LAUNCH(farm::launch_fuse_fallback(dp, (int32_t)bt.np, d_ovf, d_ovf + 1,
+                                               sel_sl, emit, d_ovf, d_ovf + 2, d_ovf + 1, d_ovf + 2 + rows_total,
+                                               max_fkeep, c.stream));
+                LAUNCH(farm::launch_fuse_fallback(dp, (int32_t)bt.np, d_ovf, d_ovf + 2,
                                                   precision == FARM_PREC_FP32 ? nullptr : ops.q32, ops.qhi, ops.qlo,
                                                   dim_pad, sel_ti, sel_tc, sel_st, sel_li, sel_lc, sel_sl, d_slab,
                                                   round_up(max_n, 4), farm::kFuseFallbackBlocks, c.d_fallback,

@@ -28,7 +28,7 @@ constexpr int kMaxAnchorCands = 256;
 // unit viewing direction f (3) and unit right vector r = f x z_up (2; its z
 // component is 0).  A view whose direction is zero or vertical has f = 0,
 // which no depth test passes (z_min >= 0).
-constexpr int kViewStride = 8;
+constexpr int kViewStride = 12;
 
 // Bits of the device error word.
 constexpr int kErrBadRow = 1;        // zero or non-finite embedding row
@@ -113,7 +113,7 @@ enum Buf {
     B_FUSE_TAU,     // uint32 [rows] per operand row: the fused selection's threshold key
     B_FUSE_CNT,     // int32 [rows] its appended candidate count
     B_FUSE_CAND,    // uint64 [rows, cap] its candidate words
-    B_FUSE_OVF,     // int32 [1 + rows] rows whose candidates overflowed (count, then launch rows)
+    B_FUSE_OVF,     // int32 [2 + 2 rows] overflow count, long-row count, overflowed launch rows, long launch rows
     B_FUSE_SLAB,    // float [blocks, n] the exact fallback's similarity rows
     B_RAW_PIPE,     // farm_query_batch's host rows: two slots, each [n_q + n_c, dim] (copy stream)
     B_COUNT
@@ -245,8 +245,11 @@ cudaError_t launch_normalize_rows(const float *src, const int32_t *dst_rows, int
 cudaError_t launch_quantize_fp8_rows(const float *src, int64_t rows, int32_t dim_pad, uint8_t *dst, float *scale,
                                      cudaStream_t s);
 
-// Pre-compute the per-view record of kViewStride floats from SoA views.
-cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_views,
+// Pre-compute the per-view record of kViewStride floats from SoA views and
+// the objects' centres pos [3, n]: {ox, oy, oz, fx, fy, fz, rx, ry} (origin,
+// unit forward, unit right in the ground plane), then the centre's depth Z_e
+// and image coordinate u_e in that view, and two zeros.
+cudaError_t launch_prepare_views(const float *views_soa, const float *pos, int64_t n, int32_t n_views,
                                  float *out, cudaStream_t s);
 
 // S[r, j] = <Q[r], D[j]> for r < rows, j < n (FP32 FMA, CUDA cores).
@@ -480,13 +483,16 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
 // fkeep) and appends the sample's entries reaching it; after the similarity
 // kernel appended the other tiles' entries, fuse_final writes each row's
 // final list of fkeep_t / fkeep_l entries from its buffer and records rows
-// whose candidates overflowed (count in *n_overflow, launch rows in overflow_rows).
+// whose candidates overflowed (count in *n_overflow, launch rows in
+// overflow_rows); rows of more than 1,024 candidates are listed in big_rows
+// (count in *n_big) and merged by a second launch of one-warp blocks.  Both
+// counts start at zero.
 cudaError_t launch_fuse_sample_tau(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,
                                    int64_t total_rows, int32_t s, const FuseEmit &emit, cudaStream_t st);
 cudaError_t launch_fuse_final(const Piece *pieces, int32_t n_pieces, int64_t total_rows, int32_t *tsel_idx,
                               float *tsel_cos, int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
-                              const FuseEmit &emit, int32_t *n_overflow, int32_t *overflow_rows, int32_t max_keep,
-                              cudaStream_t st);
+                              const FuseEmit &emit, int32_t *n_overflow, int32_t *overflow_rows, int32_t *n_big,
+                              int32_t *big_rows, int32_t max_keep, cudaStream_t st);
 
 // The exact fallback of the fused selection for the rows fuse_final recorded
 // (*n_overflow of them, launch rows in overflow_rows): a grid-stride loop of

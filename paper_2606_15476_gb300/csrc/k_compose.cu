@@ -41,61 +41,57 @@ __device__ __forceinline__ uint32_t order_key(float f)
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// The candidate's stored view v: origin o and unit forward f, unit right r
-// (x, y), as kViewStride floats {ox, oy, oz, fx, fy, fz, rx, ry}; e's own
-// depth Ze and image coordinate ue in that view are recomputed by each lane
-// (the lanes of one candidate read the same record).
-__device__ __forceinline__ void view_of(const float *__restrict__ ve, int v, float ex, float ey, float ez, float4 &o,
-                                        float4 &f, float &Ze, float &ue)
+// The relations' scale parameters as factors (a multiplication where the
+// definition divides by a constant), computed once per CTA.
+struct RelK {
+    float inv_tau_v, inv_tau_h, inv_tau_d, inv_on_gate;
+    float near_k, next_k, on_k;      // -1 / (2 sigma^2) of Near, NextTo, On's band
+    float z_min;
+};
+
+__device__ __forceinline__ RelK rel_k(const farm_params &p)
 {
-    o = __ldg(reinterpret_cast<const float4 *>(ve + v * kViewStride));        // ox, oy, oz, fx
-    f = __ldg(reinterpret_cast<const float4 *>(ve + v * kViewStride + 4));    // fy, fz, rx, ry
-    const float dex = ex - o.x, dey = ey - o.y, dez = ez - o.z;
-    Ze = dex * o.w + dey * f.x + dez * f.y;
-    ue = (dex * f.z + dey * f.w) / Ze;
+    RelK k;
+    k.inv_tau_v = 1.f / p.tau_v;
+    k.inv_tau_h = 1.f / p.tau_h;
+    k.inv_tau_d = 1.f / p.tau_d;
+    k.inv_on_gate = 1.f / p.on_gate;
+    k.near_k = -1.f / (2.f * p.sigma_near * p.sigma_near);
+    k.next_k = -1.f / (2.f * p.sigma_next * p.sigma_next);
+    k.on_k = -1.f / (2.f * p.on_band * p.on_band);
+    k.z_min = p.z_min;
+    return k;
 }
 
-// Left/right of landmark position (ax, ay, az) in the stored views ve of the
-// candidate at (ex, ey, ez) (sign +1: LeftOf, -1: RightOf): mean over the
-// views in which both lie deeper than z_min, 0.5 when none does.
-__device__ float viewpoint_lr(const float *__restrict__ ve, int n_views, float ex, float ey, float ez, float ax,
-                              float ay, float az, float sign, const farm_params &p)
+// The candidate's stored views ve, kViewStride floats each: {ox, oy, oz, fx},
+// {fy, fz, rx, ry} (origin, unit forward, unit right in the ground plane),
+// {Ze, ue, 0, 0} (the candidate's own depth and image coordinate there,
+// computed at upload).  Mean over the views in which both the candidate and
+// the landmark at (ax, ay, az) lie deeper than z_min of
+//   LR: sig(sign (u_a - u_e) / tau_h)  (sign +1 LeftOf, -1 RightOf)
+//   depth: sig(sign (Z_a - Z_e) / tau_d)  (sign +1 InFrontOf, -1 Behind)
+// and 0.5 when there is no such view.
+template <bool LR>
+__device__ float viewpoint(const float *__restrict__ ve, int n_views, float ax, float ay, float az, float sign,
+                           const RelK &k)
 {
     float acc = 0.f;
     int counted = 0;
     for (int v = 0; v < n_views; ++v) {
-        float4 o, f;
-        float Ze, ue;
-        view_of(ve, v, ex, ey, ez, o, f, Ze, ue);
-        if (!(Ze > p.z_min)) continue;
+        const float *r = ve + v * kViewStride;
+        const float2 zu = __ldg(reinterpret_cast<const float2 *>(r + 8));
+        if (!(zu.x > k.z_min)) continue;
+        const float4 o = __ldg(reinterpret_cast<const float4 *>(r));        // ox, oy, oz, fx
+        const float4 f = __ldg(reinterpret_cast<const float4 *>(r + 4));    // fy, fz, rx, ry
         const float dax = ax - o.x, day = ay - o.y, daz = az - o.z;
         const float Za = dax * o.w + day * f.x + daz * f.y;
-        if (!(Za > p.z_min)) continue;
-        const float ua = (dax * f.z + day * f.w) / Za;
-        acc += sigm(sign * (ua - ue) / p.tau_h);
-        ++counted;
-    }
-    return counted ? acc / (float)counted : 0.5f;
-}
-
-// Front/behind of landmark position (ax, ay, az) in the stored views of the
-// candidate (sign +1: InFrontOf, -1: Behind): mean over the views in which
-// both lie deeper than z_min, 0.5 when none does.
-__device__ float viewpoint_depth(const float *__restrict__ ve, int n_views, float ex, float ey, float ez, float ax,
-                                 float ay, float az, float sign, const farm_params &p)
-{
-    float acc = 0.f;
-    int counted = 0;
-    for (int v = 0; v < n_views; ++v) {
-        float4 o, f;
-        float Ze, ue;
-        view_of(ve, v, ex, ey, ez, o, f, Ze, ue);
-        (void)ue;
-        if (!(Ze > p.z_min)) continue;
-        const float dax = ax - o.x, day = ay - o.y, daz = az - o.z;
-        const float Za = dax * o.w + day * f.x + daz * f.y;
-        if (!(Za > p.z_min)) continue;
-        acc += sigm(sign * (Za - Ze) / p.tau_d);
+        if (!(Za > k.z_min)) continue;
+        if (LR) {
+            const float ua = (dax * f.z + day * f.w) / Za;
+            acc += sigm(sign * (ua - zu.y) * k.inv_tau_h);
+        } else {
+            acc += sigm(sign * (Za - zu.x) * k.inv_tau_d);
+        }
         ++counted;
     }
     return counted ? acc / (float)counted : 0.5f;
@@ -125,7 +121,7 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 // the line: sig(t / 0.1) sig((1 - t) / 0.1) exp(-d2 / (2 sigma_near^2)); 0 for
 // coincident landmarks.
 __device__ __forceinline__ float between_rel(float ex, float ey, float ez, const float *pp, const float *pq,
-                                             const farm_params &p)
+                                             const RelK &k)
 {
     // rel = e - a_p and seg = a_q - a_p exactly, each as a rounded part plus
     // its error (TwoSum): the landmarks of a Between may lie a hundred metres
@@ -152,7 +148,7 @@ __device__ __forceinline__ float between_rel(float ex, float ey, float ez, const
                ((rh[i] * sl[j] + rl[i] * sh[j]) - (rh[j] * sl[i] + rl[j] * sh[i]));
     }
     const float d2 = (c[0] * c[0] + c[1] * c[1] + c[2] * c[2]) / ss;
-    return sigm(t / 0.1f) * sigm((1.f - t) / 0.1f) * expf(-0.5f * d2 / (p.sigma_near * p.sigma_near));
+    return sigm(t / 0.1f) * sigm((1.f - t) / 0.1f) * expf(d2 * k.near_k);
 }
 
 // What a relation needs beyond the two objects: the candidate's stored views
@@ -170,7 +166,7 @@ struct RelCtx {
 // list (rank - 1), which decides membership of the Closest / Farthest set.
 __device__ __forceinline__ float relation(int pred, int32_t e, int ce, float ex, float ey, float ez, float esx,
                                           float esy, float esz, int32_t ai, float ax, float ay, float az, float asx,
-                                          float asy, float asz, const RelCtx &rc, const farm_params &p)
+                                          float asy, float asz, const RelCtx &rc, const RelK &k)
 {
     switch (pred) {
     case FARM_NEAR_H: {
@@ -233,26 +229,25 @@ __device__ __forceinline__ float relation(int pred, int32_t e, int ce, float ex,
         }
         return frac;
     }
-    case FARM_ABOVE: return sigm((ez - az) / p.tau_v);
-    case FARM_BELOW: return sigm((az - ez) / p.tau_v);
+    case FARM_ABOVE: return sigm((ez - az) * k.inv_tau_v);
+    case FARM_BELOW: return sigm((az - ez) * k.inv_tau_v);
     case FARM_NEAR:
     case FARM_NEXT_TO: {
         const float dx = ex - ax, dy = ey - ay, dz = ez - az;
         const float d2 = dx * dx + dy * dy + dz * dz;
-        const float sg = pred == FARM_NEAR ? p.sigma_near : p.sigma_next;
-        return expf(-d2 / (2.f * sg * sg));
+        return expf(d2 * (pred == FARM_NEAR ? k.near_k : k.next_k));
     }
     case FARM_ON: {
         const float dx = ex - ax, dy = ey - ay;
         const float rho = 0.5f * fmaxf(asx, asy);
-        const float gate = sigm((rho - sqrtf(dx * dx + dy * dy)) / p.on_gate);
+        const float gate = sigm((rho - sqrtf(dx * dx + dy * dy)) * k.inv_on_gate);
         const float gap = (ez - 0.5f * esz) - (az + 0.5f * asz);
-        return gate * expf(-gap * gap / (2.f * p.on_band * p.on_band));
+        return gate * expf(gap * gap * k.on_k);
     }
-    case FARM_LEFT_OF: return viewpoint_lr(rc.ve, rc.n_views, ex, ey, ez, ax, ay, az, 1.f, p);
-    case FARM_RIGHT_OF: return viewpoint_lr(rc.ve, rc.n_views, ex, ey, ez, ax, ay, az, -1.f, p);
-    case FARM_IN_FRONT_OF: return viewpoint_depth(rc.ve, rc.n_views, ex, ey, ez, ax, ay, az, 1.f, p);
-    case FARM_BEHIND: return viewpoint_depth(rc.ve, rc.n_views, ex, ey, ez, ax, ay, az, -1.f, p);
+    case FARM_LEFT_OF: return viewpoint<true>(rc.ve, rc.n_views, ax, ay, az, 1.f, k);
+    case FARM_RIGHT_OF: return viewpoint<true>(rc.ve, rc.n_views, ax, ay, az, -1.f, k);
+    case FARM_IN_FRONT_OF: return viewpoint<false>(rc.ve, rc.n_views, ax, ay, az, 1.f, k);
+    case FARM_BEHIND: return viewpoint<false>(rc.ve, rc.n_views, ax, ay, az, -1.f, k);
     case FARM_CLOSEST:
     case FARM_FARTHEST: {
         if (ce >= rc.kc) return 0.f;                // e is not in the candidate set
@@ -280,13 +275,14 @@ constexpr int WARPS = TH / 32;
 // RM, landmark list KM and Closest /
 // Farthest set KC; every section starts on a 16-byte boundary.
 struct ComposeSmem {
-    size_t best, key, lm_pos, lm_size, cset_pos, lm_idx, cand_e, ssem, surv, bytes;
+    size_t best, key, sv, lm_pos, lm_size, cset_pos, lm_idx, cand_e, ssem, surv, bytes;
     __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
     __host__ __device__ ComposeSmem(int RM, int KM, int KC)
     {
         size_t o = 0;
         best = o;   o = up16(o + (size_t)RM * FARM_MAX_CONSTRAINTS * 8);
         key = o;    o = up16(o + (size_t)RM * 8);
+        sv = o;     o = up16(o + (size_t)RM * 32);
         lm_pos = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
         lm_size = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
         cset_pos = o; o = up16(o + (size_t)KC * 3 * 4);
@@ -306,6 +302,8 @@ compose_kernel(ComposeArgs a, int32_t KC)
     const ComposeSmem L(RM, KM, KC);
     unsigned long long *best = reinterpret_cast<unsigned long long *>(sm + L.best);   // [RM][4]
     uint64_t *key = reinterpret_cast<uint64_t *>(sm + L.key);
+    // per survivor: {ex, ey, ez, esx}, {esy, esz, e, list position}
+    float4 *sv = reinterpret_cast<float4 *>(sm + L.sv);                               // [RM][2]
     float *lm_pos = reinterpret_cast<float *>(sm + L.lm_pos);                         // [4][KM][3]
     float *lm_size = reinterpret_cast<float *>(sm + L.lm_size);                       // [4][KM][3]
     float *cset_pos = reinterpret_cast<float *>(sm + L.cset_pos);                     // [KC][3]
@@ -334,20 +332,10 @@ compose_kernel(ComposeArgs a, int32_t KC)
     const farm_params p = a.p;
     const int kc = min(min(p.k_closest, R), KC);     // the Closest / Farthest set: target ranks 1..kc
 
+    const RelK K = rel_k(p);
+
     // (an index outside the scene never reaches a memory access: such a
     // landmark is skipped and such a candidate never survives)
-    for (int t = tid; t < m * klm; t += TH) {
-        const int i = t / klm, l = t - i * klm;
-        int32_t ai = a.lsel_idx[(c0 + i) * a.stride_l + l];
-        if (ai < 0 || ai >= sd.n) ai = -1;
-        lm_idx[i * KM + l] = ai;
-        lm_pos[(i * KM + l) * 3 + 0] = ai >= 0 ? sd.pos[ai] : 0.f;
-        lm_pos[(i * KM + l) * 3 + 1] = ai >= 0 ? sd.pos[sd.n + ai] : 0.f;
-        lm_pos[(i * KM + l) * 3 + 2] = ai >= 0 ? sd.pos[2 * sd.n + ai] : 0.f;
-        lm_size[(i * KM + l) * 3 + 0] = ai >= 0 ? sd.size[ai] : 0.f;
-        lm_size[(i * KM + l) * 3 + 1] = ai >= 0 ? sd.size[sd.n + ai] : 0.f;
-        lm_size[(i * KM + l) * 3 + 2] = ai >= 0 ? sd.size[2 * sd.n + ai] : 0.f;
-    }
     const int32_t *cand = a.tsel_idx + q * a.stride_t;
     for (int c = tid; c < R; c += TH) {
         const int32_t e = cand[c];
@@ -361,10 +349,24 @@ compose_kernel(ComposeArgs a, int32_t KC)
             cset_pos[3 * c + 2] = ok ? sd.pos[2 * sd.n + e] : 0.f;
         }
     }
+    for (int x = tid; x < R * FARM_MAX_CONSTRAINTS; x += TH) best[x] = 0ull;
     if (tid == 0) { s_thr = 0.f; s_ns = 0; }
     __syncthreads();
-    // S_K = the k_max-th largest s_sem; candidates below (1 - w) S_K cannot
-    // reach the TopK (k_max candidates score at least (1 - w) S_K).
+    // the landmark lists; S_K = the k_max-th largest s_sem (each candidate's
+    // rank counted against the others): candidates below (1 - w) S_K cannot
+    // reach the TopK (k_max candidates score at least (1 - w) S_K)
+    for (int t = tid; t < m * klm; t += TH) {
+        const int i = t / klm, l = t - i * klm;
+        int32_t ai = a.lsel_idx[(c0 + i) * a.stride_l + l];
+        if (ai < 0 || ai >= sd.n) ai = -1;
+        lm_idx[i * KM + l] = ai;
+        lm_pos[(i * KM + l) * 3 + 0] = ai >= 0 ? sd.pos[ai] : 0.f;
+        lm_pos[(i * KM + l) * 3 + 1] = ai >= 0 ? sd.pos[sd.n + ai] : 0.f;
+        lm_pos[(i * KM + l) * 3 + 2] = ai >= 0 ? sd.pos[2 * sd.n + ai] : 0.f;
+        lm_size[(i * KM + l) * 3 + 0] = ai >= 0 ? sd.size[ai] : 0.f;
+        lm_size[(i * KM + l) * 3 + 1] = ai >= 0 ? sd.size[sd.n + ai] : 0.f;
+        lm_size[(i * KM + l) * 3 + 2] = ai >= 0 ? sd.size[2 * sd.n + ai] : 0.f;
+    }
     if (R > p.k_max) {
         for (int c = tid; c < R; c += TH) {
             const float v = ssem[c];
@@ -379,15 +381,18 @@ compose_kernel(ComposeArgs a, int32_t KC)
     __syncthreads();
     const float thr = s_thr;
     for (int c = tid; c < R; c += TH) {
-        if (ssem[c] >= thr && cand_e[c] >= 0) {
+        const int32_t e = cand_e[c];
+        if (ssem[c] >= thr && e >= 0) {
             const int pos = atomicAdd(&s_ns, 1);
             surv[pos] = (uint16_t)c;
+            sv[2 * pos] = make_float4(__ldg(sd.pos + e), __ldg(sd.pos + sd.n + e), __ldg(sd.pos + 2 * sd.n + e),
+                                      __ldg(sd.size + e));
+            sv[2 * pos + 1] = make_float4(__ldg(sd.size + sd.n + e), __ldg(sd.size + 2 * sd.n + e),
+                                          __int_as_float(e), __int_as_float(c));
         }
     }
     __syncthreads();
     const int ns = s_ns;
-    for (int x = tid; x < ns * FARM_MAX_CONSTRAINTS; x += TH) best[x] = 0ull;
-    __syncthreads();
     // best witness per (survivor, constraint): for one constraint at a time
     // (so that a warp evaluates one predicate and its lanes do not diverge on
     // it) the lanes take consecutive (survivor, landmark) pairs; the best
@@ -397,6 +402,7 @@ compose_kernel(ComposeArgs a, int32_t KC)
     // shared-memory atomics.  r >= 0, so its bits order like the float, and a
     // zero word means no witness.
     const bool pow2 = klm <= 32 && (klm & (klm - 1)) == 0;
+    const int lk = pow2 ? __ffs(klm) - 1 : 0;
     const int pairs = ns * klm;
     for (int i = 0; i < m; ++i) {
         const int pr = pred_of(i);
@@ -406,20 +412,19 @@ compose_kernel(ComposeArgs a, int32_t KC)
             int sidx = 0;
             uint32_t h = 0u, lo = 0u;
             if (t < pairs) {
-                sidx = t / klm;
+                sidx = pow2 ? t >> lk : t / klm;
                 const int l = t - sidx * klm;
-                const int ce = surv[sidx];
-                const int32_t e = cand_e[ce];
+                const float4 sa = sv[2 * sidx], sb = sv[2 * sidx + 1];
+                const int32_t e = __float_as_int(sb.z);
+                const int ce = __float_as_int(sb.w);
                 const int32_t ai = lm_idx[i * KM + l];
                 if (ai >= 0 && ai != e) {
-                    const float ex = __ldg(sd.pos + e), ey = __ldg(sd.pos + sd.n + e), ez = __ldg(sd.pos + 2 * sd.n + e);
-                    const float esx = __ldg(sd.size + e), esy = __ldg(sd.size + sd.n + e),
-                                esz = __ldg(sd.size + 2 * sd.n + e);
+                    const float ex = sa.x, ey = sa.y, ez = sa.z, esx = sa.w, esy = sb.x, esz = sb.y;
                     const float *ap = lm_pos + (i * KM + l) * 3;
                     const float *as = lm_size + (i * KM + l) * 3;
                     const RelCtx rc{sd.views + (int64_t)e * sd.n_views * kViewStride, sd.n_views, cand_e, cset_pos, kc};
                     const float r = relation(pr, e, ce, ex, ey, ez, esx, esy, esz, ai, ap[0], ap[1], ap[2], as[0],
-                                             as[1], as[2], rc, p);
+                                             as[1], as[2], rc, K);
                     h = __float_as_uint(r);
                     lo = 0xffffffffu - (uint32_t)ai;
                 }
@@ -444,8 +449,9 @@ compose_kernel(ComposeArgs a, int32_t KC)
     for (int c = 0; c + 1 < m; ++c) any_between |= pred_of(c) == FARM_BETWEEN;
     if (any_between) {
         for (int pos = warp; pos < ns; pos += WARPS) {
-            const int32_t e = cand_e[surv[pos]];
-            const float ex = sd.pos[e], ey = sd.pos[sd.n + e], ez = sd.pos[2 * sd.n + e];
+            const float4 sa = sv[2 * pos];
+            const int32_t e = __float_as_int(sv[2 * pos + 1].z);
+            const float ex = sa.x, ey = sa.y, ez = sa.z;
             for (int c = 0; c + 1 < m; ++c) {
                 if (pred_of(c) != FARM_BETWEEN) continue;
                 uint32_t h = 0u, wp = 0u, wq = 0u;
@@ -453,7 +459,7 @@ compose_kernel(ComposeArgs a, int32_t KC)
                     const int x = t / klm, y = t - x * klm;
                     const int32_t ap = lm_idx[c * KM + x], aq = lm_idx[(c + 1) * KM + y];
                     if (ap < 0 || aq < 0 || ap == e || aq == e || ap == aq) continue;
-                    const float r = between_rel(ex, ey, ez, lm_pos + (c * KM + x) * 3, lm_pos + ((c + 1) * KM + y) * 3, p);
+                    const float r = between_rel(ex, ey, ez, lm_pos + (c * KM + x) * 3, lm_pos + ((c + 1) * KM + y) * 3, K);
                     const uint32_t rh = __float_as_uint(r), lp = 0xffffffffu - (uint32_t)ap,
                                    lq = 0xffffffffu - (uint32_t)aq;
                     if (rh > h || (rh == h && (lp > wp || (lp == wp && lq > wq)))) { h = rh; wp = lp; wq = lq; }

@@ -101,10 +101,21 @@ __device__ __forceinline__ RowList row_list(const Piece &pc, int64_t b, int32_t 
 // resident to hide the loads' latency).
 constexpr int TAU_KEYS = 1024;
 constexpr int TAU_WARPS = 4;
+// Bits resolved by sample_tau's searches below the leading bits that the
+// smallest and largest key share.  A threshold only has to be a lower bound
+// of the row's R-th largest value, and a search stopped early returns one;
+// 14 bits leave it within about 2^-12 (relative) of the exact R-th key,
+// where a row holds few entries.
+constexpr int TAU_BITS = 14;
 
-// The R-th largest of n keys in shared memory (n >= R >= 1): a bitwise search
-// below the leading bits the smallest and largest share.
-__device__ __forceinline__ uint32_t warp_kth_key(const uint32_t *keys, int n, int R, int lane)
+// A lower bound of the R-th largest of n keys in shared memory (n >= R >= 1):
+// the largest key T with at least R keys >= T among those whose bits below
+// the shared leading bits are resolved to the first `bits` -- the exact R-th
+// key when bits covers them all.  Stops as soon as exactly R keys reach the
+// candidate (no further bit changes which keys do).  Never returns a key
+// below that of -FLT_MAX other than 0 (every entry passes), so that its float
+// value is a number.
+__device__ __forceinline__ uint32_t warp_kth_lower(const uint32_t *keys, int n, int R, int bits, int lane)
 {
     uint32_t kmin = 0xffffffffu, kmax = 0u;
     for (int j = lane; j < n; j += 32) {
@@ -116,13 +127,31 @@ __device__ __forceinline__ uint32_t warp_kth_key(const uint32_t *keys, int n, in
     const uint32_t diff = kmin ^ kmax;
     const int top = diff ? 31 - __clz(diff) : -1;
     uint32_t T = top < 0 ? kmin : (top == 31 ? 0u : kmin & ~((2u << top) - 1u));
-    for (int bit = top; bit >= 0; --bit) {
+    const int stop = top - bits;
+    for (int bit = top; bit >= 0 && bit > stop; --bit) {
         const uint32_t c = T | (1u << bit);
         int cnt = 0;
         for (int j = lane; j < n; j += 32) cnt += keys[j] >= c ? 1 : 0;
-        if (__reduce_add_sync(0xffffffffu, cnt) >= R) T = c;
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (cnt >= R) {
+            T = c;
+            if (cnt == R) break;
+        }
     }
-    return T;
+    return T < 0x00800000u ? 0u : T;
+}
+
+// Eight consecutive sample values of a lane from j (16-byte aligned), zero past n.
+__device__ __forceinline__ void load8(const float *__restrict__ row, int j, int n, float (&x)[8])
+{
+    if (j + 8 <= n) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(row + j));
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(row + j + 4));
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = c.x; x[5] = c.y; x[6] = c.z; x[7] = c.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = j + u < n ? __ldg(row + j + u) : 0.f;
+    }
 }
 
 __global__ void __launch_bounds__(TAU_WARPS * 32)
@@ -140,6 +169,10 @@ sample_tau_kernel(const float *__restrict__ S, const float *__restrict__ tops, c
     const int n = pc.n;                        // valid entries of the sample row
     const float *row = S + pc.s_off + (int64_t)i * pc.ld;
     uint32_t *kw = keys[warp];
+    // the scan's first 16 values per lane are in flight during the search
+    float xa[8], xb[8];
+    load8(row, lane * 8, n, xa);
+    load8(row, 256 + lane * 8, n, xb);
     const int G = (int)group_count(n, pc.gshift);
     uint32_t T = 0u;                           // key 0: every entry passes
     if (G >= R) {
@@ -148,66 +181,60 @@ sample_tau_kernel(const float *__restrict__ S, const float *__restrict__ tops, c
 #pragma unroll 4
         for (int j = lane; j < g; j += 32) kw[j] = order_key(__ldg(tp + j));
         __syncwarp();
-        T = warp_kth_key(kw, g, R, lane);
+        T = warp_kth_lower(kw, g, R, TAU_BITS, lane);
     } else if (n >= R) {
         const int g = min(n, TAU_KEYS);
 #pragma unroll 4
         for (int j = lane; j < g; j += 32) kw[j] = order_key(__ldg(row + j));
         __syncwarp();
-        T = g >= R ? warp_kth_key(kw, g, R, lane) : 0u;
+        T = g >= R ? warp_kth_lower(kw, g, R, TAU_BITS, lane) : 0u;
     }
-    // the sample's own entries >= tau (their positions mapped to objects),
-    // their keys also staged: 8 consecutive entries per lane and step (two
-    // float4 loads; the row starts on a 16-byte boundary), places by a warp
-    // prefix sum of the lanes' counts
     __syncwarp();
+    // the sample's own entries >= tau (their positions mapped to objects),
+    // their keys also staged: 8 consecutive entries per lane and chunk, the
+    // next chunk's loads issued before this one's entries are placed; each
+    // round places one entry of every lane that still holds one (a warp
+    // ballot gives the places), so a chunk takes as many rounds as its
+    // busiest lane has entries -- usually one or none
+    const bool all = T == 0u;
+    const float tf = key_value(T);             // entries >= tf are those whose key is >= T
+    const uint32_t lt = (1u << lane) - 1u;
     uint64_t *dst = emit.cand + grow * (int64_t)emit.cap;
     int cnt = 0;
-#pragma unroll 2
     for (int j0 = 0; j0 < n; j0 += 256) {
         const int jb = j0 + lane * 8;
-        float x[8];
-        if (jb + 8 <= n) {
-            const float4 a = __ldg(reinterpret_cast<const float4 *>(row + jb));
-            const float4 c = __ldg(reinterpret_cast<const float4 *>(row + jb + 4));
-            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = c.x; x[5] = c.y; x[6] = c.z; x[7] = c.w;
-        } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = jb + u < n ? __ldg(row + jb + u) : 0.f;
-        }
         uint32_t take = 0u;
-        int mine = 0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const bool t = jb + u < n && order_key(x[u]) >= T;
-            take |= t ? (1u << u) : 0u;
-            mine += t ? 1 : 0;
-        }
-        int incl = mine;
+        for (int u = 0; u < 8; ++u) take |= (jb + u < n && (all || xa[u] >= tf)) ? (1u << u) : 0u;
+        float cur[8];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int pos = cnt + incl - mine;
+        for (int u = 0; u < 8; ++u) cur[u] = xa[u];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            if ((take >> u) & 1u) {
+        for (int u = 0; u < 8; ++u) xa[u] = xb[u];
+        if (j0 + 512 < n) load8(row, j0 + 512 + lane * 8, n, xb);
+        while (__any_sync(0xffffffffu, take != 0u)) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, take != 0u);
+            if (take) {
+                const int u = __ffs(take) - 1;
+                take &= take - 1u;
+                float v = cur[0];
+#pragma unroll
+                for (int w = 1; w < 8; ++w) v = u == w ? cur[w] : v;
+                const int pos = cnt + __popc(bal & lt);
                 const int j = jb + u;
-                const uint32_t k = order_key(x[u]);
+                const uint32_t k = order_key(v);
                 const int32_t obj = (j >> 8) * s * 256 + (j & 255);
                 if (pos < emit.cap) dst[pos] = ((uint64_t)k << 32) | (uint64_t)(0xffffffffu - (uint32_t)obj);
                 if (pos < TAU_KEYS) kw[pos] = k;
-                ++pos;
             }
+            cnt += __popc(bal);
         }
-        cnt += __shfl_sync(0xffffffffu, incl, 31);
     }
     __syncwarp();
     // the threshold for the other tiles: the R-th largest of the sample's
     // entries themselves (at least tau, still at most the row's R-th value),
     // which keeps fewer of the other tiles' entries than the group bound
-    if (T != 0u && cnt > R && cnt <= TAU_KEYS) T = warp_kth_key(kw, cnt, R, lane);
+    if (T != 0u && cnt > R && cnt <= TAU_KEYS) T = max(T, warp_kth_lower(kw, cnt, R, TAU_BITS, lane));
     if (lane == 0) {
         emit.tau_key[grow] = T;
         emit.cnt[grow] = cnt;
@@ -257,7 +284,10 @@ __device__ __forceinline__ void merge_row(const RowList &L, int ms, int total, c
 #pragma unroll
             for (int k = 0; k < REG; ++k) n += (uint32_t)(w[k] >> 32) >= c ? 1 : 0;
             n = __reduce_add_sync(0xffffffffu, n);
-            if (n >= keep) T = c;
+            if (n >= keep) {
+                T = c;
+                if (n == keep) break;     // no lower bit changes which words reach T
+            }
         }
     }
     // collect the words at or above T (the keep best and their key ties)
@@ -286,39 +316,62 @@ __device__ __forceinline__ void merge_row(const RowList &L, int ms, int total, c
     }
 }
 
-// A row merges at most MAXW = 32 MAXR words (sample list + appended); FW
-// warps (rows) per block; each row uses the fewest registers its words need.
-template <int MAXR, int FW>
+// Rows of at most FINAL_SMALL words merge in fuse_final_kernel, FW warps
+// (rows) per block, each row in the fewest registers its words need; a longer
+// row (up to the buffer's capacity) is listed for fuse_final_big_kernel, whose
+// warps hold up to 64 words a lane -- so that the common rows run at the
+// occupancy of their own register count.
+constexpr int FINAL_SMALL = 1024;
+constexpr int FINAL_BIG_BLOCKS = 152;
+
+template <int FW>
 __global__ void __launch_bounds__(FW * 32)
 fuse_final_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, int64_t total_rows, int32_t *tsel_idx,
                   float *tsel_cos, int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
-                  FuseEmit emit, int32_t *n_overflow, int32_t *overflow_rows)
+                  FuseEmit emit, int32_t *n_overflow, int32_t *overflow_rows, int32_t *n_big, int32_t *big_rows)
 {
-    constexpr int MAXW = MAXR * 32;
-    __shared__ uint64_t coll[FW][MAXW];
+    __shared__ uint64_t coll[FW][FINAL_SMALL];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t b = (int64_t)blockIdx.x * FW + warp;
     if (b >= total_rows) return;
     const Piece pc = pieces[warp_find_piece(pieces, n_pieces, b)];
     const RowList L = row_list(pc, b, tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos, stride_l);
-    const int32_t cnt = emit.cnt[L.grow];
-    const int ms = 0;       // (every candidate is in the buffer)
-    const int64_t total = cnt;
-    if (cnt > emit.cap || total > MAXW) {
-        // more candidates than the buffer or the merge holds: the exact fallback recomputes the row
+    const int32_t t = emit.cnt[L.grow];
+    if (t > FINAL_SMALL) {
+        // more candidates than the buffer holds: the exact fallback recomputes
+        // the row; else the merge of long rows takes it
         if (lane == 0) {
-            const int pos = atomicAdd(n_overflow, 1);
-            overflow_rows[pos] = (int32_t)b;
+            if (t > emit.cap) overflow_rows[atomicAdd(n_overflow, 1)] = (int32_t)b;
+            else big_rows[atomicAdd(n_big, 1)] = (int32_t)b;
         }
         return;
     }
     const uint64_t *cand = emit.cand + L.grow * (int64_t)emit.cap;
-    const int t = (int)total;
-    if (t <= 128) merge_row<4>(L, ms, t, cand, coll[warp], lane);
-    else if (t <= 256) merge_row<8>(L, ms, t, cand, coll[warp], lane);
-    else if (t <= 512) merge_row<16>(L, ms, t, cand, coll[warp], lane);
-    else if (MAXR <= 32 || t <= 1024) merge_row<(MAXR < 32 ? MAXR : 32)>(L, ms, t, cand, coll[warp], lane);
-    else merge_row<MAXR>(L, ms, t, cand, coll[warp], lane);
+    if (t <= 128) merge_row<4>(L, 0, t, cand, coll[warp], lane);
+    else if (t <= 256) merge_row<8>(L, 0, t, cand, coll[warp], lane);
+    else if (t <= 512) merge_row<16>(L, 0, t, cand, coll[warp], lane);
+    else merge_row<FINAL_SMALL / 32>(L, 0, t, cand, coll[warp], lane);
+}
+
+// The listed long rows (*n_big of them), a grid-stride loop of one-warp
+// blocks; returns at once when none is listed.
+template <int MAXR>
+__global__ void __launch_bounds__(32)
+fuse_final_big_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, int32_t *tsel_idx, float *tsel_cos,
+                      int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l, FuseEmit emit,
+                      const int32_t *__restrict__ n_big, const int32_t *__restrict__ big_rows)
+{
+    __shared__ uint64_t coll[MAXR * 32];
+    const int lane = threadIdx.x;
+    const int count = *n_big;
+    for (int k = blockIdx.x; k < count; k += gridDim.x) {
+        const int64_t b = big_rows[k];
+        const Piece pc = pieces[warp_find_piece(pieces, n_pieces, b)];
+        const RowList L = row_list(pc, b, tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos, stride_l);
+        const int32_t t = emit.cnt[L.grow];
+        merge_row<MAXR>(L, 0, t, emit.cand + L.grow * (int64_t)emit.cap, coll, lane);
+        __syncwarp();
+    }
 }
 
 constexpr int FB_TH = 256;
@@ -424,18 +477,23 @@ int fuse_merge_capacity(int32_t) { return 2048; }
 
 cudaError_t launch_fuse_final(const Piece *pieces, int32_t n_pieces, int64_t total_rows, int32_t *tsel_idx,
                               float *tsel_cos, int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
-                              const FuseEmit &emit, int32_t *n_overflow, int32_t *overflow_rows, int32_t max_keep,
-                              cudaStream_t st)
+                              const FuseEmit &emit, int32_t *n_overflow, int32_t *overflow_rows, int32_t *n_big,
+                              int32_t *big_rows, int32_t max_keep, cudaStream_t st)
 {
     if (total_rows <= 0) return cudaSuccess;
     if (n_pieces < 1 || !tsel_cos || !lsel_cos || !emit.cnt || !emit.cand || !n_overflow || !overflow_rows ||
-        max_keep < 1 || max_keep > kMaxTargetCands)
+        !n_big || !big_rows || max_keep < 1 || max_keep > kMaxTargetCands || emit.cap > 64 * 32)
         return cudaErrorInvalidValue;
-    const int64_t blocks = (total_rows + 1) / 2;
+    constexpr int FW = 4;
+    const int64_t blocks = (total_rows + FW - 1) / FW;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    fuse_final_kernel<64, 2><<<(unsigned)blocks, 64, 0, st>>>(pieces, n_pieces, total_rows, tsel_idx, tsel_cos,
-                                                             stride_t, lsel_idx, lsel_cos, stride_l, emit,
-                                                             n_overflow, overflow_rows);
+    fuse_final_kernel<FW><<<(unsigned)blocks, FW * 32, 0, st>>>(pieces, n_pieces, total_rows, tsel_idx, tsel_cos,
+                                                                stride_t, lsel_idx, lsel_cos, stride_l, emit,
+                                                                n_overflow, overflow_rows, n_big, big_rows);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fuse_final_big_kernel<64><<<FINAL_BIG_BLOCKS, 32, 0, st>>>(pieces, n_pieces, tsel_idx, tsel_cos, stride_t,
+                                                                lsel_idx, lsel_cos, stride_l, emit, n_big, big_rows);
     return cudaGetLastError();
 }
 

@@ -56,8 +56,8 @@ __global__ void normalize_rows_kernel(const float *__restrict__ src, const int32
 }
 
 // One thread per (object, view).
-__global__ void prepare_views_kernel(const float *__restrict__ v, int64_t n, int32_t n_views,
-                                     float *__restrict__ out)
+__global__ void prepare_views_kernel(const float *__restrict__ v, const float *__restrict__ pos, int64_t n,
+                                     int32_t n_views, float *__restrict__ out)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * n_views) return;
@@ -81,10 +81,16 @@ __global__ void prepare_views_kernel(const float *__restrict__ v, int64_t n, int
     } else {
         fx = fy = fz = 0.f;
     }
+    // the object's own depth and image coordinate in this view, which every
+    // relation of the object against a landmark in this view compares with
+    const float dex = pos[j] - ox, dey = pos[n + j] - oy, dez = pos[2 * n + j] - oz;
+    const float ze = dex * fx + dey * fy + dez * fz;
+    const float ue = (dex * rx + dey * ry) / ze;
     float *o = out + t * kViewStride;
     o[0] = ox; o[1] = oy; o[2] = oz;
     o[3] = fx; o[4] = fy; o[5] = fz;
     o[6] = rx; o[7] = ry;
+    o[8] = ze; o[9] = ue; o[10] = 0.f; o[11] = 0.f;
 }
 
 // One warp per unit row: scale = max|x| / 448 (the largest finite E4M3
@@ -135,13 +141,13 @@ cudaError_t launch_normalize_rows(const float *src, const int32_t *dst_rows, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_prepare_views(const float *views_soa, int64_t n, int32_t n_views, float *out,
+cudaError_t launch_prepare_views(const float *views_soa, const float *pos, int64_t n, int32_t n_views, float *out,
                                  cudaStream_t s)
 {
     const int64_t total = n * n_views;
     if (total <= 0) return cudaSuccess;
     const int th = 256;
-    prepare_views_kernel<<<(unsigned)((total + th - 1) / th), th, 0, s>>>(views_soa, n, n_views, out);
+    prepare_views_kernel<<<(unsigned)((total + th - 1) / th), th, 0, s>>>(views_soa, pos, n, n_views, out);
     return cudaGetLastError();
 }
 
