@@ -101,7 +101,7 @@ typedef enum {
 #define FARM_GRAPH 2u         /* farm_query_batch: run the batch's device work as a CUDA graph (see there) */
 #define FARM_UNFUSED 4u       /* farm_query_batch: write the whole similarity block and select from it (see there) */
 #define FARM_ASYNC 8u         /* farm_topk with host outputs: do not synchronise (see there) */
-#define FARM_FUSED 16u        /* farm_query_batch: the fused rank selection also for FARM_PREC_BF16 (see there) */
+#define FARM_FUSED 16u        /* farm_query_batch: the fused rank selection for every scene (see there) */
 
 /*
  * The method's constants.  mu = 5 (reciprocal-rank offset), w = 0.5 (blend
@@ -210,17 +210,19 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
  *              Re-uploading a scene, changing the prefilter weights or growing
  *              a work buffer starts new captures.  At most 8 graphs are kept
  *              (least recently used go).
- *              FARM_UNFUSED / FARM_FUSED: whether FARM_PREC_FP32 and
- *              FARM_PREC_BF16 select the ranks from the whole similarity
- *              block written to memory (as FP8 and the learned path always
- *              do; the default for BF16) or by the fused selection (the
- *              default for FP32), which writes only a sample of each
- *              row (every s-th tile of 256 objects), takes the row's
- *              threshold from the sample's ranks and has the similarity
- *              kernel keep only the entries reaching it (rows whose kept
- *              entries overflow their buffer are recomputed exactly).  Both
- *              give the same ranks; the defaults are the faster ones measured
- *              on a 20,000-object scene.
+ *              FARM_UNFUSED / FARM_FUSED: whether the rows of a scene
+ *              select their ranks from the whole similarity block written
+ *              to memory (as FP8 and the learned path always do) or by the
+ *              fused selection, which writes only a sample of each row
+ *              (every s-th tile of 256 objects), takes the row's threshold
+ *              from the sample's ranks and has the similarity kernel keep
+ *              only the entries reaching it (rows whose kept entries
+ *              overflow their buffer are recomputed exactly).  FARM_FUSED
+ *              fuses every scene of a FARM_PREC_FP32 or FARM_PREC_BF16
+ *              batch, FARM_UNFUSED none; by default FARM_PREC_FP32 fuses
+ *              the scenes whose sample holds at least 16 times the target
+ *              list (about 12,000 objects and more) and FARM_PREC_BF16
+ *              none, the faster choices measured.  All give the same ranks.
  *   batch_handle  receives the handle that farm_topk takes
  * Only target candidates whose rank r can still place them in the top k_max
  * are scored: a candidate scores at most 1/(mu + r) while k_max objects score

@@ -752,7 +752,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     //      merge) for the others; then one FP32 rescore launch on the
     //      reduced-precision paths
     struct Batch { size_t p0 = 0, np = 0; int64_t s_floats = 0, rows = 0, blocks = 0, tblocks = 0, tmp = 0,
-                   tops = 0; int32_t smem_sel = 1, smem_merge = 0, max_union = 1; bool chunked = false; };
+                   tops = 0, fused_rows = 0; int32_t smem_sel = 1, smem_merge = 0, max_union = 1;
+                   bool chunked = false; };
     std::vector<farm::Piece> pieces;
     std::vector<int32_t> piece_sid;
     std::vector<Batch> batches;
@@ -771,17 +772,28 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     // (FP32 and BF16 only: E4M3's few significant bits tie many FP8 entries at
     // any threshold, and the learned path's lists of 512 would need a sample
     // of half the row and still crowd the buffer)
-    // The default is the faster configuration measured on the 20,000-object
-    // site: fused for FP32 (the similarity stage gains what the threshold and
-    // merge cost, and S is never written), unfused for BF16 (its lists of 256
-    // make the sample's threshold and the merge cost more than the stores of S)
-    const bool fusable = (precision == FARM_PREC_FP32 || precision == FARM_PREC_BF16) && c.pinned_variant != 1;
-    const bool fused = fusable && !(flags & FARM_UNFUSED) &&
-                       ((flags & FARM_FUSED) || precision == FARM_PREC_FP32);
+    // Which scenes' rows are fused: FARM_FUSED fuses every scene, FARM_UNFUSED
+    // none; by default the FP32 path fuses a scene whose sample holds at
+    // least 16 times its target list (a shorter sample sets a threshold that
+    // lets a large part of the other tiles through, whose appends then cost
+    // more than storing the row), and BF16 none (measured on a 20,000-object
+    // scene: with its lists of 256 the threshold and the merge cost more
+    // than the stores of S).  A batch may hold fused and unfused scenes.
+    const bool fusable = (precision == FARM_PREC_FP32 || precision == FARM_PREC_BF16) && c.pinned_variant != 1 &&
+                         !(flags & FARM_UNFUSED);
     const int32_t keep_max = reduced ? std::max(cstride_t, cstride_l) : std::max(stride_t, stride_l);
     const int32_t fs = keep_max <= 128 ? 8 : (keep_max <= 256 ? 4 : 2);
-    // the length of a scene's selected rows: its sample's in a fused batch
-    auto sel_len = [&](int64_t n) { return fused ? farm::sample_width(n, fs) : n; };
+    auto fuse_scene = [&](const Scene &s) {
+        if (!fusable) return false;
+        if (flags & FARM_FUSED) return true;
+        if (precision != FARM_PREC_FP32) return false;
+        const int64_t Rs = std::min<int64_t>(Rb, s.n);
+        return farm::sample_width(s.n, fs) >= 16 * Rs;
+    };
+    bool fused = false;            // some scene of the batch is fused
+    for (const auto &g : groups) fused |= fuse_scene(c.scenes[g.sid]);
+    // the length of a scene's selected rows: its sample's when it is fused
+    auto sel_len = [&](const Scene &s) { return fuse_scene(s) ? farm::sample_width(s.n, fs) : s.n; };
     int32_t tmp_stride = 4;
     for (const auto &g : groups) {
         const Scene &s = c.scenes[g.sid];
@@ -789,15 +801,16 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
         const int32_t kt = reduced ? reduced_keep_target(p, precision, Rs, s.n) : Rs;
         const int32_t kl = reduced ? reduced_keep_landmark(p, precision, klm, s.n) : klm;
-        if (sel_len(s.n) > farm::kSelectRowMax)
+        if (sel_len(s) > farm::kSelectRowMax)
             tmp_stride = std::max<int32_t>(tmp_stride, (int32_t)round_up(std::max(kt, kl), 4));
     }
     int32_t max_fkeep = 1;
     for (const auto &g : groups) {
         const Scene &s = c.scenes[g.sid];
-        const int64_t nsel = sel_len(s.n);
+        const bool fz = fuse_scene(s);
+        const int64_t nsel = sel_len(s);
         // fused: the stored sample tiles, compacted
-        const int64_t ld = fused ? farm::col_tiles(s.n, 256, farm::kColSample, fs) * 256 : round_up(s.n, 32);
+        const int64_t ld = fz ? farm::col_tiles(s.n, 256, farm::kColSample, fs) * 256 : round_up(s.n, 32);
         const int64_t rows_g = g.nq + g.nc;
         const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
         const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
@@ -843,13 +856,19 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             // the select keeps the whole-row lengths, or, fused, as many of them as the sample holds
             pc.keep_t = (int32_t)std::min<int64_t>(pc.fkeep_t, nsel);
             pc.keep_l = (int32_t)std::min<int64_t>(pc.fkeep_l, nsel);
+            pc.fs = fz ? fs : 0;
             max_fkeep = std::max(max_fkeep, std::max(pc.fkeep_t, pc.fkeep_l));
             pc.tmp_off = -1;
             pc.tops_off = -1;
             // rows [0, th0): shared-memory select; rows [th0, rows): thresholded select
             pc.th0 = pc.rows;
             pc.gshift = gshift;
-            if (tile_tops) {
+            if (fz) {
+                // (the fused selection's kernels take every row of the piece)
+                pc.tops_off = bt.tops;
+                bt.tops += nr * farm::group_stride(nsel, gshift);
+                bt.fused_rows += nr;
+            } else if (tile_tops) {
                 // a row goes to the thresholded select when its group maxima
                 // number at least its list length, or it is short enough to sort whole
                 const bool small = nsel <= farm::kSelectSortAll;
@@ -861,9 +880,10 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                     bt.max_union = std::max(bt.max_union, uni);
                 }
             }
-            pc.chunks = global_select ? 0 : chunks;
+            pc.chunks = fz ? 1 : (global_select ? 0 : chunks);
             pc.chunk_len = global_select ? (int32_t)s.n : chunk_len;
-            if (pc.th0 > 0 && !global_select) {
+            if (fz) pc.th0 = pc.rows;     // no select of the unfused path
+            if (pc.th0 > 0 && !global_select && !fz) {
                 bt.blocks += (int64_t)pc.th0 * pc.chunks;
                 bt.smem_sel = std::max(bt.smem_sel, pc.chunk_len);
                 if (pc.chunks > 1) {
@@ -983,13 +1003,16 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     if (sim_mode >= 0) {
         for (int vi = 0; vi < nv; ++vi) {
             for (int t = 0; t < n_tables; ++t) {
-                const int mode = !fused ? farm::kColAll : (t == 0 ? farm::kColSample : farm::kColRest);
                 farm::GemmPiece *hg = reinterpret_cast<farm::GemmPiece *>(ctx->h_blob + gp_base(vi, t));
                 for (size_t b = 0; b < batches.size(); ++b) {
                     int64_t tiles = 0;
                     for (size_t k = batches[b].p0; k < batches[b].p0 + batches[b].np; ++k) {
                         const farm::Piece &pc = pieces[k];
                         const Scene &sc = c.scenes[piece_sid[k]];
+                        // fused pieces: their sample tiles (table 0), the others (table 1);
+                        // the others' pieces: every tile (table 0), none (table 1)
+                        const int mode = pc.fs == 0 ? (t == 0 ? farm::kColAll : -1)
+                                                    : (t == 0 ? farm::kColSample : farm::kColRest);
                         farm::GemmPiece gp{};
                         gp.q_row0 = pc.q_row0;
                         gp.s_off = mode == farm::kColRest ? 0 : pc.s_off;
@@ -1002,10 +1025,10 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                         gp.ld = pc.ld;
                         gp.tile_begin = (int32_t)tiles;
                         gp.gshift = pc.gshift;
-                        gp.col_mode = mode;
-                        gp.col_stride = fused ? fs : 0;
-                        gp.n_store = mode == farm::kColRest ? 0 : pc.n;
-                        tiles += farm::sim_cluster_tiles(pc.rows, pc.n_obj, vlist[vi], mode, fs);
+                        gp.col_mode = mode < 0 ? farm::kColRest : mode;
+                        gp.col_stride = fs;
+                        gp.n_store = mode == farm::kColAll || mode == farm::kColSample ? pc.n : 0;
+                        if (mode >= 0) tiles += farm::sim_cluster_tiles(pc.rows, pc.n_obj, vlist[vi], mode, fs);
                         hg[k] = gp;
                     }
                     if (tiles > 0x7fffffffLL) return fail(ctx, FARM_EINVAL, "similarity batch exceeds 2^31 tiles");
@@ -1130,29 +1153,29 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             mark_end(ctx, m1);
             const int m2 = mark_begin(ctx, 2);
             const farm::Piece *dp = d_pieces + bt.p0;
-            if (fused) {
+            if (bt.fused_rows > 0) {
                 // each row's threshold from its sample's group maxima; the sample's entries reaching it
-                LAUNCH(farm::launch_fuse_sample_tau(d_sim, d_tops, dp, (int32_t)bt.np, bt.rows, fs, emit, c.stream));
+                LAUNCH(farm::launch_fuse_sample_tau(d_sim, d_tops, dp, (int32_t)bt.np, bt.rows, emit, c.stream));
             }
-            if (!fused && bt.blocks > 0)
+            if (bt.blocks > 0)
                 LAUNCH(farm::launch_select_grouped(d_sim, dp, (int32_t)bt.np, bt.blocks, bt.smem_sel, sel_ti, sel_tc,
                                                    sel_st, sel_li, sel_lc, sel_sl, tmp_idx, tmp_val, tmp_stride,
                                                    c.stream));
-            if (!fused && bt.chunked)
+            if (bt.chunked)
                 LAUNCH(farm::launch_merge_chunks(dp, (int32_t)bt.np, bt.rows, bt.smem_merge, tmp_idx, tmp_val, tmp_stride,
                                                  sel_ti, sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.stream));
-            if (!fused && bt.tblocks > 0)
+            if (bt.tblocks > 0)
                 LAUNCH(farm::launch_select_thresh(d_sim, d_tops, dp, (int32_t)bt.np, bt.tblocks, bt.max_union, sel_ti,
                                                   sel_tc, sel_st, sel_li, sel_lc, sel_sl, c.d_fallback, d_rowlist,
                                                   c.stream));
-            for (size_t k = bt.p0; k < bt.p0 + bt.np && !fused; ++k) {
+            for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
                 const farm::Piece &pc = pieces[k];
-                if (pc.chunks != 0 || pc.th0 == 0) continue;
+                if (pc.fs != 0 || pc.chunks != 0 || pc.th0 == 0) continue;
                 LAUNCH(farm::launch_select_rows_ex(d_sim + pc.s_off, pc.ld, pc.n, pc.th0, pc.ntr, pc.keep_t, pc.keep_l,
                                                    sel_ti, sel_tc, pc.t_row0, sel_st, sel_li, sel_lc, pc.l_row0, sel_sl,
                                                    c.stream));
             }
-            if (fused) {
+            if (bt.fused_rows > 0) {
                 // the other tiles append what reaches the thresholds; the merge, and
                 // the exact recomputation of rows whose candidates overflowed
                 mark_end(ctx, m2);
@@ -1171,7 +1194,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                                                   c.stream));
                 mark_end(ctx, m2b);
             }
-            const int m2c = fused ? mark_begin(ctx, 2) : -1;
+            const int m2c = bt.fused_rows > 0 ? mark_begin(ctx, 2) : -1;
             if (reduced) {
                 const float band = precision == FARM_PREC_FP8 ? 16.f * p.rescore_band : p.rescore_band;
                 // (the learned path's list values are compressed-space scores: no band)
@@ -1181,7 +1204,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                                                     cstride_l, band, tsel_idx, tsel_cos, stride_t, lsel_idx, stride_l,
                                                     c.stream));
             }
-            mark_end(ctx, fused ? m2c : m2);
+            mark_end(ctx, bt.fused_rows > 0 ? m2c : m2);
         }
 
         // ---- stage 3: relations, composite, sort
@@ -1210,7 +1233,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     } else {
         // the batch's shape: everything that fixes the launch sequence and its
         // arguments (device inputs are read where the caller keeps them)
-        std::vector<int64_t> key = {precision, (int64_t)fused, n_q, n_c, dim, (int64_t)c.ws_gen, (int64_t)c.scene_gen,
+        std::vector<int64_t> key = {precision, (int64_t)(flags & (FARM_FUSED | FARM_UNFUSED)), n_q, n_c, dim, (int64_t)c.ws_gen, (int64_t)c.scene_gen,
                                     (int64_t)c.mlp.version, (int64_t)(intptr_t)src_t, (int64_t)(intptr_t)src_c,
                                     (int64_t)groups.size()};
         for (const auto &g : groups) {

@@ -440,7 +440,8 @@ struct Piece {
     int32_t th0;
     int32_t gshift;         // group maxima over 2^gshift objects (thresholded select)
     int32_t fkeep_t, fkeep_l; // fused selection: list lengths over the whole row (keep_t / keep_l: over its sample)
-    int32_t n_obj;          // objects of the scene (n: the selected row length, its sample's in a fused batch)
+    int32_t n_obj;          // objects of the scene (n: the selected row length, its sample's when fused)
+    int32_t fs;             // fused selection: the sampling stride (every fs-th tile of 256); 0: not fused
 };
 
 // Grouped select over `pieces` (device; n_pieces entries) in one launch of
@@ -475,8 +476,9 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
                                  int64_t total_blocks, int32_t max_union, int32_t *tsel_idx, float *tsel_cos,
                                  int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
                                  int32_t *n_fallback, int32_t *row_list, cudaStream_t s);
-// The fused rank selection (k_fuse_select.cu) over the launch rows of
-// `pieces`, whose sample rows (sampling stride s) the similarity kernel
+// The fused rank selection (k_fuse_select.cu) over the launch rows of the
+// fused pieces (fs > 0; the other pieces' rows are skipped), whose sample
+// rows (sampling stride fs) the similarity kernel
 // stored at S with their group maxima at tops (each piece's n, ld, s_off,
 // tops_off and gshift describe the sample rows): sample_tau sets each row's
 // threshold in `emit` (the R-th largest group maximum of its sample, R =
@@ -488,7 +490,7 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
 // (count in *n_big) and merged by a second launch of one-warp blocks.  Both
 // counts start at zero.
 cudaError_t launch_fuse_sample_tau(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,
-                                   int64_t total_rows, int32_t s, const FuseEmit &emit, cudaStream_t st);
+                                   int64_t total_rows, const FuseEmit &emit, cudaStream_t st);
 cudaError_t launch_fuse_final(const Piece *pieces, int32_t n_pieces, int64_t total_rows, int32_t *tsel_idx,
                               float *tsel_cos, int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
                               const FuseEmit &emit, int32_t *n_overflow, int32_t *overflow_rows, int32_t *n_big,

@@ -156,13 +156,15 @@ __device__ __forceinline__ void load8(const float *__restrict__ row, int j, int 
 
 __global__ void __launch_bounds__(TAU_WARPS * 32)
 sample_tau_kernel(const float *__restrict__ S, const float *__restrict__ tops, const Piece *__restrict__ pieces,
-                  int32_t n_pieces, int64_t total_rows, int32_t s, FuseEmit emit)
+                  int32_t n_pieces, int64_t total_rows, FuseEmit emit)
 {
     __shared__ uint32_t keys[TAU_WARPS][TAU_KEYS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t b = (int64_t)blockIdx.x * TAU_WARPS + warp;
     if (b >= total_rows) return;
     const Piece pc = pieces[warp_find_piece(pieces, n_pieces, b)];
+    if (pc.fs == 0) return;                    // a row of the unfused path
+    const int s = pc.fs;
     const int i = (int)(b - pc.row_begin);
     const int64_t grow = pc.q_row0 + i;
     const int R = i < pc.ntr ? pc.fkeep_t : pc.fkeep_l;
@@ -335,6 +337,7 @@ fuse_final_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, int64_t to
     const int64_t b = (int64_t)blockIdx.x * FW + warp;
     if (b >= total_rows) return;
     const Piece pc = pieces[warp_find_piece(pieces, n_pieces, b)];
+    if (pc.fs == 0) return;                    // a row of the unfused path
     const RowList L = row_list(pc, b, tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos, stride_l);
     const int32_t t = emit.cnt[L.grow];
     if (t > FINAL_SMALL) {
@@ -463,13 +466,13 @@ cudaError_t launch_fuse_fallback(const Piece *pieces, int32_t n_pieces, const in
 }
 
 cudaError_t launch_fuse_sample_tau(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,
-                                   int64_t total_rows, int32_t s, const FuseEmit &emit, cudaStream_t st)
+                                   int64_t total_rows, const FuseEmit &emit, cudaStream_t st)
 {
     if (total_rows <= 0) return cudaSuccess;
-    if (n_pieces < 1 || s < 2 || !S || !tops || !emit.tau_key || !emit.cnt || !emit.cand) return cudaErrorInvalidValue;
+    if (n_pieces < 1 || !S || !tops || !emit.tau_key || !emit.cnt || !emit.cand) return cudaErrorInvalidValue;
     const int64_t blocks = (total_rows + TAU_WARPS - 1) / TAU_WARPS;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    sample_tau_kernel<<<(unsigned)blocks, TAU_WARPS * 32, 0, st>>>(S, tops, pieces, n_pieces, total_rows, s, emit);
+    sample_tau_kernel<<<(unsigned)blocks, TAU_WARPS * 32, 0, st>>>(S, tops, pieces, n_pieces, total_rows, emit);
     return cudaGetLastError();
 }
 

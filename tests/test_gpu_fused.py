@@ -1,10 +1,13 @@
 """GPU: the fused rank selection against the unfused path and the oracle.
 
-By default the tensor-core paths store only a sample of each similarity row
-(every s-th tile of 256 objects), rank it, and let the similarity kernel keep
-only the entries of the other tiles that reach the sample's R-th value; the
-row's list is then merged from the sample's list and the kept entries.
-FARM_UNFUSED writes the whole block and selects from it.  Both see the same
+The fused selection stores only a sample of each similarity row (every s-th
+tile of 256 objects), ranks it, and lets the similarity kernel keep only the
+entries of the other tiles that reach the sample's R-th value; the row's list
+is then merged from the sample's list and the kept entries.  FARM_FUSED fuses
+every scene of a batch, FARM_UNFUSED none (the whole block is written and
+selected from), and by default the FP32 path fuses the scenes whose sample
+holds at least 16 times the target list, so that one batch mixes both
+selections.  All see the same
 tensor-core values, so their lists -- and everything after them -- must be
 bitwise equal, in every precision, graph-captured or not, over scenes of one
 tile, a ragged last sample tile, several sample tiles and rows longer than
@@ -94,6 +97,18 @@ def test_fused_equals_unfused(F, world, prec):
     fused = _run(F, ctx, qb, code, True)
     assert F.farm_select_fallbacks(ctx) == 0
     _same(fused, _run(F, ctx, qb, code, False))
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_default_mixes_fused_and_unfused_scenes_bitwise(F, world, graph):
+    """The batch's scenes of 200 to 9,000 objects take the unfused selection,
+    those of 20,000 and 30,001 the fused one, in the same launches."""
+    ctx, scenes, qb = world
+    F.farm_select_fallbacks(ctx, reset=True)
+    mixed = _run(F, ctx, qb, F.PREC_FP32, None, graph=graph)
+    assert F.farm_select_fallbacks(ctx) == 0
+    _same(mixed, _run(F, ctx, qb, F.PREC_FP32, False))
+    _same(mixed, _run(F, ctx, qb, F.PREC_FP32, True))
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
