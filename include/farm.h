@@ -193,7 +193,14 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
  *                          c_off[q] .. c_off[q+1]-1 (at most 4); c_off[0] = 0
  *   c_pred     [n_c]       host int32 farm_pred codes, n_c = c_off[n_q]
  *   c_emb      [n_c, dim]  FP32 landmark embeddings
- *   precision  a farm_precision value
+ *   precision  a farm_precision value.  With FARM_PREC_BF16 (unless
+ *              FARM_FUSED) the scenes of fewer than 16,384 objects, and with
+ *              FARM_PREC_FP8 those of fewer than 32,768, run the
+ *              FP32-accurate similarity in the same batch, their lists
+ *              final without a rescore: re-reading the FP32 descriptors of
+ *              the candidates costs more there than the FP32-accurate GEMM
+ *              over the whole scene.  A batch of such scenes only runs as a
+ *              FARM_PREC_FP32 batch.
  *   flags      FARM_PTR_DEVICE: tgt_emb and c_emb are device pointers (the
  *              other arrays are always host memory).
  *              FARM_GRAPH: the batch's kernels (row normalisation,
@@ -389,7 +396,9 @@ farm_status farm_select_fallbacks(farm_ctx *ctx, int64_t *rows_out, int32_t rese
  *
  * farm_sim_tuning: the decisions so far, up to cap records of four int32:
  * mode (0 = FP32-accurate, 1 = BF16 and the learned prefilter, 2 = FP8; plus
- * 10 for batches with the fused selection, whose two launches are timed together),
+ * 10 for batches with the fused selection, whose two launches are timed
+ * together; plus 20 for BF16 / FP8 batches whose small scenes run the
+ * FP32-accurate similarity, the two launches timed together),
  * log2 of the rows, log2 of the mean objects per row, chosen variant.
  * *count receives the number of decisions.
  */

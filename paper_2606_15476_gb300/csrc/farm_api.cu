@@ -618,15 +618,28 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     const int32_t stride_l = (int32_t)std::min<int64_t>(p.k_anchor, max_n);
     const int32_t dim_pad = (int32_t)round_up(dim, farm::kDimAlign);
 
-    // ---- plan: group queries by scene (stable), rows = [targets, constraints] per group
+    // BF16 and FP8 batches: a scene of fewer objects than the bound runs the
+    // FP32-accurate similarity (three-term FP16 split) in the same batch and
+    // its lists are final, with no rescore -- re-reading the FP32 descriptors
+    // of C candidates per row costs more than the FP32-accurate GEMM over a
+    // small scene (rows of an n-object scene: the GEMM saves about
+    // 2.8e-12 n s per row at BF16 rates, the rescore and the longer select
+    // cost about 4.7e-8 s per row, so BF16 gains from about 16,000 objects;
+    // FP8's rescore of twice the candidates in a wider band, from about 32,000)
+    const int64_t exact_below = precision == FARM_PREC_BF16 && !(flags & FARM_FUSED) ? 16384
+                                : (precision == FARM_PREC_FP8 ? 32768 : 0);
+    // ---- plan: group queries by scene (stable; the scenes that run
+    //      FP32-accurate in a reduced-precision batch last, so that their rows
+    //      end the row space), rows = [targets, constraints] per group
     struct Group { int32_t sid; int64_t nq = 0, nc = 0, row0 = 0, q0 = 0, cp0 = 0; };
+    auto scene_key = [&](int32_t sid) { return ((int64_t)(c.scenes[sid].n < exact_below) << 32) | sid; };
     std::vector<int32_t> order((size_t)n_q);
     for (int64_t q = 0; q < n_q; ++q) order[q] = (int32_t)q;
     bool sorted = true;
-    for (int64_t q = 1; q < n_q; ++q) sorted &= scene_of_q[q] >= scene_of_q[q - 1];
+    for (int64_t q = 1; q < n_q; ++q) sorted &= scene_key(scene_of_q[q]) >= scene_key(scene_of_q[q - 1]);
     if (!sorted)
         std::stable_sort(order.begin(), order.end(),
-                         [&](int32_t a, int32_t b) { return scene_of_q[a] < scene_of_q[b]; });
+                         [&](int32_t a, int32_t b) { return scene_key(scene_of_q[a]) < scene_key(scene_of_q[b]); });
     std::vector<Group> groups;
     for (int64_t i = 0; i < n_q; ++i) {
         const int32_t q = order[i];
@@ -647,6 +660,24 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         cp += g.nc;
     }
     const int64_t rows_total = row;
+    auto exact_scene = [&](const Scene &s) { return s.n < exact_below; };
+    bool any_exact = false, all_exact = exact_below > 0;
+    for (const auto &g : groups) {
+        any_exact |= exact_scene(c.scenes[g.sid]);
+        all_exact &= exact_scene(c.scenes[g.sid]);
+    }
+    // a batch of small scenes only is an FP32 batch (fused where that pays)
+    if (all_exact) {
+        precision = FARM_PREC_FP32;
+        any_exact = false;
+    }
+    // the first planned row of the FP32-accurate scenes (rows_total: none)
+    int64_t exact_row0 = rows_total;
+    for (const auto &g : groups)
+        if (any_exact && exact_scene(c.scenes[g.sid])) {
+            exact_row0 = g.row0;
+            break;
+        }
     // staging layout (int32): rowmap[n_q + n_c] | perm[n_q] | qmeta[n_q * 8]
     const size_t need = (size_t)(n_q + n_c) + (size_t)n_q + (size_t)n_q * 8;
     CK(cudaEventSynchronize(ctx->stage_done));
@@ -710,6 +741,11 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     CK(ws_get(ctx, farm::B_OUT_ANCHOR, (size_t)n_q * stride_t * 4, &o_anc));
     RowOps ops;
     CK(alloc_rows(ctx, precision, rows_total, dim_pad, ops));
+    if (any_exact) {
+        const size_t cnt = (size_t)rows_total * dim_pad;
+        CK(ws_get(ctx, farm::B_QHI, cnt, &ops.qhi));
+        CK(ws_get(ctx, farm::B_QLO, cnt, &ops.qlo));
+    }
     int32_t *bsel_t = nullptr, *bsel_l = nullptr;
     float *bsel_tv = nullptr, *bsel_lv = nullptr;
     const int32_t cstride_t = reduced_keep_target(p, precision, stride_t, max_n);
@@ -752,7 +788,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     //      merge) for the others; then one FP32 rescore launch on the
     //      reduced-precision paths
     struct Batch { size_t p0 = 0, np = 0; int64_t s_floats = 0, rows = 0, blocks = 0, tblocks = 0, tmp = 0,
-                   tops = 0, fused_rows = 0; int32_t smem_sel = 1, smem_merge = 0, max_union = 1;
+                   tops = 0, fused_rows = 0, exact_rows = 0; int32_t smem_sel = 1, smem_merge = 0, max_union = 1;
                    bool chunked = false; };
     std::vector<farm::Piece> pieces;
     std::vector<int32_t> piece_sid;
@@ -851,8 +887,9 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             pc.ld = (int32_t)ld;
             pc.R = Rs;
             pc.klm = klm;
-            pc.fkeep_t = reduced ? reduced_keep_target(p, precision, Rs, s.n) : Rs;
-            pc.fkeep_l = reduced ? reduced_keep_landmark(p, precision, klm, s.n) : klm;
+            pc.exact = reduced && exact_scene(s) ? 1 : 0;
+            pc.fkeep_t = reduced && !pc.exact ? reduced_keep_target(p, precision, Rs, s.n) : Rs;
+            pc.fkeep_l = reduced && !pc.exact ? reduced_keep_landmark(p, precision, klm, s.n) : klm;
             // the select keeps the whole-row lengths, or, fused, as many of them as the sample holds
             pc.keep_t = (int32_t)std::min<int64_t>(pc.fkeep_t, nsel);
             pc.keep_l = (int32_t)std::min<int64_t>(pc.fkeep_l, nsel);
@@ -895,6 +932,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             }
             bt.s_floats += nr * ld;
             bt.rows += nr;
+            if (pc.exact) bt.exact_rows += nr;
             bt.np += 1;
             pieces.push_back(pc);
             piece_sid.push_back(g.sid);
@@ -967,7 +1005,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         double wn = 0.0;
         for (const auto &g : groups) wn += (double)(g.nq + g.nc) * (double)c.scenes[g.sid].n;
         auto log2i = [](int64_t x) { int b = 0; while (b < 62 && (int64_t(1) << (b + 1)) <= x) ++b; return b; };
-        tune_key = (fused ? 100000 : 0) + (int64_t)sim_mode * 10000 + log2i(rows_total) * 100 +
+        tune_key = (any_exact ? 200000 : 0) + (fused ? 100000 : 0) + (int64_t)sim_mode * 10000 +
+                   log2i(rows_total) * 100 +
                    log2i((int64_t)(wn / (double)rows_total));
         auto it = c.tuned.find(tune_key);
         if (c.pinned_variant >= 0) {
@@ -983,7 +1022,9 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     // device blob: select pieces | GEMM pieces, one table per variant | tensor maps (128-byte aligned sections)
     const size_t off_gp = round_up((int64_t)(pieces.size() * sizeof(farm::Piece)), 128);
     const size_t gp_table = round_up((int64_t)(pieces.size() * sizeof(farm::GemmPiece)), 128);
-    const int n_tables = fused ? 2 : 1;        // fused: the sample tiles' table, then the others'
+    // fused: the sample tiles' table, then the others'; a reduced-precision
+    // batch with FP32-accurate scenes: its own pieces' table, then theirs
+    const int n_tables = fused || any_exact ? 2 : 1;
     const size_t off_maps = off_gp + nv * n_tables * gp_table;
     const size_t blob_bytes = off_maps + map_scenes.size() * nv * 2 * farm::kTensorMapBytes;
     uint8_t *d_blob;
@@ -1010,14 +1051,16 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                         const farm::Piece &pc = pieces[k];
                         const Scene &sc = c.scenes[piece_sid[k]];
                         // fused pieces: their sample tiles (table 0), the others (table 1);
-                        // the others' pieces: every tile (table 0), none (table 1)
-                        const int mode = pc.fs == 0 ? (t == 0 ? farm::kColAll : -1)
-                                                    : (t == 0 ? farm::kColSample : farm::kColRest);
+                        // the others' pieces: every tile (table 0), none (table 1); in a
+                        // batch with FP32-accurate scenes (never fused) theirs are table 1's
+                        const int mode = any_exact ? ((t == 1) == (pc.exact != 0) ? farm::kColAll : -1)
+                                         : pc.fs == 0 ? (t == 0 ? farm::kColAll : -1)
+                                                      : (t == 0 ? farm::kColSample : farm::kColRest);
                         farm::GemmPiece gp{};
                         gp.q_row0 = pc.q_row0;
                         gp.s_off = mode == farm::kColRest ? 0 : pc.s_off;
                         gp.tops_off = (tile_tops && mode != farm::kColRest) ? pc.tops_off : -1;
-                        gp.scale_d = sim_mode == farm::kSimFp8 ? sc.desc_scale : nullptr;
+                        gp.scale_d = sim_mode == farm::kSimFp8 && !pc.exact ? sc.desc_scale : nullptr;
                         gp.bmap = d_blob + off_maps +
                                   ((size_t)map_of_scene[piece_sid[k]] * nv + vi) * 2 * farm::kTensorMapBytes;
                         gp.rows = pc.rows;
@@ -1041,8 +1084,9 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             for (int vi = 0; vi < nv; ++vi) {
                 void *out = ctx->h_blob + off_maps + (m * nv + vi) * 2 * farm::kTensorMapBytes;
                 bool ok;
-                if (precision == FARM_PREC_FP32)
-                    ok = farm::sim_tc_encode_b(sim_mode, vlist[vi], out, sc.desc_hi, sc.desc_lo, sc.n, sc.dim_pad);
+                if (precision == FARM_PREC_FP32 || (reduced && exact_scene(sc)))
+                    ok = farm::sim_tc_encode_b(farm::kSimF16x3, vlist[vi], out, sc.desc_hi, sc.desc_lo, sc.n,
+                                               sc.dim_pad);
                 else if (precision == FARM_PREC_BF16)
                     ok = farm::sim_tc_encode_b(sim_mode, vlist[vi], out, sc.desc_bf16, nullptr, sc.n, sc.dim_pad);
                 else if (precision == FARM_PREC_LEARNED)
@@ -1073,13 +1117,16 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     if (!dev) CK(copy_inputs(cudaMemcpyHostToDevice));
     auto enqueue = [&]() -> farm_status {
         // ---- stage 0: normalisation (the staging copies above are not part of it)
+        // (with FP32-accurate scenes in a reduced-precision batch, their rows
+        // -- the last ones -- get the FP16 split only, the others no split)
+        const int64_t split = any_exact ? exact_row0 : -1;
         LAUNCH(farm::launch_normalize_rows(src_t, d_rowmap, n_q, dim, dim_pad, ops.q32, ops.qhi, ops.qlo, ops.qbf,
-                                           c.d_err, farm::kErrBadRow, c.stream));
+                                           c.d_err, farm::kErrBadRow, c.stream, split));
         if (n_c > 0)
             LAUNCH(farm::launch_normalize_rows(src_c, d_rowmap + n_q, n_c, dim, dim_pad, ops.q32, ops.qhi, ops.qlo,
-                                               ops.qbf, c.d_err, farm::kErrBadRow, c.stream));
+                                               ops.qbf, c.d_err, farm::kErrBadRow, c.stream, split));
         if (precision == FARM_PREC_FP8)
-            LAUNCH(farm::launch_quantize_fp8_rows(ops.q32, rows_total, dim_pad, ops.qf8, ops.qscale, c.stream));
+            LAUNCH(farm::launch_quantize_fp8_rows(ops.q32, exact_row0, dim_pad, ops.qf8, ops.qscale, c.stream));
         if (precision == FARM_PREC_LEARNED) CK(farm::learned_embed_rows(ctx, ops.qbf, rows_total, ops.qcomp));
         mark_end(ctx, m0);
 
@@ -1097,15 +1144,19 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             else if (precision == FARM_PREC_BF16) q0 = ops.qbf;
             else if (precision == FARM_PREC_LEARNED) { q0 = ops.qcomp; kdim = c.mlp.P; }
             else q0 = ops.qf8;
-            // table t of variant vi (fused: 0 the sample tiles, 1 the others, appending to the rows' buffers)
+            // table t of variant vi (fused: 0 the sample tiles, 1 the others, appending to
+            // the rows' buffers; with FP32-accurate scenes: 1 theirs, in that mode)
             auto launch_variant = [&](int vi, int t) {
+                const bool ex = any_exact && t == 1;
                 return farm::launch_sim_tc_grouped(
-                    sim_mode, vlist[vi], q0, q1, rows_total, kdim,
-                    reinterpret_cast<farm::GemmPiece *>(d_blob + gp_base(vi, t)) + bt.p0, (int32_t)bt.np,
+                    ex ? farm::kSimF16x3 : sim_mode, vlist[vi], ex ? ops.qhi : q0, ex ? ops.qlo : q1, rows_total,
+                    kdim, reinterpret_cast<farm::GemmPiece *>(d_blob + gp_base(vi, t)) + bt.p0, (int32_t)bt.np,
                     batch_tiles[((size_t)b * nv + vi) * n_tables + t], d_sim, tile_tops ? d_tops : nullptr,
-                    precision == FARM_PREC_FP8 ? ops.qscale : nullptr, c.num_sms, c.d_err, c.stream,
-                    t == 1 ? &emit : nullptr);
+                    precision == FARM_PREC_FP8 && !ex ? ops.qscale : nullptr, c.num_sms, c.d_err, c.stream,
+                    fused && t == 1 ? &emit : nullptr);
             };
+            // the tables launched before the selection (fused: the sample tiles only)
+            const int n_now = fused ? 1 : n_tables;
             if (sim_mode >= 0) {
                 if (vsel < 0) {
                     // autotune: every variant twice, the second run timed (fused:
@@ -1138,9 +1189,10 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                     cudaEventDestroy(e1);
                     c.tuned[tune_key] = vlist[vsel];
                     // the batch's results come from the chosen variant, as every later batch's will
-                    if (fused || vsel != nv - 1) LAUNCH(launch_variant(vsel, 0));
+                    if (fused || vsel != nv - 1)
+                        for (int t = 0; t < n_now; ++t) LAUNCH(launch_variant(vsel, t));
                 } else {
-                    LAUNCH(launch_variant(vsel, 0));
+                    for (int t = 0; t < n_now; ++t) LAUNCH(launch_variant(vsel, t));
                 }
             } else {
                 for (size_t k = bt.p0; k < bt.p0 + bt.np; ++k) {
@@ -1198,7 +1250,11 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             if (reduced) {
                 const float band = precision == FARM_PREC_FP8 ? 16.f * p.rescore_band : p.rescore_band;
                 // (the learned path's list values are compressed-space scores: no band)
-                LAUNCH(farm::launch_rescore_grouped(dp, (int32_t)bt.np, bt.rows, ops.q32, dim_pad, bsel_t,
+                // (the rows of FP32-accurate scenes, the batch's last ones, are final: copied)
+                LAUNCH(farm::launch_copy_lists(dp, (int32_t)bt.np, bt.rows - bt.exact_rows, bt.exact_rows, bsel_t,
+                                               bsel_tv, cstride_t, bsel_l, cstride_l, tsel_idx, tsel_cos, stride_t,
+                                               lsel_idx, stride_l, c.stream));
+                LAUNCH(farm::launch_rescore_grouped(dp, (int32_t)bt.np, bt.rows - bt.exact_rows, ops.q32, dim_pad, bsel_t,
                                                     precision == FARM_PREC_LEARNED ? nullptr : bsel_tv, cstride_t,
                                                     bsel_l, precision == FARM_PREC_LEARNED ? nullptr : bsel_lv,
                                                     cstride_l, band, tsel_idx, tsel_cos, stride_t, lsel_idx, stride_l,
@@ -1743,7 +1799,8 @@ farm_status farm_sim_tuning(farm_ctx *ctx, int32_t *entries, int32_t cap, int32_
     int32_t i = 0;
     for (const auto &kv : ctx->c.tuned) {
         if (i < cap) {
-            entries[4 * i + 0] = (int32_t)(kv.first / 10000 % 10) + (kv.first >= 100000 ? 10 : 0);
+            entries[4 * i + 0] = (int32_t)(kv.first / 10000 % 10) + (kv.first / 100000 % 2 ? 10 : 0) +
+                                 (kv.first / 200000 % 2 ? 20 : 0);
             entries[4 * i + 1] = (int32_t)(kv.first / 100 % 100);
             entries[4 * i + 2] = (int32_t)(kv.first % 100);
             entries[4 * i + 3] = kv.second;

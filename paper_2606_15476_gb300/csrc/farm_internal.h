@@ -236,10 +236,12 @@ cudaError_t preload_sim_tc_f16x3();
 // (zero tail); optionally also write the FP16 split and BF16 copies.  Rows
 // with zero or non-finite norm set err_bit in *err and are written as zeros.
 // dst_rows: optional int32 [rows] scatter map (src row r goes to dst row dst_rows[r]).
+// split >= 0: dst rows below split get only dst32 / dst_bf16, the others only
+// the FP16 split (a reduced-precision batch whose last rows run FP32-accurate).
 cudaError_t launch_normalize_rows(const float *src, const int32_t *dst_rows, int64_t rows,
                                   int32_t dim, int32_t dim_pad, float *dst32, uint16_t *dst_hi,
                                   uint16_t *dst_lo, uint16_t *dst_bf16, int32_t *err, int err_bit,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int64_t split = -1);
 
 // E4M3 copy of unit rows with a per-row scale (max|x| / 448).
 cudaError_t launch_quantize_fp8_rows(const float *src, int64_t rows, int32_t dim_pad, uint8_t *dst, float *scale,
@@ -442,6 +444,8 @@ struct Piece {
     int32_t fkeep_t, fkeep_l; // fused selection: list lengths over the whole row (keep_t / keep_l: over its sample)
     int32_t n_obj;          // objects of the scene (n: the selected row length, its sample's when fused)
     int32_t fs;             // fused selection: the sampling stride (every fs-th tile of 256); 0: not fused
+    int32_t exact;          // reduced-precision batch: 1 when the piece's scene runs the FP32-accurate
+                            // similarity, its lists final (the rescore copies them)
 };
 
 // Grouped select over `pieces` (device; n_pieces entries) in one launch of
@@ -514,6 +518,14 @@ constexpr int kFuseFallbackBlocks = 64;
 // with more candidates is recomputed by the fallback.  Use it as FuseEmit::cap.
 int fuse_merge_capacity(int32_t max_keep);
 
+// The final lists of launch rows [row0, row0 + rows), rows of pieces whose
+// scene ran the FP32-accurate similarity in a reduced-precision batch
+// (Piece::exact): the first R (klm) entries of bsel_t / bsel_tv (bsel_l)
+// copied to tsel_idx / tsel_cos (lsel_idx), -1 / 0 past them.
+cudaError_t launch_copy_lists(const Piece *pieces, int32_t n_pieces, int64_t row0, int64_t rows, const int32_t *bsel_t,
+                              const float *bsel_tv, int32_t cstride_t, const int32_t *bsel_l, int32_t cstride_l,
+                              int32_t *tsel_idx, float *tsel_cos, int32_t stride_t, int32_t *lsel_idx,
+                              int32_t stride_l, cudaStream_t s);
 // Grouped FP32 rescore (one block per launch row): the keep_t / keep_l
 // candidates of bsel_* (strides cstride_t / cstride_l; descending by their
 // reduced-precision values bsel_tv / bsel_lv, nullable) are re-scored with

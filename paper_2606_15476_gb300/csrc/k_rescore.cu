@@ -12,6 +12,10 @@
 // lies more than `band` below the R-th value is skipped (it would need an
 // arithmetic error above the band to belong to the top R).
 //
+// Rows of a scene that ran the FP32-accurate similarity in the same batch
+// (Piece::exact) already hold their final lists: copy_lists_kernel copies
+// them, a warp per row.
+//
 // One CTA per row: the row is staged in shared memory, each warp takes two
 // candidates at a time (lanes stride both descriptors in float4 with four
 // loads of each in flight, then shuffle reductions), and a bitonic sort over
@@ -154,7 +158,58 @@ rescore_grouped_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, const
     }
 }
 
+// The final lists of launch rows [row0, row0 + rows) -- rows of FP32-accurate
+// scenes -- copied from the candidate buffers: R (klm) entries, -1 / 0 past them.
+__global__ void __launch_bounds__(256)
+copy_lists_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, int64_t row0, int64_t rows,
+                  const int32_t *__restrict__ bsel_t, const float *__restrict__ bsel_tv, int32_t cstride_t,
+                  const int32_t *__restrict__ bsel_l, int32_t cstride_l, int32_t *__restrict__ tsel_idx,
+                  float *__restrict__ tsel_cos, int32_t stride_t, int32_t *__restrict__ lsel_idx, int32_t stride_l)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (w >= rows) return;
+    const int64_t r = row0 + w;
+    int lo = 0;
+    if (lane == 0) {
+        int hi = n_pieces - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pieces[mid].row_begin <= r) lo = mid;
+            else hi = mid - 1;
+        }
+    }
+    const Piece &pc = pieces[__shfl_sync(0xffffffffu, lo, 0)];
+    const int i = (int)(r - pc.row_begin);
+    const bool tgt = i < pc.ntr;
+    const int64_t l = pc.l_row0 + (i - pc.ntr);
+    const int64_t co = tgt ? (pc.t_row0 + i) * (int64_t)cstride_t : l * (int64_t)cstride_l;
+    const int32_t *src = (tgt ? bsel_t : bsel_l) + co;
+    int32_t *oi = tgt ? tsel_idx + (pc.t_row0 + i) * (int64_t)stride_t : lsel_idx + l * (int64_t)stride_l;
+    float *oc = tgt && tsel_cos ? tsel_cos + (pc.t_row0 + i) * (int64_t)stride_t : nullptr;
+    const int keep = tgt ? pc.R : pc.klm, out = tgt ? stride_t : stride_l;
+    for (int k = lane; k < out; k += 32) {
+        oi[k] = k < keep ? src[k] : -1;
+        if (oc) oc[k] = k < keep ? bsel_tv[co + k] : 0.f;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_copy_lists(const Piece *pieces, int32_t n_pieces, int64_t row0, int64_t rows, const int32_t *bsel_t,
+                              const float *bsel_tv, int32_t cstride_t, const int32_t *bsel_l, int32_t cstride_l,
+                              int32_t *tsel_idx, float *tsel_cos, int32_t stride_t, int32_t *lsel_idx,
+                              int32_t stride_l, cudaStream_t s)
+{
+    if (rows <= 0) return cudaSuccess;
+    if (n_pieces < 1 || (tsel_cos && !bsel_tv)) return cudaErrorInvalidValue;
+    const int64_t blocks = (rows + 7) / 8;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    copy_lists_kernel<<<(unsigned)blocks, 256, 0, s>>>(pieces, n_pieces, row0, rows, bsel_t, bsel_tv, cstride_t,
+                                                        bsel_l, cstride_l, tsel_idx, tsel_cos, stride_t, lsel_idx,
+                                                        stride_l);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rescore_grouped(const Piece *pieces, int32_t n_pieces, int64_t total_rows, const float *Q32,
                                    int32_t dim_pad, const int32_t *bsel_t, const float *bsel_tv, int32_t cstride_t,

@@ -54,11 +54,17 @@ def _run(F, ctx, qb, code, fused, graph=False):
     return F.farm_topk(ctx, h, 10, qb.n_q), F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
 
 
-def _same(a, b):
+def _same(a, b, qb=None, qs=None):
+    """Bitwise equal results (of the queries qs of batch qb, default all)."""
+    if qs is None:
+        qs = np.arange(a[0]["idx"].shape[0])
+        cs = np.arange(a[1][1].shape[0])
+    else:
+        cs = np.concatenate([np.arange(qb.c_off[q], qb.c_off[q + 1]) for q in qs]).astype(np.int64)
     for key in ("idx", "score", "pred", "anchor"):
-        np.testing.assert_array_equal(a[0][key], b[0][key], err_msg=key)
-    np.testing.assert_array_equal(a[1][0], b[1][0])
-    np.testing.assert_array_equal(a[1][1], b[1][1])
+        np.testing.assert_array_equal(a[0][key][qs], b[0][key][qs], err_msg=key)
+    np.testing.assert_array_equal(a[1][0][qs], b[1][0][qs])
+    np.testing.assert_array_equal(a[1][1][cs], b[1][1][cs])
 
 
 @pytest.fixture(scope="module")
@@ -90,13 +96,21 @@ def world(F):
 def test_fused_equals_unfused(F, world, prec):
     """(FP8 and learned batches are never fused -- E4M3 ties many entries at
     a threshold, and lists of 512 crowd the buffer -- so for them this
-    compares the default with the explicit flag.)"""
+    compares the default with the explicit flag.  An unfused BF16 batch runs
+    its scenes of fewer than 16,384 objects FP32-accurate, whose lists may
+    order near-ties differently from the BF16 stage's FP32 rescore: for BF16
+    the larger scenes' queries are compared.)"""
     ctx, scenes, qb = world
     code = _code(F, prec)
     F.farm_select_fallbacks(ctx, reset=True)
     fused = _run(F, ctx, qb, code, True)
     assert F.farm_select_fallbacks(ctx) == 0
-    _same(fused, _run(F, ctx, qb, code, False))
+    if prec == "bf16":
+        qs = np.flatnonzero([scenes[int(s)].n >= 16384 for s in qb.scene_of_q])
+        assert qs.size >= 40
+        _same(fused, _run(F, ctx, qb, code, False), qb, qs)
+    else:
+        _same(fused, _run(F, ctx, qb, code, False))
 
 
 @pytest.mark.parametrize("graph", [False, True])

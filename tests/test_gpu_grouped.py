@@ -297,3 +297,50 @@ def test_pinned_variant_gives_the_same_results(F, world):
         np.testing.assert_array_equal(l, outs[0][1][1])
     with pytest.raises(F.FarmError):
         F.farm_sim_variant_pin(ctx, 3)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_small_scenes_of_reduced_precision_batches_run_fp32_accurate(F, prec):
+    """In a BF16 (FP8) batch the scenes below 16,384 (32,768) objects take
+    the FP32-accurate similarity in the same launches and keep their lists
+    without a rescore: their results equal the FP32 path's bitwise, while
+    the large scene's stay within Recall@10 >= 0.99 of it."""
+    code = {"bf16": F.PREC_BF16, "fp8": F.PREC_FP8}[prec]
+    big = 40000
+    ctx = F.farm_create(0)
+    try:
+        scenes, parts = {}, []
+        for sid, n in ((40, 300), (41, 5000), (42, 15000), (43, big)):
+            sc = synth.make_scene(sid + 11, n, 256, extent=(40.0, 40.0, 5.0), n_classes=max(8, n // 50),
+                                  n_views=4)
+            F.farm_memory_upload(ctx, sid, sc.desc, sc.cls, sc.box, sc.views)
+            scenes[sid] = sc
+            parts.append(synth.make_queries(sid + 900, sc, 24, m_choices=(0, 1, 2, 3), scene_id=sid))
+        qb = synth.scenes.concat_batches(parts)
+        qb = qb.subset(np.random.default_rng(12).permutation(qb.n_q))
+        h, ref = _run(F, ctx, qb, F.PREC_FP32)
+        rt, rl = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
+        h, out = _run(F, ctx, qb, code)
+        ot, ol = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
+        bound = 16384 if prec == "bf16" else 32768
+        small = np.array([scenes[int(s)].n < bound for s in qb.scene_of_q])
+        assert small.any() and (~small).any() if prec == "bf16" else small.any()
+        for key in ("idx", "score", "pred", "anchor"):
+            np.testing.assert_array_equal(out[key][small], ref[key][small], err_msg=key)
+        np.testing.assert_array_equal(ot[small], rt[small])
+        cs = np.concatenate([np.arange(qb.c_off[q], qb.c_off[q + 1]) for q in np.flatnonzero(small)])
+        np.testing.assert_array_equal(ol[cs], rl[cs])
+        large = np.flatnonzero(~small)
+        if prec == "bf16" and large.size:
+            hits = sum(len(set(ref["idx"][q].tolist()) & set(out["idx"][q].tolist())) for q in large)
+            assert hits / (10.0 * large.size) >= 0.99
+        dec = F.farm_sim_tuning(ctx)
+        assert any(d[0] >= 20 for d in dec)
+        # a batch of small scenes only runs as an FP32 batch
+        sub = qb.subset(np.flatnonzero(small))
+        _, ref_s = _run(F, ctx, sub, F.PREC_FP32)
+        _, out_s = _run(F, ctx, sub, code)
+        for key in ("idx", "score", "pred", "anchor"):
+            np.testing.assert_array_equal(out_s[key], ref_s[key], err_msg=key)
+    finally:
+        F.farm_destroy(ctx)
