@@ -28,11 +28,13 @@ namespace {
 
 constexpr int TH = 128;      // small CTAs: more queries resident per SM to hide the dependent loads
 
+// 1 / (1 + e^-x) for x >= 0, e^x / (1 + e^x) below (no overflow, no
+// cancellation), without a branch: the lanes of a warp hold arguments of
+// either sign.
 __device__ __forceinline__ float sigm(float x)
 {
-    if (x >= 0.f) return 1.f / (1.f + expf(-x));
-    const float ex = expf(x);
-    return ex / (1.f + ex);
+    const float e = expf(-fabsf(x));
+    return (x >= 0.f ? 1.f : e) / (1.f + e);
 }
 
 __device__ __forceinline__ uint32_t order_key(float f)
@@ -75,24 +77,28 @@ template <bool LR>
 __device__ float viewpoint(const float *__restrict__ ve, int n_views, float ax, float ay, float az, float sign,
                            const RelK &k)
 {
+    // (every view evaluated and the ones not counted masked out, so that the
+    // lanes of a warp, which hold different landmarks, do not diverge)
     float acc = 0.f;
     int counted = 0;
+#pragma unroll 2
     for (int v = 0; v < n_views; ++v) {
         const float *r = ve + v * kViewStride;
         const float2 zu = __ldg(reinterpret_cast<const float2 *>(r + 8));
-        if (!(zu.x > k.z_min)) continue;
         const float4 o = __ldg(reinterpret_cast<const float4 *>(r));        // ox, oy, oz, fx
         const float4 f = __ldg(reinterpret_cast<const float4 *>(r + 4));    // fy, fz, rx, ry
         const float dax = ax - o.x, day = ay - o.y, daz = az - o.z;
         const float Za = dax * o.w + day * f.x + daz * f.y;
-        if (!(Za > k.z_min)) continue;
+        const bool ok = zu.x > k.z_min && Za > k.z_min;
+        float sv;
         if (LR) {
             const float ua = (dax * f.z + day * f.w) / Za;
-            acc += sigm(sign * (ua - zu.y) * k.inv_tau_h);
+            sv = sigm(sign * (ua - zu.y) * k.inv_tau_h);
         } else {
-            acc += sigm(sign * (Za - zu.x) * k.inv_tau_d);
+            sv = sigm(sign * (Za - zu.x) * k.inv_tau_d);
         }
-        ++counted;
+        acc += ok ? sv : 0.f;
+        counted += ok ? 1 : 0;
     }
     return counted ? acc / (float)counted : 0.5f;
 }
@@ -275,7 +281,7 @@ constexpr int WARPS = TH / 32;
 // RM, landmark list KM and Closest /
 // Farthest set KC; every section starts on a 16-byte boundary.
 struct ComposeSmem {
-    size_t best, key, sv, lm_pos, lm_size, cset_pos, lm_idx, cand_e, ssem, surv, bytes;
+    size_t best, key, sv, lm, cset_pos, lm_idx, cand_e, ssem, surv, bytes;
     __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
     __host__ __device__ ComposeSmem(int RM, int KM, int KC)
     {
@@ -283,8 +289,7 @@ struct ComposeSmem {
         best = o;   o = up16(o + (size_t)RM * FARM_MAX_CONSTRAINTS * 8);
         key = o;    o = up16(o + (size_t)RM * 8);
         sv = o;     o = up16(o + (size_t)RM * 32);
-        lm_pos = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
-        lm_size = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 3 * 4);
+        lm = o;     o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 32);
         cset_pos = o; o = up16(o + (size_t)KC * 3 * 4);
         lm_idx = o; o = up16(o + (size_t)FARM_MAX_CONSTRAINTS * KM * 4);
         cand_e = o; o = up16(o + (size_t)RM * 4);
@@ -294,7 +299,7 @@ struct ComposeSmem {
     }
 };
 
-__global__ void __launch_bounds__(TH, 8)
+__global__ void __launch_bounds__(TH, 10)
 compose_kernel(ComposeArgs a, int32_t KC)
 {
     extern __shared__ __align__(16) uint8_t sm[];
@@ -304,8 +309,8 @@ compose_kernel(ComposeArgs a, int32_t KC)
     uint64_t *key = reinterpret_cast<uint64_t *>(sm + L.key);
     // per survivor: {ex, ey, ez, esx}, {esy, esz, e, list position}
     float4 *sv = reinterpret_cast<float4 *>(sm + L.sv);                               // [RM][2]
-    float *lm_pos = reinterpret_cast<float *>(sm + L.lm_pos);                         // [4][KM][3]
-    float *lm_size = reinterpret_cast<float *>(sm + L.lm_size);                       // [4][KM][3]
+    // per landmark: {ax, ay, az, asx}, {asy, asz, 0, 0}
+    float4 *lm = reinterpret_cast<float4 *>(sm + L.lm);                               // [4][KM][2]
     float *cset_pos = reinterpret_cast<float *>(sm + L.cset_pos);                     // [KC][3]
     int32_t *lm_idx = reinterpret_cast<int32_t *>(sm + L.lm_idx);                     // [4][KM]
     int32_t *cand_e = reinterpret_cast<int32_t *>(sm + L.cand_e);
@@ -360,12 +365,10 @@ compose_kernel(ComposeArgs a, int32_t KC)
         int32_t ai = a.lsel_idx[(c0 + i) * a.stride_l + l];
         if (ai < 0 || ai >= sd.n) ai = -1;
         lm_idx[i * KM + l] = ai;
-        lm_pos[(i * KM + l) * 3 + 0] = ai >= 0 ? sd.pos[ai] : 0.f;
-        lm_pos[(i * KM + l) * 3 + 1] = ai >= 0 ? sd.pos[sd.n + ai] : 0.f;
-        lm_pos[(i * KM + l) * 3 + 2] = ai >= 0 ? sd.pos[2 * sd.n + ai] : 0.f;
-        lm_size[(i * KM + l) * 3 + 0] = ai >= 0 ? sd.size[ai] : 0.f;
-        lm_size[(i * KM + l) * 3 + 1] = ai >= 0 ? sd.size[sd.n + ai] : 0.f;
-        lm_size[(i * KM + l) * 3 + 2] = ai >= 0 ? sd.size[2 * sd.n + ai] : 0.f;
+        lm[2 * (i * KM + l)] = ai >= 0 ? make_float4(sd.pos[ai], sd.pos[sd.n + ai], sd.pos[2 * sd.n + ai], sd.size[ai])
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        lm[2 * (i * KM + l) + 1] = ai >= 0 ? make_float4(sd.size[sd.n + ai], sd.size[2 * sd.n + ai], 0.f, 0.f)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (R > p.k_max) {
         for (int c = tid; c < R; c += TH) {
@@ -420,11 +423,10 @@ compose_kernel(ComposeArgs a, int32_t KC)
                 const int32_t ai = lm_idx[i * KM + l];
                 if (ai >= 0 && ai != e) {
                     const float ex = sa.x, ey = sa.y, ez = sa.z, esx = sa.w, esy = sb.x, esz = sb.y;
-                    const float *ap = lm_pos + (i * KM + l) * 3;
-                    const float *as = lm_size + (i * KM + l) * 3;
+                    const float4 la = lm[2 * (i * KM + l)], lb = lm[2 * (i * KM + l) + 1];
                     const RelCtx rc{sd.views + (int64_t)e * sd.n_views * kViewStride, sd.n_views, cand_e, cset_pos, kc};
-                    const float r = relation(pr, e, ce, ex, ey, ez, esx, esy, esz, ai, ap[0], ap[1], ap[2], as[0],
-                                             as[1], as[2], rc, K);
+                    const float r = relation(pr, e, ce, ex, ey, ez, esx, esy, esz, ai, la.x, la.y, la.z, la.w, lb.x,
+                                             lb.y, rc, K);
                     h = __float_as_uint(r);
                     lo = 0xffffffffu - (uint32_t)ai;
                 }
@@ -459,7 +461,8 @@ compose_kernel(ComposeArgs a, int32_t KC)
                     const int x = t / klm, y = t - x * klm;
                     const int32_t ap = lm_idx[c * KM + x], aq = lm_idx[(c + 1) * KM + y];
                     if (ap < 0 || aq < 0 || ap == e || aq == e || ap == aq) continue;
-                    const float r = between_rel(ex, ey, ez, lm_pos + (c * KM + x) * 3, lm_pos + ((c + 1) * KM + y) * 3, K);
+                    const float r = between_rel(ex, ey, ez, reinterpret_cast<const float *>(lm + 2 * (c * KM + x)),
+                                                reinterpret_cast<const float *>(lm + 2 * ((c + 1) * KM + y)), K);
                     const uint32_t rh = __float_as_uint(r), lp = 0xffffffffu - (uint32_t)ap,
                                    lq = 0xffffffffu - (uint32_t)aq;
                     if (rh > h || (rh == h && (lp > wp || (lp == wp && lq > wq)))) { h = rh; wp = lp; wq = lq; }
