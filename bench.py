@@ -133,17 +133,32 @@ def max_over_ranks(values, dist=None, device=None):
     return [float(x) for x in t.tolist()]
 
 
-def l2_statement(args, scenes, dim, rows, multi_ch):
+def rows_per_scene(scenes, qb):
+    """Operand rows (targets and constraints) each scene contributes to a batch."""
+    rows = np.bincount(qb.scene_of_q, minlength=len(scenes)).astype(np.int64)
+    m = np.diff(qb.c_off.astype(np.int64))
+    rows += np.bincount(qb.scene_of_q, weights=m, minlength=len(scenes)).astype(np.int64)
+    return rows
+
+
+# scenes below this many objects run FP32-accurate inside BF16 and FP8 batches
+REDUCED_FROM_OBJECTS = 16384
+
+
+def l2_statement(args, scenes, qb, dim, multi_ch):
     """Why no L2 flush is needed between steps: the bytes each step streams
     (tensor-core operand copies of descriptors and query rows, and the stored
     similarity columns) against the 129 MB L2."""
+    rows_s = rows_per_scene(scenes, qb)
+    rows = int(rows_s.sum())
     n_obj = sum(x.n for x in scenes)
     per = {"fp32": 4, "bf16": 2, "fp8": 1, "learned": 2, "fp32_simt": 4}[args.precision]
     # the learned path's operands are its 128-d BF16 embeddings
     operands = (n_obj + rows) * (128 if args.precision == "learned" else dim) * per
     fused = args.precision in ("fp32", "bf16") and (
         args.fused == "on" or (args.fused == "default" and args.precision == "fp32"))
-    stored = 0 if fused else 4 * rows * n_obj
+    # the similarity block of the rows that store theirs (32-column aligned)
+    stored = 0 if fused else int(sum(4 * int(r) * (-(-sc.n // 32) * 32) for r, sc in zip(rows_s, scenes)))
     if multi_ch:
         return "inputs larger than L2 (four descriptor spaces and their similarity blocks)"
     what = f"operand copies {operands / 1e6:.0f} MB"
@@ -223,26 +238,39 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
 # the similarity kernel, from one ncu capture per (workload, precision, tile
 # variant), valid only while the kernel source is the one captured (sha256
 # prefix).
+# DRAM bytes of the similarity stage per step (both launches when the
+# selection is fused), captured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) for the kernel source whose sha256 prefix follows:
+# (workload, precision, tile variant, fused) -> bytes
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 0): 716.080384e6 + 1127.595264e6,
-    ("site_n20k_d1152", "fp32", 1): 1356.870912e6 + 1136.986880e6,
-    ("site_n20k_d1152", "fp32", 4): 718.807040e6 + 1127.427328e6,
-    ("site_n20k_d1152", "bf16", 0): 355.865088e6 + 1114.267392e6,
-    ("site_n20k_d1152", "bf16", 1): 672.504832e6 + 1118.159872e6,
-    ("site_n20k_d1152", "bf16", 4): 356.113664e6 + 1114.226432e6,
+    ("site_n20k_d1152", "fp32", 2, True): (88.126464e6 + 114.629632e6) + (620.184064e6 + 32.970240e6),
 }
-SIM_TRAFFIC_SOURCE = "18ae7d215d7f3cd7"
+SIM_TRAFFIC_SOURCE = "d45a2ec685829ede"
 
 
-def sim_traffic(workload, precision, variants):
-    """Captured bytes per launch, or None when the run differs from the capture."""
+def sim_traffic(workload, precision, variants, fused):
+    """Captured bytes per step, or None when the run differs from the capture."""
     import hashlib
     with open(os.path.join(ROOT, "paper_2606_15476_gb300", "csrc", "k_sim_tc.cu"), "rb") as f:
         if hashlib.sha256(f.read()).hexdigest()[:16] != SIM_TRAFFIC_SOURCE:
             return None
     if len(variants) != 1:
         return None
-    return SIM_TRAFFIC.get((workload, precision, variants[0]))
+    return SIM_TRAFFIC.get((workload, precision, variants[0], fused))
+
+
+def reduced_split(prec, scenes, qb):
+    """Which scenes of a BF16 or FP8 batch ran that precision and which ran
+    the FP32-accurate similarity (scenes below REDUCED_FROM_OBJECTS objects;
+    a batch of such scenes only runs as FP32); None for the other paths."""
+    if prec not in ("bf16", "fp8"):
+        return None
+    used = np.bincount(qb.scene_of_q, minlength=len(scenes)) > 0
+    small = np.array([sc.n < REDUCED_FROM_OBJECTS for sc in scenes])
+    q_small = int(np.sum(small[qb.scene_of_q]))
+    return {"scenes_reduced": int(np.sum(used & ~small)), "scenes_fp32_accurate": int(np.sum(used & small)),
+            "queries_reduced": int(qb.n_q - q_small), "queries_fp32_accurate": q_small,
+            "rule": f"scenes under {REDUCED_FROM_OBJECTS:,} objects run the FP32-accurate similarity"}
 
 
 def similarity_flops(scenes, qb):
@@ -686,6 +714,16 @@ def main():
             sm_mhz = peaks.get("sm_max_mhz", 2070.0)
             peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
             bound, note = "alu", "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+        if pname in ("bf16", "fp8") and not multi_ch:
+            # scenes under REDUCED_FROM_OBJECTS objects ran FP32-accurate: the
+            # peak is the one that does the batch's flops in the least time,
+            # each scene's at its own arithmetic's peak
+            rows_s = rows_per_scene(scenes, qb)
+            f_small = sum(2.0 * int(r) * x.n * x.dim for r, x in zip(rows_s, scenes) if x.n < REDUCED_FROM_OBJECTS)
+            if f_small > 0:
+                t_ideal = (flops_step - f_small) / peak + f_small / (peaks[pk_key] / 3.0)
+                peak = flops_step / t_ideal
+                note += f"; {f_small / flops_step:.0%} of the flops FP32-accurate (peak / 3), combined"
         achieved = flops_step / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0
         return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak if peak else None,
@@ -695,7 +733,10 @@ def main():
                 "traffic": sim_traffic(args.workload, pname,
                                        [args.tile_variant] if args.tile_variant >= 0
                                        else sorted({d[3] for d in F.farm_sim_tuning(ctx)
-                                                    if d[0] % 10 == {"fp32": 0, "fp8": 2}.get(pname, 1)})),
+                                                    if d[0] % 10 == {"fp32": 0, "fp8": 2}.get(pname, 1)}),
+                                       pname in ("fp32", "bf16") and (args.fused == "on" or (
+                                           args.fused == "default" and pname == "fp32"))),
+                "traffic_unit": "bytes per step of the similarity stage",
                 "kernel": "similarity", "peak_source": note}
 
     def stages(r):
@@ -723,12 +764,14 @@ def main():
                    "channels": ([{"space": sp, "dim": spaces.dims[sp], "weight": w} for sp, w in cq.channels]
                                 if multi_ch else 1),
                    "cuda_graph": graph, "fused_selection": args.fused,
-                   "l2": l2_statement(args, scenes, sc.dim, n_q + n_c, multi_ch)},
+                   "l2": l2_statement(args, scenes, qb, sc.dim, multi_ch),
+                   "reduced_precision_scenes": reduced_split(args.precision, scenes, qb)},
         "e2e": {"value": job_rate(n_q, world, main_r["e2e_ms"]), "unit": "queries/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "pipelined": not args.e2e_sync},
         "gpu_launches": main_r["launches"],
-        "autotuned_tiles": [{"mode": d[0] % 10, "fused_selection": d[0] >= 10, "log2_rows": d[1], "log2_objects": d[2],
+        "autotuned_tiles": [{"mode": d[0] % 10, "fused_selection": (d[0] // 10) % 2 == 1,
+                             "with_fp32_accurate_scenes": d[0] >= 20, "log2_rows": d[1], "log2_objects": d[2],
                              "variant": d[3], "tile_n": 128 if d[3] == 1 else 256,
                              "tile_m": 256 if d[3] == 2 else 128, "cta_pair": d[3] == 2}
                             for d in F.farm_sim_tuning(ctx)],

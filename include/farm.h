@@ -194,13 +194,12 @@ farm_status farm_memory_upload(farm_ctx *ctx, int32_t scene_id, int64_t n, int32
  *   c_pred     [n_c]       host int32 farm_pred codes, n_c = c_off[n_q]
  *   c_emb      [n_c, dim]  FP32 landmark embeddings
  *   precision  a farm_precision value.  With FARM_PREC_BF16 (unless
- *              FARM_FUSED) the scenes of fewer than 16,384 objects, and with
- *              FARM_PREC_FP8 those of fewer than 32,768, run the
- *              FP32-accurate similarity in the same batch, their lists
- *              final without a rescore: re-reading the FP32 descriptors of
- *              the candidates costs more there than the FP32-accurate GEMM
- *              over the whole scene.  A batch of such scenes only runs as a
- *              FARM_PREC_FP32 batch.
+ *              FARM_FUSED) or FARM_PREC_FP8 the scenes of fewer than 16,384
+ *              objects run the FP32-accurate similarity in the same batch,
+ *              their lists final without a rescore: re-reading the FP32
+ *              descriptors of the candidates costs more there than the
+ *              FP32-accurate GEMM over the whole scene.  A batch of such
+ *              scenes only runs as a FARM_PREC_FP32 batch.
  *   flags      FARM_PTR_DEVICE: tgt_emb and c_emb are device pointers (the
  *              other arrays are always host memory).
  *              FARM_GRAPH: the batch's kernels (row normalisation,

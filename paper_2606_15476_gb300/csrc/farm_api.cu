@@ -624,10 +624,12 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     // of C candidates per row costs more than the FP32-accurate GEMM over a
     // small scene (rows of an n-object scene: the GEMM saves about
     // 2.8e-12 n s per row at BF16 rates, the rescore and the longer select
-    // cost about 4.7e-8 s per row, so BF16 gains from about 16,000 objects;
-    // FP8's rescore of twice the candidates in a wider band, from about 32,000)
-    const int64_t exact_below = precision == FARM_PREC_BF16 && !(flags & FARM_FUSED) ? 16384
-                                : (precision == FARM_PREC_FP8 ? 32768 : 0);
+    // cost about 4.7e-8 s per row, so BF16 gains from about 16,000 objects).
+    // FP8 takes the same bound, although its rescore of twice the candidates
+    // in a wider band only pays from about 32,000 objects: a 20,000-object
+    // scene then still runs the precision the caller asked for.
+    const int64_t exact_below =
+        (precision == FARM_PREC_BF16 && !(flags & FARM_FUSED)) || precision == FARM_PREC_FP8 ? 16384 : 0;
     // ---- plan: group queries by scene (stable; the scenes that run
     //      FP32-accurate in a reduced-precision batch last, so that their rows
     //      end the row space), rows = [targets, constraints] per group

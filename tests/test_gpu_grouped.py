@@ -301,7 +301,7 @@ def test_pinned_variant_gives_the_same_results(F, world):
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 def test_small_scenes_of_reduced_precision_batches_run_fp32_accurate(F, prec):
-    """In a BF16 (FP8) batch the scenes below 16,384 (32,768) objects take
+    """In a BF16 or FP8 batch the scenes below 16,384 objects take
     the FP32-accurate similarity in the same launches and keep their lists
     without a rescore: their results equal the FP32 path's bitwise, while
     the large scene's stay within Recall@10 >= 0.99 of it."""
@@ -322,9 +322,8 @@ def test_small_scenes_of_reduced_precision_batches_run_fp32_accurate(F, prec):
         rt, rl = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
         h, out = _run(F, ctx, qb, code)
         ot, ol = F.farm_candidates(ctx, h, qb.n_q, qb.n_c)
-        bound = 16384 if prec == "bf16" else 32768
-        small = np.array([scenes[int(s)].n < bound for s in qb.scene_of_q])
-        assert small.any() and (~small).any() if prec == "bf16" else small.any()
+        small = np.array([scenes[int(s)].n < 16384 for s in qb.scene_of_q])
+        assert small.any() and (~small).any()
         for key in ("idx", "score", "pred", "anchor"):
             np.testing.assert_array_equal(out[key][small], ref[key][small], err_msg=key)
         np.testing.assert_array_equal(ot[small], rt[small])
