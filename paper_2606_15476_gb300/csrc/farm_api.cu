@@ -44,6 +44,23 @@ struct farm_ctx {
     std::vector<GraphEntry> graphs;
     uint64_t graph_clock = 0;
     bool capturing = false;
+    // The last FARM_GRAPH batch's query graphs and plan.  A batch whose query
+    // graphs equal them (scenes, classes, constraint offsets and predicates,
+    // precision, flags; device embeddings at the same addresses) is replayed
+    // from its cached graph without planning: the staging buffers the graph
+    // reads still hold the plan, since only farm_query_batch and
+    // farm_query_batch_rrf write them and both clear `valid` first.
+    struct Replay {
+        bool valid = false;
+        int32_t precision = 0, dim = 0, pinned = -1;
+        uint32_t flags = 0;
+        int64_t n_q = 0, n_c = 0;
+        const float *src_t = nullptr, *src_c = nullptr;
+        uint64_t ws_gen = 0, scene_gen = 0, mlp_version = 0;
+        std::vector<int32_t> scene_of_q, tgt_cls, c_off, c_pred;
+        std::vector<int64_t> key[2];      // graph key per host-row slot (slot 0 for device rows)
+        int32_t rtgt = 0, klm = 0, min_n = 0;
+    } replay;
     // profiling marks
     struct Mark { int stage; cudaEvent_t a, b; };
     std::vector<Mark> marks;
@@ -337,6 +354,102 @@ int32_t reduced_keep_landmark(const farm_params &p, int32_t prec, int32_t klm, i
 // C ABI
 // ===========================================================================
 
+namespace {
+
+// Host embedding rows of a batch: slot `slot` (one half) of the two-slot
+// device buffer (sized by the batch that planned it).
+float *raw_slot_ptr(farm_ctx *ctx, int slot)
+{
+    const farm::Ctx &c = ctx->c;
+    const size_t half = c.ws.bytes[farm::B_RAW_PIPE] / 2 / 256 * 256;
+    return reinterpret_cast<float *>(static_cast<uint8_t *>(c.ws.ptr[farm::B_RAW_PIPE]) + slot * half);
+}
+
+// The host rows into d_raw on the copy stream once the slot is free again;
+// the ctx stream waits for the copy.
+cudaError_t copy_host_rows(farm_ctx *ctx, int slot, float *d_raw, const float *tgt_emb, const float *c_emb,
+                           int64_t n_q, int64_t n_c, int32_t dim)
+{
+    cudaError_t e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_slot_free[slot], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_raw, tgt_emb, (size_t)n_q * dim * 4, cudaMemcpyHostToDevice, ctx->copy_stream);
+    if (e == cudaSuccess && n_c > 0)
+        e = cudaMemcpyAsync(d_raw + (size_t)n_q * dim, c_emb, (size_t)n_c * dim * 4, cudaMemcpyHostToDevice,
+                            ctx->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->c.stream, ctx->ev_copied[slot], 0);
+    return e;
+}
+
+template <class T>
+bool same_array(const std::vector<T> &v, const T *p, int64_t n)
+{
+    return (int64_t)v.size() == n && (n == 0 || std::memcmp(v.data(), p, (size_t)n * sizeof(T)) == 0);
+}
+
+// Whether the recorded batch has the same query graphs and launch inputs as
+// the call's (everything the recorded plan and its graphs depend on).
+bool replay_same(const farm_ctx *ctx, int64_t n_q, const int32_t *scene_of_q, const float *tgt_emb,
+                 const int32_t *tgt_cls, const int32_t *c_off, const int32_t *c_pred, const float *c_emb,
+                 int32_t precision, uint32_t flags)
+{
+    const farm_ctx::Replay &r = ctx->replay;
+    const farm::Ctx &c = ctx->c;
+    if (r.precision != precision || r.flags != flags || r.n_q != n_q || r.pinned != c.pinned_variant ||
+        r.ws_gen != c.ws_gen || r.scene_gen != c.scene_gen || r.mlp_version != c.mlp.version)
+        return false;
+    if ((flags & FARM_PTR_DEVICE) && (r.src_t != tgt_emb || r.src_c != c_emb)) return false;
+    if (!same_array(r.c_off, c_off, n_q + 1)) return false;
+    const int64_t n_c = c_off[n_q];
+    if (n_c != r.n_c || (n_c > 0 && !c_pred)) return false;
+    return same_array(r.scene_of_q, scene_of_q, n_q) && same_array(r.tgt_cls, tgt_cls, n_q) &&
+           (n_c == 0 || same_array(r.c_pred, c_pred, n_c));
+}
+
+// A batch equal to the recorded one, replayed from its graph: the host rows'
+// copy (host embeddings) and the graph launch.  `done` is false when the call
+// needs planning (no record, a different batch, or its graph evicted).
+farm_status replay_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of_q, const float *tgt_emb,
+                         const int32_t *tgt_cls, const int32_t *c_off, const int32_t *c_pred, const float *c_emb,
+                         int32_t precision, uint32_t flags, uint64_t *batch_handle, bool &done)
+{
+    done = false;
+    farm_ctx::Replay &r = ctx->replay;
+    Ctx &c = ctx->c;
+    if (!r.valid || !replay_same(ctx, n_q, scene_of_q, tgt_emb, tgt_cls, c_off, c_pred, c_emb, precision, flags))
+        return FARM_OK;
+    const bool dev = (flags & FARM_PTR_DEVICE) != 0;
+    const int slot = dev ? 0 : ctx->raw_slot;
+    if (r.key[slot].empty()) return FARM_OK;
+    farm_ctx::GraphEntry *hit = nullptr;
+    for (auto &ge : ctx->graphs)
+        if (ge.key == r.key[slot]) hit = &ge;
+    if (!hit) return FARM_OK;
+    done = true;
+    c.batch_valid = false;
+    *batch_handle = 0;
+    CK(cudaSetDevice(c.device));
+    if (!dev) {
+        CK(copy_host_rows(ctx, slot, raw_slot_ptr(ctx, slot), tgt_emb, c_emb, n_q, r.n_c, r.dim));
+        ctx->raw_slot ^= 1;
+    }
+    hit->used = ++ctx->graph_clock;
+    CK(cudaGraphLaunch(hit->exec, c.stream));
+    c.launches += hit->launches;
+    if (!dev) CK(cudaEventRecord(ctx->ev_slot_free[slot], c.stream));
+    c.batch_gen += 1;
+    c.batch_valid = true;
+    c.batch_nq = n_q;
+    c.batch_nc = r.n_c;
+    c.batch_rtgt = r.rtgt;
+    c.batch_klm = r.klm;
+    c.batch_min_n = r.min_n;
+    *batch_handle = c.batch_gen;
+    return FARM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *farm_version(void) { return "farm-gb300 0.1 (sm_103a)"; }
@@ -570,6 +683,13 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         return fail(ctx, FARM_EINVAL, "scene_of_q, tgt_emb, tgt_cls and c_off must be non-null");
     const bool dev = (flags & FARM_PTR_DEVICE) != 0;
     bool graph = (flags & FARM_GRAPH) != 0;
+    if (graph && n_q > 0) {
+        bool done = false;
+        const farm_status st = replay_batch(ctx, n_q, scene_of_q, tgt_emb, tgt_cls, c_off, c_pred, c_emb, precision,
+                                            flags, batch_handle, done);
+        if (done) return st;
+    }
+    ctx->replay.valid = false;       // planning rewrites the staging buffers
     int64_t n_c = 0;
     int32_t dim = -1;
     int64_t min_n = INT64_MAX, max_n = 0;
@@ -765,21 +885,10 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     if (!dev) {
         uint8_t *pipe = nullptr;
         CK(ws_get(ctx, farm::B_RAW_PIPE, 2 * (size_t)round_up((int64_t)(n_q + n_c) * dim * 4, 256), &pipe));
-        const size_t half = c.ws.bytes[farm::B_RAW_PIPE] / 2 / 256 * 256;
-        d_raw = reinterpret_cast<float *>(pipe + raw_slot * half);
+        d_raw = raw_slot_ptr(ctx, raw_slot);
         ctx->raw_slot ^= 1;
     }
     if (graph && precision == FARM_PREC_LEARNED) CK(farm::learned_reserve(ctx, rows_total));
-    // on the copy stream once the slot is free again; the ctx stream waits for it
-    auto copy_inputs = [&](cudaMemcpyKind kind) -> cudaError_t {
-        cudaError_t e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_slot_free[raw_slot], 0);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_raw, tgt_emb, (size_t)n_q * dim * 4, kind, ctx->copy_stream);
-        if (e == cudaSuccess && n_c > 0)
-            e = cudaMemcpyAsync(d_raw + (size_t)n_q * dim, c_emb, (size_t)n_c * dim * 4, kind, ctx->copy_stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied[raw_slot], ctx->copy_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(c.stream, ctx->ev_copied[raw_slot], 0);
-        return e;
-    };
 
     // ---- similarity batches: row ranges ("pieces") of the scene groups are
     //      laid end to end in S while they fit kSimCapBytes; each batch takes
@@ -790,8 +899,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     //      merge) for the others; then one FP32 rescore launch on the
     //      reduced-precision paths
     struct Batch { size_t p0 = 0, np = 0; int64_t s_floats = 0, rows = 0, blocks = 0, tblocks = 0, tmp = 0,
-                   tops = 0, fused_rows = 0, exact_rows = 0; int32_t smem_sel = 1, smem_merge = 0, max_union = 1;
-                   bool chunked = false; };
+                   tops = 0, fused_rows = 0, twopass_rows = 0, exact_rows = 0; int32_t smem_sel = 1, smem_merge = 0,
+                   max_union = 1, gmax_twopass = 1; bool chunked = false; };
     std::vector<farm::Piece> pieces;
     std::vector<int32_t> piece_sid;
     std::vector<Batch> batches;
@@ -809,7 +918,8 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     // over R fs of them for a list of R
     // (FP32 and BF16 only: E4M3's few significant bits tie many FP8 entries at
     // any threshold, and the learned path's lists of 512 would need a sample
-    // of half the row and still crowd the buffer)
+    // of half the row and still crowd the buffer -- it takes the two-pass
+    // form below on long rows)
     // Which scenes' rows are fused: FARM_FUSED fuses every scene, FARM_UNFUSED
     // none; by default the FP32 path fuses a scene whose sample holds at
     // least 16 times its target list (a shorter sample sets a threshold that
@@ -819,9 +929,26 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     // than the stores of S).  A batch may hold fused and unfused scenes.
     const bool fusable = (precision == FARM_PREC_FP32 || precision == FARM_PREC_BF16) && c.pinned_variant != 1 &&
                          !(flags & FARM_UNFUSED);
+    // The learned path's lists (512 target, 128 landmark candidates) over
+    // long rows take the two-pass form instead: the similarity kernel first
+    // stores only the group maxima of every tile (its 128-d products are
+    // cheap to compute twice; the values of S are the cost), the threshold is
+    // each row's R-th largest group maximum, and the second launch keeps the
+    // entries reaching it.  With G groups of 32 in a row, about R of them
+    // reach the threshold and the kept entries number about
+    // -n ln(1 - R/G) / 32: a scene takes it when G >= 4 R (some 600 entries per
+    // 512-list, inside the merge capacity), i.e. from 65,536 objects.
+    auto twopass_scene = [&](const Scene &s) {
+        if (precision != FARM_PREC_LEARNED || (flags & FARM_UNFUSED) || c.pinned_variant == 1) return false;
+        const int64_t Rs = std::min<int64_t>(Rb, s.n);
+        const int64_t kt = reduced_keep_target(p, precision, (int32_t)Rs, s.n);
+        const int64_t G = farm::group_count(s.n, farm::group_shift_for(s.n));
+        return G >= 4 * kt && G <= farm::kMaximaTauKeys;
+    };
     const int32_t keep_max = reduced ? std::max(cstride_t, cstride_l) : std::max(stride_t, stride_l);
     const int32_t fs = keep_max <= 128 ? 8 : (keep_max <= 256 ? 4 : 2);
     auto fuse_scene = [&](const Scene &s) {
+        if (twopass_scene(s)) return true;
         if (!fusable) return false;
         if (flags & FARM_FUSED) return true;
         if (precision != FARM_PREC_FP32) return false;
@@ -831,7 +958,9 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     bool fused = false;            // some scene of the batch is fused
     for (const auto &g : groups) fused |= fuse_scene(c.scenes[g.sid]);
     // the length of a scene's selected rows: its sample's when it is fused
-    auto sel_len = [&](const Scene &s) { return fuse_scene(s) ? farm::sample_width(s.n, fs) : s.n; };
+    auto sel_len = [&](const Scene &s) {
+        return fuse_scene(s) && !twopass_scene(s) ? farm::sample_width(s.n, fs) : s.n;
+    };
     int32_t tmp_stride = 4;
     for (const auto &g : groups) {
         const Scene &s = c.scenes[g.sid];
@@ -846,13 +975,15 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     for (const auto &g : groups) {
         const Scene &s = c.scenes[g.sid];
         const bool fz = fuse_scene(s);
+        const bool two = twopass_scene(s);
         const int64_t nsel = sel_len(s);
-        // fused: the stored sample tiles, compacted
-        const int64_t ld = fz ? farm::col_tiles(s.n, 256, farm::kColSample, fs) * 256 : round_up(s.n, 32);
+        // fused: the stored sample tiles, compacted; two-pass: no stored values
+        const int64_t ld = two ? 0 : (fz ? farm::col_tiles(s.n, 256, farm::kColSample, fs) * 256 : round_up(s.n, 32));
         const int64_t rows_g = g.nq + g.nc;
         const int32_t Rs = (int32_t)std::min<int64_t>(Rb, s.n);
         const int32_t klm = (int32_t)std::min<int64_t>(p.k_anchor, s.n);
-        const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(rows_g, (int64_t)(kSimCapBytes / (ld * 4))));
+        const int64_t chunk =
+            ld == 0 ? rows_g : std::max<int64_t>(1, std::min<int64_t>(rows_g, (int64_t)(kSimCapBytes / (ld * 4))));
         const int gshift = farm::group_shift_for(nsel);
         const int32_t uni = (int32_t)std::min<int64_t>(farm::group_count(nsel, gshift), 8192);
         // long rows of the shared-memory select: column chunks, merged after
@@ -895,7 +1026,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             // the select keeps the whole-row lengths, or, fused, as many of them as the sample holds
             pc.keep_t = (int32_t)std::min<int64_t>(pc.fkeep_t, nsel);
             pc.keep_l = (int32_t)std::min<int64_t>(pc.fkeep_l, nsel);
-            pc.fs = fz ? fs : 0;
+            pc.fs = two ? -1 : (fz ? fs : 0);
             max_fkeep = std::max(max_fkeep, std::max(pc.fkeep_t, pc.fkeep_l));
             pc.tmp_off = -1;
             pc.tops_off = -1;
@@ -907,6 +1038,10 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                 pc.tops_off = bt.tops;
                 bt.tops += nr * farm::group_stride(nsel, gshift);
                 bt.fused_rows += nr;
+                if (two) {
+                    bt.twopass_rows += nr;
+                    bt.gmax_twopass = std::max<int32_t>(bt.gmax_twopass, (int32_t)farm::group_count(nsel, gshift));
+                }
             } else if (tile_tops) {
                 // a row goes to the thresholded select when its group maxima
                 // number at least its list length, or it is short enough to sort whole
@@ -1053,15 +1188,18 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                         const farm::Piece &pc = pieces[k];
                         const Scene &sc = c.scenes[piece_sid[k]];
                         // fused pieces: their sample tiles (table 0), the others (table 1);
-                        // the others' pieces: every tile (table 0), none (table 1); in a
-                        // batch with FP32-accurate scenes (never fused) theirs are table 1's
+                        // two-pass pieces: every tile's group maxima (table 0), every tile
+                        // emitting (table 1); the others' pieces: every tile (table 0), none
+                        // (table 1); in a batch with FP32-accurate scenes (never fused)
+                        // theirs are table 1's
                         const int mode = any_exact ? ((t == 1) == (pc.exact != 0) ? farm::kColAll : -1)
                                          : pc.fs == 0 ? (t == 0 ? farm::kColAll : -1)
+                                         : pc.fs < 0  ? farm::kColAll
                                                       : (t == 0 ? farm::kColSample : farm::kColRest);
                         farm::GemmPiece gp{};
                         gp.q_row0 = pc.q_row0;
-                        gp.s_off = mode == farm::kColRest ? 0 : pc.s_off;
-                        gp.tops_off = (tile_tops && mode != farm::kColRest) ? pc.tops_off : -1;
+                        gp.s_off = pc.fs < 0 ? -1 : (mode == farm::kColRest ? 0 : pc.s_off);
+                        gp.tops_off = (tile_tops && mode != farm::kColRest && !(pc.fs < 0 && t == 1)) ? pc.tops_off : -1;
                         gp.scale_d = sim_mode == farm::kSimFp8 && !pc.exact ? sc.desc_scale : nullptr;
                         gp.bmap = d_blob + off_maps +
                                   ((size_t)map_of_scene[piece_sid[k]] * nv + vi) * 2 * farm::kTensorMapBytes;
@@ -1116,7 +1254,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     CK(cudaMemcpyAsync(d_meta, h_meta, (size_t)n_q * 8 * 4, cudaMemcpyHostToDevice, c.stream));
     CK(cudaMemcpyAsync(d_blob, ctx->h_blob, blob_bytes, cudaMemcpyHostToDevice, c.stream));
     CK(cudaEventRecord(ctx->stage_done, c.stream));
-    if (!dev) CK(copy_inputs(cudaMemcpyHostToDevice));
+    if (!dev) CK(copy_host_rows(ctx, raw_slot, d_raw, tgt_emb, c_emb, n_q, n_c, dim));
     auto enqueue = [&]() -> farm_status {
         // ---- stage 0: normalisation (the staging copies above are not part of it)
         // (with FP32-accurate scenes in a reduced-precision batch, their rows
@@ -1207,9 +1345,14 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
             mark_end(ctx, m1);
             const int m2 = mark_begin(ctx, 2);
             const farm::Piece *dp = d_pieces + bt.p0;
-            if (bt.fused_rows > 0) {
+            if (bt.fused_rows > bt.twopass_rows) {
                 // each row's threshold from its sample's group maxima; the sample's entries reaching it
                 LAUNCH(farm::launch_fuse_sample_tau(d_sim, d_tops, dp, (int32_t)bt.np, bt.rows, emit, c.stream));
+            }
+            if (bt.twopass_rows > 0) {
+                // two-pass rows: each row's threshold from the group maxima of its whole row
+                LAUNCH(farm::launch_fuse_maxima_tau(d_tops, dp, (int32_t)bt.np, bt.rows, emit, bt.gmax_twopass,
+                                                    c.stream));
             }
             if (bt.blocks > 0)
                 LAUNCH(farm::launch_select_grouped(d_sim, dp, (int32_t)bt.np, bt.blocks, bt.smem_sel, sel_ti, sel_tc,
@@ -1260,7 +1403,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
                                                     precision == FARM_PREC_LEARNED ? nullptr : bsel_tv, cstride_t,
                                                     bsel_l, precision == FARM_PREC_LEARNED ? nullptr : bsel_lv,
                                                     cstride_l, band, tsel_idx, tsel_cos, stride_t, lsel_idx, stride_l,
-                                                    c.stream));
+                                                    c.d_err, c.stream));
             }
             mark_end(ctx, bt.fused_rows > 0 ? m2c : m2);
         }
@@ -1285,6 +1428,7 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         return FARM_OK;
     };
 
+    std::vector<int64_t> graph_key;
     if (!graph) {
         const farm_status st = enqueue();
         if (st != FARM_OK) return st;
@@ -1293,12 +1437,13 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         // arguments (device inputs are read where the caller keeps them)
         std::vector<int64_t> key = {precision, (int64_t)(flags & (FARM_FUSED | FARM_UNFUSED)), n_q, n_c, dim, (int64_t)c.ws_gen, (int64_t)c.scene_gen,
                                     (int64_t)c.mlp.version, (int64_t)(intptr_t)src_t, (int64_t)(intptr_t)src_c,
-                                    (int64_t)groups.size()};
+                                    (int64_t)c.pinned_variant, (int64_t)groups.size()};
         for (const auto &g : groups) {
             key.push_back(g.sid);
             key.push_back(g.nq);
             key.push_back(g.nc);
         }
+        graph_key = key;
         farm_ctx::GraphEntry *hit = nullptr;
         for (auto &ge : ctx->graphs)
             if (ge.key == key) hit = &ge;
@@ -1349,6 +1494,35 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
     c.batch_klm = stride_l;
     c.batch_min_n = (int32_t)std::min<int64_t>(min_n, 0x7fffffff);
     *batch_handle = c.batch_gen;
+    if (graph && !graph_key.empty()) {
+        // record the batch for replay (its other slot's graph stays usable
+        // when the query graphs are the same as the record's)
+        farm_ctx::Replay &r = ctx->replay;
+        if (!replay_same(ctx, n_q, scene_of_q, tgt_emb, tgt_cls, c_off, c_pred, c_emb, precision, flags)) {
+            r.precision = precision;
+            r.flags = flags;
+            r.n_q = n_q;
+            r.n_c = n_c;
+            r.pinned = c.pinned_variant;
+            r.ws_gen = c.ws_gen;
+            r.scene_gen = c.scene_gen;
+            r.mlp_version = c.mlp.version;
+            r.src_t = dev ? tgt_emb : nullptr;
+            r.src_c = dev ? c_emb : nullptr;
+            r.scene_of_q.assign(scene_of_q, scene_of_q + n_q);
+            r.tgt_cls.assign(tgt_cls, tgt_cls + n_q);
+            r.c_off.assign(c_off, c_off + n_q + 1);
+            r.c_pred.assign(c_pred, c_pred + n_c);
+            r.key[0].clear();
+            r.key[1].clear();
+        }
+        r.dim = dim;
+        r.key[dev ? 0 : raw_slot] = graph_key;
+        r.rtgt = stride_t;
+        r.klm = stride_l;
+        r.min_n = c.batch_min_n;
+        r.valid = true;
+    }
     return FARM_OK;
 }
 
@@ -1422,6 +1596,7 @@ farm_status farm_query_batch_rrf(farm_ctx *ctx, int32_t scene_id, int64_t n_q, i
     Ctx &c = ctx->c;
     if (!batch_handle) return fail(ctx, FARM_EINVAL, "batch_handle must be non-null");
     if (flags & FARM_GRAPH) return fail(ctx, FARM_EINVAL, "FARM_GRAPH is not supported for fused batches");
+    ctx->replay.valid = false;       // this batch rewrites the staging buffers
     if (scene_id < 0 || scene_id >= kMaxScenes || !c.scenes[scene_id].present)
         return fail(ctx, FARM_EINVAL, "unknown scene");
     if (n_q < 1 || n_q > 0x7fffffff) return fail(ctx, FARM_EINVAL, "n_q must lie in [1, 2^31)");

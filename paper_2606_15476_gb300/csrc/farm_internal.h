@@ -327,7 +327,7 @@ __host__ __device__ inline int64_t sample_width(int64_t n, int s)
 // One block of query rows against one scene in a grouped similarity launch.
 struct GemmPiece {
     int64_t q_row0;          // first row of the block in the operand arrays
-    int64_t s_off;           // S offset of the block's first row (floats; a multiple of 4)
+    int64_t s_off;           // S offset of the block's first row (floats; a multiple of 4); -1: values not stored
     int64_t tops_off;        // group-maxima offset of the first row (floats, a multiple of 8); -1: none
     const float *scale_d;    // FP8 per-object scales of the scene
     const void *bmap;        // the scene's two B tensor maps (device memory, 64-byte aligned)
@@ -371,8 +371,10 @@ bool sim_tc_encode_b(int mode, int variant, void *out, const void *d0, const voi
 // ([rows_total, dim_pad] in the mode's element type) and FP8 row scales
 // scale_q.  S and tops are the bases the pieces' offsets refer to (tops
 // nullable).
-// With `emit` (its pieces in kColRest mode, variants 0 and 2 only) the
-// values are appended to the rows' candidate buffers instead of stored.
+// With `emit` (its pieces in kColRest mode, or kColAll for two-pass rows;
+// variants 0 and 2 only) the values reaching each row's threshold are
+// appended to the rows' candidate buffers instead of stored.  A piece with
+// s_off -1 stores no values, only its group maxima.
 cudaError_t launch_sim_tc_grouped(int mode, int variant, const void *q0, const void *q1, int64_t rows_total,
                                   int32_t dim_pad, const GemmPiece *pieces, int32_t n_pieces, int64_t total_tiles,
                                   float *S, float *tops, const float *scale_q, int num_sms, int32_t *err,
@@ -443,7 +445,8 @@ struct Piece {
     int32_t gshift;         // group maxima over 2^gshift objects (thresholded select)
     int32_t fkeep_t, fkeep_l; // fused selection: list lengths over the whole row (keep_t / keep_l: over its sample)
     int32_t n_obj;          // objects of the scene (n: the selected row length, its sample's when fused)
-    int32_t fs;             // fused selection: the sampling stride (every fs-th tile of 256); 0: not fused
+    int32_t fs;             // fused selection: the sampling stride (every fs-th tile of 256); 0: not fused;
+                            // -1: two-pass (the group maxima of every tile, then every tile emits)
     int32_t exact;          // reduced-precision batch: 1 when the piece's scene runs the FP32-accurate
                             // similarity, its lists final (the rescore copies them)
 };
@@ -495,6 +498,12 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
 // counts start at zero.
 cudaError_t launch_fuse_sample_tau(const float *S, const float *tops, const Piece *pieces, int32_t n_pieces,
                                    int64_t total_rows, const FuseEmit &emit, cudaStream_t st);
+// Two-pass rows (Piece::fs < 0): each row's threshold from the group maxima
+// of its whole row (the similarity launch stored no values), at most gmax of
+// them per row (<= kMaximaTauKeys), and a zero count.
+constexpr int kMaximaTauKeys = 12288;
+cudaError_t launch_fuse_maxima_tau(const float *tops, const Piece *pieces, int32_t n_pieces, int64_t total_rows,
+                                   const FuseEmit &emit, int32_t gmax, cudaStream_t st);
 cudaError_t launch_fuse_final(const Piece *pieces, int32_t n_pieces, int64_t total_rows, int32_t *tsel_idx,
                               float *tsel_cos, int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l,
                               const FuseEmit &emit, int32_t *n_overflow, int32_t *overflow_rows, int32_t *n_big,
@@ -532,12 +541,13 @@ cudaError_t launch_copy_lists(const Piece *pieces, int32_t n_pieces, int64_t row
 // exact FP32 dot products of the unit rows Q32 and the descriptors d32, and
 // the R / klm best in rank order go to tsel_idx / tsel_cos and lsel_idx (-1 /
 // 0 past the list).  With values, a candidate more than `band` below the
-// list's last kept value is skipped.
+// list's R-th value is skipped.  A bulk copy that does not arrive within the
+// bounded wait sets kErrTimeout in *err and leaves that row's list empty.
 cudaError_t launch_rescore_grouped(const Piece *pieces, int32_t n_pieces, int64_t total_rows, const float *Q32,
                                    int32_t dim_pad, const int32_t *bsel_t, const float *bsel_tv, int32_t cstride_t,
                                    const int32_t *bsel_l, const float *bsel_lv, int32_t cstride_l, float band,
                                    int32_t *tsel_idx, float *tsel_cos, int32_t stride_t, int32_t *lsel_idx,
-                                   int32_t stride_l, cudaStream_t s);
+                                   int32_t stride_l, int32_t *err, cudaStream_t s);
 constexpr int kSelectRowMax = 24576;    // longest row the shared-memory select stages
 
 #ifdef __CUDACC__

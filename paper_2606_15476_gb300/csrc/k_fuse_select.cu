@@ -29,7 +29,15 @@
 //    (FP32 on the CUDA cores) and selects it exactly; with no recorded row it
 //    returns at once.
 //
-// One warp per row in sample_tau and fuse_final, no block barriers.
+// Two-pass rows (Piece::fs < 0; long rows of long lists, whose sample would
+// have to be most of the row): step 1 computes every tile but stores only the
+// group maxima; maxima_tau (below) takes the R-th largest of them as the
+// threshold (a lower bound of the row's R-th value, as above) and the
+// similarity kernel's second launch appends every entry of every tile that
+// reaches it; steps 4-5 as above.  About R of the row's group maxima reach the
+// threshold, so the appended entries number R and a few more per such group.
+//
+// One warp per row in sample_tau, maxima_tau and fuse_final, no block barriers.
 #include <cuda_fp16.h>
 
 #include "select_common.cuh"
@@ -163,7 +171,7 @@ sample_tau_kernel(const float *__restrict__ S, const float *__restrict__ tops, c
     const int64_t b = (int64_t)blockIdx.x * TAU_WARPS + warp;
     if (b >= total_rows) return;
     const Piece pc = pieces[warp_find_piece(pieces, n_pieces, b)];
-    if (pc.fs == 0) return;                    // a row of the unfused path
+    if (pc.fs <= 0) return;                    // a row of the unfused path, or a two-pass row
     const int s = pc.fs;
     const int i = (int)(b - pc.row_begin);
     const int64_t grow = pc.q_row0 + i;
@@ -240,6 +248,39 @@ sample_tau_kernel(const float *__restrict__ S, const float *__restrict__ tops, c
     if (lane == 0) {
         emit.tau_key[grow] = T;
         emit.cnt[grow] = cnt;
+    }
+}
+
+// A two-pass row's threshold: the R-th largest of its group maxima over the
+// whole row (R its whole-row list length), staged in the warp's gmax keys of
+// dynamic shared memory; every entry passes when the groups are fewer than R.
+__global__ void __launch_bounds__(TAU_WARPS * 32)
+maxima_tau_kernel(const float *__restrict__ tops, const Piece *__restrict__ pieces, int32_t n_pieces,
+                  int64_t total_rows, FuseEmit emit, int32_t gmax)
+{
+    extern __shared__ uint32_t mkeys[];        // [TAU_WARPS][gmax]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t b = (int64_t)blockIdx.x * TAU_WARPS + warp;
+    if (b >= total_rows) return;
+    const Piece pc = pieces[warp_find_piece(pieces, n_pieces, b)];
+    if (pc.fs >= 0) return;                    // not a two-pass row
+    const int i = (int)(b - pc.row_begin);
+    const int64_t grow = pc.q_row0 + i;
+    const int R = i < pc.ntr ? pc.fkeep_t : pc.fkeep_l;
+    const int G = (int)group_count(pc.n, pc.gshift);
+    uint32_t T = 0u;                           // key 0: every entry passes
+    if (G >= R) {
+        uint32_t *kw = mkeys + (int64_t)warp * gmax;
+        const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(pc.n, pc.gshift);
+        const int g = min(G, gmax);            // (a prefix of the maxima still gives a lower bound)
+#pragma unroll 4
+        for (int j = lane; j < g; j += 32) kw[j] = order_key(__ldg(tp + j));
+        __syncwarp();
+        T = warp_kth_lower(kw, g, R, TAU_BITS, lane);
+    }
+    if (lane == 0) {
+        emit.tau_key[grow] = T;
+        emit.cnt[grow] = 0;
     }
 }
 
@@ -473,6 +514,24 @@ cudaError_t launch_fuse_sample_tau(const float *S, const float *tops, const Piec
     const int64_t blocks = (total_rows + TAU_WARPS - 1) / TAU_WARPS;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     sample_tau_kernel<<<(unsigned)blocks, TAU_WARPS * 32, 0, st>>>(S, tops, pieces, n_pieces, total_rows, emit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fuse_maxima_tau(const float *tops, const Piece *pieces, int32_t n_pieces, int64_t total_rows,
+                                   const FuseEmit &emit, int32_t gmax, cudaStream_t st)
+{
+    if (total_rows <= 0) return cudaSuccess;
+    if (n_pieces < 1 || !tops || !emit.tau_key || !emit.cnt || gmax < 1 || gmax > kMaximaTauKeys)
+        return cudaErrorInvalidValue;
+    const int64_t blocks = (total_rows + TAU_WARPS - 1) / TAU_WARPS;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)TAU_WARPS * gmax * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(maxima_tau_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    maxima_tau_kernel<<<(unsigned)blocks, TAU_WARPS * 32, smem, st>>>(tops, pieces, n_pieces, total_rows, emit, gmax);
     return cudaGetLastError();
 }
 

@@ -850,7 +850,8 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             }
             const int64_t ns_ = pc.n_store;       // valid stored columns (sample tiles compacted)
             const int64_t r_blk = (int64_t)m0 + quad * 32;       // first row of the warp's blocks
-            float *sblk = S + pc.s_off + r_blk * pc.ld;
+            const bool store = pc.s_off >= 0;     // s_off -1: the group maxima only (uniform across the warp)
+            float *sblk = S + (store ? pc.s_off : 0) + r_blk * pc.ld;
             const bool vec = (pc.ld % 4) == 0;
             // stored columns c0 + ... are valid below ns_ exactly where their objects n0 + ... are below n
             const float sr = (MODE == kSimFp8 && live) ? scale_q[pc.q_row0 + r] : 1.f;
@@ -904,6 +905,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                         gmax[4 * c + g] = m;
                     }
                 }
+                if (!store) continue;
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     blk[lane * 8 + (j ^ (lane & 7))] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);

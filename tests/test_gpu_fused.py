@@ -170,3 +170,46 @@ def test_overflowing_rows_are_recomputed_exactly(F, prec):
         ref = oracle.batch(sc, qb, 10)
         hits = sum(len(set(out["idx"][q].tolist()) & set(ref["idx"][q].tolist())) for q in range(qb.n_q))
         assert hits / (10.0 * qb.n_q) >= 0.99
+
+
+@pytest.fixture(scope="module")
+def big(F):
+    """One scene of 70,000 objects (2,188 groups of 32 per row, at least four
+    times the learned path's target list of 512: the two-pass selection) and
+    one of 9,000 (the unfused learned selection) in the same batches."""
+    ctx = F.farm_create(0)
+    scenes, parts = {}, []
+    for sid, n in [(80, 70000), (81, 9000)]:
+        sc = synth.make_scene(sid, n, DIM, extent=(90.0, 90.0, 8.0), n_classes=max(8, n // 50), n_views=4,
+                              distractor_classes=4, distractor_frac=0.3)
+        F.farm_memory_upload(ctx, sid, sc.desc, sc.cls, sc.box, sc.views)
+        scenes[sid] = sc
+        parts.append(synth.make_queries(sid + 500, sc, 48, m_choices=(0, 1, 2, 3, 4), scene_id=sid,
+                                        distractor_classes=4, distractor_target_frac=0.5))
+    qb = synth.scenes.concat_batches(parts)
+    qb = qb.subset(np.random.default_rng(18).permutation(qb.n_q))
+    rng = np.random.default_rng(19)
+    H, P = 128, 64
+    F.farm_mlp_set(ctx, (rng.standard_normal((H, DIM)) / math.sqrt(DIM)).astype(np.float32),
+                   (0.05 * rng.standard_normal(H)).astype(np.float32),
+                   (rng.standard_normal((P, H)) / math.sqrt(H)).astype(np.float32),
+                   (0.05 * rng.standard_normal(P)).astype(np.float32))
+    yield ctx, scenes, qb
+    F.farm_destroy(ctx)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_learned_two_pass_equals_unfused(F, big, graph):
+    """The learned path's two-pass selection (every tile's group maxima, the
+    threshold from them, every tile keeping the entries that reach it) sees
+    the same compressed-space values as the unfused path, which stores them
+    all: the candidate lists, the rescored rank lists and the results must be
+    bitwise equal, with no row recomputed by the fallback."""
+    ctx, scenes, qb = big
+    code = _code(F, "learned")
+    F.farm_select_fallbacks(ctx, reset=True)
+    two = _run(F, ctx, qb, code, None, graph=graph)
+    if graph:
+        two = _run(F, ctx, qb, code, None, graph=graph)    # (the first batch of a class tunes the tiles)
+    assert F.farm_select_fallbacks(ctx) == 0
+    _same(two, _run(F, ctx, qb, code, False))

@@ -154,3 +154,63 @@ def test_pipelined_host_batches_with_async_topk(F, world, graph):
     for o, r in zip(outs, ref):
         for key in ("idx", "score", "pred", "anchor"):
             np.testing.assert_array_equal(o[key], r[key], err_msg=key)
+
+
+def _embeddings_only(qb, seed):
+    """New embeddings, the same query graphs (scenes, classes, constraints)."""
+    rng = np.random.default_rng(seed)
+    v = qb.subset(np.arange(qb.n_q))
+    v.tgt_emb = (v.tgt_emb + 0.05 * rng.standard_normal(v.tgt_emb.shape)).astype(np.float32)
+    v.c_emb = (v.c_emb + 0.05 * rng.standard_normal(v.c_emb.shape)).astype(np.float32)
+    return v
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_graph_replay_of_the_same_query_graphs(F, world, prec):
+    """Back-to-back graph batches with the same query graphs are replayed
+    without planning (host rows still copied into alternating slots): each
+    must give its own direct result; an in-place change of a predicate or a
+    class in the caller's arrays, or a batch of another shape in between, must
+    be planned again."""
+    import torch
+    ctx, scenes, qb = world
+    code = {"fp32": F.PREC_FP32, "bf16": F.PREC_BF16}[prec]
+    batches = [_embeddings_only(qb, seed) for seed in (31, 32, 33, 34, 35)]
+    ref = [_run(F, ctx, v, code, graph=False)[0] for v in batches]
+
+    def pinned(shape, dtype):
+        return torch.empty(shape, dtype=dtype).pin_memory().numpy()
+
+    outs = []
+    for v in batches:
+        o = dict(idx=pinned((v.n_q, 10), torch.int32), score=pinned((v.n_q, 10), torch.float32),
+                 pred=pinned((v.n_q, 10, 4), torch.float32), anchor=pinned((v.n_q, 10, 4), torch.int32))
+        h = F.farm_query_batch(ctx, v.scene_of_q, v.tgt_emb, v.tgt_cls, v.c_off, v.c_pred, v.c_emb, code,
+                               graph=True)
+        F.farm_topk(ctx, h, 10, v.n_q, o["idx"], o["score"], o["pred"], o["anchor"], asynchronous=True)
+        outs.append(o)
+    F.farm_sync(ctx)
+    for o, r in zip(outs, ref):
+        for key in ("idx", "score", "pred", "anchor"):
+            np.testing.assert_array_equal(o[key], r[key], err_msg=key)
+    # the caller's arrays changed in place after a replayable batch
+    v = batches[-1]
+    _run(F, ctx, v, code, graph=True)
+    _run(F, ctx, v, code, graph=True)
+    first = int(np.flatnonzero(np.diff(v.c_off) > 0)[0])
+    v.c_pred[v.c_off[first]] = (v.c_pred[v.c_off[first]] + 1) % 5
+    got = _run(F, ctx, v, code, graph=True)
+    _same(got, _run(F, ctx, v, code, graph=False))
+    _run(F, ctx, v, code, graph=True)
+    _run(F, ctx, v, code, graph=True)
+    v.tgt_cls[1] = -1 if v.tgt_cls[1] >= 0 else 0
+    got = _run(F, ctx, v, code, graph=True)
+    _same(got, _run(F, ctx, v, code, graph=False))
+    # another shape in between, then the first again (its staging rewritten)
+    sub = v.subset(np.arange(0, v.n_q, 2))
+    _run(F, ctx, v, code, graph=True)
+    _run(F, ctx, v, code, graph=True)
+    _same(_run(F, ctx, sub, code, graph=True), _run(F, ctx, sub, code, graph=False))
+    _run(F, ctx, sub, code, graph=True)
+    got = _run(F, ctx, v, code, graph=True)
+    _same(got, _run(F, ctx, v, code, graph=False))
