@@ -473,6 +473,290 @@ def run_associate(args, F, synth, torch, dist, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_retrieval(args, F, synth, torch, dist, rank, world, local, workload, steps, extra_paths, cpu_budget_s):
+    """One retrieval workload: the device-timed steps of args.precision (and
+    of extra_paths, under 'paths'), their stage breakdown, roofline and
+    end-to-end rate; with cpu_budget_s > 0 the oracle's rate and the
+    Recall@10 of every path on a seeded query sample.  Returns the JSON line."""
+    scenes, qb = synth.workload(workload)
+    if args.queries > 0:
+        qb = qb.subset(np.arange(min(args.queries, qb.n_q)))
+    sc = scenes[0]
+    PREC = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16,
+            "fp8": F.PREC_FP8, "learned": F.PREC_LEARNED}
+    stream = torch.cuda.Stream()          # the library and the timing events share it
+    torch.cuda.set_stream(stream)
+    ctx = F.farm_create(local, stream)
+    if args.tile_variant >= 0:
+        F.farm_sim_variant_pin(ctx, args.tile_variant)
+    for sid, scn in enumerate(scenes):
+        F.farm_memory_upload(ctx, sid, scn.desc, scn.cls, scn.box, scn.views)
+    multi_ch = args.channels == "paper"
+    # the headline comparison: the reduced-precision and learned paths timed in
+    # the same run on the same workload (one scene-set, one channel)
+    extra = [] if (multi_ch or args.precision != "fp32") else list(extra_paths)
+    training = None
+    if args.precision == "learned" or "learned" in extra:
+        training = train_prefilter(F, ctx, sc.dim)
+    n_q, n_c = qb.n_q, qb.n_c
+    if multi_ch:
+        if len(scenes) != 1 or args.precision != "fp32":
+            raise SystemExit("--channels paper runs one scene in FP32")
+        spaces = synth.add_spaces(sc, 9001, dims=(1024, 2048))
+        for s_i in range(1, len(spaces.desc)):
+            F.farm_memory_add_space(ctx, 0, s_i, spaces.desc[s_i])
+        cq = synth.channel_queries(9002, sc, spaces, qb)
+        # the channels' embeddings laid end to end, as the call takes them
+        flat_t = np.concatenate([x.ravel() for x in cq.tgt])
+        flat_l = np.concatenate([x.ravel() for x in cq.lm])
+        d_tgts, d_lms = torch.from_numpy(flat_t).cuda(), torch.from_numpy(flat_l).cuda()
+        h_tgts = torch.from_numpy(flat_t).pin_memory().numpy()
+        h_lms = torch.from_numpy(flat_l).pin_memory().numpy()
+    d_tgt = torch.from_numpy(qb.tgt_emb).cuda()
+    d_cemb = torch.from_numpy(qb.c_emb).cuda()
+    o_idx = torch.empty((n_q, K_TOP), dtype=torch.int32, device="cuda")
+    o_score = torch.empty((n_q, K_TOP), dtype=torch.float32, device="cuda")
+    o_pred = torch.empty((n_q, K_TOP, 4), dtype=torch.float32, device="cuda")
+    o_anc = torch.empty((n_q, K_TOP, 4), dtype=torch.int32, device="cuda")
+    h_tgt = torch.from_numpy(qb.tgt_emb).pin_memory().numpy()
+    h_cemb = torch.from_numpy(qb.c_emb).pin_memory().numpy()
+    graph = not args.no_graph and not multi_ch
+    FUSE = {"default": None, "on": True, "off": False}[args.fused]
+
+    def timed(fn, sample_clocks):
+        """K steps between CUDA events on the library's stream, barrier and synchronize on both sides."""
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local if sample_clocks else -1) as clk:
+            ev0.record(stream)
+            for _ in range(steps):
+                fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        F.farm_sync(ctx)
+        return ev0.elapsed_time(ev1), clk
+
+    def measure(prec):
+        """One path: the K device-timed steps (graphs), a directly run pass with
+        the stage events, and the K end-to-end steps through host buffers."""
+        host_s = [0.0]
+
+        def step_device(use_graph=graph):
+            t0 = time.perf_counter()
+            if multi_ch:
+                h = F.farm_query_batch_rrf(ctx, 0, cq.channels, d_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, d_lms)
+            else:
+                h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec,
+                                       graph=use_graph, fused=FUSE)
+            host_s[0] += time.perf_counter() - t0
+            F.farm_topk(ctx, h, K_TOP, n_q, o_idx, o_score, o_pred, o_anc)
+
+        for _ in range(args.warmup):
+            step_device()
+        F.farm_sync(ctx)
+        F.farm_stage_times(ctx, reset=True)
+        F.farm_select_fallbacks(ctx, reset=True)
+        host_s[0] = 0.0
+        ms, clk = timed(step_device, True)
+        host_ms = host_s[0] * 1e3 / steps
+        fallbacks = F.farm_select_fallbacks(ctx, reset=True)
+        _, launches = F.farm_stage_times(ctx, reset=True)
+        ms_step = max_over_ranks([ms / steps], dist, "cuda" if dist else None)[0]
+        # the host's own time per call (planning, staging, graph launch), the GPU idle before each call
+        plan_s = []
+        for _ in range(min(steps, 20)):
+            F.farm_sync(ctx)
+            t0 = time.perf_counter()
+            step_device()
+            plan_s.append(time.perf_counter() - t0)
+        F.farm_sync(ctx)
+        host_plan_ms = statistics.median(plan_s) * 1e3
+        # the same steps run directly with the library's stage events: the stage
+        # breakdown and the similarity kernel's time for the roofline
+        for _ in range(min(args.warmup, 3)):
+            step_device(False)
+        F.farm_sync(ctx)
+        F.farm_stage_times(ctx, reset=True)
+        F.farm_set_profiling(ctx, True)
+        ms_prof, _ = timed(lambda: step_device(False), False)
+        stage_ms, _ = F.farm_stage_times(ctx, reset=True)
+        F.farm_set_profiling(ctx, False)
+        if dist:
+            dist.barrier()
+        # ---- end to end through host buffers (pinned), same steps
+        h_out = dict(idx=torch.empty((n_q, K_TOP), dtype=torch.int32).pin_memory().numpy(),
+                     score=torch.empty((n_q, K_TOP), dtype=torch.float32).pin_memory().numpy(),
+                     pred=torch.empty((n_q, K_TOP, 4), dtype=torch.float32).pin_memory().numpy(),
+                     anchor=torch.empty((n_q, K_TOP, 4), dtype=torch.int32).pin_memory().numpy())
+
+        def step_host(asynchronous):
+            if multi_ch:
+                h = F.farm_query_batch_rrf(ctx, 0, cq.channels, h_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, h_lms)
+            else:
+                h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec,
+                                       graph=graph, fused=FUSE)
+            F.farm_topk(ctx, h, K_TOP, n_q, h_out["idx"], h_out["score"], h_out["pred"], h_out["anchor"],
+                        asynchronous=asynchronous)
+
+        # a serving loop: each step copies its rows in and its TopK records out
+        # (pinned host buffers); with the asynchronous TopK (default) a step's
+        # input copy overlaps the previous step's kernels, and the last
+        # step's records are read after the closing farm_sync
+        asynchronous = not args.e2e_sync
+        for _ in range(args.warmup):
+            step_host(False)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step_host(asynchronous)
+        F.farm_sync(ctx)
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
+        e2e_ms = max_over_ranks([e2e_ms], dist, "cuda" if dist else None)[0]
+        return {"ms_step": ms_step, "clk": clk, "launches": int(launches), "stage_ms": stage_ms,
+                "ms_prof": ms_prof, "e2e_ms": e2e_ms, "h_out": h_out, "host_ms": host_ms,
+                "fallbacks": fallbacks / steps, "host_plan_ms": host_plan_ms}
+
+    if multi_ch:
+        h2d = flat_t.nbytes + flat_l.nbytes + 4 * (2 * n_q + 1 + n_c)
+    else:
+        h2d = (n_q + n_c) * sc.dim * 4 + 4 * (3 * n_q + 1 + n_c)
+    d2h = n_q * K_TOP * (4 + 4 + 16 + 16)
+    peaks, peak_kind = _peaks()
+    flops_full = similarity_flops(scenes, qb)
+    if multi_ch:
+        dims = spaces.dims
+        flops_full = sum(2.0 * (n_q + n_c) * sc.n * dims[sp] for sp, _ in cq.channels)
+
+    def roofline(pname, r):
+        """The similarity contraction (stage 1) over the timed steps against
+        its peak: burst for a region under a second (the stage then runs at
+        the maximum SM clock), sustained otherwise."""
+        flops_step = flops_full * (128.0 / sc.dim if pname == "learned" else 1.0)
+        gemm_ms = r["stage_ms"][1] / steps
+        region_s = r["ms_step"] * steps * 1e-3
+        pk_key, pk_word = ("bf16_tflops", "burst") if region_s < 1.0 else ("bf16_tflops_sustained", "sustained")
+        bound, unit = "tensor", "TFLOP/s"
+        if pname == "fp32":
+            # three FP16 products per FP32-accurate product; FP16 dense peak = bf16 dense peak
+            peak = peaks[pk_key] / 3.0
+            note = f"{peak_kind} {pk_word} bf16 (= fp16 dense) / 3 (three-term FP16 split)"
+        elif pname == "bf16":
+            peak, note = peaks[pk_key], f"{peak_kind} {pk_word} bf16"
+        elif pname == "learned":
+            peak, note = peaks[pk_key], f"{peak_kind} {pk_word} bf16 (128-d learned embeddings)"
+        elif pname == "fp8":
+            peak = peaks[pk_key] * (4.5 / 2.25)
+            note = f"{peak_kind} {pk_word} bf16 x 4.5/2.25 (FP8 dense)"
+        else:
+            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            bound, note = "alu", "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+        if pname in ("bf16", "fp8") and not multi_ch:
+            # scenes under REDUCED_FROM_OBJECTS objects ran FP32-accurate: the
+            # peak is the one that does the batch's flops in the least time,
+            # each scene's at its own arithmetic's peak
+            rows_s = rows_per_scene(scenes, qb)
+            f_small = sum(2.0 * int(r) * x.n * x.dim for r, x in zip(rows_s, scenes) if x.n < REDUCED_FROM_OBJECTS)
+            if f_small > 0:
+                t_ideal = (flops_step - f_small) / peak + f_small / (peaks[pk_key] / 3.0)
+                peak = flops_step / t_ideal
+                note += f"; {f_small / flops_step:.0%} of the flops FP32-accurate (peak / 3), combined"
+        achieved = flops_step / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0
+        return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak if peak else None,
+                # the whole step against the same peak: the similarity's flops over ms_per_step
+                "step_frac": flops_step / (r["ms_step"] * 1e-3) / 1e12 / peak if peak else None,
+                "timed_region_s": region_s,
+                "traffic": sim_traffic(workload, pname,
+                                       [args.tile_variant] if args.tile_variant >= 0
+                                       else sorted({d[3] for d in F.farm_sim_tuning(ctx)
+                                                    if d[0] % 10 == {"fp32": 0, "fp8": 2}.get(pname, 1)}),
+                                       pname in ("fp32", "bf16") and (args.fused == "on" or (
+                                           args.fused == "default" and pname == "fp32"))),
+                "traffic_unit": "bytes per step of the similarity stage",
+                "kernel": "similarity", "peak_source": note}
+
+    def stages(r):
+        sm = r["stage_ms"]
+        return {"prepare": sm[0] / steps, "similarity": sm[1] / steps, "select": sm[2] / steps,
+                "compose": sm[3] / steps, "direct_ms_per_step": r["ms_prof"] / steps,
+                "host_ms_per_query_batch_call": r["host_ms"],
+                "host_ms_per_step_gpu_idle": r["host_plan_ms"],
+                "exact_fallback_rows_per_step": r["fallbacks"]}
+
+    main_r = measure(PREC[args.precision])
+    extra_r = {x: measure(PREC[x]) for x in extra}
+
+    line = {
+        "metric": "relational queries/s", "value": job_rate(n_q, world, main_r["ms_step"]),
+        "unit": "queries/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": main_r["ms_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp32_simt": "f32", "bf16": "bf16", "fp8": "f8e4m3",
+                  "learned": "bf16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": workload, "scenes": len(scenes),
+                   "n_objects": int(sum(x.n for x in scenes)), "dim": sc.dim, "n_views": sc.n_views,
+                   "queries": n_q, "constraint_rows": n_c, "top_k": K_TOP,
+                   "precision": args.precision, "parallelism": f"replicas{world}",
+                   "channels": ([{"space": sp, "dim": spaces.dims[sp], "weight": w} for sp, w in cq.channels]
+                                if multi_ch else 1),
+                   "cuda_graph": graph, "fused_selection": args.fused,
+                   "l2": l2_statement(args, scenes, qb, sc.dim, multi_ch),
+                   "reduced_precision_scenes": reduced_split(args.precision, scenes, qb)},
+        "e2e": {"value": job_rate(n_q, world, main_r["e2e_ms"]), "unit": "queries/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "pipelined": not args.e2e_sync},
+        "gpu_launches": main_r["launches"],
+        "autotuned_tiles": [{"mode": d[0] % 10, "fused_selection": (d[0] // 10) % 2 == 1,
+                             "with_fp32_accurate_scenes": d[0] >= 20, "log2_rows": d[1], "log2_objects": d[2],
+                             "variant": d[3], "tile_n": 128 if d[3] == 1 else 256,
+                             "tile_m": 256 if d[3] == 2 else 128, "cta_pair": d[3] == 2}
+                            for d in F.farm_sim_tuning(ctx)],
+        "pinned_tile_variant": args.tile_variant if args.tile_variant >= 0 else None,
+        "stage_ms_per_step": stages(main_r),
+        "roofline": roofline(args.precision, main_r),
+        "clocks": main_r["clk"].summary(),
+    }
+    if extra_r:
+        line["paths"] = {}
+        for x, r in extra_r.items():
+            line["paths"][x] = {
+                "value": job_rate(n_q, world, r["ms_step"]), "unit": "queries/s", "ms_per_step": r["ms_step"],
+                "e2e": {"value": job_rate(n_q, world, r["e2e_ms"]), "unit": "queries/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "speedup_vs_fp32": main_r["ms_step"] / r["ms_step"],
+                "e2e_speedup_vs_fp32": main_r["e2e_ms"] / r["e2e_ms"],
+                "gpu_launches": r["launches"], "stage_ms_per_step": stages(r),
+                "roofline": roofline(x, r), "clocks": r["clk"].summary(),
+                "dtype": "bf16"}
+    if rank == 0 and cpu_budget_s > 0:
+        import oracle
+        oracle.build()
+        if multi_ch:
+            base, qs, ref_idx = cpu_baseline_mc(sc, spaces, qb, cq, K_TOP, args.cpu_sample, budget_s=cpu_budget_s)
+        else:
+            base, qs, ref_idx = cpu_baseline(scenes, qb, K_TOP, args.cpu_sample, budget_s=cpu_budget_s)
+        line["cpu_baseline"] = base
+
+        def recall(h_out):
+            got = h_out["idx"][qs]
+            hits = sum(len(set(got[i].tolist()) & set(ref_idx[i].tolist())) for i in range(len(qs)))
+            return {"value": hits / (K_TOP * len(qs)), "queries": int(len(qs))}
+
+        line["recall_at_10_vs_oracle"] = recall(main_r["h_out"])
+        for x, r in extra_r.items():
+            line["paths"][x]["recall_at_10_vs_oracle"] = recall(r["h_out"])
+    if training:
+        line["prefilter_training"] = training
+    F.farm_destroy(ctx)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -490,6 +774,10 @@ def main():
     ap.add_argument("--paths", default="bf16,learned",
                     help="further paths timed in the same run of an FP32 one-channel workload and reported under "
                          "'paths' (comma list of bf16, fp8, learned; 'none' for none)")
+    ap.add_argument("--prefilter-workload", default="site_n100k_d1152",
+                    help="the default run also times the FP32, BF16 and learned paths on this workload (the "
+                         "learned prefilter's configuration, 100,000 objects) and reports them under "
+                         "'prefilter_workload'; 'none' to skip")
     ap.add_argument("--e2e-sync", action="store_true",
                     help="end-to-end steps wait for each step's TopK records (no overlap of a step's input copy "
                          "with the previous step's kernels)")
@@ -535,283 +823,19 @@ def main():
         run_associate(args, F, synth, torch, dist, rank, world, local)
         return
 
-    scenes, qb = synth.workload(args.workload)
-    if args.queries > 0:
-        qb = qb.subset(np.arange(min(args.queries, qb.n_q)))
-    sc = scenes[0]
-    PREC = {"fp32": F.PREC_FP32, "fp32_simt": F.PREC_FP32_SIMT, "bf16": F.PREC_BF16,
-            "fp8": F.PREC_FP8, "learned": F.PREC_LEARNED}
-    stream = torch.cuda.Stream()          # the library and the timing events share it
-    torch.cuda.set_stream(stream)
-    ctx = F.farm_create(local, stream)
-    if args.tile_variant >= 0:
-        F.farm_sim_variant_pin(ctx, args.tile_variant)
-    for sid, scn in enumerate(scenes):
-        F.farm_memory_upload(ctx, sid, scn.desc, scn.cls, scn.box, scn.views)
-    multi_ch = args.channels == "paper"
-    # the headline comparison: the reduced-precision and learned paths timed in
-    # the same run on the same workload (one scene-set, one channel)
-    extra = [] if (multi_ch or args.paths == "none" or args.precision != "fp32") else \
-        [x for x in args.paths.split(",") if x]
-    training = None
-    if args.precision == "learned" or "learned" in extra:
-        training = train_prefilter(F, ctx, sc.dim)
-    n_q, n_c = qb.n_q, qb.n_c
-    if multi_ch:
-        if len(scenes) != 1 or args.precision != "fp32":
-            raise SystemExit("--channels paper runs one scene in FP32")
-        spaces = synth.add_spaces(sc, 9001, dims=(1024, 2048))
-        for s_i in range(1, len(spaces.desc)):
-            F.farm_memory_add_space(ctx, 0, s_i, spaces.desc[s_i])
-        cq = synth.channel_queries(9002, sc, spaces, qb)
-        # the channels' embeddings laid end to end, as the call takes them
-        flat_t = np.concatenate([x.ravel() for x in cq.tgt])
-        flat_l = np.concatenate([x.ravel() for x in cq.lm])
-        d_tgts, d_lms = torch.from_numpy(flat_t).cuda(), torch.from_numpy(flat_l).cuda()
-        h_tgts = torch.from_numpy(flat_t).pin_memory().numpy()
-        h_lms = torch.from_numpy(flat_l).pin_memory().numpy()
-    d_tgt = torch.from_numpy(qb.tgt_emb).cuda()
-    d_cemb = torch.from_numpy(qb.c_emb).cuda()
-    o_idx = torch.empty((n_q, K_TOP), dtype=torch.int32, device="cuda")
-    o_score = torch.empty((n_q, K_TOP), dtype=torch.float32, device="cuda")
-    o_pred = torch.empty((n_q, K_TOP, 4), dtype=torch.float32, device="cuda")
-    o_anc = torch.empty((n_q, K_TOP, 4), dtype=torch.int32, device="cuda")
-    h_tgt = torch.from_numpy(qb.tgt_emb).pin_memory().numpy()
-    h_cemb = torch.from_numpy(qb.c_emb).pin_memory().numpy()
-    graph = not args.no_graph and not multi_ch
-    FUSE = {"default": None, "on": True, "off": False}[args.fused]
-
-    def timed(fn, sample_clocks):
-        """K steps between CUDA events on the library's stream, barrier and synchronize on both sides."""
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local if sample_clocks else -1) as clk:
-            ev0.record(stream)
-            for _ in range(args.steps):
-                fn()
-            ev1.record(stream)
-            torch.cuda.synchronize()
-        F.farm_sync(ctx)
-        return ev0.elapsed_time(ev1), clk
-
-    def measure(prec):
-        """One path: the K device-timed steps (graphs), a directly run pass with
-        the stage events, and the K end-to-end steps through host buffers."""
-        host_s = [0.0]
-
-        def step_device(use_graph=graph):
-            t0 = time.perf_counter()
-            if multi_ch:
-                h = F.farm_query_batch_rrf(ctx, 0, cq.channels, d_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, d_lms)
-            else:
-                h = F.farm_query_batch(ctx, qb.scene_of_q, d_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, d_cemb, prec,
-                                       graph=use_graph, fused=FUSE)
-            host_s[0] += time.perf_counter() - t0
-            F.farm_topk(ctx, h, K_TOP, n_q, o_idx, o_score, o_pred, o_anc)
-
-        for _ in range(args.warmup):
-            step_device()
-        F.farm_sync(ctx)
-        F.farm_stage_times(ctx, reset=True)
-        F.farm_select_fallbacks(ctx, reset=True)
-        host_s[0] = 0.0
-        ms, clk = timed(step_device, True)
-        host_ms = host_s[0] * 1e3 / args.steps
-        fallbacks = F.farm_select_fallbacks(ctx, reset=True)
-        _, launches = F.farm_stage_times(ctx, reset=True)
-        ms_step = max_over_ranks([ms / args.steps], dist, "cuda" if dist else None)[0]
-        # the host's own time per call (planning, staging, graph launch), the GPU idle before each call
-        plan_s = []
-        for _ in range(min(args.steps, 20)):
-            F.farm_sync(ctx)
-            t0 = time.perf_counter()
-            step_device()
-            plan_s.append(time.perf_counter() - t0)
-        F.farm_sync(ctx)
-        host_plan_ms = statistics.median(plan_s) * 1e3
-        # the same steps run directly with the library's stage events: the stage
-        # breakdown and the similarity kernel's time for the roofline
-        for _ in range(min(args.warmup, 3)):
-            step_device(False)
-        F.farm_sync(ctx)
-        F.farm_stage_times(ctx, reset=True)
-        F.farm_set_profiling(ctx, True)
-        ms_prof, _ = timed(lambda: step_device(False), False)
-        stage_ms, _ = F.farm_stage_times(ctx, reset=True)
-        F.farm_set_profiling(ctx, False)
-        if dist:
-            dist.barrier()
-        # ---- end to end through host buffers (pinned), same steps
-        h_out = dict(idx=torch.empty((n_q, K_TOP), dtype=torch.int32).pin_memory().numpy(),
-                     score=torch.empty((n_q, K_TOP), dtype=torch.float32).pin_memory().numpy(),
-                     pred=torch.empty((n_q, K_TOP, 4), dtype=torch.float32).pin_memory().numpy(),
-                     anchor=torch.empty((n_q, K_TOP, 4), dtype=torch.int32).pin_memory().numpy())
-
-        def step_host(asynchronous):
-            if multi_ch:
-                h = F.farm_query_batch_rrf(ctx, 0, cq.channels, h_tgts, qb.tgt_cls, qb.c_off, qb.c_pred, h_lms)
-            else:
-                h = F.farm_query_batch(ctx, qb.scene_of_q, h_tgt, qb.tgt_cls, qb.c_off, qb.c_pred, h_cemb, prec,
-                                       graph=graph, fused=FUSE)
-            F.farm_topk(ctx, h, K_TOP, n_q, h_out["idx"], h_out["score"], h_out["pred"], h_out["anchor"],
-                        asynchronous=asynchronous)
-
-        # a serving loop: each step copies its rows in and its TopK records out
-        # (pinned host buffers); with the asynchronous TopK (default) a step's
-        # input copy overlaps the previous step's kernels, and the last
-        # step's records are read after the closing farm_sync
-        asynchronous = not args.e2e_sync
-        for _ in range(args.warmup):
-            step_host(False)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            step_host(asynchronous)
-        F.farm_sync(ctx)
-        torch.cuda.synchronize()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        e2e_ms = max_over_ranks([e2e_ms], dist, "cuda" if dist else None)[0]
-        return {"ms_step": ms_step, "clk": clk, "launches": int(launches), "stage_ms": stage_ms,
-                "ms_prof": ms_prof, "e2e_ms": e2e_ms, "h_out": h_out, "host_ms": host_ms,
-                "fallbacks": fallbacks / args.steps, "host_plan_ms": host_plan_ms}
-
-    if multi_ch:
-        h2d = flat_t.nbytes + flat_l.nbytes + 4 * (2 * n_q + 1 + n_c)
-    else:
-        h2d = (n_q + n_c) * sc.dim * 4 + 4 * (3 * n_q + 1 + n_c)
-    d2h = n_q * K_TOP * (4 + 4 + 16 + 16)
-    peaks, peak_kind = _peaks()
-    flops_full = similarity_flops(scenes, qb)
-    if multi_ch:
-        dims = spaces.dims
-        flops_full = sum(2.0 * (n_q + n_c) * sc.n * dims[sp] for sp, _ in cq.channels)
-
-    def roofline(pname, r):
-        """The similarity contraction (stage 1) over the timed steps against
-        its peak: burst for a region under a second (the stage then runs at
-        the maximum SM clock), sustained otherwise."""
-        flops_step = flops_full * (128.0 / sc.dim if pname == "learned" else 1.0)
-        gemm_ms = r["stage_ms"][1] / args.steps
-        region_s = r["ms_step"] * args.steps * 1e-3
-        pk_key, pk_word = ("bf16_tflops", "burst") if region_s < 1.0 else ("bf16_tflops_sustained", "sustained")
-        bound, unit = "tensor", "TFLOP/s"
-        if pname == "fp32":
-            # three FP16 products per FP32-accurate product; FP16 dense peak = bf16 dense peak
-            peak = peaks[pk_key] / 3.0
-            note = f"{peak_kind} {pk_word} bf16 (= fp16 dense) / 3 (three-term FP16 split)"
-        elif pname == "bf16":
-            peak, note = peaks[pk_key], f"{peak_kind} {pk_word} bf16"
-        elif pname == "learned":
-            peak, note = peaks[pk_key], f"{peak_kind} {pk_word} bf16 (128-d learned embeddings)"
-        elif pname == "fp8":
-            peak = peaks[pk_key] * (4.5 / 2.25)
-            note = f"{peak_kind} {pk_word} bf16 x 4.5/2.25 (FP8 dense)"
-        else:
-            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-            bound, note = "alu", "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
-        if pname in ("bf16", "fp8") and not multi_ch:
-            # scenes under REDUCED_FROM_OBJECTS objects ran FP32-accurate: the
-            # peak is the one that does the batch's flops in the least time,
-            # each scene's at its own arithmetic's peak
-            rows_s = rows_per_scene(scenes, qb)
-            f_small = sum(2.0 * int(r) * x.n * x.dim for r, x in zip(rows_s, scenes) if x.n < REDUCED_FROM_OBJECTS)
-            if f_small > 0:
-                t_ideal = (flops_step - f_small) / peak + f_small / (peaks[pk_key] / 3.0)
-                peak = flops_step / t_ideal
-                note += f"; {f_small / flops_step:.0%} of the flops FP32-accurate (peak / 3), combined"
-        achieved = flops_step / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0
-        return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak if peak else None,
-                # the whole step against the same peak: the similarity's flops over ms_per_step
-                "step_frac": flops_step / (r["ms_step"] * 1e-3) / 1e12 / peak if peak else None,
-                "timed_region_s": region_s,
-                "traffic": sim_traffic(args.workload, pname,
-                                       [args.tile_variant] if args.tile_variant >= 0
-                                       else sorted({d[3] for d in F.farm_sim_tuning(ctx)
-                                                    if d[0] % 10 == {"fp32": 0, "fp8": 2}.get(pname, 1)}),
-                                       pname in ("fp32", "bf16") and (args.fused == "on" or (
-                                           args.fused == "default" and pname == "fp32"))),
-                "traffic_unit": "bytes per step of the similarity stage",
-                "kernel": "similarity", "peak_source": note}
-
-    def stages(r):
-        sm = r["stage_ms"]
-        return {"prepare": sm[0] / args.steps, "similarity": sm[1] / args.steps, "select": sm[2] / args.steps,
-                "compose": sm[3] / args.steps, "direct_ms_per_step": r["ms_prof"] / args.steps,
-                "host_ms_per_query_batch_call": r["host_ms"],
-                "host_ms_per_step_gpu_idle": r["host_plan_ms"],
-                "exact_fallback_rows_per_step": r["fallbacks"]}
-
-    main_r = measure(PREC[args.precision])
-    extra_r = {x: measure(PREC[x]) for x in extra}
-
-    line = {
-        "metric": "relational queries/s", "value": job_rate(n_q, world, main_r["ms_step"]),
-        "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": main_r["ms_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp32_simt": "f32", "bf16": "bf16", "fp8": "f8e4m3",
-                  "learned": "bf16"}[args.precision],
-        "data": "synthetic",
-        "config": {"workload": args.workload, "scenes": len(scenes),
-                   "n_objects": int(sum(x.n for x in scenes)), "dim": sc.dim, "n_views": sc.n_views,
-                   "queries": n_q, "constraint_rows": n_c, "top_k": K_TOP,
-                   "precision": args.precision, "parallelism": f"replicas{world}",
-                   "channels": ([{"space": sp, "dim": spaces.dims[sp], "weight": w} for sp, w in cq.channels]
-                                if multi_ch else 1),
-                   "cuda_graph": graph, "fused_selection": args.fused,
-                   "l2": l2_statement(args, scenes, qb, sc.dim, multi_ch),
-                   "reduced_precision_scenes": reduced_split(args.precision, scenes, qb)},
-        "e2e": {"value": job_rate(n_q, world, main_r["e2e_ms"]), "unit": "queries/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "pipelined": not args.e2e_sync},
-        "gpu_launches": main_r["launches"],
-        "autotuned_tiles": [{"mode": d[0] % 10, "fused_selection": (d[0] // 10) % 2 == 1,
-                             "with_fp32_accurate_scenes": d[0] >= 20, "log2_rows": d[1], "log2_objects": d[2],
-                             "variant": d[3], "tile_n": 128 if d[3] == 1 else 256,
-                             "tile_m": 256 if d[3] == 2 else 128, "cta_pair": d[3] == 2}
-                            for d in F.farm_sim_tuning(ctx)],
-        "pinned_tile_variant": args.tile_variant if args.tile_variant >= 0 else None,
-        "stage_ms_per_step": stages(main_r),
-        "roofline": roofline(args.precision, main_r),
-        "clocks": main_r["clk"].summary(),
-    }
-    if extra_r:
-        line["paths"] = {}
-        for x, r in extra_r.items():
-            line["paths"][x] = {
-                "value": job_rate(n_q, world, r["ms_step"]), "unit": "queries/s", "ms_per_step": r["ms_step"],
-                "e2e": {"value": job_rate(n_q, world, r["e2e_ms"]), "unit": "queries/s",
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "speedup_vs_fp32": main_r["ms_step"] / r["ms_step"],
-                "e2e_speedup_vs_fp32": main_r["e2e_ms"] / r["e2e_ms"],
-                "gpu_launches": r["launches"], "stage_ms_per_step": stages(r),
-                "roofline": roofline(x, r), "clocks": r["clk"].summary(),
-                "dtype": "bf16"}
-    if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        if multi_ch:
-            base, qs, ref_idx = cpu_baseline_mc(sc, spaces, qb, cq, K_TOP, args.cpu_sample)
-        else:
-            base, qs, ref_idx = cpu_baseline(scenes, qb, K_TOP, args.cpu_sample)
-        line["cpu_baseline"] = base
-
-        def recall(h_out):
-            got = h_out["idx"][qs]
-            hits = sum(len(set(got[i].tolist()) & set(ref_idx[i].tolist())) for i in range(len(qs)))
-            return {"value": hits / (K_TOP * len(qs)), "queries": int(len(qs))}
-
-        line["recall_at_10_vs_oracle"] = recall(main_r["h_out"])
-        for x, r in extra_r.items():
-            line["paths"][x]["recall_at_10_vs_oracle"] = recall(r["h_out"])
-    if training:
-        line["prefilter_training"] = training
-    F.farm_destroy(ctx)
+    extra = [] if args.paths == "none" else [x for x in args.paths.split(",") if x]
+    line = run_retrieval(args, F, synth, torch, dist, rank, world, local, args.workload, args.steps, extra,
+                         0.0 if args.no_cpu_baseline else 15.0)
+    if (args.prefilter_workload != "none" and args.workload == WORKLOAD and args.precision == "fp32"
+            and args.channels == "one" and args.queries == 0 and args.tile_variant < 0):
+        # the learned prefilter's own configuration (100,000 objects): the
+        # learned and BF16 paths against the FP32 path, timed in the same run
+        sub = run_retrieval(args, F, synth, torch, dist, rank, world, local, args.prefilter_workload,
+                            min(args.steps, 10), ["bf16", "learned"], 0.0 if args.no_cpu_baseline else 6.0)
+        line["prefilter_workload"] = {
+            k: sub[k] for k in ("config", "value", "unit", "ms_per_step", "e2e", "stage_ms_per_step", "roofline",
+                                "clocks", "paths", "recall_at_10_vs_oracle", "cpu_baseline", "prefilter_training",
+                                "steps") if k in sub}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
