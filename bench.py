@@ -243,9 +243,9 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
 # dram__bytes_write.sum) for the kernel source whose sha256 prefix follows:
 # (workload, precision, tile variant, fused) -> bytes
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 2, True): (88.126464e6 + 114.629632e6) + (620.184064e6 + 32.970240e6),
+    ("site_n20k_d1152", "fp32", 2, True): (88.802560e6 + 113.844224e6) + (620.318976e6 + 29.381888e6),
 }
-SIM_TRAFFIC_SOURCE = "d45a2ec685829ede"
+SIM_TRAFFIC_SOURCE = "46d833a469c7bf4b"
 
 
 def sim_traffic(workload, precision, variants, fused):

@@ -774,6 +774,34 @@ farm_status farm_query_batch(farm_ctx *ctx, int64_t n_q, const int32_t *scene_of
         groups.back().nq += 1;
         groups.back().nc += c_off[q + 1] - c_off[q];
     }
+    // Reduced-precision batches: within a scene the queries are ordered by
+    // target class (stable, a counting sort).  The FP32 rescore gathers each
+    // target row's candidates -- mostly the objects of its class -- and the
+    // CTAs of consecutive rows then find those descriptor rows in L2.  Rows
+    // are independent, so the order changes no result.
+    if (reduced_precision(precision)) {
+        std::vector<int32_t> tmp, cnt;
+        for (const auto &g : groups) {
+            if (g.nq < 2) continue;
+            int32_t cmax = -1;
+            bool small = true;
+            for (int64_t k = 0; k < g.nq; ++k) {
+                const int32_t cl = tgt_cls[order[g.q0 + k]];
+                small &= cl < (1 << 20);
+                cmax = std::max(cmax, cl);
+            }
+            if (!small) continue;
+            cnt.assign((size_t)cmax + 3, 0);
+            for (int64_t k = 0; k < g.nq; ++k) cnt[(size_t)std::max(tgt_cls[order[g.q0 + k]], -1) + 2] += 1;
+            for (size_t j = 1; j < cnt.size(); ++j) cnt[j] += cnt[j - 1];
+            tmp.resize((size_t)g.nq);
+            for (int64_t k = 0; k < g.nq; ++k) {
+                const int32_t q = order[g.q0 + k];
+                tmp[(size_t)cnt[(size_t)std::max(tgt_cls[q], -1) + 1]++] = q;
+            }
+            std::copy(tmp.begin(), tmp.end(), order.begin() + g.q0);
+        }
+    }
     int64_t row = 0, cp = 0;
     for (auto &g : groups) {
         g.row0 = row;
