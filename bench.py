@@ -775,8 +775,8 @@ def main():
                     help="further paths timed in the same run of an FP32 one-channel workload and reported under "
                          "'paths' (comma list of bf16, fp8, learned; 'none' for none)")
     ap.add_argument("--prefilter-workload", default="site_n100k_d1152",
-                    help="the default run also times the FP32, BF16 and learned paths on this workload (the "
-                         "learned prefilter's configuration, 100,000 objects) and reports them under "
+                    help="the default one-GPU run also times the FP32, BF16 and learned paths on this workload "
+                         "(the learned prefilter's configuration, 100,000 objects) and reports them under "
                          "'prefilter_workload'; 'none' to skip")
     ap.add_argument("--e2e-sync", action="store_true",
                     help="end-to-end steps wait for each step's TopK records (no overlap of a step's input copy "
@@ -827,7 +827,7 @@ def main():
     line = run_retrieval(args, F, synth, torch, dist, rank, world, local, args.workload, args.steps, extra,
                          0.0 if args.no_cpu_baseline else 15.0)
     if (args.prefilter_workload != "none" and args.workload == WORKLOAD and args.precision == "fp32"
-            and args.channels == "one" and args.queries == 0 and args.tile_variant < 0):
+            and args.channels == "one" and args.queries == 0 and args.tile_variant < 0 and world == 1):
         # the learned prefilter's own configuration (100,000 objects): the
         # learned and BF16 paths against the FP32 path, timed in the same run
         sub = run_retrieval(args, F, synth, torch, dist, rank, world, local, args.prefilter_workload,
