@@ -25,6 +25,16 @@
 // 4. fuse_final (below): the R largest words of the buffer, sorted, are the
 //    row's rank list.  A row whose candidates overflowed the buffer is
 //    recorded for the exact fallback.
+//
+// The threshold of step 2 may be optimistic: tau = the sample's k-th largest
+// value for a k below R (optimistic_rank), which lets about k s of the row's
+// entries through instead of R s (a sample of every s-th tile).  It is a lower bound of the row's R-th
+// value exactly when at least R of the row's entries reach it, and then the
+// buffer holds the R best words as above; fuse_final counts the buffer's
+// words that reach tau and records a row with fewer than R for the exact
+// fallback.  With the sample a random fraction f of the row, the count of
+// entries reaching its k-th largest value is about negative-binomial, mean
+// k / f; k is chosen so that the mean lies 4.5 deviations above R.
 // 5. fuse_fallback (below) recomputes each recorded row over all its objects
 //    (FP32 on the CUDA cores) and selects it exactly; with no recorded row it
 //    returns at once.
@@ -149,6 +159,21 @@ __device__ __forceinline__ uint32_t warp_kth_lower(const uint32_t *keys, int n, 
     return T < 0x00800000u ? 0u : T;
 }
 
+// The sample rank whose value sets a row's optimistic threshold, for a list
+// of R and a sample holding the fraction f of the row: the count of the row's
+// entries reaching the sample's k-th largest is about negative-binomial, mean
+// k / f and deviation sqrt(k (1 - f)) / f, and k is the smallest whose mean
+// lies 4.5 deviations above R -- k = x^2 with x^2 - 4.5 sqrt(1 - f) x = R f --
+// at most R (a sample that is the whole row: k = R, exact).
+__device__ __forceinline__ int optimistic_rank(int R, int sample_n, int row_n)
+{
+    const float f = fminf(1.f, (float)sample_n / (float)row_n);
+    const float a = 4.5f * sqrtf(1.f - f);
+    const float x = 0.5f * (a + sqrtf(a * a + 4.f * (float)R * f));
+    const int k = (int)ceilf(x * x);
+    return k < R ? k : R;
+}
+
 // Eight consecutive sample values of a lane from j (16-byte aligned), zero past n.
 __device__ __forceinline__ void load8(const float *__restrict__ row, int j, int n, float (&x)[8])
 {
@@ -244,7 +269,10 @@ sample_tau_kernel(const float *__restrict__ S, const float *__restrict__ tops, c
     // the threshold for the other tiles: the R-th largest of the sample's
     // entries themselves (at least tau, still at most the row's R-th value),
     // which keeps fewer of the other tiles' entries than the group bound
-    if (T != 0u && cnt > R && cnt <= TAU_KEYS) T = max(T, warp_kth_lower(kw, cnt, R, TAU_BITS, lane));
+    // (optimistic: the sample's k-th largest entry, k <= R; fuse_final checks
+    // that at least R of the row's entries reached it)
+    const int k = optimistic_rank(R, n, pc.n_obj);
+    if (T != 0u && cnt > k && cnt <= TAU_KEYS) T = max(T, warp_kth_lower(kw, cnt, k, TAU_BITS, lane));
     if (lane == 0) {
         emit.tau_key[grow] = T;
         emit.cnt[grow] = cnt;
@@ -282,6 +310,17 @@ maxima_tau_kernel(const float *__restrict__ tops, const Piece *__restrict__ piec
         emit.tau_key[grow] = T;
         emit.cnt[grow] = 0;
     }
+}
+
+// Whether at least `keep` of a row's t buffered words reach its threshold
+// key T: the check of an optimistic threshold (a row that fails it is left
+// to the exact fallback).
+__device__ __forceinline__ bool threshold_held(const uint64_t *__restrict__ cand, int t, uint32_t T, int keep,
+                                               int lane)
+{
+    int reach = 0;
+    for (int j = lane; j < t; j += 32) reach += (uint32_t)(cand[j] >> 32) >= T ? 1 : 0;
+    return (int)__reduce_add_sync(0xffffffffu, (unsigned)reach) >= keep;
 }
 
 // Merge of one row held in REG words per lane (REG * 32 >= total): the
@@ -391,6 +430,10 @@ fuse_final_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, int64_t to
         return;
     }
     const uint64_t *cand = emit.cand + L.grow * (int64_t)emit.cap;
+    if (!threshold_held(cand, t, emit.tau_key[L.grow], L.keep, lane)) {
+        if (lane == 0) overflow_rows[atomicAdd(n_overflow, 1)] = (int32_t)b;
+        return;
+    }
     if (t <= 128) merge_row<4>(L, 0, t, cand, coll[warp], lane);
     else if (t <= 256) merge_row<8>(L, 0, t, cand, coll[warp], lane);
     else if (t <= 512) merge_row<16>(L, 0, t, cand, coll[warp], lane);
@@ -403,7 +446,8 @@ template <int MAXR>
 __global__ void __launch_bounds__(32)
 fuse_final_big_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, int32_t *tsel_idx, float *tsel_cos,
                       int32_t stride_t, int32_t *lsel_idx, float *lsel_cos, int32_t stride_l, FuseEmit emit,
-                      const int32_t *__restrict__ n_big, const int32_t *__restrict__ big_rows)
+                      const int32_t *__restrict__ n_big, const int32_t *__restrict__ big_rows, int32_t *n_overflow,
+                      int32_t *overflow_rows)
 {
     __shared__ uint64_t coll[MAXR * 32];
     const int lane = threadIdx.x;
@@ -413,7 +457,12 @@ fuse_final_big_kernel(const Piece *__restrict__ pieces, int32_t n_pieces, int32_
         const Piece pc = pieces[warp_find_piece(pieces, n_pieces, b)];
         const RowList L = row_list(pc, b, tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos, stride_l);
         const int32_t t = emit.cnt[L.grow];
-        merge_row<MAXR>(L, 0, t, emit.cand + L.grow * (int64_t)emit.cap, coll, lane);
+        const uint64_t *cand = emit.cand + L.grow * (int64_t)emit.cap;
+        if (threshold_held(cand, t, emit.tau_key[L.grow], L.keep, lane)) {
+            merge_row<MAXR>(L, 0, t, cand, coll, lane);
+        } else if (lane == 0) {
+            overflow_rows[atomicAdd(n_overflow, 1)] = (int32_t)b;
+        }
         __syncwarp();
     }
 }
@@ -555,7 +604,8 @@ cudaError_t launch_fuse_final(const Piece *pieces, int32_t n_pieces, int64_t tot
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     fuse_final_big_kernel<64><<<FINAL_BIG_BLOCKS, 32, 0, st>>>(pieces, n_pieces, tsel_idx, tsel_cos, stride_t,
-                                                                lsel_idx, lsel_cos, stride_l, emit, n_big, big_rows);
+                                                                lsel_idx, lsel_cos, stride_l, emit, n_big, big_rows,
+                                                                n_overflow, overflow_rows);
     return cudaGetLastError();
 }
 
