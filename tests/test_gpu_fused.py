@@ -12,8 +12,11 @@ tensor-core values, so their lists -- and everything after them -- must be
 bitwise equal, in every precision, graph-captured or not, over scenes of one
 tile, a ragged last sample tile, several sample tiles and rows longer than
 the shared-memory select.  A scene whose sample tiles hold a class the queries
-never ask for overflows the kept-entry buffers on purpose: those rows are
-recomputed exactly and the result must still match the oracle.
+never ask for overflows the kept-entry buffers on purpose, and one whose
+queried class sits in the sample tiles makes the optimistic threshold fall
+short on purpose: those rows are recomputed exactly and the result must
+still match the oracle.  The learned path's two-pass selection (no sample;
+every tile's group maxima) must equal its unfused selection bitwise.
 """
 import dataclasses
 import math
@@ -213,3 +216,39 @@ def test_learned_two_pass_equals_unfused(F, big, graph):
         two = _run(F, ctx, qb, code, None, graph=graph)    # (the first batch of a class tunes the tiles)
     assert F.farm_select_fallbacks(ctx) == 0
     _same(two, _run(F, ctx, qb, code, False))
+
+
+def test_optimistic_threshold_that_falls_short_is_recomputed(F):
+    """The fused selection sets a target row's threshold at the sample's k-th
+    entry (k < R), trusting that the rest of the row holds R - k more; a scene
+    whose queried class sits almost entirely in the sample tiles breaks that
+    trust on purpose: fuse_final must find fewer than R words reaching the
+    threshold, leave every such row to the exact fallback, and the results
+    must still match the oracle."""
+    n, fs = 4096, STRIDE["fp32"]
+    base = synth.make_scene(91, n, DIM, extent=(30.0, 30.0, 4.0), n_classes=2, n_views=4)
+    rng = np.random.default_rng(92)
+    in_sample = (np.arange(n) // 256) % fs == 0
+    cls = np.where(in_sample, 0, 1)
+    cls[rng.choice(np.flatnonzero(~in_sample), 40, replace=False)] = 0      # a few of the class elsewhere
+    cls = cls.astype(np.int32)
+    desc = base.centroids[cls] + base.noise_sigma * rng.standard_normal((n, DIM))
+    desc = (desc / np.linalg.norm(desc, axis=1, keepdims=True)).astype(np.float32)
+    sc = dataclasses.replace(base, desc=desc, cls=cls)
+    qb = synth.make_queries(93, sc, 32, m_choices=(1, 2))
+    t = base.centroids[0] + base.noise_sigma * rng.standard_normal((qb.n_q, DIM))
+    qb.tgt_emb = (t / np.linalg.norm(t, axis=1, keepdims=True)).astype(np.float32)
+    qb.tgt_cls = np.zeros(qb.n_q, np.int32)
+    ctx = F.farm_create(0)
+    try:
+        F.farm_memory_upload(ctx, 0, sc.desc, sc.cls, sc.box, sc.views)
+        F.farm_select_fallbacks(ctx, reset=True)
+        out, (t, l) = _run(F, ctx, qb, F.PREC_FP32, True)
+        recomputed = F.farm_select_fallbacks(ctx)
+    finally:
+        F.farm_destroy(ctx)
+    assert recomputed >= qb.n_q, recomputed          # every target row fell short
+    rep = parity.check_topk(sc, qb, 10, out["idx"], out["score"], out["pred"], out["anchor"])
+    assert rep.ok(), rep.summary()
+    fails = parity.check_candidates(sc, qb, t, l)
+    assert not fails, fails[:3]
