@@ -248,20 +248,42 @@ select_thresh_list_kernel(const float *__restrict__ S, const float *__restrict__
 
 // ---------------------------------------------------------------------------
 // Warp-level select: one warp per row for the common case -- a list of at
-// most WS_R entries, at most 1,024 group maxima (or, for a row with fewer
-// group maxima than its list length, at most 1,024 entries, ranked
-// directly) -- with no block barriers.
-// The R-th largest group-maximum key T is found by a bitwise search (the
-// largest T with #{keys >= T} >= R), the groups whose maximum reaches it are
-// gathered, and the candidates are ranked by counting (their words are all
+// most WS_R entries, at most 4,096 group maxima keyed as at most 1,024 keys
+// (maxima of 1, 2 or 4 consecutive groups; or, for a row with fewer group
+// maxima than its list length, at most 1,024 entries, ranked directly) --
+// with no block barriers.
+// The R-th largest key T is found by a bitwise search (the largest T with
+// #{keys >= T} >= R), the groups whose maximum reaches it are gathered, and
+// the candidates are sorted by a warp bitonic sort (their words are all
 // distinct).  A row outside these limits, or whose groups or candidates
 // overflow the warp's buffers, is appended to row_list for the block-level
 // select.
 constexpr int WS_R = 256;       // longest list a warp selects (the BF16 path's 256 candidates)
-constexpr int WS_KPL = 32;      // group maxima per lane (1,024 per row)
-constexpr int WS_GL = 320;      // qualifying groups per warp
+constexpr int WS_KPL = 32;      // keys per lane (1,024 per row)
+constexpr int WS_GL = 448;      // qualifying groups per warp
 constexpr int WS_CAP = 512;     // candidate words per warp
 constexpr int WW = 8;           // warps (rows) per CTA
+constexpr int WS_GU = 8;        // float4 loads in flight per lane while gathering the groups
+
+// Descending bitonic sort of P words (a power of two, at least 2) by one
+// warp, each lane taking compare-exchange pairs (a, a + j) of every stage.
+__device__ __forceinline__ void warp_bitonic_desc(uint64_t *w, int P, int lane)
+{
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = lane; p < (P >> 1); p += 32) {
+                const int a = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+                const uint64_t x = w[a], y = w[a + j];
+                const bool desc = (a & k) == 0;
+                if (desc ? (x < y) : (x > y)) {
+                    w[a] = y;
+                    w[a + j] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
 
 __global__ void __launch_bounds__(WW * 32, 4)
 select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, const Piece *__restrict__ pieces,
@@ -298,16 +320,39 @@ select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, 
     // a row with fewer group maxima than R (a short row) ranks its entries
     // themselves: their R-th largest key, then every entry reaching it
     const bool entries = n_groups < R;
-    if (R > WS_R || (entries ? (int64_t)n : n_groups) > 32 * WS_KPL) { hand_on(); return; }
-    const int U = entries ? n : (int)n_groups;
+    // a row of more than 1,024 group maxima keys the maxima of 2 or 4
+    // consecutive groups instead (super-groups: entries of the row too, one
+    // per super-group, so their R-th largest still bounds the row's from below)
+    int sgs = 0;
+    if (!entries)
+        while (sgs < 2 && ((n_groups + (1 << sgs) - 1) >> sgs) > 32 * WS_KPL) ++sgs;
+    const int64_t n_keys = entries ? (int64_t)n : (n_groups + (1 << sgs) - 1) >> sgs;
+    if (R > WS_R || n_keys > 32 * WS_KPL || n_keys < R) { hand_on(); return; }
+    const int U = (int)n_keys;
     const int kpl = (U + 31) >> 5;
     const float *row = S + pc.s_off + (int64_t)i * pc.ld;
+    // (a row of maxima is 16-byte aligned and holds whole tiles' groups, -inf
+    // past the row end, so the 2- and 4-wide loads stay inside it)
     const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(n, gshift);
     uint32_t key[WS_KPL];
 #pragma unroll
     for (int k = 0; k < WS_KPL; ++k) {
         const int g = lane + 32 * k;
-        key[k] = (k < kpl && g < U) ? order_key(entries ? __ldcs(row + g) : __ldg(tp + g)) : 0u;  // 0: no value
+        uint32_t kk = 0u;   // 0: no value
+        if (k < kpl && g < U) {
+            if (entries) {
+                kk = order_key(__ldcs(row + g));
+            } else if (sgs == 0) {
+                kk = order_key(__ldg(tp + g));
+            } else if (sgs == 1) {
+                const float2 v = __ldg(reinterpret_cast<const float2 *>(tp) + g);
+                kk = order_key(fmaxf(v.x, v.y));
+            } else {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(tp) + g);
+                kk = order_key(fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+            }
+        }
+        key[k] = kk;
     }
     // T: the R-th largest key.  It lies between the smallest and the largest
     // key, so it shares their common leading bits; the search sets the bits
@@ -362,53 +407,76 @@ select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, 
             cnt += __popc(bal);
         }
     } else {
-        // the groups whose maximum reaches T
+        // the groups whose maximum reaches T (those of the super-groups whose
+        // maximum does)
+        const float tau = key_value(T);
         int ng = 0;
 #pragma unroll
         for (int k = 0; k < WS_KPL; ++k) {
             if (k >= kpl) break;
-            const bool q = key[k] >= T;
-            const unsigned bal = __ballot_sync(FULL, q);
-            if (q) {
-                const int pos = ng + __popc(bal & lt);
-                if (pos < WS_GL) glist[pos] = (uint32_t)(lane + 32 * k);
+            const bool qs = key[k] >= T;
+            if (sgs == 0) {
+                const unsigned bal = __ballot_sync(FULL, qs);
+                if (qs) {
+                    const int pos = ng + __popc(bal & lt);
+                    if (pos < WS_GL) glist[pos] = (uint32_t)(lane + 32 * k);
+                }
+                ng += __popc(bal);
+            } else if (__any_sync(FULL, qs)) {
+                for (int c = 0; c < (1 << sgs); ++c) {
+                    const int g = ((lane + 32 * k) << sgs) + c;
+                    const bool q = qs && g < n_groups && __ldg(tp + g) >= tau;
+                    const unsigned bal = __ballot_sync(FULL, q);
+                    if (q) {
+                        const int pos = ng + __popc(bal & lt);
+                        if (pos < WS_GL) glist[pos] = (uint32_t)g;
+                    }
+                    ng += __popc(bal);
+                }
             }
-            ng += __popc(bal);
         }
         if (ng > WS_GL) { hand_on(); return; }
         __syncwarp();
-        // their entries >= tau
-        const float tau = key_value(T);
-        const int gmask = (1 << gshift) - 1;
-        const int slots = ng << gshift;
-        for (int s0 = 0; s0 < slots; s0 += 32 * 4) {
-            float x[4];
-            int j[4];
+        // their entries >= tau, read as float4 slots (a group of 32 is eight
+        // slots, of 8 two; group starts are 32-byte aligned and a row holds
+        // round_up(n, 32) floats, so a slot never leaves it), WS_GU slots in
+        // flight per lane
+        const int sshift = gshift - 2;
+        const int smask = (1 << sshift) - 1;
+        const int slots = ng << sshift;
+        for (int s0 = 0; s0 < slots; s0 += 32 * WS_GU) {
+            float4 v[WS_GU];
+            int j4[WS_GU];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < WS_GU; ++u) {
                 const int sl = s0 + 32 * u + lane;
-                j[u] = -1;
-                if (sl < slots) {
-                    const int jj = (int)((glist[sl >> gshift] << gshift) + (sl & gmask));
-                    if (jj < n) j[u] = jj;
-                }
-                x[u] = j[u] >= 0 ? __ldcs(row + j[u]) : 0.f;
+                j4[u] = sl < slots ? (int)((glist[sl >> sshift] << gshift) + ((sl & smask) << 2)) : n;
+                v[u] = j4[u] < n ? __ldcs(reinterpret_cast<const float4 *>(row + j4[u])) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool q = j[u] >= 0 && x[u] >= tau;
-                const unsigned bal = __ballot_sync(FULL, q);
-                if (q) {
-                    const int pos = cnt + __popc(bal & lt);
-                    if (pos < WS_CAP) cand[pos] = cand_word(order_key(x[u]), j[u]);
+            for (int u = 0; u < WS_GU; ++u) {
+                const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const bool q = j4[u] + c < n && x[c] >= tau;
+                    const unsigned bal = __ballot_sync(FULL, q);
+                    if (q) {
+                        const int pos = cnt + __popc(bal & lt);
+                        if (pos < WS_CAP) cand[pos] = cand_word(order_key(x[c]), j4[u] + c);
+                    }
+                    cnt += __popc(bal);
                 }
-                cnt += __popc(bal);
             }
         }
     }
     if (cnt > WS_CAP || cnt < R) { hand_on(); return; }
+    // sort the candidate words (distinct: distinct positions), padded with
+    // zero words to a power of two, in descending order
+    int P = 32;
+    while (P < cnt) P <<= 1;
+    for (int k = cnt + lane; k < P; k += 32) cand[k] = 0ull;
     __syncwarp();
-    // rank by counting: the words are distinct (distinct positions)
+    warp_bitonic_desc(cand, P, lane);
     int32_t *oi;
     float *oc;
     int stride;
@@ -423,14 +491,10 @@ select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, 
         oc = lsel_cos ? lsel_cos + o : nullptr;
         stride = stride_l;
     }
-    for (int ci = lane; ci < cnt; ci += 32) {
-        const uint64_t w = cand[ci];
-        int r = 0;
-        for (int k = 0; k < cnt; ++k) r += cand[k] > w ? 1 : 0;
-        if (r < R) {
-            oi[r] = (int32_t)(0xffffffffu - (uint32_t)(w & 0xffffffffu));
-            if (oc) oc[r] = key_value((uint32_t)(w >> 32));
-        }
+    for (int r = lane; r < R; r += 32) {
+        const uint64_t w = cand[r];
+        oi[r] = (int32_t)(0xffffffffu - (uint32_t)(w & 0xffffffffu));
+        if (oc) oc[r] = key_value((uint32_t)(w >> 32));
     }
     for (int k = R + lane; k < stride; k += 32) {
         oi[k] = -1;

@@ -178,11 +178,12 @@ def test_overflowing_rows_are_recomputed_exactly(F, prec):
 @pytest.fixture(scope="module")
 def big(F):
     """One scene of 70,000 objects (2,188 groups of 32 per row, at least four
-    times the learned path's target list of 512: the two-pass selection) and
-    one of 9,000 (the unfused learned selection) in the same batches."""
+    times the learned path's target list of 512: the two-pass selection), one
+    of 40,000 (1,250 groups) and one of 9,000 (the unfused learned selection)
+    in the same batches."""
     ctx = F.farm_create(0)
     scenes, parts = {}, []
-    for sid, n in [(80, 70000), (81, 9000)]:
+    for sid, n in [(80, 70000), (81, 9000), (82, 40000)]:
         sc = synth.make_scene(sid, n, DIM, extent=(90.0, 90.0, 8.0), n_classes=max(8, n // 50), n_views=4,
                               distractor_classes=4, distractor_frac=0.3)
         F.farm_memory_upload(ctx, sid, sc.desc, sc.cls, sc.box, sc.views)
@@ -216,6 +217,27 @@ def test_learned_two_pass_equals_unfused(F, big, graph):
         two = _run(F, ctx, qb, code, None, graph=graph)    # (the first batch of a class tunes the tiles)
     assert F.farm_select_fallbacks(ctx) == 0
     _same(two, _run(F, ctx, qb, code, False))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_long_rows_unfused_equal_fused(F, big, prec):
+    """Unfused, rows of 1,250 and 2,188 group maxima are keyed by the maxima
+    of 2 and 4 consecutive groups in the warp-level select (the groups of the
+    keys that reach the R-th largest key are gathered); the lists and results
+    must equal the fused selection's bitwise.  (BF16: the queries of the
+    scenes of at least 16,384 objects, which run the BF16 stage.)"""
+    ctx, scenes, qb = big
+    code = _code(F, prec)
+    F.farm_select_fallbacks(ctx, reset=True)
+    fused = _run(F, ctx, qb, code, True)
+    assert F.farm_select_fallbacks(ctx) == 0
+    unfused = _run(F, ctx, qb, code, False)
+    if prec == "bf16":
+        qs = np.flatnonzero([scenes[int(s)].n >= 16384 for s in qb.scene_of_q])
+        assert qs.size >= 90
+        _same(fused, unfused, qb, qs)
+    else:
+        _same(fused, unfused)
 
 
 def test_optimistic_threshold_that_falls_short_is_recomputed(F):
