@@ -51,7 +51,7 @@ class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region.
 
     nvidia-smi takes a while to start, so entering waits (at most 5 s) for its
-    first line; it then samples every 20 ms, and leaving waits (at most 1 s)
+    first line; it then samples every 5 ms, and leaving waits (at most 1 s)
     until at least one sample was taken after the region began, so that a
     region of a few tens of milliseconds still has one.  The summary uses the
     samples from the region's start on."""
@@ -71,7 +71,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "20"],
+                 "--format=csv,noheader,nounits", "-lms", "5"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -234,18 +234,14 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
         np.asarray(done), np.asarray(refs)
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the similarity kernel, from one ncu capture per (workload, precision, tile
-# variant), valid only while the kernel source is the one captured (sha256
-# prefix).
 # DRAM bytes of the similarity stage per step (both launches when the
 # selection is fused), captured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) for the kernel source whose sha256 prefix follows:
 # (workload, precision, tile variant, fused) -> bytes
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 2, True): (88.802560e6 + 113.844224e6) + (620.318976e6 + 29.381888e6),
+    ("site_n20k_d1152", "fp32", 2, True): (88.315904e6 + 115.206400e6) + (625.160704e6 + 23.487488e6),
 }
-SIM_TRAFFIC_SOURCE = "46d833a469c7bf4b"
+SIM_TRAFFIC_SOURCE = "9e576d6d8e0d50c4"
 
 
 def sim_traffic(workload, precision, variants, fused):

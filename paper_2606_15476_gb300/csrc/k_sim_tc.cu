@@ -62,7 +62,6 @@ namespace farm {
 namespace {
 
 constexpr int BM = kSimTileM;
-constexpr int THREADS = 192;
 constexpr int STAGE_BUDGET = 192 * 1024;     // shared memory for the operand pipeline
 constexpr uint32_t WAIT_LIMIT = 1u << 24;    // try_wait polls before giving up (about a second)
 constexpr int GROUP_M = 8;                   // tile raster: 8 cluster rows share each column tile
@@ -103,8 +102,11 @@ struct Elem<kSimFp8> {                       // FP8 E4M3
 // for a pair); PAIR: the two CTAs of a cluster compute one 256 x BN tile with
 // two-SM MMAs (cta_group::2), each holding its 128 rows of A and half of B.
 // Every CTA loads its own operand tiles: no copy is delivered to several CTAs.
-// EMIT_: the fused selection's epilogue, whose candidate slots (32 words per
-// epilogue thread, 32 KB) take the place of one pipeline stage.
+// EMIT_: the fused selection's epilogue, whose candidate slots (32 KB) take
+// the place of one pipeline stage.  Its folded FP32-accurate tiles (one tile
+// in TMEM) get eight epilogue warps, two per TMEM lane quarter, each taking
+// half of the tile's columns (16 slots per thread): the accumulator is held
+// for half as long, which is time the next tile's main products wait.
 template <int MODE, int BN_, int CM_, bool PAIR_ = false, bool EMIT_ = false>
 struct Cfg {
     using E = Elem<MODE>;
@@ -116,14 +118,17 @@ struct Cfg {
     static constexpr int B_PART = B_BYTES / CM_;                // this CTA's share of a B tile
     static constexpr int B_SMEM = PAIR_ ? B_PART : B_BYTES;     // B bytes a stage holds in this CTA
     static constexpr int STAGE_BYTES = OPS * (A_BYTES + B_SMEM);
-    static constexpr int EMIT_SLOTS = 32;
-    static constexpr int EMIT_BYTES = EMIT_ ? 4 * 32 * EMIT_SLOTS * 8 : 0;
-    static constexpr int BUDGET = STAGE_BUDGET - EMIT_BYTES;
-    static constexpr int STAGES = BUDGET / STAGE_BYTES < 8 ? BUDGET / STAGE_BYTES : 8;
     static constexpr int ACC_COLS = OPS * BN_;                  // TMEM columns of one tile's accumulators
     static constexpr int NACC = 512 / ACC_COLS >= 2 ? 2 : 1;    // tiles in flight in TMEM
-    static constexpr int STAGING_BYTES = 4 * 32 * 32 * 4;      // epilogue: one 32 x 32 FP32 block per warp
-    static constexpr int SCALE_BYTES = MODE == kSimFp8 ? 4 * BN_ * 4 : 0;   // FP8: a tile's column scales per warp
+    static constexpr bool FOLD = E::SPLIT && NACC == 1;         // the correction is folded into the main accumulator
+    static constexpr int EPI_WARPS = (EMIT_ && FOLD) ? 8 : 4;   // epilogue warps (two or one per TMEM lane quarter)
+    static constexpr int THREADS = 64 + 32 * EPI_WARPS;         // + the producer and MMA warps
+    static constexpr int EMIT_SLOTS = 32 * 4 / EPI_WARPS;       // candidate words per epilogue thread
+    static constexpr int EMIT_BYTES = EMIT_ ? EPI_WARPS * 32 * EMIT_SLOTS * 8 : 0;
+    static constexpr int BUDGET = STAGE_BUDGET - EMIT_BYTES;
+    static constexpr int STAGES = BUDGET / STAGE_BYTES < 8 ? BUDGET / STAGE_BYTES : 8;
+    static constexpr int STAGING_BYTES = EPI_WARPS * 32 * 32 * 4;      // epilogue: one 32 x 32 FP32 block per warp
+    static constexpr int SCALE_BYTES = MODE == kSimFp8 ? EPI_WARPS * BN_ * 4 : 0;   // FP8: a tile's column scales per warp
     static constexpr int SMEM_BYTES =
         STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES + SCALE_BYTES + EMIT_BYTES;
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
@@ -269,9 +274,9 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// 32 columns of the warp's 32 TMEM lanes (lane = row), without the wait.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32])
 {
-    uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -282,9 +287,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
           "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
           "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    tmem_ld32_issue(taddr, r);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Two 32-column loads behind one wait.
+__device__ __forceinline__ void tmem_ld32_pair(uint32_t ta, uint32_t tb, float (&v)[32], float (&w)[32])
+{
+    uint32_t r[32], q[32];
+    tmem_ld32_issue(ta, r);
+    tmem_ld32_issue(tb, q);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        v[i] = __uint_as_float(r[i]);
+        w[i] = __uint_as_float(q[i]);
+    }
 }
 
 // The pair's commit: arrives on the mbarrier at the offset of `bar` in both
@@ -443,7 +468,7 @@ __device__ __forceinline__ void store_rows_staged(float4 *blk, const float4 (&va
 }
 
 template <int MODE, int BN_, int CM_, bool GROUPED, bool PAIR, bool EMIT = false>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__((Cfg<MODE, BN_, CM_, PAIR, EMIT>::THREADS), 1)
 sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant__ CUtensorMap map_q1,
               const __grid_constant__ CUtensorMap map_d0, const __grid_constant__ CUtensorMap map_d1,
               const GemmPiece *__restrict__ pieces, int32_t n_pieces, const GemmPiece single,
@@ -464,7 +489,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     // columns, so the next tile's correction products (two thirds of its
     // MMAs) run while the main accumulator is drained to S (EMIT: compared
     // with the rows' thresholds).
-    constexpr bool FOLD = M::SPLIT && NACC == 1;
+    constexpr bool FOLD = C::FOLD;
     static_assert(!EMIT || GROUPED, "the fused selection runs grouped launches");
     constexpr uint32_t TMEM_ALLOC = 512;
     extern __shared__ uint8_t smem_raw[];
@@ -476,8 +501,8 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     float *staging = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256);
-    float *tile_scales = staging + 4 * 32 * 32;    // FP8 mode: [4 warps][BN]
-    // EMIT: [4 warps][32 lanes][EMIT_SLOTS] candidate words
+    float *tile_scales = staging + C::EPI_WARPS * 32 * 32;    // FP8 mode: [epilogue warps][BN]
+    // EMIT: [epilogue warps][32 lanes][EMIT_SLOTS] candidate words
     uint64_t *emit_slots = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(tile_scales) + C::SCALE_BYTES);
     uint64_t *corr_free = acc_empty + 1;      // FOLD: the correction columns are free (tile accumulators: one)
 
@@ -493,7 +518,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], PAIR ? 8 : 4);     // one arrival per epilogue warp (of both CTAs of a pair)
+            mbar_init(&acc_empty[b], (PAIR ? 2 : 1) * C::EPI_WARPS);   // one arrival per epilogue warp (of both CTAs of a pair)
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -689,12 +714,15 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             if (*abort_flag) atomicOr(err, kErrTimeout);
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31.  Each 32-row x
-        // 32-column block passes through the warp's shared-memory block (16-byte
-        // slots XOR-swizzled by row, conflict-free both ways) so that every
-        // store instruction writes four whole 128-byte row segments of S
-        // instead of 16 bytes in each of 32 rows.
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (with eight
+        // epilogue warps, warps w and w + 4 take the two halves of the
+        // columns).  Each 32-row x 32-column block passes through the warp's
+        // shared-memory block (16-byte slots XOR-swizzled by row, conflict-free
+        // both ways) so that every store instruction writes four whole 128-byte
+        // row segments of S instead of 16 bytes in each of 32 rows.
         const int quad = warp & 3;
+        constexpr int NCH = BN / 32 / (C::EPI_WARPS / 4);     // the warp's 32-column chunks
+        const int cbase = ((warp - 2) >> 2) * NCH;             // its first chunk
         float4 *blk = reinterpret_cast<float4 *>(staging + (warp - 2) * 32 * 32);
         const int sub = lane >> 3, slot = lane & 7;    // read-back: row sub + 4i, 16-byte slot
         uint32_t tc = 0;
@@ -714,24 +742,46 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
+            // EMIT with FOLD: the warp's folded chunks stay in registers and both
+            // accumulators are released at once, before the compares
+            constexpr bool REGS = EMIT && FOLD;
+            float fv[REGS ? NCH : 1][32];
             if (FOLD) {
-                // main += 2^-11 correction, in place; then the correction columns are free
+                // main += 2^-11 correction (in place, or into registers); then the
+                // correction columns are free
                 const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16);
+                if constexpr (REGS) {
 #pragma unroll
-                for (int c = 0; c < BN / 32; ++c) {
-                    float v[32], w[32];
-                    tmem_ld32(tb + (uint32_t)(c * 32), v);
-                    tmem_ld32(tb + ACC_CORR + (uint32_t)(c * 32), w);
+                    for (int cc = 0; cc < NCH; ++cc) {
+                        const uint32_t ta = tb + (uint32_t)((cbase + cc) * 32);
+                        float w[32];
+                        tmem_ld32_pair(ta, ta + ACC_CORR, fv[cc], w);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] = fmaf(w[i], RESID_SCALE_INV, v[i]);
-                    tmem_st32(tb + (uint32_t)(c * 32), v);
+                        for (int i = 0; i < 32; ++i) fv[cc][i] = fmaf(w[i], RESID_SCALE_INV, fv[cc][i]);
+                    }
+                } else {
+#pragma unroll
+                    for (int cc = 0; cc < NCH; ++cc) {
+                        const int c = cbase + cc;
+                        float v[32], w[32];
+                        tmem_ld32(tb + (uint32_t)(c * 32), v);
+                        tmem_ld32(tb + ACC_CORR + (uint32_t)(c * 32), w);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = fmaf(w[i], RESID_SCALE_INV, v[i]);
+                        tmem_st32(tb + (uint32_t)(c * 32), v);
+                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 }
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncwarp();
                 if (lane == 0) {
-                    if (PAIR && rank != 0) mbar_arrive_remote(cluster_addr(smem_u32(corr_free), 0u));
-                    else mbar_arrive(corr_free);
+                    if (PAIR && rank != 0) {
+                        mbar_arrive_remote(cluster_addr(smem_u32(corr_free), 0u));
+                        if (REGS) mbar_arrive_remote(cluster_addr(smem_u32(&acc_empty[buf]), 0u));
+                    } else {
+                        mbar_arrive(corr_free);
+                        if (REGS) mbar_arrive(&acc_empty[buf]);
+                    }
                 }
             }
             const GemmPiece pc = piece_of<GROUPED>(tile, pieces, n_pieces, single);
@@ -759,8 +809,15 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 uint64_t *slotw = emit_slots + ((warp - 2) * 32 + lane) * SLOTS;
                 float *vst = staging + (warp - 2) * 32 * 32 + lane * 32;   // 32 floats, 16-byte slots swizzled
                 const float sr = (MODE == kSimFp8 && live) ? scale_q[pc.q_row0 + r] : 1.f;
-                // the row's values of column chunk c (32 objects from n0 + 32 c)
-                auto chunk = [&](int c, float (&v)[32]) {
+                // the row's values of the warp's column chunk cc (32 objects from
+                // n0 + 32 (cbase + cc))
+                auto chunk = [&](int cc, float (&v)[32]) {
+                    if constexpr (REGS) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = fv[cc][i];
+                        return;
+                    }
+                    const int c = cbase + cc;
                     const uint32_t lane_addr = tmem + buf * (uint32_t)C::ACC_COLS + ((uint32_t)(quad * 32) << 16) +
                                                (uint32_t)(c * 32);
                     tmem_ld32(lane_addr, v);
@@ -783,19 +840,20 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 const bool dead = tk == 0xffffffffu;
                 const bool all_pass = tk == 0u;     // a sample shorter than the list: every entry
                 const float tf = (dead || all_pass) ? 0.f : key_value(tk);
-                uint32_t masks[BN / 32];
+                uint32_t masks[NCH];
                 int nh = 0;
 #pragma unroll
-                for (int c = 0; c < BN / 32; ++c) {
+                for (int cc = 0; cc < NCH; ++cc) {
+                    const int c = cbase + cc;
                     float v[32];
-                    chunk(c, v);
+                    chunk(cc, v);
                     const int64_t obj0 = (int64_t)n0 + c * 32;
                     uint32_t hit = 0u;
 #pragma unroll
                     for (int i = 0; i < 32; ++i) hit |= (v[i] >= tf || all_pass) ? (1u << i) : 0u;
                     if (obj0 + 32 > n) hit &= obj0 >= n ? 0u : (0xffffffffu >> (32 - (int)(n - obj0)));
                     if (dead) hit = 0u;
-                    masks[c] = hit;
+                    masks[cc] = hit;
                     if (hit) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
@@ -817,16 +875,17 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 const bool over = nh > SLOTS;
                 if (__any_sync(0xffffffffu, over)) {
                     int pos = over ? atomicAdd(emit.cnt + grow, nh) : 0;
-#pragma unroll 1
-                    for (int c = 0; c < BN / 32; ++c) {
-                        if (!__any_sync(0xffffffffu, over && masks[c] != 0u)) continue;    // tcgen05.ld is warp-wide
+#pragma unroll
+                    for (int cc = 0; cc < NCH; ++cc) {
+                        const int c = cbase + cc;
+                        if (!__any_sync(0xffffffffu, over && masks[cc] != 0u)) continue;    // tcgen05.ld is warp-wide
                         float v[32];
-                        chunk(c, v);
+                        chunk(cc, v);
                         if (!over) continue;
                         const int64_t obj0 = (int64_t)n0 + c * 32;
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
-                            if ((masks[c] >> i) & 1u) {
+                            if ((masks[cc] >> i) & 1u) {
                                 if (pos < emit.cap)
                                     dst[pos] = ((uint64_t)order_key(v[i]) << 32) |
                                                (uint64_t)(0xffffffffu - (uint32_t)(obj0 + i));
@@ -835,11 +894,13 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                         }
                     }
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncwarp();
-                if (lane == 0) {
-                    if (PAIR && rank != 0) mbar_arrive_remote(cluster_addr(smem_u32(&acc_empty[buf]), 0u));
-                    else mbar_arrive(&acc_empty[buf]);
+                if constexpr (!REGS) {
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (PAIR && rank != 0) mbar_arrive_remote(cluster_addr(smem_u32(&acc_empty[buf]), 0u));
+                        else mbar_arrive(&acc_empty[buf]);
+                    }
                 }
                 if (nh > 0 && !over) {
                     const int pos = atomicAdd(emit.cnt + grow, nh);
@@ -1022,7 +1083,7 @@ cudaError_t launch_impl(const CUtensorMap &mq0, const CUtensorMap &mq1, const CU
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(THREADS);
+    cfg.blockDim = dim3(C::THREADS);
     cfg.dynamicSmemBytes = smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
