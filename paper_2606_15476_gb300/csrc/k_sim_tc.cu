@@ -103,10 +103,11 @@ struct Elem<kSimFp8> {                       // FP8 E4M3
 // two-SM MMAs (cta_group::2), each holding its 128 rows of A and half of B.
 // Every CTA loads its own operand tiles: no copy is delivered to several CTAs.
 // EMIT_: the fused selection's epilogue, whose candidate slots (32 KB) take
-// the place of one pipeline stage.  Its folded FP32-accurate tiles (one tile
-// in TMEM) get eight epilogue warps, two per TMEM lane quarter, each taking
-// half of the tile's columns (16 slots per thread): the accumulator is held
-// for half as long, which is time the next tile's main products wait.
+// the place of one pipeline stage.  Folded FP32-accurate tiles (one tile in
+// TMEM) get eight epilogue warps, two per TMEM lane quarter, each taking half
+// of the tile's columns into registers (16 candidate slots per thread) and
+// releasing the accumulators before it compares or stores: the next tile's
+// main products wait only for the TMEM loads.
 template <int MODE, int BN_, int CM_, bool PAIR_ = false, bool EMIT_ = false>
 struct Cfg {
     using E = Elem<MODE>;
@@ -121,7 +122,7 @@ struct Cfg {
     static constexpr int ACC_COLS = OPS * BN_;                  // TMEM columns of one tile's accumulators
     static constexpr int NACC = 512 / ACC_COLS >= 2 ? 2 : 1;    // tiles in flight in TMEM
     static constexpr bool FOLD = E::SPLIT && NACC == 1;         // the correction is folded into the main accumulator
-    static constexpr int EPI_WARPS = (EMIT_ && FOLD) ? 8 : 4;   // epilogue warps (two or one per TMEM lane quarter)
+    static constexpr int EPI_WARPS = FOLD ? 8 : 4;              // epilogue warps (two or one per TMEM lane quarter)
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;         // + the producer and MMA warps
     static constexpr int EMIT_SLOTS = 32 * 4 / EPI_WARPS;       // candidate words per epilogue thread
     static constexpr int EMIT_BYTES = EMIT_ ? EPI_WARPS * 32 * EMIT_SLOTS * 8 : 0;
@@ -742,9 +743,10 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // EMIT with FOLD: the warp's folded chunks stay in registers and both
-            // accumulators are released at once, before the compares
-            constexpr bool REGS = EMIT && FOLD;
+            // FOLD with eight epilogue warps: the warp's folded chunks stay in
+            // registers and both accumulators are released at once, before the
+            // compares or stores
+            constexpr bool REGS = FOLD && C::EPI_WARPS == 8;
             float fv[REGS ? NCH : 1][32];
             if (FOLD) {
                 // main += 2^-11 correction (in place, or into registers); then the
@@ -925,18 +927,24 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                 __syncwarp();
             }
             const bool keep_tops = tops != nullptr && pc.tops_off >= 0;    // uniform across the warp
-            float gmax[BN / 8];      // maximum of each 8-column group of row r in this tile
+            float gmax[NCH * 4];     // maximum of each 8-column group of row r in the warp's columns
 #pragma unroll
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int cc = 0; cc < NCH; ++cc) {
+                const int c = cbase + cc;
                 float v[32];
-                const uint32_t lane_addr = tmem + buf * (uint32_t)C::ACC_COLS + ((uint32_t)(quad * 32) << 16) +
-                                           (uint32_t)(c * 32);
-                tmem_ld32(lane_addr, v);
-                if (MODE == kSimF16x3 && !FOLD) {
-                    float w[32];
-                    tmem_ld32(lane_addr + ACC_CORR, w);
+                if constexpr (REGS) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] = fmaf(w[i], RESID_SCALE_INV, v[i]);
+                    for (int i = 0; i < 32; ++i) v[i] = fv[cc][i];
+                } else {
+                    const uint32_t lane_addr = tmem + buf * (uint32_t)C::ACC_COLS + ((uint32_t)(quad * 32) << 16) +
+                                               (uint32_t)(c * 32);
+                    tmem_ld32(lane_addr, v);
+                    if (MODE == kSimF16x3 && !FOLD) {
+                        float w[32];
+                        tmem_ld32(lane_addr + ACC_CORR, w);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = fmaf(w[i], RESID_SCALE_INV, v[i]);
+                    }
                 }
                 const int64_t col0 = (int64_t)c0 + c * 32;      // stored column
                 if (MODE == kSimFp8 && live) {
@@ -963,7 +971,7 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                             for (int i = 0; i < 8; ++i)
                                 if (col0 + 8 * g + i < ns_) m = fmaxf(m, v[8 * g + i]);
                         }
-                        gmax[4 * c + g] = m;
+                        gmax[4 * cc + g] = m;
                     }
                 }
                 if (!store) continue;
@@ -993,16 +1001,17 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
             if (keep_tops) {
                 const int64_t gs = group_stride(ns_, pc.gshift);
                 float *tblk = tops + pc.tops_off + r_blk * gs;
+                // (the warp's groups start at group c0 / 8 + 4 cbase, of 32: c0 / 32 + cbase)
                 if (pc.gshift == kGroupShiftSmall) {
-                    float4 t4[BN / 32];
+                    float4 t4[NCH];
 #pragma unroll
-                    for (int j = 0; j < BN / 32; ++j)
+                    for (int j = 0; j < NCH; ++j)
                         t4[j] = make_float4(gmax[4 * j], gmax[4 * j + 1], gmax[4 * j + 2], gmax[4 * j + 3]);
-                    store_rows_staged<BN / 32>(blk, t4, lane, tblk + c0 / 8, gs, rows - r_blk);
+                    store_rows_staged<NCH>(blk, t4, lane, tblk + c0 / 8 + 4 * cbase, gs, rows - r_blk);
                 } else {
-                    float4 t4[BN / 128];
+                    float4 t4[NCH / 4];
 #pragma unroll
-                    for (int j = 0; j < BN / 128; ++j) {
+                    for (int j = 0; j < NCH / 4; ++j) {
                         float g4[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
@@ -1010,14 +1019,16 @@ sim_tc_kernel(const __grid_constant__ CUtensorMap map_q0, const __grid_constant_
                                           fmaxf(gmax[16 * j + 4 * u + 2], gmax[16 * j + 4 * u + 3]));
                         t4[j] = make_float4(g4[0], g4[1], g4[2], g4[3]);
                     }
-                    store_rows_staged<BN / 128>(blk, t4, lane, tblk + c0 / 32, gs, rows - r_blk);
+                    store_rows_staged<NCH / 4>(blk, t4, lane, tblk + c0 / 32 + cbase, gs, rows - r_blk);
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncwarp();
-            if (lane == 0) {
-                if (PAIR && rank != 0) mbar_arrive_remote(cluster_addr(smem_u32(&acc_empty[buf]), 0u));
-                else mbar_arrive(&acc_empty[buf]);
+            if constexpr (!REGS) {
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) {
+                    if (PAIR && rank != 0) mbar_arrive_remote(cluster_addr(smem_u32(&acc_empty[buf]), 0u));
+                    else mbar_arrive(&acc_empty[buf]);
+                }
             }
         }
     }
