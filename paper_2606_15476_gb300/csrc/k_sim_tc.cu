@@ -107,7 +107,7 @@ struct Elem<kSimFp8> {                       // FP8 E4M3
 // TMEM) get eight epilogue warps, two per TMEM lane quarter, each taking half
 // of the tile's columns into registers (16 candidate slots per thread) and
 // releasing the accumulators before it compares or stores: the next tile's
-// main products wait only for the TMEM loads.
+// main products wait only for the TMEM loads.  FP8 tiles get eight warps too.
 template <int MODE, int BN_, int CM_, bool PAIR_ = false, bool EMIT_ = false>
 struct Cfg {
     using E = Elem<MODE>;
@@ -122,16 +122,20 @@ struct Cfg {
     static constexpr int ACC_COLS = OPS * BN_;                  // TMEM columns of one tile's accumulators
     static constexpr int NACC = 512 / ACC_COLS >= 2 ? 2 : 1;    // tiles in flight in TMEM
     static constexpr bool FOLD = E::SPLIT && NACC == 1;         // the correction is folded into the main accumulator
-    static constexpr int EPI_WARPS = FOLD ? 8 : 4;              // epilogue warps (two or one per TMEM lane quarter)
+    // epilogue warps, two or one per TMEM lane quarter: eight for the 256-object
+    // tiles whose epilogue bounds the tile (FP32-accurate tiles, which hold
+    // TMEM alone; FP8, whose MMAs are few); BF16 tiles overlap four warps'
+    // epilogue with the next tile's MMAs
+    static constexpr int EPI_WARPS = BN_ == 256 && (FOLD || MODE == kSimFp8) ? 8 : 4;
     static constexpr int THREADS = 64 + 32 * EPI_WARPS;         // + the producer and MMA warps
     static constexpr int EMIT_SLOTS = 32 * 4 / EPI_WARPS;       // candidate words per epilogue thread
     static constexpr int EMIT_BYTES = EMIT_ ? EPI_WARPS * 32 * EMIT_SLOTS * 8 : 0;
-    static constexpr int BUDGET = STAGE_BUDGET - EMIT_BYTES;
-    static constexpr int STAGES = BUDGET / STAGE_BYTES < 8 ? BUDGET / STAGE_BYTES : 8;
     static constexpr int STAGING_BYTES = EPI_WARPS * 32 * 32 * 4;      // epilogue: one 32 x 32 FP32 block per warp
     static constexpr int SCALE_BYTES = MODE == kSimFp8 ? EPI_WARPS * BN_ * 4 : 0;   // FP8: a tile's column scales per warp
-    static constexpr int SMEM_BYTES =
-        STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES + SCALE_BYTES + EMIT_BYTES;
+    static constexpr int FIXED_BYTES = 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES + SCALE_BYTES + EMIT_BYTES;
+    static constexpr int BUDGET = STAGE_BUDGET < 227 * 1024 - FIXED_BYTES ? STAGE_BUDGET : 227 * 1024 - FIXED_BYTES;
+    static constexpr int STAGES = BUDGET / STAGE_BYTES < 8 ? BUDGET / STAGE_BYTES : 8;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + FIXED_BYTES;
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
     static_assert(BN_ % 128 == 0 && BN_ <= 256, "tile width");
     static_assert(STAGES >= 3, "pipeline depth");
