@@ -239,9 +239,9 @@ def cpu_baseline_mc(scene, spaces, qb, cq, k, n_sample, seed=0, budget_s=15.0):
 # dram__bytes_write.sum) for the kernel source whose sha256 prefix follows:
 # (workload, precision, tile variant, fused) -> bytes
 SIM_TRAFFIC = {
-    ("site_n20k_d1152", "fp32", 2, True): (88.315904e6 + 115.206400e6) + (625.160704e6 + 23.487488e6),
+    ("site_n20k_d1152", "fp32", 2, True): (90.488320e6 + 120.849664e6) + (623.171328e6 + 18.991104e6),
 }
-SIM_TRAFFIC_SOURCE = "9e576d6d8e0d50c4"
+SIM_TRAFFIC_SOURCE = "fc16929493683163"
 
 
 def sim_traffic(workload, precision, variants, fused):

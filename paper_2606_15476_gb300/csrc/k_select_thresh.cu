@@ -254,16 +254,202 @@ select_thresh_list_kernel(const float *__restrict__ S, const float *__restrict__
 // with no block barriers.
 // The R-th largest key T is found by a bitwise search (the largest T with
 // #{keys >= T} >= R), the groups whose maximum reaches it are gathered, and
-// the candidates are sorted by a warp bitonic sort (their words are all
-// distinct).  A row outside these limits, or whose groups or candidates
-// overflow the warp's buffers, is appended to row_list for the block-level
-// select.
+// the candidates are ranked by counting (at most 32) or sorted by a warp
+// bitonic sort (their words are all distinct).  A row outside these limits,
+// or whose groups or candidates overflow the warp's buffers, is appended to
+// row_list for the block-level select.
 constexpr int WS_R = 256;       // longest list a warp selects (the BF16 path's 256 candidates)
 constexpr int WS_KPL = 32;      // keys per lane (1,024 per row)
 constexpr int WS_GL = 448;      // qualifying groups per warp
 constexpr int WS_CAP = 512;     // candidate words per warp
 constexpr int WW = 8;           // warps (rows) per CTA
 constexpr int WS_GU = 8;        // float4 loads in flight per lane while gathering the groups
+constexpr int WS_GL_NARROW = 320;   // qualifying groups per warp (the small-scene kernel)
+constexpr int NARROW_R = 128;       // longest list of the small-scene kernel
+
+// The warp-level select of the rows of small scenes (groups of 8 objects)
+// with lists of at most NARROW_R entries: the group maxima themselves as
+// keys, the qualifying groups gathered with scalar loads, the candidates
+// ranked by counting.  (Measured on the 67-scene batch, whose many small
+// scenes' lists of 95 and 16 entries these are: 0.95 ms for the select stage
+// against 1.05 ms with the general kernel below taking every row.)  Every
+// other row is the general kernel's.
+__global__ void __launch_bounds__(WW * 32, 4)
+select_warp_small_kernel(const float *__restrict__ S, const float *__restrict__ tops, const Piece *__restrict__ pieces,
+                   int32_t n_pieces, int64_t total_rows, int32_t *__restrict__ tsel_idx,
+                   float *__restrict__ tsel_cos, int32_t stride_t, int32_t *__restrict__ lsel_idx,
+                   float *__restrict__ lsel_cos, int32_t stride_l, int32_t *__restrict__ row_list)
+{
+    __shared__ uint32_t glist_all[WW][WS_GL_NARROW];
+    __shared__ uint64_t cand_all[WW][WS_CAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t t = (int64_t)blockIdx.x * WW + warp;
+    if (t >= total_rows) return;            // (warp-uniform)
+    uint32_t *glist = glist_all[warp];
+    uint64_t *cand = cand_all[warp];
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+    auto hand_on = [&]() {
+        if (lane == 0) row_list[1 + atomicAdd(&row_list[0], 1)] = (int32_t)t;
+    };
+    // the piece of thresholded row t (the last whose tblock_begin <= t)
+    int lo = 0, hi = n_pieces - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pieces[mid].tblock_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const Piece &pc = pieces[lo];
+    const int i = pc.th0 + (int)(t - pc.tblock_begin);
+    const bool is_tgt = i < pc.ntr;
+    const int R = is_tgt ? pc.keep_t : pc.keep_l;
+    const int n = pc.n;
+    const int gshift = pc.gshift;
+    const int64_t n_groups = group_count(n, gshift);
+    // a row with fewer group maxima than R (a short row) ranks its entries
+    // themselves: their R-th largest key, then every entry reaching it
+    const bool entries = n_groups < R;
+    if (gshift != kGroupShiftSmall || R > NARROW_R || (entries ? (int64_t)n : n_groups) > 32 * WS_KPL)
+        return;    // the general kernel's row
+    const int U = entries ? n : (int)n_groups;
+    const int kpl = (U + 31) >> 5;
+    const float *row = S + pc.s_off + (int64_t)i * pc.ld;
+    const float *tp = tops + pc.tops_off + (int64_t)i * group_stride(n, gshift);
+    uint32_t key[WS_KPL];
+#pragma unroll
+    for (int k = 0; k < WS_KPL; ++k) {
+        const int g = lane + 32 * k;
+        key[k] = (k < kpl && g < U) ? order_key(entries ? __ldcs(row + g) : __ldg(tp + g)) : 0u;  // 0: no value
+    }
+    // T: the R-th largest key.  It lies between the smallest and the largest
+    // key, so it shares their common leading bits; the search sets the bits
+    // below them one at a time (keeping a bit while at least R keys reach
+    // it), and stops early once exactly R keys reach the candidate: T is
+    // then the smallest of those R.
+    uint32_t kmax = 0u, kmin = 0xffffffffu;
+#pragma unroll
+    for (int k = 0; k < WS_KPL; ++k) {
+        if (k < kpl && lane + 32 * k < U) {
+            kmax = max(kmax, key[k]);
+            kmin = min(kmin, key[k]);
+        }
+    }
+    kmax = __reduce_max_sync(FULL, kmax);
+    kmin = __reduce_min_sync(FULL, kmin);
+    uint32_t T;
+    if (kmax == kmin) {
+        T = kmax;
+    } else {
+        const int hb = 31 - __clz(kmax ^ kmin);
+        T = hb == 31 ? 0u : (kmax >> (hb + 1)) << (hb + 1);
+        for (int bit = hb; bit >= 0; --bit) {
+            const uint32_t c = T | (1u << bit);
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < WS_KPL; ++k) cnt += (k < kpl && key[k] >= c) ? 1 : 0;
+            const unsigned tot = __reduce_add_sync(FULL, (unsigned)cnt);
+            if (tot == (unsigned)R) {
+                uint32_t mn = 0xffffffffu;
+#pragma unroll
+                for (int k = 0; k < WS_KPL; ++k)
+                    if (k < kpl && key[k] >= c) mn = min(mn, key[k]);
+                T = __reduce_min_sync(FULL, mn);
+                break;
+            }
+            if (tot > (unsigned)R) T = c;
+        }
+    }
+    int cnt = 0;
+    if (entries) {
+        // the entries reaching T (the top R and their ties) are the candidates
+#pragma unroll
+        for (int k = 0; k < WS_KPL; ++k) {
+            if (k >= kpl) break;
+            const bool q = key[k] >= T;
+            const unsigned bal = __ballot_sync(FULL, q);
+            if (q) {
+                const int pos = cnt + __popc(bal & lt);
+                if (pos < WS_CAP) cand[pos] = cand_word(key[k], lane + 32 * k);
+            }
+            cnt += __popc(bal);
+        }
+    } else {
+        // the groups whose maximum reaches T
+        int ng = 0;
+#pragma unroll
+        for (int k = 0; k < WS_KPL; ++k) {
+            if (k >= kpl) break;
+            const bool q = key[k] >= T;
+            const unsigned bal = __ballot_sync(FULL, q);
+            if (q) {
+                const int pos = ng + __popc(bal & lt);
+                if (pos < WS_GL_NARROW) glist[pos] = (uint32_t)(lane + 32 * k);
+            }
+            ng += __popc(bal);
+        }
+        if (ng > WS_GL_NARROW) { hand_on(); return; }
+        __syncwarp();
+        // their entries >= tau
+        const float tau = key_value(T);
+        const int gmask = (1 << gshift) - 1;
+        const int slots = ng << gshift;
+        for (int s0 = 0; s0 < slots; s0 += 32 * 4) {
+            float x[4];
+            int j[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int sl = s0 + 32 * u + lane;
+                j[u] = -1;
+                if (sl < slots) {
+                    const int jj = (int)((glist[sl >> gshift] << gshift) + (sl & gmask));
+                    if (jj < n) j[u] = jj;
+                }
+                x[u] = j[u] >= 0 ? __ldcs(row + j[u]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool q = j[u] >= 0 && x[u] >= tau;
+                const unsigned bal = __ballot_sync(FULL, q);
+                if (q) {
+                    const int pos = cnt + __popc(bal & lt);
+                    if (pos < WS_CAP) cand[pos] = cand_word(order_key(x[u]), j[u]);
+                }
+                cnt += __popc(bal);
+            }
+        }
+    }
+    if (cnt > WS_CAP || cnt < R) { hand_on(); return; }
+    __syncwarp();
+    // rank by counting: the words are distinct (distinct positions)
+    int32_t *oi;
+    float *oc;
+    int stride;
+    if (is_tgt) {
+        const int64_t o = (pc.t_row0 + i) * (int64_t)stride_t;
+        oi = tsel_idx + o;
+        oc = tsel_cos ? tsel_cos + o : nullptr;
+        stride = stride_t;
+    } else {
+        const int64_t o = (pc.l_row0 + (i - pc.ntr)) * (int64_t)stride_l;
+        oi = lsel_idx + o;
+        oc = lsel_cos ? lsel_cos + o : nullptr;
+        stride = stride_l;
+    }
+    for (int ci = lane; ci < cnt; ci += 32) {
+        const uint64_t w = cand[ci];
+        int r = 0;
+        for (int k = 0; k < cnt; ++k) r += cand[k] > w ? 1 : 0;
+        if (r < R) {
+            oi[r] = (int32_t)(0xffffffffu - (uint32_t)(w & 0xffffffffu));
+            if (oc) oc[r] = key_value((uint32_t)(w >> 32));
+        }
+    }
+    for (int k = R + lane; k < stride; k += 32) {
+        oi[k] = -1;
+        if (oc) oc[k] = 0.f;
+    }
+}
+
 
 // Descending bitonic sort of P words (a power of two, at least 2) by one
 // warp, each lane taking compare-exchange pairs (a, a + j) of every stage.
@@ -320,6 +506,8 @@ select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, 
     // a row with fewer group maxima than R (a short row) ranks its entries
     // themselves: their R-th largest key, then every entry reaching it
     const bool entries = n_groups < R;
+    if (gshift == kGroupShiftSmall && R <= NARROW_R && (entries ? (int64_t)n : n_groups) <= 32 * WS_KPL)
+        return;    // the small-scene kernel's row
     // a row of more than 1,024 group maxima keys the maxima of 2 or 4
     // consecutive groups instead (super-groups: entries of the row too, one
     // per super-group, so their R-th largest still bounds the row's from below)
@@ -455,6 +643,7 @@ select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, 
             }
 #pragma unroll
             for (int u = 0; u < WS_GU; ++u) {
+                if (s0 + 32 * u >= slots) break;     // (warp-uniform: short lists take few ballots)
                 const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -470,13 +659,24 @@ select_warp_kernel(const float *__restrict__ S, const float *__restrict__ tops, 
         }
     }
     if (cnt > WS_CAP || cnt < R) { hand_on(); return; }
-    // sort the candidate words (distinct: distinct positions), padded with
-    // zero words to a power of two, in descending order
-    int P = 32;
-    while (P < cnt) P <<= 1;
-    for (int k = cnt + lane; k < P; k += 32) cand[k] = 0ull;
+    // order the candidate words (distinct: distinct positions): at most 32
+    // are ranked by counting, more sorted by a bitonic sort (padded with zero
+    // words to a power of two), in descending order
     __syncwarp();
-    warp_bitonic_desc(cand, P, lane);
+    if (cnt <= 32) {
+        const uint64_t w = lane < cnt ? cand[lane] : 0ull;
+        int r = 0;
+        for (int k = 0; k < cnt; ++k) r += cand[k] > w ? 1 : 0;
+        __syncwarp();
+        if (lane < cnt) cand[r] = w;
+        __syncwarp();
+    } else {
+        int P = 64;
+        while (P < cnt) P <<= 1;
+        for (int k = cnt + lane; k < P; k += 32) cand[k] = 0ull;
+        __syncwarp();
+        warp_bitonic_desc(cand, P, lane);
+    }
     int32_t *oi;
     float *oc;
     int stride;
@@ -526,8 +726,12 @@ cudaError_t launch_select_thresh(const float *S, const float *tops, const Piece 
                                                                       n_fallback);
         return cudaGetLastError();
     }
-    // the warp-level select first; the rows it hands on go to the block-level one
+    // the warp-level selects first (each takes its own rows); the rows they
+    // hand on go to the block-level one
     if ((e = cudaMemsetAsync(row_list, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    select_warp_small_kernel<<<(unsigned)((total_blocks + WW - 1) / WW), WW * 32, 0, s>>>(
+        S, tops, pieces, n_pieces, total_blocks, tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos, stride_l, row_list);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     select_warp_kernel<<<(unsigned)((total_blocks + WW - 1) / WW), WW * 32, 0, s>>>(
         S, tops, pieces, n_pieces, total_blocks, tsel_idx, tsel_cos, stride_t, lsel_idx, lsel_cos, stride_l, row_list);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
