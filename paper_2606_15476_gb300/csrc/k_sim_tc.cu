@@ -24,9 +24,9 @@
 // FP32.  FP16 products run at twice the TF32 rate and the operands take half
 // the bytes of a TF32 split.
 //
-// Kernel organisation (persistent: one CTA of 192 threads per SM walks the
-// 128 x BN tiles of S; in a CTA pair the two CTAs of a cluster compute one
-// 256 x 256 tile together):
+// Kernel organisation (persistent: one CTA per SM -- 192 threads, or 320
+// with eight epilogue warps -- walks the 128 x BN tiles of S; in a CTA pair
+// the two CTAs of a cluster compute one 256 x 256 tile together):
 //   warp 0      TMA producer: for each K slice (32 FP16 values, 64-byte swizzle,
 //               four tiles q_hi, q_lo, d_hi, d_lo; or 64 BF16 / 128 FP8 values,
 //               128-byte swizzle, two tiles q, d) fills one pipeline stage,
@@ -40,15 +40,19 @@
 //               of kind::f16 (BF16) / kind::f8f6f4 (E4M3), and tcgen05.commit
 //               to the stage's "empty" mbarrier, finally to the "accumulator
 //               ready" mbarrier;
-//   warps 2-5   epilogue: tcgen05.ld 32 lanes x 32 columns at a time, each
-//               32 x 32 block staged through shared memory so that stores
-//               write whole row segments of S (bounds-checked), the group
-//               maxima likewise, then release the accumulator.  FP32-accurate
-//               mode at 256-object tiles first folds the correction into the
-//               main accumulator in TMEM and releases the correction columns,
-//               so the next tile's correction products overlap the stores.
-// Stages of 48 KB (32 KB in a pair) within 192 KB, plus 16 KB of epilogue
-// staging.  Every mbarrier wait is bounded: on expiry the kernel raises the
+//   warps 2-5   epilogue (warps 2-9 when eight: two per TMEM lane quarter,
+//               each taking half of the tile's columns): tcgen05.ld 32 lanes
+//               x 32 columns at a time, each 32 x 32 block staged through
+//               shared memory so that stores write whole row segments of S
+//               (bounds-checked), the group maxima likewise, then release the
+//               accumulator.  FP32-accurate mode at 256-object tiles (eight
+//               warps) folds the correction into registers and releases both
+//               accumulators before it stores or compares, so the next tile's
+//               MMAs wait only for the TMEM loads; FP8 tiles take eight warps
+//               too.
+// Stages of 48 KB (32 KB in a pair) within 192 KB, and no more than the
+// shared memory left beside 4 KB of epilogue staging per epilogue warp (and
+// the fused selection's candidate slots).  Every mbarrier wait is bounded: on expiry the kernel raises the
 // error flag, stops issuing work, waits (bounded) for the copies it issued,
 // frees its TMEM and returns.
 #include <algorithm>

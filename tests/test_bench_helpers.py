@@ -61,3 +61,11 @@ def test_traffic_is_reported_for_the_captured_source_only(monkeypatch):
     assert bench.sim_traffic(workload, prec, [variant], not fused) is None
     monkeypatch.setattr(bench, "SIM_TRAFFIC_SOURCE", "0" * 16)                         # another source
     assert bench.sim_traffic(workload, prec, [variant], fused) is None
+
+
+def test_code_digest_ignores_comments_only():
+    src = "// header\n__global__ void k(float *x) {\n    x[0] = 1.f;   // one\n    /* block\n comment */ x[1] = 2.f;\n}\n"
+    reworded = "// another header\n__global__ void k(float *x) {\n  x[0] = 1.f;\n  /* other */ x[1] = 2.f;   // two\n}\n"
+    changed = src.replace("2.f", "3.f")
+    assert bench.code_digest(src) == bench.code_digest(reworded)
+    assert bench.code_digest(src) != bench.code_digest(changed)
